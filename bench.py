@@ -1,0 +1,344 @@
+"""Benchmark: sampled edge-sketch pairs/s of the whole hot path on one GB300.
+
+One step = one pass of the whole path over the resident graph: build R sketches
+(hash sampling, batched union-find, compression, component histograms, initial gains,
+compact sketches), select k seeds with the device lazy greedy, and the spread of those seeds.
+value = m * R (sampled edge-sketch pairs) per step / step time, summed over ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload chunglu_n1M_m10M]
+
+Under torchrun every rank runs an independent replica of the workload (the path needs no
+exchange); rank 0 prints the JSON line with the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+import graphgen  # noqa: E402
+
+METRIC = "sampled edge-sketch pairs/s"
+DEFAULT_WORKLOAD = "chunglu_n1M_m10M"
+CPU_SAMPLE_SKETCHES = 32
+PROFILES = ROOT / "profiles"
+SRC = ROOT / "paper_2311_07554_gb300" / "csrc"
+
+
+# ------------------------------------------------------------------------------ helpers
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = Path(os.environ.get("TMPDIR", "/tmp")) / f"im_clocks_{os.getpid()}.csv"
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.path.read_text().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        try:
+            self.path.unlink()
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    f = ROOT / "MEASURED_PEAKS.json"
+    if f.exists():
+        d = json.loads(f.read_text())
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _src_digest(name: str) -> str:
+    return hashlib.sha1((SRC / name).read_bytes()).hexdigest()[:12]
+
+
+def _traffic(kernel: str, units_per_launch: float):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current source."""
+    f = PROFILES / "dram_traffic.json"
+    if not f.exists():
+        return None
+    try:
+        d = json.loads(f.read_text()).get(kernel)
+        if not d or d.get("source_sha1") != _src_digest(d["source"]):
+            return None
+        return d["bytes_per_unit"] * units_per_launch
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------------------- CPU baseline
+def cpu_sample(n, u, v, prm, sketches=CPU_SAMPLE_SKETCHES):
+    """The oracle on a bounded sample: the first `sketches` sketches of the workload, all
+    steps of the path (labels, gains, compact sketches, greedy, spread)."""
+    import oracle
+    threads = oracle.max_threads()
+    t0 = time.perf_counter()
+    G = oracle.Graph(n, u, v)
+    L = G.labels(prm["seed"], prm["p"], sketches, threads=threads)
+    oracle.gains(L)
+    ctr = oracle.centers(n, prm["seed"], prm["alpha"])
+    oracle.compact(L, ctr)
+    seeds, _ = oracle.greedy(L, prm["k"])
+    oracle.spread(L, seeds)
+    dt = time.perf_counter() - t0
+    m = len(u)
+    return {"value": m * sketches / dt, "unit": "pairs/s", "cores": threads, "kind": "oracle",
+            "seconds": dt,
+            "sample": f"{sketches} of {prm['R']} sketches of {prm['name']}, k={prm['k']}, "
+                      f"whole path (BFS labels, gains, compact sketches, greedy, spread)"}
+
+
+# ----------------------------------------------------------------------------- arms
+def run_reference(args, n, u, v, prm):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        cpu_sample(n, u, v, prm, sketches=max(1, CPU_SAMPLE_SKETCHES // 8))
+    t0 = time.perf_counter()
+    res = None
+    for _ in range(args.steps):
+        res = cpu_sample(n, u, v, prm)
+    dt = (time.perf_counter() - t0) / max(1, args.steps)
+    value = len(u) * CPU_SAMPLE_SKETCHES / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": prm["name"], "n": n, "m": len(u), "p": prm["p"], "R": prm["R"],
+                   "alpha": prm["alpha"], "k": prm["k"], "sample_sketches": CPU_SAMPLE_SKETCHES},
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": res["cores"], "kind": "oracle",
+                         "sample": res["sample"]},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, n, u, v, prm):
+    import torch
+    import paper_2311_07554_gb300 as im
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    m = len(u)
+    R, k = prm["R"], prm["k"]
+    pairs = m * R
+    stream = torch.cuda.current_stream()
+    du = torch.from_numpy(u.view(np.int32)).cuda()
+    dv = torch.from_numpy(v.view(np.int32)).cuda()
+    ctx = im.IMContext(n, du, dv, stream=stream.cuda_stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
+
+    def step():
+        ctx.build_sketches(R, prm["seed"], prm["p"], prm["alpha"])
+        seeds, gains = ctx.select_seeds(k)
+        sp = ctx.spread(seeds)
+        return seeds, gains, sp
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: K steps, L2 flushed before each (outside the events)
+    im.im_profile_reset(ctx.h)
+    im.im_profile_enable(ctx.h, True)
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    times, t_build, t_select = [], [], []
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    seeds = gains = sp = None
+    for _ in range(args.steps):
+        flush.fill_(1)
+        ev[0].record(stream)
+        ctx.build_sketches(R, prm["seed"], prm["p"], prm["alpha"])
+        ev[1].record(stream)
+        seeds, gains = ctx.select_seeds(k)
+        ev[2].record(stream)
+        sp = ctx.spread(seeds)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        times.append(ev[0].elapsed_time(ev[3]))
+        t_build.append(ev[0].elapsed_time(ev[1]))
+        t_select.append(ev[1].elapsed_time(ev[2]))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    prof = im.im_profile_get(ctx.h)
+    st = ctx.stats()
+    launches = int(st["launches"])
+    im.im_profile_enable(ctx.h, False)
+    ms_step = sum(times) / len(times)
+    ms_build = sum(t_build) / len(t_build)
+    ms_select = sum(t_select) / len(t_select)
+    if dist:
+        t = torch.tensor([ms_step, ms_build, ms_select], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step, ms_build, ms_select = t.tolist()
+
+    # end to end through the public API with host buffers (pinned), copies inside
+    pu = torch.from_numpy(u.view(np.int32)).pin_memory()
+    pv = torch.from_numpy(v.view(np.int32)).pin_memory()
+
+    def e2e_step():
+        with im.IMContext(n, pu, pv, stream=stream.cuda_stream) as c2:
+            c2.build_sketches(R, prm["seed"], prm["p"], prm["alpha"])
+            s2, g2 = c2.select_seeds(k)
+            return c2.spread(s2)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = sum(e2e_times) / len(e2e_times)
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if rank == 0:
+        peaks, peak_src = _peaks()
+        total_ms = sum(x[0] for x in prof.values())
+        top = max(prof.items(), key=lambda kv: kv[1][0])
+        su_ms, su_n = prof.get("sample_union", (0.0, 0))
+        roof = None
+        if su_n:
+            # dominant kernel of sketch construction: nb * m pairs hashed per launch
+            launches_per_step = su_n / args.steps
+            units = pairs / launches_per_step                   # pairs per launch
+            avg_s = su_ms / su_n / 1e3
+            ops_per_pair = 24.0                                 # 32-bit integer ops per hash
+            sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+            alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12          # Tops/s
+            achieved = units * ops_per_pair / avg_s / 1e12
+            roof = {"kernel": "sample_union", "bound": "alu", "achieved": achieved, "peak": alu_peak,
+                    "unit": "Tops/s", "frac": achieved / alu_peak,
+                    "traffic": _traffic("sample_union", units),
+                    "peak_source": "derived: 152 SMs x 128 int32 lanes x max SM clock "
+                                   f"({sm_mhz:.0f} MHz, {peak_src})",
+                    "pairs_per_s_per_launch": units / avg_s,
+                    "share_of_device_time": su_ms / total_ms if total_ms else None}
+        cpu = cpu_sample(n, u, v, prm)
+        line = {
+            "metric": METRIC,
+            "value": pairs * ws / (ms_step / 1e3),
+            "unit": "pairs/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64", "data": "synthetic",
+            "config": {"workload": prm["name"], "n": n, "m": m, "p": prm["p"], "R": R,
+                       "alpha": prm["alpha"], "k": k, "l2": "flushed before every step",
+                       "parallelism": f"replicas{ws}"},
+            "time_to_k_ms": ms_build + ms_select,
+            "sketch_ms": ms_build, "select_ms": ms_select,
+            "sketch_pairs_per_s": pairs / (ms_build / 1e3),
+            "evaluations": int(st["evaluations"]) // max(1, args.steps),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": pairs * ws / e2e_s, "unit": "pairs/s",
+                    "h2d_bytes_per_step": 8 * m, "d2h_bytes_per_step": 12 * k + 8},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "kernels_ms_per_step": {kname: round(t / args.steps, 4) for kname, (t, _) in
+                                    sorted(prof.items(), key=lambda kv: -kv[1][0])},
+            "top_kernel": top[0],
+            "seeds_head": [int(x) for x in seeds[:5]], "spread": int(sp),
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(graphgen.WORKLOADS))
+    args = ap.parse_args()
+    n, u, v, prm = graphgen.workload(args.workload)
+    prm["name"] = args.workload
+    if args.impl == "reference":
+        return run_reference(args, n, u, v, prm)
+    return run_ours(args, n, u, v, prm)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,166 @@
+/*
+ * im_gb300.h -- C ABI of the GB300 (sm_103a) sketch engine for influence maximisation
+ * under the independent cascade (IC) model on undirected graphs, after
+ * "Fast and Space-Efficient Parallel Algorithms for Influence Maximization" (PaC-IM).
+ *
+ * The calls follow the paper's problem statement (Sec. 2: given G = (V, E), k and IC
+ * probabilities, find |S| = k maximising the expected spread sigma(S)) and its
+ * sketch-based framework (Alg. 1: Step 1 builds R sketches, Step 2 selects k seeds).
+ *
+ * Conventions shared by every call
+ *   - Return value: IM_OK (0) or a negative IM_E* code; no exception crosses the ABI.
+ *     im_last_error() then describes the failure.
+ *   - Every call is synchronous with respect to the host: when it returns, its device
+ *     work on the context's stream has finished and outputs are written.
+ *   - Output buffers are owned by the caller.  ptr_kind says whether a pointer is a host
+ *     pointer (IM_PTR_HOST) or a device pointer on the context's device (IM_PTR_DEVICE).
+ *   - Gains and spreads are integer sums over the R sketches (sigma(S) * R); the paper
+ *     divides by R (Alg. 3, Marginal), which callers may do for display.
+ *   - A context is not thread-safe; distinct contexts are independent.
+ *   - Vertex ids are uint32 with n < 2^31; edge ids are uint32 positions in the input
+ *     edge list (m < 2^32).
+ */
+#ifndef IM_GB300_H
+#define IM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IM_OK        0
+#define IM_EINVAL   (-1)   /* bad argument (sizes, ids, p, alpha, k, R, pointer kind) */
+#define IM_ENOMEM   (-2)   /* device allocation failed                                */
+#define IM_ECUDA    (-3)   /* a CUDA runtime call failed                              */
+#define IM_ESTATE   (-4)   /* call out of order (e.g. selection before sketches)      */
+#define IM_ETIMEOUT (-5)   /* a bounded device wait gave up                           */
+#define IM_EDEVICE  (-6)   /* a kernel reported an internal error through its status */
+
+#define IM_PTR_HOST   0
+#define IM_PTR_DEVICE 1
+
+typedef struct im_ctx im_ctx;
+
+/*
+ * im_create -- load the input graph G = (V, E) (Sec. 2) onto the device and build its CSR.
+ *   n        number of vertices (1 <= n < 2^31).
+ *   m        number of undirected edges (m < 2^32); m = 0 is allowed.
+ *   u, v     m endpoints each: edge e = {u[e], v[e]}, e is its id for sampling
+ *            (Alg. 3 Sample(e, r)); u[e] != v[e], both < n.  The list is copied; the
+ *            caller keeps ownership.  Canonical inputs have u[e] < v[e] sorted by (u, v).
+ *   ptr_kind IM_PTR_HOST or IM_PTR_DEVICE for u and v.
+ *   stream   a cudaStream_t to run on (NULL: the context creates its own stream).
+ *   out      receives the context; NULL on failure.
+ * Errors: IM_EINVAL (n, ids, self-loops), IM_ENOMEM, IM_ECUDA.
+ */
+int im_create(im_ctx** out, uint32_t n, uint64_t m, const uint32_t* u, const uint32_t* v,
+              int ptr_kind, void* stream);
+
+/*
+ * im_build_sketches -- Step 1 of Alg. 1: build R compact sketches (Sec. 3, Alg. 3).
+ *   R      number of sketches (1 <= R <= 65536).  Sketch r in [0, R) is the sampled graph
+ *          G'_r whose live edges are those with h(e, r) < floor(p * 2^64), where
+ *          h(e, r) = mix(mix(mix(seed + G) ^ e) + (r + 1) G), G = 0x9E3779B97F4A7C15 and
+ *          mix is the splitmix64 finaliser ("fusion" sampling, Sec. 2).  No sampled graph
+ *          is stored.
+ *   seed   hash seed; also seeds the choice of centers.
+ *   p      uniform IC probability; p <= 0 makes no edge live, p >= 1 every edge.
+ *   alpha  center fraction in (0, 1] (the paper's rate; rho = ceil(alpha * n) centers,
+ *          the rho vertices with the smallest mix(v ^ mix(seed ^ 0xC3)), indexed by
+ *          increasing vertex id).  alpha = 1 stores every vertex's component (full labels).
+ * Produces, on the device: initial gains Delta[v] = sum_r |C_r(v)|, and per sketch the
+ * compact arrays label[i] (smallest center index in the component of center i) and
+ * size[i] (component size where label[i] = i, else 0).  Resets any seed selection.
+ * Errors: IM_EINVAL (R, alpha, or R * n too large for the 64-bit packed keys),
+ *         IM_ENOMEM, IM_ECUDA, IM_EDEVICE.
+ */
+int im_build_sketches(im_ctx* ctx, uint32_t R, uint64_t seed, double p, double alpha);
+
+/*
+ * im_select_seeds -- Step 2 of Alg. 1: greedy seeds by lazy evaluation on the device
+ * (CELF, Alg. 2, with prefix-doubling batches of re-evaluations as in Alg. 4).
+ *   k          total number of seeds wanted (1 <= k <= n).  Selection is prefix-consistent:
+ *              a later call with a larger k continues from the seeds already chosen; a
+ *              smaller k returns the prefix.
+ *   seeds_out  host array of k vertex ids, in selection order.
+ *   gains_out  host array of k marginal gains Delta(s_i | S_{i-1}) (sum over sketches),
+ *              or NULL.
+ * Ties between equal gains go to the smaller vertex id (Sec. 4); a vertex already in S is
+ * never chosen again.  The result equals plain (non-lazy) greedy exactly.
+ * Errors: IM_ESTATE (no sketches), IM_EINVAL (k), IM_ECUDA, IM_EDEVICE.
+ */
+int im_select_seeds(im_ctx* ctx, uint32_t k, uint32_t* seeds_out, uint64_t* gains_out);
+
+/*
+ * im_spread -- sum_r |union_{s in S} C_r(s)| for an arbitrary seed list (the sketch estimate
+ * of sigma(S), Alg. 1, times R).  Duplicated seeds count once.
+ *   seeds      host array of k vertex ids (each < n); 0 <= k <= 16384.
+ *   spread_out host pointer to the result.
+ * Independent of, and not changing, the selection state.
+ * Errors: IM_ESTATE, IM_EINVAL, IM_ECUDA, IM_EDEVICE.
+ */
+int im_spread(im_ctx* ctx, const uint32_t* seeds, uint32_t k, uint64_t* spread_out);
+
+/* im_reset_selection -- forget the chosen seeds; the sketches are kept. */
+int im_reset_selection(im_ctx* ctx);
+
+/*
+ * im_get_labels -- connected-component labels of sketch r (Sec. 3 Sketch(r)): out[v] = the
+ * smallest vertex id in the component of v in G'_r.  Recomputed on demand (n entries).
+ * Errors: IM_ESTATE, IM_EINVAL (r >= R, ptr_kind), IM_ECUDA.
+ */
+int im_get_labels(im_ctx* ctx, uint32_t r, uint32_t* out, int ptr_kind);
+
+/* im_get_gains -- initial gains Delta[v] = sum_r |C_r(v)| (n entries, uint64). */
+int im_get_gains(im_ctx* ctx, uint64_t* out, int ptr_kind);
+
+/* im_get_centers -- center vertex ids by center index (rho entries); *rho_out = rho. */
+int im_get_centers(im_ctx* ctx, uint32_t* out, uint32_t* rho_out, int ptr_kind);
+
+/*
+ * im_get_compact -- the compact sketches of Alg. 3, center-major: label[i * R + r] and
+ * size[i * R + r] for center index i < rho and sketch r < R.  size is the component size
+ * as built (seed coverage from im_select_seeds is reported separately and not applied).
+ */
+int im_get_compact(im_ctx* ctx, uint32_t* label, uint32_t* size, int ptr_kind);
+
+typedef struct {
+    uint32_t n, R, rho, rounds;     /* rounds = seeds selected so far                    */
+    uint64_t m;
+    uint64_t evaluations;           /* re-evaluations (Marginal calls) during selection  */
+    uint64_t batches;               /* prefix-doubling batches                           */
+    uint64_t bfs_fallbacks;         /* (v, r) searches that spilled to the global queue  */
+    uint64_t launches;              /* kernels launched by this context                  */
+    uint32_t sketch_batch;          /* sketches processed per edge pass                  */
+} im_stats;
+
+int im_get_stats(im_ctx* ctx, im_stats* out);
+
+/* Per-round evaluation counts (Sec. 4, F_i): out[i] for i < min(count, rounds). */
+int im_get_round_evals(im_ctx* ctx, uint64_t* out, uint32_t count);
+
+/*
+ * Profiling: when enabled, every kernel launch is bracketed by CUDA events on the context
+ * stream and its device time accumulated per kernel kind.
+ */
+int im_profile_enable(im_ctx* ctx, int on);
+int im_profile_reset(im_ctx* ctx);
+int im_profile_get(im_ctx* ctx, int kernel_id, double* total_ms, uint64_t* launches);
+int im_kernel_count(void);
+const char* im_kernel_name(int kernel_id);
+
+/* Tuning: sketches per edge pass (power of two, 1..32; 0 = automatic).  Takes effect at the
+ * next im_build_sketches. */
+int im_set_sketch_batch(im_ctx* ctx, uint32_t batch);
+
+/* The context's stream (a cudaStream_t). */
+void* im_stream(im_ctx* ctx);
+
+const char* im_last_error(const im_ctx* ctx);
+void im_destroy(im_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IM_GB300_H */

@@ -1,0 +1,14 @@
+"""GB300 (sm_103a) engine for sketch-based influence maximisation under the IC model.
+
+The hot path (hash-sampled live-edge sketches, batched union-find connectivity, component
+histograms and gains, compact sketches, device lazy greedy, spread) runs in hand-written
+CUDA kernels behind the C ABI of ``include/im_gb300.h``; this package is its binding.
+"""
+from ._native import (  # noqa: F401
+    IM_EDEVICE, IM_EINVAL, IM_ENOMEM, IM_ESTATE, IM_OK, IM_PTR_DEVICE, IM_PTR_HOST, IMContext,
+    IMError, im_build_sketches, im_create, im_destroy, im_get_centers, im_get_compact,
+    im_get_gains, im_get_labels, im_get_round_evals, im_get_stats, im_profile_enable,
+    im_profile_get, im_profile_reset, im_reset_selection, im_select_seeds,
+    im_set_sketch_batch, im_spread, im_stream, lib)
+
+__all__ = [n for n in dir() if n.startswith("im_")] + ["IMContext", "IMError", "lib"]

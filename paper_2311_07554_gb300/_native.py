@@ -1,0 +1,269 @@
+"""ctypes binding of ``libim_gb300.so`` (the C ABI in include/im_gb300.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA kernels.
+There is no CPU fallback; a missing or unloadable library raises at first use.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+
+LIB_PATH = Path(__file__).resolve().parent / "libim_gb300.so"
+
+IM_OK, IM_EINVAL, IM_ENOMEM, IM_ECUDA, IM_ESTATE, IM_ETIMEOUT, IM_EDEVICE = 0, -1, -2, -3, -4, -5, -6
+IM_PTR_HOST, IM_PTR_DEVICE = 0, 1
+ERROR_NAMES = {0: "IM_OK", -1: "IM_EINVAL", -2: "IM_ENOMEM", -3: "IM_ECUDA", -4: "IM_ESTATE",
+               -5: "IM_ETIMEOUT", -6: "IM_EDEVICE"}
+
+_lib = None
+
+
+class IMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class im_stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32), ("R", ctypes.c_uint32), ("rho", ctypes.c_uint32),
+                ("rounds", ctypes.c_uint32), ("m", ctypes.c_uint64),
+                ("evaluations", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("bfs_fallbacks", ctypes.c_uint64), ("launches", ctypes.c_uint64),
+                ("sketch_batch", ctypes.c_uint32)]
+
+
+def lib():
+    """Load the library (raises if it is missing: there is no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not LIB_PATH.exists():
+        raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build() "
+                          "(or python -m paper_2311_07554_gb300.build)")
+    L = ctypes.CDLL(str(LIB_PATH))
+    c = ctypes
+    vp, u32, u64, i32, dbl = c.c_void_p, c.c_uint32, c.c_uint64, c.c_int, c.c_double
+    sig = {
+        "im_create": ([c.POINTER(vp), u32, u64, vp, vp, i32, vp], i32),
+        "im_build_sketches": ([vp, u32, u64, dbl, dbl], i32),
+        "im_select_seeds": ([vp, u32, vp, vp], i32),
+        "im_spread": ([vp, vp, u32, c.POINTER(u64)], i32),
+        "im_reset_selection": ([vp], i32),
+        "im_get_labels": ([vp, u32, vp, i32], i32),
+        "im_get_gains": ([vp, vp, i32], i32),
+        "im_get_centers": ([vp, vp, c.POINTER(u32), i32], i32),
+        "im_get_compact": ([vp, vp, vp, i32], i32),
+        "im_get_stats": ([vp, c.POINTER(im_stats)], i32),
+        "im_get_round_evals": ([vp, vp, u32], i32),
+        "im_profile_enable": ([vp, i32], i32),
+        "im_profile_reset": ([vp], i32),
+        "im_profile_get": ([vp, i32, c.POINTER(dbl), c.POINTER(u64)], i32),
+        "im_kernel_count": ([], i32),
+        "im_kernel_name": ([i32], c.c_char_p),
+        "im_set_sketch_batch": ([vp, u32], i32),
+        "im_stream": ([vp], vp),
+        "im_last_error": ([vp], c.c_char_p),
+        "im_destroy": ([vp], None),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _check(ctx, rc: int):
+    if rc != IM_OK:
+        msg = lib().im_last_error(ctx)
+        raise IMError(rc, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    """(pointer, ptr_kind) of a numpy array or a torch tensor (CUDA -> device pointer)."""
+    if a is None:
+        return None, IM_PTR_HOST
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr()), (IM_PTR_DEVICE if a.is_cuda else IM_PTR_HOST)
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return ctypes.c_void_p(a.ctypes.data), IM_PTR_HOST
+
+
+# ---- the C calls, same names ------------------------------------------------------------
+def im_create(n: int, u, v, stream=None):
+    """Returns an opaque context handle (int).  u, v: uint32 numpy arrays or CUDA tensors."""
+    pu, ku = _ptr(u)
+    pv, kv = _ptr(v)
+    if ku != kv:
+        raise ValueError("u and v must both be host or both be device buffers")
+    m = int(len(u))
+    if len(v) != m:
+        raise ValueError("u and v differ in length")
+    h = ctypes.c_void_p()
+    rc = lib().im_create(ctypes.byref(h), n, m, pu, pv, ku, ctypes.c_void_p(stream) if stream else None)
+    if rc != IM_OK:
+        msg = lib().im_last_error(None)
+        raise IMError(rc, msg.decode() if msg else "")
+    return h.value
+
+
+def im_build_sketches(ctx, R: int, seed: int, p: float, alpha: float):
+    _check(ctx, lib().im_build_sketches(ctx, R, seed, p, alpha))
+
+
+def im_select_seeds(ctx, k: int):
+    seeds = np.empty(k, np.uint32)
+    gains = np.empty(k, np.uint64)
+    _check(ctx, lib().im_select_seeds(ctx, k, seeds.ctypes.data, gains.ctypes.data))
+    return seeds, gains
+
+
+def im_spread(ctx, seeds) -> int:
+    s = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint32))
+    out = ctypes.c_uint64(0)
+    _check(ctx, lib().im_spread(ctx, s.ctypes.data if len(s) else None, len(s), ctypes.byref(out)))
+    return int(out.value)
+
+
+def im_reset_selection(ctx):
+    _check(ctx, lib().im_reset_selection(ctx))
+
+
+def im_get_labels(ctx, r: int, out=None, n: int | None = None):
+    if out is None:
+        out = np.empty(n if n is not None else im_get_stats(ctx)["n"], np.uint32)
+    p, kind = _ptr(out)
+    _check(ctx, lib().im_get_labels(ctx, r, p, kind))
+    return out
+
+
+def im_get_gains(ctx, out=None):
+    if out is None:
+        out = np.empty(im_get_stats(ctx)["n"], np.uint64)
+    p, kind = _ptr(out)
+    _check(ctx, lib().im_get_gains(ctx, p, kind))
+    return out
+
+
+def im_get_centers(ctx, out=None):
+    rho = ctypes.c_uint32(0)
+    _check(ctx, lib().im_get_centers(ctx, None, ctypes.byref(rho), IM_PTR_HOST))
+    if out is None:
+        out = np.empty(rho.value, np.uint32)
+    p, kind = _ptr(out)
+    _check(ctx, lib().im_get_centers(ctx, p, ctypes.byref(rho), kind))
+    return out
+
+
+def im_get_compact(ctx):
+    st = im_get_stats(ctx)
+    lab = np.empty((st["rho"], st["R"]), np.uint32)
+    sz = np.empty((st["rho"], st["R"]), np.uint32)
+    _check(ctx, lib().im_get_compact(ctx, lab.ctypes.data, sz.ctypes.data, IM_PTR_HOST))
+    return lab, sz
+
+
+def im_get_stats(ctx) -> dict:
+    s = im_stats()
+    _check(ctx, lib().im_get_stats(ctx, ctypes.byref(s)))
+    return {f: getattr(s, f) for f, _ in im_stats._fields_}
+
+
+def im_get_round_evals(ctx, count: int):
+    out = np.zeros(count, np.uint64)
+    _check(ctx, lib().im_get_round_evals(ctx, out.ctypes.data, count))
+    return out
+
+
+def im_profile_enable(ctx, on: bool = True):
+    _check(ctx, lib().im_profile_enable(ctx, 1 if on else 0))
+
+
+def im_profile_reset(ctx):
+    _check(ctx, lib().im_profile_reset(ctx))
+
+
+def im_profile_get(ctx) -> dict:
+    """{kernel name: (total device ms, launches)} for kernels launched since the reset."""
+    res = {}
+    for kid in range(lib().im_kernel_count()):
+        ms = ctypes.c_double(0)
+        nl = ctypes.c_uint64(0)
+        _check(ctx, lib().im_profile_get(ctx, kid, ctypes.byref(ms), ctypes.byref(nl)))
+        if nl.value:
+            res[lib().im_kernel_name(kid).decode()] = (ms.value, int(nl.value))
+    return res
+
+
+def im_set_sketch_batch(ctx, batch: int):
+    _check(ctx, lib().im_set_sketch_batch(ctx, batch))
+
+
+def im_stream(ctx) -> int:
+    return int(lib().im_stream(ctx) or 0)
+
+
+def im_destroy(ctx):
+    if ctx:
+        lib().im_destroy(ctx)
+
+
+class IMContext:
+    """Owning wrapper around an ``im_ctx``; methods map one-to-one onto the C calls."""
+
+    def __init__(self, n: int, u, v, stream=None):
+        self.n = int(n)
+        self.h = im_create(n, u, v, stream)
+
+    def build_sketches(self, R, seed, p, alpha):
+        im_build_sketches(self.h, R, seed, p, alpha)
+        return self
+
+    def select_seeds(self, k):
+        return im_select_seeds(self.h, k)
+
+    def spread(self, seeds):
+        return im_spread(self.h, seeds)
+
+    def reset_selection(self):
+        im_reset_selection(self.h)
+
+    def labels(self, r, out=None):
+        return im_get_labels(self.h, r, out, self.n)
+
+    def gains(self, out=None):
+        return im_get_gains(self.h, out)
+
+    def centers(self):
+        return im_get_centers(self.h)
+
+    def compact(self):
+        return im_get_compact(self.h)
+
+    def stats(self):
+        return im_get_stats(self.h)
+
+    def round_evals(self):
+        return im_get_round_evals(self.h, self.stats()["rounds"])
+
+    def close(self):
+        if self.h:
+            im_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,480 @@
+// im_api.cu -- the C ABI (include/im_gb300.h): context lifetime, argument checks, device
+// memory, the build / select / spread flows, statistics and launch profiling.
+#include <cmath>
+#include <cstring>
+#include <algorithm>
+
+#include "im_internal.cuh"
+
+using namespace imk;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+const char* const kNames[K_COUNT] = {
+    "pack_edges", "csr_degree", "scan_partial", "scan_top", "scan_apply", "csr_fill",
+    "center_hist", "center_pick", "center_flags", "center_index",
+    "batch_init", "sample_union", "compress_count", "gain_compact", "init_keys",
+    "reduce_reset", "reduce", "sel_init", "sel_hist", "sel_pick", "gather", "eval",
+    "fallback", "finalize", "mark_seed", "spread_tasks", "spread_dedup", "labels_min",
+    "labels_out"};
+
+int bitlen64(uint64_t x) {
+    int b = 0;
+    while (x) { ++b; x >>= 1; }
+    return b;
+}
+
+template <typename T>
+void dfree(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+template <typename T>
+bool dalloc(T*& p, size_t count) {
+    dfree(p);
+    void* q = nullptr;
+    if (cudaMalloc(&q, count * sizeof(T) + 16) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    p = (T*)q;
+    return true;
+}
+
+void free_sketch_state(im_ctx* c) {
+    dfree(c->d_cbits); dfree(c->d_cidx); dfree(c->d_centers);
+    dfree(c->d_label); dfree(c->d_size); dfree(c->d_gain0);
+    dfree(c->d_key); dfree(c->d_stamp); dfree(c->d_seedflag);
+    dfree(c->d_batch); dfree(c->d_fresh);
+    dfree(c->d_parent); dfree(c->d_cnt);
+    dfree(c->d_fb_queue); dfree(c->d_fb_bits); dfree(c->d_fb_tasks);
+    c->batch_alloc = 0;
+    c->fb_slots = 0;
+    c->fb_cap = 0;
+    c->compact_cap = 0;
+    c->built = false;
+}
+
+__global__ void k_mask_covered(uint32_t* p, uint64_t cnt) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        p[i] &= ~kCovered;
+}
+
+__global__ void k_iota(uint32_t* p, uint32_t cnt) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) p[i] = i;
+}
+
+void resolve_events(im_ctx* c) {
+    if (c->ev_pending.empty()) return;
+    cudaStreamSynchronize(c->stream);
+    for (auto& pe : c->ev_pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev_pool[pe.second.first], c->ev_pool[pe.second.second]) == cudaSuccess)
+            c->prof_ms[pe.first] += ms;
+    }
+    cudaGetLastError();
+    c->ev_pending.clear();
+}
+
+int next_event(im_ctx* c) {
+    size_t used = c->ev_pending.size() * 2;
+    if (used + 2 > 8192) { resolve_events(c); used = 0; }
+    while (c->ev_pool.size() < used + 2) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return -1;
+        c->ev_pool.push_back(e);
+    }
+    return (int)used;
+}
+
+}  // namespace
+
+const char* imk::kernel_name(int id) { return (id >= 0 && id < K_COUNT) ? kNames[id] : "?"; }
+
+void im_prof_begin(im_ctx* c, int kid, int* ev0) {
+    c->launches++;
+    c->prof_launches[kid]++;
+    *ev0 = -1;
+    if (!c->prof) return;
+    int e = next_event(c);
+    if (e < 0) return;
+    cudaEventRecord(c->ev_pool[e], c->stream);
+    *ev0 = e;
+}
+
+void im_prof_end(im_ctx* c, int kid, int ev0) {
+    if (!c->prof || ev0 < 0) return;
+    cudaEventRecord(c->ev_pool[ev0 + 1], c->stream);
+    c->ev_pending.push_back({kid, {ev0, ev0 + 1}});
+}
+
+int im_fail(im_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+int im_cuda_check(im_ctx* c, cudaError_t e, const char* what) {
+    std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();
+    return im_fail(c, e == cudaErrorMemoryAllocation ? IM_ENOMEM : IM_ECUDA, msg);
+}
+
+// ------------------------------------------------------------------------------------
+extern "C" {
+
+int im_create(im_ctx** out, uint32_t n, uint64_t m, const uint32_t* u, const uint32_t* v,
+              int ptr_kind, void* stream) {
+    if (!out) return im_fail(nullptr, IM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n == 0 || n >= 0x80000000u) return im_fail(nullptr, IM_EINVAL, "n must be in [1, 2^31)");
+    if (m >= 0xFFFFFFFFull) return im_fail(nullptr, IM_EINVAL, "m must be < 2^32");
+    if (ptr_kind != IM_PTR_HOST && ptr_kind != IM_PTR_DEVICE)
+        return im_fail(nullptr, IM_EINVAL, "bad ptr_kind");
+    if (m > 0 && (!u || !v)) return im_fail(nullptr, IM_EINVAL, "edge arrays are NULL");
+    im_ctx* c = new (std::nothrow) im_ctx();
+    if (!c) return im_fail(nullptr, IM_ENOMEM, "context");
+    c->n = n;
+    c->m = m;
+    cudaGetDevice(&c->device);
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            g_create_error = "cudaStreamCreate failed";
+            delete c;
+            return IM_ECUDA;
+        }
+        c->own_stream = true;
+    }
+    uint32_t *du = nullptr, *dv = nullptr;
+    int rc = IM_OK;
+    do {
+        if (cudaMalloc(&c->d_sel, sizeof(SelState)) != cudaSuccess ||
+            cudaMallocHost(&c->h_sel, sizeof(SelState)) != cudaSuccess) {
+            rc = im_fail(c, IM_ENOMEM, "selection state");
+            break;
+        }
+        cudaMemsetAsync(c->d_sel, 0, sizeof(SelState), c->stream);
+        memset(c->h_sel, 0, sizeof(SelState));
+        if (cudaMalloc(&c->d_spread_total, sizeof(unsigned long long)) != cudaSuccess) {
+            rc = im_fail(c, IM_ENOMEM, "spread total");
+            break;
+        }
+        const uint32_t *pu = u, *pv = v;
+        if (ptr_kind == IM_PTR_HOST && m > 0) {
+            if (cudaMalloc(&du, m * sizeof(uint32_t)) != cudaSuccess ||
+                cudaMalloc(&dv, m * sizeof(uint32_t)) != cudaSuccess) {
+                rc = im_fail(c, IM_ENOMEM, "edge upload");
+                break;
+            }
+            if (cudaMemcpyAsync(du, u, m * sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+                cudaMemcpyAsync(dv, v, m * sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+                rc = im_fail(c, IM_ECUDA, "edge upload");
+                break;
+            }
+            pu = du;
+            pv = dv;
+        }
+        rc = im_graph_build(c, pu, pv);
+    } while (0);
+    if (du) cudaFree(du);
+    if (dv) cudaFree(dv);
+    if (rc != IM_OK) {
+        g_create_error = c->err;
+        im_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return IM_OK;
+}
+
+int im_set_sketch_batch(im_ctx* c, uint32_t batch) {
+    if (!c) return IM_EINVAL;
+    if (batch != 0 && (batch > 32 || (batch & (batch - 1)) != 0))
+        return im_fail(c, IM_EINVAL, "sketch batch must be 0 or a power of two <= 32");
+    c->batch_req = batch;
+    return IM_OK;
+}
+
+int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alpha) {
+    if (!c) return IM_EINVAL;
+    if (R == 0 || R > 65536) return im_fail(c, IM_EINVAL, "R must be in [1, 65536]");
+    if (!(alpha > 0.0) || alpha > 1.0) return im_fail(c, IM_EINVAL, "alpha must be in (0, 1]");
+    if (std::isnan(p)) return im_fail(c, IM_EINVAL, "p is NaN");
+    const uint32_t n = c->n;
+    const int bits = bitlen64(n);
+    if (bits + bitlen64((uint64_t)R * n) > 64)
+        return im_fail(c, IM_EINVAL, "R * n too large for 64-bit packed gain keys");
+    double rr = std::ceil(alpha * (double)n);
+    uint32_t rho = rr >= (double)n ? n : (uint32_t)rr;
+    if (rho == 0) rho = 1;
+    const uint32_t all = rho == n ? 1u : 0u;
+
+    // sampler (Sec. 2 fusion; threshold T = floor(p 2^64), exact)
+    Sampler smp;
+    smp.salt = mix64(seed + kGamma);
+    smp.all_live = 0;
+    smp.T = 0;
+    if (p >= 1.0) smp.all_live = 1;
+    else if (p > 0.0) smp.T = (uint64_t)std::ldexp(p, 64);
+
+    uint32_t B = c->batch_req;
+    if (B == 0) {
+        uint64_t per = (uint64_t)n * 8;
+        uint64_t fit = per ? (64ull << 20) / per : 32;
+        B = 8;
+        while (B < 32 && (uint64_t)B * 2 <= fit) B *= 2;
+    }
+    uint32_t rp2 = 1;
+    while (rp2 < R) rp2 <<= 1;
+    if (B > rp2) B = rp2;
+
+    free_sketch_state(c);
+    c->R = R; c->seed = seed; c->p = p; c->alpha = alpha; c->rho = rho; c->all_centers = all;
+    c->key_bits = (uint32_t)bits;
+    c->smp = smp;
+    c->batch_used = B;
+    const size_t nc = (size_t)rho * R;
+    bool ok = dalloc(c->d_gain0, n) && dalloc(c->d_key, n) && dalloc(c->d_stamp, n) &&
+              dalloc(c->d_seedflag, n) && dalloc(c->d_batch, n) && dalloc(c->d_fresh, n) &&
+              dalloc(c->d_label, nc) && dalloc(c->d_size, nc) &&
+              dalloc(c->d_parent, (size_t)B * n) && dalloc(c->d_cnt, (size_t)B * n);
+    if (ok && !all) {
+        const size_t nw = ((size_t)n + 31) / 32;
+        c->fb_slots = 8;
+        c->fb_cap = 1u << 22;
+        ok = dalloc(c->d_cbits, nw) && dalloc(c->d_cidx, n) && dalloc(c->d_centers, rho) &&
+             dalloc(c->d_fb_queue, (size_t)c->fb_slots * n) && dalloc(c->d_fb_bits, (size_t)c->fb_slots * nw) &&
+             dalloc(c->d_fb_tasks, c->fb_cap);
+        if (ok) ok = cudaMemsetAsync(c->d_fb_bits, 0, (size_t)c->fb_slots * nw * 4, c->stream) == cudaSuccess;
+    }
+    if (!ok) {
+        free_sketch_state(c);
+        return im_fail(c, IM_ENOMEM, "sketch memory");
+    }
+    c->batch_alloc = B;
+    c->compact_cap = nc;
+    int rc = IM_OK;
+    if (!all) {
+        uint32_t* flags = nullptr;
+        uint64_t* pos = nullptr;
+        if (!dalloc(flags, n) || !dalloc(pos, (size_t)n + 1)) {
+            dfree(flags);
+            dfree(pos);
+            free_sketch_state(c);
+            return im_fail(c, IM_ENOMEM, "center scratch");
+        }
+        rc = im_select_centers(c, flags, pos);
+        dfree(flags);
+        dfree(pos);
+        if (rc) { free_sketch_state(c); return rc; }
+    }
+    rc = im_sketch_batches(c);
+    if (!rc) rc = im_selection_init(c);
+    if (!rc) {
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) rc = im_cuda_check(c, e, "sketch construction");
+    }
+    if (rc) { free_sketch_state(c); return rc; }
+    c->built = true;
+    return IM_OK;
+}
+
+int im_select_seeds(im_ctx* c, uint32_t k, uint32_t* seeds_out, uint64_t* gains_out) {
+    if (!c) return IM_EINVAL;
+    if (!c->built) return im_fail(c, IM_ESTATE, "im_build_sketches has not run");
+    if (k == 0 || k > c->n) return im_fail(c, IM_EINVAL, "k must be in [1, n]");
+    if (!seeds_out) return im_fail(c, IM_EINVAL, "seeds_out is NULL");
+    while (c->seeds.size() < k) {
+        int rc = im_select_round(c);
+        if (rc) return rc;
+    }
+    IM_CUDA(c, cudaStreamSynchronize(c->stream));
+    memcpy(seeds_out, c->seeds.data(), k * sizeof(uint32_t));
+    if (gains_out) memcpy(gains_out, c->seed_gains.data(), k * sizeof(uint64_t));
+    return IM_OK;
+}
+
+int im_reset_selection(im_ctx* c) {
+    if (!c) return IM_EINVAL;
+    if (!c->built) return im_fail(c, IM_ESTATE, "im_build_sketches has not run");
+    int rc = im_selection_init(c);
+    if (rc) return rc;
+    IM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return IM_OK;
+}
+
+int im_spread(im_ctx* c, const uint32_t* seeds, uint32_t k, uint64_t* spread_out) {
+    if (!c) return IM_EINVAL;
+    if (!c->built) return im_fail(c, IM_ESTATE, "im_build_sketches has not run");
+    if (!spread_out) return im_fail(c, IM_EINVAL, "spread_out is NULL");
+    if (k > kSpreadKMax) return im_fail(c, IM_EINVAL, "k exceeds 16384");
+    if (k > 0 && !seeds) return im_fail(c, IM_EINVAL, "seeds is NULL");
+    for (uint32_t i = 0; i < k; ++i)
+        if (seeds[i] >= c->n) return im_fail(c, IM_EINVAL, "seed id >= n");
+    size_t need = (size_t)k * c->R;
+    if (need > c->spread_cap) {
+        if (!dalloc(c->d_spread_pairs, need)) { c->spread_cap = 0; return im_fail(c, IM_ENOMEM, "spread"); }
+        c->spread_cap = need;
+    }
+    if (!c->d_spread_seeds && !dalloc(c->d_spread_seeds, kSpreadKMax))
+        return im_fail(c, IM_ENOMEM, "spread seeds");
+    if (k > 0)
+        IM_CUDA(c, cudaMemcpyAsync(c->d_spread_seeds, seeds, k * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                                   c->stream));
+    return im_spread_run(c, k, spread_out);
+}
+
+int im_get_labels(im_ctx* c, uint32_t r, uint32_t* out, int ptr_kind) {
+    if (!c) return IM_EINVAL;
+    if (!c->built) return im_fail(c, IM_ESTATE, "im_build_sketches has not run");
+    if (r >= c->R) return im_fail(c, IM_EINVAL, "r >= R");
+    if (!out || (ptr_kind != IM_PTR_HOST && ptr_kind != IM_PTR_DEVICE)) return im_fail(c, IM_EINVAL, "out");
+    uint32_t* d = out;
+    if (ptr_kind == IM_PTR_HOST) {
+        d = nullptr;
+        if (!dalloc(d, c->n)) return im_fail(c, IM_ENOMEM, "labels");
+    }
+    int rc = im_labels_min(c, r, d);
+    if (!rc && ptr_kind == IM_PTR_HOST) {
+        cudaError_t e = cudaMemcpyAsync(out, d, (size_t)c->n * 4, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) rc = im_cuda_check(c, e, "labels copy");
+    } else if (!rc) {
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) rc = im_cuda_check(c, e, "labels");
+    }
+    if (ptr_kind == IM_PTR_HOST) dfree(d);
+    return rc;
+}
+
+static int copy_out(im_ctx* c, void* dst, const void* src, size_t bytes, int ptr_kind) {
+    if (!dst || (ptr_kind != IM_PTR_HOST && ptr_kind != IM_PTR_DEVICE)) return im_fail(c, IM_EINVAL, "out");
+    IM_CUDA(c, cudaMemcpyAsync(dst, src, bytes,
+                               ptr_kind == IM_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                               c->stream));
+    IM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return IM_OK;
+}
+
+int im_get_gains(im_ctx* c, uint64_t* out, int ptr_kind) {
+    if (!c) return IM_EINVAL;
+    if (!c->built) return im_fail(c, IM_ESTATE, "im_build_sketches has not run");
+    return copy_out(c, out, c->d_gain0, (size_t)c->n * 8, ptr_kind);
+}
+
+int im_get_centers(im_ctx* c, uint32_t* out, uint32_t* rho_out, int ptr_kind) {
+    if (!c) return IM_EINVAL;
+    if (!c->built) return im_fail(c, IM_ESTATE, "im_build_sketches has not run");
+    if (rho_out) *rho_out = c->rho;
+    if (!out) return IM_OK;
+    if (!c->all_centers) return copy_out(c, out, c->d_centers, (size_t)c->rho * 4, ptr_kind);
+    if (ptr_kind == IM_PTR_HOST) {
+        for (uint32_t i = 0; i < c->rho; ++i) out[i] = i;
+        return IM_OK;
+    }
+    if (ptr_kind != IM_PTR_DEVICE) return im_fail(c, IM_EINVAL, "ptr_kind");
+    k_iota<<<grid_for(c->rho, 256), 256, 0, c->stream>>>(out, c->rho);
+    IM_CUDA(c, cudaGetLastError());
+    IM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return IM_OK;
+}
+
+int im_get_compact(im_ctx* c, uint32_t* label, uint32_t* size, int ptr_kind) {
+    if (!c) return IM_EINVAL;
+    if (!c->built) return im_fail(c, IM_ESTATE, "im_build_sketches has not run");
+    const size_t cnt = (size_t)c->rho * c->R;
+    if (label) {
+        int rc = copy_out(c, label, c->d_label, cnt * 4, ptr_kind);
+        if (rc) return rc;
+    }
+    if (size) {
+        int rc = copy_out(c, size, c->d_size, cnt * 4, ptr_kind);
+        if (rc) return rc;
+        if (ptr_kind == IM_PTR_HOST) {
+            for (size_t i = 0; i < cnt; ++i) size[i] &= ~kCovered;
+        } else {
+            k_mask_covered<<<grid_for(cnt, 256), 256, 0, c->stream>>>(size, cnt);
+            IM_CUDA(c, cudaGetLastError());
+            IM_CUDA(c, cudaStreamSynchronize(c->stream));
+        }
+    }
+    return IM_OK;
+}
+
+int im_get_stats(im_ctx* c, im_stats* out) {
+    if (!c || !out) return IM_EINVAL;
+    memset(out, 0, sizeof *out);
+    out->n = c->n; out->m = c->m; out->R = c->R; out->rho = c->rho;
+    out->rounds = (uint32_t)c->seeds.size();
+    out->launches = c->launches;
+    out->batches = c->batches;
+    out->sketch_batch = c->batch_used;
+    uint64_t ev = 0;
+    for (auto x : c->round_evals) ev += x;
+    out->evaluations = ev;
+    if (c->h_sel) {
+        cudaMemcpyAsync(c->h_sel, c->d_sel, sizeof(SelState), cudaMemcpyDeviceToHost, c->stream);
+        cudaStreamSynchronize(c->stream);
+        out->bfs_fallbacks = c->h_sel->fb_total;
+    }
+    return IM_OK;
+}
+
+int im_get_round_evals(im_ctx* c, uint64_t* out, uint32_t count) {
+    if (!c || (!out && count)) return IM_EINVAL;
+    for (uint32_t i = 0; i < count && i < c->round_evals.size(); ++i) out[i] = c->round_evals[i];
+    return IM_OK;
+}
+
+int im_profile_enable(im_ctx* c, int on) {
+    if (!c) return IM_EINVAL;
+    resolve_events(c);
+    c->prof = on != 0;
+    return IM_OK;
+}
+
+int im_profile_reset(im_ctx* c) {
+    if (!c) return IM_EINVAL;
+    resolve_events(c);
+    for (int i = 0; i < K_COUNT; ++i) { c->prof_ms[i] = 0; c->prof_launches[i] = 0; }
+    c->launches = 0;
+    return IM_OK;
+}
+
+int im_profile_get(im_ctx* c, int kernel_id, double* total_ms, uint64_t* launches) {
+    if (!c || kernel_id < 0 || kernel_id >= K_COUNT) return IM_EINVAL;
+    resolve_events(c);
+    if (total_ms) *total_ms = c->prof_ms[kernel_id];
+    if (launches) *launches = c->prof_launches[kernel_id];
+    return IM_OK;
+}
+
+int im_kernel_count(void) { return K_COUNT; }
+
+const char* im_kernel_name(int kernel_id) { return kernel_name(kernel_id); }
+
+void* im_stream(im_ctx* c) { return c ? (void*)c->stream : nullptr; }
+
+const char* im_last_error(const im_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+void im_destroy(im_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_sketch_state(c);
+    dfree(c->d_edges); dfree(c->d_off); dfree(c->d_arcs);
+    dfree(c->d_spread_pairs); dfree(c->d_spread_seeds); dfree(c->d_spread_total);
+    if (c->d_sel) cudaFree(c->d_sel);
+    if (c->h_sel) cudaFreeHost(c->h_sel);
+    if (c->d_tmp) cudaFree(c->d_tmp);
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+}  // extern "C"

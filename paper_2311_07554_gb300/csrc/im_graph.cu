@@ -1,0 +1,209 @@
+// im_graph.cu -- graph load: edge packing with validation, CSR build (Sec. 5 stores the
+// input as CSR), and the exclusive scan used for CSR offsets and center indices.
+#include "im_internal.cuh"
+
+using namespace imk;
+
+namespace {
+
+// Pack (u[e], v[e]) into one 8-byte record; flag ids >= n and self-loops.
+__global__ void k_pack_edges(const uint32_t* __restrict__ u, const uint32_t* __restrict__ v,
+                             uint64_t m, uint32_t n, uint2* __restrict__ edges,
+                             unsigned int* __restrict__ bad) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        uint32_t a = u[e], b = v[e];
+        if (a >= n || b >= n || a == b) atomicOr(bad, 1u);
+        edges[e] = make_uint2(a, b);
+    }
+}
+
+__global__ void k_csr_degree(const uint2* __restrict__ edges, uint64_t m,
+                             uint32_t* __restrict__ deg) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        uint2 ed = edges[e];
+        atomicAdd(deg + ed.x, 1u);
+        atomicAdd(deg + ed.y, 1u);
+    }
+}
+
+// Each arc (x -> y) of edge e is written at off[x] + (its arrival order at x).  The order
+// inside an adjacency list is not fixed; no result depends on it.
+__global__ void k_csr_fill(const uint2* __restrict__ edges, uint64_t m,
+                           const uint64_t* __restrict__ off, uint32_t* __restrict__ cursor,
+                           uint2* __restrict__ arcs) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        uint2 ed = edges[e];
+        uint64_t pa = off[ed.x] + atomicAdd(cursor + ed.x, 1u);
+        arcs[pa] = make_uint2(ed.y, (uint32_t)e);
+        uint64_t pb = off[ed.y] + atomicAdd(cursor + ed.y, 1u);
+        arcs[pb] = make_uint2(ed.x, (uint32_t)e);
+    }
+}
+
+// ---- exclusive scan, u32 -> u64 (tiles of 4096: 1024 threads x 4 items) -------------
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr uint64_t kScanTile = (uint64_t)kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t x, uint64_t* warp_sums,
+                                                         uint64_t* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint64_t inc = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint64_t y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += y;
+    }
+    if (lane == 31) warp_sums[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        uint64_t w = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0;
+        uint64_t wi = w;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint64_t y = __shfl_up_sync(0xffffffffu, wi, d);
+            if (lane >= d) wi += y;
+        }
+        warp_sums[lane] = wi - w;          // exclusive prefix of warp totals
+        if (lane == 31) *total = wi;
+    }
+    __syncthreads();
+    uint64_t r = warp_sums[wid] + inc - x;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_partial(const uint32_t* __restrict__ in, uint64_t count, uint64_t* __restrict__ part) {
+    __shared__ uint64_t ws[32];
+    __shared__ uint64_t tot;
+    uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
+    uint64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i)
+        if (base + i < count) s += in[base + i];
+    block_exclusive_scan(s, ws, &tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+// one block scans all tile totals in place (exclusive), 1024 at a time
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_top(uint64_t* __restrict__ part, uint64_t nparts) {
+    __shared__ uint64_t ws[32];
+    __shared__ uint64_t tot;
+    uint64_t carry = 0;
+    for (uint64_t base = 0; base < nparts; base += kScanThreads) {
+        uint64_t i = base + threadIdx.x;
+        uint64_t x = i < nparts ? part[i] : 0;
+        uint64_t ex = block_exclusive_scan(x, ws, &tot);
+        if (i < nparts) part[i] = carry + ex;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[nparts] = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_apply(const uint32_t* __restrict__ in, uint64_t count, const uint64_t* __restrict__ part,
+             uint64_t* __restrict__ out) {
+    __shared__ uint64_t ws[32];
+    __shared__ uint64_t tot;
+    uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
+    uint32_t vals[kScanItems];
+    uint64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        vals[i] = (base + i < count) ? in[base + i] : 0u;
+        s += vals[i];
+    }
+    uint64_t ex = block_exclusive_scan(s, ws, &tot) + part[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        if (base + i < count) out[base + i] = ex;
+        ex += vals[i];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[count] = part[gridDim.x];
+}
+
+}  // namespace
+
+// out[0..count] = exclusive prefix sums of in[0..count), out[count] = total.
+// Uses c->d_tmp for tile totals (grown on demand).
+int im_scan_u32_to_u64(im_ctx* c, const uint32_t* d_in, uint64_t* d_out, uint64_t count) {
+    uint64_t tiles = (count + kScanTile - 1) / kScanTile;
+    if (tiles == 0) {
+        IM_CUDA(c, cudaMemsetAsync(d_out, 0, sizeof(uint64_t), c->stream));
+        return IM_OK;
+    }
+    size_t need = (tiles + 1) * sizeof(uint64_t);
+    if (need > c->tmp_bytes) {
+        if (c->d_tmp) cudaFree(c->d_tmp);
+        c->d_tmp = nullptr;
+        c->tmp_bytes = 0;
+        if (cudaMalloc(&c->d_tmp, need) != cudaSuccess) return im_fail(c, IM_ENOMEM, "scan scratch");
+        c->tmp_bytes = need;
+    }
+    uint64_t* part = (uint64_t*)c->d_tmp;
+    IM_LAUNCH(c, K_SCAN_PARTIAL, k_scan_partial, (unsigned)tiles, kScanThreads, 0, d_in, count, part);
+    IM_LAUNCH(c, K_SCAN_TOP, k_scan_top, 1, kScanThreads, 0, part, tiles);
+    IM_LAUNCH(c, K_SCAN_APPLY, k_scan_apply, (unsigned)tiles, kScanThreads, 0, d_in, count, part, d_out);
+    IM_CUDA(c, cudaGetLastError());
+    return IM_OK;
+}
+
+// Pack and validate the edge list, then build the CSR (offsets u64, arcs (nbr, eid)).
+int im_graph_build(im_ctx* c, const uint32_t* d_u, const uint32_t* d_v) {
+    const uint32_t n = c->n;
+    const uint64_t m = c->m;
+    uint64_t m_pad = (m + 1) & ~1ull;
+    if (m_pad == 0) m_pad = 2;
+    if (cudaMalloc(&c->d_edges, m_pad * sizeof(uint2)) != cudaSuccess)
+        return im_fail(c, IM_ENOMEM, "edge list");
+    IM_CUDA(c, cudaMemsetAsync(c->d_edges, 0, m_pad * sizeof(uint2), c->stream));
+    if (cudaMalloc(&c->d_off, ((size_t)n + 1) * sizeof(uint64_t)) != cudaSuccess)
+        return im_fail(c, IM_ENOMEM, "csr offsets");
+    if (cudaMalloc(&c->d_arcs, (2 * m + 2) * sizeof(uint2)) != cudaSuccess)
+        return im_fail(c, IM_ENOMEM, "csr arcs");
+    uint32_t* deg = nullptr;
+    unsigned int* bad = nullptr;
+    if (cudaMalloc(&deg, ((size_t)n + 1) * sizeof(uint32_t) + 16) != cudaSuccess)
+        return im_fail(c, IM_ENOMEM, "degree scratch");
+    bad = (unsigned int*)(deg + n + 1);
+    int rc = IM_OK;
+    do {
+        if (cudaMemsetAsync(deg, 0, ((size_t)n + 1) * sizeof(uint32_t) + 16, c->stream) != cudaSuccess) {
+            rc = im_fail(c, IM_ECUDA, "memset");
+            break;
+        }
+        const unsigned B = 256;
+        if (m > 0) {
+            IM_LAUNCH(c, K_PACK_EDGES, k_pack_edges, grid_for(m, B), B, 0, d_u, d_v, m, n, c->d_edges, bad);
+            IM_LAUNCH(c, K_CSR_DEGREE, k_csr_degree, grid_for(m, B), B, 0, c->d_edges, m, deg);
+        }
+        unsigned int h_bad = 0;
+        if (cudaMemcpyAsync(&h_bad, bad, sizeof(h_bad), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            rc = im_cuda_check(c, cudaGetLastError(), "edge validation");
+            break;
+        }
+        if (h_bad) {
+            rc = im_fail(c, IM_EINVAL, "edge list has an id >= n or a self-loop");
+            break;
+        }
+        rc = im_scan_u32_to_u64(c, deg, c->d_off, n);
+        if (rc) break;
+        if (cudaMemsetAsync(deg, 0, (size_t)n * sizeof(uint32_t), c->stream) != cudaSuccess) {
+            rc = im_fail(c, IM_ECUDA, "memset");
+            break;
+        }
+        if (m > 0)
+            IM_LAUNCH(c, K_CSR_FILL, k_csr_fill, grid_for(m, B), B, 0, c->d_edges, m, c->d_off, deg, c->d_arcs);
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) rc = im_cuda_check(c, e, "csr build");
+    } while (0);
+    cudaFree(deg);
+    return rc;
+}

@@ -1,0 +1,220 @@
+// im_internal.cuh -- device helpers and host-side plumbing shared by the CUDA sources.
+// Internal to the library; the public contract is include/im_gb300.h.
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "../../include/im_gb300.h"
+
+namespace imk {
+
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;   // splitmix64 increment
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint32_t kCovered = 0x80000000u;            // size word: component holds a seed
+constexpr uint32_t kNoCenterTag = 0x80000000u;        // spread: component id without a center
+constexpr uint32_t kQcap = 256;                       // per-warp BFS queue (shared memory)
+constexpr uint32_t kSpreadKMax = 16384;
+
+// splitmix64 output finaliser (Steele, Lea, Flood 2014).
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Live-edge rule of the "fusion" sampling (Sec. 2, Alg. 3 Sample): edge e is live in
+// sketch r iff mix(key_e + (r+1) G) < T, key_e = mix(salt ^ e), salt = mix(seed + G),
+// T = floor(p 2^64); all_live covers p >= 1.
+struct Sampler {
+    uint64_t salt;
+    uint64_t T;
+    uint32_t all_live;
+};
+
+__device__ __forceinline__ uint64_t edge_key(const Sampler& s, uint64_t e) {
+    return mix64(s.salt ^ e);
+}
+
+__device__ __forceinline__ bool edge_live(const Sampler& s, uint64_t key, uint32_t r) {
+    return s.all_live || mix64(key + (uint64_t)(r + 1u) * kGamma) < s.T;
+}
+
+struct GraphView {
+    uint32_t n;
+    uint64_t m;
+    const uint2* edges;     // m (padded to even): (u, v)
+    const uint64_t* off;    // n + 1 CSR offsets
+    const uint2* arcs;      // 2m: (neighbour, edge id)
+};
+
+struct SketchView {
+    uint32_t R, rho, all_centers;
+    const uint32_t* cbits;   // center bitmap, ceil(n/32) words (unused when all_centers)
+    const uint32_t* cidx;    // center index per vertex, kNone otherwise (unused when all)
+    const uint32_t* label;   // [rho][R]
+    uint32_t* size;          // [rho][R], bit 31 = covered by a seed
+    const uint8_t* seed_flag;
+    Sampler smp;
+};
+
+__device__ __forceinline__ bool is_center(const SketchView& s, uint32_t x) {
+    return s.all_centers || ((__ldg(s.cbits + (x >> 5)) >> (x & 31)) & 1u);
+}
+__device__ __forceinline__ uint32_t center_index(const SketchView& s, uint32_t x) {
+    return s.all_centers ? x : __ldg(s.cidx + x);
+}
+
+// Device-side selection state (one per context).
+struct SelState {
+    unsigned long long best;        // max fresh key this round
+    unsigned long long stale_max;   // max stale key over unevaluated candidates
+    unsigned long long n_unev;      // number of unevaluated candidates
+    unsigned long long prefix, prefmask, need, taken, theta, borig;
+    int shift, done;
+    unsigned int hist[256];
+    unsigned long long eval_next;   // task counter of the evaluation kernel
+    unsigned int batch_n;
+    unsigned int fb_n;              // fallback tasks queued
+    unsigned int fb_overflow;
+    unsigned long long evals_total;
+    unsigned long long fb_total;
+    unsigned int err;
+    unsigned int pad;
+};
+
+struct FbTask {
+    uint32_t v, r, kind, idx;
+};
+enum FbKind : uint32_t { FB_EVAL = 0, FB_MARK = 1, FB_SPREAD = 2 };
+
+enum KernelId {
+    K_PACK_EDGES = 0, K_CSR_DEGREE, K_SCAN_PARTIAL, K_SCAN_TOP, K_SCAN_APPLY, K_CSR_FILL,
+    K_CENTER_HIST, K_CENTER_PICK, K_CENTER_FLAGS, K_CENTER_INDEX,
+    K_BATCH_INIT, K_SAMPLE_UNION, K_COMPRESS_COUNT, K_GAIN_COMPACT, K_INIT_KEYS,
+    K_REDUCE_RESET, K_REDUCE, K_SEL_INIT, K_SEL_HIST, K_SEL_PICK, K_GATHER, K_EVAL,
+    K_FALLBACK, K_FINALIZE, K_MARK_SEED, K_SPREAD_TASKS, K_SPREAD_DEDUP, K_LABELS_MIN,
+    K_LABELS_OUT, K_COUNT
+};
+
+const char* kernel_name(int id);
+
+}  // namespace imk
+
+// ----------------------------------------------------------------------------------
+// Host context.
+// ----------------------------------------------------------------------------------
+struct im_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+
+    // graph
+    uint32_t n = 0;
+    uint64_t m = 0;
+    uint2* d_edges = nullptr;
+    uint64_t* d_off = nullptr;
+    uint2* d_arcs = nullptr;
+
+    // sketches
+    bool built = false;
+    uint32_t R = 0, rho = 0, all_centers = 1, key_bits = 1;
+    uint64_t seed = 0;
+    double p = 0.0, alpha = 1.0;
+    imk::Sampler smp{};
+    uint32_t* d_cbits = nullptr;
+    uint32_t* d_cidx = nullptr;
+    uint32_t* d_centers = nullptr;
+    uint32_t* d_label = nullptr;
+    uint32_t* d_size = nullptr;
+    uint64_t* d_gain0 = nullptr;
+    size_t compact_cap = 0;          // entries allocated for label / size
+
+    // selection
+    uint64_t* d_key = nullptr;
+    uint32_t* d_stamp = nullptr;
+    uint8_t* d_seedflag = nullptr;
+    uint32_t* d_batch = nullptr;
+    uint64_t* d_fresh = nullptr;
+    imk::SelState* d_sel = nullptr;
+    imk::SelState* h_sel = nullptr;  // pinned mirror
+    std::vector<uint32_t> seeds;
+    std::vector<uint64_t> seed_gains;
+    std::vector<uint64_t> round_evals;
+    uint64_t batches = 0;
+
+    // sketch-batch scratch
+    uint32_t batch_req = 0, batch_used = 0, batch_alloc = 0;
+    uint32_t* d_parent = nullptr;
+    uint32_t* d_cnt = nullptr;
+
+    // BFS fallback scratch
+    uint32_t fb_slots = 0;
+    uint32_t fb_cap = 0;
+    uint32_t* d_fb_queue = nullptr;
+    uint32_t* d_fb_bits = nullptr;
+    imk::FbTask* d_fb_tasks = nullptr;
+
+    // spread scratch
+    uint64_t* d_spread_pairs = nullptr;
+    size_t spread_cap = 0;
+    uint32_t* d_spread_seeds = nullptr;
+    unsigned long long* d_spread_total = nullptr;
+
+    // misc scratch (scan partials, center select)
+    void* d_tmp = nullptr;
+    size_t tmp_bytes = 0;
+
+    // accounting
+    uint64_t launches = 0;
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<int, int>>> ev_pending;   // (kernel, (ev0, ev1))
+    double prof_ms[imk::K_COUNT] = {};
+    uint64_t prof_launches[imk::K_COUNT] = {};
+};
+
+// launch accounting (defined in im_api.cu)
+void im_prof_begin(im_ctx* c, int kid, int* ev0);
+void im_prof_end(im_ctx* c, int kid, int ev0);
+
+#define IM_LAUNCH(ctx, kid, kern, grid, block, smem, ...)                               \
+    do {                                                                                \
+        int _ev0 = -1;                                                                  \
+        im_prof_begin((ctx), (kid), &_ev0);                                             \
+        kern<<<(grid), (block), (smem), (ctx)->stream>>>(__VA_ARGS__);                  \
+        im_prof_end((ctx), (kid), _ev0);                                                \
+    } while (0)
+
+// ---- launch wrappers (host) ------------------------------------------------------
+// im_graph.cu
+int im_graph_build(im_ctx* c, const uint32_t* d_u, const uint32_t* d_v);
+int im_scan_u32_to_u64(im_ctx* c, const uint32_t* d_in, uint64_t* d_out, uint64_t count);
+// im_sketch.cu
+int im_select_centers(im_ctx* c, uint32_t* d_flags_tmp, uint64_t* d_scan_tmp);
+int im_sketch_batches(im_ctx* c);
+int im_labels_min(im_ctx* c, uint32_t r, uint32_t* d_out);
+// im_select.cu
+int im_selection_init(im_ctx* c);
+int im_select_round(im_ctx* c);
+int im_spread_run(im_ctx* c, uint32_t k, uint64_t* out);
+
+int im_fail(im_ctx* c, int code, const std::string& msg);
+int im_cuda_check(im_ctx* c, cudaError_t e, const char* what);
+
+#define IM_CUDA(c, call)                                                                \
+    do {                                                                                \
+        cudaError_t _e = (call);                                                        \
+        if (_e != cudaSuccess) return im_cuda_check((c), _e, #call);                    \
+    } while (0)
+
+inline unsigned grid_for(uint64_t work, unsigned block, unsigned cap = 152u * 32u) {
+    uint64_t g = (work + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (unsigned)g;
+}

@@ -1,0 +1,647 @@
+// im_select.cu -- Step 2 of Alg. 1 on the device: lazy greedy seed selection (CELF, Alg. 2)
+// with prefix-doubling batches of re-evaluations (the batch schedule of Alg. 4), the
+// compact-sketch procedures GetCenter / Marginal / MarkSeed of Alg. 3, and the spread sum.
+//
+// Stale scores are kept as packed 64-bit keys  key = (gain << b) | (2^b - 1 - v), b = bit
+// length of n, so a larger key means a larger gain and, for equal gains, a smaller id
+// (Sec. 4 breaks ties by vertex id).  Within a round, a batch X of unevaluated candidates
+// with the largest stale keys is re-evaluated; the round ends when the best fresh key beats
+// every stale key not yet re-evaluated (Alg. 2's stop test on keys; Alg. 4's loop).  Stale
+// keys are upper bounds by submodularity (Eq. 2), so the winner equals plain greedy's.
+#include "im_internal.cuh"
+
+using namespace imk;
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kEvalWarps = 4;   // warps per block of the search kernels
+
+__device__ __forceinline__ uint64_t pack_key(uint64_t gain, uint32_t v, uint32_t bits) {
+    const uint64_t mask = (1ull << bits) - 1ull;
+    return (gain << bits) | (mask - v);
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
+#pragma unroll
+    for (int d = 16; d; d >>= 1) x += __shfl_xor_sync(kFull, x, d);
+    return x;
+}
+
+// ---- GetCenter (Alg. 3) for a start vertex that is not a center ----------------------
+// Warp-cooperative BFS on G'_r with the queue (= visited list) in shared memory.  Arcs of
+// the current vertex are scanned 32 at a time, each lane re-hashing one arc.  Stops at the
+// first center met (every center of a component carries the same label).  If the queue
+// would exceed kQcap the search is abandoned (overflow) and redone by k_fallback.
+struct BfsOut {
+    uint32_t label;   // label of the component's centers, or kNone
+    uint32_t count;   // vertices visited (the whole component when label == kNone)
+    uint32_t minv;    // smallest vertex id visited
+    uint32_t seen;    // a seed was visited
+    uint32_t overflow;
+};
+
+__device__ BfsOut warp_bfs(const GraphView& g, const SketchView& s, uint32_t v, uint32_t r,
+                           uint32_t* q, bool want_seed) {
+    const unsigned lane = threadIdx.x & 31;
+    BfsOut o;
+    o.label = kNone; o.count = 0; o.minv = v; o.seen = 0; o.overflow = 0;
+    if (lane == 0) q[0] = v;
+    __syncwarp();
+    uint32_t head = 0, tail = 1;
+    uint32_t seen = want_seed ? (uint32_t)s.seed_flag[v] : 0u;
+    uint32_t minv = v;
+    while (head < tail) {
+        const uint32_t x = q[head++];
+        const uint64_t a0 = g.off[x], a1 = g.off[x + 1];
+        for (uint64_t base = a0; base < a1; base += 32) {
+            const uint64_t a = base + lane;
+            bool live = false;
+            uint32_t y = 0;
+            if (a < a1) {
+                const uint2 arc = g.arcs[a];
+                y = arc.x;
+                live = edge_live(s.smp, edge_key(s.smp, arc.y), r);
+            }
+            const unsigned cb = __ballot_sync(kFull, live && is_center(s, y));
+            if (cb) {
+                const uint32_t yc = __shfl_sync(kFull, y, __ffs(cb) - 1);
+                o.label = s.label[(size_t)center_index(s, yc) * s.R + r];
+                return o;
+            }
+            bool fresh = live;
+            if (live)
+                for (uint32_t t = 0; t < tail; ++t)
+                    if (q[t] == y) { fresh = false; break; }
+            const unsigned fm = __ballot_sync(kFull, fresh);
+            if (fresh) {   // parallel edges: keep one lane per neighbour
+                const unsigned grp = __match_any_sync(fm, y);
+                if (lane != (unsigned)(__ffs(grp) - 1)) fresh = false;
+            }
+            const unsigned nbm = __ballot_sync(kFull, fresh);
+            const uint32_t cnt = __popc(nbm);
+            if (tail + cnt > kQcap) { o.overflow = 1; return o; }
+            if (fresh) {
+                q[tail + __popc(nbm & ((1u << lane) - 1u))] = y;
+                if (want_seed && s.seed_flag[y]) seen = 1;
+                minv = min(minv, y);
+            }
+            tail += cnt;
+            __syncwarp();
+        }
+    }
+    o.seen = __any_sync(kFull, seen) ? 1u : 0u;
+#pragma unroll
+    for (int d = 16; d; d >>= 1) minv = min(minv, __shfl_xor_sync(kFull, minv, d));
+    o.minv = minv;
+    o.count = tail;
+    return o;
+}
+
+__device__ __forceinline__ void push_fallback(SelState* st, FbTask* tasks, uint32_t cap, uint32_t v,
+                                              uint32_t r, uint32_t kind, uint32_t idx) {
+    uint32_t t = atomicAdd(&st->fb_n, 1u);
+    if (t < cap) {
+        FbTask f;
+        f.v = v; f.r = r; f.kind = kind; f.idx = idx;
+        tasks[t] = f;
+    } else {
+        st->fb_overflow = 1;
+    }
+}
+
+// ---- selection kernels ---------------------------------------------------------------
+__global__ void k_init_keys(const uint64_t* __restrict__ gain0, uint32_t n, uint32_t bits,
+                            uint64_t* __restrict__ key, uint32_t* __restrict__ stamp,
+                            uint8_t* __restrict__ seedflag, uint32_t* __restrict__ size,
+                            uint64_t nsize) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        key[i] = pack_key(gain0[i], (uint32_t)i, bits);
+        stamp[i] = 0;
+        seedflag[i] = 0;
+    }
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nsize; i += stride)
+        size[i] &= ~kCovered;
+}
+
+__global__ void k_reduce_reset(SelState* st) {
+    if (threadIdx.x == 0) { st->best = 0; st->stale_max = 0; st->n_unev = 0; }
+}
+
+// best = max fresh key (evaluated this round), stale_max / n_unev over the others.
+__global__ void __launch_bounds__(256)
+k_reduce(const uint64_t* __restrict__ key, const uint32_t* __restrict__ stamp,
+         const uint8_t* __restrict__ seedflag, uint32_t n, uint32_t round, SelState* st) {
+    unsigned long long bf = 0, sm = 0, cnt = 0;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        if (seedflag[v]) continue;
+        const unsigned long long k = key[v];
+        if (stamp[v] == round) bf = max(bf, k);
+        else { sm = max(sm, k); ++cnt; }
+    }
+#pragma unroll
+    for (int d = 16; d; d >>= 1) {
+        bf = max(bf, __shfl_xor_sync(kFull, bf, d));
+        sm = max(sm, __shfl_xor_sync(kFull, sm, d));
+        cnt += __shfl_xor_sync(kFull, cnt, d);
+    }
+    __shared__ unsigned long long s_bf[8], s_sm[8], s_cnt[8];
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { s_bf[w] = bf; s_sm[w] = sm; s_cnt[w] = cnt; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+            bf = max(bf, s_bf[i]); sm = max(sm, s_sm[i]); cnt += s_cnt[i];
+        }
+        if (bf) atomicMax(&st->best, bf);
+        if (sm) atomicMax(&st->stale_max, sm);
+        if (cnt) atomicAdd(&st->n_unev, cnt);
+    }
+}
+
+// Start of a batch: decide how to pick ~B of the largest stale keys (radix select on the
+// key bytes below the top byte of stale_max); take all when at most 2B remain.
+__global__ void k_sel_init(SelState* st, unsigned long long B) {
+    if (threadIdx.x != 0) return;
+    const unsigned long long nu = st->n_unev, smax = st->stale_max;
+    st->borig = B;
+    st->need = B;
+    st->taken = 0;
+    st->prefix = 0;
+    st->theta = 0;
+    if (nu <= 2 * B || smax == 0) {
+        st->done = 1;
+        st->shift = 0;
+        st->prefmask = 0;
+    } else {
+        const int top = 63 - __clzll((long long)smax);
+        const int shift = (top / 8) * 8;
+        st->shift = shift;
+        st->prefmask = (shift + 8 >= 64) ? 0ull : ~((1ull << (shift + 8)) - 1ull);
+        st->done = 0;
+    }
+    for (int i = 0; i < 256; ++i) st->hist[i] = 0;
+    st->batch_n = 0;
+    st->eval_next = 0;
+    st->fb_n = 0;
+    st->best = 0;
+    st->stale_max = 0;
+    st->n_unev = 0;
+}
+
+__global__ void __launch_bounds__(256)
+k_sel_hist(const uint64_t* __restrict__ key, const uint32_t* __restrict__ stamp,
+           const uint8_t* __restrict__ seedflag, uint32_t n, uint32_t round, SelState* st) {
+    if (st->done) return;
+    __shared__ unsigned int h[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const unsigned long long prefix = st->prefix, pm = st->prefmask;
+    const int shift = st->shift;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        if (seedflag[v] || stamp[v] == round) continue;
+        const unsigned long long k = key[v];
+        if ((k & pm) == prefix) atomicAdd(&h[(k >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 256; i += blockDim.x)
+        if (h[i]) atomicAdd(&st->hist[i], h[i]);
+}
+
+__global__ void k_sel_pick(SelState* st) {
+    if (threadIdx.x != 0 || st->done) return;
+    unsigned long long above = 0;
+    int d = 255;
+    for (; d > 0; --d) {
+        if (above + st->hist[d] >= st->need) break;
+        above += st->hist[d];
+    }
+    const unsigned long long with_bin = st->taken + above + st->hist[d];
+    if (with_bin <= 2 * st->borig || st->shift == 0) {
+        st->theta = st->prefix | ((unsigned long long)d << st->shift);
+        st->done = 1;
+    } else {
+        st->taken += above;
+        st->need -= above;
+        st->prefix |= (unsigned long long)d << st->shift;
+        st->prefmask |= 255ull << st->shift;
+        st->shift -= 8;
+    }
+    for (int i = 0; i < 256; ++i) st->hist[i] = 0;
+}
+
+__global__ void __launch_bounds__(256)
+k_gather(const uint64_t* __restrict__ key, const uint32_t* __restrict__ stamp,
+         const uint8_t* __restrict__ seedflag, uint32_t n, uint32_t round, SelState* st,
+         uint32_t* __restrict__ batch, unsigned long long* __restrict__ fresh) {
+    const unsigned long long theta = st->theta;
+    const unsigned lane = threadIdx.x & 31;
+    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const uint32_t v = base + threadIdx.x;
+        bool take = false;
+        if (v < n && !seedflag[v] && stamp[v] != round) take = key[v] >= theta;
+        const unsigned bal = __ballot_sync(kFull, take);
+        if (!bal) continue;
+        uint32_t pos0 = 0;
+        if (lane == 0) pos0 = atomicAdd(&st->batch_n, (unsigned)__popc(bal));
+        pos0 = __shfl_sync(kFull, pos0, 0);
+        if (take) {
+            const uint32_t j = pos0 + __popc(bal & ((1u << lane) - 1u));
+            batch[j] = v;
+            fresh[j] = 0;
+        }
+    }
+}
+
+// Marginal (Alg. 3) of every batch member: tasks (member j, chunk of 32 sketches).
+__global__ void __launch_bounds__(kEvalWarps * 32)
+k_eval(GraphView g, SketchView s, SelState* st, const uint32_t* __restrict__ batch,
+       unsigned long long* __restrict__ fresh, FbTask* __restrict__ fbt, uint32_t fb_cap,
+       uint32_t nchunk) {
+    __shared__ uint32_t qs[kEvalWarps][kQcap];
+    uint32_t* q = qs[threadIdx.x >> 5];
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned long long total = (unsigned long long)st->batch_n * nchunk;
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(&st->eval_next, 1ull);
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= total) break;
+        const uint32_t j = (uint32_t)(t / nchunk), ch = (uint32_t)(t % nchunk);
+        const uint32_t x = batch[j];
+        const uint32_t r_lo = ch * 32, r_hi = min(s.R, r_lo + 32);
+        unsigned long long sum = 0;
+        if (is_center(s, x)) {
+            const uint32_t r = r_lo + lane;
+            if (r < r_hi) {
+                const uint32_t l = s.label[(size_t)center_index(s, x) * s.R + r];
+                const uint32_t sz = s.size[(size_t)l * s.R + r];
+                sum = (sz & kCovered) ? 0u : sz;
+            }
+            sum = warp_sum_u64(sum);
+        } else {
+            for (uint32_t r = r_lo; r < r_hi; ++r) {
+                const BfsOut o = warp_bfs(g, s, x, r, q, true);
+                if (o.overflow) {
+                    if (lane == 0) push_fallback(st, fbt, fb_cap, x, r, FB_EVAL, j);
+                } else if (o.label != kNone) {
+                    const uint32_t sz = s.size[(size_t)o.label * s.R + r];
+                    sum += (sz & kCovered) ? 0u : sz;
+                } else {
+                    sum += o.seen ? 0u : o.count;
+                }
+                __syncwarp();
+            }
+        }
+        if (lane == 0 && sum) atomicAdd(fresh + j, sum);
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_finalize(SelState* st, const uint32_t* __restrict__ batch,
+           const unsigned long long* __restrict__ fresh, uint64_t* __restrict__ key,
+           uint32_t* __restrict__ stamp, uint32_t bits, uint32_t round) {
+    const uint32_t bn = st->batch_n;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < bn; j += gridDim.x * blockDim.x) {
+        const uint32_t x = batch[j];
+        key[x] = pack_key(fresh[j], x, bits);
+        stamp[x] = round;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->evals_total += bn;
+        st->fb_total += min(st->fb_n, 0xFFFFFFFFu);
+    }
+}
+
+// MarkSeed (Alg. 3): in every sketch, flag the component of s as covered.
+__global__ void __launch_bounds__(kEvalWarps * 32)
+k_mark_seed(GraphView g, SketchView s, SelState* st, uint32_t sd, FbTask* __restrict__ fbt,
+            uint32_t fb_cap, uint32_t nchunk, uint8_t* __restrict__ seedflag,
+            uint64_t* __restrict__ key) {
+    __shared__ uint32_t qs[kEvalWarps][kQcap];
+    uint32_t* q = qs[threadIdx.x >> 5];
+    const unsigned lane = threadIdx.x & 31;
+    const uint32_t ch = blockIdx.x * kEvalWarps + (threadIdx.x >> 5);
+    if (ch < nchunk) {
+        const uint32_t r_lo = ch * 32, r_hi = min(s.R, r_lo + 32);
+        if (is_center(s, sd)) {
+            const uint32_t r = r_lo + lane;
+            if (r < r_hi) {
+                const uint32_t l = s.label[(size_t)center_index(s, sd) * s.R + r];
+                atomicOr(s.size + (size_t)l * s.R + r, kCovered);
+            }
+        } else {
+            for (uint32_t r = r_lo; r < r_hi; ++r) {
+                const BfsOut o = warp_bfs(g, s, sd, r, q, false);
+                if (lane == 0) {
+                    if (o.overflow) push_fallback(st, fbt, fb_cap, sd, r, FB_MARK, 0);
+                    else if (o.label != kNone) atomicOr(s.size + (size_t)o.label * s.R + r, kCovered);
+                }
+                __syncwarp();
+            }
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        seedflag[sd] = 1;
+        key[sd] = 0;
+    }
+}
+
+__global__ void k_phase_reset(SelState* st) {
+    if (threadIdx.x == 0) { st->fb_n = 0; st->eval_next = 0; st->batch_n = 0; }
+}
+
+// Searches that overflowed the shared-memory queue: one warp per slot, queue and visited
+// bitmap in global scratch (n entries / n bits per slot).
+__global__ void __launch_bounds__(32)
+k_fallback(GraphView g, SketchView s, SelState* st, const FbTask* __restrict__ fbt, uint32_t fb_cap,
+           uint32_t* __restrict__ fbq, uint32_t* __restrict__ fbb,
+           unsigned long long* __restrict__ fresh, uint64_t* __restrict__ spread_pairs) {
+    const unsigned lane = threadIdx.x & 31;
+    const uint32_t ntask = min(st->fb_n, fb_cap);
+    const uint32_t n = g.n;
+    const uint32_t nw = (n + 31) >> 5;
+    uint32_t* q = fbq + (size_t)blockIdx.x * n;
+    uint32_t* bits = fbb + (size_t)blockIdx.x * nw;
+    for (uint32_t t = blockIdx.x; t < ntask; t += gridDim.x) {
+        const FbTask f = fbt[t];
+        const uint32_t v = f.v, r = f.r;
+        const bool want_seed = f.kind == FB_EVAL;
+        if (lane == 0) {
+            q[0] = v;
+            atomicOr(bits + (v >> 5), 1u << (v & 31));
+        }
+        __syncwarp();
+        uint32_t head = 0, tail = 1, label = kNone, minv = v;
+        uint32_t seen = want_seed ? (uint32_t)s.seed_flag[v] : 0u;
+        while (head < tail && label == kNone) {
+            const uint32_t x = q[head++];
+            const uint64_t a0 = g.off[x], a1 = g.off[x + 1];
+            for (uint64_t base = a0; base < a1; base += 32) {
+                const uint64_t a = base + lane;
+                bool live = false;
+                uint32_t y = 0;
+                if (a < a1) {
+                    const uint2 arc = g.arcs[a];
+                    y = arc.x;
+                    live = edge_live(s.smp, edge_key(s.smp, arc.y), r);
+                }
+                const unsigned cb = __ballot_sync(kFull, live && is_center(s, y));
+                if (cb) {
+                    const uint32_t yc = __shfl_sync(kFull, y, __ffs(cb) - 1);
+                    label = s.label[(size_t)center_index(s, yc) * s.R + r];
+                    break;
+                }
+                bool fresh_v = false;
+                if (live) {
+                    const uint32_t bit = 1u << (y & 31);
+                    fresh_v = !(atomicOr(bits + (y >> 5), bit) & bit);
+                }
+                const unsigned nbm = __ballot_sync(kFull, fresh_v);
+                if (fresh_v) {
+                    q[tail + __popc(nbm & ((1u << lane) - 1u))] = y;
+                    if (want_seed && s.seed_flag[y]) seen = 1;
+                    minv = min(minv, y);
+                }
+                tail += __popc(nbm);
+                __syncwarp();
+            }
+        }
+        seen = __any_sync(kFull, seen) ? 1u : 0u;
+#pragma unroll
+        for (int d = 16; d; d >>= 1) minv = min(minv, __shfl_xor_sync(kFull, minv, d));
+        for (uint32_t i = lane; i < tail; i += 32) bits[q[i] >> 5] = 0u;   // private slot
+        __syncwarp();
+        if (lane == 0) {
+            if (f.kind == FB_EVAL) {
+                unsigned long long d;
+                if (label != kNone) {
+                    const uint32_t sz = s.size[(size_t)label * s.R + r];
+                    d = (sz & kCovered) ? 0u : sz;
+                } else {
+                    d = seen ? 0u : tail;
+                }
+                if (d) atomicAdd(fresh + f.idx, d);
+            } else if (f.kind == FB_MARK) {
+                if (label != kNone) atomicOr(s.size + (size_t)label * s.R + r, kCovered);
+            } else {
+                uint64_t pr;
+                if (label != kNone)
+                    pr = ((uint64_t)label << 32) | (s.size[(size_t)label * s.R + r] & ~kCovered);
+                else
+                    pr = ((uint64_t)(kNoCenterTag | minv) << 32) | tail;
+                spread_pairs[f.idx] = pr;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ---- spread: per (seed i, sketch r) the component's identity and size, then dedup -----
+__global__ void __launch_bounds__(kEvalWarps * 32)
+k_spread_tasks(GraphView g, SketchView s, SelState* st, const uint32_t* __restrict__ sd, uint32_t k,
+               uint32_t nchunk, FbTask* __restrict__ fbt, uint32_t fb_cap,
+               uint64_t* __restrict__ pairs) {
+    __shared__ uint32_t qs[kEvalWarps][kQcap];
+    uint32_t* q = qs[threadIdx.x >> 5];
+    const unsigned lane = threadIdx.x & 31;
+    const uint64_t total = (uint64_t)k * nchunk;
+    const uint64_t wstride = (uint64_t)gridDim.x * kEvalWarps;
+    for (uint64_t t = (uint64_t)blockIdx.x * kEvalWarps + (threadIdx.x >> 5); t < total; t += wstride) {
+        const uint32_t i = (uint32_t)(t / nchunk), ch = (uint32_t)(t % nchunk);
+        const uint32_t x = sd[i];
+        const uint32_t r_lo = ch * 32, r_hi = min(s.R, r_lo + 32);
+        if (is_center(s, x)) {
+            const uint32_t r = r_lo + lane;
+            if (r < r_hi) {
+                const uint32_t l = s.label[(size_t)center_index(s, x) * s.R + r];
+                const uint32_t sz = s.size[(size_t)l * s.R + r] & ~kCovered;
+                pairs[(size_t)r * k + i] = ((uint64_t)l << 32) | sz;
+            }
+        } else {
+            for (uint32_t r = r_lo; r < r_hi; ++r) {
+                const BfsOut o = warp_bfs(g, s, x, r, q, false);
+                if (lane == 0) {
+                    const size_t idx = (size_t)r * k + i;
+                    if (o.overflow) {
+                        push_fallback(st, fbt, fb_cap, x, r, FB_SPREAD, (uint32_t)idx);
+                    } else if (o.label != kNone) {
+                        pairs[idx] = ((uint64_t)o.label << 32) |
+                                     (s.size[(size_t)o.label * s.R + r] & ~kCovered);
+                    } else {
+                        pairs[idx] = ((uint64_t)(kNoCenterTag | o.minv) << 32) | o.count;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+    }
+}
+
+// one block per sketch: sort the k (component id, size) words, add sizes of distinct ones
+__global__ void __launch_bounds__(1024)
+k_spread_dedup(const uint64_t* __restrict__ pairs, uint32_t k, uint32_t kp2,
+               unsigned long long* __restrict__ total) {
+    extern __shared__ uint64_t sv[];
+    const uint64_t* row = pairs + (size_t)blockIdx.x * k;
+    for (uint32_t i = threadIdx.x; i < kp2; i += blockDim.x) sv[i] = i < k ? row[i] : ~0ull;
+    __syncthreads();
+    for (uint32_t len = 2; len <= kp2; len <<= 1) {
+        for (uint32_t stp = len >> 1; stp > 0; stp >>= 1) {
+            for (uint32_t i = threadIdx.x; i < kp2; i += blockDim.x) {
+                const uint32_t jx = i ^ stp;
+                if (jx > i) {
+                    const bool up = (i & len) == 0;
+                    const uint64_t a = sv[i], b = sv[jx];
+                    if ((a > b) == up) { sv[i] = b; sv[jx] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    unsigned long long acc = 0;
+    for (uint32_t i = threadIdx.x; i < k; i += blockDim.x)
+        if (i == 0 || sv[i] != sv[i - 1]) acc += sv[i] & 0xFFFFFFFFull;
+    acc = warp_sum_u64(acc);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(total, acc);
+}
+
+GraphView graph_view(const im_ctx* c) {
+    GraphView g;
+    g.n = c->n; g.m = c->m; g.edges = c->d_edges; g.off = c->d_off; g.arcs = c->d_arcs;
+    return g;
+}
+
+SketchView sketch_view(const im_ctx* c) {
+    SketchView s;
+    s.R = c->R; s.rho = c->rho; s.all_centers = c->all_centers;
+    s.cbits = c->d_cbits; s.cidx = c->d_cidx; s.label = c->d_label; s.size = c->d_size;
+    s.seed_flag = c->d_seedflag; s.smp = c->smp;
+    return s;
+}
+
+int sync_state(im_ctx* c) {
+    IM_CUDA(c, cudaMemcpyAsync(c->h_sel, c->d_sel, sizeof(SelState), cudaMemcpyDeviceToHost, c->stream));
+    IM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (c->h_sel->fb_overflow) return im_fail(c, IM_EDEVICE, "BFS fallback queue capacity exceeded");
+    if (c->h_sel->err) return im_fail(c, IM_EDEVICE, "selection kernel reported an error");
+    return IM_OK;
+}
+
+void launch_fallback(im_ctx* c, const GraphView& g, const SketchView& s) {
+    if (c->all_centers || c->fb_slots == 0) return;
+    IM_LAUNCH(c, K_FALLBACK, k_fallback, c->fb_slots, 32, 0, g, s, c->d_sel, c->d_fb_tasks, c->fb_cap,
+              c->d_fb_queue, c->d_fb_bits, (unsigned long long*)c->d_fresh, c->d_spread_pairs);
+}
+
+unsigned search_grid(uint64_t tasks) {
+    return grid_for(tasks, kEvalWarps, 152u * 16u);   // one task per warp to start
+}
+
+}  // namespace
+
+// Reset the selection state: keys from the initial gains, no seeds, no coverage.
+int im_selection_init(im_ctx* c) {
+    const unsigned T = 256;
+    const uint64_t nsize = (uint64_t)c->rho * c->R;
+    IM_LAUNCH(c, K_INIT_KEYS, k_init_keys, grid_for(c->n > nsize ? c->n : nsize, T, 152u * 16u), T, 0,
+              c->d_gain0, c->n, c->key_bits, c->d_key, c->d_stamp, c->d_seedflag, c->d_size, nsize);
+    IM_CUDA(c, cudaMemsetAsync(c->d_sel, 0, sizeof(SelState), c->stream));
+    IM_CUDA(c, cudaGetLastError());
+    c->seeds.clear();
+    c->seed_gains.clear();
+    c->round_evals.clear();
+    c->batches = 0;
+    return IM_OK;
+}
+
+// One round of lazy greedy: NextSeed + MarkSeed.
+int im_select_round(im_ctx* c) {
+    const uint32_t n = c->n;
+    const uint32_t round = (uint32_t)c->seeds.size();
+    const unsigned T = 256;
+    const unsigned gridn = grid_for(n, T, 152u * 8u);
+    const GraphView g = graph_view(c);
+    const SketchView s = sketch_view(c);
+    const uint32_t nchunk = (c->R + 31) / 32;
+    SelState* st = c->d_sel;
+
+    IM_LAUNCH(c, K_REDUCE_RESET, k_reduce_reset, 1, 32, 0, st);
+    IM_LAUNCH(c, K_REDUCE, k_reduce, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n, round, st);
+    int rc = sync_state(c);
+    if (rc) return rc;
+    uint64_t evals = 0;
+    for (int j = 0;; ++j) {
+        const SelState& h = *c->h_sel;
+        if (h.n_unev == 0 || h.best > h.stale_max) break;
+        unsigned long long B = 1ull << (j < 40 ? j : 40);
+        if (B > h.n_unev) B = h.n_unev;
+        const uint64_t expect = (2 * B < h.n_unev ? 2 * B : h.n_unev);
+        IM_LAUNCH(c, K_SEL_INIT, k_sel_init, 1, 32, 0, st, B);
+        if (h.n_unev > 2 * B) {
+            for (int pass = 0; pass < 8; ++pass) {
+                IM_LAUNCH(c, K_SEL_HIST, k_sel_hist, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n,
+                          round, st);
+                IM_LAUNCH(c, K_SEL_PICK, k_sel_pick, 1, 32, 0, st);
+            }
+        }
+        IM_LAUNCH(c, K_GATHER, k_gather, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n, round, st,
+                  c->d_batch, (unsigned long long*)c->d_fresh);
+        IM_LAUNCH(c, K_EVAL, k_eval, search_grid(expect * nchunk), kEvalWarps * 32, 0, g, s, st,
+                  c->d_batch, (unsigned long long*)c->d_fresh, c->d_fb_tasks, c->fb_cap, nchunk);
+        launch_fallback(c, g, s);
+        IM_LAUNCH(c, K_FINALIZE, k_finalize, grid_for(expect, T, 152u * 8u), T, 0, st, c->d_batch,
+                  (const unsigned long long*)c->d_fresh, c->d_key, c->d_stamp, c->key_bits, round);
+        IM_LAUNCH(c, K_REDUCE, k_reduce, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n, round, st);
+        rc = sync_state(c);
+        if (rc) return rc;
+        if (c->h_sel->batch_n == 0 || j > 80)
+            return im_fail(c, IM_EDEVICE, "re-evaluation batch made no progress");
+        evals += c->h_sel->batch_n;
+        c->batches++;
+    }
+    const unsigned long long best = c->h_sel->best;
+    if (best == 0) return im_fail(c, IM_EDEVICE, "no candidate left for the next seed");
+    const uint64_t mask = (1ull << c->key_bits) - 1ull;
+    const uint32_t sd = (uint32_t)(mask - (best & mask));
+    const uint64_t gain = best >> c->key_bits;
+    if (sd >= n) return im_fail(c, IM_EDEVICE, "selected id out of range");
+    IM_LAUNCH(c, K_REDUCE_RESET, k_phase_reset, 1, 32, 0, st);
+    IM_LAUNCH(c, K_MARK_SEED, k_mark_seed, (nchunk + kEvalWarps - 1) / kEvalWarps, kEvalWarps * 32, 0,
+              g, s, st, sd, c->d_fb_tasks, c->fb_cap, nchunk, c->d_seedflag, c->d_key);
+    launch_fallback(c, g, s);
+    IM_CUDA(c, cudaGetLastError());
+    c->seeds.push_back(sd);
+    c->seed_gains.push_back(gain);
+    c->round_evals.push_back(evals);
+    return IM_OK;
+}
+
+int im_spread_run(im_ctx* c, uint32_t k, uint64_t* out) {
+    const GraphView g = graph_view(c);
+    const SketchView s = sketch_view(c);
+    const uint32_t nchunk = (c->R + 31) / 32;
+    IM_LAUNCH(c, K_REDUCE_RESET, k_phase_reset, 1, 32, 0, c->d_sel);
+    IM_CUDA(c, cudaMemsetAsync(c->d_spread_total, 0, sizeof(unsigned long long), c->stream));
+    if (k > 0) {
+        IM_LAUNCH(c, K_SPREAD_TASKS, k_spread_tasks, search_grid((uint64_t)k * nchunk), kEvalWarps * 32, 0,
+                  g, s, c->d_sel, c->d_spread_seeds, k, nchunk, c->d_fb_tasks, c->fb_cap,
+                  c->d_spread_pairs);
+        launch_fallback(c, g, s);
+        uint32_t kp2 = 1;
+        while (kp2 < k) kp2 <<= 1;
+        const size_t smem = (size_t)kp2 * sizeof(uint64_t);
+        IM_CUDA(c, cudaFuncSetAttribute(k_spread_dedup, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(smem > 48 * 1024 ? smem : 48 * 1024)));
+        IM_LAUNCH(c, K_SPREAD_DEDUP, k_spread_dedup, c->R, 1024, smem, c->d_spread_pairs, k, kp2,
+                  c->d_spread_total);
+    }
+    IM_CUDA(c, cudaGetLastError());
+    unsigned long long h = 0;
+    IM_CUDA(c, cudaMemcpyAsync(&h, c->d_spread_total, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    int rc = sync_state(c);
+    if (rc) return rc;
+    *out = h;
+    return IM_OK;
+}

@@ -1,0 +1,334 @@
+// im_sketch.cu -- Step 1 of Alg. 1: sketch construction (Sec. 3, Alg. 3 Sketch(r)).
+//
+// Per batch of B sketches sharing one pass over the edge list:
+//   init        parent[b][v] = v, cnt[b][v] = 0
+//   sample+UF   for every edge e and sketch r of the batch: if h(e, r) < T, union(u, v)
+//               (hooking with atomicCAS; the root of every component is its earliest vertex
+//               in "center-first" order: the smallest-id center if the component has one,
+//               else its smallest id)
+//   compress    parent[b][v] <- root, cnt[b][root] += 1 (warp-aggregated)
+//   gain        Delta[v] += sum_b cnt[b][root_b(v)]; for centers: label, size (Alg. 3)
+#include "im_internal.cuh"
+
+using namespace imk;
+
+namespace {
+
+// ---- union-find ---------------------------------------------------------------------
+// Reads go through L2 (__ldcg) so that a spin over a root another SM has just hooked
+// always sees the new parent.
+
+template <bool kAll>
+__device__ __forceinline__ bool before(const uint32_t* __restrict__ cbits, uint32_t a, uint32_t b) {
+    if (kAll) return a < b;
+    uint32_t ca = (__ldg(cbits + (a >> 5)) >> (a & 31)) & 1u;
+    uint32_t cb = (__ldg(cbits + (b >> 5)) >> (b & 31)) & 1u;
+    return ca != cb ? ca > cb : a < b;
+}
+
+__device__ __forceinline__ uint32_t find_root(uint32_t* P, uint32_t x) {
+    for (;;) {
+        uint32_t p = __ldcg(P + x);
+        if (p == x) return x;
+        uint32_t gp = __ldcg(P + p);
+        if (gp == p) return p;
+        __stcg(P + x, gp);   // path halving: gp is an ancestor of x
+        x = gp;
+    }
+}
+
+template <bool kAll>
+__device__ __forceinline__ void unite(uint32_t* P, const uint32_t* cbits, uint32_t a, uint32_t b) {
+    for (;;) {
+        a = find_root(P, a);
+        b = find_root(P, b);
+        if (a == b) return;
+        if (before<kAll>(cbits, b, a)) { uint32_t t = a; a = b; b = t; }
+        // hook the later root b under the earlier root a
+        uint32_t old = atomicCAS(P + b, b, a);
+        if (old == b) return;
+        b = old;
+    }
+}
+
+__global__ void k_batch_init(uint32_t* __restrict__ parent, uint32_t* __restrict__ cnt,
+                             uint32_t n, uint32_t nb) {
+    uint64_t total = (uint64_t)n * nb;
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        parent[i] = (uint32_t)(i % n);
+        if (cnt) cnt[i] = 0;
+    }
+}
+
+// Each thread takes two edges (one 16-byte load) and all nb <= B sketches of the batch.
+template <int B, bool kAll>
+__global__ void __launch_bounds__(256)
+k_sample_union(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, uint32_t r0,
+               uint32_t nb, uint32_t* __restrict__ parent, uint32_t n,
+               const uint32_t* __restrict__ cbits) {
+    const uint64_t npairs = (m + 1) >> 1;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t g0 = (uint64_t)(r0 + 1u) * kGamma;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npairs; i += stride) {
+        const uint4 two = edge_pairs[i];
+        const uint64_t e0 = 2 * i, e1 = 2 * i + 1;
+        const bool has1 = e1 < m;
+        uint64_t x0 = mix64(smp.salt ^ e0) + g0;
+        uint64_t x1 = mix64(smp.salt ^ e1) + g0;
+        uint32_t live0 = 0, live1 = 0;
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            if (b < (int)nb) {
+                if (smp.all_live || mix64(x0) < smp.T) live0 |= 1u << b;
+                if (smp.all_live || mix64(x1) < smp.T) live1 |= 1u << b;
+            }
+            x0 += kGamma;
+            x1 += kGamma;
+        }
+        if (!has1) live1 = 0;
+        while (live0) {
+            int b = __ffs(live0) - 1;
+            live0 &= live0 - 1;
+            unite<kAll>(parent + (size_t)b * n, cbits, two.x, two.y);
+        }
+        while (live1) {
+            int b = __ffs(live1) - 1;
+            live1 &= live1 - 1;
+            unite<kAll>(parent + (size_t)b * n, cbits, two.z, two.w);
+        }
+    }
+}
+
+// grid.y = sketch within the batch; full compression + component-size histogram.
+// No unions run here, so every root is final; the only value ever written is a vertex's
+// root (a path-halving write of an intermediate ancestor could land after another thread
+// stored the root and leave the array not fully compressed).
+__global__ void __launch_bounds__(256)
+k_compress_count(uint32_t* __restrict__ parent, uint32_t* __restrict__ cnt, uint32_t n) {
+    uint32_t* P = parent + (size_t)blockIdx.y * n;
+    uint32_t* C = cnt ? cnt + (size_t)blockIdx.y * n : nullptr;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += stride) {
+        uint32_t v = base + threadIdx.x;
+        bool act = v < n;
+        uint32_t root = 0;
+        if (act) {
+            root = v;
+            for (uint32_t p = __ldcg(P + root); p != root; p = __ldcg(P + root)) root = p;
+            for (uint32_t x = v; x != root;) {
+                const uint32_t nx = __ldcg(P + x);
+                if (nx != root) __stcg(P + x, root);
+                x = nx;
+            }
+        }
+        if (C) {
+            unsigned am = __ballot_sync(0xffffffffu, act);
+            if (act) {
+                unsigned grp = __match_any_sync(am, root);
+                if ((threadIdx.x & 31) == (unsigned)(__ffs(grp) - 1)) atomicAdd(C + root, __popc(grp));
+            }
+        }
+    }
+}
+
+template <bool kAll>
+__global__ void __launch_bounds__(256)
+k_gain_compact(const uint32_t* __restrict__ parent, const uint32_t* __restrict__ cnt, uint32_t n,
+               uint32_t nb, uint32_t r0, uint32_t R, uint64_t* __restrict__ gain, int first,
+               const uint32_t* __restrict__ cidx, uint32_t* __restrict__ label,
+               uint32_t* __restrict__ size) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        uint64_t g = 0;
+        uint32_t ci = kAll ? v : cidx[v];
+        for (uint32_t b = 0; b < nb; ++b) {
+            uint32_t root = parent[(size_t)b * n + v];
+            uint32_t c = cnt[(size_t)b * n + root];
+            g += c;
+            if (ci != kNone) {
+                size_t o = (size_t)ci * R + r0 + b;
+                label[o] = kAll ? root : cidx[root];
+                size[o] = (root == v) ? c : 0u;
+            }
+        }
+        gain[v] = first ? g : gain[v] + g;
+    }
+}
+
+// ---- centers: the rho smallest ckey(v) = mix(v ^ csalt) (distinct: mix is a bijection) ----
+struct CenterSel {
+    unsigned long long prefix, prefmask, need;
+    int shift;
+    unsigned int pad;
+    unsigned int hist[256];
+};
+
+__global__ void k_center_hist(uint32_t n, uint64_t csalt, CenterSel* st) {
+    __shared__ unsigned int h[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const unsigned long long prefix = st->prefix, pm = st->prefmask;
+    const int shift = st->shift;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        uint64_t key = mix64((uint64_t)v ^ csalt);
+        if ((key & pm) == prefix) atomicAdd(&h[(key >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 256; i += blockDim.x)
+        if (h[i]) atomicAdd(&st->hist[i], h[i]);
+}
+
+__global__ void k_center_pick(CenterSel* st) {
+    if (threadIdx.x != 0) return;
+    unsigned long long cum = 0;
+    int d = 0;
+    for (; d < 255; ++d) {
+        if (cum + st->hist[d] >= st->need) break;
+        cum += st->hist[d];
+    }
+    st->need -= cum;
+    st->prefix |= (unsigned long long)d << st->shift;
+    st->prefmask |= 255ull << st->shift;
+    st->shift -= 8;
+    for (int i = 0; i < 256; ++i) st->hist[i] = 0;
+}
+
+__global__ void k_center_flags(uint32_t n, uint64_t csalt, const CenterSel* st,
+                               uint32_t* __restrict__ flags, uint32_t* __restrict__ cbits) {
+    const unsigned long long theta = st->prefix;   // the rho-th smallest key
+    // blockDim.x is a multiple of 32, so every warp covers one aligned 32-vertex word
+    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const uint32_t v = base + threadIdx.x;
+        bool f = false;
+        if (v < n) f = mix64((uint64_t)v ^ csalt) <= theta;
+        unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (v < n) flags[v] = f ? 1u : 0u;
+        if ((threadIdx.x & 31) == 0 && v < n) cbits[v >> 5] = bal;
+    }
+}
+
+__global__ void k_center_index(uint32_t n, uint32_t rho, const uint32_t* __restrict__ flags,
+                               const uint64_t* __restrict__ pos, uint32_t* __restrict__ cidx,
+                               uint32_t* __restrict__ centers) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        if (flags[v] && pos[v] < rho) {
+            uint32_t i = (uint32_t)pos[v];
+            cidx[v] = i;
+            centers[i] = v;
+        } else {
+            cidx[v] = kNone;
+        }
+    }
+}
+
+__global__ void k_labels_out(const uint32_t* __restrict__ P, uint32_t n, uint32_t* __restrict__ out) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        out[v] = P[v];
+}
+
+template <bool kAll>
+int launch_sample_union(im_ctx* c, uint32_t r0, uint32_t nb) {
+    const unsigned T = 256;
+    const uint64_t npairs = (c->m + 1) >> 1;
+    unsigned grid = grid_for(npairs, T, 152u * 16u);
+    const uint4* ep = reinterpret_cast<const uint4*>(c->d_edges);
+    const uint32_t* cb = c->d_cbits;
+#define IM_SU(BB)                                                                                \
+    IM_LAUNCH(c, K_SAMPLE_UNION, (k_sample_union<BB, kAll>), grid, T, 0, ep, c->m, c->smp, r0, nb, \
+              c->d_parent, c->n, cb)
+    uint32_t cap = c->batch_used;
+    if (cap <= 1) IM_SU(1);
+    else if (cap <= 2) IM_SU(2);
+    else if (cap <= 4) IM_SU(4);
+    else if (cap <= 8) IM_SU(8);
+    else if (cap <= 16) IM_SU(16);
+    else IM_SU(32);
+#undef IM_SU
+    return IM_OK;
+}
+
+}  // namespace
+
+int im_select_centers(im_ctx* c, uint32_t* d_flags, uint64_t* d_pos) {
+    const uint32_t n = c->n;
+    CenterSel* st = nullptr;
+    if (cudaMalloc(&st, sizeof(CenterSel)) != cudaSuccess) return im_fail(c, IM_ENOMEM, "center select");
+    CenterSel h{};
+    h.prefix = 0;
+    h.prefmask = 0;
+    h.need = c->rho;
+    h.shift = 56;
+    int rc = IM_OK;
+    do {
+        if (cudaMemcpyAsync(st, &h, sizeof h, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+            rc = im_fail(c, IM_ECUDA, "memcpy");
+            break;
+        }
+        const uint64_t csalt = mix64(c->seed ^ 0xC3ull);
+        const unsigned T = 256;
+        for (int pass = 0; pass < 8; ++pass) {
+            IM_LAUNCH(c, K_CENTER_HIST, k_center_hist, grid_for(n, T, 152u * 8u), T, 0, n, csalt, st);
+            IM_LAUNCH(c, K_CENTER_PICK, k_center_pick, 1, 32, 0, st);
+        }
+        IM_LAUNCH(c, K_CENTER_FLAGS, k_center_flags, grid_for(n, T, 152u * 8u), T, 0, n, csalt, st,
+                  d_flags, c->d_cbits);
+        rc = im_scan_u32_to_u64(c, d_flags, d_pos, n);
+        if (rc) break;
+        IM_LAUNCH(c, K_CENTER_INDEX, k_center_index, grid_for(n, T, 152u * 8u), T, 0, n, c->rho, d_flags, d_pos,
+                  c->d_cidx, c->d_centers);
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) rc = im_cuda_check(c, e, "center selection");
+    } while (0);
+    cudaFree(st);
+    return rc;
+}
+
+// Build all R sketches batch by batch; writes gain0, label, size.
+int im_sketch_batches(im_ctx* c) {
+    const uint32_t n = c->n, R = c->R;
+    const unsigned T = 256;
+    const bool any_live = c->smp.all_live || c->smp.T != 0;
+    for (uint32_t r0 = 0; r0 < R; r0 += c->batch_used) {
+        uint32_t nb = R - r0 < c->batch_used ? R - r0 : c->batch_used;
+        IM_LAUNCH(c, K_BATCH_INIT, k_batch_init, grid_for((uint64_t)n * nb, T, 152u * 16u), T, 0,
+                  c->d_parent, c->d_cnt, n, nb);
+        if (any_live && c->m > 0) {
+            int rc = c->all_centers ? launch_sample_union<true>(c, r0, nb)
+                                    : launch_sample_union<false>(c, r0, nb);
+            if (rc) return rc;
+        }
+        dim3 g(grid_for(n, T, 152u * 8u), nb);
+        IM_LAUNCH(c, K_COMPRESS_COUNT, k_compress_count, g, T, 0, c->d_parent, c->d_cnt, n);
+        if (c->all_centers)
+            IM_LAUNCH(c, K_GAIN_COMPACT, k_gain_compact<true>, grid_for(n, T, 152u * 16u), T, 0,
+                      c->d_parent, c->d_cnt, n, nb, r0, R, c->d_gain0, r0 == 0 ? 1 : 0, c->d_cidx,
+                      c->d_label, c->d_size);
+        else
+            IM_LAUNCH(c, K_GAIN_COMPACT, k_gain_compact<false>, grid_for(n, T, 152u * 16u), T, 0,
+                      c->d_parent, c->d_cnt, n, nb, r0, R, c->d_gain0, r0 == 0 ? 1 : 0, c->d_cidx,
+                      c->d_label, c->d_size);
+    }
+    IM_CUDA(c, cudaGetLastError());
+    return IM_OK;
+}
+
+// Min-id labels of one sketch (test hook): union-find with plain smallest-id hooking.
+int im_labels_min(im_ctx* c, uint32_t r, uint32_t* d_out) {
+    const uint32_t n = c->n;
+    const unsigned T = 256;
+    IM_LAUNCH(c, K_BATCH_INIT, k_batch_init, grid_for(n, T, 152u * 16u), T, 0, c->d_parent,
+              (uint32_t*)nullptr, n, 1u);
+    if ((c->smp.all_live || c->smp.T != 0) && c->m > 0) {
+        uint32_t saved = c->batch_used;
+        c->batch_used = 1;
+        int rc = launch_sample_union<true>(c, r, 1);
+        c->batch_used = saved;
+        if (rc) return rc;
+    }
+    dim3 g(grid_for(n, T, 152u * 8u), 1);
+    IM_LAUNCH(c, K_LABELS_MIN, k_compress_count, g, T, 0, c->d_parent, (uint32_t*)nullptr, n);
+    IM_LAUNCH(c, K_LABELS_OUT, k_labels_out, grid_for(n, T, 152u * 8u), T, 0, c->d_parent, n, d_out);
+    IM_CUDA(c, cudaGetLastError());
+    return IM_OK;
+}

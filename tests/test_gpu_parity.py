@@ -1,0 +1,230 @@
+"""GPU path (through the C ABI) against the CPU oracle, element by element.
+
+Everything is integer, so every comparison is exact: labels, component sizes, initial gains,
+centers, compact label/size arrays, the seed sequence, the gains along it and the spread.
+"""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2311_07554_gb300 as im  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    im.lib()
+
+
+def _run(n, u, v, seed, p, R, alpha, k, batch=0, spread_sets=()):
+    with im.IMContext(n, u, v) as ctx:
+        if batch:
+            im.im_set_sketch_batch(ctx.h, batch)
+        ctx.build_sketches(R, seed, p, alpha)
+        out = dict(gains=ctx.gains(), centers=ctx.centers())
+        out["label"], out["size"] = ctx.compact()
+        if k:
+            out["seeds"], out["seed_gains"] = ctx.select_seeds(k)
+            out["spread"] = ctx.spread(out["seeds"])
+            out["round_evals"] = ctx.round_evals()
+        out["spreads"] = [ctx.spread(s) for s in spread_sets]
+        out["stats"] = ctx.stats()
+        out["labels"] = {r: ctx.labels(r) for r in range(min(R, 8))}
+    return out
+
+
+def _oracle(n, u, v, seed, p, R, alpha, k):
+    G = oracle.Graph(n, u, v)
+    L = G.labels(seed, p, R)
+    ctr = oracle.centers(n, seed, alpha)
+    lab, sz = oracle.compact(L, ctr)
+    o = dict(L=L, gains=oracle.gains(L), centers=ctr, label=lab, size=sz)
+    if k:
+        o["seeds"], o["seed_gains"] = oracle.greedy(L, k)
+        o["spread"] = oracle.spread(L, o["seeds"])
+    return o
+
+
+def _compare(g, o, k):
+    for r, lab in g["labels"].items():
+        assert np.array_equal(lab, o["L"][r]), f"labels of sketch {r}"
+    assert np.array_equal(g["gains"], o["gains"]), "initial gains"
+    assert np.array_equal(g["centers"], o["centers"]), "centers"
+    assert np.array_equal(g["label"], o["label"]), "compact labels"
+    assert np.array_equal(g["size"], o["size"]), "compact sizes"
+    if k:
+        assert np.array_equal(g["seeds"], o["seeds"]), (g["seeds"], o["seeds"])
+        assert np.array_equal(g["seed_gains"], o["seed_gains"])
+        assert g["spread"] == o["spread"] == int(o["seed_gains"].sum())
+
+
+def test_er_full_labels_workload():
+    """n=2000, m=10^4 Erdos-Renyi, p=0.05, R=256, full labels, k=10 (all sketches checked)."""
+    n, u, v, prm = graphgen.workload("er_n2000_m10000")
+    g = _run(n, u, v, prm["seed"], prm["p"], prm["R"], prm["alpha"], prm["k"])
+    o = _oracle(n, u, v, prm["seed"], prm["p"], prm["R"], prm["alpha"], prm["k"])
+    _compare(g, o, prm["k"])
+    with im.IMContext(n, u, v) as ctx:
+        ctx.build_sketches(prm["R"], prm["seed"], prm["p"], prm["alpha"])
+        for r in range(prm["R"]):
+            assert np.array_equal(ctx.labels(r), o["L"][r]), r
+
+
+@pytest.mark.parametrize("alpha", [0.5, 0.1, 0.01])
+@pytest.mark.parametrize("p", [0.05, 0.2])
+def test_compact_sketches(alpha, p):
+    n, u, v = graphgen.erdos_renyi(3001, 9007, 4)
+    g = _run(n, u, v, 42, p, 77, alpha, 12)
+    o = _oracle(n, u, v, 42, p, 77, alpha, 12)
+    _compare(g, o, 12)
+
+
+def test_small_alpha_forces_global_fallback_search():
+    # p well above the percolation threshold: a giant component with very few centers, so
+    # many searches exceed the shared-memory queue and spill to the global one
+    n, u, v = graphgen.erdos_renyi(4000, 12000, 9)
+    g = _run(n, u, v, 7, 0.4, 40, 0.001, 6)
+    o = _oracle(n, u, v, 7, 0.4, 40, 0.001, 6)
+    _compare(g, o, 6)
+    assert g["stats"]["bfs_fallbacks"] > 0
+
+
+@pytest.mark.parametrize("batch", [1, 2, 4, 8, 16, 32])
+def test_sketch_batch_sizes_agree(batch):
+    n, u, v = graphgen.erdos_renyi(1500, 6001, 3)
+    g = _run(n, u, v, 42, 0.1, 45, 0.2, 5, batch=batch)
+    o = _oracle(n, u, v, 42, 0.1, 45, 0.2, 5)
+    _compare(g, o, 5)
+
+
+@pytest.mark.parametrize("R", [1, 31, 33, 64])
+def test_ragged_sketch_counts(R):
+    n, u, v = graphgen.erdos_renyi(777, 3333, 5)
+    g = _run(n, u, v, 11, 0.1, R, 0.3, 7)
+    o = _oracle(n, u, v, 11, 0.1, R, 0.3, 7)
+    _compare(g, o, 7)
+
+
+def test_p_zero_and_p_one():
+    n, u, v = graphgen.erdos_renyi(500, 700, 2)
+    for p in (0.0, 1.0):
+        for alpha in (1.0, 0.25):
+            g = _run(n, u, v, 42, p, 16, alpha, 5)
+            o = _oracle(n, u, v, 42, p, 16, alpha, 5)
+            _compare(g, o, 5)
+    g = _run(n, u, v, 42, 0.0, 16, 1.0, 5)
+    assert list(g["seeds"]) == [0, 1, 2, 3, 4] and g["spread"] == 5 * 16
+
+
+def test_no_edges_and_single_vertex():
+    e = np.zeros(0, np.uint32)
+    g = _run(5, e, e, 42, 0.5, 8, 1.0, 5)
+    assert list(g["seeds"]) == [0, 1, 2, 3, 4] and np.all(g["gains"] == 8)
+    g = _run(1, e, e, 42, 0.5, 3, 1.0, 1)
+    assert list(g["seeds"]) == [0] and g["spread"] == 3
+
+
+def test_select_every_vertex():
+    n, u, v = graphgen.erdos_renyi(60, 150, 8)
+    g = _run(n, u, v, 42, 0.3, 20, 0.5, n)
+    o = _oracle(n, u, v, 42, 0.3, 20, 0.5, n)
+    _compare(g, o, n)
+    assert sorted(g["seeds"].tolist()) == list(range(n))
+
+
+def test_parallel_edges_are_sampled_independently():
+    # a multigraph: every edge twice, each copy with its own edge id
+    n, u, v = graphgen.erdos_renyi(400, 900, 12)
+    uu, vv = np.concatenate([u, u]), np.concatenate([v, v])
+    g = _run(n, uu, vv, 42, 0.2, 32, 0.2, 6)
+    o = _oracle(n, uu, vv, 42, 0.2, 32, 0.2, 6)
+    _compare(g, o, 6)
+
+
+def test_prefix_consistency_and_reset():
+    n, u, v = graphgen.erdos_renyi(2000, 8000, 6)
+    with im.IMContext(n, u, v) as ctx:
+        ctx.build_sketches(64, 42, 0.08, 0.2)
+        s5, g5 = ctx.select_seeds(5)
+        s12, g12 = ctx.select_seeds(12)
+        s3, _ = ctx.select_seeds(3)
+        assert np.array_equal(s12[:5], s5) and np.array_equal(g12[:5], g5)
+        assert np.array_equal(s3, s5[:3])
+        ctx.reset_selection()
+        s12b, g12b = ctx.select_seeds(12)
+        assert np.array_equal(s12, s12b) and np.array_equal(g12, g12b)
+
+
+def test_spread_of_arbitrary_seed_sets():
+    n, u, v = graphgen.erdos_renyi(2500, 9000, 13)
+    rng = np.random.default_rng(1)
+    sets = [rng.choice(n, k, replace=True).astype(np.uint32) for k in (1, 7, 50, 333)]
+    sets.append(np.array([5, 5, 5], np.uint32))
+    sets.append(np.zeros(0, np.uint32))
+    for alpha in (1.0, 0.05):
+        g = _run(n, u, v, 42, 0.15, 48, alpha, 0, spread_sets=sets)
+        L = oracle.Graph(n, u, v).labels(42, 0.15, 48)
+        for s, got in zip(sets, g["spreads"]):
+            assert got == (oracle.spread(L, s) if len(s) else 0)
+
+
+def test_device_pointer_input_and_torch_stream():
+    n, u, v = graphgen.erdos_renyi(1000, 4000, 14)
+    du = torch.from_numpy(u.view(np.int32)).cuda()
+    dv = torch.from_numpy(v.view(np.int32)).cuda()
+    stream = torch.cuda.Stream()
+    with im.IMContext(n, du, dv, stream=stream.cuda_stream) as ctx:
+        ctx.build_sketches(32, 42, 0.1, 0.3)
+        seeds, gains = ctx.select_seeds(6)
+        out = torch.empty(n, dtype=torch.int32, device="cuda")
+        ctx.labels(3, out)
+        torch.cuda.synchronize()
+    o = _oracle(n, u, v, 42, 0.1, 32, 0.3, 6)
+    assert np.array_equal(seeds, o["seeds"]) and np.array_equal(gains, o["seed_gains"])
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), o["L"][3])
+
+
+def test_argument_errors():
+    n, u, v = graphgen.erdos_renyi(100, 200, 1)
+    with im.IMContext(n, u, v) as ctx:
+        with pytest.raises(im.IMError) as e:
+            ctx.select_seeds(1)
+        assert e.value.code == im.IM_ESTATE
+        for bad in [dict(R=0, alpha=1.0), dict(R=4, alpha=0.0), dict(R=4, alpha=1.5)]:
+            with pytest.raises(im.IMError) as e:
+                ctx.build_sketches(bad["R"], 42, 0.1, bad["alpha"])
+            assert e.value.code == im.IM_EINVAL
+        ctx.build_sketches(4, 42, 0.1, 1.0)
+        with pytest.raises(im.IMError):
+            ctx.select_seeds(101)
+        with pytest.raises(im.IMError):
+            ctx.spread(np.array([100], np.uint32))
+        with pytest.raises(im.IMError):
+            ctx.labels(4)
+    bad_u = np.array([0, 3], np.uint32)
+    bad_v = np.array([1, 3], np.uint32)
+    with pytest.raises(im.IMError) as e:
+        im.IMContext(4, bad_u, bad_v)
+    assert e.value.code == im.IM_EINVAL
+
+
+def test_lazy_evaluation_counts_are_bounded():
+    # Sec. 4: batched lazy evaluation does at most a constant factor more work than CELF
+    n, u, v, prm = graphgen.workload("er_n2000_m10000")
+    G = oracle.Graph(n, u, v)
+    L = G.labels(prm["seed"], prm["p"], prm["R"])
+    k = 30
+    _, _, ev_celf = oracle.celf(L, k)
+    with im.IMContext(n, u, v) as ctx:
+        ctx.build_sketches(prm["R"], prm["seed"], prm["p"], 1.0)
+        ctx.select_seeds(k)
+        ev = ctx.round_evals()
+    assert ev[0] == 0
+    assert np.all(ev <= 4 * ev_celf + 2)
