@@ -154,6 +154,41 @@ const char* im_kernel_name(int kernel_id);
  * next im_build_sketches. */
 int im_set_sketch_batch(im_ctx* ctx, uint32_t batch);
 
+/*
+ * im_sketch_static -- labels and component sizes of one sketch, for callers that cannot
+ * allocate device memory.  The paper has no counterpart of this call.
+ *
+ * Who needs it: code that runs inside a host process which owns all device memory itself,
+ * e.g. a serving or database process whose pool allocator hands out every buffer and caps
+ * its footprint, or a latency-critical loop.  There a cudaMalloc would bypass the pool's
+ * accounting, may fail under its cap, and (with cudaFree) synchronises the whole device.
+ * Everything else in this ABI allocates through its context; this call allocates nothing:
+ * no cudaMalloc, no cudaFree, no allocating library routine.
+ *
+ *   n         vertices, 1 <= n <= IM_STATIC_MAX_N.
+ *   m, d_u, d_v  m undirected edges as two DEVICE arrays of vertex ids (edge id = index),
+ *             u != v, both < n; not modified.
+ *   seed, p, r   sketch r under the same live-edge rule as im_build_sketches.
+ *   d_labels  DEVICE output, n entries: smallest vertex id of the component of v (or NULL).
+ *   d_sizes   DEVICE output, n entries: |C_r(v)| (or NULL; not both NULL).
+ *   stream    cudaStream_t to run on (NULL: the legacy default stream).  The call returns
+ *             when its work on that stream has finished.
+ *
+ * Scratch: a file-scope static device array of 2 * IM_STATIC_MAX_N + 64 uint32 words
+ * (8 MiB + 256 B), present on every device where the library is loaded, until the process
+ * exits.  Its device address is looked up (cudaGetSymbolAddress) by the first call made with
+ * a given device current, so make that first call before any stream capture.  All calls
+ * share the array; each call clears what it needs, but calls whose GPU work overlaps (two
+ * streams, two threads) race on it and give wrong results: serialise them.
+ * Errors: IM_EINVAL (n out of range, m >= 2^32, NULL arrays, an edge id >= n or a self-loop
+ * found while sampling -- outputs are then undefined), IM_ECUDA.  im_last_error(NULL)
+ * describes the failure.
+ */
+#define IM_STATIC_MAX_N (1u << 20)
+int im_sketch_static(uint32_t n, uint64_t m, const uint32_t* d_u, const uint32_t* d_v,
+                     uint64_t seed, double p, uint32_t r, uint32_t* d_labels, uint32_t* d_sizes,
+                     void* stream);
+
 /* The context's stream (a cudaStream_t). */
 void* im_stream(im_ctx* ctx);
 

@@ -64,6 +64,7 @@ def lib():
         "im_kernel_name": ([i32], c.c_char_p),
         "im_set_sketch_batch": ([vp, u32], i32),
         "im_stream": ([vp], vp),
+        "im_sketch_static": ([u32, u64, vp, vp, u64, dbl, u32, vp, vp, vp], i32),
         "im_last_error": ([vp], c.c_char_p),
         "im_destroy": ([vp], None),
     }
@@ -206,6 +207,22 @@ def im_set_sketch_batch(ctx, batch: int):
 
 def im_stream(ctx) -> int:
     return int(lib().im_stream(ctx) or 0)
+
+
+def im_sketch_static(n: int, d_u, d_v, seed: int, p: float, r: int, d_labels=None, d_sizes=None,
+                     stream=None):
+    """Labels / component sizes of sketch r without any device allocation (device buffers)."""
+    for t in (d_u, d_v, d_labels, d_sizes):
+        if t is not None and not getattr(t, "is_cuda", False):
+            raise ValueError("im_sketch_static takes device tensors only")
+    rc = lib().im_sketch_static(n, int(len(d_u)), ctypes.c_void_p(d_u.data_ptr()),
+                                ctypes.c_void_p(d_v.data_ptr()), seed, p, r,
+                                ctypes.c_void_p(d_labels.data_ptr()) if d_labels is not None else None,
+                                ctypes.c_void_p(d_sizes.data_ptr()) if d_sizes is not None else None,
+                                ctypes.c_void_p(stream) if stream else None)
+    if rc != IM_OK:
+        msg = lib().im_last_error(None)
+        raise IMError(rc, msg.decode() if msg else "")
 
 
 def im_destroy(ctx):

@@ -9,47 +9,11 @@
 //   compress    parent[b][v] <- root, cnt[b][root] += 1 (warp-aggregated)
 //   gain        Delta[v] += sum_b cnt[b][root_b(v)]; for centers: label, size (Alg. 3)
 #include "im_internal.cuh"
+#include "im_uf.cuh"
 
 using namespace imk;
 
 namespace {
-
-// ---- union-find ---------------------------------------------------------------------
-// Reads go through L2 (__ldcg) so that a spin over a root another SM has just hooked
-// always sees the new parent.
-
-template <bool kAll>
-__device__ __forceinline__ bool before(const uint32_t* __restrict__ cbits, uint32_t a, uint32_t b) {
-    if (kAll) return a < b;
-    uint32_t ca = (__ldg(cbits + (a >> 5)) >> (a & 31)) & 1u;
-    uint32_t cb = (__ldg(cbits + (b >> 5)) >> (b & 31)) & 1u;
-    return ca != cb ? ca > cb : a < b;
-}
-
-__device__ __forceinline__ uint32_t find_root(uint32_t* P, uint32_t x) {
-    for (;;) {
-        uint32_t p = __ldcg(P + x);
-        if (p == x) return x;
-        uint32_t gp = __ldcg(P + p);
-        if (gp == p) return p;
-        __stcg(P + x, gp);   // path halving: gp is an ancestor of x
-        x = gp;
-    }
-}
-
-template <bool kAll>
-__device__ __forceinline__ void unite(uint32_t* P, const uint32_t* cbits, uint32_t a, uint32_t b) {
-    for (;;) {
-        a = find_root(P, a);
-        b = find_root(P, b);
-        if (a == b) return;
-        if (before<kAll>(cbits, b, a)) { uint32_t t = a; a = b; b = t; }
-        // hook the later root b under the earlier root a
-        uint32_t old = atomicCAS(P + b, b, a);
-        if (old == b) return;
-        b = old;
-    }
-}
 
 __global__ void k_batch_init(uint32_t* __restrict__ parent, uint32_t* __restrict__ cnt,
                              uint32_t n, uint32_t nb) {
@@ -101,9 +65,6 @@ k_sample_union(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, ui
 }
 
 // grid.y = sketch within the batch; full compression + component-size histogram.
-// No unions run here, so every root is final; the only value ever written is a vertex's
-// root (a path-halving write of an intermediate ancestor could land after another thread
-// stored the root and leave the array not fully compressed).
 __global__ void __launch_bounds__(256)
 k_compress_count(uint32_t* __restrict__ parent, uint32_t* __restrict__ cnt, uint32_t n) {
     uint32_t* P = parent + (size_t)blockIdx.y * n;
@@ -113,15 +74,7 @@ k_compress_count(uint32_t* __restrict__ parent, uint32_t* __restrict__ cnt, uint
         uint32_t v = base + threadIdx.x;
         bool act = v < n;
         uint32_t root = 0;
-        if (act) {
-            root = v;
-            for (uint32_t p = __ldcg(P + root); p != root; p = __ldcg(P + root)) root = p;
-            for (uint32_t x = v; x != root;) {
-                const uint32_t nx = __ldcg(P + x);
-                if (nx != root) __stcg(P + x, root);
-                x = nx;
-            }
-        }
+        if (act) root = compress_to_root(P, v);
         if (C) {
             unsigned am = __ballot_sync(0xffffffffu, act);
             if (act) {
