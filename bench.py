@@ -306,7 +306,8 @@ def run_ours(args, n, u, v, prm):
             "time_to_k_ms": ms_build + ms_select,
             "sketch_ms": ms_build, "select_ms": ms_select,
             "sketch_pairs_per_s": pairs / (ms_build / 1e3),
-            "evaluations": int(st["evaluations"]) // max(1, args.steps),
+            "evaluations": int(st["evaluations"]),
+            "refresh_batches": int(st["refresh_batches"]),
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": pairs * ws / e2e_s, "unit": "pairs/s",

@@ -133,6 +133,10 @@ typedef struct {
     uint64_t bfs_fallbacks;         /* (v, r) searches that spilled to the global queue  */
     uint64_t launches;              /* kernels launched by this context                  */
     uint32_t sketch_batch;          /* sketches processed per edge pass                  */
+    uint64_t hop1_arcs;             /* arcs scanned by first-hop searches (32 sketches each) */
+    uint64_t hop2_searches;         /* (vertex, sketch) searches that went past the 1st hop */
+    uint64_t hop2_chunks;           /* 32-arc chunks scanned by those searches             */
+    uint64_t refresh_batches;       /* batches evaluated by recomputing the sketches        */
 } im_stats;
 
 int im_get_stats(im_ctx* ctx, im_stats* out);
@@ -188,6 +192,13 @@ int im_set_sketch_batch(im_ctx* ctx, uint32_t batch);
 int im_sketch_static(uint32_t n, uint64_t m, const uint32_t* d_u, const uint32_t* d_v,
                      uint64_t seed, double p, uint32_t r, uint32_t* d_labels, uint32_t* d_sizes,
                      void* stream);
+
+/* Tuning: re-evaluation batches of at least `min_batch` candidates are evaluated by
+ * recomputing every sketch's components (Sketch(r), Alg. 3) and looking each candidate up,
+ * instead of one GetCenter search per (candidate, sketch); the values are identical.
+ * 0 = automatic (max(16384, n / 16)); UINT64_MAX disables it.  Takes effect at the next
+ * im_build_sketches. */
+int im_set_refresh_threshold(im_ctx* ctx, uint64_t min_batch);
 
 /* The context's stream (a cudaStream_t). */
 void* im_stream(im_ctx* ctx);

@@ -18,7 +18,7 @@ const char* const kNames[K_COUNT] = {
     "batch_init", "sample_union", "compress_count", "gain_compact", "init_keys",
     "reduce_reset", "reduce", "sel_init", "sel_hist", "sel_pick", "gather", "eval",
     "fallback", "finalize", "mark_seed", "spread_tasks", "spread_dedup", "labels_min",
-    "labels_out"};
+    "labels_out", "arc_keys", "sample_emit", "union", "cover_roots", "refresh_gather"};
 
 int bitlen64(uint64_t x) {
     int b = 0;
@@ -48,8 +48,9 @@ void free_sketch_state(im_ctx* c) {
     dfree(c->d_cbits); dfree(c->d_cidx); dfree(c->d_centers);
     dfree(c->d_label); dfree(c->d_size); dfree(c->d_gain0);
     dfree(c->d_key); dfree(c->d_stamp); dfree(c->d_seedflag);
-    dfree(c->d_batch); dfree(c->d_fresh);
-    dfree(c->d_parent); dfree(c->d_cnt);
+    dfree(c->d_batch); dfree(c->d_fresh); dfree(c->d_seed_list);
+    dfree(c->d_parent); dfree(c->d_cnt); dfree(c->d_live); dfree(c->d_live_n);
+    c->live_cap = 0;
     dfree(c->d_fb_queue); dfree(c->d_fb_bits); dfree(c->d_fb_tasks);
     c->batch_alloc = 0;
     c->fb_slots = 0;
@@ -201,6 +202,13 @@ int im_set_sketch_batch(im_ctx* c, uint32_t batch) {
     return IM_OK;
 }
 
+int im_set_refresh_threshold(im_ctx* c, uint64_t min_batch) {
+    if (!c) return IM_EINVAL;
+    c->refresh_req = min_batch;
+    if (c->built) c->refresh_min = min_batch ? min_batch : std::max<uint64_t>(16384, c->n / 16);
+    return IM_OK;
+}
+
 int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alpha) {
     if (!c) return IM_EINVAL;
     if (R == 0 || R > 65536) return im_fail(c, IM_EINVAL, "R must be in [1, 65536]");
@@ -242,8 +250,18 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
     const size_t nc = (size_t)rho * R;
     bool ok = dalloc(c->d_gain0, n) && dalloc(c->d_key, n) && dalloc(c->d_stamp, n) &&
               dalloc(c->d_seedflag, n) && dalloc(c->d_batch, n) && dalloc(c->d_fresh, n) &&
+              dalloc(c->d_seed_list, n) &&
               dalloc(c->d_label, nc) && dalloc(c->d_size, nc) &&
               dalloc(c->d_parent, (size_t)B * n) && dalloc(c->d_cnt, (size_t)B * n);
+    if (ok && c->m > 0 && (smp.all_live || smp.T != 0)) {
+        // live-pair records of one batch: expected p m B, with a generous margin; a batch that
+        // still overflows falls back to the fused sample+union loop on the device
+        const double ex = (smp.all_live ? 1.0 : p) * (double)c->m * B;
+        double cap = 1.3 * ex + 16.0 * std::sqrt(ex) + 65536.0;
+        if (cap > (double)(1ull << 26)) cap = (double)(1ull << 26);
+        c->live_cap = (uint64_t)cap;
+        ok = dalloc(c->d_live, c->live_cap) && dalloc(c->d_live_n, 1);
+    }
     if (ok && !all) {
         const size_t nw = ((size_t)n + 31) / 32;
         c->fb_slots = 8;
@@ -259,6 +277,7 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
     }
     c->batch_alloc = B;
     c->compact_cap = nc;
+    c->refresh_min = c->refresh_req ? c->refresh_req : std::max<uint64_t>(16384, n / 16);
     int rc = IM_OK;
     if (!all) {
         uint32_t* flags = nullptr;
@@ -274,7 +293,8 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
         dfree(pos);
         if (rc) { free_sketch_state(c); return rc; }
     }
-    rc = im_sketch_batches(c);
+    rc = im_arc_keys(c, smp.salt);
+    if (!rc) rc = im_sketch_batches(c);
     if (!rc) rc = im_selection_init(c);
     if (!rc) {
         cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -422,6 +442,10 @@ int im_get_stats(im_ctx* c, im_stats* out) {
         cudaMemcpyAsync(c->h_sel, c->d_sel, sizeof(SelState), cudaMemcpyDeviceToHost, c->stream);
         cudaStreamSynchronize(c->stream);
         out->bfs_fallbacks = c->h_sel->fb_total;
+        out->hop1_arcs = c->h_sel->hop1_arcs;
+        out->hop2_searches = c->h_sel->hop2_calls;
+        out->hop2_chunks = c->h_sel->hop2_chunks;
+        out->refresh_batches = c->refresh_batches;
     }
     return IM_OK;
 }

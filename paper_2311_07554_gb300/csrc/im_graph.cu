@@ -32,14 +32,27 @@ __global__ void k_csr_degree(const uint2* __restrict__ edges, uint64_t m,
 // inside an adjacency list is not fixed; no result depends on it.
 __global__ void k_csr_fill(const uint2* __restrict__ edges, uint64_t m,
                            const uint64_t* __restrict__ off, uint32_t* __restrict__ cursor,
-                           uint2* __restrict__ arcs) {
+                           uint4* __restrict__ arcs) {
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
         uint2 ed = edges[e];
         uint64_t pa = off[ed.x] + atomicAdd(cursor + ed.x, 1u);
-        arcs[pa] = make_uint2(ed.y, (uint32_t)e);
+        arcs[pa] = make_uint4(ed.y, (uint32_t)e, 0u, 0u);
         uint64_t pb = off[ed.y] + atomicAdd(cursor + ed.y, 1u);
-        arcs[pb] = make_uint2(ed.x, (uint32_t)e);
+        arcs[pb] = make_uint4(ed.x, (uint32_t)e, 0u, 0u);
+    }
+}
+
+// Store the per-edge hash key mix(salt ^ e) in every arc (Sec. 2 fusion: the sampling of
+// edge e in sketch r is then one more mix of key + (r+1) G).
+__global__ void k_arc_keys(uint4* __restrict__ arcs, uint64_t narcs, uint64_t salt) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < narcs; a += stride) {
+        uint4 x = arcs[a];
+        const uint64_t key = mix64(salt ^ (uint64_t)x.y);
+        x.z = (uint32_t)key;
+        x.w = (uint32_t)(key >> 32);
+        arcs[a] = x;
     }
 }
 
@@ -165,7 +178,7 @@ int im_graph_build(im_ctx* c, const uint32_t* d_u, const uint32_t* d_v) {
     IM_CUDA(c, cudaMemsetAsync(c->d_edges, 0, m_pad * sizeof(uint2), c->stream));
     if (cudaMalloc(&c->d_off, ((size_t)n + 1) * sizeof(uint64_t)) != cudaSuccess)
         return im_fail(c, IM_ENOMEM, "csr offsets");
-    if (cudaMalloc(&c->d_arcs, (2 * m + 2) * sizeof(uint2)) != cudaSuccess)
+    if (cudaMalloc(&c->d_arcs, (2 * m + 2) * sizeof(uint4)) != cudaSuccess)
         return im_fail(c, IM_ENOMEM, "csr arcs");
     uint32_t* deg = nullptr;
     unsigned int* bad = nullptr;
@@ -206,4 +219,14 @@ int im_graph_build(im_ctx* c, const uint32_t* d_u, const uint32_t* d_v) {
     } while (0);
     cudaFree(deg);
     return rc;
+}
+
+int im_arc_keys(im_ctx* c, uint64_t salt) {
+    if (c->arc_keys_valid && c->arc_salt == salt) return IM_OK;
+    if (c->m > 0)
+        IM_LAUNCH(c, K_ARC_KEYS, k_arc_keys, grid_for(2 * c->m, 256, 152u * 16u), 256, 0, c->d_arcs, 2 * c->m, salt);
+    IM_CUDA(c, cudaGetLastError());
+    c->arc_salt = salt;
+    c->arc_keys_valid = true;
+    return IM_OK;
 }

@@ -48,7 +48,7 @@ struct GraphView {
     uint64_t m;
     const uint2* edges;     // m (padded to even): (u, v)
     const uint64_t* off;    // n + 1 CSR offsets
-    const uint2* arcs;      // 2m: (neighbour, edge id)
+    const uint4* arcs;      // 2m: (neighbour, edge id, key lo, key hi), key = mix(salt ^ e)
 };
 
 struct SketchView {
@@ -76,12 +76,16 @@ struct SelState {
     unsigned long long prefix, prefmask, need, taken, theta, borig;
     int shift, done;
     unsigned int hist[256];
+    unsigned int pass_blocks;       // blocks of the current radix pass that have finished
     unsigned long long eval_next;   // task counter of the evaluation kernel
     unsigned int batch_n;
     unsigned int fb_n;              // fallback tasks queued
     unsigned int fb_overflow;
     unsigned long long evals_total;
     unsigned long long fb_total;
+    unsigned long long hop1_arcs;       // arcs scanned by the first hop (per 32 sketches)
+    unsigned long long hop2_calls;      // (vertex, sketch) searches needing more than one hop
+    unsigned long long hop2_chunks;     // 32-arc chunks scanned by those searches
     unsigned int err;
     unsigned int pad;
 };
@@ -97,7 +101,7 @@ enum KernelId {
     K_BATCH_INIT, K_SAMPLE_UNION, K_COMPRESS_COUNT, K_GAIN_COMPACT, K_INIT_KEYS,
     K_REDUCE_RESET, K_REDUCE, K_SEL_INIT, K_SEL_HIST, K_SEL_PICK, K_GATHER, K_EVAL,
     K_FALLBACK, K_FINALIZE, K_MARK_SEED, K_SPREAD_TASKS, K_SPREAD_DEDUP, K_LABELS_MIN,
-    K_LABELS_OUT, K_COUNT
+    K_LABELS_OUT, K_ARC_KEYS, K_SAMPLE_EMIT, K_UNION, K_COVER_ROOTS, K_REFRESH_GATHER, K_COUNT
 };
 
 const char* kernel_name(int id);
@@ -118,7 +122,9 @@ struct im_ctx {
     uint64_t m = 0;
     uint2* d_edges = nullptr;
     uint64_t* d_off = nullptr;
-    uint2* d_arcs = nullptr;
+    uint4* d_arcs = nullptr;
+    uint64_t arc_salt = 0;
+    bool arc_keys_valid = false;
 
     // sketches
     bool built = false;
@@ -142,6 +148,10 @@ struct im_ctx {
     uint64_t* d_fresh = nullptr;
     imk::SelState* d_sel = nullptr;
     imk::SelState* h_sel = nullptr;  // pinned mirror
+    uint32_t* d_seed_list = nullptr;   // seeds chosen so far, on the device (n entries)
+    uint64_t refresh_min = 0;          // batches at least this large are evaluated by refresh
+    uint64_t refresh_req = 0;          // user setting (0 = automatic)
+    uint64_t refresh_batches = 0;
     std::vector<uint32_t> seeds;
     std::vector<uint64_t> seed_gains;
     std::vector<uint64_t> round_evals;
@@ -151,6 +161,9 @@ struct im_ctx {
     uint32_t batch_req = 0, batch_used = 0, batch_alloc = 0;
     uint32_t* d_parent = nullptr;
     uint32_t* d_cnt = nullptr;
+    uint4* d_live = nullptr;                 // live (u, v, sketch) records of one batch
+    unsigned long long* d_live_n = nullptr;
+    uint64_t live_cap = 0;
 
     // BFS fallback scratch
     uint32_t fb_slots = 0;
@@ -193,11 +206,15 @@ void im_prof_end(im_ctx* c, int kid, int ev0);
 // ---- launch wrappers (host) ------------------------------------------------------
 // im_graph.cu
 int im_graph_build(im_ctx* c, const uint32_t* d_u, const uint32_t* d_v);
+int im_arc_keys(im_ctx* c, uint64_t salt);
 int im_scan_u32_to_u64(im_ctx* c, const uint32_t* d_in, uint64_t* d_out, uint64_t count);
 // im_sketch.cu
 int im_select_centers(im_ctx* c, uint32_t* d_flags_tmp, uint64_t* d_scan_tmp);
 int im_sketch_batches(im_ctx* c);
 int im_labels_min(im_ctx* c, uint32_t r, uint32_t* d_out);
+int im_refresh_eval(im_ctx* c, const uint32_t* d_batch, const unsigned int* d_batch_n,
+                    unsigned long long* d_fresh, const uint32_t* d_seeds, uint32_t nseeds,
+                    uint64_t batch_hint);
 // im_select.cu
 int im_selection_init(im_ctx* c);
 int im_select_round(im_ctx* c);

@@ -41,32 +41,48 @@ struct BfsOut {
     uint32_t overflow;
 };
 
-__device__ BfsOut warp_bfs(const GraphView& g, const SketchView& s, uint32_t v, uint32_t r,
-                           uint32_t* q, bool want_seed) {
+// If init != nullptr, x's own arcs were already scanned: the queue starts as
+// [x, init[0], init[stride], ...] (x's live non-center neighbours, distinct) with head = 1.
+__device__ BfsOut warp_bfs_from(const GraphView& g, const SketchView& s, uint32_t v, uint32_t r,
+                                uint32_t* q, bool want_seed, const uint32_t* init, uint32_t ninit,
+                                uint32_t init_stride, SelState* st_counters) {
+    uint32_t chunks = 0;
     const unsigned lane = threadIdx.x & 31;
     BfsOut o;
     o.label = kNone; o.count = 0; o.minv = v; o.seen = 0; o.overflow = 0;
-    if (lane == 0) q[0] = v;
-    __syncwarp();
     uint32_t head = 0, tail = 1;
     uint32_t seen = want_seed ? (uint32_t)s.seed_flag[v] : 0u;
     uint32_t minv = v;
+    if (lane == 0) q[0] = v;
+    if (init) {
+        for (uint32_t t = lane; t < ninit; t += 32) {
+            const uint32_t y = init[t * init_stride];
+            q[1 + t] = y;
+            if (want_seed && s.seed_flag[y]) seen = 1;
+            minv = min(minv, y);
+        }
+        head = 1;
+        tail = 1 + ninit;
+    }
+    __syncwarp();
     while (head < tail) {
         const uint32_t x = q[head++];
         const uint64_t a0 = g.off[x], a1 = g.off[x + 1];
         for (uint64_t base = a0; base < a1; base += 32) {
+            ++chunks;
             const uint64_t a = base + lane;
             bool live = false;
             uint32_t y = 0;
             if (a < a1) {
-                const uint2 arc = g.arcs[a];
+                const uint4 arc = g.arcs[a];
                 y = arc.x;
-                live = edge_live(s.smp, edge_key(s.smp, arc.y), r);
+                live = edge_live(s.smp, ((uint64_t)arc.w << 32) | arc.z, r);
             }
             const unsigned cb = __ballot_sync(kFull, live && is_center(s, y));
             if (cb) {
                 const uint32_t yc = __shfl_sync(kFull, y, __ffs(cb) - 1);
                 o.label = s.label[(size_t)center_index(s, yc) * s.R + r];
+                if (lane == 0 && st_counters) atomicAdd(&st_counters->hop2_chunks, (unsigned long long)chunks);
                 return o;
             }
             bool fresh = live;
@@ -90,11 +106,94 @@ __device__ BfsOut warp_bfs(const GraphView& g, const SketchView& s, uint32_t v, 
             __syncwarp();
         }
     }
+    if (lane == 0 && st_counters) atomicAdd(&st_counters->hop2_chunks, (unsigned long long)chunks);
     o.seen = __any_sync(kFull, seen) ? 1u : 0u;
 #pragma unroll
     for (int d = 16; d; d >>= 1) minv = min(minv, __shfl_xor_sync(kFull, minv, d));
     o.minv = minv;
     o.count = tail;
+    return o;
+}
+
+// ---- GetCenter (Alg. 3) for 32 sketches at once: lane l answers sketch r_lo + l ---------
+// First hop: the warp loads 32 arcs of the start vertex x with one coalesced load, then
+// broadcasts them one by one (shuffles); every lane tests the arc in its own sketch.  A lane
+// is done when it meets a center, or when x has no live arc in its sketch.  A lane that saw
+// only non-center live neighbours keeps them (up to kLaneQ - 1, interleaved by lane in
+// shared memory) and is finished by the warp-cooperative search, which starts from that
+// frontier instead of rescanning x.  Searches that outgrow kQcap go to k_fallback.
+constexpr uint32_t kLaneQ = 32;
+
+struct LaneRes {
+    uint32_t label, count, minv, seen, overflow;
+};
+
+__device__ BfsOut warp_bfs_from(const GraphView& g, const SketchView& s, uint32_t v, uint32_t r,
+                                uint32_t* q, bool want_seed, const uint32_t* init, uint32_t ninit,
+                                uint32_t init_stride, SelState* st_counters);
+
+__device__ LaneRes get_center_32(const GraphView& g, const SketchView& s, uint32_t x, uint32_t r_lo,
+                                 uint32_t r_hi, uint32_t* ql, uint32_t* qw, bool want_seed,
+                                 SelState* st_counters) {
+    const unsigned lane = threadIdx.x & 31;
+    const uint32_t r = r_lo + lane;
+    bool act = r < r_hi;
+    LaneRes o;
+    o.label = kNone; o.count = 1; o.minv = x; o.overflow = 0;
+    o.seen = (act && want_seed) ? (uint32_t)s.seed_flag[x] : 0u;
+    uint32_t cnt = 0;        // live non-center neighbours of x recorded
+    bool over = false;       // more than kLaneQ - 1 of them
+    const uint64_t rg = (uint64_t)(r + 1u) * kGamma;
+    const uint64_t a0 = g.off[x], a1 = g.off[x + 1];
+    for (uint64_t base = a0; base < a1; base += 32) {
+        if (!__any_sync(kFull, act)) break;
+        const uint64_t a = base + lane;
+        uint4 arc = make_uint4(0, 0, 0, 0);
+        if (a < a1) arc = g.arcs[a];
+        const uint32_t nv = (uint32_t)min((uint64_t)32, a1 - base);
+        for (uint32_t i = 0; i < nv; ++i) {
+            const uint32_t y = __shfl_sync(kFull, arc.x, i);
+            const uint32_t klo = __shfl_sync(kFull, arc.z, i);
+            const uint32_t khi = __shfl_sync(kFull, arc.w, i);
+            if (act) {
+                const uint64_t key = ((uint64_t)khi << 32) | klo;
+                if (s.smp.all_live || mix64(key + rg) < s.smp.T) {
+                    if (is_center(s, y)) {
+                        o.label = s.label[(size_t)center_index(s, y) * s.R + r];
+                        act = false;
+                    } else if (!over) {
+                        bool dup = false;   // parallel edges reach the same neighbour twice
+                        for (uint32_t t = 0; t < cnt; ++t)
+                            if (ql[t * 32 + lane] == y) { dup = true; break; }
+                        if (!dup) {
+                            if (cnt == kLaneQ - 1) over = true;
+                            else ql[(cnt++) * 32 + lane] = y;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    __syncwarp();
+    // lanes still active: no center among x's neighbours; cnt == 0 means x is alone
+    unsigned need = __ballot_sync(kFull, act && (cnt > 0 || over));
+    if (lane == 0 && st_counters) {
+        atomicAdd(&st_counters->hop1_arcs, (unsigned long long)(a1 - a0));
+        atomicAdd(&st_counters->hop2_calls, (unsigned long long)__popc(need));
+    }
+    while (need) {
+        const int l = __ffs(need) - 1;
+        need &= need - 1;
+        const uint32_t ninit = __shfl_sync(kFull, over ? 0xFFFFFFFFu : cnt, l);
+        const BfsOut w = (ninit == 0xFFFFFFFFu)
+                             ? warp_bfs_from(g, s, x, r_lo + l, qw, want_seed, nullptr, 0, 0, st_counters)
+                             : warp_bfs_from(g, s, x, r_lo + l, qw, want_seed, ql + l, ninit, 32, st_counters);
+        if ((int)lane == l) {
+            o.label = w.label; o.count = w.count; o.minv = w.minv; o.seen = w.seen;
+            o.overflow = w.overflow;
+        }
+        __syncwarp();
+    }
     return o;
 }
 
@@ -163,38 +262,51 @@ k_reduce(const uint64_t* __restrict__ key, const uint32_t* __restrict__ stamp,
 // Start of a batch: decide how to pick ~B of the largest stale keys (radix select on the
 // key bytes below the top byte of stale_max); take all when at most 2B remain.
 __global__ void k_sel_init(SelState* st, unsigned long long B) {
-    if (threadIdx.x != 0) return;
-    const unsigned long long nu = st->n_unev, smax = st->stale_max;
-    st->borig = B;
-    st->need = B;
-    st->taken = 0;
-    st->prefix = 0;
-    st->theta = 0;
-    if (nu <= 2 * B || smax == 0) {
-        st->done = 1;
-        st->shift = 0;
-        st->prefmask = 0;
-    } else {
-        const int top = 63 - __clzll((long long)smax);
-        const int shift = (top / 8) * 8;
-        st->shift = shift;
-        st->prefmask = (shift + 8 >= 64) ? 0ull : ~((1ull << (shift + 8)) - 1ull);
-        st->done = 0;
+    if (threadIdx.x == 0) {
+        const unsigned long long nu = st->n_unev, smax = st->stale_max;
+        st->borig = B;
+        st->need = B;
+        st->taken = 0;
+        st->prefix = 0;
+        st->theta = 0;
+        st->pass_blocks = 0;
+        if (nu <= 2 * B || smax == 0) {
+            st->done = 1;                // take every unevaluated candidate
+            st->shift = 0;
+            st->prefmask = 0;
+        } else if (B == 1) {
+            st->done = 1;                // keys are distinct: exactly the top stale key
+            st->theta = smax;
+            st->shift = 0;
+            st->prefmask = 0;
+        } else {
+            const int top = 63 - __clzll((long long)smax);
+            const int shift = (top / 8) * 8;
+            st->shift = shift;
+            st->prefmask = (shift + 8 >= 64) ? 0ull : ~((1ull << (shift + 8)) - 1ull);
+            st->done = 0;
+        }
+        st->batch_n = 0;
+        st->eval_next = 0;
+        st->fb_n = 0;
+        st->best = 0;
+        st->stale_max = 0;
+        st->n_unev = 0;
     }
-    for (int i = 0; i < 256; ++i) st->hist[i] = 0;
-    st->batch_n = 0;
-    st->eval_next = 0;
-    st->fb_n = 0;
-    st->best = 0;
-    st->stale_max = 0;
-    st->n_unev = 0;
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) st->hist[i] = 0;
 }
 
+// One radix pass over the unevaluated candidates: block histograms of the next key byte,
+// added to st->hist; the last block to finish picks the byte (parallel over 256 bins) and
+// either fixes the threshold theta (batch between B and 2B, or exact at the last byte) or
+// narrows the prefix for the next pass.
 __global__ void __launch_bounds__(256)
-k_sel_hist(const uint64_t* __restrict__ key, const uint32_t* __restrict__ stamp,
+k_sel_pass(const uint64_t* __restrict__ key, const uint32_t* __restrict__ stamp,
            const uint8_t* __restrict__ seedflag, uint32_t n, uint32_t round, SelState* st) {
     if (st->done) return;
     __shared__ unsigned int h[256];
+    __shared__ unsigned long long sfx[256];
+    __shared__ int s_last;
     for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
     __syncthreads();
     const unsigned long long prefix = st->prefix, pm = st->prefmask;
@@ -207,28 +319,47 @@ k_sel_hist(const uint64_t* __restrict__ key, const uint32_t* __restrict__ stamp,
     __syncthreads();
     for (int i = threadIdx.x; i < 256; i += blockDim.x)
         if (h[i]) atomicAdd(&st->hist[i], h[i]);
-}
-
-__global__ void k_sel_pick(SelState* st) {
-    if (threadIdx.x != 0 || st->done) return;
-    unsigned long long above = 0;
-    int d = 255;
-    for (; d > 0; --d) {
-        if (above + st->hist[d] >= st->need) break;
-        above += st->hist[d];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&st->pass_blocks, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // last block: suffix sums over the 256 bins (bin d counts keys whose byte is d)
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) sfx[i] = __ldcg(&st->hist[i]);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        // lane l owns bins 8l .. 8l+7; inclusive suffix sum from the top bin down
+        const int l = threadIdx.x;
+        unsigned long long loc[8], acc = 0;
+        for (int i = 7; i >= 0; --i) { acc += sfx[8 * l + i]; loc[i] = acc; }
+        unsigned long long tot_above = 0;   // keys in the bins of the lanes above
+        for (int j = 0; j < 32; ++j) {
+            const unsigned long long y = __shfl_sync(0xffffffffu, acc, j);
+            if (j > l) tot_above += y;
+        }
+        for (int i = 0; i < 8; ++i) sfx[8 * l + i] = loc[i] + tot_above;   // keys with byte >= bin
     }
-    const unsigned long long with_bin = st->taken + above + st->hist[d];
-    if (with_bin <= 2 * st->borig || st->shift == 0) {
-        st->theta = st->prefix | ((unsigned long long)d << st->shift);
-        st->done = 1;
-    } else {
-        st->taken += above;
-        st->need -= above;
-        st->prefix |= (unsigned long long)d << st->shift;
-        st->prefmask |= 255ull << st->shift;
-        st->shift -= 8;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long need = st->need;
+        int d = 255;
+        while (d > 0 && sfx[d] < need) --d;      // highest bin whose suffix reaches need
+        const unsigned long long above = (d < 255) ? sfx[d + 1] : 0ull;
+        const unsigned long long with_bin = st->taken + sfx[d];
+        if (with_bin <= 2 * st->borig || st->shift == 0) {
+            st->theta = st->prefix | ((unsigned long long)d << st->shift);
+            st->done = 1;
+        } else {
+            st->taken += above;
+            st->need -= above;
+            st->prefix |= (unsigned long long)d << st->shift;
+            st->prefmask |= 255ull << st->shift;
+            st->shift -= 8;
+        }
+        st->pass_blocks = 0;
     }
-    for (int i = 0; i < 256; ++i) st->hist[i] = 0;
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) st->hist[i] = 0;
 }
 
 __global__ void __launch_bounds__(256)
@@ -259,8 +390,10 @@ __global__ void __launch_bounds__(kEvalWarps * 32)
 k_eval(GraphView g, SketchView s, SelState* st, const uint32_t* __restrict__ batch,
        unsigned long long* __restrict__ fresh, FbTask* __restrict__ fbt, uint32_t fb_cap,
        uint32_t nchunk) {
-    __shared__ uint32_t qs[kEvalWarps][kQcap];
-    uint32_t* q = qs[threadIdx.x >> 5];
+    __shared__ uint32_t qls[kEvalWarps][32 * kLaneQ];
+    __shared__ uint32_t qws[kEvalWarps][kQcap];
+    uint32_t* ql = qls[threadIdx.x >> 5];
+    uint32_t* qw = qws[threadIdx.x >> 5];
     const unsigned lane = threadIdx.x & 31;
     const unsigned long long total = (unsigned long long)st->batch_n * nchunk;
     for (;;) {
@@ -271,29 +404,28 @@ k_eval(GraphView g, SketchView s, SelState* st, const uint32_t* __restrict__ bat
         const uint32_t j = (uint32_t)(t / nchunk), ch = (uint32_t)(t % nchunk);
         const uint32_t x = batch[j];
         const uint32_t r_lo = ch * 32, r_hi = min(s.R, r_lo + 32);
-        unsigned long long sum = 0;
+        const uint32_t r = r_lo + lane;
+        unsigned long long d = 0;
         if (is_center(s, x)) {
-            const uint32_t r = r_lo + lane;
             if (r < r_hi) {
                 const uint32_t l = s.label[(size_t)center_index(s, x) * s.R + r];
                 const uint32_t sz = s.size[(size_t)l * s.R + r];
-                sum = (sz & kCovered) ? 0u : sz;
+                d = (sz & kCovered) ? 0u : sz;
             }
-            sum = warp_sum_u64(sum);
         } else {
-            for (uint32_t r = r_lo; r < r_hi; ++r) {
-                const BfsOut o = warp_bfs(g, s, x, r, q, true);
+            const LaneRes o = get_center_32(g, s, x, r_lo, r_hi, ql, qw, true, st);
+            if (r < r_hi) {
                 if (o.overflow) {
-                    if (lane == 0) push_fallback(st, fbt, fb_cap, x, r, FB_EVAL, j);
+                    push_fallback(st, fbt, fb_cap, x, r, FB_EVAL, j);
                 } else if (o.label != kNone) {
                     const uint32_t sz = s.size[(size_t)o.label * s.R + r];
-                    sum += (sz & kCovered) ? 0u : sz;
+                    d = (sz & kCovered) ? 0u : sz;
                 } else {
-                    sum += o.seen ? 0u : o.count;
+                    d = o.seen ? 0u : o.count;
                 }
-                __syncwarp();
             }
         }
+        const unsigned long long sum = warp_sum_u64(d);
         if (lane == 0 && sum) atomicAdd(fresh + j, sum);
     }
 }
@@ -314,37 +446,34 @@ k_finalize(SelState* st, const uint32_t* __restrict__ batch,
     }
 }
 
-// MarkSeed (Alg. 3): in every sketch, flag the component of s as covered.
+// MarkSeed (Alg. 3): in every sketch, flag the component of s as covered.  One warp per
+// sketch: a single vertex is marked per round, so latency, not total work, decides.
 __global__ void __launch_bounds__(kEvalWarps * 32)
 k_mark_seed(GraphView g, SketchView s, SelState* st, uint32_t sd, FbTask* __restrict__ fbt,
-            uint32_t fb_cap, uint32_t nchunk, uint8_t* __restrict__ seedflag,
-            uint64_t* __restrict__ key) {
-    __shared__ uint32_t qs[kEvalWarps][kQcap];
-    uint32_t* q = qs[threadIdx.x >> 5];
+            uint32_t fb_cap, uint8_t* __restrict__ seedflag, uint64_t* __restrict__ key,
+            uint32_t* __restrict__ seed_list, uint32_t round) {
+    __shared__ uint32_t qws[kEvalWarps][kQcap];
+    uint32_t* qw = qws[threadIdx.x >> 5];
     const unsigned lane = threadIdx.x & 31;
-    const uint32_t ch = blockIdx.x * kEvalWarps + (threadIdx.x >> 5);
-    if (ch < nchunk) {
-        const uint32_t r_lo = ch * 32, r_hi = min(s.R, r_lo + 32);
+    const uint32_t r = blockIdx.x * kEvalWarps + (threadIdx.x >> 5);
+    if (r < s.R) {
         if (is_center(s, sd)) {
-            const uint32_t r = r_lo + lane;
-            if (r < r_hi) {
+            if (lane == 0) {
                 const uint32_t l = s.label[(size_t)center_index(s, sd) * s.R + r];
                 atomicOr(s.size + (size_t)l * s.R + r, kCovered);
             }
         } else {
-            for (uint32_t r = r_lo; r < r_hi; ++r) {
-                const BfsOut o = warp_bfs(g, s, sd, r, q, false);
-                if (lane == 0) {
-                    if (o.overflow) push_fallback(st, fbt, fb_cap, sd, r, FB_MARK, 0);
-                    else if (o.label != kNone) atomicOr(s.size + (size_t)o.label * s.R + r, kCovered);
-                }
-                __syncwarp();
+            const BfsOut o = warp_bfs_from(g, s, sd, r, qw, false, nullptr, 0, 0, st);
+            if (lane == 0) {
+                if (o.overflow) push_fallback(st, fbt, fb_cap, sd, r, FB_MARK, 0);
+                else if (o.label != kNone) atomicOr(s.size + (size_t)o.label * s.R + r, kCovered);
             }
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         seedflag[sd] = 1;
         key[sd] = 0;
+        seed_list[round] = sd;
     }
 }
 
@@ -383,9 +512,9 @@ k_fallback(GraphView g, SketchView s, SelState* st, const FbTask* __restrict__ f
                 bool live = false;
                 uint32_t y = 0;
                 if (a < a1) {
-                    const uint2 arc = g.arcs[a];
+                    const uint4 arc = g.arcs[a];
                     y = arc.x;
-                    live = edge_live(s.smp, edge_key(s.smp, arc.y), r);
+                    live = edge_live(s.smp, ((uint64_t)arc.w << 32) | arc.z, r);
                 }
                 const unsigned cb = __ballot_sync(kFull, live && is_center(s, y));
                 if (cb) {
@@ -443,8 +572,10 @@ __global__ void __launch_bounds__(kEvalWarps * 32)
 k_spread_tasks(GraphView g, SketchView s, SelState* st, const uint32_t* __restrict__ sd, uint32_t k,
                uint32_t nchunk, FbTask* __restrict__ fbt, uint32_t fb_cap,
                uint64_t* __restrict__ pairs) {
-    __shared__ uint32_t qs[kEvalWarps][kQcap];
-    uint32_t* q = qs[threadIdx.x >> 5];
+    __shared__ uint32_t qls[kEvalWarps][32 * kLaneQ];
+    __shared__ uint32_t qws[kEvalWarps][kQcap];
+    uint32_t* ql = qls[threadIdx.x >> 5];
+    uint32_t* qw = qws[threadIdx.x >> 5];
     const unsigned lane = threadIdx.x & 31;
     const uint64_t total = (uint64_t)k * nchunk;
     const uint64_t wstride = (uint64_t)gridDim.x * kEvalWarps;
@@ -452,28 +583,24 @@ k_spread_tasks(GraphView g, SketchView s, SelState* st, const uint32_t* __restri
         const uint32_t i = (uint32_t)(t / nchunk), ch = (uint32_t)(t % nchunk);
         const uint32_t x = sd[i];
         const uint32_t r_lo = ch * 32, r_hi = min(s.R, r_lo + 32);
+        const uint32_t r = r_lo + lane;
+        const size_t idx = (size_t)r * k + i;
         if (is_center(s, x)) {
-            const uint32_t r = r_lo + lane;
             if (r < r_hi) {
                 const uint32_t l = s.label[(size_t)center_index(s, x) * s.R + r];
                 const uint32_t sz = s.size[(size_t)l * s.R + r] & ~kCovered;
-                pairs[(size_t)r * k + i] = ((uint64_t)l << 32) | sz;
+                pairs[idx] = ((uint64_t)l << 32) | sz;
             }
         } else {
-            for (uint32_t r = r_lo; r < r_hi; ++r) {
-                const BfsOut o = warp_bfs(g, s, x, r, q, false);
-                if (lane == 0) {
-                    const size_t idx = (size_t)r * k + i;
-                    if (o.overflow) {
-                        push_fallback(st, fbt, fb_cap, x, r, FB_SPREAD, (uint32_t)idx);
-                    } else if (o.label != kNone) {
-                        pairs[idx] = ((uint64_t)o.label << 32) |
-                                     (s.size[(size_t)o.label * s.R + r] & ~kCovered);
-                    } else {
-                        pairs[idx] = ((uint64_t)(kNoCenterTag | o.minv) << 32) | o.count;
-                    }
+            const LaneRes o = get_center_32(g, s, x, r_lo, r_hi, ql, qw, false, st);
+            if (r < r_hi) {
+                if (o.overflow) {
+                    push_fallback(st, fbt, fb_cap, x, r, FB_SPREAD, (uint32_t)idx);
+                } else if (o.label != kNone) {
+                    pairs[idx] = ((uint64_t)o.label << 32) | (s.size[(size_t)o.label * s.R + r] & ~kCovered);
+                } else {
+                    pairs[idx] = ((uint64_t)(kNoCenterTag | o.minv) << 32) | o.count;
                 }
-                __syncwarp();
             }
         }
     }
@@ -553,6 +680,7 @@ int im_selection_init(im_ctx* c) {
     c->seed_gains.clear();
     c->round_evals.clear();
     c->batches = 0;
+    c->refresh_batches = 0;
     return IM_OK;
 }
 
@@ -577,20 +705,33 @@ int im_select_round(im_ctx* c) {
         if (h.n_unev == 0 || h.best > h.stale_max) break;
         unsigned long long B = 1ull << (j < 40 ? j : 40);
         if (B > h.n_unev) B = h.n_unev;
-        const uint64_t expect = (2 * B < h.n_unev ? 2 * B : h.n_unev);
-        IM_LAUNCH(c, K_SEL_INIT, k_sel_init, 1, 32, 0, st, B);
-        if (h.n_unev > 2 * B) {
-            for (int pass = 0; pass < 8; ++pass) {
-                IM_LAUNCH(c, K_SEL_HIST, k_sel_hist, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n,
+        uint64_t expect = (2 * B < h.n_unev ? 2 * B : h.n_unev);
+        // a batch this large is evaluated by recomputing the sketches, for all remaining
+        // candidates at once (the round then ends with every key fresh)
+        const bool refresh = expect >= c->refresh_min;
+        if (refresh) {
+            B = h.n_unev;
+            expect = h.n_unev;
+        }
+        IM_LAUNCH(c, K_SEL_INIT, k_sel_init, 1, 256, 0, st, B);
+        if (h.n_unev > 2 * B && B > 1) {
+            const int top = 63 - __builtin_clzll(h.stale_max);
+            for (int pass = 0; pass <= top / 8; ++pass)
+                IM_LAUNCH(c, K_SEL_HIST, k_sel_pass, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n,
                           round, st);
-                IM_LAUNCH(c, K_SEL_PICK, k_sel_pick, 1, 32, 0, st);
-            }
         }
         IM_LAUNCH(c, K_GATHER, k_gather, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n, round, st,
                   c->d_batch, (unsigned long long*)c->d_fresh);
-        IM_LAUNCH(c, K_EVAL, k_eval, search_grid(expect * nchunk), kEvalWarps * 32, 0, g, s, st,
-                  c->d_batch, (unsigned long long*)c->d_fresh, c->d_fb_tasks, c->fb_cap, nchunk);
-        launch_fallback(c, g, s);
+        if (refresh) {
+            rc = im_refresh_eval(c, c->d_batch, &st->batch_n, (unsigned long long*)c->d_fresh,
+                                 c->d_seed_list, round, expect);
+            if (rc) return rc;
+            c->refresh_batches++;
+        } else {
+            IM_LAUNCH(c, K_EVAL, k_eval, search_grid(expect * nchunk), kEvalWarps * 32, 0, g, s, st,
+                      c->d_batch, (unsigned long long*)c->d_fresh, c->d_fb_tasks, c->fb_cap, nchunk);
+            launch_fallback(c, g, s);
+        }
         IM_LAUNCH(c, K_FINALIZE, k_finalize, grid_for(expect, T, 152u * 8u), T, 0, st, c->d_batch,
                   (const unsigned long long*)c->d_fresh, c->d_key, c->d_stamp, c->key_bits, round);
         IM_LAUNCH(c, K_REDUCE, k_reduce, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n, round, st);
@@ -608,8 +749,8 @@ int im_select_round(im_ctx* c) {
     const uint64_t gain = best >> c->key_bits;
     if (sd >= n) return im_fail(c, IM_EDEVICE, "selected id out of range");
     IM_LAUNCH(c, K_REDUCE_RESET, k_phase_reset, 1, 32, 0, st);
-    IM_LAUNCH(c, K_MARK_SEED, k_mark_seed, (nchunk + kEvalWarps - 1) / kEvalWarps, kEvalWarps * 32, 0,
-              g, s, st, sd, c->d_fb_tasks, c->fb_cap, nchunk, c->d_seedflag, c->d_key);
+    IM_LAUNCH(c, K_MARK_SEED, k_mark_seed, (c->R + kEvalWarps - 1) / kEvalWarps, kEvalWarps * 32, 0,
+              g, s, st, sd, c->d_fb_tasks, c->fb_cap, c->d_seedflag, c->d_key, c->d_seed_list, round);
     launch_fallback(c, g, s);
     IM_CUDA(c, cudaGetLastError());
     c->seeds.push_back(sd);

@@ -64,24 +64,183 @@ k_sample_union(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, ui
     }
 }
 
-// grid.y = sketch within the batch; full compression + component-size histogram.
+// Sampling alone: every live (edge, sketch) pair of the batch becomes a record (u, v, b, 0),
+// appended with one atomic per warp.  The hash work (nb mixes per edge) is pure ALU; the
+// latency-bound unions then run one thread per record in k_union_live.
+template <int B>
 __global__ void __launch_bounds__(256)
-k_compress_count(uint32_t* __restrict__ parent, uint32_t* __restrict__ cnt, uint32_t n) {
-    uint32_t* P = parent + (size_t)blockIdx.y * n;
-    uint32_t* C = cnt ? cnt + (size_t)blockIdx.y * n : nullptr;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += stride) {
-        uint32_t v = base + threadIdx.x;
-        bool act = v < n;
-        uint32_t root = 0;
-        if (act) root = compress_to_root(P, v);
-        if (C) {
-            unsigned am = __ballot_sync(0xffffffffu, act);
-            if (act) {
-                unsigned grp = __match_any_sync(am, root);
-                if ((threadIdx.x & 31) == (unsigned)(__ffs(grp) - 1)) atomicAdd(C + root, __popc(grp));
+k_sample_emit(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, uint32_t r0,
+              uint32_t nb, uint4* __restrict__ out, unsigned long long* __restrict__ out_n,
+              uint64_t cap) {
+    const uint64_t npairs = (m + 1) >> 1;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t g0 = (uint64_t)(r0 + 1u) * kGamma;
+    const unsigned lane = threadIdx.x & 31;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < npairs; base += stride) {
+        const uint64_t i = base + threadIdx.x;
+        uint32_t live0 = 0, live1 = 0;
+        uint4 two = make_uint4(0, 0, 0, 0);
+        if (i < npairs) {
+            two = edge_pairs[i];
+            const uint64_t e0 = 2 * i, e1 = 2 * i + 1;
+            uint64_t x0 = mix64(smp.salt ^ e0) + g0;
+            uint64_t x1 = mix64(smp.salt ^ e1) + g0;
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                if (b < (int)nb) {
+                    if (smp.all_live || mix64(x0) < smp.T) live0 |= 1u << b;
+                    if (smp.all_live || mix64(x1) < smp.T) live1 |= 1u << b;
+                }
+                x0 += kGamma;
+                x1 += kGamma;
+            }
+            if (e1 >= m) live1 = 0;
+        }
+        const uint32_t cntl = __popc(live0) + __popc(live1);
+        uint32_t incl = cntl;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+            if ((int)lane >= d) incl += y;
+        }
+        const uint32_t wtotal = __shfl_sync(0xffffffffu, incl, 31);
+        if (wtotal == 0) continue;
+        unsigned long long wbase = 0;
+        if (lane == 31) wbase = atomicAdd(out_n, (unsigned long long)wtotal);
+        wbase = __shfl_sync(0xffffffffu, wbase, 31);
+        uint64_t pos = wbase + incl - cntl;
+        while (live0) {
+            const uint32_t b = __ffs(live0) - 1;
+            live0 &= live0 - 1;
+            if (pos < cap) out[pos] = make_uint4(two.x, two.y, b, 0u);
+            ++pos;
+        }
+        while (live1) {
+            const uint32_t b = __ffs(live1) - 1;
+            live1 &= live1 - 1;
+            if (pos < cap) out[pos] = make_uint4(two.z, two.w, b, 0u);
+            ++pos;
+        }
+    }
+}
+
+// One thread per live record; if the record buffer overflowed, redo the batch with the fused
+// sample+union loop instead (decided on the device, so no host round trip).
+template <int B, bool kAll>
+__global__ void __launch_bounds__(256)
+k_union_live(const uint4* __restrict__ recs, const unsigned long long* __restrict__ rec_n, uint64_t cap,
+             uint32_t* __restrict__ parent, uint32_t n, const uint32_t* __restrict__ cbits,
+             const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, uint32_t r0, uint32_t nb) {
+    const unsigned long long cnt = *rec_n;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    if (cnt > cap) {
+        const uint64_t npairs = (m + 1) >> 1;
+        const uint64_t g0 = (uint64_t)(r0 + 1u) * kGamma;
+        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npairs; i += stride) {
+            const uint4 two = edge_pairs[i];
+            uint64_t x0 = mix64(smp.salt ^ (2 * i)) + g0;
+            uint64_t x1 = mix64(smp.salt ^ (2 * i + 1)) + g0;
+            const bool has1 = 2 * i + 1 < m;
+            for (uint32_t b = 0; b < nb; ++b) {
+                if (smp.all_live || mix64(x0) < smp.T) unite<kAll>(parent + (size_t)b * n, cbits, two.x, two.y);
+                if (has1 && (smp.all_live || mix64(x1) < smp.T))
+                    unite<kAll>(parent + (size_t)b * n, cbits, two.z, two.w);
+                x0 += kGamma;
+                x1 += kGamma;
             }
         }
+        return;
+    }
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < cnt; j += stride) {
+        const uint4 rc = recs[j];
+        unite<kAll>(parent + (size_t)rc.z * n, cbits, rc.x, rc.y);
+    }
+}
+
+__global__ void k_zero_u64(unsigned long long* p) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *p = 0;
+}
+
+// grid.y = sketch within the batch; full compression + component-size histogram.
+// Each block owns tiles of kCountTile vertices.  Roots are first merged inside a warp
+// (match_any) and then in a shared-memory hash table, so a giant component costs one global
+// atomic per tile instead of one per warp.
+constexpr int kCountTile = 2048;
+constexpr int kCountSlots = 4096;   // power of two, > 2 x tile
+
+__global__ void __launch_bounds__(256)
+k_compress_count(uint32_t* __restrict__ parent, uint32_t* __restrict__ cnt, uint32_t n) {
+    __shared__ uint32_t tkey[kCountSlots];
+    __shared__ uint32_t tval[kCountSlots];
+    uint32_t* P = parent + (size_t)blockIdx.y * n;
+    uint32_t* C = cnt ? cnt + (size_t)blockIdx.y * n : nullptr;
+    const unsigned lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < kCountSlots; i += blockDim.x) { tkey[i] = kNone; tval[i] = 0; }
+    __syncthreads();
+    for (uint32_t t0 = blockIdx.x * kCountTile; t0 < n; t0 += gridDim.x * kCountTile) {
+        for (uint32_t off = 0; off < (uint32_t)kCountTile; off += blockDim.x) {
+            const uint32_t v = t0 + off + threadIdx.x;
+            const bool act = v < n;
+            uint32_t root = 0;
+            if (act) root = compress_to_root(P, v);
+            if (C) {
+                const unsigned am = __ballot_sync(0xffffffffu, act);
+                if (act) {
+                    const unsigned grp = __match_any_sync(am, root);
+                    if (lane == (unsigned)(__ffs(grp) - 1)) {
+                        uint32_t h = (root * 0x9E3779B1u) >> (32 - 12);
+                        for (;;) {
+                            const uint32_t old = atomicCAS(&tkey[h], kNone, root);
+                            if (old == kNone || old == root) {
+                                atomicAdd(&tval[h], (uint32_t)__popc(grp));
+                                break;
+                            }
+                            h = (h + 1) & (kCountSlots - 1);
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (C) {
+            for (int i = threadIdx.x; i < kCountSlots; i += blockDim.x) {
+                if (tkey[i] != kNone) {
+                    atomicAdd(C + tkey[i], tval[i]);
+                    tkey[i] = kNone;
+                    tval[i] = 0;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Refresh evaluation: mark the components that hold a seed (bit 31 of their count).
+__global__ void k_cover_roots(const uint32_t* __restrict__ parent, uint32_t* __restrict__ cnt,
+                              uint32_t n, uint32_t nb, const uint32_t* __restrict__ seeds,
+                              uint32_t nseeds) {
+    const uint32_t total = nb * nseeds;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const uint32_t b = i / nseeds, sd = seeds[i % nseeds];
+        const uint32_t root = parent[(size_t)b * n + sd];
+        atomicOr(cnt + (size_t)b * n + root, kCovered);
+    }
+}
+
+// Refresh evaluation: fresh[j] += sum_b size of batch member j's component unless covered.
+__global__ void k_refresh_gather(const uint32_t* __restrict__ parent, const uint32_t* __restrict__ cnt,
+                                 uint32_t n, uint32_t nb, const uint32_t* __restrict__ batch,
+                                 const unsigned int* __restrict__ batch_n,
+                                 unsigned long long* __restrict__ fresh) {
+    const uint32_t bn = *batch_n;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < bn; j += gridDim.x * blockDim.x) {
+        const uint32_t x = batch[j];
+        unsigned long long d = 0;
+        for (uint32_t b = 0; b < nb; ++b) {
+            const uint32_t c = cnt[(size_t)b * n + parent[(size_t)b * n + x]];
+            d += (c & kCovered) ? 0u : c;
+        }
+        fresh[j] += d;
     }
 }
 
@@ -180,6 +339,34 @@ __global__ void k_labels_out(const uint32_t* __restrict__ P, uint32_t n, uint32_
         out[v] = P[v];
 }
 
+// Sampling and unions of one batch as two kernels (records of live pairs in between).
+template <bool kAll>
+int launch_sample_split(im_ctx* c, uint32_t r0, uint32_t nb) {
+    const unsigned T = 256;
+    const uint64_t npairs = (c->m + 1) >> 1;
+    const uint4* ep = reinterpret_cast<const uint4*>(c->d_edges);
+    const unsigned gs = grid_for(npairs, T, 152u * 16u);
+    const double pl = c->smp.all_live ? 1.0 : c->p;
+    const unsigned gu = grid_for((uint64_t)(pl * (double)c->m * nb) + 1, T, 152u * 16u);
+    IM_LAUNCH(c, K_SAMPLE_EMIT, k_zero_u64, 1, 32, 0, c->d_live_n);
+#define IM_SE(BB)                                                                                 \
+    do {                                                                                          \
+        IM_LAUNCH(c, K_SAMPLE_EMIT, k_sample_emit<BB>, gs, T, 0, ep, c->m, c->smp, r0, nb, c->d_live, \
+                  c->d_live_n, c->live_cap);                                                      \
+        IM_LAUNCH(c, K_UNION, (k_union_live<BB, kAll>), gu, T, 0, c->d_live, c->d_live_n, c->live_cap, \
+                  c->d_parent, c->n, c->d_cbits, ep, c->m, c->smp, r0, nb);                       \
+    } while (0)
+    const uint32_t cap = c->batch_used;
+    if (cap <= 1) IM_SE(1);
+    else if (cap <= 2) IM_SE(2);
+    else if (cap <= 4) IM_SE(4);
+    else if (cap <= 8) IM_SE(8);
+    else if (cap <= 16) IM_SE(16);
+    else IM_SE(32);
+#undef IM_SE
+    return IM_OK;
+}
+
 template <bool kAll>
 int launch_sample_union(im_ctx* c, uint32_t r0, uint32_t nb) {
     const unsigned T = 256;
@@ -247,11 +434,16 @@ int im_sketch_batches(im_ctx* c) {
         IM_LAUNCH(c, K_BATCH_INIT, k_batch_init, grid_for((uint64_t)n * nb, T, 152u * 16u), T, 0,
                   c->d_parent, c->d_cnt, n, nb);
         if (any_live && c->m > 0) {
-            int rc = c->all_centers ? launch_sample_union<true>(c, r0, nb)
+            int rc;
+            if (c->d_live)
+                rc = c->all_centers ? launch_sample_split<true>(c, r0, nb)
+                                    : launch_sample_split<false>(c, r0, nb);
+            else
+                rc = c->all_centers ? launch_sample_union<true>(c, r0, nb)
                                     : launch_sample_union<false>(c, r0, nb);
             if (rc) return rc;
         }
-        dim3 g(grid_for(n, T, 152u * 8u), nb);
+        dim3 g(grid_for(n, kCountTile, 152u * 8u), nb);
         IM_LAUNCH(c, K_COMPRESS_COUNT, k_compress_count, g, T, 0, c->d_parent, c->d_cnt, n);
         if (c->all_centers)
             IM_LAUNCH(c, K_GAIN_COMPACT, k_gain_compact<true>, grid_for(n, T, 152u * 16u), T, 0,
@@ -279,9 +471,39 @@ int im_labels_min(im_ctx* c, uint32_t r, uint32_t* d_out) {
         c->batch_used = saved;
         if (rc) return rc;
     }
-    dim3 g(grid_for(n, T, 152u * 8u), 1);
+    dim3 g(grid_for(n, kCountTile, 152u * 8u), 1);
     IM_LAUNCH(c, K_LABELS_MIN, k_compress_count, g, T, 0, c->d_parent, (uint32_t*)nullptr, n);
     IM_LAUNCH(c, K_LABELS_OUT, k_labels_out, grid_for(n, T, 152u * 8u), T, 0, c->d_parent, n, d_out);
+    IM_CUDA(c, cudaGetLastError());
+    return IM_OK;
+}
+
+// Batched re-evaluation by recomputation: for every batch member x, Marginal(S, x) =
+// sum_r [C_r(x) holds no seed] |C_r(x)|, obtained by recomputing each sketch's components
+// (Sketch(r) of Alg. 3) instead of one search per (x, r).  Same values as GetCenter; cheaper
+// when the batch is a large part of V.  The batch list and its size live on the device.
+int im_refresh_eval(im_ctx* c, const uint32_t* d_batch, const unsigned int* d_batch_n,
+                    unsigned long long* d_fresh, const uint32_t* d_seeds, uint32_t nseeds,
+                    uint64_t batch_hint) {
+    const uint32_t n = c->n, R = c->R;
+    const unsigned T = 256;
+    const bool any_live = c->smp.all_live || c->smp.T != 0;
+    for (uint32_t r0 = 0; r0 < R; r0 += c->batch_used) {
+        const uint32_t nb = R - r0 < c->batch_used ? R - r0 : c->batch_used;
+        IM_LAUNCH(c, K_BATCH_INIT, k_batch_init, grid_for((uint64_t)n * nb, T, 152u * 16u), T, 0,
+                  c->d_parent, c->d_cnt, n, nb);
+        if (any_live && c->m > 0) {
+            int rc = c->d_live ? launch_sample_split<true>(c, r0, nb) : launch_sample_union<true>(c, r0, nb);
+            if (rc) return rc;
+        }
+        dim3 g(grid_for(n, kCountTile, 152u * 8u), nb);
+        IM_LAUNCH(c, K_COMPRESS_COUNT, k_compress_count, g, T, 0, c->d_parent, c->d_cnt, n);
+        if (nseeds)
+            IM_LAUNCH(c, K_COVER_ROOTS, k_cover_roots, grid_for((uint64_t)nb * nseeds, T), T, 0, c->d_parent,
+                      c->d_cnt, n, nb, d_seeds, nseeds);
+        IM_LAUNCH(c, K_REFRESH_GATHER, k_refresh_gather, grid_for(batch_hint, T, 152u * 16u), T, 0,
+                  c->d_parent, c->d_cnt, n, nb, d_batch, d_batch_n, d_fresh);
+    }
     IM_CUDA(c, cudaGetLastError());
     return IM_OK;
 }

@@ -228,3 +228,23 @@ def test_lazy_evaluation_counts_are_bounded():
         ev = ctx.round_evals()
     assert ev[0] == 0
     assert np.all(ev <= 4 * ev_celf + 2)
+
+
+@pytest.mark.parametrize("threshold", [1, 2**64 - 1])
+@pytest.mark.parametrize("alpha", [1.0, 0.1])
+def test_both_batch_evaluators_give_identical_seeds(threshold, alpha):
+    # threshold 1: every re-evaluation batch recomputes the sketches; 2^64-1: every batch
+    # runs one GetCenter search per (candidate, sketch).  Both must equal plain greedy.
+    n, u, v = graphgen.chung_lu(20000, 120000, 2.1, 2000.0, 5)
+    seed, p, R, k = 42, 0.05, 64, 25
+    with im.IMContext(n, u, v) as ctx:
+        im.im_set_refresh_threshold(ctx.h, threshold)
+        ctx.build_sketches(R, seed, p, alpha)
+        seeds, gains = ctx.select_seeds(k)
+        st = ctx.stats()
+    o = _oracle(n, u, v, seed, p, R, alpha, k)
+    assert np.array_equal(seeds, o["seeds"]) and np.array_equal(gains, o["seed_gains"])
+    if threshold == 1:
+        assert st["refresh_batches"] > 0
+    else:
+        assert st["refresh_batches"] == 0
