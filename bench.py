@@ -191,6 +191,8 @@ def run_ours(args, n, u, v, prm):
     du = torch.from_numpy(u.view(np.int32)).cuda()
     dv = torch.from_numpy(v.view(np.int32)).cuda()
     ctx = im.IMContext(n, du, dv, stream=stream.cuda_stream)
+    if args.sketch_batch:
+        im.im_set_sketch_batch(ctx.h, args.sketch_batch)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
 
     def step():
@@ -333,6 +335,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(graphgen.WORKLOADS))
+    ap.add_argument("--sketch-batch", type=int, default=0, help="sketches per edge pass (0 = auto)")
     args = ap.parse_args()
     n, u, v, prm = graphgen.workload(args.workload)
     prm["name"] = args.workload

@@ -18,7 +18,8 @@ const char* const kNames[K_COUNT] = {
     "batch_init", "sample_union", "compress_count", "gain_compact", "init_keys",
     "reduce_reset", "reduce", "sel_init", "sel_hist", "sel_pick", "gather", "eval",
     "fallback", "finalize", "mark_seed", "spread_tasks", "spread_dedup", "labels_min",
-    "labels_out", "arc_keys", "sample_emit", "union", "cover_roots", "refresh_gather"};
+    "labels_out", "arc_keys", "sample_emit", "union", "cover_roots", "refresh_gather",
+    "count_above"};
 
 int bitlen64(uint64_t x) {
     int b = 0;
@@ -49,7 +50,7 @@ void free_sketch_state(im_ctx* c) {
     dfree(c->d_label); dfree(c->d_size); dfree(c->d_gain0);
     dfree(c->d_key); dfree(c->d_stamp); dfree(c->d_seedflag);
     dfree(c->d_batch); dfree(c->d_fresh); dfree(c->d_seed_list);
-    dfree(c->d_parent); dfree(c->d_cnt); dfree(c->d_live); dfree(c->d_live_n);
+    dfree(c->d_parent); dfree(c->d_word); dfree(c->d_live); dfree(c->d_live_n);
     c->live_cap = 0;
     dfree(c->d_fb_queue); dfree(c->d_fb_bits); dfree(c->d_fb_tasks);
     c->batch_alloc = 0;
@@ -231,12 +232,13 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
     if (p >= 1.0) smp.all_live = 1;
     else if (p > 0.0) smp.T = (uint64_t)std::ldexp(p, 64);
 
+    // sketches per edge pass: union-find launches are bound by their critical path, not by
+    // their size, so fewer, larger batches win; memory is 12 bytes per vertex per sketch
     uint32_t B = c->batch_req;
     if (B == 0) {
-        uint64_t per = (uint64_t)n * 8;
-        uint64_t fit = per ? (64ull << 20) / per : 32;
-        B = 8;
-        while (B < 32 && (uint64_t)B * 2 <= fit) B *= 2;
+        const uint64_t per = (uint64_t)n * 12;
+        B = 32;
+        while (B > 1 && (uint64_t)B * per > (8ull << 30)) B /= 2;
     }
     uint32_t rp2 = 1;
     while (rp2 < R) rp2 <<= 1;
@@ -252,13 +254,13 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
               dalloc(c->d_seedflag, n) && dalloc(c->d_batch, n) && dalloc(c->d_fresh, n) &&
               dalloc(c->d_seed_list, n) &&
               dalloc(c->d_label, nc) && dalloc(c->d_size, nc) &&
-              dalloc(c->d_parent, (size_t)B * n) && dalloc(c->d_cnt, (size_t)B * n);
+              dalloc(c->d_parent, (size_t)B * n) && dalloc(c->d_word, (size_t)B * n);
     if (ok && c->m > 0 && (smp.all_live || smp.T != 0)) {
         // live-pair records of one batch: expected p m B, with a generous margin; a batch that
         // still overflows falls back to the fused sample+union loop on the device
         const double ex = (smp.all_live ? 1.0 : p) * (double)c->m * B;
         double cap = 1.3 * ex + 16.0 * std::sqrt(ex) + 65536.0;
-        if (cap > (double)(1ull << 26)) cap = (double)(1ull << 26);
+        if (cap > (double)(1ull << 28)) cap = (double)(1ull << 28);
         c->live_cap = (uint64_t)cap;
         ok = dalloc(c->d_live, c->live_cap) && dalloc(c->d_live_n, 1);
     }

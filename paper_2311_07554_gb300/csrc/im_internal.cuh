@@ -73,6 +73,8 @@ struct SelState {
     unsigned long long best;        // max fresh key this round
     unsigned long long stale_max;   // max stale key over unevaluated candidates
     unsigned long long n_unev;      // number of unevaluated candidates
+    unsigned long long count_above; // unevaluated candidates whose stale key beats best
+    unsigned long long best_prev;   // best fresh key when the current batch was chosen
     unsigned long long prefix, prefmask, need, taken, theta, borig;
     int shift, done;
     unsigned int hist[256];
@@ -101,7 +103,8 @@ enum KernelId {
     K_BATCH_INIT, K_SAMPLE_UNION, K_COMPRESS_COUNT, K_GAIN_COMPACT, K_INIT_KEYS,
     K_REDUCE_RESET, K_REDUCE, K_SEL_INIT, K_SEL_HIST, K_SEL_PICK, K_GATHER, K_EVAL,
     K_FALLBACK, K_FINALIZE, K_MARK_SEED, K_SPREAD_TASKS, K_SPREAD_DEDUP, K_LABELS_MIN,
-    K_LABELS_OUT, K_ARC_KEYS, K_SAMPLE_EMIT, K_UNION, K_COVER_ROOTS, K_REFRESH_GATHER, K_COUNT
+    K_LABELS_OUT, K_ARC_KEYS, K_SAMPLE_EMIT, K_UNION, K_COVER_ROOTS, K_REFRESH_GATHER, K_COUNT_ABOVE,
+    K_COUNT
 };
 
 const char* kernel_name(int id);
@@ -160,7 +163,7 @@ struct im_ctx {
     // sketch-batch scratch
     uint32_t batch_req = 0, batch_used = 0, batch_alloc = 0;
     uint32_t* d_parent = nullptr;
-    uint32_t* d_cnt = nullptr;
+    uint64_t* d_word = nullptr;              // per root: size (low half), min label key (high)
     uint4* d_live = nullptr;                 // live (u, v, sketch) records of one batch
     unsigned long long* d_live_n = nullptr;
     uint64_t live_cap = 0;

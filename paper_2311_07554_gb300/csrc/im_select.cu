@@ -16,6 +16,8 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kEvalWarps = 4;   // warps per block of the search kernels
+// batches with at most this many (member, sketch) searches use one warp per search
+constexpr uint64_t kSingleTasks = 152ull * 64;
 
 __device__ __forceinline__ uint64_t pack_key(uint64_t gain, uint32_t v, uint32_t bits) {
     const uint64_t mask = (1ull << bits) - 1ull;
@@ -225,7 +227,7 @@ __global__ void k_init_keys(const uint64_t* __restrict__ gain0, uint32_t n, uint
 }
 
 __global__ void k_reduce_reset(SelState* st) {
-    if (threadIdx.x == 0) { st->best = 0; st->stale_max = 0; st->n_unev = 0; }
+    if (threadIdx.x == 0) { st->best = 0; st->stale_max = 0; st->n_unev = 0; st->count_above = 0; }
 }
 
 // best = max fresh key (evaluated this round), stale_max / n_unev over the others.
@@ -259,6 +261,27 @@ k_reduce(const uint64_t* __restrict__ key, const uint32_t* __restrict__ stamp,
     }
 }
 
+// Unevaluated candidates whose stale key beats the best fresh key of the round: an upper
+// bound on what is left to evaluate in this round (the winner's fresh key is >= best).
+__global__ void __launch_bounds__(256)
+k_count_above(const uint64_t* __restrict__ key, const uint32_t* __restrict__ stamp,
+              const uint8_t* __restrict__ seedflag, uint32_t n, uint32_t round, SelState* st) {
+    const unsigned long long best = st->best;
+    unsigned long long cnt = 0;
+    if (best)
+        for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+            if (!seedflag[v] && stamp[v] != round && key[v] > best) ++cnt;
+#pragma unroll
+    for (int d = 16; d; d >>= 1) cnt += __shfl_xor_sync(kFull, cnt, d);
+    __shared__ unsigned long long s_cnt[8];
+    if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) cnt += s_cnt[i];
+        if (cnt) atomicAdd(&st->count_above, cnt);
+    }
+}
+
 // Start of a batch: decide how to pick ~B of the largest stale keys (radix select on the
 // key bytes below the top byte of stale_max); take all when at most 2B remain.
 __global__ void k_sel_init(SelState* st, unsigned long long B) {
@@ -289,9 +312,11 @@ __global__ void k_sel_init(SelState* st, unsigned long long B) {
         st->batch_n = 0;
         st->eval_next = 0;
         st->fb_n = 0;
+        st->best_prev = st->best;
         st->best = 0;
         st->stale_max = 0;
         st->n_unev = 0;
+        st->count_above = 0;
     }
     for (int i = threadIdx.x; i < 256; i += blockDim.x) st->hist[i] = 0;
 }
@@ -366,7 +391,9 @@ __global__ void __launch_bounds__(256)
 k_gather(const uint64_t* __restrict__ key, const uint32_t* __restrict__ stamp,
          const uint8_t* __restrict__ seedflag, uint32_t n, uint32_t round, SelState* st,
          uint32_t* __restrict__ batch, unsigned long long* __restrict__ fresh) {
-    const unsigned long long theta = st->theta;
+    // a candidate whose stale key is below the best fresh key cannot win (keys are distinct)
+    const unsigned long long bp = st->best_prev;
+    const unsigned long long theta = max(st->theta, bp ? bp + 1 : 0ull);
     const unsigned lane = threadIdx.x & 31;
     for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
         const uint32_t v = base + threadIdx.x;
@@ -430,6 +457,41 @@ k_eval(GraphView g, SketchView s, SelState* st, const uint32_t* __restrict__ bat
     }
 }
 
+// Marginal for small batches: one warp per (member j, sketch r), so a round that
+// re-evaluates a handful of vertices finishes in the latency of one search.
+__global__ void __launch_bounds__(kEvalWarps * 32)
+k_eval_single(GraphView g, SketchView s, SelState* st, const uint32_t* __restrict__ batch,
+              unsigned long long* __restrict__ fresh, FbTask* __restrict__ fbt, uint32_t fb_cap) {
+    __shared__ uint32_t qws[kEvalWarps][kQcap];
+    uint32_t* qw = qws[threadIdx.x >> 5];
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned long long total = (unsigned long long)st->batch_n * s.R;
+    const unsigned long long wstride = (unsigned long long)gridDim.x * kEvalWarps;
+    for (unsigned long long t = (unsigned long long)blockIdx.x * kEvalWarps + (threadIdx.x >> 5); t < total;
+         t += wstride) {
+        const uint32_t j = (uint32_t)(t / s.R), r = (uint32_t)(t % s.R);
+        const uint32_t x = batch[j];
+        unsigned long long d = 0;
+        if (is_center(s, x)) {
+            const uint32_t l = s.label[(size_t)center_index(s, x) * s.R + r];
+            const uint32_t sz = s.size[(size_t)l * s.R + r];
+            d = (sz & kCovered) ? 0u : sz;
+        } else {
+            const BfsOut o = warp_bfs_from(g, s, x, r, qw, true, nullptr, 0, 0, st);
+            if (o.overflow) {
+                if (lane == 0) push_fallback(st, fbt, fb_cap, x, r, FB_EVAL, j);
+            } else if (o.label != kNone) {
+                const uint32_t sz = s.size[(size_t)o.label * s.R + r];
+                d = (sz & kCovered) ? 0u : sz;
+            } else {
+                d = o.seen ? 0u : o.count;
+            }
+        }
+        if (lane == 0 && d) atomicAdd(fresh + j, d);
+        __syncwarp();
+    }
+}
+
 __global__ void __launch_bounds__(256)
 k_finalize(SelState* st, const uint32_t* __restrict__ batch,
            const unsigned long long* __restrict__ fresh, uint64_t* __restrict__ key,
@@ -443,6 +505,7 @@ k_finalize(SelState* st, const uint32_t* __restrict__ batch,
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->evals_total += bn;
         st->fb_total += min(st->fb_n, 0xFFFFFFFFu);
+        st->fb_n = 0;   // the fallback kernel has run; MarkSeed may queue its own searches
     }
 }
 
@@ -474,6 +537,11 @@ k_mark_seed(GraphView g, SketchView s, SelState* st, uint32_t sd, FbTask* __rest
         seedflag[sd] = 1;
         key[sd] = 0;
         seed_list[round] = sd;
+        // the next round's first reduction starts from zero
+        st->best = 0;
+        st->stale_max = 0;
+        st->n_unev = 0;
+        st->count_above = 0;
     }
 }
 
@@ -695,10 +763,21 @@ int im_select_round(im_ctx* c) {
     const uint32_t nchunk = (c->R + 31) / 32;
     SelState* st = c->d_sel;
 
-    IM_LAUNCH(c, K_REDUCE_RESET, k_reduce_reset, 1, 32, 0, st);
+    // Round start: recount over the new round's stamps.  After round 0 no key is fresh and at
+    // least one candidate is left, so the first batch (B = 1: the top stale key, chosen on the
+    // device) is queued without waiting for the host to see the counts.
+    if (round == 0) IM_LAUNCH(c, K_REDUCE_RESET, k_reduce_reset, 1, 32, 0, st);
     IM_LAUNCH(c, K_REDUCE, k_reduce, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n, round, st);
-    int rc = sync_state(c);
-    if (rc) return rc;
+    int rc = IM_OK;
+    if (round == 0) {
+        rc = sync_state(c);
+        if (rc) return rc;
+    } else {
+        c->h_sel->n_unev = n - round;   // what the host may assume before the first sync
+        c->h_sel->best = 0;
+        c->h_sel->stale_max = ~0ull;
+        c->h_sel->count_above = 0;
+    }
     uint64_t evals = 0;
     for (int j = 0;; ++j) {
         const SelState& h = *c->h_sel;
@@ -706,12 +785,13 @@ int im_select_round(im_ctx* c) {
         unsigned long long B = 1ull << (j < 40 ? j : 40);
         if (B > h.n_unev) B = h.n_unev;
         uint64_t expect = (2 * B < h.n_unev ? 2 * B : h.n_unev);
-        // a batch this large is evaluated by recomputing the sketches, for all remaining
-        // candidates at once (the round then ends with every key fresh)
-        const bool refresh = expect >= c->refresh_min;
+        // When many candidates could still beat the best fresh key (or the doubling batch has
+        // grown large), evaluate every one of them at once by recomputing the sketches; the
+        // round then ends, since all remaining stale keys are below the new best.
+        const bool refresh = expect >= c->refresh_min || (h.best && h.count_above >= c->refresh_min);
         if (refresh) {
             B = h.n_unev;
-            expect = h.n_unev;
+            expect = h.best ? h.count_above : h.n_unev;
         }
         IM_LAUNCH(c, K_SEL_INIT, k_sel_init, 1, 256, 0, st, B);
         if (h.n_unev > 2 * B && B > 1) {
@@ -728,8 +808,12 @@ int im_select_round(im_ctx* c) {
             if (rc) return rc;
             c->refresh_batches++;
         } else {
-            IM_LAUNCH(c, K_EVAL, k_eval, search_grid(expect * nchunk), kEvalWarps * 32, 0, g, s, st,
-                      c->d_batch, (unsigned long long*)c->d_fresh, c->d_fb_tasks, c->fb_cap, nchunk);
+            if (expect * c->R <= kSingleTasks)
+                IM_LAUNCH(c, K_EVAL, k_eval_single, search_grid(expect * c->R), kEvalWarps * 32, 0, g, s, st,
+                          c->d_batch, (unsigned long long*)c->d_fresh, c->d_fb_tasks, c->fb_cap);
+            else
+                IM_LAUNCH(c, K_EVAL, k_eval, search_grid(expect * nchunk), kEvalWarps * 32, 0, g, s, st,
+                          c->d_batch, (unsigned long long*)c->d_fresh, c->d_fb_tasks, c->fb_cap, nchunk);
             launch_fallback(c, g, s);
         }
         IM_LAUNCH(c, K_FINALIZE, k_finalize, grid_for(expect, T, 152u * 8u), T, 0, st, c->d_batch,
@@ -741,6 +825,13 @@ int im_select_round(im_ctx* c) {
             return im_fail(c, IM_EDEVICE, "re-evaluation batch made no progress");
         evals += c->h_sel->batch_n;
         c->batches++;
+        if (c->h_sel->n_unev > 0 && c->h_sel->best <= c->h_sel->stale_max) {
+            // the round goes on: how many candidates could still beat the best fresh key?
+            IM_LAUNCH(c, K_COUNT_ABOVE, k_count_above, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag,
+                      n, round, st);
+            rc = sync_state(c);
+            if (rc) return rc;
+        }
     }
     const unsigned long long best = c->h_sel->best;
     if (best == 0) return im_fail(c, IM_EDEVICE, "no candidate left for the next seed");
@@ -748,7 +839,6 @@ int im_select_round(im_ctx* c) {
     const uint32_t sd = (uint32_t)(mask - (best & mask));
     const uint64_t gain = best >> c->key_bits;
     if (sd >= n) return im_fail(c, IM_EDEVICE, "selected id out of range");
-    IM_LAUNCH(c, K_REDUCE_RESET, k_phase_reset, 1, 32, 0, st);
     IM_LAUNCH(c, K_MARK_SEED, k_mark_seed, (c->R + kEvalWarps - 1) / kEvalWarps, kEvalWarps * 32, 0,
               g, s, st, sd, c->d_fb_tasks, c->fb_cap, c->d_seedflag, c->d_key, c->d_seed_list, round);
     launch_fallback(c, g, s);

@@ -1,13 +1,17 @@
 // im_sketch.cu -- Step 1 of Alg. 1: sketch construction (Sec. 3, Alg. 3 Sketch(r)).
 //
-// Per batch of B sketches sharing one pass over the edge list:
-//   init        parent[b][v] = v, cnt[b][v] = 0
-//   sample+UF   for every edge e and sketch r of the batch: if h(e, r) < T, union(u, v)
-//               (hooking with atomicCAS; the root of every component is its earliest vertex
-//               in "center-first" order: the smallest-id center if the component has one,
-//               else its smallest id)
-//   compress    parent[b][v] <- root, cnt[b][root] += 1 (warp-aggregated)
-//   gain        Delta[v] += sum_b cnt[b][root_b(v)]; for centers: label, size (Alg. 3)
+// Batches of B sketches share one pass over the edge list.  Per sketch b of a batch:
+//   init        P[b][v] = v;  W[b][v] = (key = ~0, count = 0)
+//   sample      every live (edge, sketch) pair of the batch becomes a record (u, v, b)
+//   union       one thread per record, randomized linking (expected log-depth trees)
+//   compress    P[b][v] <- root; per root: count += 1 and key = min over members of the
+//               label key of its centers (center index) -- with every vertex a center this
+//               is the smallest id (Alg. 3's canonical label)
+//   gain        Delta[v] += sum_b count(root_b(v)); for a center c_i: label[i] = key of its
+//               root (the smallest center index in its component), size[i] = count if
+//               label[i] = i, else 0 (Alg. 3)
+// W[b][x] is one 64-bit word per root: low half = component size (bit 31 is the "holds a
+// seed" flag of the recomputation evaluator), high half = the component's minimum key.
 #include "im_internal.cuh"
 #include "im_uf.cuh"
 
@@ -15,53 +19,46 @@ using namespace imk;
 
 namespace {
 
-__global__ void k_batch_init(uint32_t* __restrict__ parent, uint32_t* __restrict__ cnt,
+constexpr uint64_t kWordInit = 0xFFFFFFFF00000000ull;
+
+__device__ __forceinline__ uint32_t* w_count(uint64_t* w) { return reinterpret_cast<uint32_t*>(w); }
+__device__ __forceinline__ uint32_t* w_key(uint64_t* w) { return reinterpret_cast<uint32_t*>(w) + 1; }
+
+__global__ void k_batch_init(uint32_t* __restrict__ parent, uint64_t* __restrict__ word,
                              uint32_t n, uint32_t nb) {
-    uint64_t total = (uint64_t)n * nb;
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t total = (uint64_t)n * nb;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
         parent[i] = (uint32_t)(i % n);
-        if (cnt) cnt[i] = 0;
+        word[i] = kWordInit;
     }
 }
 
-// Each thread takes two edges (one 16-byte load) and all nb <= B sketches of the batch.
-template <int B, bool kAll>
+// Fused sampling + union (used when the record buffer is absent or overflows).
+template <int B>
+__device__ __forceinline__ void sample_union_pair(const uint4& two, uint64_t i, uint64_t m,
+                                                  const Sampler& smp, uint64_t g0, uint32_t nb,
+                                                  uint32_t* parent, uint32_t n) {
+    uint64_t x0 = mix64(smp.salt ^ (2 * i)) + g0;
+    uint64_t x1 = mix64(smp.salt ^ (2 * i + 1)) + g0;
+    const bool has1 = 2 * i + 1 < m;
+    for (uint32_t b = 0; b < nb; ++b) {
+        if (smp.all_live || mix64(x0) < smp.T) unite_rand(parent + (size_t)b * n, two.x, two.y);
+        if (has1 && (smp.all_live || mix64(x1) < smp.T)) unite_rand(parent + (size_t)b * n, two.z, two.w);
+        x0 += kGamma;
+        x1 += kGamma;
+    }
+}
+
+template <int B>
 __global__ void __launch_bounds__(256)
 k_sample_union(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, uint32_t r0,
-               uint32_t nb, uint32_t* __restrict__ parent, uint32_t n,
-               const uint32_t* __restrict__ cbits) {
+               uint32_t nb, uint32_t* __restrict__ parent, uint32_t n) {
     const uint64_t npairs = (m + 1) >> 1;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t g0 = (uint64_t)(r0 + 1u) * kGamma;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npairs; i += stride) {
-        const uint4 two = edge_pairs[i];
-        const uint64_t e0 = 2 * i, e1 = 2 * i + 1;
-        const bool has1 = e1 < m;
-        uint64_t x0 = mix64(smp.salt ^ e0) + g0;
-        uint64_t x1 = mix64(smp.salt ^ e1) + g0;
-        uint32_t live0 = 0, live1 = 0;
-#pragma unroll
-        for (int b = 0; b < B; ++b) {
-            if (b < (int)nb) {
-                if (smp.all_live || mix64(x0) < smp.T) live0 |= 1u << b;
-                if (smp.all_live || mix64(x1) < smp.T) live1 |= 1u << b;
-            }
-            x0 += kGamma;
-            x1 += kGamma;
-        }
-        if (!has1) live1 = 0;
-        while (live0) {
-            int b = __ffs(live0) - 1;
-            live0 &= live0 - 1;
-            unite<kAll>(parent + (size_t)b * n, cbits, two.x, two.y);
-        }
-        while (live1) {
-            int b = __ffs(live1) - 1;
-            live1 &= live1 - 1;
-            unite<kAll>(parent + (size_t)b * n, cbits, two.z, two.w);
-        }
-    }
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npairs; i += stride)
+        sample_union_pair<B>(edge_pairs[i], i, m, smp, g0, nb, parent, n);
 }
 
 // Sampling alone: every live (edge, sketch) pair of the batch becomes a record (u, v, b, 0),
@@ -81,7 +78,7 @@ k_sample_emit(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, uin
         uint32_t live0 = 0, live1 = 0;
         uint4 two = make_uint4(0, 0, 0, 0);
         if (i < npairs) {
-            two = edge_pairs[i];
+            two = __ldcs(edge_pairs + i);   // streamed once per batch: keep L2 for the forest
             const uint64_t e0 = 2 * i, e1 = 2 * i + 1;
             uint64_t x0 = mix64(smp.salt ^ e0) + g0;
             uint64_t x1 = mix64(smp.salt ^ e1) + g0;
@@ -126,34 +123,23 @@ k_sample_emit(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, uin
 
 // One thread per live record; if the record buffer overflowed, redo the batch with the fused
 // sample+union loop instead (decided on the device, so no host round trip).
-template <int B, bool kAll>
+template <int B>
 __global__ void __launch_bounds__(256)
 k_union_live(const uint4* __restrict__ recs, const unsigned long long* __restrict__ rec_n, uint64_t cap,
-             uint32_t* __restrict__ parent, uint32_t n, const uint32_t* __restrict__ cbits,
-             const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, uint32_t r0, uint32_t nb) {
+             uint32_t* __restrict__ parent, uint32_t n, const uint4* __restrict__ edge_pairs,
+             uint64_t m, Sampler smp, uint32_t r0, uint32_t nb) {
     const unsigned long long cnt = *rec_n;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     if (cnt > cap) {
         const uint64_t npairs = (m + 1) >> 1;
         const uint64_t g0 = (uint64_t)(r0 + 1u) * kGamma;
-        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npairs; i += stride) {
-            const uint4 two = edge_pairs[i];
-            uint64_t x0 = mix64(smp.salt ^ (2 * i)) + g0;
-            uint64_t x1 = mix64(smp.salt ^ (2 * i + 1)) + g0;
-            const bool has1 = 2 * i + 1 < m;
-            for (uint32_t b = 0; b < nb; ++b) {
-                if (smp.all_live || mix64(x0) < smp.T) unite<kAll>(parent + (size_t)b * n, cbits, two.x, two.y);
-                if (has1 && (smp.all_live || mix64(x1) < smp.T))
-                    unite<kAll>(parent + (size_t)b * n, cbits, two.z, two.w);
-                x0 += kGamma;
-                x1 += kGamma;
-            }
-        }
+        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npairs; i += stride)
+            sample_union_pair<B>(edge_pairs[i], i, m, smp, g0, nb, parent, n);
         return;
     }
     for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < cnt; j += stride) {
         const uint4 rc = recs[j];
-        unite<kAll>(parent + (size_t)rc.z * n, cbits, rc.x, rc.y);
+        unite_rand(parent + (size_t)rc.z * n, rc.x, rc.y);
     }
 }
 
@@ -161,74 +147,109 @@ __global__ void k_zero_u64(unsigned long long* p) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *p = 0;
 }
 
-// grid.y = sketch within the batch; full compression + component-size histogram.
-// Each block owns tiles of kCountTile vertices.  Roots are first merged inside a warp
-// (match_any) and then in a shared-memory hash table, so a giant component costs one global
-// atomic per tile instead of one per warp.
-constexpr int kCountTile = 2048;
-constexpr int kCountSlots = 4096;   // power of two, > 2 x tile
+// grid.y = sketch within the batch.  Full compression, then per root the component size and
+// the minimum label key.  Each block owns tiles of kCountTile vertices; equal roots are merged
+// inside a warp (match_any) and then in a shared-memory hash table, so a giant component costs
+// one global atomic pair per tile instead of one per warp.
+// key_mode 0: every vertex offers lk(v) = v (the smallest id); 1: only centers offer their
+// center index (components without a center need no label); 2: sizes only.
+constexpr int kCountTile = 1024;
+constexpr int kCountSlots = 2048;   // power of two, >= 2 x tile
 
 __global__ void __launch_bounds__(256)
-k_compress_count(uint32_t* __restrict__ parent, uint32_t* __restrict__ cnt, uint32_t n) {
+k_compress_count(uint32_t* __restrict__ parent, uint64_t* __restrict__ word, uint32_t n,
+                 const uint32_t* __restrict__ cidx, int key_mode) {
     __shared__ uint32_t tkey[kCountSlots];
-    __shared__ uint32_t tval[kCountSlots];
+    __shared__ uint32_t tcnt[kCountSlots];
+    __shared__ uint32_t tmin[kCountSlots];
     uint32_t* P = parent + (size_t)blockIdx.y * n;
-    uint32_t* C = cnt ? cnt + (size_t)blockIdx.y * n : nullptr;
+    uint64_t* W = word + (size_t)blockIdx.y * n;
     const unsigned lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < kCountSlots; i += blockDim.x) { tkey[i] = kNone; tval[i] = 0; }
+    for (int i = threadIdx.x; i < kCountSlots; i += blockDim.x) { tkey[i] = kNone; tcnt[i] = 0; tmin[i] = kNone; }
     __syncthreads();
     for (uint32_t t0 = blockIdx.x * kCountTile; t0 < n; t0 += gridDim.x * kCountTile) {
         for (uint32_t off = 0; off < (uint32_t)kCountTile; off += blockDim.x) {
             const uint32_t v = t0 + off + threadIdx.x;
             const bool act = v < n;
-            uint32_t root = 0;
-            if (act) root = compress_to_root(P, v);
-            if (C) {
-                const unsigned am = __ballot_sync(0xffffffffu, act);
-                if (act) {
-                    const unsigned grp = __match_any_sync(am, root);
-                    if (lane == (unsigned)(__ffs(grp) - 1)) {
-                        uint32_t h = (root * 0x9E3779B1u) >> (32 - 12);
-                        for (;;) {
-                            const uint32_t old = atomicCAS(&tkey[h], kNone, root);
-                            if (old == kNone || old == root) {
-                                atomicAdd(&tval[h], (uint32_t)__popc(grp));
-                                break;
-                            }
-                            h = (h + 1) & (kCountSlots - 1);
+            uint32_t root = 0, lk = kNone;
+            if (act) {
+                root = compress_to_root(P, v);
+                if (key_mode == 0) lk = v;
+                else if (key_mode == 1) lk = cidx[v];
+            }
+            const unsigned am = __ballot_sync(0xffffffffu, act);
+            if (act) {
+                const unsigned grp = __match_any_sync(am, root);
+                const uint32_t gmin = __reduce_min_sync(grp, lk);
+                if (lane == (unsigned)(__ffs(grp) - 1)) {
+                    uint32_t h = (root * 0x9E3779B1u) >> (32 - 11);
+                    for (;;) {
+                        const uint32_t old = atomicCAS(&tkey[h], kNone, root);
+                        if (old == kNone || old == root) {
+                            atomicAdd(&tcnt[h], (uint32_t)__popc(grp));
+                            if (gmin != kNone) atomicMin(&tmin[h], gmin);
+                            break;
                         }
+                        h = (h + 1) & (kCountSlots - 1);
                     }
                 }
             }
         }
         __syncthreads();
-        if (C) {
-            for (int i = threadIdx.x; i < kCountSlots; i += blockDim.x) {
-                if (tkey[i] != kNone) {
-                    atomicAdd(C + tkey[i], tval[i]);
-                    tkey[i] = kNone;
-                    tval[i] = 0;
-                }
+        for (int i = threadIdx.x; i < kCountSlots; i += blockDim.x) {
+            const uint32_t rt = tkey[i];
+            if (rt != kNone) {
+                atomicAdd(w_count(W + rt), tcnt[i]);
+                if (tmin[i] != kNone) atomicMin(w_key(W + rt), tmin[i]);
+                tkey[i] = kNone;
+                tcnt[i] = 0;
+                tmin[i] = kNone;
             }
         }
         __syncthreads();
     }
 }
 
-// Refresh evaluation: mark the components that hold a seed (bit 31 of their count).
-__global__ void k_cover_roots(const uint32_t* __restrict__ parent, uint32_t* __restrict__ cnt,
+template <bool kAll>
+__global__ void __launch_bounds__(256)
+k_gain_compact(const uint32_t* __restrict__ parent, const uint64_t* __restrict__ word, uint32_t n,
+               uint32_t nb, uint32_t r0, uint32_t R, uint64_t* __restrict__ gain, int first,
+               const uint32_t* __restrict__ cidx, uint32_t* __restrict__ label,
+               uint32_t* __restrict__ size) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        uint64_t g = 0;
+        const uint32_t ci = kAll ? v : cidx[v];
+        for (uint32_t b = 0; b < nb; ++b) {
+            const uint32_t root = parent[(size_t)b * n + v];
+            const uint64_t w = word[(size_t)b * n + root];
+            const uint32_t c = (uint32_t)w;
+            g += c;
+            if (ci != kNone) {
+                const uint32_t l = (uint32_t)(w >> 32);   // smallest center index of the component
+                const size_t o = (size_t)ci * R + r0 + b;
+                label[o] = l;
+                size[o] = (l == ci) ? c : 0u;
+            }
+        }
+        gain[v] = first ? g : gain[v] + g;
+    }
+}
+
+// Recomputation evaluator: flag the components that hold a seed (bit 31 of their size).
+__global__ void k_cover_roots(const uint32_t* __restrict__ parent, uint64_t* __restrict__ word,
                               uint32_t n, uint32_t nb, const uint32_t* __restrict__ seeds,
                               uint32_t nseeds) {
     const uint32_t total = nb * nseeds;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
         const uint32_t b = i / nseeds, sd = seeds[i % nseeds];
         const uint32_t root = parent[(size_t)b * n + sd];
-        atomicOr(cnt + (size_t)b * n + root, kCovered);
+        atomicOr(w_count(word + (size_t)b * n + root), kCovered);
     }
 }
 
-// Refresh evaluation: fresh[j] += sum_b size of batch member j's component unless covered.
-__global__ void k_refresh_gather(const uint32_t* __restrict__ parent, const uint32_t* __restrict__ cnt,
+// Recomputation evaluator: fresh[j] += sum_b size of member j's component unless covered.
+__global__ void k_refresh_gather(const uint32_t* __restrict__ parent, const uint64_t* __restrict__ word,
                                  uint32_t n, uint32_t nb, const uint32_t* __restrict__ batch,
                                  const unsigned int* __restrict__ batch_n,
                                  unsigned long long* __restrict__ fresh) {
@@ -237,35 +258,17 @@ __global__ void k_refresh_gather(const uint32_t* __restrict__ parent, const uint
         const uint32_t x = batch[j];
         unsigned long long d = 0;
         for (uint32_t b = 0; b < nb; ++b) {
-            const uint32_t c = cnt[(size_t)b * n + parent[(size_t)b * n + x]];
+            const uint32_t c = (uint32_t)word[(size_t)b * n + parent[(size_t)b * n + x]];
             d += (c & kCovered) ? 0u : c;
         }
         fresh[j] += d;
     }
 }
 
-template <bool kAll>
-__global__ void __launch_bounds__(256)
-k_gain_compact(const uint32_t* __restrict__ parent, const uint32_t* __restrict__ cnt, uint32_t n,
-               uint32_t nb, uint32_t r0, uint32_t R, uint64_t* __restrict__ gain, int first,
-               const uint32_t* __restrict__ cidx, uint32_t* __restrict__ label,
-               uint32_t* __restrict__ size) {
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
-        uint64_t g = 0;
-        uint32_t ci = kAll ? v : cidx[v];
-        for (uint32_t b = 0; b < nb; ++b) {
-            uint32_t root = parent[(size_t)b * n + v];
-            uint32_t c = cnt[(size_t)b * n + root];
-            g += c;
-            if (ci != kNone) {
-                size_t o = (size_t)ci * R + r0 + b;
-                label[o] = kAll ? root : cidx[root];
-                size[o] = (root == v) ? c : 0u;
-            }
-        }
-        gain[v] = first ? g : gain[v] + g;
-    }
+__global__ void k_labels_out(const uint32_t* __restrict__ P, const uint64_t* __restrict__ W, uint32_t n,
+                             uint32_t* __restrict__ out) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        out[v] = (uint32_t)(W[P[v]] >> 32);
 }
 
 // ---- centers: the rho smallest ckey(v) = mix(v ^ csalt) (distinct: mix is a bijection) ----
@@ -334,13 +337,8 @@ __global__ void k_center_index(uint32_t n, uint32_t rho, const uint32_t* __restr
     }
 }
 
-__global__ void k_labels_out(const uint32_t* __restrict__ P, uint32_t n, uint32_t* __restrict__ out) {
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-        out[v] = P[v];
-}
 
 // Sampling and unions of one batch as two kernels (records of live pairs in between).
-template <bool kAll>
 int launch_sample_split(im_ctx* c, uint32_t r0, uint32_t nb) {
     const unsigned T = 256;
     const uint64_t npairs = (c->m + 1) >> 1;
@@ -353,8 +351,8 @@ int launch_sample_split(im_ctx* c, uint32_t r0, uint32_t nb) {
     do {                                                                                          \
         IM_LAUNCH(c, K_SAMPLE_EMIT, k_sample_emit<BB>, gs, T, 0, ep, c->m, c->smp, r0, nb, c->d_live, \
                   c->d_live_n, c->live_cap);                                                      \
-        IM_LAUNCH(c, K_UNION, (k_union_live<BB, kAll>), gu, T, 0, c->d_live, c->d_live_n, c->live_cap, \
-                  c->d_parent, c->n, c->d_cbits, ep, c->m, c->smp, r0, nb);                       \
+        IM_LAUNCH(c, K_UNION, k_union_live<BB>, gu, T, 0, c->d_live, c->d_live_n, c->live_cap,      \
+                  c->d_parent, c->n, ep, c->m, c->smp, r0, nb);                                   \
     } while (0)
     const uint32_t cap = c->batch_used;
     if (cap <= 1) IM_SE(1);
@@ -367,24 +365,28 @@ int launch_sample_split(im_ctx* c, uint32_t r0, uint32_t nb) {
     return IM_OK;
 }
 
-template <bool kAll>
-int launch_sample_union(im_ctx* c, uint32_t r0, uint32_t nb) {
+int launch_sample_fused(im_ctx* c, uint32_t r0, uint32_t nb) {
     const unsigned T = 256;
     const uint64_t npairs = (c->m + 1) >> 1;
-    unsigned grid = grid_for(npairs, T, 152u * 16u);
+    const unsigned grid = grid_for(npairs, T, 152u * 16u);
     const uint4* ep = reinterpret_cast<const uint4*>(c->d_edges);
-    const uint32_t* cb = c->d_cbits;
-#define IM_SU(BB)                                                                                \
-    IM_LAUNCH(c, K_SAMPLE_UNION, (k_sample_union<BB, kAll>), grid, T, 0, ep, c->m, c->smp, r0, nb, \
-              c->d_parent, c->n, cb)
-    uint32_t cap = c->batch_used;
-    if (cap <= 1) IM_SU(1);
-    else if (cap <= 2) IM_SU(2);
-    else if (cap <= 4) IM_SU(4);
-    else if (cap <= 8) IM_SU(8);
-    else if (cap <= 16) IM_SU(16);
-    else IM_SU(32);
-#undef IM_SU
+    IM_LAUNCH(c, K_SAMPLE_UNION, k_sample_union<1>, grid, T, 0, ep, c->m, c->smp, r0, nb, c->d_parent, c->n);
+    return IM_OK;
+}
+
+// init + sampling + unions + compression of sketches r0 .. r0+nb-1
+int batch_components(im_ctx* c, uint32_t r0, uint32_t nb, int key_mode) {
+    const uint32_t n = c->n;
+    const unsigned T = 256;
+    IM_LAUNCH(c, K_BATCH_INIT, k_batch_init, grid_for((uint64_t)n * nb, T, 152u * 16u), T, 0,
+              c->d_parent, c->d_word, n, nb);
+    if ((c->smp.all_live || c->smp.T != 0) && c->m > 0) {
+        const int rc = (c->d_live && nb <= c->batch_used) ? launch_sample_split(c, r0, nb)
+                                                           : launch_sample_fused(c, r0, nb);
+        if (rc) return rc;
+    }
+    dim3 g(grid_for(n, kCountTile, 152u * 8u), nb);
+    IM_LAUNCH(c, K_COMPRESS_COUNT, k_compress_count, g, T, 0, c->d_parent, c->d_word, n, c->d_cidx, key_mode);
     return IM_OK;
 }
 
@@ -428,52 +430,30 @@ int im_select_centers(im_ctx* c, uint32_t* d_flags, uint64_t* d_pos) {
 int im_sketch_batches(im_ctx* c) {
     const uint32_t n = c->n, R = c->R;
     const unsigned T = 256;
-    const bool any_live = c->smp.all_live || c->smp.T != 0;
     for (uint32_t r0 = 0; r0 < R; r0 += c->batch_used) {
-        uint32_t nb = R - r0 < c->batch_used ? R - r0 : c->batch_used;
-        IM_LAUNCH(c, K_BATCH_INIT, k_batch_init, grid_for((uint64_t)n * nb, T, 152u * 16u), T, 0,
-                  c->d_parent, c->d_cnt, n, nb);
-        if (any_live && c->m > 0) {
-            int rc;
-            if (c->d_live)
-                rc = c->all_centers ? launch_sample_split<true>(c, r0, nb)
-                                    : launch_sample_split<false>(c, r0, nb);
-            else
-                rc = c->all_centers ? launch_sample_union<true>(c, r0, nb)
-                                    : launch_sample_union<false>(c, r0, nb);
-            if (rc) return rc;
-        }
-        dim3 g(grid_for(n, kCountTile, 152u * 8u), nb);
-        IM_LAUNCH(c, K_COMPRESS_COUNT, k_compress_count, g, T, 0, c->d_parent, c->d_cnt, n);
+        const uint32_t nb = R - r0 < c->batch_used ? R - r0 : c->batch_used;
+        int rc = batch_components(c, r0, nb, c->all_centers ? 0 : 1);
+        if (rc) return rc;
         if (c->all_centers)
             IM_LAUNCH(c, K_GAIN_COMPACT, k_gain_compact<true>, grid_for(n, T, 152u * 16u), T, 0,
-                      c->d_parent, c->d_cnt, n, nb, r0, R, c->d_gain0, r0 == 0 ? 1 : 0, c->d_cidx,
+                      c->d_parent, c->d_word, n, nb, r0, R, c->d_gain0, r0 == 0 ? 1 : 0, c->d_cidx,
                       c->d_label, c->d_size);
         else
             IM_LAUNCH(c, K_GAIN_COMPACT, k_gain_compact<false>, grid_for(n, T, 152u * 16u), T, 0,
-                      c->d_parent, c->d_cnt, n, nb, r0, R, c->d_gain0, r0 == 0 ? 1 : 0, c->d_cidx,
+                      c->d_parent, c->d_word, n, nb, r0, R, c->d_gain0, r0 == 0 ? 1 : 0, c->d_cidx,
                       c->d_label, c->d_size);
     }
     IM_CUDA(c, cudaGetLastError());
     return IM_OK;
 }
 
-// Min-id labels of one sketch (test hook): union-find with plain smallest-id hooking.
+// Min-id labels of one sketch (test hook): the component minimum of lk(v) = v.
 int im_labels_min(im_ctx* c, uint32_t r, uint32_t* d_out) {
     const uint32_t n = c->n;
     const unsigned T = 256;
-    IM_LAUNCH(c, K_BATCH_INIT, k_batch_init, grid_for(n, T, 152u * 16u), T, 0, c->d_parent,
-              (uint32_t*)nullptr, n, 1u);
-    if ((c->smp.all_live || c->smp.T != 0) && c->m > 0) {
-        uint32_t saved = c->batch_used;
-        c->batch_used = 1;
-        int rc = launch_sample_union<true>(c, r, 1);
-        c->batch_used = saved;
-        if (rc) return rc;
-    }
-    dim3 g(grid_for(n, kCountTile, 152u * 8u), 1);
-    IM_LAUNCH(c, K_LABELS_MIN, k_compress_count, g, T, 0, c->d_parent, (uint32_t*)nullptr, n);
-    IM_LAUNCH(c, K_LABELS_OUT, k_labels_out, grid_for(n, T, 152u * 8u), T, 0, c->d_parent, n, d_out);
+    int rc = batch_components(c, r, 1, 0);
+    if (rc) return rc;
+    IM_LAUNCH(c, K_LABELS_OUT, k_labels_out, grid_for(n, T, 152u * 8u), T, 0, c->d_parent, c->d_word, n, d_out);
     IM_CUDA(c, cudaGetLastError());
     return IM_OK;
 }
@@ -487,22 +467,15 @@ int im_refresh_eval(im_ctx* c, const uint32_t* d_batch, const unsigned int* d_ba
                     uint64_t batch_hint) {
     const uint32_t n = c->n, R = c->R;
     const unsigned T = 256;
-    const bool any_live = c->smp.all_live || c->smp.T != 0;
     for (uint32_t r0 = 0; r0 < R; r0 += c->batch_used) {
         const uint32_t nb = R - r0 < c->batch_used ? R - r0 : c->batch_used;
-        IM_LAUNCH(c, K_BATCH_INIT, k_batch_init, grid_for((uint64_t)n * nb, T, 152u * 16u), T, 0,
-                  c->d_parent, c->d_cnt, n, nb);
-        if (any_live && c->m > 0) {
-            int rc = c->d_live ? launch_sample_split<true>(c, r0, nb) : launch_sample_union<true>(c, r0, nb);
-            if (rc) return rc;
-        }
-        dim3 g(grid_for(n, kCountTile, 152u * 8u), nb);
-        IM_LAUNCH(c, K_COMPRESS_COUNT, k_compress_count, g, T, 0, c->d_parent, c->d_cnt, n);
+        int rc = batch_components(c, r0, nb, 2);
+        if (rc) return rc;
         if (nseeds)
             IM_LAUNCH(c, K_COVER_ROOTS, k_cover_roots, grid_for((uint64_t)nb * nseeds, T), T, 0, c->d_parent,
-                      c->d_cnt, n, nb, d_seeds, nseeds);
+                      c->d_word, n, nb, d_seeds, nseeds);
         IM_LAUNCH(c, K_REFRESH_GATHER, k_refresh_gather, grid_for(batch_hint, T, 152u * 16u), T, 0,
-                  c->d_parent, c->d_cnt, n, nb, d_batch, d_batch_n, d_fresh);
+                  c->d_parent, c->d_word, n, nb, d_batch, d_batch_n, d_fresh);
     }
     IM_CUDA(c, cudaGetLastError());
     return IM_OK;

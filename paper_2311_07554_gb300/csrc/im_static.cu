@@ -44,7 +44,7 @@ __global__ void k_static_sample_union(const uint32_t* __restrict__ u, const uint
             atomicOr(status, 1u);
             continue;
         }
-        if (edge_live(smp, edge_key(smp, e), r)) unite<true>(P, nullptr, a, b);
+        if (edge_live(smp, edge_key(smp, e), r)) unite_min(P, a, b);
     }
 }
 
