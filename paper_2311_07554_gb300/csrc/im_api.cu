@@ -49,7 +49,7 @@ void free_sketch_state(im_ctx* c) {
     dfree(c->d_cbits); dfree(c->d_cidx); dfree(c->d_centers);
     dfree(c->d_label); dfree(c->d_size); dfree(c->d_gain0);
     dfree(c->d_key); dfree(c->d_stamp); dfree(c->d_seedflag);
-    dfree(c->d_batch); dfree(c->d_fresh); dfree(c->d_seed_list);
+    dfree(c->d_batch); dfree(c->d_fresh); dfree(c->d_seed_list); dfree(c->d_labcache);
     dfree(c->d_parent); dfree(c->d_word); dfree(c->d_live); dfree(c->d_live_n);
     c->live_cap = 0;
     dfree(c->d_fb_queue); dfree(c->d_fb_bits); dfree(c->d_fb_tasks);
@@ -252,7 +252,7 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
     const size_t nc = (size_t)rho * R;
     bool ok = dalloc(c->d_gain0, n) && dalloc(c->d_key, n) && dalloc(c->d_stamp, n) &&
               dalloc(c->d_seedflag, n) && dalloc(c->d_batch, n) && dalloc(c->d_fresh, n) &&
-              dalloc(c->d_seed_list, n) &&
+              dalloc(c->d_seed_list, n) && dalloc(c->d_labcache, (size_t)kLabSlots * R) &&
               dalloc(c->d_label, nc) && dalloc(c->d_size, nc) &&
               dalloc(c->d_parent, (size_t)B * n) && dalloc(c->d_word, (size_t)B * n);
     if (ok && c->m > 0 && (smp.all_live || smp.T != 0)) {

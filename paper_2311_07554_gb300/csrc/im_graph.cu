@@ -43,13 +43,18 @@ __global__ void k_csr_fill(const uint2* __restrict__ edges, uint64_t m,
     }
 }
 
-// Store the per-edge hash key mix(salt ^ e) in every arc (Sec. 2 fusion: the sampling of
-// edge e in sketch r is then one more mix of key + (r+1) G).
-__global__ void k_arc_keys(uint4* __restrict__ arcs, uint64_t narcs, uint64_t salt) {
+// Store in every arc the per-edge hash key mix(salt ^ e) (Sec. 2 fusion: the sampling of
+// edge e in sketch r is then one more mix of key + (r+1) G) and whether its neighbour is a
+// center (bit 31 of the neighbour id), so a search step needs no other lookup.
+__global__ void k_arc_keys(uint4* __restrict__ arcs, uint64_t narcs, uint64_t salt,
+                           const uint32_t* __restrict__ cbits, int all_centers) {
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < narcs; a += stride) {
         uint4 x = arcs[a];
         const uint64_t key = mix64(salt ^ (uint64_t)x.y);
+        const uint32_t y = x.x & kArcIdMask;
+        const uint32_t cen = all_centers ? 1u : ((cbits[y >> 5] >> (y & 31)) & 1u);
+        x.x = y | (cen << 31);
         x.z = (uint32_t)key;
         x.w = (uint32_t)(key >> 32);
         arcs[a] = x;
@@ -222,9 +227,9 @@ int im_graph_build(im_ctx* c, const uint32_t* d_u, const uint32_t* d_v) {
 }
 
 int im_arc_keys(im_ctx* c, uint64_t salt) {
-    if (c->arc_keys_valid && c->arc_salt == salt) return IM_OK;
     if (c->m > 0)
-        IM_LAUNCH(c, K_ARC_KEYS, k_arc_keys, grid_for(2 * c->m, 256, 152u * 16u), 256, 0, c->d_arcs, 2 * c->m, salt);
+        IM_LAUNCH(c, K_ARC_KEYS, k_arc_keys, grid_for(2 * c->m, 256, 152u * 16u), 256, 0, c->d_arcs, 2 * c->m,
+                  salt, c->d_cbits, (int)c->all_centers);
     IM_CUDA(c, cudaGetLastError());
     c->arc_salt = salt;
     c->arc_keys_valid = true;

@@ -18,6 +18,8 @@ constexpr uint32_t kCovered = 0x80000000u;            // size word: component ho
 constexpr uint32_t kNoCenterTag = 0x80000000u;        // spread: component id without a center
 constexpr uint32_t kQcap = 256;                       // per-warp BFS queue (shared memory)
 constexpr uint32_t kSpreadKMax = 16384;
+constexpr uint32_t kArcIdMask = 0x7FFFFFFFu;            // arc word 0: neighbour id | center bit
+constexpr uint32_t kLabSlots = 256;                     // label cache: vertex slots (x mod 256)
 
 // splitmix64 output finaliser (Steele, Lea, Flood 2014).
 __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
@@ -48,7 +50,8 @@ struct GraphView {
     uint64_t m;
     const uint2* edges;     // m (padded to even): (u, v)
     const uint64_t* off;    // n + 1 CSR offsets
-    const uint4* arcs;      // 2m: (neighbour, edge id, key lo, key hi), key = mix(salt ^ e)
+    const uint4* arcs;      // 2m: (neighbour | center bit << 31, edge id, key lo, key hi),
+                            // key = mix(salt ^ e); both rewritten by every build
 };
 
 struct SketchView {
@@ -58,6 +61,7 @@ struct SketchView {
     const uint32_t* label;   // [rho][R]
     uint32_t* size;          // [rho][R], bit 31 = covered by a seed
     const uint8_t* seed_flag;
+    uint64_t* labcache;      // [kLabSlots][R] labels found by searches, reused by MarkSeed
     Sampler smp;
 };
 
@@ -152,6 +156,7 @@ struct im_ctx {
     imk::SelState* d_sel = nullptr;
     imk::SelState* h_sel = nullptr;  // pinned mirror
     uint32_t* d_seed_list = nullptr;   // seeds chosen so far, on the device (n entries)
+    uint64_t* d_labcache = nullptr;    // [kLabSlots][R]: (vertex << 32) | label found by GetCenter
     uint64_t refresh_min = 0;          // batches at least this large are evaluated by refresh
     uint64_t refresh_req = 0;          // user setting (0 = automatic)
     uint64_t refresh_batches = 0;
@@ -209,7 +214,7 @@ void im_prof_end(im_ctx* c, int kid, int ev0);
 // ---- launch wrappers (host) ------------------------------------------------------
 // im_graph.cu
 int im_graph_build(im_ctx* c, const uint32_t* d_u, const uint32_t* d_v);
-int im_arc_keys(im_ctx* c, uint64_t salt);
+int im_arc_keys(im_ctx* c, uint64_t salt);   // keys and center bits of every arc
 int im_scan_u32_to_u64(im_ctx* c, const uint32_t* d_in, uint64_t* d_out, uint64_t count);
 // im_sketch.cu
 int im_select_centers(im_ctx* c, uint32_t* d_flags_tmp, uint64_t* d_scan_tmp);

@@ -75,12 +75,14 @@ __device__ BfsOut warp_bfs_from(const GraphView& g, const SketchView& s, uint32_
             const uint64_t a = base + lane;
             bool live = false;
             uint32_t y = 0;
+            bool cen = false;
             if (a < a1) {
                 const uint4 arc = g.arcs[a];
-                y = arc.x;
+                y = arc.x & kArcIdMask;
+                cen = arc.x >> 31;
                 live = edge_live(s.smp, ((uint64_t)arc.w << 32) | arc.z, r);
             }
-            const unsigned cb = __ballot_sync(kFull, live && is_center(s, y));
+            const unsigned cb = __ballot_sync(kFull, live && cen);
             if (cb) {
                 const uint32_t yc = __shfl_sync(kFull, y, __ffs(cb) - 1);
                 o.label = s.label[(size_t)center_index(s, yc) * s.R + r];
@@ -154,13 +156,14 @@ __device__ LaneRes get_center_32(const GraphView& g, const SketchView& s, uint32
         if (a < a1) arc = g.arcs[a];
         const uint32_t nv = (uint32_t)min((uint64_t)32, a1 - base);
         for (uint32_t i = 0; i < nv; ++i) {
-            const uint32_t y = __shfl_sync(kFull, arc.x, i);
+            const uint32_t yc = __shfl_sync(kFull, arc.x, i);
             const uint32_t klo = __shfl_sync(kFull, arc.z, i);
             const uint32_t khi = __shfl_sync(kFull, arc.w, i);
             if (act) {
                 const uint64_t key = ((uint64_t)khi << 32) | klo;
                 if (s.smp.all_live || mix64(key + rg) < s.smp.T) {
-                    if (is_center(s, y)) {
+                    const uint32_t y = yc & kArcIdMask;
+                    if (yc >> 31) {
                         o.label = s.label[(size_t)center_index(s, y) * s.R + r];
                         act = false;
                     } else if (!over) {
@@ -441,6 +444,8 @@ k_eval(GraphView g, SketchView s, SelState* st, const uint32_t* __restrict__ bat
             }
         } else {
             const LaneRes o = get_center_32(g, s, x, r_lo, r_hi, ql, qw, true, st);
+            if (r < r_hi && !o.overflow)
+                s.labcache[(size_t)(x & (kLabSlots - 1)) * s.R + r] = ((uint64_t)x << 32) | o.label;
             if (r < r_hi) {
                 if (o.overflow) {
                     push_fallback(st, fbt, fb_cap, x, r, FB_EVAL, j);
@@ -478,6 +483,8 @@ k_eval_single(GraphView g, SketchView s, SelState* st, const uint32_t* __restric
             d = (sz & kCovered) ? 0u : sz;
         } else {
             const BfsOut o = warp_bfs_from(g, s, x, r, qw, true, nullptr, 0, 0, st);
+            if (!o.overflow && lane == 0)
+                s.labcache[(size_t)(x & (kLabSlots - 1)) * s.R + r] = ((uint64_t)x << 32) | o.label;
             if (o.overflow) {
                 if (lane == 0) push_fallback(st, fbt, fb_cap, x, r, FB_EVAL, j);
             } else if (o.label != kNone) {
@@ -526,10 +533,17 @@ k_mark_seed(GraphView g, SketchView s, SelState* st, uint32_t sd, FbTask* __rest
                 atomicOr(s.size + (size_t)l * s.R + r, kCovered);
             }
         } else {
-            const BfsOut o = warp_bfs_from(g, s, sd, r, qw, false, nullptr, 0, 0, st);
-            if (lane == 0) {
-                if (o.overflow) push_fallback(st, fbt, fb_cap, sd, r, FB_MARK, 0);
-                else if (o.label != kNone) atomicOr(s.size + (size_t)o.label * s.R + r, kCovered);
+            // a label found when sd was evaluated is still valid: labels depend on the sketch only
+            const uint64_t e = s.labcache[(size_t)(sd & (kLabSlots - 1)) * s.R + r];
+            if ((uint32_t)(e >> 32) == sd) {
+                const uint32_t l = (uint32_t)e;
+                if (lane == 0 && l != kNone) atomicOr(s.size + (size_t)l * s.R + r, kCovered);
+            } else {
+                const BfsOut o = warp_bfs_from(g, s, sd, r, qw, false, nullptr, 0, 0, st);
+                if (lane == 0) {
+                    if (o.overflow) push_fallback(st, fbt, fb_cap, sd, r, FB_MARK, 0);
+                    else if (o.label != kNone) atomicOr(s.size + (size_t)o.label * s.R + r, kCovered);
+                }
             }
         }
     }
@@ -579,12 +593,14 @@ k_fallback(GraphView g, SketchView s, SelState* st, const FbTask* __restrict__ f
                 const uint64_t a = base + lane;
                 bool live = false;
                 uint32_t y = 0;
+                bool cen = false;
                 if (a < a1) {
                     const uint4 arc = g.arcs[a];
-                    y = arc.x;
+                    y = arc.x & kArcIdMask;
+                    cen = arc.x >> 31;
                     live = edge_live(s.smp, ((uint64_t)arc.w << 32) | arc.z, r);
                 }
-                const unsigned cb = __ballot_sync(kFull, live && is_center(s, y));
+                const unsigned cb = __ballot_sync(kFull, live && cen);
                 if (cb) {
                     const uint32_t yc = __shfl_sync(kFull, y, __ffs(cb) - 1);
                     label = s.label[(size_t)center_index(s, yc) * s.R + r];
@@ -712,7 +728,7 @@ SketchView sketch_view(const im_ctx* c) {
     SketchView s;
     s.R = c->R; s.rho = c->rho; s.all_centers = c->all_centers;
     s.cbits = c->d_cbits; s.cidx = c->d_cidx; s.label = c->d_label; s.size = c->d_size;
-    s.seed_flag = c->d_seedflag; s.smp = c->smp;
+    s.seed_flag = c->d_seedflag; s.labcache = c->d_labcache; s.smp = c->smp;
     return s;
 }
 
@@ -743,6 +759,7 @@ int im_selection_init(im_ctx* c) {
     IM_LAUNCH(c, K_INIT_KEYS, k_init_keys, grid_for(c->n > nsize ? c->n : nsize, T, 152u * 16u), T, 0,
               c->d_gain0, c->n, c->key_bits, c->d_key, c->d_stamp, c->d_seedflag, c->d_size, nsize);
     IM_CUDA(c, cudaMemsetAsync(c->d_sel, 0, sizeof(SelState), c->stream));
+    IM_CUDA(c, cudaMemsetAsync(c->d_labcache, 0xFF, (size_t)kLabSlots * c->R * sizeof(uint64_t), c->stream));
     IM_CUDA(c, cudaGetLastError());
     c->seeds.clear();
     c->seed_gains.clear();

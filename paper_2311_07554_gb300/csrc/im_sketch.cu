@@ -1,10 +1,11 @@
 // im_sketch.cu -- Step 1 of Alg. 1: sketch construction (Sec. 3, Alg. 3 Sketch(r)).
 //
 // Batches of B sketches share one pass over the edge list.  Per sketch b of a batch:
-//   init        P[b][v] = v;  W[b][v] = (key = ~0, count = 0)
+//   init        P[b][v] = v;  W[b][v] = (key = lk(v), count = 1)
 //   sample      every live (edge, sketch) pair of the batch becomes a record (u, v, b)
 //   union       one thread per record, randomized linking (expected log-depth trees)
-//   compress    P[b][v] <- root; per root: count += 1 and key = min over members of the
+//   compress    P[b][v] <- root; per root, for every other member: count += 1 and
+//               key = min over members of the
 //               label key of its centers (center index) -- with every vertex a center this
 //               is the smallest id (Alg. 3's canonical label)
 //   gain        Delta[v] += sum_b count(root_b(v)); for a center c_i: label[i] = key of its
@@ -19,18 +20,23 @@ using namespace imk;
 
 namespace {
 
-constexpr uint64_t kWordInit = 0xFFFFFFFF00000000ull;
-
 __device__ __forceinline__ uint32_t* w_count(uint64_t* w) { return reinterpret_cast<uint32_t*>(w); }
 __device__ __forceinline__ uint32_t* w_key(uint64_t* w) { return reinterpret_cast<uint32_t*>(w) + 1; }
 
+// Every vertex starts as the root of its own component: size 1, key = its own label key.
+// Compression then only has to add the vertices that stopped being roots.
+__device__ __forceinline__ uint32_t label_key(uint32_t v, int key_mode, const uint32_t* cidx) {
+    return key_mode == 0 ? v : (key_mode == 1 ? cidx[v] : kNone);
+}
+
 __global__ void k_batch_init(uint32_t* __restrict__ parent, uint64_t* __restrict__ word,
-                             uint32_t n, uint32_t nb) {
+                             uint32_t n, uint32_t nb, const uint32_t* __restrict__ cidx, int key_mode) {
     const uint64_t total = (uint64_t)n * nb;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-        parent[i] = (uint32_t)(i % n);
-        word[i] = kWordInit;
+        const uint32_t v = (uint32_t)(i % n);
+        parent[i] = v;
+        if (word) word[i] = ((uint64_t)label_key(v, key_mode, cidx) << 32) | 1u;
     }
 }
 
@@ -172,13 +178,14 @@ k_compress_count(uint32_t* __restrict__ parent, uint64_t* __restrict__ word, uin
             const uint32_t v = t0 + off + threadIdx.x;
             const bool act = v < n;
             uint32_t root = 0, lk = kNone;
+            bool member = false;   // v stopped being a root: its root must count it
             if (act) {
                 root = compress_to_root(P, v);
-                if (key_mode == 0) lk = v;
-                else if (key_mode == 1) lk = cidx[v];
+                member = root != v;
+                if (member) lk = label_key(v, key_mode, cidx);
             }
-            const unsigned am = __ballot_sync(0xffffffffu, act);
-            if (act) {
+            const unsigned am = __ballot_sync(0xffffffffu, member);
+            if (member) {
                 const unsigned grp = __match_any_sync(am, root);
                 const uint32_t gmin = __reduce_min_sync(grp, lk);
                 if (lane == (unsigned)(__ffs(grp) - 1)) {
@@ -379,7 +386,7 @@ int batch_components(im_ctx* c, uint32_t r0, uint32_t nb, int key_mode) {
     const uint32_t n = c->n;
     const unsigned T = 256;
     IM_LAUNCH(c, K_BATCH_INIT, k_batch_init, grid_for((uint64_t)n * nb, T, 152u * 16u), T, 0,
-              c->d_parent, c->d_word, n, nb);
+              c->d_parent, c->d_word, n, nb, c->d_cidx, key_mode);
     if ((c->smp.all_live || c->smp.T != 0) && c->m > 0) {
         const int rc = (c->d_live && nb <= c->batch_used) ? launch_sample_split(c, r0, nb)
                                                            : launch_sample_fused(c, r0, nb);
