@@ -124,6 +124,51 @@ def _traffic(kernel: str, units_per_launch: float):
         return None
 
 
+# Algorithmic work per unit (stated in DESIGN.md, section "Roofline model"):
+#   sample_emit  one hash per (edge, sketch) pair: 22 32-bit integer operations (64-bit add,
+#                three 64-bit xor-shifts, two 64-bit multiplies, 64-bit compare) -> bound "alu"
+#   union        one live (edge, sketch) pair: its 16-byte record read plus two random
+#                32-byte sector reads for the endpoints' parents -> 80 bytes, bound "hbm"
+#   compress     one (vertex, sketch): parent read + write, root word update -> 16 bytes, "hbm"
+ALU_OPS_PER_PAIR = 22.0
+UNION_BYTES_PER_PAIR = 80.0
+COMPRESS_BYTES_PER_VERTEX = 16.0
+
+
+def kernel_rooflines(prof, st, live0, n, m, R, steps, peaks, peak_src, clk):
+    out = {}
+    total_ms = sum(x[0] for x in prof.values()) or 1.0
+    refresh = int(st.get("refresh_batches", 0)) // max(1, steps)
+    passes = (1 + refresh) * steps                      # sketch passes over all R sketches
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = 152 * 128 * mhz * 1e6 / 1e12             # Tops/s: 152 SMs x 128 int32 lanes
+    hbm = peaks.get("hbm_gbs", 6800.0)
+
+    def entry(name, bound, units, per_unit, unit, peak, psrc):
+        ms, nl = prof[name]
+        avg_s = ms / nl / 1e3
+        per_launch = units / nl
+        ach = per_launch * per_unit / avg_s / (1e12 if unit == "Tops/s" else 1e9)
+        return {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
+                "frac": ach / peak, "traffic": _traffic(name, per_launch),
+                "units_per_launch": per_launch, "avg_launch_ms": avg_s * 1e3,
+                "share_of_device_time": ms / total_ms, "peak_source": psrc}
+
+    if "sample_emit" in prof:
+        out["sample_emit"] = entry("sample_emit", "alu", float(m) * R * passes, ALU_OPS_PER_PAIR,
+                                   "Tops/s", alu_peak,
+                                   f"derived: 152 SMs x 128 int32 lanes x {mhz:.0f} MHz ({peak_src} max clock)")
+    live = st.get("live_pairs", 0) - live0
+    if "union" in prof and live > 0:
+        out["union"] = entry("union", "hbm", float(live), UNION_BYTES_PER_PAIR, "GB/s", hbm,
+                             f"hbm_gbs of MEASURED_PEAKS.json ({peak_src})")
+    if "compress_count" in prof:
+        out["compress_count"] = entry("compress_count", "hbm", float(n) * R * passes,
+                                      COMPRESS_BYTES_PER_VERTEX, "GB/s", hbm,
+                                      f"hbm_gbs of MEASURED_PEAKS.json ({peak_src})")
+    return out
+
+
 # ----------------------------------------------------------------------- CPU baseline
 def cpu_sample(n, u, v, prm, sketches=CPU_SAMPLE_SKETCHES):
     """The oracle on a bounded sample: the first `sketches` sketches of the workload, all
@@ -209,6 +254,7 @@ def run_ours(args, n, u, v, prm):
     # timed region: K steps, L2 flushed before each (outside the events)
     im.im_profile_reset(ctx.h)
     im.im_profile_enable(ctx.h, True)
+    live0 = ctx.stats()["live_pairs"]
     clocks = ClockSampler(local)
     if dist:
         dist.barrier()
@@ -275,24 +321,9 @@ def run_ours(args, n, u, v, prm):
         peaks, peak_src = _peaks()
         total_ms = sum(x[0] for x in prof.values())
         top = max(prof.items(), key=lambda kv: kv[1][0])
-        su_ms, su_n = prof.get("sample_union", (0.0, 0))
-        roof = None
-        if su_n:
-            # dominant kernel of sketch construction: nb * m pairs hashed per launch
-            launches_per_step = su_n / args.steps
-            units = pairs / launches_per_step                   # pairs per launch
-            avg_s = su_ms / su_n / 1e3
-            ops_per_pair = 24.0                                 # 32-bit integer ops per hash
-            sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-            alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12          # Tops/s
-            achieved = units * ops_per_pair / avg_s / 1e12
-            roof = {"kernel": "sample_union", "bound": "alu", "achieved": achieved, "peak": alu_peak,
-                    "unit": "Tops/s", "frac": achieved / alu_peak,
-                    "traffic": _traffic("sample_union", units),
-                    "peak_source": "derived: 152 SMs x 128 int32 lanes x max SM clock "
-                                   f"({sm_mhz:.0f} MHz, {peak_src})",
-                    "pairs_per_s_per_launch": units / avg_s,
-                    "share_of_device_time": su_ms / total_ms if total_ms else None}
+        roofs = kernel_rooflines(prof, st, live0, n, m, R, args.steps, peaks, peak_src, clk)
+        roof = roofs.get(top[0]) or (max(roofs.values(), key=lambda r: r["share_of_device_time"])
+                                     if roofs else None)
         cpu = cpu_sample(n, u, v, prm)
         line = {
             "metric": METRIC,
@@ -311,6 +342,7 @@ def run_ours(args, n, u, v, prm):
             "evaluations": int(st["evaluations"]),
             "refresh_batches": int(st["refresh_batches"]),
             "roofline": roof,
+            "kernel_rooflines": list(roofs.values()),
             "cpu_baseline": cpu,
             "e2e": {"value": pairs * ws / e2e_s, "unit": "pairs/s",
                     "h2d_bytes_per_step": 8 * m, "d2h_bytes_per_step": 12 * k + 8},

@@ -137,6 +137,7 @@ typedef struct {
     uint64_t hop2_searches;         /* (vertex, sketch) searches that went past the 1st hop */
     uint64_t hop2_chunks;           /* 32-arc chunks scanned by those searches             */
     uint64_t refresh_batches;       /* batches evaluated by recomputing the sketches        */
+    uint64_t live_pairs;            /* live (edge, sketch) pairs unioned since im_create    */
 } im_stats;
 
 int im_get_stats(im_ctx* ctx, im_stats* out);
@@ -199,6 +200,11 @@ int im_sketch_static(uint32_t n, uint64_t m, const uint32_t* d_u, const uint32_t
  * 0 = automatic (max(16384, n / 16)); UINT64_MAX disables it.  Takes effect at the next
  * im_build_sketches. */
 int im_set_refresh_threshold(im_ctx* ctx, uint64_t min_batch);
+
+/* Tuning: 2 runs consecutive sketch batches on two streams so that one batch's hashing
+ * overlaps another's union-find (both lanes' scratch is allocated either way); 1 (default)
+ * runs them in order on the context stream. */
+int im_set_pipeline(im_ctx* ctx, uint32_t lanes);
 
 /* The context's stream (a cudaStream_t). */
 void* im_stream(im_ctx* ctx);

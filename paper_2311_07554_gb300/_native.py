@@ -33,7 +33,7 @@ class im_stats(ctypes.Structure):
                 ("bfs_fallbacks", ctypes.c_uint64), ("launches", ctypes.c_uint64),
                 ("sketch_batch", ctypes.c_uint32), ("hop1_arcs", ctypes.c_uint64),
                 ("hop2_searches", ctypes.c_uint64), ("hop2_chunks", ctypes.c_uint64),
-                ("refresh_batches", ctypes.c_uint64)]
+                ("refresh_batches", ctypes.c_uint64), ("live_pairs", ctypes.c_uint64)]
 
 
 def lib():
@@ -66,6 +66,7 @@ def lib():
         "im_kernel_name": ([i32], c.c_char_p),
         "im_set_sketch_batch": ([vp, u32], i32),
         "im_set_refresh_threshold": ([vp, u64], i32),
+        "im_set_pipeline": ([vp, u32], i32),
         "im_stream": ([vp], vp),
         "im_sketch_static": ([u32, u64, vp, vp, u64, dbl, u32, vp, vp, vp], i32),
         "im_last_error": ([vp], c.c_char_p),
@@ -210,6 +211,10 @@ def im_set_sketch_batch(ctx, batch: int):
 
 def im_set_refresh_threshold(ctx, min_batch: int):
     _check(ctx, lib().im_set_refresh_threshold(ctx, min_batch))
+
+
+def im_set_pipeline(ctx, lanes: int):
+    _check(ctx, lib().im_set_pipeline(ctx, lanes))
 
 
 def im_stream(ctx) -> int:

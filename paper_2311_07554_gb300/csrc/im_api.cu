@@ -50,7 +50,9 @@ void free_sketch_state(im_ctx* c) {
     dfree(c->d_label); dfree(c->d_size); dfree(c->d_gain0);
     dfree(c->d_key); dfree(c->d_stamp); dfree(c->d_seedflag);
     dfree(c->d_batch); dfree(c->d_fresh); dfree(c->d_seed_list); dfree(c->d_labcache);
-    dfree(c->d_parent); dfree(c->d_word); dfree(c->d_live); dfree(c->d_live_n);
+    for (auto& L : c->lane) {
+        dfree(L.parent); dfree(L.word); dfree(L.live); dfree(L.live_n); dfree(L.gain); dfree(L.fresh);
+    }
     c->live_cap = 0;
     dfree(c->d_fb_queue); dfree(c->d_fb_bits); dfree(c->d_fb_tasks);
     c->batch_alloc = 0;
@@ -73,6 +75,7 @@ __global__ void k_iota(uint32_t* p, uint32_t cnt) {
 void resolve_events(im_ctx* c) {
     if (c->ev_pending.empty()) return;
     cudaStreamSynchronize(c->stream);
+    if (c->lane_stream1) cudaStreamSynchronize(c->lane_stream1);
     for (auto& pe : c->ev_pending) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, c->ev_pool[pe.second.first], c->ev_pool[pe.second.second]) == cudaSuccess)
@@ -104,13 +107,13 @@ void im_prof_begin(im_ctx* c, int kid, int* ev0) {
     if (!c->prof) return;
     int e = next_event(c);
     if (e < 0) return;
-    cudaEventRecord(c->ev_pool[e], c->stream);
+    cudaEventRecord(c->ev_pool[e], c->cur);
     *ev0 = e;
 }
 
 void im_prof_end(im_ctx* c, int kid, int ev0) {
     if (!c->prof || ev0 < 0) return;
-    cudaEventRecord(c->ev_pool[ev0 + 1], c->stream);
+    cudaEventRecord(c->ev_pool[ev0 + 1], c->cur);
     c->ev_pending.push_back({kid, {ev0, ev0 + 1}});
 }
 
@@ -153,6 +156,16 @@ int im_create(im_ctx** out, uint32_t n, uint64_t m, const uint32_t* u, const uin
         }
         c->own_stream = true;
     }
+    c->cur = c->stream;
+    if (cudaStreamCreateWithFlags(&c->lane_stream1, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        g_create_error = "stream or event creation failed";
+        im_destroy(c);
+        return IM_ECUDA;
+    }
+    c->lane[0].stream = c->stream;
+    c->lane[1].stream = c->lane_stream1;
     uint32_t *du = nullptr, *dv = nullptr;
     int rc = IM_OK;
     do {
@@ -163,6 +176,11 @@ int im_create(im_ctx** out, uint32_t n, uint64_t m, const uint32_t* u, const uin
         }
         cudaMemsetAsync(c->d_sel, 0, sizeof(SelState), c->stream);
         memset(c->h_sel, 0, sizeof(SelState));
+        if (cudaMalloc(&c->d_live_total, sizeof(unsigned long long)) != cudaSuccess ||
+            cudaMemsetAsync(c->d_live_total, 0, sizeof(unsigned long long), c->stream) != cudaSuccess) {
+            rc = im_fail(c, IM_ENOMEM, "counters");
+            break;
+        }
         if (cudaMalloc(&c->d_spread_total, sizeof(unsigned long long)) != cudaSuccess) {
             rc = im_fail(c, IM_ENOMEM, "spread total");
             break;
@@ -200,6 +218,13 @@ int im_set_sketch_batch(im_ctx* c, uint32_t batch) {
     if (batch != 0 && (batch > 32 || (batch & (batch - 1)) != 0))
         return im_fail(c, IM_EINVAL, "sketch batch must be 0 or a power of two <= 32");
     c->batch_req = batch;
+    return IM_OK;
+}
+
+int im_set_pipeline(im_ctx* c, uint32_t lanes) {
+    if (!c) return IM_EINVAL;
+    if (lanes != 1 && lanes != 2) return im_fail(c, IM_EINVAL, "lanes must be 1 or 2");
+    c->lanes = lanes;
     return IM_OK;
 }
 
@@ -254,7 +279,9 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
               dalloc(c->d_seedflag, n) && dalloc(c->d_batch, n) && dalloc(c->d_fresh, n) &&
               dalloc(c->d_seed_list, n) && dalloc(c->d_labcache, (size_t)kLabSlots * R) &&
               dalloc(c->d_label, nc) && dalloc(c->d_size, nc) &&
-              dalloc(c->d_parent, (size_t)B * n) && dalloc(c->d_word, (size_t)B * n);
+              dalloc(c->lane[0].parent, (size_t)B * n) && dalloc(c->lane[0].word, (size_t)B * n) &&
+              dalloc(c->lane[1].parent, (size_t)B * n) && dalloc(c->lane[1].word, (size_t)B * n) &&
+              dalloc(c->lane[1].gain, n) && dalloc(c->lane[1].fresh, n);
     if (ok && c->m > 0 && (smp.all_live || smp.T != 0)) {
         // live-pair records of one batch: expected p m B, with a generous margin; a batch that
         // still overflows falls back to the fused sample+union loop on the device
@@ -262,7 +289,8 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
         double cap = 1.3 * ex + 16.0 * std::sqrt(ex) + 65536.0;
         if (cap > (double)(1ull << 28)) cap = (double)(1ull << 28);
         c->live_cap = (uint64_t)cap;
-        ok = dalloc(c->d_live, c->live_cap) && dalloc(c->d_live_n, 1);
+        ok = dalloc(c->lane[0].live, c->live_cap) && dalloc(c->lane[0].live_n, 1) &&
+             dalloc(c->lane[1].live, c->live_cap) && dalloc(c->lane[1].live_n, 1);
     }
     if (ok && !all) {
         const size_t nw = ((size_t)n + 31) / 32;
@@ -448,6 +476,9 @@ int im_get_stats(im_ctx* c, im_stats* out) {
         out->hop2_searches = c->h_sel->hop2_calls;
         out->hop2_chunks = c->h_sel->hop2_chunks;
         out->refresh_batches = c->refresh_batches;
+        unsigned long long lt = 0;
+        cudaMemcpy(&lt, c->d_live_total, sizeof lt, cudaMemcpyDeviceToHost);
+        out->live_pairs = lt;
     }
     return IM_OK;
 }
@@ -494,11 +525,14 @@ void im_destroy(im_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_sketch_state(c);
     dfree(c->d_edges); dfree(c->d_off); dfree(c->d_arcs);
-    dfree(c->d_spread_pairs); dfree(c->d_spread_seeds); dfree(c->d_spread_total);
+    dfree(c->d_spread_pairs); dfree(c->d_spread_seeds); dfree(c->d_spread_total); dfree(c->d_live_total);
     if (c->d_sel) cudaFree(c->d_sel);
     if (c->h_sel) cudaFreeHost(c->h_sel);
     if (c->d_tmp) cudaFree(c->d_tmp);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
+    if (c->lane_stream1) { cudaStreamSynchronize(c->lane_stream1); cudaStreamDestroy(c->lane_stream1); }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }

@@ -165,13 +165,25 @@ struct im_ctx {
     std::vector<uint64_t> round_evals;
     uint64_t batches = 0;
 
-    // sketch-batch scratch
+    // sketch-batch scratch: two lanes, each with its own stream, so that consecutive batches
+    // overlap (one batch's hashing with the other's union-find)
+    struct Lane {
+        cudaStream_t stream = nullptr;
+        uint32_t* parent = nullptr;
+        uint64_t* word = nullptr;                // per root: size (low half), min label key (high)
+        uint4* live = nullptr;                   // live (u, v, sketch) records of one batch
+        unsigned long long* live_n = nullptr;
+        uint64_t* gain = nullptr;                // lane 1: its share of the initial gains
+        unsigned long long* fresh = nullptr;     // lane 1: its share of a refresh evaluation
+    };
+    Lane lane[2];
+    cudaStream_t lane_stream1 = nullptr;         // owned
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t cur = nullptr;                  // stream the next launch goes to
+    uint32_t lanes = 1;                          // 1: batches in order on the context stream
     uint32_t batch_req = 0, batch_used = 0, batch_alloc = 0;
-    uint32_t* d_parent = nullptr;
-    uint64_t* d_word = nullptr;              // per root: size (low half), min label key (high)
-    uint4* d_live = nullptr;                 // live (u, v, sketch) records of one batch
-    unsigned long long* d_live_n = nullptr;
     uint64_t live_cap = 0;
+    unsigned long long* d_live_total = nullptr;  // live (edge, sketch) pairs unioned, cumulative
 
     // BFS fallback scratch
     uint32_t fb_slots = 0;
@@ -207,7 +219,7 @@ void im_prof_end(im_ctx* c, int kid, int ev0);
     do {                                                                                \
         int _ev0 = -1;                                                                  \
         im_prof_begin((ctx), (kid), &_ev0);                                             \
-        kern<<<(grid), (block), (smem), (ctx)->stream>>>(__VA_ARGS__);                  \
+        kern<<<(grid), (block), (smem), (ctx)->cur>>>(__VA_ARGS__);                     \
         im_prof_end((ctx), (kid), _ev0);                                                \
     } while (0)
 

@@ -133,8 +133,9 @@ template <int B>
 __global__ void __launch_bounds__(256)
 k_union_live(const uint4* __restrict__ recs, const unsigned long long* __restrict__ rec_n, uint64_t cap,
              uint32_t* __restrict__ parent, uint32_t n, const uint4* __restrict__ edge_pairs,
-             uint64_t m, Sampler smp, uint32_t r0, uint32_t nb) {
+             uint64_t m, Sampler smp, uint32_t r0, uint32_t nb, unsigned long long* __restrict__ total) {
     const unsigned long long cnt = *rec_n;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(total, cnt);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     if (cnt > cap) {
         const uint64_t npairs = (m + 1) >> 1;
@@ -346,20 +347,20 @@ __global__ void k_center_index(uint32_t n, uint32_t rho, const uint32_t* __restr
 
 
 // Sampling and unions of one batch as two kernels (records of live pairs in between).
-int launch_sample_split(im_ctx* c, uint32_t r0, uint32_t nb) {
+int launch_sample_split(im_ctx* c, im_ctx::Lane& L, uint32_t r0, uint32_t nb) {
     const unsigned T = 256;
     const uint64_t npairs = (c->m + 1) >> 1;
     const uint4* ep = reinterpret_cast<const uint4*>(c->d_edges);
     const unsigned gs = grid_for(npairs, T, 152u * 16u);
     const double pl = c->smp.all_live ? 1.0 : c->p;
     const unsigned gu = grid_for((uint64_t)(pl * (double)c->m * nb) + 1, T, 152u * 16u);
-    IM_LAUNCH(c, K_SAMPLE_EMIT, k_zero_u64, 1, 32, 0, c->d_live_n);
+    IM_LAUNCH(c, K_SAMPLE_EMIT, k_zero_u64, 1, 32, 0, L.live_n);
 #define IM_SE(BB)                                                                                 \
     do {                                                                                          \
-        IM_LAUNCH(c, K_SAMPLE_EMIT, k_sample_emit<BB>, gs, T, 0, ep, c->m, c->smp, r0, nb, c->d_live, \
-                  c->d_live_n, c->live_cap);                                                      \
-        IM_LAUNCH(c, K_UNION, k_union_live<BB>, gu, T, 0, c->d_live, c->d_live_n, c->live_cap,      \
-                  c->d_parent, c->n, ep, c->m, c->smp, r0, nb);                                   \
+        IM_LAUNCH(c, K_SAMPLE_EMIT, k_sample_emit<BB>, gs, T, 0, ep, c->m, c->smp, r0, nb, L.live,   \
+                  L.live_n, c->live_cap);                                                         \
+        IM_LAUNCH(c, K_UNION, k_union_live<BB>, gu, T, 0, L.live, L.live_n, c->live_cap, L.parent, \
+                  c->n, ep, c->m, c->smp, r0, nb, c->d_live_total);                               \
     } while (0)
     const uint32_t cap = c->batch_used;
     if (cap <= 1) IM_SE(1);
@@ -372,28 +373,50 @@ int launch_sample_split(im_ctx* c, uint32_t r0, uint32_t nb) {
     return IM_OK;
 }
 
-int launch_sample_fused(im_ctx* c, uint32_t r0, uint32_t nb) {
+int launch_sample_fused(im_ctx* c, im_ctx::Lane& L, uint32_t r0, uint32_t nb) {
     const unsigned T = 256;
     const uint64_t npairs = (c->m + 1) >> 1;
     const unsigned grid = grid_for(npairs, T, 152u * 16u);
     const uint4* ep = reinterpret_cast<const uint4*>(c->d_edges);
-    IM_LAUNCH(c, K_SAMPLE_UNION, k_sample_union<1>, grid, T, 0, ep, c->m, c->smp, r0, nb, c->d_parent, c->n);
+    IM_LAUNCH(c, K_SAMPLE_UNION, k_sample_union<1>, grid, T, 0, ep, c->m, c->smp, r0, nb, L.parent, c->n);
     return IM_OK;
 }
 
-// init + sampling + unions + compression of sketches r0 .. r0+nb-1
-int batch_components(im_ctx* c, uint32_t r0, uint32_t nb, int key_mode) {
+// init + sampling + unions + compression of sketches r0 .. r0+nb-1 in lane L (on c->cur)
+int batch_components(im_ctx* c, im_ctx::Lane& L, uint32_t r0, uint32_t nb, int key_mode) {
     const uint32_t n = c->n;
     const unsigned T = 256;
     IM_LAUNCH(c, K_BATCH_INIT, k_batch_init, grid_for((uint64_t)n * nb, T, 152u * 16u), T, 0,
-              c->d_parent, c->d_word, n, nb, c->d_cidx, key_mode);
+              L.parent, L.word, n, nb, c->d_cidx, key_mode);
     if ((c->smp.all_live || c->smp.T != 0) && c->m > 0) {
-        const int rc = (c->d_live && nb <= c->batch_used) ? launch_sample_split(c, r0, nb)
-                                                           : launch_sample_fused(c, r0, nb);
+        const int rc = (L.live && nb <= c->batch_used) ? launch_sample_split(c, L, r0, nb)
+                                                       : launch_sample_fused(c, L, r0, nb);
         if (rc) return rc;
     }
     dim3 g(grid_for(n, kCountTile, 152u * 8u), nb);
-    IM_LAUNCH(c, K_COMPRESS_COUNT, k_compress_count, g, T, 0, c->d_parent, c->d_word, n, c->d_cidx, key_mode);
+    IM_LAUNCH(c, K_COMPRESS_COUNT, k_compress_count, g, T, 0, L.parent, L.word, n, c->d_cidx, key_mode);
+    return IM_OK;
+}
+
+__global__ void k_add_u64(unsigned long long* __restrict__ dst, const unsigned long long* __restrict__ src,
+                          uint64_t count, const unsigned int* __restrict__ count_dev) {
+    const uint64_t cnt = count_dev ? *count_dev : count;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (uint64_t)gridDim.x * blockDim.x)
+        dst[i] += src[i];
+}
+
+// Lane 1 starts after everything queued so far on the context stream ...
+int lanes_fork(im_ctx* c) {
+    IM_CUDA(c, cudaEventRecord(c->ev_fork, c->stream));
+    IM_CUDA(c, cudaStreamWaitEvent(c->lane_stream1, c->ev_fork, 0));
+    return IM_OK;
+}
+
+// ... and the context stream continues after everything queued on lane 1.
+int lanes_join(im_ctx* c) {
+    c->cur = c->stream;
+    IM_CUDA(c, cudaEventRecord(c->ev_join, c->lane_stream1));
+    IM_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     return IM_OK;
 }
 
@@ -433,23 +456,35 @@ int im_select_centers(im_ctx* c, uint32_t* d_flags, uint64_t* d_pos) {
     return rc;
 }
 
-// Build all R sketches batch by batch; writes gain0, label, size.
+// Build all R sketches batch by batch; writes gain0, label, size.  Batch i runs on lane
+// i mod lanes; lane 1 (if used) accumulates its gains separately, added at the end.
 int im_sketch_batches(im_ctx* c) {
     const uint32_t n = c->n, R = c->R;
     const unsigned T = 256;
-    for (uint32_t r0 = 0; r0 < R; r0 += c->batch_used) {
+    int rc = lanes_fork(c);
+    if (rc) return rc;
+    uint32_t i = 0;
+    for (uint32_t r0 = 0; r0 < R; r0 += c->batch_used, ++i) {
         const uint32_t nb = R - r0 < c->batch_used ? R - r0 : c->batch_used;
-        int rc = batch_components(c, r0, nb, c->all_centers ? 0 : 1);
-        if (rc) return rc;
+        im_ctx::Lane& L = c->lane[i % c->lanes];
+        c->cur = L.stream;
+        rc = batch_components(c, L, r0, nb, c->all_centers ? 0 : 1);
+        if (rc) { lanes_join(c); return rc; }
+        uint64_t* gain = (i % c->lanes) ? L.gain : c->d_gain0;
+        const int first = i < c->lanes ? 1 : 0;
         if (c->all_centers)
             IM_LAUNCH(c, K_GAIN_COMPACT, k_gain_compact<true>, grid_for(n, T, 152u * 16u), T, 0,
-                      c->d_parent, c->d_word, n, nb, r0, R, c->d_gain0, r0 == 0 ? 1 : 0, c->d_cidx,
-                      c->d_label, c->d_size);
+                      L.parent, L.word, n, nb, r0, R, gain, first, c->d_cidx, c->d_label, c->d_size);
         else
             IM_LAUNCH(c, K_GAIN_COMPACT, k_gain_compact<false>, grid_for(n, T, 152u * 16u), T, 0,
-                      c->d_parent, c->d_word, n, nb, r0, R, c->d_gain0, r0 == 0 ? 1 : 0, c->d_cidx,
-                      c->d_label, c->d_size);
+                      L.parent, L.word, n, nb, r0, R, gain, first, c->d_cidx, c->d_label, c->d_size);
     }
+    rc = lanes_join(c);
+    if (rc) return rc;
+    if (c->lanes > 1 && i > 1)
+        IM_LAUNCH(c, K_GAIN_COMPACT, k_add_u64, grid_for(n, T, 152u * 8u), T, 0,
+                  (unsigned long long*)c->d_gain0, (const unsigned long long*)c->lane[1].gain, (uint64_t)n,
+                  (const unsigned int*)nullptr);
     IM_CUDA(c, cudaGetLastError());
     return IM_OK;
 }
@@ -458,9 +493,11 @@ int im_sketch_batches(im_ctx* c) {
 int im_labels_min(im_ctx* c, uint32_t r, uint32_t* d_out) {
     const uint32_t n = c->n;
     const unsigned T = 256;
-    int rc = batch_components(c, r, 1, 0);
+    c->cur = c->stream;
+    int rc = batch_components(c, c->lane[0], r, 1, 0);
     if (rc) return rc;
-    IM_LAUNCH(c, K_LABELS_OUT, k_labels_out, grid_for(n, T, 152u * 8u), T, 0, c->d_parent, c->d_word, n, d_out);
+    IM_LAUNCH(c, K_LABELS_OUT, k_labels_out, grid_for(n, T, 152u * 8u), T, 0, c->lane[0].parent,
+              c->lane[0].word, n, d_out);
     IM_CUDA(c, cudaGetLastError());
     return IM_OK;
 }
@@ -474,16 +511,28 @@ int im_refresh_eval(im_ctx* c, const uint32_t* d_batch, const unsigned int* d_ba
                     uint64_t batch_hint) {
     const uint32_t n = c->n, R = c->R;
     const unsigned T = 256;
-    for (uint32_t r0 = 0; r0 < R; r0 += c->batch_used) {
+    int rc = lanes_fork(c);
+    if (rc) return rc;
+    if (c->lanes > 1)
+        IM_CUDA(c, cudaMemsetAsync(c->lane[1].fresh, 0, (size_t)n * sizeof(uint64_t), c->lane_stream1));
+    uint32_t i = 0;
+    for (uint32_t r0 = 0; r0 < R; r0 += c->batch_used, ++i) {
         const uint32_t nb = R - r0 < c->batch_used ? R - r0 : c->batch_used;
-        int rc = batch_components(c, r0, nb, 2);
-        if (rc) return rc;
+        im_ctx::Lane& L = c->lane[i % c->lanes];
+        c->cur = L.stream;
+        rc = batch_components(c, L, r0, nb, 2);
+        if (rc) { lanes_join(c); return rc; }
         if (nseeds)
-            IM_LAUNCH(c, K_COVER_ROOTS, k_cover_roots, grid_for((uint64_t)nb * nseeds, T), T, 0, c->d_parent,
-                      c->d_word, n, nb, d_seeds, nseeds);
+            IM_LAUNCH(c, K_COVER_ROOTS, k_cover_roots, grid_for((uint64_t)nb * nseeds, T), T, 0, L.parent,
+                      L.word, n, nb, d_seeds, nseeds);
         IM_LAUNCH(c, K_REFRESH_GATHER, k_refresh_gather, grid_for(batch_hint, T, 152u * 16u), T, 0,
-                  c->d_parent, c->d_word, n, nb, d_batch, d_batch_n, d_fresh);
+                  L.parent, L.word, n, nb, d_batch, d_batch_n, (i % c->lanes) ? L.fresh : d_fresh);
     }
+    rc = lanes_join(c);
+    if (rc) return rc;
+    if (c->lanes > 1 && i > 1)
+        IM_LAUNCH(c, K_REFRESH_GATHER, k_add_u64, grid_for(batch_hint, T, 152u * 8u), T, 0, d_fresh,
+                  (const unsigned long long*)c->lane[1].fresh, (uint64_t)0, d_batch_n);
     IM_CUDA(c, cudaGetLastError());
     return IM_OK;
 }

@@ -23,10 +23,11 @@ def _cuda():
     im.lib()
 
 
-def _run(n, u, v, seed, p, R, alpha, k, batch=0, spread_sets=()):
+def _run(n, u, v, seed, p, R, alpha, k, batch=0, spread_sets=(), lanes=1):
     with im.IMContext(n, u, v) as ctx:
         if batch:
             im.im_set_sketch_batch(ctx.h, batch)
+        im.im_set_pipeline(ctx.h, lanes)
         ctx.build_sketches(R, seed, p, alpha)
         out = dict(gains=ctx.gains(), centers=ctx.centers())
         out["label"], out["size"] = ctx.compact()
@@ -96,10 +97,11 @@ def test_small_alpha_forces_global_fallback_search():
     assert g["stats"]["bfs_fallbacks"] > 0
 
 
+@pytest.mark.parametrize("lanes", [1, 2])
 @pytest.mark.parametrize("batch", [1, 2, 4, 8, 16, 32])
-def test_sketch_batch_sizes_agree(batch):
+def test_sketch_batch_sizes_agree(batch, lanes):
     n, u, v = graphgen.erdos_renyi(1500, 6001, 3)
-    g = _run(n, u, v, 42, 0.1, 45, 0.2, 5, batch=batch)
+    g = _run(n, u, v, 42, 0.1, 45, 0.2, 5, batch=batch, lanes=lanes)
     o = _oracle(n, u, v, 42, 0.1, 45, 0.2, 5)
     _compare(g, o, 5)
 
