@@ -19,7 +19,7 @@ const char* const kNames[K_COUNT] = {
     "reduce_reset", "reduce", "sel_init", "sel_hist", "sel_pick", "gather", "eval",
     "fallback", "finalize", "mark_seed", "spread_tasks", "spread_dedup", "labels_min",
     "labels_out", "arc_keys", "sample_emit", "union", "cover_roots", "refresh_gather",
-    "count_above"};
+    "count_above", "zero"};
 
 int bitlen64(uint64_t x) {
     int b = 0;

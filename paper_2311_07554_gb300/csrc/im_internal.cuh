@@ -45,6 +45,30 @@ __device__ __forceinline__ bool edge_live(const Sampler& s, uint64_t key, uint32
     return s.all_live || mix64(key + (uint64_t)(r + 1u) * kGamma) < s.T;
 }
 
+__device__ __forceinline__ uint32_t mix64_hi(uint64_t x);
+
+// Same decision as edge_live, deciding on the high word of the hash whenever it differs from
+// the high word of T (all but a 2^-32 fraction of the pairs).
+__device__ __forceinline__ bool edge_live_fast(const Sampler& s, uint64_t key, uint64_t rg) {
+    if (s.all_live) return true;
+    const uint32_t hh = mix64_hi(key + rg), th = (uint32_t)(s.T >> 32);
+    if (hh != th) return hh < th;
+    return mix64(key + rg) < s.T;
+}
+
+// High 32 bits of mix64(x), computed without the low half of the last multiply and shift:
+// if w = z * C2 (mod 2^64), the finaliser returns w ^ (w >> 31), whose high word is
+// hi(w) ^ (hi(w) >> 31).  hi(mix64(x)) <= hi(T) is a superset test of mix64(x) < T (equal
+// high words need the full value), so callers confirm those pairs with edge_live().
+__device__ __forceinline__ uint32_t mix64_hi(uint64_t x) {
+    uint64_t z = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = z ^ (z >> 27);
+    const uint32_t zl = (uint32_t)z, zh = (uint32_t)(z >> 32);
+    const uint32_t cl = 0x133111EBu, ch = 0x94D049BBu;          // 0x94D049BB133111EB
+    const uint32_t wh = __umulhi(zl, cl) + zl * ch + zh * cl;  // hi 32 bits of z * C2
+    return wh ^ (wh >> 31);
+}
+
 struct GraphView {
     uint32_t n;
     uint64_t m;
@@ -108,7 +132,7 @@ enum KernelId {
     K_REDUCE_RESET, K_REDUCE, K_SEL_INIT, K_SEL_HIST, K_SEL_PICK, K_GATHER, K_EVAL,
     K_FALLBACK, K_FINALIZE, K_MARK_SEED, K_SPREAD_TASKS, K_SPREAD_DEDUP, K_LABELS_MIN,
     K_LABELS_OUT, K_ARC_KEYS, K_SAMPLE_EMIT, K_UNION, K_COVER_ROOTS, K_REFRESH_GATHER, K_COUNT_ABOVE,
-    K_COUNT
+    K_ZERO, K_COUNT
 };
 
 const char* kernel_name(int id);

@@ -45,16 +45,23 @@ struct BfsOut {
 
 // If init != nullptr, x's own arcs were already scanned: the queue starts as
 // [x, init[0], init[stride], ...] (x's live non-center neighbours, distinct) with head = 1.
+//
+// The frontier is expanded up to 32 queued vertices at a time: lane i loads the offsets of
+// queue entry head + i, a warp scan lays their arcs out one after the other, and every chunk
+// of 32 arcs is tested at once (each lane finds the vertex owning its arc by a binary search
+// over the prefix sums held in the lanes).  A search thus costs a few dependent load rounds
+// per BFS level instead of two per visited vertex.
 __device__ BfsOut warp_bfs_from(const GraphView& g, const SketchView& s, uint32_t v, uint32_t r,
                                 uint32_t* q, bool want_seed, const uint32_t* init, uint32_t ninit,
                                 uint32_t init_stride, SelState* st_counters) {
-    uint32_t chunks = 0;
     const unsigned lane = threadIdx.x & 31;
     BfsOut o;
     o.label = kNone; o.count = 0; o.minv = v; o.seen = 0; o.overflow = 0;
+    uint32_t chunks = 0;
     uint32_t head = 0, tail = 1;
     uint32_t seen = want_seed ? (uint32_t)s.seed_flag[v] : 0u;
     uint32_t minv = v;
+    const uint64_t rg = (uint64_t)(r + 1u) * kGamma;
     if (lane == 0) q[0] = v;
     if (init) {
         for (uint32_t t = lane; t < ninit; t += 32) {
@@ -68,46 +75,84 @@ __device__ BfsOut warp_bfs_from(const GraphView& g, const SketchView& s, uint32_
     }
     __syncwarp();
     while (head < tail) {
-        const uint32_t x = q[head++];
-        const uint64_t a0 = g.off[x], a1 = g.off[x + 1];
-        for (uint64_t base = a0; base < a1; base += 32) {
-            ++chunks;
-            const uint64_t a = base + lane;
-            bool live = false;
-            uint32_t y = 0;
-            bool cen = false;
-            if (a < a1) {
-                const uint4 arc = g.arcs[a];
-                y = arc.x & kArcIdMask;
-                cen = arc.x >> 31;
-                live = edge_live(s.smp, ((uint64_t)arc.w << 32) | arc.z, r);
+        const uint32_t nv = min(32u, tail - head);
+        uint64_t a0 = 0;
+        uint32_t deg = 0;
+        if (lane < nv) {
+            const uint32_t x = q[head + lane];
+            a0 = g.off[x];
+            deg = (uint32_t)(g.off[x + 1] - a0);
+        }
+        uint32_t pre = deg;   // inclusive scan of the degrees
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, pre, d);
+            if ((int)lane >= d) pre += y;
+        }
+        const uint32_t total = __shfl_sync(kFull, pre, 31);
+        pre -= deg;           // exclusive
+        head += nv;
+        // four 32-arc chunks per step: their loads are in flight together
+        for (uint32_t base = 0; base < total; base += 128) {
+            uint4 arcs4[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t t = base + 32u * k + lane;
+                uint32_t lo = 0;
+                if (nv > 1) {   // owner of arc t: the largest i < nv with pre_i <= t
+                    uint32_t hi = nv - 1;
+#pragma unroll
+                    for (int it = 0; it < 5; ++it) {
+                        const uint32_t mid = (lo + hi + 1) >> 1;
+                        const uint32_t pm = __shfl_sync(kFull, pre, mid);
+                        if (pm <= t) lo = mid; else hi = mid - 1;
+                        if (lo > hi) hi = lo;
+                    }
+                }
+                const uint64_t ao = __shfl_sync(kFull, a0, lo);
+                const uint32_t po = __shfl_sync(kFull, pre, lo);
+                arcs4[k] = (t < total) ? g.arcs[ao + (t - po)] : make_uint4(0, 0, 0, 0);
             }
-            const unsigned cb = __ballot_sync(kFull, live && cen);
-            if (cb) {
-                const uint32_t yc = __shfl_sync(kFull, y, __ffs(cb) - 1);
-                o.label = s.label[(size_t)center_index(s, yc) * s.R + r];
-                if (lane == 0 && st_counters) atomicAdd(&st_counters->hop2_chunks, (unsigned long long)chunks);
-                return o;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (base + 32u * k >= total) break;
+                ++chunks;
+                const uint32_t t = base + 32u * k + lane;
+                bool live = false, cen = false;
+                uint32_t y = 0;
+                if (t < total) {
+                    const uint4 arc = arcs4[k];
+                    y = arc.x & kArcIdMask;
+                    cen = arc.x >> 31;
+                    live = edge_live_fast(s.smp, ((uint64_t)arc.w << 32) | arc.z, rg);
+                }
+                const unsigned cb = __ballot_sync(kFull, live && cen);
+                if (cb) {
+                    const uint32_t yc = __shfl_sync(kFull, y, __ffs(cb) - 1);
+                    o.label = s.label[(size_t)center_index(s, yc) * s.R + r];
+                    if (lane == 0 && st_counters) atomicAdd(&st_counters->hop2_chunks, (unsigned long long)chunks);
+                    return o;
+                }
+                bool fresh = live;
+                if (live)
+                    for (uint32_t u = 0; u < tail; ++u)
+                        if (q[u] == y) { fresh = false; break; }
+                const unsigned fm = __ballot_sync(kFull, fresh);
+                if (fresh) {   // parallel edges / several frontier vertices reaching y: keep one lane
+                    const unsigned grp = __match_any_sync(fm, y);
+                    if (lane != (unsigned)(__ffs(grp) - 1)) fresh = false;
+                }
+                const unsigned nbm = __ballot_sync(kFull, fresh);
+                const uint32_t cnt = __popc(nbm);
+                if (tail + cnt > kQcap) { o.overflow = 1; return o; }
+                if (fresh) {
+                    q[tail + __popc(nbm & ((1u << lane) - 1u))] = y;
+                    if (want_seed && s.seed_flag[y]) seen = 1;
+                    minv = min(minv, y);
+                }
+                tail += cnt;
+                __syncwarp();
             }
-            bool fresh = live;
-            if (live)
-                for (uint32_t t = 0; t < tail; ++t)
-                    if (q[t] == y) { fresh = false; break; }
-            const unsigned fm = __ballot_sync(kFull, fresh);
-            if (fresh) {   // parallel edges: keep one lane per neighbour
-                const unsigned grp = __match_any_sync(fm, y);
-                if (lane != (unsigned)(__ffs(grp) - 1)) fresh = false;
-            }
-            const unsigned nbm = __ballot_sync(kFull, fresh);
-            const uint32_t cnt = __popc(nbm);
-            if (tail + cnt > kQcap) { o.overflow = 1; return o; }
-            if (fresh) {
-                q[tail + __popc(nbm & ((1u << lane) - 1u))] = y;
-                if (want_seed && s.seed_flag[y]) seen = 1;
-                minv = min(minv, y);
-            }
-            tail += cnt;
-            __syncwarp();
         }
     }
     if (lane == 0 && st_counters) atomicAdd(&st_counters->hop2_chunks, (unsigned long long)chunks);
@@ -161,7 +206,7 @@ __device__ LaneRes get_center_32(const GraphView& g, const SketchView& s, uint32
             const uint32_t khi = __shfl_sync(kFull, arc.w, i);
             if (act) {
                 const uint64_t key = ((uint64_t)khi << 32) | klo;
-                if (s.smp.all_live || mix64(key + rg) < s.smp.T) {
+                if (edge_live_fast(s.smp, key, rg)) {
                     const uint32_t y = yc & kArcIdMask;
                     if (yc >> 31) {
                         o.label = s.label[(size_t)center_index(s, y) * s.R + r];
@@ -598,7 +643,7 @@ k_fallback(GraphView g, SketchView s, SelState* st, const FbTask* __restrict__ f
                     const uint4 arc = g.arcs[a];
                     y = arc.x & kArcIdMask;
                     cen = arc.x >> 31;
-                    live = edge_live(s.smp, ((uint64_t)arc.w << 32) | arc.z, r);
+                    live = edge_live_fast(s.smp, ((uint64_t)arc.w << 32) | arc.z, (uint64_t)(r + 1u) * kGamma);
                 }
                 const unsigned cb = __ballot_sync(kFull, live && cen);
                 if (cb) {

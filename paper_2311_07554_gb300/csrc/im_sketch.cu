@@ -83,19 +83,47 @@ k_sample_emit(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, uin
         const uint64_t i = base + threadIdx.x;
         uint32_t live0 = 0, live1 = 0;
         uint4 two = make_uint4(0, 0, 0, 0);
+        uint64_t k0 = 0, k1 = 0;
         if (i < npairs) {
             two = __ldcs(edge_pairs + i);   // streamed once per batch: keep L2 for the forest
             const uint64_t e0 = 2 * i, e1 = 2 * i + 1;
-            uint64_t x0 = mix64(smp.salt ^ e0) + g0;
-            uint64_t x1 = mix64(smp.salt ^ e1) + g0;
+            k0 = mix64(smp.salt ^ e0);
+            k1 = mix64(smp.salt ^ e1);
+            if (smp.all_live) {
+                live0 = live1 = (nb >= 32) ? 0xFFFFFFFFu : ((1u << nb) - 1u);
+            } else {
+                // candidates by the high word of the hash (a superset of the live pairs);
+                // the few with an equal high word are settled exactly below
+                const uint32_t th = (uint32_t)(smp.T >> 32);
+                uint64_t x0 = k0 + g0, x1 = k1 + g0;
+                if (nb == (uint32_t)B) {
 #pragma unroll
-            for (int b = 0; b < B; ++b) {
-                if (b < (int)nb) {
-                    if (smp.all_live || mix64(x0) < smp.T) live0 |= 1u << b;
-                    if (smp.all_live || mix64(x1) < smp.T) live1 |= 1u << b;
+                    for (int b = 0; b < B; ++b) {
+                        if (mix64_hi(x0) <= th) live0 |= 1u << b;
+                        if (mix64_hi(x1) <= th) live1 |= 1u << b;
+                        x0 += kGamma;
+                        x1 += kGamma;
+                    }
+                } else {
+#pragma unroll
+                    for (int b = 0; b < B; ++b) {
+                        if (b < (int)nb) {
+                            if (mix64_hi(x0) <= th) live0 |= 1u << b;
+                            if (mix64_hi(x1) <= th) live1 |= 1u << b;
+                        }
+                        x0 += kGamma;
+                        x1 += kGamma;
+                    }
                 }
-                x0 += kGamma;
-                x1 += kGamma;
+                // exact test for the candidates (about a fraction p of all pairs)
+                for (uint32_t t = live0; t; t &= t - 1) {
+                    const int b = __ffs(t) - 1;
+                    if (!edge_live(smp, k0, r0 + b)) live0 &= ~(1u << b);
+                }
+                for (uint32_t t = live1; t; t &= t - 1) {
+                    const int b = __ffs(t) - 1;
+                    if (!edge_live(smp, k1, r0 + b)) live1 &= ~(1u << b);
+                }
             }
             if (e1 >= m) live1 = 0;
         }
@@ -169,6 +197,7 @@ k_compress_count(uint32_t* __restrict__ parent, uint64_t* __restrict__ word, uin
     __shared__ uint32_t tkey[kCountSlots];
     __shared__ uint32_t tcnt[kCountSlots];
     __shared__ uint32_t tmin[kCountSlots];
+
     uint32_t* P = parent + (size_t)blockIdx.y * n;
     uint64_t* W = word + (size_t)blockIdx.y * n;
     const unsigned lane = threadIdx.x & 31;
@@ -354,7 +383,7 @@ int launch_sample_split(im_ctx* c, im_ctx::Lane& L, uint32_t r0, uint32_t nb) {
     const unsigned gs = grid_for(npairs, T, 152u * 16u);
     const double pl = c->smp.all_live ? 1.0 : c->p;
     const unsigned gu = grid_for((uint64_t)(pl * (double)c->m * nb) + 1, T, 152u * 16u);
-    IM_LAUNCH(c, K_SAMPLE_EMIT, k_zero_u64, 1, 32, 0, L.live_n);
+    IM_LAUNCH(c, K_ZERO, k_zero_u64, 1, 32, 0, L.live_n);
 #define IM_SE(BB)                                                                                 \
     do {                                                                                          \
         IM_LAUNCH(c, K_SAMPLE_EMIT, k_sample_emit<BB>, gs, T, 0, ep, c->m, c->smp, r0, nb, L.live,   \
