@@ -138,6 +138,7 @@ typedef struct {
     uint64_t hop2_chunks;           /* 32-arc chunks scanned by those searches             */
     uint64_t refresh_batches;       /* batches evaluated by recomputing the sketches        */
     uint64_t live_pairs;            /* live (edge, sketch) pairs unioned since im_create    */
+    uint64_t build_live_pairs;      /* of those, unioned by the last im_build_sketches      */
 } im_stats;
 
 int im_get_stats(im_ctx* ctx, im_stats* out);
@@ -205,6 +206,12 @@ int im_set_refresh_threshold(im_ctx* ctx, uint64_t min_batch);
  * overlaps another's union-find (both lanes' scratch is allocated either way); 1 (default)
  * runs them in order on the context stream. */
 int im_set_pipeline(im_ctx* ctx, uint32_t lanes);
+
+/* Execution of the selection loop (Alg. 2 / Alg. 4 rounds).  1 (default): the whole loop is
+ * one CUDA graph whose while / switch nodes are set by the device, so rounds and batches run
+ * without the host; 0: the host launches every batch after reading the device's decision.
+ * Both run the same kernels and give identical results. */
+int im_set_graph(im_ctx* ctx, int on);
 
 /* The context's stream (a cudaStream_t). */
 void* im_stream(im_ctx* ctx);

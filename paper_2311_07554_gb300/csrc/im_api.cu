@@ -16,10 +16,10 @@ const char* const kNames[K_COUNT] = {
     "pack_edges", "csr_degree", "scan_partial", "scan_top", "scan_apply", "csr_fill",
     "center_hist", "center_pick", "center_flags", "center_index",
     "batch_init", "sample_union", "compress_count", "gain_compact", "init_keys",
-    "reduce_reset", "reduce", "sel_init", "sel_hist", "sel_pick", "gather", "eval",
+    "reduce_reset", "reduce", "plan", "sel_hist", "sel_pick", "gather", "eval",
     "fallback", "finalize", "mark_seed", "spread_tasks", "spread_dedup", "labels_min",
     "labels_out", "arc_keys", "sample_emit", "union", "cover_roots", "refresh_gather",
-    "count_above", "zero"};
+    "count_above", "zero", "select_graph", "sel_begin"};
 
 int bitlen64(uint64_t x) {
     int b = 0;
@@ -50,6 +50,8 @@ void free_sketch_state(im_ctx* c) {
     dfree(c->d_label); dfree(c->d_size); dfree(c->d_gain0);
     dfree(c->d_key); dfree(c->d_stamp); dfree(c->d_seedflag);
     dfree(c->d_batch); dfree(c->d_fresh); dfree(c->d_seed_list); dfree(c->d_labcache);
+    dfree(c->d_gain_list); dfree(c->d_round_evals);
+    im_select_graph_free(c);   // the graph holds pointers to the buffers freed here
     for (auto& L : c->lane) {
         dfree(L.parent); dfree(L.word); dfree(L.live); dfree(L.live_n); dfree(L.gain); dfree(L.fresh);
     }
@@ -100,10 +102,11 @@ int next_event(im_ctx* c) {
 
 const char* imk::kernel_name(int id) { return (id >= 0 && id < K_COUNT) ? kNames[id] : "?"; }
 
-void im_prof_begin(im_ctx* c, int kid, int* ev0) {
-    c->launches++;
-    c->prof_launches[kid]++;
+void im_prof_begin(im_ctx* c, int kid, int* ev0, bool count_launch) {
     *ev0 = -1;
+    if (c->capturing) return;   // a captured launch runs (and is counted) with its graph
+    if (count_launch) c->launches++;
+    c->prof_launches[kid]++;
     if (!c->prof) return;
     int e = next_event(c);
     if (e < 0) return;
@@ -221,6 +224,12 @@ int im_set_sketch_batch(im_ctx* c, uint32_t batch) {
     return IM_OK;
 }
 
+int im_set_graph(im_ctx* c, int on) {
+    if (!c) return IM_EINVAL;
+    c->use_graph = on != 0;
+    return IM_OK;
+}
+
 int im_set_pipeline(im_ctx* c, uint32_t lanes) {
     if (!c) return IM_EINVAL;
     if (lanes != 1 && lanes != 2) return im_fail(c, IM_EINVAL, "lanes must be 1 or 2");
@@ -278,6 +287,7 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
     bool ok = dalloc(c->d_gain0, n) && dalloc(c->d_key, n) && dalloc(c->d_stamp, n) &&
               dalloc(c->d_seedflag, n) && dalloc(c->d_batch, n) && dalloc(c->d_fresh, n) &&
               dalloc(c->d_seed_list, n) && dalloc(c->d_labcache, (size_t)kLabSlots * R) &&
+              dalloc(c->d_gain_list, n) && dalloc(c->d_round_evals, n) &&
               dalloc(c->d_label, nc) && dalloc(c->d_size, nc) &&
               dalloc(c->lane[0].parent, (size_t)B * n) && dalloc(c->lane[0].word, (size_t)B * n) &&
               dalloc(c->lane[1].parent, (size_t)B * n) && dalloc(c->lane[1].word, (size_t)B * n) &&
@@ -323,13 +333,23 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
         dfree(pos);
         if (rc) { free_sketch_state(c); return rc; }
     }
-    rc = im_arc_keys(c, smp.salt);
+    unsigned long long live0 = 0, live1 = 0;
+    {
+        cudaError_t e = cudaMemcpyAsync(&live0, c->d_live_total, sizeof live0, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) rc = im_cuda_check(c, e, "live pair counter");
+    }
+    if (!rc) rc = im_arc_keys(c, smp.salt);
     if (!rc) rc = im_sketch_batches(c);
     if (!rc) rc = im_selection_init(c);
     if (!rc) {
         cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&live1, c->d_live_total, sizeof live1, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) rc = im_cuda_check(c, e, "sketch construction");
     }
+    c->build_live_pairs = live1 - live0;
     if (rc) { free_sketch_state(c); return rc; }
     c->built = true;
     return IM_OK;
@@ -340,11 +360,10 @@ int im_select_seeds(im_ctx* c, uint32_t k, uint32_t* seeds_out, uint64_t* gains_
     if (!c->built) return im_fail(c, IM_ESTATE, "im_build_sketches has not run");
     if (k == 0 || k > c->n) return im_fail(c, IM_EINVAL, "k must be in [1, n]");
     if (!seeds_out) return im_fail(c, IM_EINVAL, "seeds_out is NULL");
-    while (c->seeds.size() < k) {
-        int rc = im_select_round(c);
+    if (c->seeds.size() < k) {
+        const int rc = im_select_run(c, k);
         if (rc) return rc;
     }
-    IM_CUDA(c, cudaStreamSynchronize(c->stream));
     memcpy(seeds_out, c->seeds.data(), k * sizeof(uint32_t));
     if (gains_out) memcpy(gains_out, c->seed_gains.data(), k * sizeof(uint64_t));
     return IM_OK;
@@ -463,7 +482,7 @@ int im_get_stats(im_ctx* c, im_stats* out) {
     out->n = c->n; out->m = c->m; out->R = c->R; out->rho = c->rho;
     out->rounds = (uint32_t)c->seeds.size();
     out->launches = c->launches;
-    out->batches = c->batches;
+
     out->sketch_batch = c->batch_used;
     uint64_t ev = 0;
     for (auto x : c->round_evals) ev += x;
@@ -475,10 +494,12 @@ int im_get_stats(im_ctx* c, im_stats* out) {
         out->hop1_arcs = c->h_sel->hop1_arcs;
         out->hop2_searches = c->h_sel->hop2_calls;
         out->hop2_chunks = c->h_sel->hop2_chunks;
-        out->refresh_batches = c->refresh_batches;
+        out->refresh_batches = c->h_sel->refresh_batches;
+        out->batches = c->h_sel->batches;
         unsigned long long lt = 0;
         cudaMemcpy(&lt, c->d_live_total, sizeof lt, cudaMemcpyDeviceToHost);
         out->live_pairs = lt;
+        out->build_live_pairs = c->build_live_pairs;
     }
     return IM_OK;
 }
@@ -531,6 +552,7 @@ void im_destroy(im_ctx* c) {
     if (c->d_tmp) cudaFree(c->d_tmp);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     if (c->lane_stream1) { cudaStreamSynchronize(c->lane_stream1); cudaStreamDestroy(c->lane_stream1); }
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

@@ -116,8 +116,43 @@ struct SelState {
     unsigned long long hop1_arcs;       // arcs scanned by the first hop (per 32 sketches)
     unsigned long long hop2_calls;      // (vertex, sketch) searches needing more than one hop
     unsigned long long hop2_chunks;     // 32-arc chunks scanned by those searches
-    unsigned int err;
+    unsigned int err;               // SelError: the selection stopped (the host reports it)
     unsigned int pad;
+    // round and batch control, decided on the device (k_plan / k_mark_seed)
+    unsigned int round;             // seeds chosen so far
+    unsigned int round_end;         // stop after this many seeds
+    unsigned int j;                 // batches evaluated in the current round
+    unsigned int cont;              // the current round needs another batch
+    unsigned int mode;              // SelMode of that batch
+    unsigned int sd;                // the round's winner (valid once cont == 0)
+    unsigned long long refresh_min; // batches at least this large are evaluated by refresh
+    unsigned long long evals_mark;  // evals_total when the round started
+    unsigned long long batches, refresh_batches;
+    unsigned long long launches;    // kernels launched by the selection graph
+};
+
+enum SelError : unsigned int {
+    SEL_OK = 0, SEL_FB_OVERFLOW = 1, SEL_NO_PROGRESS = 2, SEL_NO_CANDIDATE = 3, SEL_RANGE = 4
+};
+
+// Launch sequences of one re-evaluation batch (the switch of the selection graph).
+enum SelMode : unsigned int {
+    M_DIRECT = 0,         // B = 1: the top stale key is the batch; one warp per search
+    M_GATHER_SINGLE = 1,  // threshold known: gather, one warp per search
+    M_HIST_SINGLE = 2,    // radix passes, gather, one warp per search
+    M_GATHER_CHUNK = 3,   // gather, one warp per (member, 32 sketches)
+    M_HIST_CHUNK = 4,     // radix passes, gather, one warp per (member, 32 sketches)
+    M_REFRESH = 5,        // gather, recompute the sketches
+    M_COUNT = 6,
+    M_NONE = 7            // no batch: the round is over
+};
+
+// Conditional-node handles of the selection graph; on == 0 outside the graph.
+struct SelHandles {
+    cudaGraphConditionalHandle round, batch, mode;
+    unsigned int on;
+    unsigned int launches[M_COUNT];   // kernels each batch mode launches
+    unsigned int round_launches;      // kernels of a round outside its batches
 };
 
 struct FbTask {
@@ -132,7 +167,7 @@ enum KernelId {
     K_REDUCE_RESET, K_REDUCE, K_SEL_INIT, K_SEL_HIST, K_SEL_PICK, K_GATHER, K_EVAL,
     K_FALLBACK, K_FINALIZE, K_MARK_SEED, K_SPREAD_TASKS, K_SPREAD_DEDUP, K_LABELS_MIN,
     K_LABELS_OUT, K_ARC_KEYS, K_SAMPLE_EMIT, K_UNION, K_COVER_ROOTS, K_REFRESH_GATHER, K_COUNT_ABOVE,
-    K_ZERO, K_COUNT
+    K_ZERO, K_SELECT_GRAPH, K_SEL_BEGIN, K_COUNT
 };
 
 const char* kernel_name(int id);
@@ -183,11 +218,21 @@ struct im_ctx {
     uint64_t* d_labcache = nullptr;    // [kLabSlots][R]: (vertex << 32) | label found by GetCenter
     uint64_t refresh_min = 0;          // batches at least this large are evaluated by refresh
     uint64_t refresh_req = 0;          // user setting (0 = automatic)
-    uint64_t refresh_batches = 0;
     std::vector<uint32_t> seeds;
     std::vector<uint64_t> seed_gains;
     std::vector<uint64_t> round_evals;
-    uint64_t batches = 0;
+    uint64_t* d_gain_list = nullptr;   // gain of each chosen seed (n entries)
+    uint64_t* d_round_evals = nullptr; // re-evaluations of each round (n entries)
+    // the selection loop as one CUDA graph (conditional nodes set by the device)
+    bool use_graph = true;
+    cudaStream_t cap_stream = nullptr;   // owned; only used to capture
+    cudaGraph_t sel_graph = nullptr;
+    cudaGraphExec_t sel_exec = nullptr;
+    bool capturing = false;              // launches go into a graph: no events, no counting
+    bool count_only = false;             // launches are only counted (dry run)
+    uint64_t dry_count = 0;
+    unsigned long long dev_launches_seen = 0;  // SelState::launches already added to launches
+    unsigned long long build_live_pairs = 0;   // live pairs unioned by the last build
 
     // sketch-batch scratch: two lanes, each with its own stream, so that consecutive batches
     // overlap (one batch's hashing with the other's union-find)
@@ -236,11 +281,12 @@ struct im_ctx {
 };
 
 // launch accounting (defined in im_api.cu)
-void im_prof_begin(im_ctx* c, int kid, int* ev0);
+void im_prof_begin(im_ctx* c, int kid, int* ev0, bool count_launch = true);
 void im_prof_end(im_ctx* c, int kid, int ev0);
 
 #define IM_LAUNCH(ctx, kid, kern, grid, block, smem, ...)                               \
     do {                                                                                \
+        if ((ctx)->count_only) { (ctx)->dry_count++; break; }                           \
         int _ev0 = -1;                                                                  \
         im_prof_begin((ctx), (kid), &_ev0);                                             \
         kern<<<(grid), (block), (smem), (ctx)->cur>>>(__VA_ARGS__);                     \
@@ -257,11 +303,11 @@ int im_select_centers(im_ctx* c, uint32_t* d_flags_tmp, uint64_t* d_scan_tmp);
 int im_sketch_batches(im_ctx* c);
 int im_labels_min(im_ctx* c, uint32_t r, uint32_t* d_out);
 int im_refresh_eval(im_ctx* c, const uint32_t* d_batch, const unsigned int* d_batch_n,
-                    unsigned long long* d_fresh, const uint32_t* d_seeds, uint32_t nseeds,
-                    uint64_t batch_hint);
+                    unsigned long long* d_fresh, const uint32_t* d_seeds, const unsigned int* d_nseeds);
 // im_select.cu
 int im_selection_init(im_ctx* c);
-int im_select_round(im_ctx* c);
+int im_select_run(im_ctx* c, uint32_t k);   // rounds until k seeds are chosen
+void im_select_graph_free(im_ctx* c);
 int im_spread_run(im_ctx* c, uint32_t k, uint64_t* out);
 
 int im_fail(im_ctx* c, int code, const std::string& msg);

@@ -8,6 +8,8 @@
 // with the largest stale keys is re-evaluated; the round ends when the best fresh key beats
 // every stale key not yet re-evaluated (Alg. 2's stop test on keys; Alg. 4's loop).  Stale
 // keys are upper bounds by submodularity (Eq. 2), so the winner equals plain greedy's.
+#include <cstring>
+
 #include "im_internal.cuh"
 
 using namespace imk;
@@ -274,14 +276,15 @@ __global__ void k_init_keys(const uint64_t* __restrict__ gain0, uint32_t n, uint
         size[i] &= ~kCovered;
 }
 
-__global__ void k_reduce_reset(SelState* st) {
-    if (threadIdx.x == 0) { st->best = 0; st->stale_max = 0; st->n_unev = 0; st->count_above = 0; }
-}
-
-// best = max fresh key (evaluated this round), stale_max / n_unev over the others.
+// best = max fresh key (evaluated this round), stale_max / n_unev over the others.  At the
+// start of a round (open_batches) it also opens the graph's batch loop, whose first pass
+// decides whether the round needs any batch.
 __global__ void __launch_bounds__(256)
 k_reduce(const uint64_t* __restrict__ key, const uint32_t* __restrict__ stamp,
-         const uint8_t* __restrict__ seedflag, uint32_t n, uint32_t round, SelState* st) {
+         const uint8_t* __restrict__ seedflag, uint32_t n, SelState* st, SelHandles hd,
+         int open_batches) {
+    if (open_batches && hd.on && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(hd.batch, 1u);
+    const uint32_t round = st->round;
     unsigned long long bf = 0, sm = 0, cnt = 0;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         if (seedflag[v]) continue;
@@ -313,8 +316,11 @@ k_reduce(const uint64_t* __restrict__ key, const uint32_t* __restrict__ stamp,
 // bound on what is left to evaluate in this round (the winner's fresh key is >= best).
 __global__ void __launch_bounds__(256)
 k_count_above(const uint64_t* __restrict__ key, const uint32_t* __restrict__ stamp,
-              const uint8_t* __restrict__ seedflag, uint32_t n, uint32_t round, SelState* st) {
+              const uint8_t* __restrict__ seedflag, uint32_t n, SelState* st) {
     const unsigned long long best = st->best;
+    // only needed when the round goes on (the next batch's size depends on it)
+    if (!(st->n_unev > 0 && best <= st->stale_max)) return;
+    const uint32_t round = st->round;
     unsigned long long cnt = 0;
     if (best)
         for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
@@ -330,41 +336,110 @@ k_count_above(const uint64_t* __restrict__ key, const uint32_t* __restrict__ sta
     }
 }
 
-// Start of a batch: decide how to pick ~B of the largest stale keys (radix select on the
-// key bytes below the top byte of stale_max); take all when at most 2B remain.
-__global__ void k_sel_init(SelState* st, unsigned long long B) {
+// Next step of the round, decided from the state the last reduction left (Alg. 2's stop
+// test; Alg. 4's doubling batch size): either a batch of ~B of the largest stale keys, picked
+// by radix selection on the key bytes below the top byte of stale_max (all of them when at
+// most 2B remain, exactly the top key when B = 1), or the end of the round, whose winner
+// (the best fresh key) is recorded.  Large batches are evaluated by recomputing the sketches
+// (M_REFRESH) instead of by searches.  Errors stop the selection.  One thread decides; the
+// block clears the radix histogram.
+__global__ void __launch_bounds__(256)
+k_plan(SelState* st, uint32_t* __restrict__ batch, unsigned long long* __restrict__ fresh,
+       uint32_t* __restrict__ seed_list, uint64_t* __restrict__ gain_list,
+       uint64_t* __restrict__ round_evals, uint32_t n, uint32_t R, uint32_t bits, SelHandles hd) {
     if (threadIdx.x == 0) {
-        const unsigned long long nu = st->n_unev, smax = st->stale_max;
-        st->borig = B;
-        st->need = B;
-        st->taken = 0;
-        st->prefix = 0;
-        st->theta = 0;
-        st->pass_blocks = 0;
-        if (nu <= 2 * B || smax == 0) {
-            st->done = 1;                // take every unevaluated candidate
-            st->shift = 0;
-            st->prefmask = 0;
-        } else if (B == 1) {
-            st->done = 1;                // keys are distinct: exactly the top stale key
-            st->theta = smax;
-            st->shift = 0;
-            st->prefmask = 0;
-        } else {
-            const int top = 63 - __clzll((long long)smax);
-            const int shift = (top / 8) * 8;
-            st->shift = shift;
-            st->prefmask = (shift + 8 >= 64) ? 0ull : ~((1ull << (shift + 8)) - 1ull);
-            st->done = 0;
+        unsigned cont = 0, mode = M_NONE;
+        const unsigned long long nu = st->n_unev, smax = st->stale_max, best = st->best;
+        const unsigned j = st->j;
+        const uint64_t mask = (1ull << bits) - 1ull;
+        if (!st->err && st->fb_overflow) st->err = SEL_FB_OVERFLOW;
+        if (!st->err && j > 0 && st->batch_n == 0) st->err = SEL_NO_PROGRESS;
+        if (!st->err && nu > 0 && best <= smax) {
+            if (j > 81) st->err = SEL_NO_PROGRESS;   // doubling covers any n within 64 batches
+            else cont = 1;
         }
-        st->batch_n = 0;
-        st->eval_next = 0;
-        st->fb_n = 0;
-        st->best_prev = st->best;
-        st->best = 0;
-        st->stale_max = 0;
-        st->n_unev = 0;
-        st->count_above = 0;
+        if (cont) {
+            unsigned long long B = 1ull << (j < 40 ? j : 40);
+            if (B > nu) B = nu;
+            unsigned long long expect = 2 * B < nu ? 2 * B : nu;
+            // When many candidates could still beat the best fresh key (or the doubling batch
+            // has grown large), evaluate every one of them at once by recomputing the
+            // sketches; the round then ends, since all remaining stale keys are below the new best.
+            const unsigned long long rmin = st->refresh_min;
+            const bool refresh = expect >= rmin || (best && st->count_above >= rmin);
+            if (refresh) {
+                B = nu;
+                expect = best ? st->count_above : nu;
+            }
+            st->borig = B;
+            st->need = B;
+            st->taken = 0;
+            st->prefix = 0;
+            st->theta = 0;
+            st->pass_blocks = 0;
+            bool hist = false, direct = false;
+            if (nu <= 2 * B || smax == 0) {
+                st->done = 1;                // take every unevaluated candidate
+                st->shift = 0;
+                st->prefmask = 0;
+            } else if (B == 1) {
+                st->done = 1;                // keys are distinct: exactly the top stale key
+                st->theta = smax;
+                st->shift = 0;
+                st->prefmask = 0;
+                direct = best < smax;        // no gather needed: the key names the vertex
+            } else {
+                const int top = 63 - __clzll((long long)smax);
+                const int shift = (top / 8) * 8;
+                st->shift = shift;
+                st->prefmask = (shift + 8 >= 64) ? 0ull : ~((1ull << (shift + 8)) - 1ull);
+                st->done = 0;
+                hist = true;
+            }
+            st->batch_n = 0;
+            st->eval_next = 0;
+            st->fb_n = 0;
+            st->best_prev = best;
+            st->best = 0;
+            st->stale_max = 0;
+            st->n_unev = 0;
+            st->count_above = 0;
+            if (direct) {
+                batch[0] = (uint32_t)(mask - (smax & mask));
+                fresh[0] = 0;
+                st->batch_n = 1;
+            }
+            const bool single = expect * R <= kSingleTasks;
+            mode = refresh ? M_REFRESH
+                 : direct  ? M_DIRECT
+                 : single  ? (hist ? M_HIST_SINGLE : M_GATHER_SINGLE)
+                           : (hist ? M_HIST_CHUNK : M_GATHER_CHUNK);
+            st->j = j + 1;
+            st->batches++;
+            if (refresh) st->refresh_batches++;
+            st->launches += hd.launches[mode];
+        } else if (!st->err) {
+            // the round is over: the best fresh key beats every stale one
+            const uint32_t sd = (uint32_t)(mask - (best & mask));
+            if (best == 0) {
+                st->err = SEL_NO_CANDIDATE;
+            } else if (sd >= n) {
+                st->err = SEL_RANGE;
+            } else {
+                const uint32_t rd = st->round;
+                st->sd = sd;
+                seed_list[rd] = sd;
+                gain_list[rd] = best >> bits;
+                round_evals[rd] = st->evals_total - st->evals_mark;
+            }
+        }
+        st->cont = cont;
+        st->mode = mode;
+        st->launches += 1;
+        if (hd.on) {
+            cudaGraphSetConditional(hd.batch, cont);
+            cudaGraphSetConditional(hd.mode, mode);
+        }
     }
     for (int i = threadIdx.x; i < 256; i += blockDim.x) st->hist[i] = 0;
 }
@@ -375,8 +450,9 @@ __global__ void k_sel_init(SelState* st, unsigned long long B) {
 // narrows the prefix for the next pass.
 __global__ void __launch_bounds__(256)
 k_sel_pass(const uint64_t* __restrict__ key, const uint32_t* __restrict__ stamp,
-           const uint8_t* __restrict__ seedflag, uint32_t n, uint32_t round, SelState* st) {
+           const uint8_t* __restrict__ seedflag, uint32_t n, SelState* st) {
     if (st->done) return;
+    const uint32_t round = st->round;
     __shared__ unsigned int h[256];
     __shared__ unsigned long long sfx[256];
     __shared__ int s_last;
@@ -437,8 +513,9 @@ k_sel_pass(const uint64_t* __restrict__ key, const uint32_t* __restrict__ stamp,
 
 __global__ void __launch_bounds__(256)
 k_gather(const uint64_t* __restrict__ key, const uint32_t* __restrict__ stamp,
-         const uint8_t* __restrict__ seedflag, uint32_t n, uint32_t round, SelState* st,
+         const uint8_t* __restrict__ seedflag, uint32_t n, SelState* st,
          uint32_t* __restrict__ batch, unsigned long long* __restrict__ fresh) {
+    const uint32_t round = st->round;
     // a candidate whose stale key is below the best fresh key cannot win (keys are distinct)
     const unsigned long long bp = st->best_prev;
     const unsigned long long theta = max(st->theta, bp ? bp + 1 : 0ull);
@@ -547,8 +624,8 @@ k_eval_single(GraphView g, SketchView s, SelState* st, const uint32_t* __restric
 __global__ void __launch_bounds__(256)
 k_finalize(SelState* st, const uint32_t* __restrict__ batch,
            const unsigned long long* __restrict__ fresh, uint64_t* __restrict__ key,
-           uint32_t* __restrict__ stamp, uint32_t bits, uint32_t round) {
-    const uint32_t bn = st->batch_n;
+           uint32_t* __restrict__ stamp, uint32_t bits) {
+    const uint32_t bn = st->batch_n, round = st->round;
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < bn; j += gridDim.x * blockDim.x) {
         const uint32_t x = batch[j];
         key[x] = pack_key(fresh[j], x, bits);
@@ -564,10 +641,14 @@ k_finalize(SelState* st, const uint32_t* __restrict__ batch,
 // MarkSeed (Alg. 3): in every sketch, flag the component of s as covered.  One warp per
 // sketch: a single vertex is marked per round, so latency, not total work, decides.
 __global__ void __launch_bounds__(kEvalWarps * 32)
-k_mark_seed(GraphView g, SketchView s, SelState* st, uint32_t sd, FbTask* __restrict__ fbt,
-            uint32_t fb_cap, uint8_t* __restrict__ seedflag, uint64_t* __restrict__ key,
-            uint32_t* __restrict__ seed_list, uint32_t round) {
+k_mark_seed(GraphView g, SketchView s, SelState* st, FbTask* __restrict__ fbt, uint32_t fb_cap,
+            uint8_t* __restrict__ seedflag, uint64_t* __restrict__ key, SelHandles hd) {
     __shared__ uint32_t qws[kEvalWarps][kQcap];
+    if (st->err) {   // the round chose no seed: the selection stops
+        if (hd.on && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(hd.round, 0u);
+        return;
+    }
+    const uint32_t sd = st->sd;
     uint32_t* qw = qws[threadIdx.x >> 5];
     const unsigned lane = threadIdx.x & 31;
     const uint32_t r = blockIdx.x * kEvalWarps + (threadIdx.x >> 5);
@@ -595,12 +676,33 @@ k_mark_seed(GraphView g, SketchView s, SelState* st, uint32_t sd, FbTask* __rest
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         seedflag[sd] = 1;
         key[sd] = 0;
-        seed_list[round] = sd;
         // the next round's first reduction starts from zero
         st->best = 0;
         st->stale_max = 0;
         st->n_unev = 0;
         st->count_above = 0;
+        st->j = 0;
+        st->evals_mark = st->evals_total;
+        const unsigned rd = st->round + 1;
+        st->round = rd;
+        st->launches += hd.round_launches;
+        if (hd.on) cudaGraphSetConditional(hd.round, rd < st->round_end ? 1u : 0u);
+    }
+}
+
+// Before a selection run: the number of seeds to reach and the refresh threshold.
+__global__ void k_set_target(SelState* st, uint32_t round_end, unsigned long long refresh_min) {
+    if (threadIdx.x == 0) {
+        st->round_end = round_end;
+        st->refresh_min = refresh_min;
+    }
+}
+
+// First node of the selection graph: enter the round loop if seeds are still missing.
+__global__ void k_sel_begin(SelState* st, SelHandles hd) {
+    if (threadIdx.x == 0) {
+        st->launches += 1;
+        if (hd.on) cudaGraphSetConditional(hd.round, (!st->err && st->round < st->round_end) ? 1u : 0u);
     }
 }
 
@@ -777,6 +879,13 @@ SketchView sketch_view(const im_ctx* c) {
     return s;
 }
 
+// copy the device state to the pinned mirror and wait
+int pull_state(im_ctx* c) {
+    IM_CUDA(c, cudaMemcpyAsync(c->h_sel, c->d_sel, sizeof(SelState), cudaMemcpyDeviceToHost, c->stream));
+    IM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return IM_OK;
+}
+
 int sync_state(im_ctx* c) {
     IM_CUDA(c, cudaMemcpyAsync(c->h_sel, c->d_sel, sizeof(SelState), cudaMemcpyDeviceToHost, c->stream));
     IM_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -809,105 +918,285 @@ int im_selection_init(im_ctx* c) {
     c->seeds.clear();
     c->seed_gains.clear();
     c->round_evals.clear();
-    c->batches = 0;
-    c->refresh_batches = 0;
+    c->dev_launches_seen = 0;
     return IM_OK;
 }
 
-// One round of lazy greedy: NextSeed + MarkSeed.
-int im_select_round(im_ctx* c) {
+namespace {
+
+// Radix passes a batch can need: one per key byte from the top byte of the largest key
+// (gains are at most R n, so keys stay below 2^(b + bitlen(R n))).
+int max_radix_passes(const im_ctx* c) {
+    uint64_t top = (uint64_t)c->R * c->n;
+    int bl = 0;
+    while (top) { ++bl; top >>= 1; }
+    const int key_top = (int)c->key_bits + bl - 1;
+    return (key_top > 63 ? 63 : key_top) / 8 + 1;
+}
+
+// The launches of one batch of the given mode (the body of the graph's switch); passes =
+// radix passes to queue (each returns at once once the threshold is fixed).
+int enqueue_mode(im_ctx* c, unsigned mode, int passes) {
     const uint32_t n = c->n;
-    const uint32_t round = (uint32_t)c->seeds.size();
     const unsigned T = 256;
     const unsigned gridn = grid_for(n, T, 152u * 8u);
     const GraphView g = graph_view(c);
     const SketchView s = sketch_view(c);
-    const uint32_t nchunk = (c->R + 31) / 32;
     SelState* st = c->d_sel;
+    unsigned long long* fresh = (unsigned long long*)c->d_fresh;
+    if (mode == M_HIST_SINGLE || mode == M_HIST_CHUNK)
+        for (int p = 0; p < passes; ++p)
+            IM_LAUNCH(c, K_SEL_HIST, k_sel_pass, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n, st);
+    if (mode != M_DIRECT)
+        IM_LAUNCH(c, K_GATHER, k_gather, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n, st, c->d_batch,
+                  fresh);
+    unsigned fin_grid = grid_for(n, T, 152u * 4u);
+    switch (mode) {
+    case M_DIRECT:
+        IM_LAUNCH(c, K_EVAL, k_eval_single, search_grid(c->R), kEvalWarps * 32, 0, g, s, st, c->d_batch, fresh,
+                  c->d_fb_tasks, c->fb_cap);
+        launch_fallback(c, g, s);
+        fin_grid = 1;
+        break;
+    case M_GATHER_SINGLE:
+    case M_HIST_SINGLE:
+        IM_LAUNCH(c, K_EVAL, k_eval_single, search_grid(kSingleTasks), kEvalWarps * 32, 0, g, s, st, c->d_batch,
+                  fresh, c->d_fb_tasks, c->fb_cap);
+        launch_fallback(c, g, s);
+        fin_grid = grid_for(kSingleTasks, T);
+        break;
+    case M_GATHER_CHUNK:
+    case M_HIST_CHUNK: {
+        const uint32_t nchunk = (c->R + 31) / 32;
+        IM_LAUNCH(c, K_EVAL, k_eval, search_grid((uint64_t)n * nchunk), kEvalWarps * 32, 0, g, s, st, c->d_batch,
+                  fresh, c->d_fb_tasks, c->fb_cap, nchunk);
+        launch_fallback(c, g, s);
+        break;
+    }
+    case M_REFRESH: {
+        const int rc = im_refresh_eval(c, c->d_batch, &st->batch_n, fresh, c->d_seed_list, &st->round);
+        if (rc) return rc;
+        break;
+    }
+    default:
+        return im_fail(c, IM_EDEVICE, "unknown batch mode");
+    }
+    IM_LAUNCH(c, K_FINALIZE, k_finalize, fin_grid, T, 0, st, c->d_batch, (const unsigned long long*)fresh,
+              c->d_key, c->d_stamp, c->key_bits);
+    IM_LAUNCH(c, K_REDUCE, k_reduce, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n, st, SelHandles{}, 0);
+    IM_LAUNCH(c, K_COUNT_ABOVE, k_count_above, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n, st);
+    return IM_OK;
+}
 
-    // Round start: recount over the new round's stamps.  After round 0 no key is fresh and at
-    // least one candidate is left, so the first batch (B = 1: the top stale key, chosen on the
-    // device) is queued without waiting for the host to see the counts.
-    if (round == 0) IM_LAUNCH(c, K_REDUCE_RESET, k_reduce_reset, 1, 32, 0, st);
-    IM_LAUNCH(c, K_REDUCE, k_reduce, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n, round, st);
-    int rc = IM_OK;
-    if (round == 0) {
-        rc = sync_state(c);
-        if (rc) return rc;
-    } else {
-        c->h_sel->n_unev = n - round;   // what the host may assume before the first sync
-        c->h_sel->best = 0;
-        c->h_sel->stale_max = ~0ull;
-        c->h_sel->count_above = 0;
-    }
-    uint64_t evals = 0;
-    for (int j = 0;; ++j) {
-        const SelState& h = *c->h_sel;
-        if (h.n_unev == 0 || h.best > h.stale_max) break;
-        unsigned long long B = 1ull << (j < 40 ? j : 40);
-        if (B > h.n_unev) B = h.n_unev;
-        uint64_t expect = (2 * B < h.n_unev ? 2 * B : h.n_unev);
-        // When many candidates could still beat the best fresh key (or the doubling batch has
-        // grown large), evaluate every one of them at once by recomputing the sketches; the
-        // round then ends, since all remaining stale keys are below the new best.
-        const bool refresh = expect >= c->refresh_min || (h.best && h.count_above >= c->refresh_min);
-        if (refresh) {
-            B = h.n_unev;
-            expect = h.best ? h.count_above : h.n_unev;
-        }
-        IM_LAUNCH(c, K_SEL_INIT, k_sel_init, 1, 256, 0, st, B);
-        if (h.n_unev > 2 * B && B > 1) {
-            const int top = 63 - __builtin_clzll(h.stale_max);
-            for (int pass = 0; pass <= top / 8; ++pass)
-                IM_LAUNCH(c, K_SEL_HIST, k_sel_pass, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n,
-                          round, st);
-        }
-        IM_LAUNCH(c, K_GATHER, k_gather, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n, round, st,
-                  c->d_batch, (unsigned long long*)c->d_fresh);
-        if (refresh) {
-            rc = im_refresh_eval(c, c->d_batch, &st->batch_n, (unsigned long long*)c->d_fresh,
-                                 c->d_seed_list, round, expect);
-            if (rc) return rc;
-            c->refresh_batches++;
-        } else {
-            if (expect * c->R <= kSingleTasks)
-                IM_LAUNCH(c, K_EVAL, k_eval_single, search_grid(expect * c->R), kEvalWarps * 32, 0, g, s, st,
-                          c->d_batch, (unsigned long long*)c->d_fresh, c->d_fb_tasks, c->fb_cap);
-            else
-                IM_LAUNCH(c, K_EVAL, k_eval, search_grid(expect * nchunk), kEvalWarps * 32, 0, g, s, st,
-                          c->d_batch, (unsigned long long*)c->d_fresh, c->d_fb_tasks, c->fb_cap, nchunk);
-            launch_fallback(c, g, s);
-        }
-        IM_LAUNCH(c, K_FINALIZE, k_finalize, grid_for(expect, T, 152u * 8u), T, 0, st, c->d_batch,
-                  (const unsigned long long*)c->d_fresh, c->d_key, c->d_stamp, c->key_bits, round);
-        IM_LAUNCH(c, K_REDUCE, k_reduce, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n, round, st);
-        rc = sync_state(c);
-        if (rc) return rc;
-        if (c->h_sel->batch_n == 0 || j > 80)
-            return im_fail(c, IM_EDEVICE, "re-evaluation batch made no progress");
-        evals += c->h_sel->batch_n;
-        c->batches++;
-        if (c->h_sel->n_unev > 0 && c->h_sel->best <= c->h_sel->stale_max) {
-            // the round goes on: how many candidates could still beat the best fresh key?
-            IM_LAUNCH(c, K_COUNT_ABOVE, k_count_above, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag,
-                      n, round, st);
-            rc = sync_state(c);
-            if (rc) return rc;
-        }
-    }
-    const unsigned long long best = c->h_sel->best;
-    if (best == 0) return im_fail(c, IM_EDEVICE, "no candidate left for the next seed");
-    const uint64_t mask = (1ull << c->key_bits) - 1ull;
-    const uint32_t sd = (uint32_t)(mask - (best & mask));
-    const uint64_t gain = best >> c->key_bits;
-    if (sd >= n) return im_fail(c, IM_EDEVICE, "selected id out of range");
-    IM_LAUNCH(c, K_MARK_SEED, k_mark_seed, (c->R + kEvalWarps - 1) / kEvalWarps, kEvalWarps * 32, 0,
-              g, s, st, sd, c->d_fb_tasks, c->fb_cap, c->d_seedflag, c->d_key, c->d_seed_list, round);
+int launch_plan(im_ctx* c, const SelHandles& hd) {
+    IM_LAUNCH(c, K_SEL_INIT, k_plan, 1, 256, 0, c->d_sel, c->d_batch, (unsigned long long*)c->d_fresh,
+              c->d_seed_list, c->d_gain_list, c->d_round_evals, c->n, c->R, c->key_bits, hd);
+    return IM_OK;
+}
+
+int launch_round_start(im_ctx* c, const SelHandles& hd) {
+    IM_LAUNCH(c, K_REDUCE, k_reduce, grid_for(c->n, 256, 152u * 8u), 256, 0, c->d_key, c->d_stamp,
+              c->d_seedflag, c->n, c->d_sel, hd, 1);
+    return IM_OK;
+}
+
+int launch_mark(im_ctx* c, const SelHandles& hd) {
+    const GraphView g = graph_view(c);
+    const SketchView s = sketch_view(c);
+    IM_LAUNCH(c, K_MARK_SEED, k_mark_seed, (c->R + kEvalWarps - 1) / kEvalWarps, kEvalWarps * 32, 0, g, s,
+              c->d_sel, c->d_fb_tasks, c->fb_cap, c->d_seedflag, c->d_key, hd);
     launch_fallback(c, g, s);
-    IM_CUDA(c, cudaGetLastError());
-    c->seeds.push_back(sd);
-    c->seed_gains.push_back(gain);
-    c->round_evals.push_back(evals);
+    return IM_OK;
+}
+
+int cap_begin(im_ctx* c, cudaGraph_t graph) {
+    IM_CUDA(c, cudaStreamBeginCaptureToGraph(c->cap_stream, graph, nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeRelaxed));
+    c->cur = c->cap_stream;
+    c->capturing = true;
+    return IM_OK;
+}
+
+int cap_end(im_ctx* c) {
+    cudaGraph_t out = nullptr;
+    c->capturing = false;
+    c->cur = c->stream;
+    IM_CUDA(c, cudaStreamEndCapture(c->cap_stream, &out));
+    return IM_OK;
+}
+
+// Append a conditional node after the captured work and continue the capture after it.
+int cap_conditional(im_ctx* c, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                    unsigned size, cudaGraph_t* bodies) {
+    cudaStreamCaptureStatus status;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edata = nullptr;
+    size_t ndeps = 0;
+    IM_CUDA(c, cudaStreamGetCaptureInfo(c->cap_stream, &status, nullptr, &cg, &deps, &edata, &ndeps));
+    if (status != cudaStreamCaptureStatusActive) return im_fail(c, IM_ECUDA, "selection graph capture");
+    cudaGraphNodeParams prm = {cudaGraphNodeTypeConditional};
+    memset(&prm, 0, sizeof prm);   // reserved fields and padding must be zero
+    prm.type = cudaGraphNodeTypeConditional;
+    prm.conditional.handle = h;
+    prm.conditional.type = type;
+    prm.conditional.size = size;
+    cudaGraphNode_t node = nullptr;
+    IM_CUDA(c, cudaGraphAddNode(&node, cg, deps, edata, ndeps, &prm));
+    for (unsigned i = 0; i < size; ++i) bodies[i] = prm.conditional.phGraph_out[i];
+    IM_CUDA(c, cudaStreamUpdateCaptureDependencies(c->cap_stream, &node, nullptr, 1,
+                                                   cudaStreamSetCaptureDependencies));
+    return IM_OK;
+}
+
+// The whole lazy-greedy loop as one graph, so that rounds run back to back without the host:
+//   sel_begin; while (round) { reduce; while (batch) { plan; switch (mode) { batch kinds } };
+//                              mark_seed; fallback }
+// Every decision is taken by k_plan / k_mark_seed on the device.  Both loops are bounded:
+// a round ends after at most 82 batches (k_plan), the selection after round_end rounds.
+int build_select_graph_steps(im_ctx* c) {
+    SelHandles hd{};
+    hd.on = 1;
+    const int passes = max_radix_passes(c);
+    // launches per batch mode and per round, counted by dry runs of the same code
+    c->count_only = true;
+    int rc = IM_OK;
+    for (unsigned m = 0; m < M_COUNT && !rc; ++m) {
+        c->dry_count = 0;
+        rc = enqueue_mode(c, m, passes);
+        hd.launches[m] = (unsigned)c->dry_count;
+    }
+    c->dry_count = 0;
+    if (!rc) rc = launch_round_start(c, hd);
+    if (!rc) rc = launch_mark(c, hd);
+    hd.round_launches = (unsigned)c->dry_count;
+    c->count_only = false;
+    if (rc) return rc;
+
+    IM_CUDA(c, cudaGraphCreate(&c->sel_graph, 0));
+    IM_CUDA(c, cudaGraphConditionalHandleCreate(&hd.round, c->sel_graph, 0, 0));
+    cudaGraph_t wround = nullptr, wbatch = nullptr, cases[M_COUNT] = {};
+    if ((rc = cap_begin(c, c->sel_graph))) return rc;
+    IM_LAUNCH(c, K_SEL_BEGIN, k_sel_begin, 1, 32, 0, c->d_sel, hd);
+    if ((rc = cap_conditional(c, hd.round, cudaGraphCondTypeWhile, 1, &wround))) return rc;
+    if ((rc = cap_end(c))) return rc;
+
+    IM_CUDA(c, cudaGraphConditionalHandleCreate(&hd.batch, wround, 0, 0));
+    if ((rc = cap_begin(c, wround))) return rc;
+    if ((rc = launch_round_start(c, hd))) return rc;
+    if ((rc = cap_conditional(c, hd.batch, cudaGraphCondTypeWhile, 1, &wbatch))) return rc;
+    if ((rc = launch_mark(c, hd))) return rc;
+    if ((rc = cap_end(c))) return rc;
+
+    IM_CUDA(c, cudaGraphConditionalHandleCreate(&hd.mode, wbatch, M_NONE, 0));
+    if ((rc = cap_begin(c, wbatch))) return rc;
+    if ((rc = launch_plan(c, hd))) return rc;
+    if ((rc = cap_conditional(c, hd.mode, cudaGraphCondTypeSwitch, M_COUNT, cases))) return rc;
+    if ((rc = cap_end(c))) return rc;
+
+    for (unsigned m = 0; m < M_COUNT; ++m) {
+        if ((rc = cap_begin(c, cases[m]))) return rc;
+        if ((rc = enqueue_mode(c, m, passes))) return rc;
+        if ((rc = cap_end(c))) return rc;
+    }
+    IM_CUDA(c, cudaGraphInstantiate(&c->sel_exec, c->sel_graph, 0));
+    return IM_OK;
+}
+
+int build_select_graph(im_ctx* c) {
+    if (c->sel_exec) return IM_OK;
+    if (!c->cap_stream) IM_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    const int rc = build_select_graph_steps(c);
+    if (rc) {
+        c->count_only = false;
+        if (c->capturing) {
+            cudaGraph_t out = nullptr;
+            cudaStreamEndCapture(c->cap_stream, &out);
+            c->capturing = false;
+        }
+        c->cur = c->stream;
+        cudaGetLastError();
+        im_select_graph_free(c);
+    }
+    return rc;
+}
+
+const char* sel_error_text(unsigned e) {
+    switch (e) {
+    case SEL_FB_OVERFLOW: return "BFS fallback queue capacity exceeded";
+    case SEL_NO_PROGRESS: return "re-evaluation batch made no progress";
+    case SEL_NO_CANDIDATE: return "no candidate left for the next seed";
+    case SEL_RANGE: return "selected id out of range";
+    default: return "selection kernel reported an error";
+    }
+}
+
+// The same rounds driven from the host: one synchronisation per batch to read k_plan's decision.
+int run_rounds_host(im_ctx* c) {
+    const SelHandles none{};
+    for (;;) {
+        int rc = pull_state(c);
+        if (rc) return rc;
+        if (c->h_sel->err || c->h_sel->round >= c->h_sel->round_end) return IM_OK;
+        if ((rc = launch_round_start(c, none))) return rc;
+        for (;;) {
+            if ((rc = launch_plan(c, none))) return rc;
+            if ((rc = pull_state(c))) return rc;
+            const SelState& h = *c->h_sel;
+            if (!h.cont) break;
+            const int passes = h.mode == M_HIST_SINGLE || h.mode == M_HIST_CHUNK ? h.shift / 8 + 1 : 0;
+            if ((rc = enqueue_mode(c, h.mode, passes))) return rc;
+        }
+        if ((rc = launch_mark(c, none))) return rc;
+    }
+}
+
+}  // namespace
+
+void im_select_graph_free(im_ctx* c) {
+    if (c->sel_exec) cudaGraphExecDestroy(c->sel_exec);
+    if (c->sel_graph) cudaGraphDestroy(c->sel_graph);
+    c->sel_exec = nullptr;
+    c->sel_graph = nullptr;
+}
+
+// Rounds of lazy greedy (NextSeed + MarkSeed) until k seeds are chosen.
+int im_select_run(im_ctx* c, uint32_t k) {
+    const uint32_t r0 = (uint32_t)c->seeds.size();
+    if (r0 >= k) return IM_OK;
+    IM_LAUNCH(c, K_SEL_BEGIN, k_set_target, 1, 32, 0, c->d_sel, k, (unsigned long long)c->refresh_min);
+    int rc = IM_OK;
+    if (c->use_graph) {
+        if ((rc = build_select_graph(c))) return rc;
+        int ev0 = -1;
+        im_prof_begin(c, K_SELECT_GRAPH, &ev0, false);
+        IM_CUDA(c, cudaGraphLaunch(c->sel_exec, c->stream));
+        im_prof_end(c, K_SELECT_GRAPH, ev0);
+    } else {
+        rc = run_rounds_host(c);
+        if (rc) return rc;
+    }
+    if ((rc = pull_state(c))) return rc;
+    const SelState& h = *c->h_sel;
+    if (c->use_graph) c->launches += h.launches - c->dev_launches_seen;
+    c->dev_launches_seen = h.launches;
+    // rounds completed before any error keep their seeds
+    const uint32_t r1 = h.round < k ? h.round : k;
+    if (r1 > r0) {
+        const size_t cnt = r1 - r0;
+        std::vector<uint32_t> sd(cnt);
+        std::vector<uint64_t> gn(cnt), ev(cnt);
+        IM_CUDA(c, cudaMemcpyAsync(sd.data(), c->d_seed_list + r0, cnt * 4, cudaMemcpyDeviceToHost, c->stream));
+        IM_CUDA(c, cudaMemcpyAsync(gn.data(), c->d_gain_list + r0, cnt * 8, cudaMemcpyDeviceToHost, c->stream));
+        IM_CUDA(c, cudaMemcpyAsync(ev.data(), c->d_round_evals + r0, cnt * 8, cudaMemcpyDeviceToHost, c->stream));
+        IM_CUDA(c, cudaStreamSynchronize(c->stream));
+        c->seeds.insert(c->seeds.end(), sd.begin(), sd.end());
+        c->seed_gains.insert(c->seed_gains.end(), gn.begin(), gn.end());
+        c->round_evals.insert(c->round_evals.end(), ev.begin(), ev.end());
+    }
+    if (h.err) return im_fail(c, IM_EDEVICE, sel_error_text(h.err));
+    if (h.fb_overflow) return im_fail(c, IM_EDEVICE, sel_error_text(SEL_FB_OVERFLOW));
+    if (r1 < k) return im_fail(c, IM_EDEVICE, "selection stopped early");
     return IM_OK;
 }
 

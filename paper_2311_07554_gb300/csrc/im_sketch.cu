@@ -276,7 +276,8 @@ k_gain_compact(const uint32_t* __restrict__ parent, const uint64_t* __restrict__
 // Recomputation evaluator: flag the components that hold a seed (bit 31 of their size).
 __global__ void k_cover_roots(const uint32_t* __restrict__ parent, uint64_t* __restrict__ word,
                               uint32_t n, uint32_t nb, const uint32_t* __restrict__ seeds,
-                              uint32_t nseeds) {
+                              const unsigned int* __restrict__ nseeds_dev) {
+    const uint32_t nseeds = *nseeds_dev;
     const uint32_t total = nb * nseeds;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
         const uint32_t b = i / nseeds, sd = seeds[i % nseeds];
@@ -536,32 +537,40 @@ int im_labels_min(im_ctx* c, uint32_t r, uint32_t* d_out) {
 // (Sketch(r) of Alg. 3) instead of one search per (x, r).  Same values as GetCenter; cheaper
 // when the batch is a large part of V.  The batch list and its size live on the device.
 int im_refresh_eval(im_ctx* c, const uint32_t* d_batch, const unsigned int* d_batch_n,
-                    unsigned long long* d_fresh, const uint32_t* d_seeds, uint32_t nseeds,
-                    uint64_t batch_hint) {
+                    unsigned long long* d_fresh, const uint32_t* d_seeds, const unsigned int* d_nseeds) {
     const uint32_t n = c->n, R = c->R;
     const unsigned T = 256;
-    int rc = lanes_fork(c);
-    if (rc) return rc;
-    if (c->lanes > 1)
+    // The member count and the seed count are read on the device, so the launches do not
+    // depend on them and the sequence can be captured in the selection graph.  Captured, it
+    // stays on the capturing stream (one lane); otherwise two lanes may alternate.
+    const uint32_t lanes = (c->capturing || c->count_only) ? 1u : c->lanes;
+    cudaStream_t s0 = c->cur;
+    int rc = IM_OK;
+    if (lanes > 1) {
+        rc = lanes_fork(c);
+        if (rc) return rc;
         IM_CUDA(c, cudaMemsetAsync(c->lane[1].fresh, 0, (size_t)n * sizeof(uint64_t), c->lane_stream1));
+    }
     uint32_t i = 0;
     for (uint32_t r0 = 0; r0 < R; r0 += c->batch_used, ++i) {
         const uint32_t nb = R - r0 < c->batch_used ? R - r0 : c->batch_used;
-        im_ctx::Lane& L = c->lane[i % c->lanes];
-        c->cur = L.stream;
+        const uint32_t li = i % lanes;
+        im_ctx::Lane& L = c->lane[li];
+        c->cur = li ? c->lane_stream1 : s0;
         rc = batch_components(c, L, r0, nb, 2);
-        if (rc) { lanes_join(c); return rc; }
-        if (nseeds)
-            IM_LAUNCH(c, K_COVER_ROOTS, k_cover_roots, grid_for((uint64_t)nb * nseeds, T), T, 0, L.parent,
-                      L.word, n, nb, d_seeds, nseeds);
-        IM_LAUNCH(c, K_REFRESH_GATHER, k_refresh_gather, grid_for(batch_hint, T, 152u * 16u), T, 0,
-                  L.parent, L.word, n, nb, d_batch, d_batch_n, (i % c->lanes) ? L.fresh : d_fresh);
+        if (rc) break;
+        IM_LAUNCH(c, K_COVER_ROOTS, k_cover_roots, 152u * 4u, T, 0, L.parent, L.word, n, nb, d_seeds,
+                  d_nseeds);
+        IM_LAUNCH(c, K_REFRESH_GATHER, k_refresh_gather, grid_for(n, T, 152u * 16u), T, 0,
+                  L.parent, L.word, n, nb, d_batch, d_batch_n, li ? L.fresh : d_fresh);
     }
-    rc = lanes_join(c);
-    if (rc) return rc;
-    if (c->lanes > 1 && i > 1)
-        IM_LAUNCH(c, K_REFRESH_GATHER, k_add_u64, grid_for(batch_hint, T, 152u * 8u), T, 0, d_fresh,
-                  (const unsigned long long*)c->lane[1].fresh, (uint64_t)0, d_batch_n);
-    IM_CUDA(c, cudaGetLastError());
-    return IM_OK;
+    c->cur = s0;
+    if (lanes > 1) {
+        const int rj = lanes_join(c);
+        if (!rc) rc = rj;
+        if (!rc && i > 1)
+            IM_LAUNCH(c, K_REFRESH_GATHER, k_add_u64, grid_for(n, T, 152u * 8u), T, 0, d_fresh,
+                      (const unsigned long long*)c->lane[1].fresh, (uint64_t)0, d_batch_n);
+    }
+    return rc;
 }

@@ -250,3 +250,35 @@ def test_both_batch_evaluators_give_identical_seeds(threshold, alpha):
         assert st["refresh_batches"] > 0
     else:
         assert st["refresh_batches"] == 0
+
+
+@pytest.mark.parametrize("threshold", [1, 64, 2**64 - 1])
+def test_graph_and_host_driven_selection_agree(threshold):
+    """The selection loop as one CUDA graph (while / switch nodes set by k_plan and
+    k_mark_seed) and the same kernels launched batch by batch from the host: identical seeds,
+    gains, per-round evaluation counts and batch counts, equal to the oracle's greedy.
+    threshold 1 evaluates every batch by refresh, 2^64-1 every batch by searches, 64 mixes."""
+    n, u, v = graphgen.erdos_renyi(3001, 9007, 4)
+    k = 40
+    G = oracle.Graph(n, u, v)
+    L = G.labels(42, 0.2, 77)
+    o_seeds, o_gains = oracle.greedy(L, k)
+    got = []
+    for graph in (True, False):
+        with im.IMContext(n, u, v) as ctx:
+            im.im_set_graph(ctx.h, graph)
+            im.im_set_refresh_threshold(ctx.h, threshold)
+            ctx.build_sketches(77, 42, 0.2, 0.1)
+            s1, _ = ctx.select_seeds(7)            # a prefix, then the rest
+            seeds, gains = ctx.select_seeds(k)
+            st = ctx.stats()
+            got.append((seeds, gains, ctx.round_evals(), st["batches"], st["refresh_batches"]))
+            assert np.array_equal(s1, seeds[:7])
+    (sg, gg, eg, bg, rg), (sh, gh, eh, bh, rh) = got
+    assert np.array_equal(sg, o_seeds) and np.array_equal(gg, o_gains)
+    assert np.array_equal(sh, sg) and np.array_equal(gh, gg)
+    assert np.array_equal(eg, eh) and bg == bh and rg == rh
+    if threshold == 1:
+        assert rg == bg > 0
+    if threshold == 2**64 - 1:
+        assert rg == 0
