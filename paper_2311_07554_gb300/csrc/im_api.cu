@@ -57,6 +57,7 @@ void free_sketch_state(im_ctx* c) {
     }
     c->live_cap = 0;
     dfree(c->d_fb_queue); dfree(c->d_fb_bits); dfree(c->d_fb_tasks);
+    dfree(c->d_cflags); dfree(c->d_cpos); dfree(c->d_csel);
     c->batch_alloc = 0;
     c->fb_slots = 0;
     c->fb_cap = 0;
@@ -173,7 +174,8 @@ int im_create(im_ctx** out, uint32_t n, uint64_t m, const uint32_t* u, const uin
     int rc = IM_OK;
     do {
         if (cudaMalloc(&c->d_sel, sizeof(SelState)) != cudaSuccess ||
-            cudaMallocHost(&c->h_sel, sizeof(SelState)) != cudaSuccess) {
+            cudaMallocHost(&c->h_sel, sizeof(SelState)) != cudaSuccess ||
+            cudaMallocHost(&c->h_live, 2 * sizeof(unsigned long long)) != cudaSuccess) {
             rc = im_fail(c, IM_ENOMEM, "selection state");
             break;
         }
@@ -278,78 +280,81 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
     while (rp2 < R) rp2 <<= 1;
     if (B > rp2) B = rp2;
 
-    free_sketch_state(c);
+    // live-pair records of one batch: expected p m B, with a generous margin; a batch that
+    // still overflows falls back to the fused sample+union loop on the device
+    uint64_t live_cap = 0;
+    if (c->m > 0 && (smp.all_live || smp.T != 0)) {
+        const double ex = (smp.all_live ? 1.0 : p) * (double)c->m * B;
+        double cap = 1.3 * ex + 16.0 * std::sqrt(ex) + 65536.0;
+        if (cap > (double)(1ull << 28)) cap = (double)(1ull << 28);
+        live_cap = (uint64_t)cap;
+    }
+    const size_t nc = (size_t)rho * R;
+    // A build with the same shapes reuses the device buffers (no cudaFree / cudaMalloc, which
+    // synchronise the device) and, if the sampler is unchanged too, the selection graph.
+    const bool same_layout = c->built && c->R == R && c->batch_alloc == B && c->compact_cap == nc &&
+                             c->all_centers == all && c->live_cap == live_cap;
+    if (!same_layout) {
+        free_sketch_state(c);
+    } else if (c->smp.salt != smp.salt || c->smp.T != smp.T || c->smp.all_live != smp.all_live) {
+        im_select_graph_free(c);   // the captured kernels carry the sampler
+    }
+    c->built = false;
     c->R = R; c->seed = seed; c->p = p; c->alpha = alpha; c->rho = rho; c->all_centers = all;
     c->key_bits = (uint32_t)bits;
     c->smp = smp;
     c->batch_used = B;
-    const size_t nc = (size_t)rho * R;
-    bool ok = dalloc(c->d_gain0, n) && dalloc(c->d_key, n) && dalloc(c->d_stamp, n) &&
-              dalloc(c->d_seedflag, n) && dalloc(c->d_batch, n) && dalloc(c->d_fresh, n) &&
-              dalloc(c->d_seed_list, n) && dalloc(c->d_labcache, (size_t)kLabSlots * R) &&
-              dalloc(c->d_gain_list, n) && dalloc(c->d_round_evals, n) &&
-              dalloc(c->d_label, nc) && dalloc(c->d_size, nc) &&
-              dalloc(c->lane[0].parent, (size_t)B * n) && dalloc(c->lane[0].word, (size_t)B * n) &&
-              dalloc(c->lane[1].parent, (size_t)B * n) && dalloc(c->lane[1].word, (size_t)B * n) &&
-              dalloc(c->lane[1].gain, n) && dalloc(c->lane[1].fresh, n);
-    if (ok && c->m > 0 && (smp.all_live || smp.T != 0)) {
-        // live-pair records of one batch: expected p m B, with a generous margin; a batch that
-        // still overflows falls back to the fused sample+union loop on the device
-        const double ex = (smp.all_live ? 1.0 : p) * (double)c->m * B;
-        double cap = 1.3 * ex + 16.0 * std::sqrt(ex) + 65536.0;
-        if (cap > (double)(1ull << 28)) cap = (double)(1ull << 28);
-        c->live_cap = (uint64_t)cap;
-        ok = dalloc(c->lane[0].live, c->live_cap) && dalloc(c->lane[0].live_n, 1) &&
-             dalloc(c->lane[1].live, c->live_cap) && dalloc(c->lane[1].live_n, 1);
+    if (!same_layout) {
+        bool ok = dalloc(c->d_gain0, n) && dalloc(c->d_key, n) && dalloc(c->d_stamp, n) &&
+                  dalloc(c->d_seedflag, n) && dalloc(c->d_batch, n) && dalloc(c->d_fresh, n) &&
+                  dalloc(c->d_seed_list, n) && dalloc(c->d_labcache, (size_t)kLabSlots * R) &&
+                  dalloc(c->d_gain_list, n) && dalloc(c->d_round_evals, n) &&
+                  dalloc(c->d_label, nc) && dalloc(c->d_size, nc) &&
+                  dalloc(c->lane[0].parent, (size_t)B * n) && dalloc(c->lane[0].word, (size_t)B * n) &&
+                  dalloc(c->lane[1].parent, (size_t)B * n) && dalloc(c->lane[1].word, (size_t)B * n) &&
+                  dalloc(c->lane[1].gain, n) && dalloc(c->lane[1].fresh, n);
+        if (ok && live_cap) {
+            c->live_cap = live_cap;
+            ok = dalloc(c->lane[0].live, c->live_cap) && dalloc(c->lane[0].live_n, 1) &&
+                 dalloc(c->lane[1].live, c->live_cap) && dalloc(c->lane[1].live_n, 1);
+        }
+        if (ok && !all) {
+            const size_t nw = ((size_t)n + 31) / 32;
+            c->fb_slots = 8;
+            c->fb_cap = 1u << 22;
+            ok = dalloc(c->d_cbits, nw) && dalloc(c->d_cidx, n) && dalloc(c->d_centers, rho) &&
+                 dalloc(c->d_fb_queue, (size_t)c->fb_slots * n) &&
+                 dalloc(c->d_fb_bits, (size_t)c->fb_slots * nw) && dalloc(c->d_fb_tasks, c->fb_cap) &&
+                 dalloc(c->d_cflags, n) && dalloc(c->d_cpos, (size_t)n + 1) &&
+                 dalloc(c->d_csel, kCenterSelBytes);
+            if (ok) ok = cudaMemsetAsync(c->d_fb_bits, 0, (size_t)c->fb_slots * nw * 4, c->stream) == cudaSuccess;
+        }
+        if (!ok) {
+            free_sketch_state(c);
+            return im_fail(c, IM_ENOMEM, "sketch memory");
+        }
+        c->batch_alloc = B;
+        c->compact_cap = nc;
     }
-    if (ok && !all) {
-        const size_t nw = ((size_t)n + 31) / 32;
-        c->fb_slots = 8;
-        c->fb_cap = 1u << 22;
-        ok = dalloc(c->d_cbits, nw) && dalloc(c->d_cidx, n) && dalloc(c->d_centers, rho) &&
-             dalloc(c->d_fb_queue, (size_t)c->fb_slots * n) && dalloc(c->d_fb_bits, (size_t)c->fb_slots * nw) &&
-             dalloc(c->d_fb_tasks, c->fb_cap);
-        if (ok) ok = cudaMemsetAsync(c->d_fb_bits, 0, (size_t)c->fb_slots * nw * 4, c->stream) == cudaSuccess;
-    }
-    if (!ok) {
-        free_sketch_state(c);
-        return im_fail(c, IM_ENOMEM, "sketch memory");
-    }
-    c->batch_alloc = B;
-    c->compact_cap = nc;
     c->refresh_min = c->refresh_req ? c->refresh_req : std::max<uint64_t>(16384, n / 16);
     int rc = IM_OK;
+    // live pairs before the build, read with the build's final synchronisation
+    IM_CUDA(c, cudaMemcpyAsync(c->h_live, c->d_live_total, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                               c->stream));
     if (!all) {
-        uint32_t* flags = nullptr;
-        uint64_t* pos = nullptr;
-        if (!dalloc(flags, n) || !dalloc(pos, (size_t)n + 1)) {
-            dfree(flags);
-            dfree(pos);
-            free_sketch_state(c);
-            return im_fail(c, IM_ENOMEM, "center scratch");
-        }
-        rc = im_select_centers(c, flags, pos);
-        dfree(flags);
-        dfree(pos);
+        rc = im_select_centers(c, c->d_cflags, c->d_cpos);
         if (rc) { free_sketch_state(c); return rc; }
-    }
-    unsigned long long live0 = 0, live1 = 0;
-    {
-        cudaError_t e = cudaMemcpyAsync(&live0, c->d_live_total, sizeof live0, cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) rc = im_cuda_check(c, e, "live pair counter");
     }
     if (!rc) rc = im_arc_keys(c, smp.salt);
     if (!rc) rc = im_sketch_batches(c);
     if (!rc) rc = im_selection_init(c);
     if (!rc) {
-        cudaError_t e = cudaStreamSynchronize(c->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(&live1, c->d_live_total, sizeof live1, cudaMemcpyDeviceToHost, c->stream);
+        cudaError_t e = cudaMemcpyAsync(c->h_live + 1, c->d_live_total, sizeof(unsigned long long),
+                                        cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) rc = im_cuda_check(c, e, "sketch construction");
     }
-    c->build_live_pairs = live1 - live0;
+    c->build_live_pairs = c->h_live[1] - c->h_live[0];
     if (rc) { free_sketch_state(c); return rc; }
     c->built = true;
     return IM_OK;
@@ -549,6 +554,7 @@ void im_destroy(im_ctx* c) {
     dfree(c->d_spread_pairs); dfree(c->d_spread_seeds); dfree(c->d_spread_total); dfree(c->d_live_total);
     if (c->d_sel) cudaFree(c->d_sel);
     if (c->h_sel) cudaFreeHost(c->h_sel);
+    if (c->h_live) cudaFreeHost(c->h_live);
     if (c->d_tmp) cudaFree(c->d_tmp);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     if (c->lane_stream1) { cudaStreamSynchronize(c->lane_stream1); cudaStreamDestroy(c->lane_stream1); }

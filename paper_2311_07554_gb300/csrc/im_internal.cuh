@@ -20,6 +20,7 @@ constexpr uint32_t kQcap = 256;                       // per-warp BFS queue (sha
 constexpr uint32_t kSpreadKMax = 16384;
 constexpr uint32_t kArcIdMask = 0x7FFFFFFFu;            // arc word 0: neighbour id | center bit
 constexpr uint32_t kLabSlots = 256;                     // label cache: vertex slots (x mod 256)
+constexpr size_t kCenterSelBytes = 4096;                // device state of the center radix select
 
 // splitmix64 output finaliser (Steele, Lea, Flood 2014).
 __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
@@ -266,6 +267,12 @@ struct im_ctx {
     size_t spread_cap = 0;
     uint32_t* d_spread_seeds = nullptr;
     unsigned long long* d_spread_total = nullptr;
+
+    // center selection scratch
+    uint32_t* d_cflags = nullptr;        // n: center flags
+    uint64_t* d_cpos = nullptr;          // n + 1: their exclusive scan
+    uint8_t* d_csel = nullptr;           // kCenterSelBytes: radix-select state
+    unsigned long long* h_live = nullptr;   // pinned: live-pair counter before / after a build
 
     // misc scratch (scan partials, center select)
     void* d_tmp = nullptr;

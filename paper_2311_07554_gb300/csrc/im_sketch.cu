@@ -317,6 +317,17 @@ struct CenterSel {
     unsigned int hist[256];
 };
 
+__global__ void k_center_init(CenterSel* st, uint32_t rho) {
+    if (threadIdx.x == 0) {
+        st->prefix = 0;
+        st->prefmask = 0;
+        st->need = rho;
+        st->shift = 56;
+        st->pad = 0;
+    }
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) st->hist[i] = 0;
+}
+
 __global__ void k_center_hist(uint32_t n, uint64_t csalt, CenterSel* st) {
     __shared__ unsigned int h[256];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
@@ -453,37 +464,24 @@ int lanes_join(im_ctx* c) {
 }  // namespace
 
 int im_select_centers(im_ctx* c, uint32_t* d_flags, uint64_t* d_pos) {
+    static_assert(sizeof(CenterSel) <= kCenterSelBytes, "center select scratch");
     const uint32_t n = c->n;
-    CenterSel* st = nullptr;
-    if (cudaMalloc(&st, sizeof(CenterSel)) != cudaSuccess) return im_fail(c, IM_ENOMEM, "center select");
-    CenterSel h{};
-    h.prefix = 0;
-    h.prefmask = 0;
-    h.need = c->rho;
-    h.shift = 56;
-    int rc = IM_OK;
-    do {
-        if (cudaMemcpyAsync(st, &h, sizeof h, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
-            rc = im_fail(c, IM_ECUDA, "memcpy");
-            break;
-        }
-        const uint64_t csalt = mix64(c->seed ^ 0xC3ull);
-        const unsigned T = 256;
-        for (int pass = 0; pass < 8; ++pass) {
-            IM_LAUNCH(c, K_CENTER_HIST, k_center_hist, grid_for(n, T, 152u * 8u), T, 0, n, csalt, st);
-            IM_LAUNCH(c, K_CENTER_PICK, k_center_pick, 1, 32, 0, st);
-        }
-        IM_LAUNCH(c, K_CENTER_FLAGS, k_center_flags, grid_for(n, T, 152u * 8u), T, 0, n, csalt, st,
-                  d_flags, c->d_cbits);
-        rc = im_scan_u32_to_u64(c, d_flags, d_pos, n);
-        if (rc) break;
-        IM_LAUNCH(c, K_CENTER_INDEX, k_center_index, grid_for(n, T, 152u * 8u), T, 0, n, c->rho, d_flags, d_pos,
-                  c->d_cidx, c->d_centers);
-        cudaError_t e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) rc = im_cuda_check(c, e, "center selection");
-    } while (0);
-    cudaFree(st);
-    return rc;
+    CenterSel* st = reinterpret_cast<CenterSel*>(c->d_csel);
+    const uint64_t csalt = mix64(c->seed ^ 0xC3ull);
+    const unsigned T = 256;
+    IM_LAUNCH(c, K_CENTER_PICK, k_center_init, 1, 256, 0, st, c->rho);
+    for (int pass = 0; pass < 8; ++pass) {
+        IM_LAUNCH(c, K_CENTER_HIST, k_center_hist, grid_for(n, T, 152u * 8u), T, 0, n, csalt, st);
+        IM_LAUNCH(c, K_CENTER_PICK, k_center_pick, 1, 32, 0, st);
+    }
+    IM_LAUNCH(c, K_CENTER_FLAGS, k_center_flags, grid_for(n, T, 152u * 8u), T, 0, n, csalt, st,
+              d_flags, c->d_cbits);
+    const int rc = im_scan_u32_to_u64(c, d_flags, d_pos, n);
+    if (rc) return rc;
+    IM_LAUNCH(c, K_CENTER_INDEX, k_center_index, grid_for(n, T, 152u * 8u), T, 0, n, c->rho, d_flags, d_pos,
+              c->d_cidx, c->d_centers);
+    IM_CUDA(c, cudaGetLastError());
+    return IM_OK;
 }
 
 // Build all R sketches batch by batch; writes gain0, label, size.  Batch i runs on lane

@@ -282,3 +282,25 @@ def test_graph_and_host_driven_selection_agree(threshold):
         assert rg == bg > 0
     if threshold == 2**64 - 1:
         assert rg == 0
+
+
+def test_rebuilds_in_one_context_match_fresh_contexts():
+    """Builds that reuse the device buffers and the selection graph (same shapes, same
+    sampler), re-capture the graph (new seed) or re-allocate (new p, R, alpha) all give the
+    results of a fresh context; the last configuration is also checked against the oracle."""
+    n, u, v = graphgen.erdos_renyi(2000, 8000, 12)
+    cfgs = [(42, 0.1, 50, 0.2), (42, 0.1, 50, 0.2), (7, 0.1, 50, 0.2), (7, 0.3, 50, 0.2),
+            (7, 0.3, 64, 0.05)]
+    k = 8
+    with im.IMContext(n, u, v) as ctx:
+        for seed, p, R, alpha in cfgs:
+            ctx.build_sketches(R, seed, p, alpha)
+            got = ctx.select_seeds(k) + ctx.compact() + (ctx.gains(),)
+            with im.IMContext(n, u, v) as fresh:
+                fresh.build_sketches(R, seed, p, alpha)
+                want = fresh.select_seeds(k) + fresh.compact() + (fresh.gains(),)
+            for a, b in zip(got, want):
+                assert np.array_equal(a, b), (seed, p, R, alpha)
+    o = _oracle(n, u, v, 7, 0.3, 64, 0.05, k)
+    assert np.array_equal(got[0], o["seeds"]) and np.array_equal(got[1], o["seed_gains"])
+    assert np.array_equal(got[2], o["label"]) and np.array_equal(got[3], o["size"])
