@@ -550,7 +550,7 @@ void im_destroy(im_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_sketch_state(c);
-    dfree(c->d_edges); dfree(c->d_off); dfree(c->d_arcs);
+    dfree(c->d_edges); dfree(c->d_off); dfree(c->d_arcs); dfree(c->d_arc_cur);
     dfree(c->d_spread_pairs); dfree(c->d_spread_seeds); dfree(c->d_spread_total); dfree(c->d_live_total);
     if (c->d_sel) cudaFree(c->d_sel);
     if (c->h_sel) cudaFreeHost(c->h_sel);

@@ -28,36 +28,52 @@ __global__ void k_csr_degree(const uint2* __restrict__ edges, uint64_t m,
     }
 }
 
-// Each arc (x -> y) of edge e is written at off[x] + (its arrival order at x).  The order
-// inside an adjacency list is not fixed; no result depends on it.
-__global__ void k_csr_fill(const uint2* __restrict__ edges, uint64_t m,
-                           const uint64_t* __restrict__ off, uint32_t* __restrict__ cursor,
-                           uint4* __restrict__ arcs) {
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
-        uint2 ed = edges[e];
-        uint64_t pa = off[ed.x] + atomicAdd(cursor + ed.x, 1u);
-        arcs[pa] = make_uint4(ed.y, (uint32_t)e, 0u, 0u);
-        uint64_t pb = off[ed.y] + atomicAdd(cursor + ed.y, 1u);
-        arcs[pb] = make_uint4(ed.x, (uint32_t)e, 0u, 0u);
-    }
+// Every build rewrites the arcs (x -> y) of each edge e: (y | center bit << 31, e, key lo,
+// key hi) with the per-edge hash key mix(salt ^ e) (Sec. 2 fusion: the sampling of edge e in
+// sketch r is then one more mix of key + (r+1) G) and whether y is a center, so a search
+// step needs no other lookup.  Inside each adjacency list the arcs to centers come first
+// (cursor ccur from the front, ncur from the back): GetCenter stops at the first live center
+// it meets, and on a hub it then meets one after ~1/p arcs instead of ~1/(p alpha).  The
+// order inside each group is arrival order; no result depends on the order of an adjacency
+// list (every center of a component carries the component's label, and a search without a
+// center visits the whole component).  Arcs of one source in a warp share one atomic.
+__device__ __forceinline__ uint64_t arc_slot(bool valid, uint32_t x, bool to_center,
+                                             const uint64_t* __restrict__ off, uint32_t* __restrict__ ccur,
+                                             uint32_t* __restrict__ ncur) {
+    // x < 2^31, so (x << 1) | c never equals the key of an idle lane
+    const unsigned key = valid ? ((x << 1) | (to_center ? 1u : 0u)) : 0xFFFFFFFFu;
+    const unsigned grp = __match_any_sync(0xffffffffu, key);
+    const int leader = __ffs(grp) - 1;
+    const unsigned rank = __popc(grp & ((1u << (threadIdx.x & 31)) - 1u));
+    uint32_t base = 0;
+    if (valid && (int)(threadIdx.x & 31) == leader)
+        base = atomicAdd(to_center ? ccur + x : ncur + x, (unsigned)__popc(grp));
+    base = __shfl_sync(0xffffffffu, base, leader) + rank;
+    if (!valid) return 0;
+    return to_center ? off[x] + base : off[x + 1] - 1 - base;
 }
 
-// Store in every arc the per-edge hash key mix(salt ^ e) (Sec. 2 fusion: the sampling of
-// edge e in sketch r is then one more mix of key + (r+1) G) and whether its neighbour is a
-// center (bit 31 of the neighbour id), so a search step needs no other lookup.
-__global__ void k_arc_keys(uint4* __restrict__ arcs, uint64_t narcs, uint64_t salt,
-                           const uint32_t* __restrict__ cbits, int all_centers) {
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < narcs; a += stride) {
-        uint4 x = arcs[a];
-        const uint64_t key = mix64(salt ^ (uint64_t)x.y);
-        const uint32_t y = x.x & kArcIdMask;
-        const uint32_t cen = all_centers ? 1u : ((cbits[y >> 5] >> (y & 31)) & 1u);
-        x.x = y | (cen << 31);
-        x.z = (uint32_t)key;
-        x.w = (uint32_t)(key >> 32);
-        arcs[a] = x;
+__global__ void __launch_bounds__(256)
+k_arc_fill(const uint2* __restrict__ edges, uint64_t m, const uint64_t* __restrict__ off,
+           uint32_t* __restrict__ ccur, uint32_t* __restrict__ ncur, uint4* __restrict__ arcs,
+           uint64_t salt, const uint32_t* __restrict__ cbits, int all_centers) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    // the loop bound is uniform over the block, so every warp-wide call has all lanes
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < m; base += stride) {
+        const uint64_t e = base + threadIdx.x;
+        const bool valid = e < m;
+        uint2 ed = make_uint2(0, 0);
+        if (valid) ed = edges[e];
+        const uint64_t key = mix64(salt ^ e);
+        const bool cx = valid && (all_centers || ((cbits[ed.x >> 5] >> (ed.x & 31)) & 1u));
+        const bool cy = valid && (all_centers || ((cbits[ed.y >> 5] >> (ed.y & 31)) & 1u));
+        const uint64_t pa = arc_slot(valid, ed.x, cy, off, ccur, ncur);
+        const uint64_t pb = arc_slot(valid, ed.y, cx, off, ccur, ncur);
+        if (valid) {
+            const uint32_t klo = (uint32_t)key, khi = (uint32_t)(key >> 32);
+            arcs[pa] = make_uint4(ed.y | ((cy ? 1u : 0u) << 31), (uint32_t)e, klo, khi);
+            arcs[pb] = make_uint4(ed.x | ((cx ? 1u : 0u) << 31), (uint32_t)e, klo, khi);
+        }
     }
 }
 
@@ -172,7 +188,8 @@ int im_scan_u32_to_u64(im_ctx* c, const uint32_t* d_in, uint64_t* d_out, uint64_
     return IM_OK;
 }
 
-// Pack and validate the edge list, then build the CSR (offsets u64, arcs (nbr, eid)).
+// Pack and validate the edge list and build the CSR offsets (u64); the arcs themselves are
+// written by every build (im_arc_keys), which knows the centers.
 int im_graph_build(im_ctx* c, const uint32_t* d_u, const uint32_t* d_v) {
     const uint32_t n = c->n;
     const uint64_t m = c->m;
@@ -185,11 +202,11 @@ int im_graph_build(im_ctx* c, const uint32_t* d_u, const uint32_t* d_v) {
         return im_fail(c, IM_ENOMEM, "csr offsets");
     if (cudaMalloc(&c->d_arcs, (2 * m + 2) * sizeof(uint4)) != cudaSuccess)
         return im_fail(c, IM_ENOMEM, "csr arcs");
-    uint32_t* deg = nullptr;
-    unsigned int* bad = nullptr;
-    if (cudaMalloc(&deg, ((size_t)n + 1) * sizeof(uint32_t) + 16) != cudaSuccess)
-        return im_fail(c, IM_ENOMEM, "degree scratch");
-    bad = (unsigned int*)(deg + n + 1);
+    // two cursors per vertex for the arc fill; the first n + 5 words serve as degree scratch
+    if (cudaMalloc(&c->d_arc_cur, (2 * (size_t)n + 8) * sizeof(uint32_t)) != cudaSuccess)
+        return im_fail(c, IM_ENOMEM, "arc cursors");
+    uint32_t* deg = c->d_arc_cur;
+    unsigned int* bad = (unsigned int*)(deg + n + 1);
     int rc = IM_OK;
     do {
         if (cudaMemsetAsync(deg, 0, ((size_t)n + 1) * sizeof(uint32_t) + 16, c->stream) != cudaSuccess) {
@@ -213,23 +230,19 @@ int im_graph_build(im_ctx* c, const uint32_t* d_u, const uint32_t* d_v) {
         }
         rc = im_scan_u32_to_u64(c, deg, c->d_off, n);
         if (rc) break;
-        if (cudaMemsetAsync(deg, 0, (size_t)n * sizeof(uint32_t), c->stream) != cudaSuccess) {
-            rc = im_fail(c, IM_ECUDA, "memset");
-            break;
-        }
-        if (m > 0)
-            IM_LAUNCH(c, K_CSR_FILL, k_csr_fill, grid_for(m, B), B, 0, c->d_edges, m, c->d_off, deg, c->d_arcs);
         cudaError_t e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) rc = im_cuda_check(c, e, "csr build");
     } while (0);
-    cudaFree(deg);
     return rc;
 }
 
 int im_arc_keys(im_ctx* c, uint64_t salt) {
-    if (c->m > 0)
-        IM_LAUNCH(c, K_ARC_KEYS, k_arc_keys, grid_for(2 * c->m, 256, 152u * 16u), 256, 0, c->d_arcs, 2 * c->m,
-                  salt, c->d_cbits, (int)c->all_centers);
+    if (c->m > 0) {
+        const uint32_t n = c->n;
+        IM_CUDA(c, cudaMemsetAsync(c->d_arc_cur, 0, 2 * (size_t)n * sizeof(uint32_t), c->stream));
+        IM_LAUNCH(c, K_ARC_KEYS, k_arc_fill, grid_for(c->m, 256, 152u * 16u), 256, 0, c->d_edges, c->m, c->d_off,
+                  c->d_arc_cur, c->d_arc_cur + n, c->d_arcs, salt, c->d_cbits, (int)c->all_centers);
+    }
     IM_CUDA(c, cudaGetLastError());
     c->arc_salt = salt;
     c->arc_keys_valid = true;

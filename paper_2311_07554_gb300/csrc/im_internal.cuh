@@ -190,6 +190,7 @@ struct im_ctx {
     uint2* d_edges = nullptr;
     uint64_t* d_off = nullptr;
     uint4* d_arcs = nullptr;
+    uint32_t* d_arc_cur = nullptr;   // 2n arc-fill cursors (centers from the front, others from the back)
     uint64_t arc_salt = 0;
     bool arc_keys_valid = false;
 
