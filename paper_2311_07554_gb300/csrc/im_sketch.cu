@@ -3,7 +3,7 @@
 // Batches of B sketches share one pass over the edge list.  Per sketch b of a batch:
 //   init        P[b][v] = v;  W[b][v] = (key = lk(v), count = 1)
 //   sample      every live (edge, sketch) pair of the batch becomes a record (u, v, b)
-//   union       one thread per record, randomized linking (expected log-depth trees)
+//   union       one thread per record, Rem's union with splicing (parents below children)
 //   compress    P[b][v] <- root; per root, for every other member: count += 1 and
 //               key = min over members of the
 //               label key of its centers (center index) -- with every vertex a center this
@@ -49,8 +49,8 @@ __device__ __forceinline__ void sample_union_pair(const uint4& two, uint64_t i, 
     uint64_t x1 = mix64(smp.salt ^ (2 * i + 1)) + g0;
     const bool has1 = 2 * i + 1 < m;
     for (uint32_t b = 0; b < nb; ++b) {
-        if (smp.all_live || mix64(x0) < smp.T) unite_rand(parent + (size_t)b * n, two.x, two.y);
-        if (has1 && (smp.all_live || mix64(x1) < smp.T)) unite_rand(parent + (size_t)b * n, two.z, two.w);
+        if (smp.all_live || mix64(x0) < smp.T) unite_rem(parent + (size_t)b * n, two.x, two.y);
+        if (has1 && (smp.all_live || mix64(x1) < smp.T)) unite_rem(parent + (size_t)b * n, two.z, two.w);
         x0 += kGamma;
         x1 += kGamma;
     }
@@ -174,7 +174,7 @@ k_union_live(const uint4* __restrict__ recs, const unsigned long long* __restric
     }
     for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < cnt; j += stride) {
         const uint4 rc = recs[j];
-        unite_rand(parent + (size_t)rc.z * n, rc.x, rc.y);
+        unite_rem(parent + (size_t)rc.z * n, rc.x, rc.y);
     }
 }
 

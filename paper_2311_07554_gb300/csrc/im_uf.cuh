@@ -1,10 +1,10 @@
 // im_uf.cuh -- union-find primitives shared by the sketch kernels (internal).
 //
-// Parent pointers only ever move to an ancestor and a vertex that stops being a root never
-// becomes one again, so a stale parent read from L1 is still an ancestor: climbing it is
-// correct, and a stale "is a root" answer is caught by the atomicCAS that hooks it.  Climbs
-// therefore read through L1 (__ldca): every climb in a giant component ends at the same root
-// entry, which would otherwise be one hot L2 sector for the whole GPU.
+// Parent ids only ever decrease and a vertex that stops being a root never becomes one again,
+// so a stale parent read from L1 is a former parent in the same set: climbing it is correct,
+// and a stale "is a root" answer is caught by the atomicCAS that hooks it.  Climbs therefore
+// read through L1 (__ldca): every climb in a giant component ends at the same root entry,
+// which would otherwise be one hot L2 sector for the whole GPU.
 #pragma once
 
 #include "im_internal.cuh"
@@ -22,33 +22,6 @@ __device__ __forceinline__ uint32_t find_root(uint32_t* P, uint32_t x) {
     }
 }
 
-// Link priority: a fixed random permutation of the ids (the "lowbias32" integer mixer of
-// C. Wellons, a bijection of 32-bit words).  Hooking the root of larger priority under the
-// other gives trees of expected logarithmic depth whatever order the edges arrive in, where
-// hooking by id lets a subtree be re-rooted again and again.
-__device__ __forceinline__ uint32_t link_prio(uint32_t x) {
-    x ^= x >> 16;
-    x *= 0x7feb352du;
-    x ^= x >> 15;
-    x *= 0x846ca68bu;
-    x ^= x >> 16;
-    return x;
-}
-
-// Union with randomized linking; the root is not a canonical label (labels are computed
-// afterwards as a per-component minimum).
-__device__ __forceinline__ void unite_rand(uint32_t* P, uint32_t a, uint32_t b) {
-    for (;;) {
-        a = find_root(P, a);
-        b = find_root(P, b);
-        if (a == b) return;
-        if (link_prio(b) < link_prio(a)) { uint32_t t = a; a = b; b = t; }
-        const uint32_t old = atomicCAS(P + b, b, a);   // hook b under a
-        if (old == b) return;
-        b = old;
-    }
-}
-
 // Union with smallest-id hooking: the root of every tree is its smallest id.
 __device__ __forceinline__ void unite_min(uint32_t* P, uint32_t a, uint32_t b) {
     for (;;) {
@@ -59,6 +32,36 @@ __device__ __forceinline__ void unite_min(uint32_t* P, uint32_t a, uint32_t b) {
         const uint32_t old = atomicCAS(P + b, b, a);
         if (old == b) return;
         b = old;
+    }
+}
+
+// Rem's union with splicing (Patwary, Blair, Manne, "Experiments on union-find algorithms for
+// the disjoint-set data structure", 2010), in the concurrent form with compare-and-swap used
+// by ConnectIt (Dhulipala, Hong, Shun, 2020).  Invariant: a parent has a smaller id than its
+// child, so roots are component minima.  Both endpoints climb in one loop: each step moves
+// the side whose parent is larger, either hooking it (a root) under the other side's parent
+// or splicing it there (P[rx] := py) and continuing from its old parent.  The two parent
+// loads of a step are independent, and the climb ends where the paths meet, not at the root.
+// Every write joins the two sets being united, and each step lowers rx, so stale (L1) reads
+// cost extra steps but neither correctness nor termination.
+__device__ __forceinline__ void unite_rem(uint32_t* P, uint32_t x, uint32_t y) {
+    uint32_t rx = x, ry = y;
+    uint32_t px = __ldca(P + rx), py = __ldca(P + ry);
+    while (px != py) {
+        if (px < py) {
+            uint32_t t = rx; rx = ry; ry = t;
+            t = px; px = py; py = t;
+        }
+        // now py < px <= rx
+        if (rx == px) {
+            const uint32_t old = atomicCAS(P + rx, rx, py);   // hook the root rx under py
+            if (old == rx) return;
+            px = old;                                         // rx got a parent meanwhile
+            continue;
+        }
+        atomicCAS(P + rx, px, py);                            // splice
+        rx = px;
+        px = __ldca(P + rx);
     }
 }
 
