@@ -13,6 +13,8 @@
 //               label[i] = i, else 0 (Alg. 3)
 // W[b][x] is one 64-bit word per root: low half = component size (bit 31 is the "holds a
 // seed" flag of the recomputation evaluator), high half = the component's minimum key.
+#include <algorithm>
+
 #include "im_internal.cuh"
 #include "im_uf.cuh"
 
@@ -183,13 +185,13 @@ __global__ void k_zero_u64(unsigned long long* p) {
 }
 
 // grid.y = sketch within the batch.  Full compression, then per root the component size and
-// the minimum label key.  Each block owns tiles of kCountTile vertices; equal roots are merged
-// inside a warp (match_any) and then in a shared-memory hash table, so a giant component costs
-// one global atomic pair per tile instead of one per warp.
+// the minimum label key.  Equal roots are merged inside a warp (match_any); each block keeps
+// a small direct-mapped cache of roots (claimed by the first root that maps to a slot), so
+// the roots that recur within a block -- a giant component's above all -- cost one global
+// atomic pair per block, flushed once at its end; other roots are updated in place.
 // key_mode 0: every vertex offers lk(v) = v (the smallest id); 1: only centers offer their
 // center index (components without a center need no label); 2: sizes only.
-constexpr int kCountTile = 1024;
-constexpr int kCountSlots = 2048;   // power of two, >= 2 x tile
+constexpr int kCountSlots = 64;
 
 __global__ void __launch_bounds__(256)
 k_compress_count(uint32_t* __restrict__ parent, uint64_t* __restrict__ word, uint32_t n,
@@ -203,47 +205,45 @@ k_compress_count(uint32_t* __restrict__ parent, uint64_t* __restrict__ word, uin
     const unsigned lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < kCountSlots; i += blockDim.x) { tkey[i] = kNone; tcnt[i] = 0; tmin[i] = kNone; }
     __syncthreads();
-    for (uint32_t t0 = blockIdx.x * kCountTile; t0 < n; t0 += gridDim.x * kCountTile) {
-        for (uint32_t off = 0; off < (uint32_t)kCountTile; off += blockDim.x) {
-            const uint32_t v = t0 + off + threadIdx.x;
-            const bool act = v < n;
-            uint32_t root = 0, lk = kNone;
-            bool member = false;   // v stopped being a root: its root must count it
-            if (act) {
-                root = compress_to_root(P, v);
-                member = root != v;
-                if (member) lk = label_key(v, key_mode, cidx);
-            }
-            const unsigned am = __ballot_sync(0xffffffffu, member);
-            if (member) {
-                const unsigned grp = __match_any_sync(am, root);
-                const uint32_t gmin = __reduce_min_sync(grp, lk);
-                if (lane == (unsigned)(__ffs(grp) - 1)) {
-                    uint32_t h = (root * 0x9E3779B1u) >> (32 - 11);
-                    for (;;) {
-                        const uint32_t old = atomicCAS(&tkey[h], kNone, root);
-                        if (old == kNone || old == root) {
-                            atomicAdd(&tcnt[h], (uint32_t)__popc(grp));
-                            if (gmin != kNone) atomicMin(&tmin[h], gmin);
-                            break;
-                        }
-                        h = (h + 1) & (kCountSlots - 1);
-                    }
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v - threadIdx.x < n; v += stride) {
+        const bool act = v < n;
+        uint32_t root = 0, lk = kNone;
+        bool member = false;   // v stopped being a root: its root must count it
+        if (act) {
+            root = compress_to_root(P, v);
+            member = root != v;
+            if (member) lk = label_key(v, key_mode, cidx);
+        }
+        const unsigned am = __ballot_sync(0xffffffffu, member);
+        if (member) {
+            const unsigned grp = __match_any_sync(am, root);
+            const uint32_t gmin = __reduce_min_sync(grp, lk);
+            if (lane == (unsigned)(__ffs(grp) - 1)) {
+                const uint32_t cnt = (uint32_t)__popc(grp);
+                const uint32_t h = (root * 0x9E3779B1u) >> (32 - 6);
+                uint32_t k = tkey[h];
+                if (k == kNone) {
+                    k = atomicCAS(&tkey[h], kNone, root);
+                    if (k == kNone) k = root;
+                }
+                if (k == root) {
+                    atomicAdd(&tcnt[h], cnt);
+                    if (gmin != kNone) atomicMin(&tmin[h], gmin);
+                } else {
+                    atomicAdd(w_count(W + root), cnt);
+                    if (gmin != kNone) atomicMin(w_key(W + root), gmin);
                 }
             }
         }
-        __syncthreads();
-        for (int i = threadIdx.x; i < kCountSlots; i += blockDim.x) {
-            const uint32_t rt = tkey[i];
-            if (rt != kNone) {
-                atomicAdd(w_count(W + rt), tcnt[i]);
-                if (tmin[i] != kNone) atomicMin(w_key(W + rt), tmin[i]);
-                tkey[i] = kNone;
-                tcnt[i] = 0;
-                tmin[i] = kNone;
-            }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kCountSlots; i += blockDim.x) {
+        const uint32_t rt = tkey[i];
+        if (rt != kNone) {
+            atomicAdd(w_count(W + rt), tcnt[i]);
+            if (tmin[i] != kNone) atomicMin(w_key(W + rt), tmin[i]);
         }
-        __syncthreads();
     }
 }
 
@@ -434,7 +434,8 @@ int batch_components(im_ctx* c, im_ctx::Lane& L, uint32_t r0, uint32_t nb, int k
                                                        : launch_sample_fused(c, L, r0, nb);
         if (rc) return rc;
     }
-    dim3 g(grid_for(n, kCountTile, 152u * 8u), nb);
+    // about 8 blocks per SM in all: each block sweeps a stretch of one sketch
+    dim3 g(std::max(1u, std::min(grid_for(n, T), (152u * 8u + nb - 1) / nb)), nb);
     IM_LAUNCH(c, K_COMPRESS_COUNT, k_compress_count, g, T, 0, L.parent, L.word, n, c->d_cidx, key_mode);
     return IM_OK;
 }
