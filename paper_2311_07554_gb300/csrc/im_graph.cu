@@ -18,13 +18,27 @@ __global__ void k_pack_edges(const uint32_t* __restrict__ u, const uint32_t* __r
     }
 }
 
-__global__ void k_csr_degree(const uint2* __restrict__ edges, uint64_t m,
-                             uint32_t* __restrict__ deg) {
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
-        uint2 ed = edges[e];
-        atomicAdd(deg + ed.x, 1u);
-        atomicAdd(deg + ed.y, 1u);
+// Degrees; equal endpoints within a warp share one atomic, so a hub's counter (and edges
+// sorted by their first endpoint) do not serialise the whole kernel.
+__device__ __forceinline__ void add_degree(bool valid, uint32_t x, uint32_t* __restrict__ deg) {
+    const unsigned key = valid ? x : 0xFFFFFFFFu;   // ids are < 2^31
+    const unsigned grp = __match_any_sync(0xffffffffu, key);
+    if (valid && (int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(deg + x, (unsigned)__popc(grp));
+}
+
+// Runs before the host has read k_pack_edges' verdict, so edges with an id >= n (which fail
+// the build afterwards) are skipped here rather than counted out of bounds.
+__global__ void __launch_bounds__(256)
+k_csr_degree(const uint2* __restrict__ edges, uint64_t m, uint32_t n, uint32_t* __restrict__ deg) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    // the loop bound is uniform over the block, so the warp-wide calls have all lanes
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < m; base += stride) {
+        const uint64_t e = base + threadIdx.x;
+        uint2 ed = make_uint2(0, 0);
+        if (e < m) ed = edges[e];
+        const bool valid = e < m && ed.x < n && ed.y < n;
+        add_degree(valid, ed.x, deg);
+        add_degree(valid, ed.y, deg);
     }
 }
 
@@ -216,7 +230,7 @@ int im_graph_build(im_ctx* c, const uint32_t* d_u, const uint32_t* d_v) {
         const unsigned B = 256;
         if (m > 0) {
             IM_LAUNCH(c, K_PACK_EDGES, k_pack_edges, grid_for(m, B), B, 0, d_u, d_v, m, n, c->d_edges, bad);
-            IM_LAUNCH(c, K_CSR_DEGREE, k_csr_degree, grid_for(m, B), B, 0, c->d_edges, m, deg);
+            IM_LAUNCH(c, K_CSR_DEGREE, k_csr_degree, grid_for(m, B), B, 0, c->d_edges, m, n, deg);
         }
         unsigned int h_bad = 0;
         if (cudaMemcpyAsync(&h_bad, bad, sizeof(h_bad), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||

@@ -69,6 +69,17 @@ k_sample_union(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, ui
         sample_union_pair<B>(edge_pairs[i], i, m, smp, g0, nb, parent, n);
 }
 
+// High word of mix64(x) before its last step (w ^ (w >> 31) for the high word w of z * C2):
+// the final high word differs from w at most in bit 0, so  final <= th  implies  w <= th + 1,
+// which makes w a candidate test that needs neither the low half of the last product nor the
+// last shift.
+__device__ __forceinline__ uint32_t mix64_hi_raw(uint64_t x) {
+    uint64_t z = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = z ^ (z >> 27);
+    const uint32_t zl = (uint32_t)z, zh = (uint32_t)(z >> 32);
+    return __umulhi(zl, 0x133111EBu) + zl * 0x94D049BBu + zh * 0x133111EBu;   // hi(z * C2)
+}
+
 // Sampling alone: every live (edge, sketch) pair of the batch becomes a record (u, v, b, 0),
 // appended with one atomic per warp.  The hash work (nb mixes per edge) is pure ALU; the
 // latency-bound unions then run one thread per record in k_union_live.
@@ -94,15 +105,16 @@ k_sample_emit(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, uin
             if (smp.all_live) {
                 live0 = live1 = (nb >= 32) ? 0xFFFFFFFFu : ((1u << nb) - 1u);
             } else {
-                // candidates by the high word of the hash (a superset of the live pairs);
-                // the few with an equal high word are settled exactly below
+                // candidates by the high word of the hash (a superset of the live pairs, about
+                // 2^-31 larger); they are settled exactly below
                 const uint32_t th = (uint32_t)(smp.T >> 32);
+                const uint32_t th1 = th == 0xFFFFFFFFu ? th : th + 1u;
                 uint64_t x0 = k0 + g0, x1 = k1 + g0;
                 if (nb == (uint32_t)B) {
 #pragma unroll
                     for (int b = 0; b < B; ++b) {
-                        if (mix64_hi(x0) <= th) live0 |= 1u << b;
-                        if (mix64_hi(x1) <= th) live1 |= 1u << b;
+                        if (mix64_hi_raw(x0) <= th1) live0 |= 1u << b;
+                        if (mix64_hi_raw(x1) <= th1) live1 |= 1u << b;
                         x0 += kGamma;
                         x1 += kGamma;
                     }
@@ -110,8 +122,8 @@ k_sample_emit(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, uin
 #pragma unroll
                     for (int b = 0; b < B; ++b) {
                         if (b < (int)nb) {
-                            if (mix64_hi(x0) <= th) live0 |= 1u << b;
-                            if (mix64_hi(x1) <= th) live1 |= 1u << b;
+                            if (mix64_hi_raw(x0) <= th1) live0 |= 1u << b;
+                            if (mix64_hi_raw(x1) <= th1) live1 |= 1u << b;
                         }
                         x0 += kGamma;
                         x1 += kGamma;

@@ -210,11 +210,12 @@ def test_argument_errors():
             ctx.spread(np.array([100], np.uint32))
         with pytest.raises(im.IMError):
             ctx.labels(4)
-    bad_u = np.array([0, 3], np.uint32)
-    bad_v = np.array([1, 3], np.uint32)
-    with pytest.raises(im.IMError) as e:
-        im.IMContext(4, bad_u, bad_v)
-    assert e.value.code == im.IM_EINVAL
+    for bad_u, bad_v in [([0, 3], [1, 3]),            # self-loop
+                         ([0, 7], [1, 2]),            # id >= n (skipped by the degree count)
+                         ([0, 1], [0x80000000, 2])]:  # id >= 2^31
+        with pytest.raises(im.IMError) as e:
+            im.IMContext(4, np.array(bad_u, np.uint32), np.array(bad_v, np.uint32))
+        assert e.value.code == im.IM_EINVAL
 
 
 def test_lazy_evaluation_counts_are_bounded():
