@@ -42,10 +42,10 @@ k_csr_degree(const uint2* __restrict__ edges, uint64_t m, uint32_t n, uint32_t* 
     }
 }
 
-// Every build rewrites the arcs (x -> y) of each edge e: (y | center bit << 31, e, key lo,
-// key hi) with the per-edge hash key mix(salt ^ e) (Sec. 2 fusion: the sampling of edge e in
+// Every build rewrites the arcs (x -> y) of each edge e: (y | center bit << 31, center index
+// of y (kNone if y is no center), key lo, key hi) with the per-edge hash key mix(salt ^ e) (Sec. 2 fusion: the sampling of edge e in
 // sketch r is then one more mix of key + (r+1) G) and whether y is a center, so a search
-// step needs no other lookup.  Inside each adjacency list the arcs to centers come first
+// step needs no other lookup (a search that meets a center reads its label directly).  Inside each adjacency list the arcs to centers come first
 // (cursor ccur from the front, ncur from the back): GetCenter stops at the first live center
 // it meets, and on a hub it then meets one after ~1/p arcs instead of ~1/(p alpha).  The
 // order inside each group is arrival order; no result depends on the order of an adjacency
@@ -70,7 +70,8 @@ __device__ __forceinline__ uint64_t arc_slot(bool valid, uint32_t x, bool to_cen
 __global__ void __launch_bounds__(256)
 k_arc_fill(const uint2* __restrict__ edges, uint64_t m, const uint64_t* __restrict__ off,
            uint32_t* __restrict__ ccur, uint32_t* __restrict__ ncur, uint4* __restrict__ arcs,
-           uint64_t salt, const uint32_t* __restrict__ cbits, int all_centers) {
+           uint64_t salt, const uint32_t* __restrict__ cbits, const uint32_t* __restrict__ cidx,
+           int all_centers) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     // the loop bound is uniform over the block, so every warp-wide call has all lanes
     for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < m; base += stride) {
@@ -85,8 +86,10 @@ k_arc_fill(const uint2* __restrict__ edges, uint64_t m, const uint64_t* __restri
         const uint64_t pb = arc_slot(valid, ed.y, cx, off, ccur, ncur);
         if (valid) {
             const uint32_t klo = (uint32_t)key, khi = (uint32_t)(key >> 32);
-            arcs[pa] = make_uint4(ed.y | ((cy ? 1u : 0u) << 31), (uint32_t)e, klo, khi);
-            arcs[pb] = make_uint4(ed.x | ((cx ? 1u : 0u) << 31), (uint32_t)e, klo, khi);
+            const uint32_t iy = !cy ? kNone : all_centers ? ed.y : cidx[ed.y];
+            const uint32_t ix = !cx ? kNone : all_centers ? ed.x : cidx[ed.x];
+            arcs[pa] = make_uint4(ed.y | ((cy ? 1u : 0u) << 31), iy, klo, khi);
+            arcs[pb] = make_uint4(ed.x | ((cx ? 1u : 0u) << 31), ix, klo, khi);
         }
     }
 }
@@ -255,7 +258,7 @@ int im_arc_keys(im_ctx* c, uint64_t salt) {
         const uint32_t n = c->n;
         IM_CUDA(c, cudaMemsetAsync(c->d_arc_cur, 0, 2 * (size_t)n * sizeof(uint32_t), c->stream));
         IM_LAUNCH(c, K_ARC_KEYS, k_arc_fill, grid_for(c->m, 256, 152u * 16u), 256, 0, c->d_edges, c->m, c->d_off,
-                  c->d_arc_cur, c->d_arc_cur + n, c->d_arcs, salt, c->d_cbits, (int)c->all_centers);
+                  c->d_arc_cur, c->d_arc_cur + n, c->d_arcs, salt, c->d_cbits, c->d_cidx, (int)c->all_centers);
     }
     IM_CUDA(c, cudaGetLastError());
     c->arc_salt = salt;

@@ -75,8 +75,10 @@ struct GraphView {
     uint64_t m;
     const uint2* edges;     // m (padded to even): (u, v)
     const uint64_t* off;    // n + 1 CSR offsets
-    const uint4* arcs;      // 2m: (neighbour | center bit << 31, edge id, key lo, key hi),
-                            // key = mix(salt ^ e); both rewritten by every build
+    const uint4* arcs;      // 2m: (neighbour | center bit << 31, neighbour's center index or
+                            // kNone, key lo, key hi), key = mix(salt ^ e); rewritten by every
+                            // build, arcs to centers first in each adjacency list
+    const uint32_t* ccnt;   // n: arcs to centers of each vertex (the first ccnt[x] of its list)
 };
 
 struct SketchView {
@@ -130,6 +132,8 @@ struct SelState {
     unsigned long long evals_mark;  // evals_total when the round started
     unsigned long long batches, refresh_batches;
     unsigned long long launches;    // kernels launched by the selection graph
+    unsigned int ticket;            // blocks of k_reduce_plan done (the last one plans)
+    unsigned int pending;           // a batch was evaluated and awaits its accounting
 };
 
 enum SelError : unsigned int {
@@ -144,8 +148,9 @@ enum SelMode : unsigned int {
     M_GATHER_CHUNK = 3,   // gather, one warp per (member, 32 sketches)
     M_HIST_CHUNK = 4,     // radix passes, gather, one warp per (member, 32 sketches)
     M_REFRESH = 5,        // gather, recompute the sketches
-    M_COUNT = 6,
-    M_NONE = 7            // no batch: the round is over
+    M_COUNT_ABOVE = 6,    // no batch yet: count the candidates above the best fresh key first
+    M_COUNT = 7,
+    M_NONE = 8            // no batch: the round is over
 };
 
 // Conditional-node handles of the selection graph; on == 0 outside the graph.

@@ -79,20 +79,28 @@ __device__ BfsOut warp_bfs_from(const GraphView& g, const SketchView& s, uint32_
     while (head < tail) {
         const uint32_t nv = min(32u, tail - head);
         uint64_t a0 = 0;
-        uint32_t deg = 0;
+        uint32_t deg = 0, cc = 0;
         if (lane < nv) {
             const uint32_t x = q[head + lane];
             a0 = g.off[x];
             deg = (uint32_t)(g.off[x + 1] - a0);
+            cc = g.ccnt[x];   // its arcs to centers, stored first
         }
-        uint32_t pre = deg;   // inclusive scan of the degrees
+        // The step's arcs in two runs: the arcs to centers of every frontier vertex, then the
+        // others, so that a live center anywhere in the frontier is met before any vertex's
+        // long tail of non-center arcs.  Inclusive scans of both lengths:
+        uint32_t preC = cc, preN = deg - cc;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(kFull, pre, d);
-            if ((int)lane >= d) pre += y;
+            const uint32_t yc = __shfl_up_sync(kFull, preC, d);
+            const uint32_t yn = __shfl_up_sync(kFull, preN, d);
+            if ((int)lane >= d) { preC += yc; preN += yn; }
         }
-        const uint32_t total = __shfl_sync(kFull, pre, 31);
-        pre -= deg;           // exclusive
+        const uint32_t totC = __shfl_sync(kFull, preC, 31);
+        const uint32_t total = totC + __shfl_sync(kFull, preN, 31);
+        preC -= cc;           // exclusive
+        preN -= deg - cc;
+        const uint64_t aN = a0 + cc;   // where the non-center arcs start
         head += nv;
         // four 32-arc chunks per step: their loads are in flight together
         for (uint32_t base = 0; base < total; base += 128) {
@@ -100,20 +108,27 @@ __device__ BfsOut warp_bfs_from(const GraphView& g, const SketchView& s, uint32_
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const uint32_t t = base + 32u * k + lane;
+                const bool inC = t < totC;
+                const uint32_t tt = inC ? t : t - totC;   // position within its run
                 uint32_t lo = 0;
-                if (nv > 1) {   // owner of arc t: the largest i < nv with pre_i <= t
+                if (nv > 1) {   // owner of arc tt in its run: the largest i < nv with pre_i <= tt
                     uint32_t hi = nv - 1;
 #pragma unroll
                     for (int it = 0; it < 5; ++it) {
                         const uint32_t mid = (lo + hi + 1) >> 1;
-                        const uint32_t pm = __shfl_sync(kFull, pre, mid);
-                        if (pm <= t) lo = mid; else hi = mid - 1;
+                        const uint32_t pc = __shfl_sync(kFull, preC, mid);
+                        const uint32_t pn = __shfl_sync(kFull, preN, mid);
+                        if ((inC ? pc : pn) <= tt) lo = mid; else hi = mid - 1;
                         if (lo > hi) hi = lo;
                     }
                 }
-                const uint64_t ao = __shfl_sync(kFull, a0, lo);
-                const uint32_t po = __shfl_sync(kFull, pre, lo);
-                arcs4[k] = (t < total) ? g.arcs[ao + (t - po)] : make_uint4(0, 0, 0, 0);
+                const uint64_t aoc = __shfl_sync(kFull, a0, lo);
+                const uint64_t aon = __shfl_sync(kFull, aN, lo);
+                const uint32_t poc = __shfl_sync(kFull, preC, lo);
+                const uint32_t pon = __shfl_sync(kFull, preN, lo);
+                const uint64_t ao = inC ? aoc : aon;
+                const uint32_t po = inC ? poc : pon;
+                arcs4[k] = (t < total) ? g.arcs[ao + (tt - po)] : make_uint4(0, 0, 0, 0);
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -121,17 +136,18 @@ __device__ BfsOut warp_bfs_from(const GraphView& g, const SketchView& s, uint32_
                 ++chunks;
                 const uint32_t t = base + 32u * k + lane;
                 bool live = false, cen = false;
-                uint32_t y = 0;
+                uint32_t y = 0, ci = 0;
                 if (t < total) {
                     const uint4 arc = arcs4[k];
                     y = arc.x & kArcIdMask;
                     cen = arc.x >> 31;
+                    ci = arc.y;
                     live = edge_live_fast(s.smp, ((uint64_t)arc.w << 32) | arc.z, rg);
                 }
                 const unsigned cb = __ballot_sync(kFull, live && cen);
                 if (cb) {
-                    const uint32_t yc = __shfl_sync(kFull, y, __ffs(cb) - 1);
-                    o.label = s.label[(size_t)center_index(s, yc) * s.R + r];
+                    const uint32_t c0 = __shfl_sync(kFull, ci, __ffs(cb) - 1);   // the arc's center index
+                    o.label = s.label[(size_t)c0 * s.R + r];
                     if (lane == 0 && st_counters) atomicAdd(&st_counters->hop2_chunks, (unsigned long long)chunks);
                     return o;
                 }
@@ -276,42 +292,6 @@ __global__ void k_init_keys(const uint64_t* __restrict__ gain0, uint32_t n, uint
         size[i] &= ~kCovered;
 }
 
-// best = max fresh key (evaluated this round), stale_max / n_unev over the others.  At the
-// start of a round (open_batches) it also opens the graph's batch loop, whose first pass
-// decides whether the round needs any batch.
-__global__ void __launch_bounds__(256)
-k_reduce(const uint64_t* __restrict__ key, const uint32_t* __restrict__ stamp,
-         const uint8_t* __restrict__ seedflag, uint32_t n, SelState* st, SelHandles hd,
-         int open_batches) {
-    if (open_batches && hd.on && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(hd.batch, 1u);
-    const uint32_t round = st->round;
-    unsigned long long bf = 0, sm = 0, cnt = 0;
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        if (seedflag[v]) continue;
-        const unsigned long long k = key[v];
-        if (stamp[v] == round) bf = max(bf, k);
-        else { sm = max(sm, k); ++cnt; }
-    }
-#pragma unroll
-    for (int d = 16; d; d >>= 1) {
-        bf = max(bf, __shfl_xor_sync(kFull, bf, d));
-        sm = max(sm, __shfl_xor_sync(kFull, sm, d));
-        cnt += __shfl_xor_sync(kFull, cnt, d);
-    }
-    __shared__ unsigned long long s_bf[8], s_sm[8], s_cnt[8];
-    const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) { s_bf[w] = bf; s_sm[w] = sm; s_cnt[w] = cnt; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
-            bf = max(bf, s_bf[i]); sm = max(sm, s_sm[i]); cnt += s_cnt[i];
-        }
-        if (bf) atomicMax(&st->best, bf);
-        if (sm) atomicMax(&st->stale_max, sm);
-        if (cnt) atomicAdd(&st->n_unev, cnt);
-    }
-}
-
 // Unevaluated candidates whose stale key beats the best fresh key of the round: an upper
 // bound on what is left to evaluate in this round (the winner's fresh key is >= best).
 __global__ void __launch_bounds__(256)
@@ -336,112 +316,190 @@ k_count_above(const uint64_t* __restrict__ key, const uint32_t* __restrict__ sta
     }
 }
 
+constexpr uint32_t kPending = 0x80000000u;   // stamp bit: batch member awaiting its fresh key
+
 // Next step of the round, decided from the state the last reduction left (Alg. 2's stop
 // test; Alg. 4's doubling batch size): either a batch of ~B of the largest stale keys, picked
 // by radix selection on the key bytes below the top byte of stale_max (all of them when at
 // most 2B remain, exactly the top key when B = 1), or the end of the round, whose winner
 // (the best fresh key) is recorded.  Large batches are evaluated by recomputing the sketches
-// (M_REFRESH) instead of by searches.  Errors stop the selection.  One thread decides; the
-// block clears the radix histogram.
-__global__ void __launch_bounds__(256)
-k_plan(SelState* st, uint32_t* __restrict__ batch, unsigned long long* __restrict__ fresh,
-       uint32_t* __restrict__ seed_list, uint64_t* __restrict__ gain_list,
-       uint64_t* __restrict__ round_evals, uint32_t n, uint32_t R, uint32_t bits, SelHandles hd) {
-    if (threadIdx.x == 0) {
-        unsigned cont = 0, mode = M_NONE;
-        const unsigned long long nu = st->n_unev, smax = st->stale_max, best = st->best;
-        const unsigned j = st->j;
-        const uint64_t mask = (1ull << bits) - 1ull;
-        if (!st->err && st->fb_overflow) st->err = SEL_FB_OVERFLOW;
-        if (!st->err && j > 0 && st->batch_n == 0) st->err = SEL_NO_PROGRESS;
-        if (!st->err && nu > 0 && best <= smax) {
-            if (j > 81) st->err = SEL_NO_PROGRESS;   // doubling covers any n within 64 batches
-            else cont = 1;
+// (M_REFRESH) instead of by searches; that choice needs the number of candidates above the
+// best fresh key, which a first M_COUNT_ABOVE step counts.  Errors stop the selection.  Run
+// by one thread; sets the selection graph's batch loop and batch switch.
+__device__ void plan_step(SelState* st, uint32_t* __restrict__ batch, unsigned long long* __restrict__ fresh,
+                          uint64_t* __restrict__ key, uint32_t* __restrict__ stamp,
+                          uint32_t* __restrict__ seed_list, uint64_t* __restrict__ gain_list,
+                          uint64_t* __restrict__ round_evals, uint32_t n, uint32_t R, uint32_t bits,
+                          const SelHandles& hd, bool have_count) {
+    unsigned cont = 0, mode = M_NONE;
+    const unsigned long long nu = __ldcg(&st->n_unev), smax = __ldcg(&st->stale_max), best = __ldcg(&st->best);
+    const unsigned j = st->j;
+    const uint64_t mask = (1ull << bits) - 1ull;
+    if (st->pending) {   // the batch evaluated since the last step
+        st->pending = 0;
+        const unsigned bn = st->batch_n;
+        st->evals_total += bn;
+        st->fb_total += min(__ldcg(&st->fb_n), 0xFFFFFFFFu);
+        st->fb_n = 0;    // the fallback kernel has run; MarkSeed may queue its own searches
+        if (!st->err && bn == 0) st->err = SEL_NO_PROGRESS;
+    }
+    if (!st->err && __ldcg(&st->fb_overflow)) st->err = SEL_FB_OVERFLOW;
+    if (!st->err && nu > 0 && best <= smax) {
+        if (j > 81) st->err = SEL_NO_PROGRESS;   // doubling covers any n within 64 batches
+        else cont = 1;
+    }
+    if (cont && best && !have_count) {
+        mode = M_COUNT_ABOVE;
+        st->count_above = 0;
+    } else if (cont) {
+        unsigned long long B = 1ull << (j < 40 ? j : 40);
+        if (B > nu) B = nu;
+        unsigned long long expect = 2 * B < nu ? 2 * B : nu;
+        // When many candidates could still beat the best fresh key (or the doubling batch
+        // has grown large), evaluate every one of them at once by recomputing the sketches;
+        // the round then ends, since all remaining stale keys are below the new best.
+        const unsigned long long rmin = st->refresh_min;
+        const unsigned long long above = __ldcg(&st->count_above);
+        const bool refresh = expect >= rmin || (best && above >= rmin);
+        if (refresh) {
+            B = nu;
+            expect = best ? above : nu;
         }
-        if (cont) {
-            unsigned long long B = 1ull << (j < 40 ? j : 40);
-            if (B > nu) B = nu;
-            unsigned long long expect = 2 * B < nu ? 2 * B : nu;
-            // When many candidates could still beat the best fresh key (or the doubling batch
-            // has grown large), evaluate every one of them at once by recomputing the
-            // sketches; the round then ends, since all remaining stale keys are below the new best.
-            const unsigned long long rmin = st->refresh_min;
-            const bool refresh = expect >= rmin || (best && st->count_above >= rmin);
-            if (refresh) {
-                B = nu;
-                expect = best ? st->count_above : nu;
-            }
-            st->borig = B;
-            st->need = B;
-            st->taken = 0;
-            st->prefix = 0;
-            st->theta = 0;
-            st->pass_blocks = 0;
-            bool hist = false, direct = false;
-            if (nu <= 2 * B || smax == 0) {
-                st->done = 1;                // take every unevaluated candidate
-                st->shift = 0;
-                st->prefmask = 0;
-            } else if (B == 1) {
-                st->done = 1;                // keys are distinct: exactly the top stale key
-                st->theta = smax;
-                st->shift = 0;
-                st->prefmask = 0;
-                direct = best < smax;        // no gather needed: the key names the vertex
-            } else {
-                const int top = 63 - __clzll((long long)smax);
-                const int shift = (top / 8) * 8;
-                st->shift = shift;
-                st->prefmask = (shift + 8 >= 64) ? 0ull : ~((1ull << (shift + 8)) - 1ull);
-                st->done = 0;
-                hist = true;
-            }
-            st->batch_n = 0;
-            st->eval_next = 0;
-            st->fb_n = 0;
-            st->best_prev = best;
-            st->best = 0;
-            st->stale_max = 0;
-            st->n_unev = 0;
-            st->count_above = 0;
-            if (direct) {
-                batch[0] = (uint32_t)(mask - (smax & mask));
-                fresh[0] = 0;
-                st->batch_n = 1;
-            }
-            const bool single = expect * R <= kSingleTasks;
-            mode = refresh ? M_REFRESH
-                 : direct  ? M_DIRECT
-                 : single  ? (hist ? M_HIST_SINGLE : M_GATHER_SINGLE)
-                           : (hist ? M_HIST_CHUNK : M_GATHER_CHUNK);
-            st->j = j + 1;
-            st->batches++;
-            if (refresh) st->refresh_batches++;
-            st->launches += hd.launches[mode];
-        } else if (!st->err) {
-            // the round is over: the best fresh key beats every stale one
-            const uint32_t sd = (uint32_t)(mask - (best & mask));
-            if (best == 0) {
-                st->err = SEL_NO_CANDIDATE;
-            } else if (sd >= n) {
-                st->err = SEL_RANGE;
-            } else {
-                const uint32_t rd = st->round;
-                st->sd = sd;
-                seed_list[rd] = sd;
-                gain_list[rd] = best >> bits;
-                round_evals[rd] = st->evals_total - st->evals_mark;
-            }
+        st->borig = B;
+        st->need = B;
+        st->taken = 0;
+        st->prefix = 0;
+        st->theta = 0;
+        st->pass_blocks = 0;
+        bool hist = false, direct = false;
+        if (nu <= 2 * B || smax == 0) {
+            st->done = 1;                // take every unevaluated candidate
+            st->shift = 0;
+            st->prefmask = 0;
+        } else if (B == 1) {
+            st->done = 1;                // keys are distinct: exactly the top stale key
+            st->theta = smax;
+            st->shift = 0;
+            st->prefmask = 0;
+            direct = best < smax;        // no gather needed: the key names the vertex
+        } else {
+            const int top = 63 - __clzll((long long)smax);
+            const int shift = (top / 8) * 8;
+            st->shift = shift;
+            st->prefmask = (shift + 8 >= 64) ? 0ull : ~((1ull << (shift + 8)) - 1ull);
+            st->done = 0;
+            hist = true;
         }
-        st->cont = cont;
-        st->mode = mode;
-        st->launches += 1;
-        if (hd.on) {
-            cudaGraphSetConditional(hd.batch, cont);
-            cudaGraphSetConditional(hd.mode, mode);
+        st->batch_n = 0;
+        st->eval_next = 0;
+        st->fb_n = 0;
+        st->best_prev = best;
+        st->best = 0;
+        st->stale_max = 0;
+        st->n_unev = 0;
+        st->count_above = 0;
+        if (direct) {
+            const uint32_t x = (uint32_t)(mask - (smax & mask));
+            batch[0] = x;
+            fresh[0] = 0;
+            key[x] = 0;                       // its batch slot
+            stamp[x] = st->round | kPending;
+            st->batch_n = 1;
+        }
+        const bool single = expect * R <= kSingleTasks;
+        mode = refresh ? M_REFRESH
+             : direct  ? M_DIRECT
+             : single  ? (hist ? M_HIST_SINGLE : M_GATHER_SINGLE)
+                       : (hist ? M_HIST_CHUNK : M_GATHER_CHUNK);
+        st->pending = 1;
+        st->j = j + 1;
+        st->batches++;
+        if (refresh) st->refresh_batches++;
+    } else if (!st->err) {
+        // the round is over: the best fresh key beats every stale one
+        const uint32_t sd = (uint32_t)(mask - (best & mask));
+        if (best == 0) {
+            st->err = SEL_NO_CANDIDATE;
+        } else if (sd >= n) {
+            st->err = SEL_RANGE;
+        } else {
+            const uint32_t rd = st->round;
+            st->sd = sd;
+            seed_list[rd] = sd;
+            gain_list[rd] = best >> bits;
+            round_evals[rd] = st->evals_total - st->evals_mark;
         }
     }
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) st->hist[i] = 0;
+    st->cont = cont;
+    st->mode = mode;
+    if (cont) st->launches += hd.launches[mode];
+    if (hd.on) {
+        cudaGraphSetConditional(hd.batch, cont);
+        cudaGraphSetConditional(hd.mode, mode);
+    }
+}
+
+// The planning step after k_count_above.
+__global__ void k_decide(SelState* st, uint32_t* __restrict__ batch, unsigned long long* __restrict__ fresh,
+                         uint64_t* __restrict__ key, uint32_t* __restrict__ stamp,
+                         uint32_t* __restrict__ seed_list, uint64_t* __restrict__ gain_list,
+                         uint64_t* __restrict__ round_evals, uint32_t n, uint32_t R, uint32_t bits,
+                         SelHandles hd) {
+    if (threadIdx.x == 0)
+        plan_step(st, batch, fresh, key, stamp, seed_list, gain_list, round_evals, n, R, bits, hd, true);
+}
+
+// One pass over the candidates: the members of the batch just evaluated (stamp kPending, key
+// = their batch slot) receive their fresh keys; then best = max fresh key of the round,
+// stale_max / n_unev over the others.  The last block to finish plans the next step.
+__global__ void __launch_bounds__(256)
+k_reduce_plan(uint64_t* __restrict__ key, uint32_t* __restrict__ stamp, const uint8_t* __restrict__ seedflag,
+              SelState* st, uint32_t* __restrict__ batch, unsigned long long* __restrict__ fresh,
+              uint32_t* __restrict__ seed_list, uint64_t* __restrict__ gain_list,
+              uint64_t* __restrict__ round_evals, uint32_t n, uint32_t R, uint32_t bits, SelHandles hd) {
+    __shared__ unsigned long long s_bf[8], s_sm[8], s_cnt[8];
+    __shared__ int s_last;
+    const uint32_t round = st->round;
+    unsigned long long bf = 0, sm = 0, cnt = 0;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        if (seedflag[v]) continue;
+        unsigned long long k = key[v];
+        uint32_t sp = stamp[v];
+        if (sp & kPending) {   // evaluated in this batch: its fresh key (Alg. 2)
+            k = pack_key(fresh[(uint32_t)k], v, bits);
+            key[v] = k;
+            stamp[v] = round;
+            sp = round;
+        }
+        if (sp == round) bf = max(bf, k);
+        else { sm = max(sm, k); ++cnt; }
+    }
+#pragma unroll
+    for (int d = 16; d; d >>= 1) {
+        bf = max(bf, __shfl_xor_sync(kFull, bf, d));
+        sm = max(sm, __shfl_xor_sync(kFull, sm, d));
+        cnt += __shfl_xor_sync(kFull, cnt, d);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { s_bf[w] = bf; s_sm[w] = sm; s_cnt[w] = cnt; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+            bf = max(bf, s_bf[i]); sm = max(sm, s_sm[i]); cnt += s_cnt[i];
+        }
+        if (bf) atomicMax(&st->best, bf);
+        if (sm) atomicMax(&st->stale_max, sm);
+        if (cnt) atomicAdd(&st->n_unev, cnt);
+        __threadfence();
+        s_last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        st->ticket = 0;
+        plan_step(st, batch, fresh, key, stamp, seed_list, gain_list, round_evals, n, R, bits, hd, false);
+    }
 }
 
 // One radix pass over the unevaluated candidates: block histograms of the next key byte,
@@ -512,8 +570,7 @@ k_sel_pass(const uint64_t* __restrict__ key, const uint32_t* __restrict__ stamp,
 }
 
 __global__ void __launch_bounds__(256)
-k_gather(const uint64_t* __restrict__ key, const uint32_t* __restrict__ stamp,
-         const uint8_t* __restrict__ seedflag, uint32_t n, SelState* st,
+k_gather(uint64_t* key, uint32_t* stamp, const uint8_t* __restrict__ seedflag, uint32_t n, SelState* st,
          uint32_t* __restrict__ batch, unsigned long long* __restrict__ fresh) {
     const uint32_t round = st->round;
     // a candidate whose stale key is below the best fresh key cannot win (keys are distinct)
@@ -533,6 +590,8 @@ k_gather(const uint64_t* __restrict__ key, const uint32_t* __restrict__ stamp,
             const uint32_t j = pos0 + __popc(bal & ((1u << lane) - 1u));
             batch[j] = v;
             fresh[j] = 0;
+            key[v] = j;                      // its batch slot, until k_reduce_plan
+            stamp[v] = round | kPending;
         }
     }
 }
@@ -618,23 +677,6 @@ k_eval_single(GraphView g, SketchView s, SelState* st, const uint32_t* __restric
         }
         if (lane == 0 && d) atomicAdd(fresh + j, d);
         __syncwarp();
-    }
-}
-
-__global__ void __launch_bounds__(256)
-k_finalize(SelState* st, const uint32_t* __restrict__ batch,
-           const unsigned long long* __restrict__ fresh, uint64_t* __restrict__ key,
-           uint32_t* __restrict__ stamp, uint32_t bits) {
-    const uint32_t bn = st->batch_n, round = st->round;
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < bn; j += gridDim.x * blockDim.x) {
-        const uint32_t x = batch[j];
-        key[x] = pack_key(fresh[j], x, bits);
-        stamp[x] = round;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        st->evals_total += bn;
-        st->fb_total += min(st->fb_n, 0xFFFFFFFFu);
-        st->fb_n = 0;   // the fallback kernel has run; MarkSeed may queue its own searches
     }
 }
 
@@ -739,18 +781,19 @@ k_fallback(GraphView g, SketchView s, SelState* st, const FbTask* __restrict__ f
             for (uint64_t base = a0; base < a1; base += 32) {
                 const uint64_t a = base + lane;
                 bool live = false;
-                uint32_t y = 0;
+                uint32_t y = 0, ci = 0;
                 bool cen = false;
                 if (a < a1) {
                     const uint4 arc = g.arcs[a];
                     y = arc.x & kArcIdMask;
                     cen = arc.x >> 31;
+                    ci = arc.y;
                     live = edge_live_fast(s.smp, ((uint64_t)arc.w << 32) | arc.z, (uint64_t)(r + 1u) * kGamma);
                 }
                 const unsigned cb = __ballot_sync(kFull, live && cen);
                 if (cb) {
-                    const uint32_t yc = __shfl_sync(kFull, y, __ffs(cb) - 1);
-                    label = s.label[(size_t)center_index(s, yc) * s.R + r];
+                    const uint32_t c0 = __shfl_sync(kFull, ci, __ffs(cb) - 1);   // the arc's center index
+                    label = s.label[(size_t)c0 * s.R + r];
                     break;
                 }
                 bool fresh_v = false;
@@ -868,6 +911,7 @@ k_spread_dedup(const uint64_t* __restrict__ pairs, uint32_t k, uint32_t kp2,
 GraphView graph_view(const im_ctx* c) {
     GraphView g;
     g.n = c->n; g.m = c->m; g.edges = c->d_edges; g.off = c->d_off; g.arcs = c->d_arcs;
+    g.ccnt = c->d_arc_cur;   // the arc fill's front cursors: arcs to centers per vertex
     return g;
 }
 
@@ -936,7 +980,14 @@ int max_radix_passes(const im_ctx* c) {
 
 // The launches of one batch of the given mode (the body of the graph's switch); passes =
 // radix passes to queue (each returns at once once the threshold is fixed).
-int enqueue_mode(im_ctx* c, unsigned mode, int passes) {
+int launch_reduce_plan(im_ctx* c, const SelHandles& hd) {
+    IM_LAUNCH(c, K_REDUCE, k_reduce_plan, grid_for(c->n, 256, 152u * 8u), 256, 0, c->d_key, c->d_stamp,
+              c->d_seedflag, c->d_sel, c->d_batch, (unsigned long long*)c->d_fresh, c->d_seed_list,
+              c->d_gain_list, c->d_round_evals, c->n, c->R, c->key_bits, hd);
+    return IM_OK;
+}
+
+int enqueue_mode(im_ctx* c, unsigned mode, int passes, const SelHandles& hd) {
     const uint32_t n = c->n;
     const unsigned T = 256;
     const unsigned gridn = grid_for(n, T, 152u * 8u);
@@ -944,26 +995,29 @@ int enqueue_mode(im_ctx* c, unsigned mode, int passes) {
     const SketchView s = sketch_view(c);
     SelState* st = c->d_sel;
     unsigned long long* fresh = (unsigned long long*)c->d_fresh;
+    if (mode == M_COUNT_ABOVE) {
+        IM_LAUNCH(c, K_COUNT_ABOVE, k_count_above, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n, st);
+        IM_LAUNCH(c, K_SEL_INIT, k_decide, 1, 32, 0, st, c->d_batch, fresh, c->d_key, c->d_stamp, c->d_seed_list,
+                  c->d_gain_list, c->d_round_evals, n, c->R, c->key_bits, hd);
+        return IM_OK;
+    }
     if (mode == M_HIST_SINGLE || mode == M_HIST_CHUNK)
         for (int p = 0; p < passes; ++p)
             IM_LAUNCH(c, K_SEL_HIST, k_sel_pass, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n, st);
     if (mode != M_DIRECT)
         IM_LAUNCH(c, K_GATHER, k_gather, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n, st, c->d_batch,
                   fresh);
-    unsigned fin_grid = grid_for(n, T, 152u * 4u);
     switch (mode) {
     case M_DIRECT:
         IM_LAUNCH(c, K_EVAL, k_eval_single, search_grid(c->R), kEvalWarps * 32, 0, g, s, st, c->d_batch, fresh,
                   c->d_fb_tasks, c->fb_cap);
         launch_fallback(c, g, s);
-        fin_grid = 1;
         break;
     case M_GATHER_SINGLE:
     case M_HIST_SINGLE:
         IM_LAUNCH(c, K_EVAL, k_eval_single, search_grid(kSingleTasks), kEvalWarps * 32, 0, g, s, st, c->d_batch,
                   fresh, c->d_fb_tasks, c->fb_cap);
         launch_fallback(c, g, s);
-        fin_grid = grid_for(kSingleTasks, T);
         break;
     case M_GATHER_CHUNK:
     case M_HIST_CHUNK: {
@@ -981,23 +1035,7 @@ int enqueue_mode(im_ctx* c, unsigned mode, int passes) {
     default:
         return im_fail(c, IM_EDEVICE, "unknown batch mode");
     }
-    IM_LAUNCH(c, K_FINALIZE, k_finalize, fin_grid, T, 0, st, c->d_batch, (const unsigned long long*)fresh,
-              c->d_key, c->d_stamp, c->key_bits);
-    IM_LAUNCH(c, K_REDUCE, k_reduce, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n, st, SelHandles{}, 0);
-    IM_LAUNCH(c, K_COUNT_ABOVE, k_count_above, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n, st);
-    return IM_OK;
-}
-
-int launch_plan(im_ctx* c, const SelHandles& hd) {
-    IM_LAUNCH(c, K_SEL_INIT, k_plan, 1, 256, 0, c->d_sel, c->d_batch, (unsigned long long*)c->d_fresh,
-              c->d_seed_list, c->d_gain_list, c->d_round_evals, c->n, c->R, c->key_bits, hd);
-    return IM_OK;
-}
-
-int launch_round_start(im_ctx* c, const SelHandles& hd) {
-    IM_LAUNCH(c, K_REDUCE, k_reduce, grid_for(c->n, 256, 152u * 8u), 256, 0, c->d_key, c->d_stamp,
-              c->d_seedflag, c->n, c->d_sel, hd, 1);
-    return IM_OK;
+    return launch_reduce_plan(c, hd);
 }
 
 int launch_mark(im_ctx* c, const SelHandles& hd) {
@@ -1009,8 +1047,8 @@ int launch_mark(im_ctx* c, const SelHandles& hd) {
     return IM_OK;
 }
 
-int cap_begin(im_ctx* c, cudaGraph_t graph) {
-    IM_CUDA(c, cudaStreamBeginCaptureToGraph(c->cap_stream, graph, nullptr, nullptr, 0,
+int cap_begin(im_ctx* c, cudaGraph_t graph, const cudaGraphNode_t* deps, size_t ndeps) {
+    IM_CUDA(c, cudaStreamBeginCaptureToGraph(c->cap_stream, graph, deps, nullptr, ndeps,
                                              cudaStreamCaptureModeRelaxed));
     c->cur = c->cap_stream;
     c->capturing = true;
@@ -1022,6 +1060,31 @@ int cap_end(im_ctx* c) {
     c->capturing = false;
     c->cur = c->stream;
     IM_CUDA(c, cudaStreamEndCapture(c->cap_stream, &out));
+    return IM_OK;
+}
+
+// The single node the capture currently ends at.
+int cap_frontier(im_ctx* c, cudaGraphNode_t* node) {
+    cudaStreamCaptureStatus status;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    IM_CUDA(c, cudaStreamGetCaptureInfo(c->cap_stream, &status, nullptr, nullptr, &deps, nullptr, &ndeps));
+    if (status != cudaStreamCaptureStatusActive || ndeps != 1) return im_fail(c, IM_ECUDA, "selection graph capture");
+    *node = deps[0];
+    return IM_OK;
+}
+
+// A conditional node without dependencies, added to a graph directly.
+int add_conditional(im_ctx* c, cudaGraph_t graph, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                    unsigned size, cudaGraph_t* bodies, cudaGraphNode_t* node) {
+    cudaGraphNodeParams prm = {cudaGraphNodeTypeConditional};
+    memset(&prm, 0, sizeof prm);   // reserved fields and padding must be zero
+    prm.type = cudaGraphNodeTypeConditional;
+    prm.conditional.handle = h;
+    prm.conditional.type = type;
+    prm.conditional.size = size;
+    IM_CUDA(c, cudaGraphAddNode(node, graph, nullptr, nullptr, 0, &prm));
+    for (unsigned i = 0; i < size; ++i) bodies[i] = prm.conditional.phGraph_out[i];
     return IM_OK;
 }
 
@@ -1050,10 +1113,12 @@ int cap_conditional(im_ctx* c, cudaGraphConditionalHandle h, cudaGraphConditiona
 }
 
 // The whole lazy-greedy loop as one graph, so that rounds run back to back without the host:
-//   sel_begin; while (round) { reduce; while (batch) { plan; switch (mode) { batch kinds } };
-//                              mark_seed; fallback }
-// Every decision is taken by k_plan / k_mark_seed on the device.  Both loops are bounded:
-// a round ends after at most 82 batches (k_plan), the selection after round_end rounds.
+//   sel_begin;
+//   while (round) { reduce_plan;
+//                   while (batch) { switch (mode) { batch kinds, each ending in reduce_plan } };
+//                   mark_seed; fallback }
+// Every decision is taken on the device (k_reduce_plan / k_decide, k_mark_seed).  Both loops
+// are bounded: a round ends after at most 82 batches, the selection after round_end rounds.
 int build_select_graph_steps(im_ctx* c) {
     SelHandles hd{};
     hd.on = 1;
@@ -1063,11 +1128,11 @@ int build_select_graph_steps(im_ctx* c) {
     int rc = IM_OK;
     for (unsigned m = 0; m < M_COUNT && !rc; ++m) {
         c->dry_count = 0;
-        rc = enqueue_mode(c, m, passes);
+        rc = enqueue_mode(c, m, passes, hd);
         hd.launches[m] = (unsigned)c->dry_count;
     }
     c->dry_count = 0;
-    if (!rc) rc = launch_round_start(c, hd);
+    if (!rc) rc = launch_reduce_plan(c, hd);
     if (!rc) rc = launch_mark(c, hd);
     hd.round_launches = (unsigned)c->dry_count;
     c->count_only = false;
@@ -1076,27 +1141,33 @@ int build_select_graph_steps(im_ctx* c) {
     IM_CUDA(c, cudaGraphCreate(&c->sel_graph, 0));
     IM_CUDA(c, cudaGraphConditionalHandleCreate(&hd.round, c->sel_graph, 0, 0));
     cudaGraph_t wround = nullptr, wbatch = nullptr, cases[M_COUNT] = {};
-    if ((rc = cap_begin(c, c->sel_graph))) return rc;
+    if ((rc = cap_begin(c, c->sel_graph, nullptr, 0))) return rc;
     IM_LAUNCH(c, K_SEL_BEGIN, k_sel_begin, 1, 32, 0, c->d_sel, hd);
     if ((rc = cap_conditional(c, hd.round, cudaGraphCondTypeWhile, 1, &wround))) return rc;
     if ((rc = cap_end(c))) return rc;
 
+    // round body: the batch loop is added first, so that its switch's handle exists before
+    // the round's first reduce_plan (which sets it) is captured in front of it
     IM_CUDA(c, cudaGraphConditionalHandleCreate(&hd.batch, wround, 0, 0));
-    if ((rc = cap_begin(c, wround))) return rc;
-    if ((rc = launch_round_start(c, hd))) return rc;
-    if ((rc = cap_conditional(c, hd.batch, cudaGraphCondTypeWhile, 1, &wbatch))) return rc;
+    cudaGraphNode_t wnode = nullptr;
+    if ((rc = add_conditional(c, wround, hd.batch, cudaGraphCondTypeWhile, 1, &wbatch, &wnode))) return rc;
+    IM_CUDA(c, cudaGraphConditionalHandleCreate(&hd.mode, wbatch, M_NONE, 0));
+    if ((rc = cap_begin(c, wround, nullptr, 0))) return rc;
+    if ((rc = launch_reduce_plan(c, hd))) return rc;
+    cudaGraphNode_t last = nullptr;
+    if ((rc = cap_frontier(c, &last))) return rc;
+    if ((rc = cap_end(c))) return rc;
+    IM_CUDA(c, cudaGraphAddDependencies(wround, &last, &wnode, nullptr, 1));
+    if ((rc = cap_begin(c, wround, &wnode, 1))) return rc;
     if ((rc = launch_mark(c, hd))) return rc;
     if ((rc = cap_end(c))) return rc;
 
-    IM_CUDA(c, cudaGraphConditionalHandleCreate(&hd.mode, wbatch, M_NONE, 0));
-    if ((rc = cap_begin(c, wbatch))) return rc;
-    if ((rc = launch_plan(c, hd))) return rc;
+    if ((rc = cap_begin(c, wbatch, nullptr, 0))) return rc;
     if ((rc = cap_conditional(c, hd.mode, cudaGraphCondTypeSwitch, M_COUNT, cases))) return rc;
     if ((rc = cap_end(c))) return rc;
-
     for (unsigned m = 0; m < M_COUNT; ++m) {
-        if ((rc = cap_begin(c, cases[m]))) return rc;
-        if ((rc = enqueue_mode(c, m, passes))) return rc;
+        if ((rc = cap_begin(c, cases[m], nullptr, 0))) return rc;
+        if ((rc = enqueue_mode(c, m, passes, hd))) return rc;
         if ((rc = cap_end(c))) return rc;
     }
     IM_CUDA(c, cudaGraphInstantiate(&c->sel_exec, c->sel_graph, 0));
@@ -1131,21 +1202,20 @@ const char* sel_error_text(unsigned e) {
     }
 }
 
-// The same rounds driven from the host: one synchronisation per batch to read k_plan's decision.
+// The same rounds driven from the host: one synchronisation per step to read the decision.
 int run_rounds_host(im_ctx* c) {
     const SelHandles none{};
     for (;;) {
         int rc = pull_state(c);
         if (rc) return rc;
         if (c->h_sel->err || c->h_sel->round >= c->h_sel->round_end) return IM_OK;
-        if ((rc = launch_round_start(c, none))) return rc;
+        if ((rc = launch_reduce_plan(c, none))) return rc;
         for (;;) {
-            if ((rc = launch_plan(c, none))) return rc;
             if ((rc = pull_state(c))) return rc;
             const SelState& h = *c->h_sel;
             if (!h.cont) break;
             const int passes = h.mode == M_HIST_SINGLE || h.mode == M_HIST_CHUNK ? h.shift / 8 + 1 : 0;
-            if ((rc = enqueue_mode(c, h.mode, passes))) return rc;
+            if ((rc = enqueue_mode(c, h.mode, passes, none))) return rc;
         }
         if ((rc = launch_mark(c, none))) return rc;
     }
