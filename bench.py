@@ -347,6 +347,7 @@ def run_ours(args, n, u, v, prm):
             "sketch_pairs_per_s": pairs / (ms_build / 1e3),
             "evaluations": int(st["evaluations"]),
             "refresh_batches": int(st["refresh_batches"]),
+            "spec_batches": int(st["spec_batches"]),
             "roofline": roof,
             "kernel_rooflines": list(roofs.values()),
             "cpu_baseline": cpu,

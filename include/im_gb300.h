@@ -139,6 +139,8 @@ typedef struct {
     uint64_t refresh_batches;       /* batches evaluated by recomputing the sketches        */
     uint64_t live_pairs;            /* live (edge, sketch) pairs unioned since im_create    */
     uint64_t build_live_pairs;      /* of those, unioned by the last im_build_sketches      */
+    uint64_t spec_batches;          /* batches evaluated from a candidate first seed's
+                                       overlaps (see im_set_seed_speculation)             */
 } im_stats;
 
 int im_get_stats(im_ctx* ctx, im_stats* out);
@@ -212,6 +214,15 @@ int im_set_pipeline(im_ctx* ctx, uint32_t lanes);
  * without the host; 0: the host launches every batch after reading the device's decision.
  * Both run the same kernels and give identical results. */
 int im_set_graph(im_ctx* ctx, int on);
+
+/* Tuning: while building, also sum for `candidates` likely first seeds c -- the vertices with
+ * the largest gains over the first batch of sketches, ties to the smaller id --
+ * ov_c(v) = sum_r |C_r(v)| [c in C_r(v)].  If the first seed is one of them, the second round's
+ * batches are evaluated as Marginal(v | {c}) = gain0(v) - ov_c(v) (exact) instead of by
+ * searches or by recomputing the sketches.  0 disables; default 4, at most 8; costs 8 n bytes
+ * per candidate; needs the single-lane pipeline; takes effect at the next im_build_sketches.
+ * Seeds, gains and evaluation counts do not depend on it. */
+int im_set_seed_speculation(im_ctx* ctx, uint32_t candidates);
 
 /* The context's stream (a cudaStream_t). */
 void* im_stream(im_ctx* ctx);

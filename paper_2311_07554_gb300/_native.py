@@ -34,7 +34,7 @@ class im_stats(ctypes.Structure):
                 ("sketch_batch", ctypes.c_uint32), ("hop1_arcs", ctypes.c_uint64),
                 ("hop2_searches", ctypes.c_uint64), ("hop2_chunks", ctypes.c_uint64),
                 ("refresh_batches", ctypes.c_uint64), ("live_pairs", ctypes.c_uint64),
-                ("build_live_pairs", ctypes.c_uint64)]
+                ("build_live_pairs", ctypes.c_uint64), ("spec_batches", ctypes.c_uint64)]
 
 
 def lib():
@@ -69,6 +69,7 @@ def lib():
         "im_set_refresh_threshold": ([vp, u64], i32),
         "im_set_pipeline": ([vp, u32], i32),
         "im_set_graph": ([vp, i32], i32),
+        "im_set_seed_speculation": ([vp, u32], i32),
         "im_stream": ([vp], vp),
         "im_sketch_static": ([u32, u64, vp, vp, u64, dbl, u32, vp, vp, vp], i32),
         "im_last_error": ([vp], c.c_char_p),
@@ -221,6 +222,10 @@ def im_set_pipeline(ctx, lanes: int):
 
 def im_set_graph(ctx, on: bool):
     _check(ctx, lib().im_set_graph(ctx, 1 if on else 0))
+
+
+def im_set_seed_speculation(ctx, candidates: int):
+    _check(ctx, lib().im_set_seed_speculation(ctx, candidates))
 
 
 def im_stream(ctx) -> int:

@@ -54,6 +54,7 @@ void free_sketch_state(im_ctx* c) {
     im_select_graph_free(c);   // the graph holds pointers to the buffers freed here
     for (auto& L : c->lane) {
         dfree(L.parent); dfree(L.word); dfree(L.live); dfree(L.live_n); dfree(L.gain); dfree(L.fresh);
+        dfree(L.spec_ov);
     }
     c->live_cap = 0;
     dfree(c->d_fb_queue); dfree(c->d_fb_bits); dfree(c->d_fb_tasks);
@@ -226,6 +227,13 @@ int im_set_sketch_batch(im_ctx* c, uint32_t batch) {
     return IM_OK;
 }
 
+int im_set_seed_speculation(im_ctx* c, uint32_t candidates) {
+    if (!c) return IM_EINVAL;
+    if (candidates > kSpecMax) return im_fail(c, IM_EINVAL, "at most 8 candidate first seeds");
+    c->spec_req = candidates;
+    return IM_OK;
+}
+
 int im_set_graph(im_ctx* c, int on) {
     if (!c) return IM_EINVAL;
     c->use_graph = on != 0;
@@ -290,10 +298,12 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
         live_cap = (uint64_t)cap;
     }
     const size_t nc = (size_t)rho * R;
+    // candidate first seeds need the batches in order (they are chosen after the first one)
+    const uint32_t nspec = c->lanes == 1 ? std::min<uint32_t>(c->spec_req, n) : 0u;
     // A build with the same shapes reuses the device buffers (no cudaFree / cudaMalloc, which
     // synchronise the device) and, if the sampler is unchanged too, the selection graph.
     const bool same_layout = c->built && c->R == R && c->batch_alloc == B && c->compact_cap == nc &&
-                             c->all_centers == all && c->live_cap == live_cap;
+                             c->all_centers == all && c->live_cap == live_cap && c->spec_count == nspec;
     if (!same_layout) {
         free_sketch_state(c);
     } else if (c->smp.salt != smp.salt || c->smp.T != smp.T || c->smp.all_live != smp.all_live) {
@@ -304,6 +314,7 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
     c->key_bits = (uint32_t)bits;
     c->smp = smp;
     c->batch_used = B;
+    c->spec_count = nspec;
     if (!same_layout) {
         bool ok = dalloc(c->d_gain0, n) && dalloc(c->d_key, n) && dalloc(c->d_stamp, n) &&
                   dalloc(c->d_seedflag, n) && dalloc(c->d_batch, n) && dalloc(c->d_fresh, n) &&
@@ -313,6 +324,7 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
                   dalloc(c->lane[0].parent, (size_t)B * n) && dalloc(c->lane[0].word, (size_t)B * n) &&
                   dalloc(c->lane[1].parent, (size_t)B * n) && dalloc(c->lane[1].word, (size_t)B * n) &&
                   dalloc(c->lane[1].gain, n) && dalloc(c->lane[1].fresh, n);
+        if (ok && nspec) ok = dalloc(c->lane[0].spec_ov, (size_t)nspec * n);
         if (ok && live_cap) {
             c->live_cap = live_cap;
             ok = dalloc(c->lane[0].live, c->live_cap) && dalloc(c->lane[0].live_n, 1) &&
@@ -344,6 +356,10 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
     if (!all) {
         rc = im_select_centers(c, c->d_cflags, c->d_cpos);
         if (rc) { free_sketch_state(c); return rc; }
+    }
+    if (!rc && nspec && !c->d_spec_keys) {
+        if (!dalloc(c->d_spec_keys, kSpecMax) || !dalloc(c->d_spec_ids, kSpecMax))
+            rc = im_fail(c, IM_ENOMEM, "first seed candidates");
     }
     if (!rc) rc = im_arc_keys(c, smp.salt);
     if (!rc) rc = im_sketch_batches(c);
@@ -501,6 +517,7 @@ int im_get_stats(im_ctx* c, im_stats* out) {
         out->hop2_chunks = c->h_sel->hop2_chunks;
         out->refresh_batches = c->h_sel->refresh_batches;
         out->batches = c->h_sel->batches;
+        out->spec_batches = c->h_sel->spec_batches;
         unsigned long long lt = 0;
         cudaMemcpy(&lt, c->d_live_total, sizeof lt, cudaMemcpyDeviceToHost);
         out->live_pairs = lt;
@@ -556,6 +573,8 @@ void im_destroy(im_ctx* c) {
     if (c->h_sel) cudaFreeHost(c->h_sel);
     if (c->h_live) cudaFreeHost(c->h_live);
     if (c->d_tmp) cudaFree(c->d_tmp);
+    dfree(c->d_spec_keys);
+    dfree(c->d_spec_ids);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     if (c->lane_stream1) { cudaStreamSynchronize(c->lane_stream1); cudaStreamDestroy(c->lane_stream1); }
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);

@@ -21,6 +21,7 @@ constexpr uint32_t kSpreadKMax = 16384;
 constexpr uint32_t kArcIdMask = 0x7FFFFFFFu;            // arc word 0: neighbour id | center bit
 constexpr uint32_t kLabSlots = 256;                     // label cache: vertex slots (x mod 256)
 constexpr size_t kCenterSelBytes = 4096;                // device state of the center radix select
+constexpr uint32_t kSpecMax = 8;                        // candidate first seeds (see im_ctx::spec_req)
 
 // splitmix64 output finaliser (Steele, Lea, Flood 2014).
 __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
@@ -134,6 +135,11 @@ struct SelState {
     unsigned long long launches;    // kernels launched by the selection graph
     unsigned int ticket;            // blocks of k_reduce_plan done (the last one plans)
     unsigned int pending;           // a batch was evaluated and awaits its accounting
+    // candidate first seeds whose overlaps the build accumulated (M_SPEC evaluates round 1)
+    unsigned int spec_count;
+    unsigned int spec_idx;          // which candidate the first seed is, else kNone
+    unsigned int spec_ids[kSpecMax];
+    unsigned long long spec_batches;
 };
 
 enum SelError : unsigned int {
@@ -149,8 +155,12 @@ enum SelMode : unsigned int {
     M_HIST_CHUNK = 4,     // radix passes, gather, one warp per (member, 32 sketches)
     M_REFRESH = 5,        // gather, recompute the sketches
     M_COUNT_ABOVE = 6,    // no batch yet: count the candidates above the best fresh key first
-    M_COUNT = 7,
-    M_NONE = 8            // no batch: the round is over
+    // round 1 after a candidate first seed: the batch's Marginals are gain0 - its overlap sums
+    M_SPEC_DIRECT = 7,    // B = 1
+    M_SPEC_GATHER = 8,    // threshold known: gather
+    M_SPEC_HIST = 9,      // radix passes, gather
+    M_COUNT = 10,
+    M_NONE = 11           // no batch: the round is over
 };
 
 // Conditional-node handles of the selection graph; on == 0 outside the graph.
@@ -240,6 +250,14 @@ struct im_ctx {
     uint64_t dry_count = 0;
     unsigned long long dev_launches_seen = 0;  // SelState::launches already added to launches
     unsigned long long build_live_pairs = 0;   // live pairs unioned by the last build
+    // Candidate first seeds: the spec_count vertices with the largest gains over the first
+    // batch of sketches (ties to the smaller id).  The build also sums, for each candidate c,
+    // ov_c(v) = sum_r |C_r(v)| [c in C_r(v)], so that if the first seed is one of them round 1's
+    // Marginals are gain0(v) - ov_c(v) without recomputing the sketches (exact).
+    uint32_t spec_req = 4;               // user setting (0 disables)
+    uint32_t spec_count = 0;             // candidates of the current build
+    uint64_t* d_spec_keys = nullptr;     // kSpecMax packed gain keys, largest first
+    uint32_t* d_spec_ids = nullptr;      // kSpecMax candidate ids
 
     // sketch-batch scratch: two lanes, each with its own stream, so that consecutive batches
     // overlap (one batch's hashing with the other's union-find)
@@ -251,6 +269,7 @@ struct im_ctx {
         unsigned long long* live_n = nullptr;
         uint64_t* gain = nullptr;                // lane 1: its share of the initial gains
         unsigned long long* fresh = nullptr;     // lane 1: its share of a refresh evaluation
+        uint64_t* spec_ov = nullptr;             // [spec][n] overlap sums (lane 0's is the total)
     };
     Lane lane[2];
     cudaStream_t lane_stream1 = nullptr;         // owned
@@ -314,6 +333,7 @@ int im_scan_u32_to_u64(im_ctx* c, const uint32_t* d_in, uint64_t* d_out, uint64_
 // im_sketch.cu
 int im_select_centers(im_ctx* c, uint32_t* d_flags_tmp, uint64_t* d_scan_tmp);
 int im_sketch_batches(im_ctx* c);
+
 int im_labels_min(im_ctx* c, uint32_t r, uint32_t* d_out);
 int im_refresh_eval(im_ctx* c, const uint32_t* d_batch, const unsigned int* d_batch_n,
                     unsigned long long* d_fresh, const uint32_t* d_seeds, const unsigned int* d_nseeds);

@@ -20,6 +20,22 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kEvalWarps = 4;   // warps per block of the search kernels
 // batches with at most this many (member, sketch) searches use one warp per search
 constexpr uint64_t kSingleTasks = 152ull * 64;
+// chunks of 32 arcs a warp search loads per step
+constexpr int kBfsChunks = 4;
+// per-warp visited set of a search (open addressing, >= 2 x the queue capacity + one chunk)
+constexpr uint32_t kHashSlots = 512;
+
+// Insert y into a warp's visited set; true if it was not there.  The set never holds more
+// than kQcap + 32 ids, so a free slot is always found.
+__device__ __forceinline__ bool visit(uint32_t* hs, uint32_t y) {
+    uint32_t h = (y * 0x9E3779B1u) >> (32 - 9);
+    for (;;) {
+        const uint32_t old = atomicCAS(hs + h, kNone, y);
+        if (old == kNone) return true;
+        if (old == y) return false;
+        h = (h + 1) & (kHashSlots - 1);
+    }
+}
 
 __device__ __forceinline__ uint64_t pack_key(uint64_t gain, uint32_t v, uint32_t bits) {
     const uint64_t mask = (1ull << bits) - 1ull;
@@ -64,11 +80,18 @@ __device__ BfsOut warp_bfs_from(const GraphView& g, const SketchView& s, uint32_
     uint32_t seen = want_seed ? (uint32_t)s.seed_flag[v] : 0u;
     uint32_t minv = v;
     const uint64_t rg = (uint64_t)(r + 1u) * kGamma;
-    if (lane == 0) q[0] = v;
+    uint32_t* hs = q + kQcap;   // visited set (the queue holds the same ids, in order)
+    for (uint32_t i = lane; i < kHashSlots; i += 32) hs[i] = kNone;
+    __syncwarp();
+    if (lane == 0) {
+        q[0] = v;
+        visit(hs, v);
+    }
     if (init) {
         for (uint32_t t = lane; t < ninit; t += 32) {
-            const uint32_t y = init[t * init_stride];
+            const uint32_t y = init[t * init_stride];   // distinct neighbours of v
             q[1 + t] = y;
+            visit(hs, y);
             if (want_seed && s.seed_flag[y]) seen = 1;
             minv = min(minv, y);
         }
@@ -102,11 +125,11 @@ __device__ BfsOut warp_bfs_from(const GraphView& g, const SketchView& s, uint32_
         preN -= deg - cc;
         const uint64_t aN = a0 + cc;   // where the non-center arcs start
         head += nv;
-        // four 32-arc chunks per step: their loads are in flight together
-        for (uint32_t base = 0; base < total; base += 128) {
-            uint4 arcs4[4];
+        // kBfsChunks 32-arc chunks per step: their loads are in flight together
+        for (uint32_t base = 0; base < total; base += 32u * kBfsChunks) {
+            uint4 arcs4[kBfsChunks];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < kBfsChunks; ++k) {
                 const uint32_t t = base + 32u * k + lane;
                 const bool inC = t < totC;
                 const uint32_t tt = inC ? t : t - totC;   // position within its run
@@ -131,7 +154,7 @@ __device__ BfsOut warp_bfs_from(const GraphView& g, const SketchView& s, uint32_
                 arcs4[k] = (t < total) ? g.arcs[ao + (tt - po)] : make_uint4(0, 0, 0, 0);
             }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < kBfsChunks; ++k) {
                 if (base + 32u * k >= total) break;
                 ++chunks;
                 const uint32_t t = base + 32u * k + lane;
@@ -151,15 +174,9 @@ __device__ BfsOut warp_bfs_from(const GraphView& g, const SketchView& s, uint32_
                     if (lane == 0 && st_counters) atomicAdd(&st_counters->hop2_chunks, (unsigned long long)chunks);
                     return o;
                 }
-                bool fresh = live;
-                if (live)
-                    for (uint32_t u = 0; u < tail; ++u)
-                        if (q[u] == y) { fresh = false; break; }
-                const unsigned fm = __ballot_sync(kFull, fresh);
-                if (fresh) {   // parallel edges / several frontier vertices reaching y: keep one lane
-                    const unsigned grp = __match_any_sync(fm, y);
-                    if (lane != (unsigned)(__ffs(grp) - 1)) fresh = false;
-                }
+                // first visit (parallel edges or several frontier vertices reaching y in this
+                // chunk: the set's CAS keeps exactly one lane)
+                const bool fresh = live && visit(hs, y);
                 const unsigned nbm = __ballot_sync(kFull, fresh);
                 const uint32_t cnt = __popc(nbm);
                 if (tail + cnt > kQcap) { o.overflow = 1; return o; }
@@ -407,14 +424,18 @@ __device__ void plan_step(SelState* st, uint32_t* __restrict__ batch, unsigned l
             st->batch_n = 1;
         }
         const bool single = expect * R <= kSingleTasks;
-        mode = refresh ? M_REFRESH
+        // Round 1 after a candidate first seed: the same batches, evaluated from the overlap sums
+        const bool spec = st->round == 1 && st->spec_idx < st->spec_count;
+        mode = spec    ? (direct ? M_SPEC_DIRECT : hist ? M_SPEC_HIST : M_SPEC_GATHER)
+             : refresh ? M_REFRESH
              : direct  ? M_DIRECT
              : single  ? (hist ? M_HIST_SINGLE : M_GATHER_SINGLE)
                        : (hist ? M_HIST_CHUNK : M_GATHER_CHUNK);
         st->pending = 1;
         st->j = j + 1;
         st->batches++;
-        if (refresh) st->refresh_batches++;
+        if (spec) st->spec_batches++;
+        else if (refresh) st->refresh_batches++;
     } else if (!st->err) {
         // the round is over: the best fresh key beats every stale one
         const uint32_t sd = (uint32_t)(mask - (best & mask));
@@ -426,6 +447,9 @@ __device__ void plan_step(SelState* st, uint32_t* __restrict__ batch, unsigned l
             const uint32_t rd = st->round;
             st->sd = sd;
             seed_list[rd] = sd;
+            if (rd == 0)
+                for (unsigned k = 0; k < st->spec_count; ++k)
+                    if (st->spec_ids[k] == sd) st->spec_idx = k;
             gain_list[rd] = best >> bits;
             round_evals[rd] = st->evals_total - st->evals_mark;
         }
@@ -499,6 +523,27 @@ k_reduce_plan(uint64_t* __restrict__ key, uint32_t* __restrict__ stamp, const ui
         __threadfence();
         st->ticket = 0;
         plan_step(st, batch, fresh, key, stamp, seed_list, gain_list, round_evals, n, R, bits, hd, false);
+    }
+}
+
+// Candidate first seeds of this build.
+__global__ void k_spec_init(SelState* st, const uint32_t* __restrict__ ids, uint32_t count) {
+    if (threadIdx.x == 0) {
+        st->spec_count = count;
+        st->spec_idx = kNone;
+        for (uint32_t k = 0; k < count; ++k) st->spec_ids[k] = ids[k];
+    }
+}
+
+// M_SPEC: Marginal(x | {s0}) = gain0(x) - sum_r |C_r(x)| [s0 in C_r(x)] for every batch member.
+__global__ void __launch_bounds__(256)
+k_spec_eval(const SelState* st, const uint32_t* __restrict__ batch, const uint64_t* __restrict__ gain0,
+            const uint64_t* __restrict__ spec_ov, uint32_t n, unsigned long long* __restrict__ fresh) {
+    const uint32_t bn = st->batch_n;
+    const uint64_t* ov = spec_ov + (size_t)st->spec_idx * n;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < bn; j += gridDim.x * blockDim.x) {
+        const uint32_t x = batch[j];
+        fresh[j] = gain0[x] - ov[x];
     }
 }
 
@@ -602,7 +647,7 @@ k_eval(GraphView g, SketchView s, SelState* st, const uint32_t* __restrict__ bat
        unsigned long long* __restrict__ fresh, FbTask* __restrict__ fbt, uint32_t fb_cap,
        uint32_t nchunk) {
     __shared__ uint32_t qls[kEvalWarps][32 * kLaneQ];
-    __shared__ uint32_t qws[kEvalWarps][kQcap];
+    __shared__ uint32_t qws[kEvalWarps][kQcap + kHashSlots];
     uint32_t* ql = qls[threadIdx.x >> 5];
     uint32_t* qw = qws[threadIdx.x >> 5];
     const unsigned lane = threadIdx.x & 31;
@@ -648,7 +693,7 @@ k_eval(GraphView g, SketchView s, SelState* st, const uint32_t* __restrict__ bat
 __global__ void __launch_bounds__(kEvalWarps * 32)
 k_eval_single(GraphView g, SketchView s, SelState* st, const uint32_t* __restrict__ batch,
               unsigned long long* __restrict__ fresh, FbTask* __restrict__ fbt, uint32_t fb_cap) {
-    __shared__ uint32_t qws[kEvalWarps][kQcap];
+    __shared__ uint32_t qws[kEvalWarps][kQcap + kHashSlots];
     uint32_t* qw = qws[threadIdx.x >> 5];
     const unsigned lane = threadIdx.x & 31;
     const unsigned long long total = (unsigned long long)st->batch_n * s.R;
@@ -685,7 +730,7 @@ k_eval_single(GraphView g, SketchView s, SelState* st, const uint32_t* __restric
 __global__ void __launch_bounds__(kEvalWarps * 32)
 k_mark_seed(GraphView g, SketchView s, SelState* st, FbTask* __restrict__ fbt, uint32_t fb_cap,
             uint8_t* __restrict__ seedflag, uint64_t* __restrict__ key, SelHandles hd) {
-    __shared__ uint32_t qws[kEvalWarps][kQcap];
+    __shared__ uint32_t qws[kEvalWarps][kQcap + kHashSlots];
     if (st->err) {   // the round chose no seed: the selection stops
         if (hd.on && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(hd.round, 0u);
         return;
@@ -847,7 +892,7 @@ k_spread_tasks(GraphView g, SketchView s, SelState* st, const uint32_t* __restri
                uint32_t nchunk, FbTask* __restrict__ fbt, uint32_t fb_cap,
                uint64_t* __restrict__ pairs) {
     __shared__ uint32_t qls[kEvalWarps][32 * kLaneQ];
-    __shared__ uint32_t qws[kEvalWarps][kQcap];
+    __shared__ uint32_t qws[kEvalWarps][kQcap + kHashSlots];
     uint32_t* ql = qls[threadIdx.x >> 5];
     uint32_t* qw = qws[threadIdx.x >> 5];
     const unsigned lane = threadIdx.x & 31;
@@ -958,6 +1003,7 @@ int im_selection_init(im_ctx* c) {
               c->d_gain0, c->n, c->key_bits, c->d_key, c->d_stamp, c->d_seedflag, c->d_size, nsize);
     IM_CUDA(c, cudaMemsetAsync(c->d_sel, 0, sizeof(SelState), c->stream));
     IM_CUDA(c, cudaMemsetAsync(c->d_labcache, 0xFF, (size_t)kLabSlots * c->R * sizeof(uint64_t), c->stream));
+    IM_LAUNCH(c, K_SEL_BEGIN, k_spec_init, 1, 32, 0, c->d_sel, c->d_spec_ids, c->spec_count);
     IM_CUDA(c, cudaGetLastError());
     c->seeds.clear();
     c->seed_gains.clear();
@@ -1001,10 +1047,10 @@ int enqueue_mode(im_ctx* c, unsigned mode, int passes, const SelHandles& hd) {
                   c->d_gain_list, c->d_round_evals, n, c->R, c->key_bits, hd);
         return IM_OK;
     }
-    if (mode == M_HIST_SINGLE || mode == M_HIST_CHUNK)
+    if (mode == M_HIST_SINGLE || mode == M_HIST_CHUNK || mode == M_SPEC_HIST)
         for (int p = 0; p < passes; ++p)
             IM_LAUNCH(c, K_SEL_HIST, k_sel_pass, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n, st);
-    if (mode != M_DIRECT)
+    if (mode != M_DIRECT && mode != M_SPEC_DIRECT)
         IM_LAUNCH(c, K_GATHER, k_gather, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n, st, c->d_batch,
                   fresh);
     switch (mode) {
@@ -1032,6 +1078,12 @@ int enqueue_mode(im_ctx* c, unsigned mode, int passes, const SelHandles& hd) {
         if (rc) return rc;
         break;
     }
+    case M_SPEC_DIRECT:
+    case M_SPEC_GATHER:
+    case M_SPEC_HIST:
+        IM_LAUNCH(c, K_REFRESH_GATHER, k_spec_eval, gridn, T, 0, st, c->d_batch, c->d_gain0, c->lane[0].spec_ov, n,
+                  fresh);
+        break;
     default:
         return im_fail(c, IM_EDEVICE, "unknown batch mode");
     }
@@ -1214,7 +1266,8 @@ int run_rounds_host(im_ctx* c) {
             if ((rc = pull_state(c))) return rc;
             const SelState& h = *c->h_sel;
             if (!h.cont) break;
-            const int passes = h.mode == M_HIST_SINGLE || h.mode == M_HIST_CHUNK ? h.shift / 8 + 1 : 0;
+            const bool hist = h.mode == M_HIST_SINGLE || h.mode == M_HIST_CHUNK || h.mode == M_SPEC_HIST;
+            const int passes = hist ? h.shift / 8 + 1 : 0;
             if ((rc = enqueue_mode(c, h.mode, passes, none))) return rc;
         }
         if ((rc = launch_mark(c, none))) return rc;

@@ -259,21 +259,36 @@ k_compress_count(uint32_t* __restrict__ parent, uint64_t* __restrict__ word, uin
     }
 }
 
+// Initial gains and compact sketches of one batch; with nspec > 0 also the overlap sums of
+// the candidate first seeds (their roots per sketch staged in shared memory).
 template <bool kAll>
 __global__ void __launch_bounds__(256)
 k_gain_compact(const uint32_t* __restrict__ parent, const uint64_t* __restrict__ word, uint32_t n,
                uint32_t nb, uint32_t r0, uint32_t R, uint64_t* __restrict__ gain, int first,
                const uint32_t* __restrict__ cidx, uint32_t* __restrict__ label,
-               uint32_t* __restrict__ size) {
+               uint32_t* __restrict__ size, const uint32_t* __restrict__ spec_ids, uint32_t nspec,
+               uint64_t* __restrict__ spec_ov) {
+    __shared__ uint32_t sroot[32][kSpecMax];
+    for (uint32_t i = threadIdx.x; i < nb * nspec; i += blockDim.x) {
+        const uint32_t b = i / nspec, k = i % nspec;
+        sroot[b][k] = parent[(size_t)b * n + spec_ids[k]];
+    }
+    __syncthreads();
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
         uint64_t g = 0;
+        uint64_t ov[kSpecMax];
+#pragma unroll
+        for (uint32_t k = 0; k < kSpecMax; ++k) ov[k] = 0;
         const uint32_t ci = kAll ? v : cidx[v];
         for (uint32_t b = 0; b < nb; ++b) {
             const uint32_t root = parent[(size_t)b * n + v];
             const uint64_t w = word[(size_t)b * n + root];
             const uint32_t c = (uint32_t)w;
             g += c;
+#pragma unroll
+            for (uint32_t k = 0; k < kSpecMax; ++k)
+                if (k < nspec && root == sroot[b][k]) ov[k] += c;
             if (ci != kNone) {
                 const uint32_t l = (uint32_t)(w >> 32);   // smallest center index of the component
                 const size_t o = (size_t)ci * R + r0 + b;
@@ -282,8 +297,68 @@ k_gain_compact(const uint32_t* __restrict__ parent, const uint64_t* __restrict__
             }
         }
         gain[v] = first ? g : gain[v] + g;
+#pragma unroll
+        for (uint32_t k = 0; k < kSpecMax; ++k)
+            if (k < nspec && ov[k]) spec_ov[(size_t)k * n + v] += ov[k];
     }
 }
+
+// The first batch's overlap sums, once the candidates are known (its forest is still there).
+__global__ void __launch_bounds__(256)
+k_spec_overlap(const uint32_t* __restrict__ parent, const uint64_t* __restrict__ word, uint32_t n,
+               uint32_t nb, const uint32_t* __restrict__ spec_ids, uint32_t nspec,
+               uint64_t* __restrict__ spec_ov) {
+    __shared__ uint32_t sroot[32][kSpecMax];
+    for (uint32_t i = threadIdx.x; i < nb * nspec; i += blockDim.x) {
+        const uint32_t b = i / nspec, k = i % nspec;
+        sroot[b][k] = parent[(size_t)b * n + spec_ids[k]];
+    }
+    __syncthreads();
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        uint64_t ov[kSpecMax];
+#pragma unroll
+        for (uint32_t k = 0; k < kSpecMax; ++k) ov[k] = 0;
+        for (uint32_t b = 0; b < nb; ++b) {
+            const uint32_t root = parent[(size_t)b * n + v];
+            bool any = false;
+#pragma unroll
+            for (uint32_t k = 0; k < kSpecMax; ++k) any |= k < nspec && root == sroot[b][k];
+            if (!any) continue;
+            const uint32_t c = (uint32_t)word[(size_t)b * n + root];
+#pragma unroll
+            for (uint32_t k = 0; k < kSpecMax; ++k)
+                if (k < nspec && root == sroot[b][k]) ov[k] += c;
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < kSpecMax; ++k)
+            if (k < nspec) spec_ov[(size_t)k * n + v] = ov[k];
+    }
+}
+
+// Candidate first seeds: launch i finds the largest gain key (gain << bits | (2^bits - 1 - v))
+// below the one launch i - 1 found (keys are distinct), so keys[0..count) belong to the count
+// largest gains, ties to the smaller id; the last launch converts them to ids.
+__global__ void __launch_bounds__(256)
+k_top_gain(const uint64_t* __restrict__ gain, uint32_t n, uint32_t bits, uint64_t* __restrict__ keys,
+           uint32_t i, uint32_t* __restrict__ ids) {
+    const uint64_t mask = (1ull << bits) - 1ull;
+    const uint64_t bound = i ? keys[i - 1] : ~0ull;
+    unsigned long long best = 0;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const uint64_t k = (gain[v] << bits) | (mask - v);
+        if (k < bound && k > best) best = k;
+    }
+#pragma unroll
+    for (int d = 16; d; d >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, d));
+    if ((threadIdx.x & 31) == 0 && best) atomicMax((unsigned long long*)keys + i, best);
+}
+
+__global__ void k_spec_ids(const uint64_t* __restrict__ keys, uint32_t count, uint32_t bits,
+                           uint32_t* __restrict__ ids) {
+    const uint64_t mask = (1ull << bits) - 1ull;
+    if (threadIdx.x < count) ids[threadIdx.x] = (uint32_t)(mask - (keys[threadIdx.x] & mask));
+}
+
 
 // Recomputation evaluator: flag the components that hold a seed (bit 31 of their size).
 __global__ void k_cover_roots(const uint32_t* __restrict__ parent, uint64_t* __restrict__ word,
@@ -476,6 +551,7 @@ int lanes_join(im_ctx* c) {
 
 }  // namespace
 
+
 int im_select_centers(im_ctx* c, uint32_t* d_flags, uint64_t* d_pos) {
     static_assert(sizeof(CenterSel) <= kCenterSelBytes, "center select scratch");
     const uint32_t n = c->n;
@@ -513,19 +589,34 @@ int im_sketch_batches(im_ctx* c) {
         if (rc) { lanes_join(c); return rc; }
         uint64_t* gain = (i % c->lanes) ? L.gain : c->d_gain0;
         const int first = i < c->lanes ? 1 : 0;
+        const uint32_t nspec = i ? c->spec_count : 0;   // candidates are known after batch 0
         if (c->all_centers)
             IM_LAUNCH(c, K_GAIN_COMPACT, k_gain_compact<true>, grid_for(n, T, 152u * 16u), T, 0,
-                      L.parent, L.word, n, nb, r0, R, gain, first, c->d_cidx, c->d_label, c->d_size);
+                      L.parent, L.word, n, nb, r0, R, gain, first, c->d_cidx, c->d_label, c->d_size,
+                      c->d_spec_ids, nspec, c->lane[0].spec_ov);
         else
             IM_LAUNCH(c, K_GAIN_COMPACT, k_gain_compact<false>, grid_for(n, T, 152u * 16u), T, 0,
-                      L.parent, L.word, n, nb, r0, R, gain, first, c->d_cidx, c->d_label, c->d_size);
+                      L.parent, L.word, n, nb, r0, R, gain, first, c->d_cidx, c->d_label, c->d_size,
+                      c->d_spec_ids, nspec, c->lane[0].spec_ov);
+        if (i == 0 && c->spec_count) {
+            // candidate first seeds: the largest gains so far; then this batch's overlap sums
+            IM_CUDA(c, cudaMemsetAsync(c->d_spec_keys, 0, kSpecMax * sizeof(uint64_t), c->cur));
+            for (uint32_t k = 0; k < c->spec_count; ++k)
+                IM_LAUNCH(c, K_CENTER_HIST, k_top_gain, grid_for(n, T, 152u * 8u), T, 0, c->d_gain0, n, c->key_bits,
+                          c->d_spec_keys, k, c->d_spec_ids);
+            IM_LAUNCH(c, K_CENTER_PICK, k_spec_ids, 1, 32, 0, c->d_spec_keys, c->spec_count, c->key_bits,
+                      c->d_spec_ids);
+            IM_LAUNCH(c, K_GAIN_COMPACT, k_spec_overlap, grid_for(n, T, 152u * 16u), T, 0, L.parent, L.word, n, nb,
+                      c->d_spec_ids, c->spec_count, c->lane[0].spec_ov);
+        }
     }
     rc = lanes_join(c);
     if (rc) return rc;
-    if (c->lanes > 1 && i > 1)
+    if (c->lanes > 1 && i > 1) {
         IM_LAUNCH(c, K_GAIN_COMPACT, k_add_u64, grid_for(n, T, 152u * 8u), T, 0,
                   (unsigned long long*)c->d_gain0, (const unsigned long long*)c->lane[1].gain, (uint64_t)n,
                   (const unsigned int*)nullptr);
+    }
     IM_CUDA(c, cudaGetLastError());
     return IM_OK;
 }

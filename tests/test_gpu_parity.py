@@ -23,10 +23,12 @@ def _cuda():
     im.lib()
 
 
-def _run(n, u, v, seed, p, R, alpha, k, batch=0, spread_sets=(), lanes=1):
+def _run(n, u, v, seed, p, R, alpha, k, batch=0, spread_sets=(), lanes=1, spec=None):
     with im.IMContext(n, u, v) as ctx:
         if batch:
             im.im_set_sketch_batch(ctx.h, batch)
+        if spec is not None:
+            im.im_set_seed_speculation(ctx.h, spec)
         im.im_set_pipeline(ctx.h, lanes)
         ctx.build_sketches(R, seed, p, alpha)
         out = dict(gains=ctx.gains(), centers=ctx.centers())
@@ -91,7 +93,7 @@ def test_small_alpha_forces_global_fallback_search():
     # p well above the percolation threshold: a giant component with very few centers, so
     # many searches exceed the shared-memory queue and spill to the global one
     n, u, v = graphgen.erdos_renyi(4000, 12000, 9)
-    g = _run(n, u, v, 7, 0.4, 40, 0.001, 6)
+    g = _run(n, u, v, 7, 0.4, 40, 0.001, 6, spec=0)   # round 1 by searches, not overlap sums
     o = _oracle(n, u, v, 7, 0.4, 40, 0.001, 6)
     _compare(g, o, 6)
     assert g["stats"]["bfs_fallbacks"] > 0
@@ -242,6 +244,7 @@ def test_both_batch_evaluators_give_identical_seeds(threshold, alpha):
     seed, p, R, k = 42, 0.05, 64, 25
     with im.IMContext(n, u, v) as ctx:
         im.im_set_refresh_threshold(ctx.h, threshold)
+        im.im_set_seed_speculation(ctx.h, 0)   # round 1 by the evaluator under test too
         ctx.build_sketches(R, seed, p, alpha)
         seeds, gains = ctx.select_seeds(k)
         st = ctx.stats()
@@ -273,14 +276,15 @@ def test_graph_and_host_driven_selection_agree(threshold):
             s1, _ = ctx.select_seeds(7)            # a prefix, then the rest
             seeds, gains = ctx.select_seeds(k)
             st = ctx.stats()
-            got.append((seeds, gains, ctx.round_evals(), st["batches"], st["refresh_batches"]))
+            got.append((seeds, gains, ctx.round_evals(), st["batches"], st["refresh_batches"],
+                        st["spec_batches"]))
             assert np.array_equal(s1, seeds[:7])
-    (sg, gg, eg, bg, rg), (sh, gh, eh, bh, rh) = got
+    (sg, gg, eg, bg, rg, _), (sh, gh, eh, bh, rh, _) = got
     assert np.array_equal(sg, o_seeds) and np.array_equal(gg, o_gains)
     assert np.array_equal(sh, sg) and np.array_equal(gh, gg)
     assert np.array_equal(eg, eh) and bg == bh and rg == rh
     if threshold == 1:
-        assert rg == bg > 0
+        assert rg + got[0][5] == bg > 0     # every batch but a speculative round 1 refreshes
     if threshold == 2**64 - 1:
         assert rg == 0
 
@@ -305,3 +309,45 @@ def test_rebuilds_in_one_context_match_fresh_contexts():
     o = _oracle(n, u, v, 7, 0.3, 64, 0.05, k)
     assert np.array_equal(got[0], o["seeds"]) and np.array_equal(got[1], o["seed_gains"])
     assert np.array_equal(got[2], o["label"]) and np.array_equal(got[3], o["size"])
+
+
+@pytest.mark.parametrize("graph", ["chunglu", "er"])
+@pytest.mark.parametrize("candidates", [0, 1, 4, 8])
+def test_first_seed_speculation_gives_the_same_selection(candidates, graph):
+    """Round 1's batches evaluated from the build's overlap sums of candidate first seeds (the
+    vertices with the largest gains over the first batch of 32 sketches) give the plain
+    selection, with the same batches and evaluation counts; the speculation is used exactly
+    when the first seed is among the candidates (computed here from the oracle's labels).
+    On the Chung-Lu graph the hubs tie at the top and the smallest id wins, as in the full
+    argmax; on the Erdos-Renyi graph the first seed ranks third, so one candidate misses it."""
+    if graph == "chunglu":
+        n, u, v = graphgen.chung_lu(20000, 100000, 2.1, 2000.0, 5)
+    else:
+        n, u, v = graphgen.erdos_renyi(2000, 10000, 7)
+    G = oracle.Graph(n, u, v)
+    L = G.labels(42, 0.05, 64)
+    o_seeds, o_gains = oracle.greedy(L, 8)
+    g32 = oracle.gains(L[:32]).astype(np.int64)
+    cand = np.lexsort((np.arange(n), -g32))[:candidates]
+    hit = bool(np.isin(o_seeds[0], cand))
+    with im.IMContext(n, u, v) as ctx:
+        im.im_set_seed_speculation(ctx.h, candidates)
+        ctx.build_sketches(64, 42, 0.05, 0.1)
+        assert ctx.stats()["sketch_batch"] == 32
+        s1, g1 = ctx.select_seeds(2)                 # through round 1, then the rest
+        seeds, gains = ctx.select_seeds(8)
+        st = ctx.stats()
+        ev = ctx.round_evals()
+    with im.IMContext(n, u, v) as ref:
+        im.im_set_seed_speculation(ref.h, 0)
+        ref.build_sketches(64, 42, 0.05, 0.1)
+        ref.select_seeds(8)
+        assert np.array_equal(ev, ref.round_evals()) and st["batches"] == ref.stats()["batches"]
+    assert np.array_equal(s1, seeds[:2])
+    assert np.array_equal(seeds, o_seeds) and np.array_equal(gains, o_gains)
+    assert (st["spec_batches"] > 0) == hit
+    assert hit == (candidates >= (1 if graph == "chunglu" else 3))
+    with pytest.raises(im.IMError) as e:
+        with im.IMContext(n, u, v) as ctx:
+            im.im_set_seed_speculation(ctx.h, 9)
+    assert e.value.code == im.IM_EINVAL
