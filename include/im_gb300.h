@@ -58,6 +58,19 @@ int im_create(im_ctx** out, uint32_t n, uint64_t m, const uint32_t* u, const uin
               int ptr_kind, void* stream);
 
 /*
+ * im_load_graph -- replace the context's graph by another edge list (same conventions as
+ * im_create; host lists are copied through a staging buffer the context keeps).  Device
+ * buffers are reused while n and m are unchanged, and the sketch buffers and selection graph
+ * of the next im_build_sketches too when its shapes are; a long-lived context thus serves one
+ * graph after another without allocating.  The sketches and any selection are discarded:
+ * im_build_sketches must run next.  On failure no graph is loaded (IM_ESTATE until a
+ * successful load).
+ * Errors: IM_EINVAL (n, m, ids, self-loops), IM_ENOMEM, IM_ECUDA.
+ */
+int im_load_graph(im_ctx* ctx, uint32_t n, uint64_t m, const uint32_t* u, const uint32_t* v,
+                  int ptr_kind);
+
+/*
  * im_build_sketches -- Step 1 of Alg. 1: build R compact sketches (Sec. 3, Alg. 3).
  *   R      number of sketches (1 <= R <= 65536).  Sketch r in [0, R) is the sampled graph
  *          G'_r whose live edges are those with h(e, r) < floor(p * 2^64), where

@@ -51,6 +51,7 @@ def lib():
     sig = {
         "im_create": ([c.POINTER(vp), u32, u64, vp, vp, i32, vp], i32),
         "im_build_sketches": ([vp, u32, u64, dbl, dbl], i32),
+        "im_load_graph": ([vp, u32, u64, vp, vp, i32], i32),
         "im_select_seeds": ([vp, u32, vp, vp], i32),
         "im_spread": ([vp, vp, u32, c.POINTER(u64)], i32),
         "im_reset_selection": ([vp], i32),
@@ -118,6 +119,18 @@ def im_create(n: int, u, v, stream=None):
         msg = lib().im_last_error(None)
         raise IMError(rc, msg.decode() if msg else "")
     return h.value
+
+
+def im_load_graph(ctx, n: int, u, v):
+    """Replace the context's graph (same argument conventions as im_create)."""
+    pu, ku = _ptr(u)
+    pv, kv = _ptr(v)
+    if ku != kv:
+        raise ValueError("u and v must both be host or both be device buffers")
+    m = int(len(u))
+    if len(v) != m:
+        raise ValueError("u and v differ in length")
+    _check(ctx, lib().im_load_graph(ctx, n, m, pu, pv, ku))
 
 
 def im_build_sketches(ctx, R: int, seed: int, p: float, alpha: float):
@@ -259,6 +272,11 @@ class IMContext:
     def __init__(self, n: int, u, v, stream=None):
         self.n = int(n)
         self.h = im_create(n, u, v, stream)
+
+    def load_graph(self, n, u, v):
+        im_load_graph(self.h, n, u, v)
+        self.n = int(n)
+        return self
 
     def build_sketches(self, R, seed, p, alpha):
         im_build_sketches(self.h, R, seed, p, alpha)

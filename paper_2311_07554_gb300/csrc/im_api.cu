@@ -134,6 +134,29 @@ int im_cuda_check(im_ctx* c, cudaError_t e, const char* what) {
     return im_fail(c, e == cudaErrorMemoryAllocation ? IM_ENOMEM : IM_ECUDA, msg);
 }
 
+// Upload (host lists through a staging buffer kept by the context), validate and build the
+// CSR of the edge list for c->n, c->m; buffers are reused while n and m are unchanged.
+static int load_graph(im_ctx* c, const uint32_t* u, const uint32_t* v, int ptr_kind) {
+    c->graph_ok = false;
+    const uint64_t m = c->m;
+    const uint32_t *pu = u, *pv = v;
+    if (ptr_kind == IM_PTR_HOST && m > 0) {
+        if (c->upload_cap < m) {
+            dfree(c->d_upload);
+            c->upload_cap = 0;
+            if (!dalloc(c->d_upload, 2 * m)) return im_fail(c, IM_ENOMEM, "edge upload");
+            c->upload_cap = m;
+        }
+        IM_CUDA(c, cudaMemcpyAsync(c->d_upload, u, m * sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream));
+        IM_CUDA(c, cudaMemcpyAsync(c->d_upload + m, v, m * sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream));
+        pu = c->d_upload;
+        pv = c->d_upload + m;
+    }
+    const int rc = im_graph_build(c, pu, pv);   // synchronises: the caller's lists may go
+    if (rc == IM_OK) c->graph_ok = true;
+    return rc;
+}
+
 // ------------------------------------------------------------------------------------
 extern "C" {
 
@@ -171,7 +194,6 @@ int im_create(im_ctx** out, uint32_t n, uint64_t m, const uint32_t* u, const uin
     }
     c->lane[0].stream = c->stream;
     c->lane[1].stream = c->lane_stream1;
-    uint32_t *du = nullptr, *dv = nullptr;
     int rc = IM_OK;
     do {
         if (cudaMalloc(&c->d_sel, sizeof(SelState)) != cudaSuccess ||
@@ -191,25 +213,8 @@ int im_create(im_ctx** out, uint32_t n, uint64_t m, const uint32_t* u, const uin
             rc = im_fail(c, IM_ENOMEM, "spread total");
             break;
         }
-        const uint32_t *pu = u, *pv = v;
-        if (ptr_kind == IM_PTR_HOST && m > 0) {
-            if (cudaMalloc(&du, m * sizeof(uint32_t)) != cudaSuccess ||
-                cudaMalloc(&dv, m * sizeof(uint32_t)) != cudaSuccess) {
-                rc = im_fail(c, IM_ENOMEM, "edge upload");
-                break;
-            }
-            if (cudaMemcpyAsync(du, u, m * sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
-                cudaMemcpyAsync(dv, v, m * sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
-                rc = im_fail(c, IM_ECUDA, "edge upload");
-                break;
-            }
-            pu = du;
-            pv = dv;
-        }
-        rc = im_graph_build(c, pu, pv);
+        rc = load_graph(c, u, v, ptr_kind);
     } while (0);
-    if (du) cudaFree(du);
-    if (dv) cudaFree(dv);
     if (rc != IM_OK) {
         g_create_error = c->err;
         im_destroy(c);
@@ -254,8 +259,26 @@ int im_set_refresh_threshold(im_ctx* c, uint64_t min_batch) {
     return IM_OK;
 }
 
+int im_load_graph(im_ctx* c, uint32_t n, uint64_t m, const uint32_t* u, const uint32_t* v, int ptr_kind) {
+    if (!c) return IM_EINVAL;
+    if (n == 0 || n >= 0x80000000u) return im_fail(c, IM_EINVAL, "n must be in [1, 2^31)");
+    if (m >= 0xFFFFFFFFull) return im_fail(c, IM_EINVAL, "m must be < 2^32");
+    if (ptr_kind != IM_PTR_HOST && ptr_kind != IM_PTR_DEVICE) return im_fail(c, IM_EINVAL, "bad ptr_kind");
+    if (m > 0 && (!u || !v)) return im_fail(c, IM_EINVAL, "edge arrays are NULL");
+    IM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (n != c->n) free_sketch_state(c);   // every per-vertex buffer changes size
+    c->built = false;
+    c->seeds.clear();
+    c->seed_gains.clear();
+    c->round_evals.clear();
+    c->n = n;
+    c->m = m;
+    return load_graph(c, u, v, ptr_kind);
+}
+
 int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alpha) {
     if (!c) return IM_EINVAL;
+    if (!c->graph_ok) return im_fail(c, IM_ESTATE, "no valid graph is loaded");
     if (R == 0 || R > 65536) return im_fail(c, IM_EINVAL, "R must be in [1, 65536]");
     if (!(alpha > 0.0) || alpha > 1.0) return im_fail(c, IM_EINVAL, "alpha must be in (0, 1]");
     if (std::isnan(p)) return im_fail(c, IM_EINVAL, "p is NaN");
@@ -302,7 +325,7 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
     const uint32_t nspec = c->lanes == 1 ? std::min<uint32_t>(c->spec_req, n) : 0u;
     // A build with the same shapes reuses the device buffers (no cudaFree / cudaMalloc, which
     // synchronise the device) and, if the sampler is unchanged too, the selection graph.
-    const bool same_layout = c->built && c->R == R && c->batch_alloc == B && c->compact_cap == nc &&
+    const bool same_layout = c->batch_alloc == B && c->R == R && c->compact_cap == nc &&
                              c->all_centers == all && c->live_cap == live_cap && c->spec_count == nspec;
     if (!same_layout) {
         free_sketch_state(c);
@@ -567,7 +590,7 @@ void im_destroy(im_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_sketch_state(c);
-    dfree(c->d_edges); dfree(c->d_off); dfree(c->d_arcs); dfree(c->d_arc_cur);
+    dfree(c->d_edges); dfree(c->d_off); dfree(c->d_arcs); dfree(c->d_arc_cur); dfree(c->d_upload);
     dfree(c->d_spread_pairs); dfree(c->d_spread_seeds); dfree(c->d_spread_total); dfree(c->d_live_total);
     if (c->d_sel) cudaFree(c->d_sel);
     if (c->h_sel) cudaFreeHost(c->h_sel);

@@ -205,7 +205,12 @@ struct im_ctx {
     uint2* d_edges = nullptr;
     uint64_t* d_off = nullptr;
     uint4* d_arcs = nullptr;
-    uint32_t* d_arc_cur = nullptr;   // 2n arc-fill cursors (centers from the front, others from the back)
+    uint32_t* d_arc_cur = nullptr;
+    uint32_t graph_n_alloc = 0;      // n, m the graph buffers were allocated for
+    uint64_t graph_m_alloc = 0;
+    bool graph_ok = false;           // a valid edge list is loaded
+    uint32_t* d_upload = nullptr;    // staging for host edge lists (2 x upload_cap ids)
+    uint64_t upload_cap = 0;   // 2n arc-fill cursors (centers from the front, others from the back)
     uint64_t arc_salt = 0;
     bool arc_keys_valid = false;
 

@@ -351,3 +351,44 @@ def test_first_seed_speculation_gives_the_same_selection(candidates, graph):
         with im.IMContext(n, u, v) as ctx:
             im.im_set_seed_speculation(ctx.h, 9)
     assert e.value.code == im.IM_EINVAL
+
+
+def test_load_graph_serves_one_graph_after_another():
+    """One context, several graphs (same n and m: buffers and selection graph reused; other
+    sizes: reallocated; host and device edge lists): each gives the results of a fresh
+    context.  A failed load leaves no graph (IM_ESTATE) until a good one is loaded."""
+    graphs = [graphgen.erdos_renyi(1500, 6001, 3), graphgen.erdos_renyi(1500, 6001, 4),
+              graphgen.erdos_renyi(900, 5000, 5), graphgen.erdos_renyi(1500, 6001, 3)]
+    R, seed, p, alpha, k = 45, 42, 0.1, 0.2, 5
+
+    def results(ctx):
+        return ctx.select_seeds(k) + ctx.compact() + (ctx.gains(), np.array([ctx.spread(np.arange(3))]))
+
+    n0, u0, v0 = graphs[0]
+    with im.IMContext(n0, u0, v0) as ctx:
+        for i, (n, u, v) in enumerate(graphs):
+            if i % 2:
+                ctx.load_graph(n, torch.from_numpy(u.view(np.int32)).cuda(), torch.from_numpy(v.view(np.int32)).cuda())
+            else:
+                ctx.load_graph(n, u, v)
+            with pytest.raises(im.IMError) as e:
+                ctx.select_seeds(1)
+            assert e.value.code == im.IM_ESTATE
+            ctx.build_sketches(R, seed, p, alpha)
+            got = results(ctx)
+            with im.IMContext(n, u, v) as fresh:
+                fresh.build_sketches(R, seed, p, alpha)
+                want = results(fresh)
+            for a, b in zip(got, want):
+                assert np.array_equal(a, b), i
+        o = _oracle(*graphs[-1], seed, p, R, alpha, k)
+        assert np.array_equal(got[0], o["seeds"]) and np.array_equal(got[1], o["seed_gains"])
+        with pytest.raises(im.IMError) as e:
+            ctx.load_graph(4, np.array([0, 7], np.uint32), np.array([1, 2], np.uint32))
+        assert e.value.code == im.IM_EINVAL
+        with pytest.raises(im.IMError) as e:
+            ctx.build_sketches(R, seed, p, alpha)
+        assert e.value.code == im.IM_ESTATE
+        ctx.load_graph(n0, u0, v0)
+        ctx.build_sketches(R, seed, p, alpha)
+        assert np.array_equal(ctx.select_seeds(k)[0], got[0])
