@@ -61,7 +61,7 @@ class ClockSampler:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
                 stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -124,9 +124,10 @@ def _traffic(kernel: str, units_per_launch: float):
         return None
 
 
-# Algorithmic work per unit (stated in DESIGN.md, section "Roofline model"):
+# Algorithmic work per unit:
 #   sample_emit  one hash per (edge, sketch) pair: 22 32-bit integer operations (64-bit add,
-#                three 64-bit xor-shifts, two 64-bit multiplies, 64-bit compare) -> bound "alu"
+#                three 64-bit xor-shifts, two 64-bit multiplies, 64-bit compare) -> bound "alu";
+#                its peak is measured by im_hash_peak (the same per-pair compute on registers)
 #   union        one live (edge, sketch) pair: its 16-byte record read plus two random
 #                32-byte sector reads for the endpoints' parents -> 80 bytes, bound "hbm"
 #   compress     one (vertex, sketch): parent read + write, root word update -> 16 bytes, "hbm"
@@ -135,7 +136,7 @@ UNION_BYTES_PER_PAIR = 80.0
 COMPRESS_BYTES_PER_VERTEX = 16.0
 
 
-def kernel_rooflines(prof, live_build, n, m, R, steps, peaks, peak_src, clk):
+def kernel_rooflines(prof, live_build, n, m, R, steps, peaks, peak_src, clk, hash_peak):
     """Rooflines of the sketch kernels launched by the builds of the timed steps.
 
     The refresh passes of the selection run inside the selection graph, whose time is one
@@ -145,7 +146,8 @@ def kernel_rooflines(prof, live_build, n, m, R, steps, peaks, peak_src, clk):
     total_ms = sum(x[0] for x in prof.values()) or 1.0
     passes = steps                                      # sketch passes over all R sketches
     mhz = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = 152 * 128 * mhz * 1e6 / 1e12             # Tops/s: 152 SMs x 128 int32 lanes
+    nominal = 152 * 128 * mhz * 1e6 / 1e12              # Tops/s: 152 SMs x 128 int32 lanes
+    alu_peak = ALU_OPS_PER_PAIR * hash_peak / 1e12      # Tops/s at the measured pair rate
     hbm = peaks.get("hbm_gbs", 6800.0)
 
     def entry(name, bound, units, per_unit, unit, peak, psrc):
@@ -161,7 +163,10 @@ def kernel_rooflines(prof, live_build, n, m, R, steps, peaks, peak_src, clk):
     if "sample_emit" in prof:
         out["sample_emit"] = entry("sample_emit", "alu", float(m) * R * passes, ALU_OPS_PER_PAIR,
                                    "Tops/s", alu_peak,
-                                   f"derived: 152 SMs x 128 int32 lanes x {mhz:.0f} MHz ({peak_src} max clock)")
+                                   f"measured: im_hash_peak, the per-pair compute on registers "
+                                   f"({hash_peak:.3e} pairs/s x {ALU_OPS_PER_PAIR:.0f} ops)")
+        out["sample_emit"]["nominal_peak"] = nominal
+        out["sample_emit"]["nominal_peak_source"] = f"152 SMs x 128 int32 lanes x {mhz:.0f} MHz"
     live = live_build
     if "union" in prof and live > 0:
         out["union"] = entry("union", "hbm", float(live), UNION_BYTES_PER_PAIR, "GB/s", hbm,
@@ -331,7 +336,8 @@ def run_ours(args, n, u, v, prm):
         total_ms = sum(x[0] for x in prof.values())
         # the selection graph is a sequence of kernels, not one: rank real kernels only
         top = max(((kn, x) for kn, x in prof.items() if kn != "select_graph"), key=lambda kv: kv[1][0])
-        roofs = kernel_rooflines(prof, live_build, n, m, R, args.steps, peaks, peak_src, clk)
+        hash_peak = im.im_hash_peak(4096)
+        roofs = kernel_rooflines(prof, live_build, n, m, R, args.steps, peaks, peak_src, clk, hash_peak)
         roof = roofs.get(top[0]) or (max(roofs.values(), key=lambda r: r["share_of_device_time"])
                                      if roofs else None)
         cpu = cpu_sample(n, u, v, prm)
@@ -374,7 +380,7 @@ def run_ours(args, n, u, v, prm):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(graphgen.WORKLOADS))

@@ -237,6 +237,13 @@ int im_set_graph(im_ctx* ctx, int on);
  * Seeds, gains and evaluation counts do not depend on it. */
 int im_set_seed_speculation(im_ctx* ctx, uint32_t candidates);
 
+/* Measurement: the rate of the sampling kernel's per-pair compute (64-bit add, high word of
+ * the hash, compare, live-mask update) on register values only -- the ceiling of the
+ * sampling with no memory traffic -- in (edge, sketch) pairs per second on the current
+ * device; `iters` (a positive multiple of 32) sketches per key, 2 keys per thread, 1216 blocks
+ * of 256 threads.  Blocks until done.  Errors: IM_EINVAL, IM_ECUDA. */
+int im_hash_peak(uint32_t iters, double* pairs_per_s);
+
 /* The context's stream (a cudaStream_t). */
 void* im_stream(im_ctx* ctx);
 

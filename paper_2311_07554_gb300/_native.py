@@ -70,6 +70,7 @@ def lib():
         "im_set_refresh_threshold": ([vp, u64], i32),
         "im_set_pipeline": ([vp, u32], i32),
         "im_set_graph": ([vp, i32], i32),
+        "im_hash_peak": ([u32, c.POINTER(dbl)], i32),
         "im_set_seed_speculation": ([vp, u32], i32),
         "im_stream": ([vp], vp),
         "im_sketch_static": ([u32, u64, vp, vp, u64, dbl, u32, vp, vp, vp], i32),
@@ -239,6 +240,15 @@ def im_set_graph(ctx, on: bool):
 
 def im_set_seed_speculation(ctx, candidates: int):
     _check(ctx, lib().im_set_seed_speculation(ctx, candidates))
+
+
+def im_hash_peak(iters: int = 4096) -> float:
+    """Pairs per second of the sampling kernel's per-pair compute on registers only."""
+    out = ctypes.c_double(0)
+    rc = lib().im_hash_peak(iters, ctypes.byref(out))
+    if rc != IM_OK:
+        raise IMError(rc, "im_hash_peak failed")
+    return out.value
 
 
 def im_stream(ctx) -> int:

@@ -71,6 +71,17 @@ __device__ __forceinline__ uint32_t mix64_hi(uint64_t x) {
     return wh ^ (wh >> 31);
 }
 
+// High word of mix64(x) before its last step (w ^ (w >> 31) for the high word w of z * C2):
+// the final high word differs from w at most in bit 0, so  final <= th  implies  w <= th + 1,
+// which makes w a candidate test that needs neither the low half of the last product nor the
+// last shift.
+__device__ __forceinline__ uint32_t mix64_hi_raw(uint64_t x) {
+    uint64_t z = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = z ^ (z >> 27);
+    const uint32_t zl = (uint32_t)z, zh = (uint32_t)(z >> 32);
+    return __umulhi(zl, 0x133111EBu) + zl * 0x94D049BBu + zh * 0x133111EBu;   // hi(z * C2)
+}
+
 struct GraphView {
     uint32_t n;
     uint64_t m;

@@ -69,17 +69,6 @@ k_sample_union(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, ui
         sample_union_pair<B>(edge_pairs[i], i, m, smp, g0, nb, parent, n);
 }
 
-// High word of mix64(x) before its last step (w ^ (w >> 31) for the high word w of z * C2):
-// the final high word differs from w at most in bit 0, so  final <= th  implies  w <= th + 1,
-// which makes w a candidate test that needs neither the low half of the last product nor the
-// last shift.
-__device__ __forceinline__ uint32_t mix64_hi_raw(uint64_t x) {
-    uint64_t z = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = z ^ (z >> 27);
-    const uint32_t zl = (uint32_t)z, zh = (uint32_t)(z >> 32);
-    return __umulhi(zl, 0x133111EBu) + zl * 0x94D049BBu + zh * 0x133111EBu;   // hi(z * C2)
-}
-
 // Sampling alone: every live (edge, sketch) pair of the batch becomes a record (u, v, b, 0),
 // appended with one atomic per warp.  The hash work (nb mixes per edge) is pure ALU; the
 // latency-bound unions then run one thread per record in k_union_live.
@@ -260,26 +249,29 @@ k_compress_count(uint32_t* __restrict__ parent, uint64_t* __restrict__ word, uin
 }
 
 // Initial gains and compact sketches of one batch; with nspec > 0 also the overlap sums of
-// the candidate first seeds (their roots per sketch staged in shared memory).
-template <bool kAll>
-__global__ void __launch_bounds__(256)
+// the candidate first seeds (their roots per sketch staged in shared memory).  kSpec is the
+// capacity of the per-thread overlap accumulators (0, 4 or 8; nspec <= kSpec).
+template <bool kAll, int kSpec>
+__global__ void __launch_bounds__(256, 6)
 k_gain_compact(const uint32_t* __restrict__ parent, const uint64_t* __restrict__ word, uint32_t n,
                uint32_t nb, uint32_t r0, uint32_t R, uint64_t* __restrict__ gain, int first,
                const uint32_t* __restrict__ cidx, uint32_t* __restrict__ label,
                uint32_t* __restrict__ size, const uint32_t* __restrict__ spec_ids, uint32_t nspec,
                uint64_t* __restrict__ spec_ov) {
-    __shared__ uint32_t sroot[32][kSpecMax];
-    for (uint32_t i = threadIdx.x; i < nb * nspec; i += blockDim.x) {
-        const uint32_t b = i / nspec, k = i % nspec;
-        sroot[b][k] = parent[(size_t)b * n + spec_ids[k]];
+    __shared__ uint32_t sroot[32][kSpec > 0 ? kSpec : 1];
+    if (kSpec > 0) {
+        for (uint32_t i = threadIdx.x; i < nb * nspec; i += blockDim.x) {
+            const uint32_t b = i / nspec, k = i % nspec;
+            sroot[b][k] = parent[(size_t)b * n + spec_ids[k]];
+        }
+        __syncthreads();
     }
-    __syncthreads();
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
         uint64_t g = 0;
-        uint64_t ov[kSpecMax];
+        uint64_t ov[kSpec > 0 ? kSpec : 1];
 #pragma unroll
-        for (uint32_t k = 0; k < kSpecMax; ++k) ov[k] = 0;
+        for (int k = 0; k < kSpec; ++k) ov[k] = 0;
         const uint32_t ci = kAll ? v : cidx[v];
         for (uint32_t b = 0; b < nb; ++b) {
             const uint32_t root = parent[(size_t)b * n + v];
@@ -287,8 +279,8 @@ k_gain_compact(const uint32_t* __restrict__ parent, const uint64_t* __restrict__
             const uint32_t c = (uint32_t)w;
             g += c;
 #pragma unroll
-            for (uint32_t k = 0; k < kSpecMax; ++k)
-                if (k < nspec && root == sroot[b][k]) ov[k] += c;
+            for (int k = 0; k < kSpec; ++k)
+                if ((uint32_t)k < nspec && root == sroot[b][k]) ov[k] += c;
             if (ci != kNone) {
                 const uint32_t l = (uint32_t)(w >> 32);   // smallest center index of the component
                 const size_t o = (size_t)ci * R + r0 + b;
@@ -298,8 +290,8 @@ k_gain_compact(const uint32_t* __restrict__ parent, const uint64_t* __restrict__
         }
         gain[v] = first ? g : gain[v] + g;
 #pragma unroll
-        for (uint32_t k = 0; k < kSpecMax; ++k)
-            if (k < nspec && ov[k]) spec_ov[(size_t)k * n + v] += ov[k];
+        for (int k = 0; k < kSpec; ++k)
+            if ((uint32_t)k < nspec && ov[k]) spec_ov[(size_t)k * n + v] += ov[k];
     }
 }
 
@@ -590,14 +582,20 @@ int im_sketch_batches(im_ctx* c) {
         uint64_t* gain = (i % c->lanes) ? L.gain : c->d_gain0;
         const int first = i < c->lanes ? 1 : 0;
         const uint32_t nspec = i ? c->spec_count : 0;   // candidates are known after batch 0
-        if (c->all_centers)
-            IM_LAUNCH(c, K_GAIN_COMPACT, k_gain_compact<true>, grid_for(n, T, 152u * 16u), T, 0,
-                      L.parent, L.word, n, nb, r0, R, gain, first, c->d_cidx, c->d_label, c->d_size,
-                      c->d_spec_ids, nspec, c->lane[0].spec_ov);
-        else
-            IM_LAUNCH(c, K_GAIN_COMPACT, k_gain_compact<false>, grid_for(n, T, 152u * 16u), T, 0,
-                      L.parent, L.word, n, nb, r0, R, gain, first, c->d_cidx, c->d_label, c->d_size,
-                      c->d_spec_ids, nspec, c->lane[0].spec_ov);
+#define IM_GAIN(ALL, K)                                                                             \
+    IM_LAUNCH(c, K_GAIN_COMPACT, (k_gain_compact<ALL, K>), grid_for(n, T, 152u * 16u), T, 0, L.parent, L.word, \
+              n, nb, r0, R, gain, first, c->d_cidx, c->d_label, c->d_size, c->d_spec_ids, nspec,        \
+              c->lane[0].spec_ov)
+        if (c->all_centers) {
+            if (nspec == 0) IM_GAIN(true, 0);
+            else if (nspec <= 4) IM_GAIN(true, 4);
+            else IM_GAIN(true, 8);
+        } else {
+            if (nspec == 0) IM_GAIN(false, 0);
+            else if (nspec <= 4) IM_GAIN(false, 4);
+            else IM_GAIN(false, 8);
+        }
+#undef IM_GAIN
         if (i == 0 && c->spec_count) {
             // candidate first seeds: the largest gains so far; then this batch's overlap sums
             IM_CUDA(c, cudaMemsetAsync(c->d_spec_keys, 0, kSpecMax * sizeof(uint64_t), c->cur));
