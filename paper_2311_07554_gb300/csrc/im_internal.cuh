@@ -100,9 +100,15 @@ struct SketchView {
     const uint32_t* label;   // [rho][R]
     uint32_t* size;          // [rho][R], bit 31 = covered by a seed
     const uint8_t* seed_flag;
+    uint32_t pend;           // a seed whose flag is being set concurrently (kNone: none)
     uint64_t* labcache;      // [kLabSlots][R] labels found by searches, reused by MarkSeed
     Sampler smp;
 };
+
+// Whether x is a seed: its flag, or the seed a MarkSeed running in the same kernel is adding.
+__device__ __forceinline__ bool is_seed(const SketchView& s, uint32_t x) {
+    return s.seed_flag[x] || x == s.pend;
+}
 
 __device__ __forceinline__ bool is_center(const SketchView& s, uint32_t x) {
     return s.all_centers || ((__ldg(s.cbits + (x >> 5)) >> (x & 31)) & 1u);
@@ -170,22 +176,24 @@ enum SelMode : unsigned int {
     M_SPEC_DIRECT = 7,    // B = 1
     M_SPEC_GATHER = 8,    // threshold known: gather
     M_SPEC_HIST = 9,      // radix passes, gather
-    M_COUNT = 10,
-    M_NONE = 11           // no batch: the round is over
+    M_ROUND_START = 10,   // no batch: the reduction and planning step that open a round
+    M_MARK = 11,          // MarkSeed of the last round's winner, then the next round opens
+    M_MARK_DIRECT = 12,   // MarkSeed of the last round's winner fused with a B = 1 batch
+    M_COUNT = 13,
+    M_NONE = 14           // nothing: the selection is over
 };
 
 // Conditional-node handles of the selection graph; on == 0 outside the graph.
 struct SelHandles {
-    cudaGraphConditionalHandle round, batch, mode;
+    cudaGraphConditionalHandle loop, mode;
     unsigned int on;
-    unsigned int launches[M_COUNT];   // kernels each batch mode launches
-    unsigned int round_launches;      // kernels of a round outside its batches
+    unsigned int launches[M_COUNT];   // kernels each step mode launches
 };
 
 struct FbTask {
     uint32_t v, r, kind, idx;
 };
-enum FbKind : uint32_t { FB_EVAL = 0, FB_MARK = 1, FB_SPREAD = 2 };
+enum FbKind : uint32_t { FB_EVAL = 0, FB_MARK = 1, FB_SPREAD = 2, FB_MARK_EVAL = 3 };
 
 enum KernelId {
     K_PACK_EDGES = 0, K_CSR_DEGREE, K_SCAN_PARTIAL, K_SCAN_TOP, K_SCAN_APPLY, K_CSR_FILL,

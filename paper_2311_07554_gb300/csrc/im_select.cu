@@ -77,7 +77,7 @@ __device__ BfsOut warp_bfs_from(const GraphView& g, const SketchView& s, uint32_
     o.label = kNone; o.count = 0; o.minv = v; o.seen = 0; o.overflow = 0;
     uint32_t chunks = 0;
     uint32_t head = 0, tail = 1;
-    uint32_t seen = want_seed ? (uint32_t)s.seed_flag[v] : 0u;
+    uint32_t seen = want_seed ? (uint32_t)is_seed(s, v) : 0u;
     uint32_t minv = v;
     const uint64_t rg = (uint64_t)(r + 1u) * kGamma;
     uint32_t* hs = q + kQcap;   // visited set (the queue holds the same ids, in order)
@@ -92,7 +92,7 @@ __device__ BfsOut warp_bfs_from(const GraphView& g, const SketchView& s, uint32_
             const uint32_t y = init[t * init_stride];   // distinct neighbours of v
             q[1 + t] = y;
             visit(hs, y);
-            if (want_seed && s.seed_flag[y]) seen = 1;
+            if (want_seed && is_seed(s, y)) seen = 1;
             minv = min(minv, y);
         }
         head = 1;
@@ -182,7 +182,7 @@ __device__ BfsOut warp_bfs_from(const GraphView& g, const SketchView& s, uint32_
                 if (tail + cnt > kQcap) { o.overflow = 1; return o; }
                 if (fresh) {
                     q[tail + __popc(nbm & ((1u << lane) - 1u))] = y;
-                    if (want_seed && s.seed_flag[y]) seen = 1;
+                    if (want_seed && is_seed(s, y)) seen = 1;
                     minv = min(minv, y);
                 }
                 tail += cnt;
@@ -224,7 +224,7 @@ __device__ LaneRes get_center_32(const GraphView& g, const SketchView& s, uint32
     bool act = r < r_hi;
     LaneRes o;
     o.label = kNone; o.count = 1; o.minv = x; o.overflow = 0;
-    o.seen = (act && want_seed) ? (uint32_t)s.seed_flag[x] : 0u;
+    o.seen = (act && want_seed) ? (uint32_t)is_seed(s, x) : 0u;
     uint32_t cnt = 0;        // live non-center neighbours of x recorded
     bool over = false;       // more than kLaneQ - 1 of them
     const uint64_t rg = (uint64_t)(r + 1u) * kGamma;
@@ -352,6 +352,19 @@ __device__ void plan_step(SelState* st, uint32_t* __restrict__ batch, unsigned l
     const unsigned long long nu = __ldcg(&st->n_unev), smax = __ldcg(&st->stale_max), best = __ldcg(&st->best);
     const unsigned j = st->j;
     const uint64_t mask = (1ull << bits) - 1ull;
+    if (j == 0 && st->round >= st->round_end) {   // every requested seed is chosen and marked
+        st->best = 0;                              // a later run opens this round again
+        st->stale_max = 0;
+        st->n_unev = 0;
+        st->count_above = 0;
+        st->cont = 0;
+        st->mode = M_NONE;
+        if (hd.on) {
+            cudaGraphSetConditional(hd.loop, 0u);
+            cudaGraphSetConditional(hd.mode, M_NONE);
+        }
+        return;
+    }
     if (st->pending) {   // the batch evaluated since the last step
         st->pending = 0;
         const unsigned bn = st->batch_n;
@@ -451,14 +464,50 @@ __device__ void plan_step(SelState* st, uint32_t* __restrict__ batch, unsigned l
                 for (unsigned k = 0; k < st->spec_count; ++k)
                     if (st->spec_ids[k] == sd) st->spec_idx = k;
             gain_list[rd] = best >> bits;
-            round_evals[rd] = st->evals_total - st->evals_mark;
+            const unsigned long long evals = st->evals_total - st->evals_mark;
+            round_evals[rd] = evals;
+            // The next round.  If this one evaluated its winner only, every other key is as it
+            // was at its start, so the next round's top key is this reduction's stale_max and
+            // its first batch (B = 1, that key) is known now: it runs fused with the MarkSeed.
+            st->round = rd + 1;
+            st->j = 0;
+            st->evals_mark = st->evals_total;
+            st->best = 0;
+            st->stale_max = 0;
+            st->n_unev = 0;
+            st->count_above = 0;
+            cont = 1;
+            mode = M_MARK;
+            if (rd + 1 < st->round_end && rd >= 1 && evals == 1 && nu > 2 && smax > 0 && st->refresh_min > 2) {
+                const uint32_t y = (uint32_t)(mask - (smax & mask));
+                batch[0] = y;
+                fresh[0] = 0;
+                key[y] = 0;                        // its batch slot
+                stamp[y] = (rd + 1) | kPending;
+                st->batch_n = 1;
+                st->eval_next = 0;
+                st->fb_n = 0;
+                st->best_prev = 0;
+                st->borig = 1;
+                st->need = 1;
+                st->taken = 0;
+                st->prefix = 0;
+                st->theta = smax;
+                st->shift = 0;
+                st->prefmask = 0;
+                st->done = 1;
+                st->pending = 1;
+                st->j = 1;
+                st->batches++;
+                mode = M_MARK_DIRECT;
+            }
         }
     }
     st->cont = cont;
     st->mode = mode;
     if (cont) st->launches += hd.launches[mode];
     if (hd.on) {
-        cudaGraphSetConditional(hd.batch, cont);
+        cudaGraphSetConditional(hd.loop, cont);
         cudaGraphSetConditional(hd.mode, mode);
     }
 }
@@ -725,16 +774,13 @@ k_eval_single(GraphView g, SketchView s, SelState* st, const uint32_t* __restric
     }
 }
 
-// MarkSeed (Alg. 3): in every sketch, flag the component of s as covered.  One warp per
-// sketch: a single vertex is marked per round, so latency, not total work, decides.
+// MarkSeed (Alg. 3): in every sketch, flag the component of the last round's winner as
+// covered.  One warp per sketch: a single vertex is marked per round, so latency, not total
+// work, decides.
 __global__ void __launch_bounds__(kEvalWarps * 32)
 k_mark_seed(GraphView g, SketchView s, SelState* st, FbTask* __restrict__ fbt, uint32_t fb_cap,
-            uint8_t* __restrict__ seedflag, uint64_t* __restrict__ key, SelHandles hd) {
+            uint8_t* __restrict__ seedflag, uint64_t* __restrict__ key) {
     __shared__ uint32_t qws[kEvalWarps][kQcap + kHashSlots];
-    if (st->err) {   // the round chose no seed: the selection stops
-        if (hd.on && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(hd.round, 0u);
-        return;
-    }
     const uint32_t sd = st->sd;
     uint32_t* qw = qws[threadIdx.x >> 5];
     const unsigned lane = threadIdx.x & 31;
@@ -763,17 +809,68 @@ k_mark_seed(GraphView g, SketchView s, SelState* st, FbTask* __restrict__ fbt, u
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         seedflag[sd] = 1;
         key[sd] = 0;
-        // the next round's first reduction starts from zero
-        st->best = 0;
-        st->stale_max = 0;
-        st->n_unev = 0;
-        st->count_above = 0;
-        st->j = 0;
-        st->evals_mark = st->evals_total;
-        const unsigned rd = st->round + 1;
-        st->round = rd;
-        st->launches += hd.round_launches;
-        if (hd.on) cudaGraphSetConditional(hd.round, rd < st->round_end ? 1u : 0u);
+    }
+}
+
+// MarkSeed of the last round's winner x fused with the Marginal of this round's only
+// candidate y (batch slot 0), one warp per sketch: the warp marks x's component first, so
+// that y's search finds it covered; a component without a center that holds x counts as
+// holding a seed through s.pend (x's flag is set concurrently).  If x's search overflows,
+// the fallback kernel does both for that sketch (FB_MARK_EVAL), in the same order.
+__global__ void __launch_bounds__(kEvalWarps * 32)
+k_mark_eval(GraphView g, SketchView s, SelState* st, const uint32_t* __restrict__ batch,
+            unsigned long long* __restrict__ fresh, FbTask* __restrict__ fbt, uint32_t fb_cap,
+            uint8_t* __restrict__ seedflag, uint64_t* __restrict__ key) {
+    __shared__ uint32_t qws[kEvalWarps][kQcap + kHashSlots];
+    const uint32_t x = st->sd, y = batch[0];
+    s.pend = x;
+    uint32_t* qw = qws[threadIdx.x >> 5];
+    const unsigned lane = threadIdx.x & 31;
+    const uint32_t r = blockIdx.x * kEvalWarps + (threadIdx.x >> 5);
+    if (r < s.R) {
+        uint32_t lx = kNone;
+        bool marked = true;
+        if (is_center(s, x)) {
+            lx = s.label[(size_t)center_index(s, x) * s.R + r];
+        } else {
+            const uint64_t e = s.labcache[(size_t)(x & (kLabSlots - 1)) * s.R + r];
+            if ((uint32_t)(e >> 32) == x) {
+                lx = (uint32_t)e;
+            } else {
+                const BfsOut o = warp_bfs_from(g, s, x, r, qw, false, nullptr, 0, 0, st);
+                if (o.overflow) marked = false;
+                else lx = o.label;
+            }
+        }
+        if (!marked) {
+            if (lane == 0) push_fallback(st, fbt, fb_cap, x, r, FB_MARK_EVAL, y);
+        } else {
+            if (lane == 0 && lx != kNone) atomicOr(s.size + (size_t)lx * s.R + r, kCovered);
+            __syncwarp();
+            unsigned long long d = 0;
+            if (is_center(s, y)) {
+                const uint32_t l = s.label[(size_t)center_index(s, y) * s.R + r];
+                const uint32_t sz = __ldcg(s.size + (size_t)l * s.R + r);
+                d = (sz & kCovered) ? 0u : sz;
+            } else {
+                const BfsOut o = warp_bfs_from(g, s, y, r, qw, true, nullptr, 0, 0, st);
+                if (!o.overflow && lane == 0)
+                    s.labcache[(size_t)(y & (kLabSlots - 1)) * s.R + r] = ((uint64_t)y << 32) | o.label;
+                if (o.overflow) {
+                    if (lane == 0) push_fallback(st, fbt, fb_cap, y, r, FB_EVAL, 0);
+                } else if (o.label != kNone) {
+                    const uint32_t sz = __ldcg(s.size + (size_t)o.label * s.R + r);
+                    d = (sz & kCovered) ? 0u : sz;
+                } else {
+                    d = o.seen ? 0u : o.count;
+                }
+            }
+            if (lane == 0 && d) atomicAdd(fresh, d);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        seedflag[x] = 1;
+        key[x] = 0;
     }
 }
 
@@ -785,11 +882,15 @@ __global__ void k_set_target(SelState* st, uint32_t round_end, unsigned long lon
     }
 }
 
-// First node of the selection graph: enter the round loop if seeds are still missing.
+// First node of the selection graph: enter the loop, opening a round, if seeds are missing.
 __global__ void k_sel_begin(SelState* st, SelHandles hd) {
     if (threadIdx.x == 0) {
-        st->launches += 1;
-        if (hd.on) cudaGraphSetConditional(hd.round, (!st->err && st->round < st->round_end) ? 1u : 0u);
+        const unsigned go = (!st->err && st->round < st->round_end) ? 1u : 0u;
+        st->launches += 1 + (go ? hd.launches[M_ROUND_START] : 0u);
+        if (hd.on) {
+            cudaGraphSetConditional(hd.loop, go);
+            cudaGraphSetConditional(hd.mode, M_ROUND_START);
+        }
     }
 }
 
@@ -797,8 +898,82 @@ __global__ void k_phase_reset(SelState* st) {
     if (threadIdx.x == 0) { st->fb_n = 0; st->eval_next = 0; st->batch_n = 0; }
 }
 
+// A search from v in sketch r with the queue and visited bitmap of a fallback slot (global
+// memory: no size limit); the bitmap is cleared again before returning.
+struct FbOut {
+    uint32_t label, tail, seen, minv;
+};
+
+__device__ FbOut fb_search(const GraphView& g, const SketchView& s, uint32_t v, uint32_t r, bool want_seed,
+                           uint32_t* __restrict__ q, uint32_t* __restrict__ bits) {
+    const unsigned lane = threadIdx.x & 31;
+    if (lane == 0) {
+        q[0] = v;
+        atomicOr(bits + (v >> 5), 1u << (v & 31));
+    }
+    __syncwarp();
+    uint32_t head = 0, tail = 1, label = kNone, minv = v;
+    uint32_t seen = want_seed ? (uint32_t)is_seed(s, v) : 0u;
+    while (head < tail && label == kNone) {
+        const uint32_t x = q[head++];
+        const uint64_t a0 = g.off[x], a1 = g.off[x + 1];
+        for (uint64_t base = a0; base < a1; base += 32) {
+            const uint64_t a = base + lane;
+            bool live = false;
+            uint32_t y = 0, ci = 0;
+            bool cen = false;
+            if (a < a1) {
+                const uint4 arc = g.arcs[a];
+                y = arc.x & kArcIdMask;
+                cen = arc.x >> 31;
+                ci = arc.y;
+                live = edge_live_fast(s.smp, ((uint64_t)arc.w << 32) | arc.z, (uint64_t)(r + 1u) * kGamma);
+            }
+            const unsigned cb = __ballot_sync(kFull, live && cen);
+            if (cb) {
+                const uint32_t c0 = __shfl_sync(kFull, ci, __ffs(cb) - 1);   // the arc's center index
+                label = s.label[(size_t)c0 * s.R + r];
+                break;
+            }
+            bool fresh_v = false;
+            if (live) {
+                const uint32_t bit = 1u << (y & 31);
+                fresh_v = !(atomicOr(bits + (y >> 5), bit) & bit);
+            }
+            const unsigned nbm = __ballot_sync(kFull, fresh_v);
+            if (fresh_v) {
+                q[tail + __popc(nbm & ((1u << lane) - 1u))] = y;
+                if (want_seed && is_seed(s, y)) seen = 1;
+                minv = min(minv, y);
+            }
+            tail += __popc(nbm);
+            __syncwarp();
+        }
+    }
+    FbOut o;
+    o.seen = __any_sync(kFull, seen) ? 1u : 0u;
+#pragma unroll
+    for (int d = 16; d; d >>= 1) minv = min(minv, __shfl_xor_sync(kFull, minv, d));
+    for (uint32_t i = lane; i < tail; i += 32) bits[q[i] >> 5] = 0u;   // private slot
+    __syncwarp();
+    o.label = label;
+    o.tail = tail;
+    o.minv = minv;
+    return o;
+}
+
+// Delta of one (candidate, sketch) from its search: the component's size unless a seed covers it.
+__device__ __forceinline__ unsigned long long fb_delta(const SketchView& s, uint32_t r, const FbOut& o) {
+    if (o.label != kNone) {
+        const uint32_t sz = __ldcg(s.size + (size_t)o.label * s.R + r);   // a mark may precede it
+        return (sz & kCovered) ? 0u : sz;
+    }
+    return o.seen ? 0u : o.tail;
+}
+
 // Searches that overflowed the shared-memory queue: one warp per slot, queue and visited
-// bitmap in global scratch (n entries / n bits per slot).
+// bitmap in global scratch (n entries / n bits per slot).  FB_MARK_EVAL (from k_mark_eval):
+// MarkSeed of the winner f.v, then the Marginal of the candidate f.idx (batch slot 0), in order.
 __global__ void __launch_bounds__(32)
 k_fallback(GraphView g, SketchView s, SelState* st, const FbTask* __restrict__ fbt, uint32_t fb_cap,
            uint32_t* __restrict__ fbq, uint32_t* __restrict__ fbb,
@@ -811,74 +986,34 @@ k_fallback(GraphView g, SketchView s, SelState* st, const FbTask* __restrict__ f
     uint32_t* bits = fbb + (size_t)blockIdx.x * nw;
     for (uint32_t t = blockIdx.x; t < ntask; t += gridDim.x) {
         const FbTask f = fbt[t];
-        const uint32_t v = f.v, r = f.r;
-        const bool want_seed = f.kind == FB_EVAL;
-        if (lane == 0) {
-            q[0] = v;
-            atomicOr(bits + (v >> 5), 1u << (v & 31));
-        }
-        __syncwarp();
-        uint32_t head = 0, tail = 1, label = kNone, minv = v;
-        uint32_t seen = want_seed ? (uint32_t)s.seed_flag[v] : 0u;
-        while (head < tail && label == kNone) {
-            const uint32_t x = q[head++];
-            const uint64_t a0 = g.off[x], a1 = g.off[x + 1];
-            for (uint64_t base = a0; base < a1; base += 32) {
-                const uint64_t a = base + lane;
-                bool live = false;
-                uint32_t y = 0, ci = 0;
-                bool cen = false;
-                if (a < a1) {
-                    const uint4 arc = g.arcs[a];
-                    y = arc.x & kArcIdMask;
-                    cen = arc.x >> 31;
-                    ci = arc.y;
-                    live = edge_live_fast(s.smp, ((uint64_t)arc.w << 32) | arc.z, (uint64_t)(r + 1u) * kGamma);
-                }
-                const unsigned cb = __ballot_sync(kFull, live && cen);
-                if (cb) {
-                    const uint32_t c0 = __shfl_sync(kFull, ci, __ffs(cb) - 1);   // the arc's center index
-                    label = s.label[(size_t)c0 * s.R + r];
-                    break;
-                }
-                bool fresh_v = false;
-                if (live) {
-                    const uint32_t bit = 1u << (y & 31);
-                    fresh_v = !(atomicOr(bits + (y >> 5), bit) & bit);
-                }
-                const unsigned nbm = __ballot_sync(kFull, fresh_v);
-                if (fresh_v) {
-                    q[tail + __popc(nbm & ((1u << lane) - 1u))] = y;
-                    if (want_seed && s.seed_flag[y]) seen = 1;
-                    minv = min(minv, y);
-                }
-                tail += __popc(nbm);
-                __syncwarp();
+        const uint32_t r = f.r;
+        if (f.kind == FB_MARK_EVAL) {
+            const FbOut a = fb_search(g, s, f.v, r, false, q, bits);
+            if (lane == 0 && a.label != kNone) atomicOr(s.size + (size_t)a.label * s.R + r, kCovered);
+            __syncwarp();
+            SketchView sp = s;
+            sp.pend = f.v;
+            const FbOut b = fb_search(g, sp, f.idx, r, true, q, bits);
+            if (lane == 0) {
+                const unsigned long long d = fb_delta(sp, r, b);
+                if (d) atomicAdd(fresh, d);
             }
+            __syncwarp();
+            continue;
         }
-        seen = __any_sync(kFull, seen) ? 1u : 0u;
-#pragma unroll
-        for (int d = 16; d; d >>= 1) minv = min(minv, __shfl_xor_sync(kFull, minv, d));
-        for (uint32_t i = lane; i < tail; i += 32) bits[q[i] >> 5] = 0u;   // private slot
-        __syncwarp();
+        const FbOut o = fb_search(g, s, f.v, r, f.kind == FB_EVAL, q, bits);
         if (lane == 0) {
             if (f.kind == FB_EVAL) {
-                unsigned long long d;
-                if (label != kNone) {
-                    const uint32_t sz = s.size[(size_t)label * s.R + r];
-                    d = (sz & kCovered) ? 0u : sz;
-                } else {
-                    d = seen ? 0u : tail;
-                }
+                const unsigned long long d = fb_delta(s, r, o);
                 if (d) atomicAdd(fresh + f.idx, d);
             } else if (f.kind == FB_MARK) {
-                if (label != kNone) atomicOr(s.size + (size_t)label * s.R + r, kCovered);
+                if (o.label != kNone) atomicOr(s.size + (size_t)o.label * s.R + r, kCovered);
             } else {
                 uint64_t pr;
-                if (label != kNone)
-                    pr = ((uint64_t)label << 32) | (s.size[(size_t)label * s.R + r] & ~kCovered);
+                if (o.label != kNone)
+                    pr = ((uint64_t)o.label << 32) | (s.size[(size_t)o.label * s.R + r] & ~kCovered);
                 else
-                    pr = ((uint64_t)(kNoCenterTag | minv) << 32) | tail;
+                    pr = ((uint64_t)(kNoCenterTag | o.minv) << 32) | o.tail;
                 spread_pairs[f.idx] = pr;
             }
         }
@@ -965,6 +1100,7 @@ SketchView sketch_view(const im_ctx* c) {
     s.R = c->R; s.rho = c->rho; s.all_centers = c->all_centers;
     s.cbits = c->d_cbits; s.cidx = c->d_cidx; s.label = c->d_label; s.size = c->d_size;
     s.seed_flag = c->d_seedflag; s.labcache = c->d_labcache; s.smp = c->smp;
+    s.pend = kNone;
     return s;
 }
 
@@ -1041,6 +1177,17 @@ int enqueue_mode(im_ctx* c, unsigned mode, int passes, const SelHandles& hd) {
     const SketchView s = sketch_view(c);
     SelState* st = c->d_sel;
     unsigned long long* fresh = (unsigned long long*)c->d_fresh;
+    if (mode == M_ROUND_START) return launch_reduce_plan(c, hd);
+    if (mode == M_MARK || mode == M_MARK_DIRECT) {
+        if (mode == M_MARK)
+            IM_LAUNCH(c, K_MARK_SEED, k_mark_seed, (c->R + kEvalWarps - 1) / kEvalWarps, kEvalWarps * 32, 0, g, s,
+                      st, c->d_fb_tasks, c->fb_cap, c->d_seedflag, c->d_key);
+        else
+            IM_LAUNCH(c, K_MARK_SEED, k_mark_eval, (c->R + kEvalWarps - 1) / kEvalWarps, kEvalWarps * 32, 0, g, s,
+                      st, c->d_batch, fresh, c->d_fb_tasks, c->fb_cap, c->d_seedflag, c->d_key);
+        launch_fallback(c, g, s);
+        return launch_reduce_plan(c, hd);
+    }
     if (mode == M_COUNT_ABOVE) {
         IM_LAUNCH(c, K_COUNT_ABOVE, k_count_above, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n, st);
         IM_LAUNCH(c, K_SEL_INIT, k_decide, 1, 32, 0, st, c->d_batch, fresh, c->d_key, c->d_stamp, c->d_seed_list,
@@ -1090,14 +1237,6 @@ int enqueue_mode(im_ctx* c, unsigned mode, int passes, const SelHandles& hd) {
     return launch_reduce_plan(c, hd);
 }
 
-int launch_mark(im_ctx* c, const SelHandles& hd) {
-    const GraphView g = graph_view(c);
-    const SketchView s = sketch_view(c);
-    IM_LAUNCH(c, K_MARK_SEED, k_mark_seed, (c->R + kEvalWarps - 1) / kEvalWarps, kEvalWarps * 32, 0, g, s,
-              c->d_sel, c->d_fb_tasks, c->fb_cap, c->d_seedflag, c->d_key, hd);
-    launch_fallback(c, g, s);
-    return IM_OK;
-}
 
 int cap_begin(im_ctx* c, cudaGraph_t graph, const cudaGraphNode_t* deps, size_t ndeps) {
     IM_CUDA(c, cudaStreamBeginCaptureToGraph(c->cap_stream, graph, deps, nullptr, ndeps,
@@ -1165,17 +1304,16 @@ int cap_conditional(im_ctx* c, cudaGraphConditionalHandle h, cudaGraphConditiona
 }
 
 // The whole lazy-greedy loop as one graph, so that rounds run back to back without the host:
-//   sel_begin;
-//   while (round) { reduce_plan;
-//                   while (batch) { switch (mode) { batch kinds, each ending in reduce_plan } };
-//                   mark_seed; fallback }
-// Every decision is taken on the device (k_reduce_plan / k_decide, k_mark_seed).  Both loops
-// are bounded: a round ends after at most 82 batches, the selection after round_end rounds.
+//   sel_begin; while (loop) { switch (mode) { one step: a round's opening reduction, a batch,
+//                                             a count, or a MarkSeed (possibly fused with
+//                                             the next round's first batch) } }
+// Every decision is taken on the device (k_reduce_plan / k_decide via plan_step).  The loop
+// is bounded: a round ends after at most 82 batches, the selection after round_end rounds.
 int build_select_graph_steps(im_ctx* c) {
     SelHandles hd{};
     hd.on = 1;
     const int passes = max_radix_passes(c);
-    // launches per batch mode and per round, counted by dry runs of the same code
+    // launches per step mode, counted by dry runs of the same code
     c->count_only = true;
     int rc = IM_OK;
     for (unsigned m = 0; m < M_COUNT && !rc; ++m) {
@@ -1183,38 +1321,25 @@ int build_select_graph_steps(im_ctx* c) {
         rc = enqueue_mode(c, m, passes, hd);
         hd.launches[m] = (unsigned)c->dry_count;
     }
-    c->dry_count = 0;
-    if (!rc) rc = launch_reduce_plan(c, hd);
-    if (!rc) rc = launch_mark(c, hd);
-    hd.round_launches = (unsigned)c->dry_count;
     c->count_only = false;
     if (rc) return rc;
 
     IM_CUDA(c, cudaGraphCreate(&c->sel_graph, 0));
-    IM_CUDA(c, cudaGraphConditionalHandleCreate(&hd.round, c->sel_graph, 0, 0));
-    cudaGraph_t wround = nullptr, wbatch = nullptr, cases[M_COUNT] = {};
+    // the loop node first, so that its switch's handle exists before sel_begin (which sets
+    // it) is captured in front of it
+    IM_CUDA(c, cudaGraphConditionalHandleCreate(&hd.loop, c->sel_graph, 0, 0));
+    cudaGraph_t wloop = nullptr, cases[M_COUNT] = {};
+    cudaGraphNode_t lnode = nullptr;
+    if ((rc = add_conditional(c, c->sel_graph, hd.loop, cudaGraphCondTypeWhile, 1, &wloop, &lnode))) return rc;
+    IM_CUDA(c, cudaGraphConditionalHandleCreate(&hd.mode, wloop, M_NONE, 0));
     if ((rc = cap_begin(c, c->sel_graph, nullptr, 0))) return rc;
     IM_LAUNCH(c, K_SEL_BEGIN, k_sel_begin, 1, 32, 0, c->d_sel, hd);
-    if ((rc = cap_conditional(c, hd.round, cudaGraphCondTypeWhile, 1, &wround))) return rc;
+    cudaGraphNode_t first = nullptr;
+    if ((rc = cap_frontier(c, &first))) return rc;
     if ((rc = cap_end(c))) return rc;
+    IM_CUDA(c, cudaGraphAddDependencies(c->sel_graph, &first, &lnode, nullptr, 1));
 
-    // round body: the batch loop is added first, so that its switch's handle exists before
-    // the round's first reduce_plan (which sets it) is captured in front of it
-    IM_CUDA(c, cudaGraphConditionalHandleCreate(&hd.batch, wround, 0, 0));
-    cudaGraphNode_t wnode = nullptr;
-    if ((rc = add_conditional(c, wround, hd.batch, cudaGraphCondTypeWhile, 1, &wbatch, &wnode))) return rc;
-    IM_CUDA(c, cudaGraphConditionalHandleCreate(&hd.mode, wbatch, M_NONE, 0));
-    if ((rc = cap_begin(c, wround, nullptr, 0))) return rc;
-    if ((rc = launch_reduce_plan(c, hd))) return rc;
-    cudaGraphNode_t last = nullptr;
-    if ((rc = cap_frontier(c, &last))) return rc;
-    if ((rc = cap_end(c))) return rc;
-    IM_CUDA(c, cudaGraphAddDependencies(wround, &last, &wnode, nullptr, 1));
-    if ((rc = cap_begin(c, wround, &wnode, 1))) return rc;
-    if ((rc = launch_mark(c, hd))) return rc;
-    if ((rc = cap_end(c))) return rc;
-
-    if ((rc = cap_begin(c, wbatch, nullptr, 0))) return rc;
+    if ((rc = cap_begin(c, wloop, nullptr, 0))) return rc;
     if ((rc = cap_conditional(c, hd.mode, cudaGraphCondTypeSwitch, M_COUNT, cases))) return rc;
     if ((rc = cap_end(c))) return rc;
     for (unsigned m = 0; m < M_COUNT; ++m) {
@@ -1254,23 +1379,19 @@ const char* sel_error_text(unsigned e) {
     }
 }
 
-// The same rounds driven from the host: one synchronisation per step to read the decision.
+// The same steps driven from the host: one synchronisation per step to read the decision.
 int run_rounds_host(im_ctx* c) {
     const SelHandles none{};
+    int rc = pull_state(c);
+    if (rc) return rc;
+    if (c->h_sel->err || c->h_sel->round >= c->h_sel->round_end) return IM_OK;
+    unsigned mode = M_ROUND_START;
     for (;;) {
-        int rc = pull_state(c);
-        if (rc) return rc;
-        if (c->h_sel->err || c->h_sel->round >= c->h_sel->round_end) return IM_OK;
-        if ((rc = launch_reduce_plan(c, none))) return rc;
-        for (;;) {
-            if ((rc = pull_state(c))) return rc;
-            const SelState& h = *c->h_sel;
-            if (!h.cont) break;
-            const bool hist = h.mode == M_HIST_SINGLE || h.mode == M_HIST_CHUNK || h.mode == M_SPEC_HIST;
-            const int passes = hist ? h.shift / 8 + 1 : 0;
-            if ((rc = enqueue_mode(c, h.mode, passes, none))) return rc;
-        }
-        if ((rc = launch_mark(c, none))) return rc;
+        const bool hist = mode == M_HIST_SINGLE || mode == M_HIST_CHUNK || mode == M_SPEC_HIST;
+        if ((rc = enqueue_mode(c, mode, hist ? c->h_sel->shift / 8 + 1 : 0, none))) return rc;
+        if ((rc = pull_state(c))) return rc;
+        if (!c->h_sel->cont) return IM_OK;
+        mode = c->h_sel->mode;
     }
 }
 
