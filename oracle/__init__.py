@@ -23,8 +23,9 @@ _SRC = _HERE / "im_oracle.c"
 _LIB = _HERE / "liboracle.so"
 _lib = None
 
-MODE_HASH = 0     # Alg. 3 Sample(e, r): hash rule
+MODE_HASH = 0     # Alg. 3 Sample(e, r): hash rule, one probability p for every edge
 MODE_WORLDS = 1   # sketch r = the live-edge world whose live set is the bit set of r
+MODE_EDGE = 2     # hash rule with each edge's own probability (Graph.set_probs / set_wic)
 
 
 def build(force: bool = False) -> Path:
@@ -56,6 +57,8 @@ def _load():
     lib.or_graph_new.argtypes = [c.c_uint32, c.c_uint64, U32P, U32P]
     lib.or_graph_new.restype = c.c_void_p
     lib.or_graph_free.argtypes = [c.c_void_p]
+    lib.or_graph_set_probs.argtypes = [c.c_void_p, c.POINTER(c.c_double)]
+    lib.or_graph_set_wic.argtypes = [c.c_void_p, c.POINTER(c.c_double)]
     lib.or_labels.argtypes = [c.c_void_p, c.c_int, c.c_uint64, c.c_double, c.c_uint32,
                               c.c_uint32, U32P, c.c_int]
     lib.or_gains.argtypes = [c.c_uint32, c.c_uint32, U32P, U64P]
@@ -131,6 +134,22 @@ class Graph:
         if getattr(self, "_h", None) and _lib is not None:
             _lib.or_graph_free(self._h)
             self._h = None
+
+    # per-edge IC probabilities (Sec. 2: the IC model gives every edge its own p_e)
+    def set_probs(self, p: np.ndarray) -> None:
+        """p[e] for every edge of the input list; used by mode=MODE_EDGE."""
+        pa = np.ascontiguousarray(p, np.float64)
+        if pa.shape != (self.m,):
+            raise ValueError("one probability per edge")
+        _ok(_load().or_graph_set_probs(self._h, pa.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+            "set_probs")
+
+    def set_wic(self) -> np.ndarray:
+        """Weighted cascade p_e = 2 / (d_u + d_v); returns the probabilities."""
+        out = np.empty(self.m, np.float64)
+        _ok(_load().or_graph_set_wic(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+            "set_wic")
+        return out
 
     # per-sketch connected components (Sec. 3 "Sketch Construction")
     def labels(self, seed: int, p: float, R: int, r0: int = 0, mode: int = MODE_HASH,

@@ -12,7 +12,8 @@
  * What it computes, each with the passage it follows:
  *   - live-edge rule, Sec. 2 "fusion" sampling and Alg. 3 Sample(e, r):
  *       edge e is live in sketch r iff random(e, r) is below p_e; here random(e, r) is a
- *       64-bit splitmix64-derived word h(e, r) and the test is h < floor(p * 2^64).
+ *       64-bit splitmix64-derived word h(e, r) and the test is h < floor(p_e * 2^64), with
+ *       one p for all edges or per-edge p_e (given, or the weighted cascade 2/(d_u+d_v)).
  *   - per-sketch connected components, Sec. 3 "Sketch Construction": a plain BFS per
  *     sketch over the CSR, re-hashing every arc; the label is the smallest vertex id.
  *   - component sizes (histogram) and the initial scores Delta[v] = sum_r |C_r(v)|,
@@ -76,33 +77,10 @@ void or_threshold(double p, uint64_t* T, int* all_live) {
 }
 
 /* ------------------------------------------------------------------------
- * The sampler.  mode 0: the hash rule above.  mode 1 ("worlds"): edge e is live in
- * sketch r iff bit e of r is set, so R = 2^m sketches enumerate every live-edge world
- * exactly once (used to pin the oracle against exact expectations).
- * ------------------------------------------------------------------------ */
-typedef struct {
-    int mode;
-    uint64_t seed;
-    uint64_t T;
-    int all_live;
-} or_sampler;
-
-static int or_live(const or_sampler* s, uint64_t e, uint32_t r) {
-    if (s->mode == 1) return (int)((r >> e) & 1u);
-    if (s->all_live) return 1;
-    return or_edge_hash(s->seed, e, r) < s->T;
-}
-
-static int or_make_sampler(or_sampler* s, int mode, uint64_t seed, double p) {
-    s->mode = mode;
-    s->seed = seed;
-    or_threshold(p, &s->T, &s->all_live);
-    return (mode == 0 || mode == 1) ? OR_OK : OR_EINVAL;
-}
-
-/* ------------------------------------------------------------------------
  * Graph: an undirected edge list (u[e], v[e]) and its CSR, each arc tagged by the
  * id e of its edge (both directions share e: the sampling is direction-oblivious).
+ * Optionally per-edge IC probabilities p_e (the IC model of Sec. 2 assigns one to every
+ * edge), kept as thresholds floor(p_e * 2^64) and "always live" flags.
  * ------------------------------------------------------------------------ */
 typedef struct {
     uint32_t n;
@@ -110,7 +88,44 @@ typedef struct {
     uint64_t* off;    /* n + 1 */
     uint32_t* adj;    /* 2m    */
     uint64_t* aeid;   /* 2m    */
+    uint64_t* eT;     /* m, or NULL: per-edge thresholds */
+    uint8_t* eall;    /* m, or NULL: p_e >= 1            */
 } or_graph;
+
+/* ------------------------------------------------------------------------
+ * The sampler.  mode 0: the hash rule above with one p.  mode 1 ("worlds"): edge e is
+ * live in sketch r iff bit e of r is set, so R = 2^m sketches enumerate every live-edge
+ * world exactly once (used to pin the oracle against exact expectations).  mode 2: the
+ * hash rule with edge e's own threshold (or_graph_set_probs / or_graph_set_wic).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int mode;
+    uint64_t seed;
+    uint64_t T;
+    int all_live;
+    const uint64_t* eT;
+    const uint8_t* eall;
+} or_sampler;
+
+static int or_live(const or_sampler* s, uint64_t e, uint32_t r) {
+    if (s->mode == 1) return (int)((r >> e) & 1u);
+    if (s->mode == 2) {
+        if (s->eall[e]) return 1;
+        return or_edge_hash(s->seed, e, r) < s->eT[e];
+    }
+    if (s->all_live) return 1;
+    return or_edge_hash(s->seed, e, r) < s->T;
+}
+
+static int or_make_sampler(or_sampler* s, int mode, uint64_t seed, double p, const or_graph* g) {
+    s->mode = mode;
+    s->seed = seed;
+    or_threshold(p, &s->T, &s->all_live);
+    s->eT = g ? g->eT : NULL;
+    s->eall = g ? g->eall : NULL;
+    if (mode == 2) return (s->eT && s->eall) ? OR_OK : OR_EINVAL;
+    return (mode == 0 || mode == 1) ? OR_OK : OR_EINVAL;
+}
 
 or_graph* or_graph_new(uint32_t n, uint64_t m, const uint32_t* eu, const uint32_t* ev) {
     for (uint64_t e = 0; e < m; ++e)
@@ -142,7 +157,48 @@ or_graph* or_graph_new(uint32_t n, uint64_t m, const uint32_t* eu, const uint32_
 
 void or_graph_free(or_graph* g) {
     if (!g) return;
-    free(g->off); free(g->adj); free(g->aeid); free(g);
+    free(g->off); free(g->adj); free(g->aeid); free(g->eT); free(g->eall); free(g);
+}
+
+/* Per-edge probabilities p[e] (edge order of the input list). */
+int or_graph_set_probs(or_graph* g, const double* p) {
+    if (!g || (!p && g->m)) return OR_EINVAL;
+    if (!g->eT) g->eT = (uint64_t*)malloc((g->m + 1) * sizeof(uint64_t));
+    if (!g->eall) g->eall = (uint8_t*)malloc(g->m + 1);
+    if (!g->eT || !g->eall) return OR_ENOMEM;
+    for (uint64_t e = 0; e < g->m; ++e) {
+        int all = 0;
+        or_threshold(p[e], &g->eT[e], &all);
+        g->eall[e] = (uint8_t)all;
+    }
+    return OR_OK;
+}
+
+/* The weighted cascade on an undirected graph: p_e = 2 / (d_u + d_v), the mean of the two
+ * directions' 1 / d (degrees count every edge of the list, parallel edges included). */
+int or_graph_set_wic(or_graph* g, double* p_out) {
+    if (!g) return OR_EINVAL;
+    double* p = (double*)malloc((g->m + 1) * sizeof(double));
+    if (!p) return OR_ENOMEM;
+    /* the endpoints of e are read back from the arcs tagged e */
+    uint32_t* eu = (uint32_t*)malloc((g->m + 1) * sizeof(uint32_t));
+    uint32_t* ev = (uint32_t*)malloc((g->m + 1) * sizeof(uint32_t));
+    uint8_t* seen = (uint8_t*)calloc(g->m + 1, 1);
+    if (!eu || !ev || !seen) { free(p); free(eu); free(ev); free(seen); return OR_ENOMEM; }
+    for (uint32_t x = 0; x < g->n; ++x)
+        for (uint64_t a = g->off[x]; a < g->off[x + 1]; ++a) {
+            uint64_t e = g->aeid[a];
+            if (!seen[e]) { eu[e] = x; ev[e] = g->adj[a]; seen[e] = 1; }
+        }
+    for (uint64_t e = 0; e < g->m; ++e) {
+        double du = (double)(g->off[eu[e] + 1] - g->off[eu[e]]);
+        double dv = (double)(g->off[ev[e] + 1] - g->off[ev[e]]);
+        p[e] = 2.0 / (du + dv);
+    }
+    int rc = or_graph_set_probs(g, p);
+    if (p_out) memcpy(p_out, p, g->m * sizeof(double));
+    free(p); free(eu); free(ev); free(seen);
+    return rc;
 }
 
 /* ------------------------------------------------------------------------
@@ -176,7 +232,7 @@ static void or_bfs_labels(const or_graph* g, const or_sampler* s, uint32_t r,
 int or_labels(const or_graph* g, int mode, uint64_t seed, double p, uint32_t r0, uint32_t count,
               uint32_t* L, int nthreads) {
     or_sampler s;
-    if (!g || or_make_sampler(&s, mode, seed, p) != OR_OK) return OR_EINVAL;
+    if (!g || or_make_sampler(&s, mode, seed, p, g) != OR_OK) return OR_EINVAL;
     int err = OR_OK;
     if (nthreads < 1) nthreads = 1;
 #pragma omp parallel num_threads(nthreads)
@@ -528,7 +584,7 @@ int or_compact_greedy(const or_graph* g, int mode, uint64_t seed, double p, uint
     const uint32_t n = g->n;
     or_compact_ctx C;
     memset(&C, 0, sizeof C);
-    if (or_make_sampler(&C.s, mode, seed, p) != OR_OK) return OR_EINVAL;
+    if (or_make_sampler(&C.s, mode, seed, p, g) != OR_OK) return OR_EINVAL;
     C.g = g; C.R = R; C.label = label;
     uint32_t* cidx = (uint32_t*)malloc(((size_t)n + 1) * sizeof(uint32_t));
     uint8_t* in_s = (uint8_t*)calloc((size_t)n + 1, 1);
@@ -573,7 +629,7 @@ int or_compact_marginal(const or_graph* g, int mode, uint64_t seed, double p, ui
     if (!g || v >= g->n) return OR_EINVAL;
     or_compact_ctx C;
     memset(&C, 0, sizeof C);
-    if (or_make_sampler(&C.s, mode, seed, p) != OR_OK) return OR_EINVAL;
+    if (or_make_sampler(&C.s, mode, seed, p, g) != OR_OK) return OR_EINVAL;
     C.g = g; C.R = R; C.label = label; C.size = (uint32_t*)size; C.cidx = cidx; C.in_s = in_s;
     C.queue = (uint32_t*)malloc(((size_t)g->n + 1) * sizeof(uint32_t));
     C.stamp = (uint32_t*)calloc((size_t)g->n + 1, sizeof(uint32_t));

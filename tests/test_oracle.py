@@ -360,3 +360,74 @@ def test_oracle_rejects_bad_edges():
         oracle.Graph(3, np.array([0], np.uint32), np.array([3], np.uint32))
     with pytest.raises(ValueError):
         oracle.Graph(3, np.array([1], np.uint32), np.array([1], np.uint32))
+
+
+# ---- per-edge probabilities (Sec. 2: the IC model gives every edge its own p_e) --------
+
+@pytest.mark.parametrize("p", [0.0, 0.05, 0.37, 1.0])
+def test_per_edge_mode_with_equal_probabilities_is_the_uniform_mode(p):
+    n, u, v = graphgen.erdos_renyi(400, 1500, 11)
+    G = oracle.Graph(n, u, v)
+    G.set_probs(np.full(len(u), p))
+    assert np.array_equal(G.labels(7, -1.0, 12, mode=oracle.MODE_EDGE), G.labels(7, p, 12))
+
+
+def test_per_edge_zero_one_probabilities_give_components_of_the_always_live_edges():
+    n, u, v = graphgen.erdos_renyi(500, 1400, 12)
+    rng = np.random.default_rng(3)
+    p = rng.integers(0, 2, len(u)).astype(np.float64)
+    G = oracle.Graph(n, u, v)
+    G.set_probs(p)
+    keep = p == 1.0
+    A = coo_matrix((np.ones(keep.sum()), (u[keep], v[keep])), shape=(n, n))
+    _, comp = connected_components(A, directed=False)
+    first = {}
+    for x in range(n):
+        first.setdefault(comp[x], x)
+    want = np.array([first[comp[x]] for x in range(n)], np.uint32)
+    L = G.labels(5, -1.0, 6, mode=oracle.MODE_EDGE)
+    for r in range(6):
+        assert np.array_equal(L[r], want)
+
+
+def test_per_edge_live_frequencies_follow_each_probability():
+    # a perfect matching: u and its partner share a component in sketch r iff the edge is
+    # live there, so (gain(u) - R) / R is the edge's live fraction
+    m, R = 64, 4096
+    u = np.arange(0, 2 * m, 2, dtype=np.uint32)
+    v = u + 1
+    p = np.linspace(0.01, 0.99, m)
+    G = oracle.Graph(2 * m, u, v)
+    G.set_probs(p)
+    gain = oracle.gains(G.labels(21, -1.0, R, mode=oracle.MODE_EDGE)).astype(np.int64)
+    frac = (gain[u] - R) / R
+    sd = np.sqrt(p * (1 - p) / R)
+    assert np.all(np.abs(frac - p) <= 5 * sd + 1e-12)
+    assert np.array_equal(gain[u], gain[v])
+
+
+def test_wic_probabilities_closed_forms():
+    # star K_{1,d}: every edge joins a vertex of degree d and one of degree 1
+    d = 9
+    G = oracle.Graph(d + 1, np.zeros(d, np.uint32), np.arange(1, d + 1, dtype=np.uint32))
+    assert np.allclose(G.set_wic(), 2.0 / (d + 1))
+    # path 0-1-2-3-4: end edges 2/3, inner edges 2/4
+    G = oracle.Graph(5, np.array([0, 1, 2, 3], np.uint32), np.array([1, 2, 3, 4], np.uint32))
+    assert np.array_equal(G.set_wic(), np.array([2 / 3, 0.5, 0.5, 2 / 3]))
+    # a single edge: p = 1, always live
+    G = oracle.Graph(2, np.array([0], np.uint32), np.array([1], np.uint32))
+    assert np.array_equal(G.set_wic(), [1.0])
+    assert np.all(G.labels(3, -1.0, 4, mode=oracle.MODE_EDGE) == 0)
+
+
+def test_per_edge_mode_compact_greedy_equals_memoised_greedy():
+    n, u, v = graphgen.erdos_renyi(600, 2400, 13)
+    G = oracle.Graph(n, u, v)
+    G.set_probs(np.random.default_rng(8).uniform(0.1, 0.3, len(u)))
+    R, k = 24, 6
+    L = G.labels(42, -1.0, R, mode=oracle.MODE_EDGE)
+    ctr = oracle.centers(n, 42, 0.2)
+    lab, sz = oracle.compact(L, ctr)
+    s1, g1 = oracle.greedy(L, k)
+    s2, g2 = G.compact_greedy(42, -1.0, R, ctr, lab, sz, k, mode=oracle.MODE_EDGE)
+    assert np.array_equal(s1, s2) and np.array_equal(g1, g2)
