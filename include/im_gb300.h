@@ -71,6 +71,25 @@ int im_load_graph(im_ctx* ctx, uint32_t n, uint64_t m, const uint32_t* u, const 
                   int ptr_kind);
 
 /*
+ * im_set_edge_probs -- the IC probability of every edge (Sec. 2: the IC model gives each edge
+ * its own p_e; the paper's other workloads are uniform random and weighted-cascade ones).
+ *   model  IM_PROBS_UNIFORM: one p for every edge, the p argument of im_build_sketches
+ *                            (the default; p is ignored otherwise);
+ *          IM_PROBS_ARRAY:   p[e] for edge e of the loaded list (m doubles, host or device
+ *                            per ptr_kind; values >= 1 always live, <= 0 or NaN never);
+ *          IM_PROBS_WIC:     weighted cascade p_e = 2 / (d_u + d_v), degrees counting every
+ *                            edge of the list at both ends (p is ignored).
+ * Edge e is live in sketch r iff h(e, r) < floor(p_e * 2^64) (h as in im_build_sketches).
+ * Costs 24 m bytes of device memory.  Discards the sketches and any selection;
+ * im_load_graph returns to IM_PROBS_UNIFORM.
+ * Errors: IM_EINVAL, IM_ESTATE (no graph), IM_ENOMEM, IM_ECUDA.
+ */
+#define IM_PROBS_UNIFORM 0
+#define IM_PROBS_ARRAY 1
+#define IM_PROBS_WIC 2
+int im_set_edge_probs(im_ctx* ctx, int model, const double* p, int ptr_kind);
+
+/*
  * im_build_sketches -- Step 1 of Alg. 1: build R compact sketches (Sec. 3, Alg. 3).
  *   R      number of sketches (1 <= R <= 65536).  Sketch r in [0, R) is the sampled graph
  *          G'_r whose live edges are those with h(e, r) < floor(p * 2^64), where

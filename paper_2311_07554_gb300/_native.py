@@ -52,6 +52,7 @@ def lib():
         "im_create": ([c.POINTER(vp), u32, u64, vp, vp, i32, vp], i32),
         "im_build_sketches": ([vp, u32, u64, dbl, dbl], i32),
         "im_load_graph": ([vp, u32, u64, vp, vp, i32], i32),
+        "im_set_edge_probs": ([vp, i32, vp, i32], i32),
         "im_select_seeds": ([vp, u32, vp, vp], i32),
         "im_spread": ([vp, vp, u32, c.POINTER(u64)], i32),
         "im_reset_selection": ([vp], i32),
@@ -132,6 +133,20 @@ def im_load_graph(ctx, n: int, u, v):
     if len(v) != m:
         raise ValueError("u and v differ in length")
     _check(ctx, lib().im_load_graph(ctx, n, m, pu, pv, ku))
+
+
+IM_PROBS_UNIFORM, IM_PROBS_ARRAY, IM_PROBS_WIC = 0, 1, 2
+
+
+def im_set_edge_probs(ctx, model: int, p=None):
+    """model IM_PROBS_UNIFORM / IM_PROBS_WIC (p ignored) or IM_PROBS_ARRAY with p: one float64
+    per edge (numpy array or CUDA tensor)."""
+    pp, kind = (None, IM_PTR_HOST)
+    if model == IM_PROBS_ARRAY:
+        if hasattr(p, "dtype") and str(p.dtype) not in ("float64", "torch.float64"):
+            raise ValueError("probabilities must be float64")
+        pp, kind = _ptr(p)
+    _check(ctx, lib().im_set_edge_probs(ctx, model, pp, kind))
 
 
 def im_build_sketches(ctx, R: int, seed: int, p: float, alpha: float):
@@ -286,6 +301,10 @@ class IMContext:
     def load_graph(self, n, u, v):
         im_load_graph(self.h, n, u, v)
         self.n = int(n)
+        return self
+
+    def set_edge_probs(self, model, p=None):
+        im_set_edge_probs(self.h, model, p)
         return self
 
     def build_sketches(self, R, seed, p, alpha):

@@ -267,6 +267,8 @@ int im_load_graph(im_ctx* c, uint32_t n, uint64_t m, const uint32_t* u, const ui
     if (m > 0 && (!u || !v)) return im_fail(c, IM_EINVAL, "edge arrays are NULL");
     IM_CUDA(c, cudaStreamSynchronize(c->stream));
     if (n != c->n) free_sketch_state(c);   // every per-vertex buffer changes size
+    if (m != c->m) { dfree(c->d_edgeT); dfree(c->d_arcT); }
+    c->prob_model = IM_PROBS_UNIFORM;      // probabilities belong to the old edge list
     c->built = false;
     c->seeds.clear();
     c->seed_gains.clear();
@@ -274,6 +276,40 @@ int im_load_graph(im_ctx* c, uint32_t n, uint64_t m, const uint32_t* u, const ui
     c->n = n;
     c->m = m;
     return load_graph(c, u, v, ptr_kind);
+}
+
+int im_set_edge_probs(im_ctx* c, int model, const double* p, int ptr_kind) {
+    if (!c) return IM_EINVAL;
+    if (!c->graph_ok) return im_fail(c, IM_ESTATE, "no valid graph is loaded");
+    if (model != IM_PROBS_UNIFORM && model != IM_PROBS_ARRAY && model != IM_PROBS_WIC)
+        return im_fail(c, IM_EINVAL, "unknown probability model");
+    if (model == IM_PROBS_ARRAY && c->m > 0) {
+        if (!p) return im_fail(c, IM_EINVAL, "p is NULL");
+        if (ptr_kind != IM_PTR_HOST && ptr_kind != IM_PTR_DEVICE) return im_fail(c, IM_EINVAL, "bad ptr_kind");
+    }
+    IM_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->built = false;   // the sketches belong to the old probabilities
+    c->seeds.clear();
+    c->seed_gains.clear();
+    c->round_evals.clear();
+    im_select_graph_free(c);
+    c->prob_model = IM_PROBS_UNIFORM;
+    if (model == IM_PROBS_UNIFORM) return IM_OK;
+    const double* dp = p;
+    double* tmp = nullptr;
+    if (model == IM_PROBS_ARRAY && ptr_kind == IM_PTR_HOST && c->m > 0) {
+        if (!dalloc(tmp, c->m)) return im_fail(c, IM_ENOMEM, "probabilities");
+        if (cudaMemcpyAsync(tmp, p, c->m * sizeof(double), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+            dfree(tmp);
+            return im_fail(c, IM_ECUDA, "probabilities");
+        }
+        dp = tmp;
+    }
+    const int rc = im_edge_probs(c, model, dp);
+    dfree(tmp);
+    if (rc) return rc;
+    c->prob_model = model;
+    return IM_OK;
 }
 
 int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alpha) {
@@ -292,12 +328,14 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
     const uint32_t all = rho == n ? 1u : 0u;
 
     // sampler (Sec. 2 fusion; threshold T = floor(p 2^64), exact)
-    Sampler smp;
+    Sampler smp{};
     smp.salt = mix64(seed + kGamma);
     smp.all_live = 0;
     smp.T = 0;
     if (p >= 1.0) smp.all_live = 1;
     else if (p > 0.0) smp.T = (uint64_t)std::ldexp(p, 64);
+    smp.eT = c->prob_model != IM_PROBS_UNIFORM ? c->d_edgeT : nullptr;
+    smp.aT = c->prob_model != IM_PROBS_UNIFORM ? c->d_arcT : nullptr;
 
     // sketches per edge pass: union-find launches are bound by their critical path, not by
     // their size, so fewer, larger batches win; memory is 12 bytes per vertex per sketch
@@ -314,8 +352,9 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
     // live-pair records of one batch: expected p m B, with a generous margin; a batch that
     // still overflows falls back to the fused sample+union loop on the device
     uint64_t live_cap = 0;
-    if (c->m > 0 && (smp.all_live || smp.T != 0)) {
-        const double ex = (smp.all_live ? 1.0 : p) * (double)c->m * B;
+    if (c->m > 0 && (smp.eT || smp.all_live || smp.T != 0)) {
+        const double pe = smp.eT ? c->mean_p : smp.all_live ? 1.0 : p;
+        const double ex = pe * (double)c->m * B;
         double cap = 1.3 * ex + 16.0 * std::sqrt(ex) + 65536.0;
         if (cap > (double)(1ull << 28)) cap = (double)(1ull << 28);
         live_cap = (uint64_t)cap;
@@ -329,7 +368,8 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
                              c->all_centers == all && c->live_cap == live_cap && c->spec_count == nspec;
     if (!same_layout) {
         free_sketch_state(c);
-    } else if (c->smp.salt != smp.salt || c->smp.T != smp.T || c->smp.all_live != smp.all_live) {
+    } else if (c->smp.salt != smp.salt || c->smp.T != smp.T || c->smp.all_live != smp.all_live ||
+               c->smp.eT != smp.eT || c->smp.aT != smp.aT) {
         im_select_graph_free(c);   // the captured kernels carry the sampler
     }
     c->built = false;
@@ -591,6 +631,7 @@ void im_destroy(im_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_sketch_state(c);
     dfree(c->d_edges); dfree(c->d_off); dfree(c->d_arcs); dfree(c->d_arc_cur); dfree(c->d_upload);
+    dfree(c->d_edgeT); dfree(c->d_arcT);
     dfree(c->d_spread_pairs); dfree(c->d_spread_seeds); dfree(c->d_spread_total); dfree(c->d_live_total);
     if (c->d_sel) cudaFree(c->d_sel);
     if (c->h_sel) cudaFreeHost(c->h_sel);

@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(256)
 k_arc_fill(const uint2* __restrict__ edges, uint64_t m, const uint64_t* __restrict__ off,
            uint32_t* __restrict__ ccur, uint32_t* __restrict__ ncur, uint4* __restrict__ arcs,
            uint64_t salt, const uint32_t* __restrict__ cbits, const uint32_t* __restrict__ cidx,
-           int all_centers) {
+           int all_centers, const uint64_t* __restrict__ eT, uint64_t* __restrict__ aT) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     // the loop bound is uniform over the block, so every warp-wide call has all lanes
     for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < m; base += stride) {
@@ -90,8 +90,47 @@ k_arc_fill(const uint2* __restrict__ edges, uint64_t m, const uint64_t* __restri
             const uint32_t ix = !cx ? kNone : all_centers ? ed.x : cidx[ed.x];
             arcs[pa] = make_uint4(ed.y | ((cy ? 1u : 0u) << 31), iy, klo, khi);
             arcs[pb] = make_uint4(ed.x | ((cx ? 1u : 0u) << 31), ix, klo, khi);
+            if (eT) {   // per-edge probabilities: each arc carries its edge's threshold
+                const uint64_t T = eT[e];
+                aT[pa] = T;
+                aT[pb] = T;
+            }
         }
     }
+}
+
+// Threshold word of a probability: floor(p 2^64) (exact: ldexp scales by a power of two and
+// the conversion truncates), kAllLive for p >= 1, 0 for p <= 0 or NaN.
+__device__ __forceinline__ uint64_t prob_T(double p) {
+    if (p >= 1.0) return kAllLive;
+    if (!(p > 0.0)) return 0;
+    return (uint64_t)ldexp(p, 64);
+}
+
+__global__ void k_probs_T(const double* __restrict__ p, uint64_t m, uint64_t* __restrict__ eT) {
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (uint64_t)gridDim.x * blockDim.x)
+        eT[e] = prob_T(p[e]);
+}
+
+// Weighted cascade on an undirected graph: p_e = 2 / (d_u + d_v), the mean of the two
+// directions' 1/d (degrees count every edge of the list at both ends).
+__global__ void k_wic_T(const uint2* __restrict__ edges, uint64_t m, const uint64_t* __restrict__ off,
+                        uint64_t* __restrict__ eT) {
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint2 ed = edges[e];
+        const double du = (double)(off[ed.x + 1] - off[ed.x]), dv = (double)(off[ed.y + 1] - off[ed.y]);
+        eT[e] = prob_T(2.0 / (du + dv));
+    }
+}
+
+// Sum of the probabilities the thresholds stand for (sizing of the live-record buffers).
+__global__ void k_T_sum(const uint64_t* __restrict__ eT, uint64_t m, double* __restrict__ sum) {
+    double acc = 0.0;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (uint64_t)gridDim.x * blockDim.x)
+        acc += eT[e] == kAllLive ? 1.0 : (double)eT[e] * 0x1p-64;
+#pragma unroll
+    for (int d = 16; d; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+    if ((threadIdx.x & 31) == 0) atomicAdd(sum, acc);
 }
 
 // ---- exclusive scan, u32 -> u64 (tiles of 4096: 1024 threads x 4 items) -------------
@@ -263,12 +302,40 @@ int im_graph_build(im_ctx* c, const uint32_t* d_u, const uint32_t* d_v) {
     return rc;
 }
 
+// Per-edge probabilities: thresholds of every edge (and their mean), on the device.
+int im_edge_probs(im_ctx* c, int model, const double* d_p) {
+    const uint64_t m = c->m;
+    const uint64_t m_pad = (m + 1) & ~1ull;   // k_sample_emit reads them in pairs
+    if (!c->d_edgeT) {
+        if (cudaMalloc(&c->d_edgeT, (m_pad + 2) * sizeof(uint64_t)) != cudaSuccess ||
+            cudaMalloc(&c->d_arcT, (2 * m + 2) * sizeof(uint64_t)) != cudaSuccess)
+            return im_fail(c, IM_ENOMEM, "edge thresholds");
+    }
+    IM_CUDA(c, cudaMemsetAsync(c->d_edgeT, 0, (m_pad + 2) * sizeof(uint64_t), c->stream));
+    if (m > 0) {
+        if (model == IM_PROBS_WIC)
+            IM_LAUNCH(c, K_ARC_KEYS, k_wic_T, grid_for(m, 256), 256, 0, c->d_edges, m, c->d_off, c->d_edgeT);
+        else
+            IM_LAUNCH(c, K_ARC_KEYS, k_probs_T, grid_for(m, 256), 256, 0, d_p, m, c->d_edgeT);
+    }
+    double* d_sum = reinterpret_cast<double*>(c->d_edgeT + m_pad + 1);   // a spare word
+    IM_CUDA(c, cudaMemsetAsync(d_sum, 0, sizeof(double), c->stream));
+    if (m > 0)
+        IM_LAUNCH(c, K_ARC_KEYS, k_T_sum, grid_for(m, 256, 152u * 8u), 256, 0, c->d_edgeT, m, d_sum);
+    double sum = 0.0;
+    IM_CUDA(c, cudaMemcpyAsync(&sum, d_sum, sizeof sum, cudaMemcpyDeviceToHost, c->stream));
+    IM_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->mean_p = m ? sum / (double)m : 0.0;
+    return IM_OK;
+}
+
 int im_arc_keys(im_ctx* c, uint64_t salt) {
     if (c->m > 0) {
         const uint32_t n = c->n;
         IM_CUDA(c, cudaMemsetAsync(c->d_arc_cur, 0, 2 * (size_t)n * sizeof(uint32_t), c->stream));
         IM_LAUNCH(c, K_ARC_KEYS, k_arc_fill, grid_for(c->m, 256, 152u * 16u), 256, 0, c->d_edges, c->m, c->d_off,
-                  c->d_arc_cur, c->d_arc_cur + n, c->d_arcs, salt, c->d_cbits, c->d_cidx, (int)c->all_centers);
+                  c->d_arc_cur, c->d_arc_cur + n, c->d_arcs, salt, c->d_cbits, c->d_cidx, (int)c->all_centers,
+                  c->smp.eT, c->d_arcT);
     }
     IM_CUDA(c, cudaGetLastError());
     c->arc_salt = salt;

@@ -31,31 +31,47 @@ __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 }
 
 // Live-edge rule of the "fusion" sampling (Sec. 2, Alg. 3 Sample): edge e is live in
-// sketch r iff mix(key_e + (r+1) G) < T, key_e = mix(salt ^ e), salt = mix(seed + G),
-// T = floor(p 2^64); all_live covers p >= 1.
+// sketch r iff mix(key_e + (r+1) G) < T_e, key_e = mix(salt ^ e), salt = mix(seed + G),
+// T_e = floor(p_e 2^64) -- one p for every edge (T, all_live for p >= 1), or per edge
+// (Sec. 2's IC model gives each edge its own p_e): eT by edge, aT by arc, with the word
+// kAllLive for p_e >= 1 (no p_e < 1 reaches it).
+constexpr uint64_t kAllLive = ~0ull;
+
 struct Sampler {
     uint64_t salt;
     uint64_t T;
     uint32_t all_live;
+    const uint64_t* eT;   // per-edge threshold words (input edge order), or nullptr
+    const uint64_t* aT;   // the same per arc (arc order), or nullptr
 };
+
+// The threshold word of every edge when there is one p.
+__host__ __device__ __forceinline__ uint64_t uniform_T(const Sampler& s) {
+    return s.all_live ? kAllLive : s.T;
+}
 
 __device__ __forceinline__ uint64_t edge_key(const Sampler& s, uint64_t e) {
     return mix64(s.salt ^ e);
 }
 
-__device__ __forceinline__ bool edge_live(const Sampler& s, uint64_t key, uint32_t r) {
-    return s.all_live || mix64(key + (uint64_t)(r + 1u) * kGamma) < s.T;
-}
-
 __device__ __forceinline__ uint32_t mix64_hi(uint64_t x);
 
-// Same decision as edge_live, deciding on the high word of the hash whenever it differs from
-// the high word of T (all but a 2^-32 fraction of the pairs).
-__device__ __forceinline__ bool edge_live_fast(const Sampler& s, uint64_t key, uint64_t rg) {
-    if (s.all_live) return true;
-    const uint32_t hh = mix64_hi(key + rg), th = (uint32_t)(s.T >> 32);
+// Exact live test of a (key, sketch) pair against the threshold word T.
+__device__ __forceinline__ bool live_T(uint64_t key, uint64_t rg, uint64_t T) {
+    return T == kAllLive || mix64(key + rg) < T;
+}
+
+// Same decision, taken on the high word of the hash whenever it differs from the high word
+// of T (all but a 2^-32 fraction of the pairs).
+__device__ __forceinline__ bool live_T_fast(uint64_t key, uint64_t rg, uint64_t T) {
+    if (T == kAllLive) return true;
+    const uint32_t hh = mix64_hi(key + rg), th = (uint32_t)(T >> 32);
     if (hh != th) return hh < th;
-    return mix64(key + rg) < s.T;
+    return mix64(key + rg) < T;
+}
+
+__device__ __forceinline__ bool edge_live(const Sampler& s, uint64_t key, uint32_t r) {
+    return live_T(key, (uint64_t)(r + 1u) * kGamma, uniform_T(s));
 }
 
 // High 32 bits of mix64(x), computed without the low half of the last multiply and shift:
@@ -228,6 +244,11 @@ struct im_ctx {
     uint32_t graph_n_alloc = 0;      // n, m the graph buffers were allocated for
     uint64_t graph_m_alloc = 0;
     bool graph_ok = false;           // a valid edge list is loaded
+    // per-edge IC probabilities (im_set_edge_probs)
+    int prob_model = 0;              // IM_PROBS_*
+    uint64_t* d_edgeT = nullptr;     // threshold words by edge (input order, padded to even)
+    uint64_t* d_arcT = nullptr;      // the same by arc, written by every arc fill
+    double mean_p = 0.0;
     uint32_t* d_upload = nullptr;    // staging for host edge lists (2 x upload_cap ids)
     uint64_t upload_cap = 0;   // 2n arc-fill cursors (centers from the front, others from the back)
     uint64_t arc_salt = 0;
@@ -353,6 +374,7 @@ void im_prof_end(im_ctx* c, int kid, int ev0);
 // im_graph.cu
 int im_graph_build(im_ctx* c, const uint32_t* d_u, const uint32_t* d_v);
 int im_arc_keys(im_ctx* c, uint64_t salt);   // keys and center bits of every arc
+int im_edge_probs(im_ctx* c, int model, const double* d_p);   // per-edge thresholds
 int im_scan_u32_to_u64(im_ctx* c, const uint32_t* d_in, uint64_t* d_out, uint64_t count);
 // im_sketch.cu
 int im_select_centers(im_ctx* c, uint32_t* d_flags_tmp, uint64_t* d_scan_tmp);

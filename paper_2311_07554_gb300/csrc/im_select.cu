@@ -80,6 +80,7 @@ __device__ BfsOut warp_bfs_from(const GraphView& g, const SketchView& s, uint32_
     uint32_t seen = want_seed ? (uint32_t)is_seed(s, v) : 0u;
     uint32_t minv = v;
     const uint64_t rg = (uint64_t)(r + 1u) * kGamma;
+    const uint64_t Tw = uniform_T(s.smp);   // every arc's threshold, unless they have their own
     uint32_t* hs = q + kQcap;   // visited set (the queue holds the same ids, in order)
     for (uint32_t i = lane; i < kHashSlots; i += 32) hs[i] = kNone;
     __syncwarp();
@@ -128,6 +129,7 @@ __device__ BfsOut warp_bfs_from(const GraphView& g, const SketchView& s, uint32_
         // kBfsChunks 32-arc chunks per step: their loads are in flight together
         for (uint32_t base = 0; base < total; base += 32u * kBfsChunks) {
             uint4 arcs4[kBfsChunks];
+            uint64_t tk[kBfsChunks];
 #pragma unroll
             for (int k = 0; k < kBfsChunks; ++k) {
                 const uint32_t t = base + 32u * k + lane;
@@ -151,7 +153,9 @@ __device__ BfsOut warp_bfs_from(const GraphView& g, const SketchView& s, uint32_
                 const uint32_t pon = __shfl_sync(kFull, preN, lo);
                 const uint64_t ao = inC ? aoc : aon;
                 const uint32_t po = inC ? poc : pon;
-                arcs4[k] = (t < total) ? g.arcs[ao + (tt - po)] : make_uint4(0, 0, 0, 0);
+                const uint64_t ai = ao + (tt - po);
+                arcs4[k] = (t < total) ? g.arcs[ai] : make_uint4(0, 0, 0, 0);
+                tk[k] = (t < total && s.smp.aT) ? s.smp.aT[ai] : Tw;
             }
 #pragma unroll
             for (int k = 0; k < kBfsChunks; ++k) {
@@ -165,7 +169,7 @@ __device__ BfsOut warp_bfs_from(const GraphView& g, const SketchView& s, uint32_
                     y = arc.x & kArcIdMask;
                     cen = arc.x >> 31;
                     ci = arc.y;
-                    live = edge_live_fast(s.smp, ((uint64_t)arc.w << 32) | arc.z, rg);
+                    live = live_T_fast(((uint64_t)arc.w << 32) | arc.z, rg, tk[k]);
                 }
                 const unsigned cb = __ballot_sync(kFull, live && cen);
                 if (cb) {
@@ -228,20 +232,26 @@ __device__ LaneRes get_center_32(const GraphView& g, const SketchView& s, uint32
     uint32_t cnt = 0;        // live non-center neighbours of x recorded
     bool over = false;       // more than kLaneQ - 1 of them
     const uint64_t rg = (uint64_t)(r + 1u) * kGamma;
+    const uint64_t Tw = uniform_T(s.smp);
     const uint64_t a0 = g.off[x], a1 = g.off[x + 1];
     for (uint64_t base = a0; base < a1; base += 32) {
         if (!__any_sync(kFull, act)) break;
         const uint64_t a = base + lane;
         uint4 arc = make_uint4(0, 0, 0, 0);
-        if (a < a1) arc = g.arcs[a];
+        uint64_t ta = Tw;
+        if (a < a1) {
+            arc = g.arcs[a];
+            if (s.smp.aT) ta = s.smp.aT[a];
+        }
         const uint32_t nv = (uint32_t)min((uint64_t)32, a1 - base);
         for (uint32_t i = 0; i < nv; ++i) {
             const uint32_t yc = __shfl_sync(kFull, arc.x, i);
             const uint32_t klo = __shfl_sync(kFull, arc.z, i);
             const uint32_t khi = __shfl_sync(kFull, arc.w, i);
+            const uint64_t Ti = s.smp.aT ? __shfl_sync(kFull, ta, i) : Tw;
             if (act) {
                 const uint64_t key = ((uint64_t)khi << 32) | klo;
-                if (edge_live_fast(s.smp, key, rg)) {
+                if (live_T_fast(key, rg, Ti)) {
                     const uint32_t y = yc & kArcIdMask;
                     if (yc >> 31) {
                         o.label = s.label[(size_t)center_index(s, y) * s.R + r];
@@ -927,7 +937,8 @@ __device__ FbOut fb_search(const GraphView& g, const SketchView& s, uint32_t v, 
                 y = arc.x & kArcIdMask;
                 cen = arc.x >> 31;
                 ci = arc.y;
-                live = edge_live_fast(s.smp, ((uint64_t)arc.w << 32) | arc.z, (uint64_t)(r + 1u) * kGamma);
+                live = live_T_fast(((uint64_t)arc.w << 32) | arc.z, (uint64_t)(r + 1u) * kGamma,
+                                   s.smp.aT ? s.smp.aT[a] : uniform_T(s.smp));
             }
             const unsigned cb = __ballot_sync(kFull, live && cen);
             if (cb) {

@@ -47,14 +47,15 @@ template <int B>
 __device__ __forceinline__ void sample_union_pair(const uint4& two, uint64_t i, uint64_t m,
                                                   const Sampler& smp, uint64_t g0, uint32_t nb,
                                                   uint32_t* parent, uint32_t n) {
-    uint64_t x0 = mix64(smp.salt ^ (2 * i)) + g0;
-    uint64_t x1 = mix64(smp.salt ^ (2 * i + 1)) + g0;
+    const uint64_t k0 = mix64(smp.salt ^ (2 * i)), k1 = mix64(smp.salt ^ (2 * i + 1));
     const bool has1 = 2 * i + 1 < m;
+    const uint64_t T0 = smp.eT ? smp.eT[2 * i] : uniform_T(smp);
+    const uint64_t T1 = (smp.eT && has1) ? smp.eT[2 * i + 1] : uniform_T(smp);
+    uint64_t rg = g0;
     for (uint32_t b = 0; b < nb; ++b) {
-        if (smp.all_live || mix64(x0) < smp.T) unite_rem(parent + (size_t)b * n, two.x, two.y);
-        if (has1 && (smp.all_live || mix64(x1) < smp.T)) unite_rem(parent + (size_t)b * n, two.z, two.w);
-        x0 += kGamma;
-        x1 += kGamma;
+        if (live_T(k0, rg, T0)) unite_rem(parent + (size_t)b * n, two.x, two.y);
+        if (has1 && live_T(k1, rg, T1)) unite_rem(parent + (size_t)b * n, two.z, two.w);
+        rg += kGamma;
     }
 }
 
@@ -91,18 +92,26 @@ k_sample_emit(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, uin
             const uint64_t e0 = 2 * i, e1 = 2 * i + 1;
             k0 = mix64(smp.salt ^ e0);
             k1 = mix64(smp.salt ^ e1);
-            if (smp.all_live) {
-                live0 = live1 = (nb >= 32) ? 0xFFFFFFFFu : ((1u << nb) - 1u);
+            uint64_t T0 = uniform_T(smp), T1 = T0;
+            if (smp.eT) {   // per-edge thresholds, stored pairwise like the edges
+                const ulonglong2 tt = __ldcs(reinterpret_cast<const ulonglong2*>(smp.eT) + i);
+                T0 = tt.x;
+                T1 = tt.y;
+            }
+            const uint32_t all = (nb >= 32) ? 0xFFFFFFFFu : ((1u << nb) - 1u);
+            if (T0 == kAllLive && T1 == kAllLive) {
+                live0 = live1 = all;
             } else {
                 // candidates by the high word of the hash (a superset of the live pairs, about
                 // 2^-31 larger); they are settled exactly below
-                const uint32_t th = (uint32_t)(smp.T >> 32);
-                const uint32_t th1 = th == 0xFFFFFFFFu ? th : th + 1u;
+                const uint32_t h0 = (uint32_t)(T0 >> 32), h1 = (uint32_t)(T1 >> 32);
+                const uint32_t th0 = h0 == 0xFFFFFFFFu ? h0 : h0 + 1u;
+                const uint32_t th1 = h1 == 0xFFFFFFFFu ? h1 : h1 + 1u;
                 uint64_t x0 = k0 + g0, x1 = k1 + g0;
                 if (nb == (uint32_t)B) {
 #pragma unroll
                     for (int b = 0; b < B; ++b) {
-                        if (mix64_hi_raw(x0) <= th1) live0 |= 1u << b;
+                        if (mix64_hi_raw(x0) <= th0) live0 |= 1u << b;
                         if (mix64_hi_raw(x1) <= th1) live1 |= 1u << b;
                         x0 += kGamma;
                         x1 += kGamma;
@@ -111,7 +120,7 @@ k_sample_emit(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, uin
 #pragma unroll
                     for (int b = 0; b < B; ++b) {
                         if (b < (int)nb) {
-                            if (mix64_hi_raw(x0) <= th1) live0 |= 1u << b;
+                            if (mix64_hi_raw(x0) <= th0) live0 |= 1u << b;
                             if (mix64_hi_raw(x1) <= th1) live1 |= 1u << b;
                         }
                         x0 += kGamma;
@@ -119,14 +128,18 @@ k_sample_emit(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, uin
                     }
                 }
                 // exact test for the candidates (about a fraction p of all pairs)
-                for (uint32_t t = live0; t; t &= t - 1) {
-                    const int b = __ffs(t) - 1;
-                    if (!edge_live(smp, k0, r0 + b)) live0 &= ~(1u << b);
-                }
-                for (uint32_t t = live1; t; t &= t - 1) {
-                    const int b = __ffs(t) - 1;
-                    if (!edge_live(smp, k1, r0 + b)) live1 &= ~(1u << b);
-                }
+                if (T0 == kAllLive) live0 = all;
+                else
+                    for (uint32_t t = live0; t; t &= t - 1) {
+                        const int b = __ffs(t) - 1;
+                        if (!live_T(k0, (uint64_t)(r0 + b + 1u) * kGamma, T0)) live0 &= ~(1u << b);
+                    }
+                if (T1 == kAllLive) live1 = all;
+                else
+                    for (uint32_t t = live1; t; t &= t - 1) {
+                        const int b = __ffs(t) - 1;
+                        if (!live_T(k1, (uint64_t)(r0 + b + 1u) * kGamma, T1)) live1 &= ~(1u << b);
+                    }
             }
             if (e1 >= m) live1 = 0;
         }
@@ -472,7 +485,7 @@ int launch_sample_split(im_ctx* c, im_ctx::Lane& L, uint32_t r0, uint32_t nb) {
     const uint64_t npairs = (c->m + 1) >> 1;
     const uint4* ep = reinterpret_cast<const uint4*>(c->d_edges);
     const unsigned gs = grid_for(npairs, T, 152u * 16u);
-    const double pl = c->smp.all_live ? 1.0 : c->p;
+    const double pl = c->smp.eT ? c->mean_p : c->smp.all_live ? 1.0 : c->p;
     const unsigned gu = grid_for((uint64_t)(pl * (double)c->m * nb) + 1, T, 152u * 16u);
     IM_LAUNCH(c, K_ZERO, k_zero_u64, 1, 32, 0, L.live_n);
 #define IM_SE(BB)                                                                                 \
@@ -508,7 +521,7 @@ int batch_components(im_ctx* c, im_ctx::Lane& L, uint32_t r0, uint32_t nb, int k
     const unsigned T = 256;
     IM_LAUNCH(c, K_BATCH_INIT, k_batch_init, grid_for((uint64_t)n * nb, T, 152u * 16u), T, 0,
               L.parent, L.word, n, nb, c->d_cidx, key_mode);
-    if ((c->smp.all_live || c->smp.T != 0) && c->m > 0) {
+    if ((c->smp.eT || c->smp.all_live || c->smp.T != 0) && c->m > 0) {
         const int rc = (L.live && nb <= c->batch_used) ? launch_sample_split(c, L, r0, nb)
                                                        : launch_sample_fused(c, L, r0, nb);
         if (rc) return rc;

@@ -110,7 +110,7 @@ extern "C" int im_sketch_static(uint32_t n, uint64_t m, const uint32_t* d_u, con
     uint32_t* C = base + IM_STATIC_MAX_N;
     uint32_t* status = base + 2 * (size_t)IM_STATIC_MAX_N;
     cudaStream_t st = (cudaStream_t)stream;
-    Sampler smp;
+    Sampler smp{};   // one p for every edge: no per-edge thresholds
     smp.salt = mix64(seed + kGamma);
     smp.all_live = p >= 1.0 ? 1u : 0u;
     smp.T = (p > 0.0 && p < 1.0) ? (uint64_t)std::ldexp(p, 64) : 0ull;

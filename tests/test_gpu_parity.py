@@ -392,3 +392,78 @@ def test_load_graph_serves_one_graph_after_another():
         ctx.load_graph(n0, u0, v0)
         ctx.build_sketches(R, seed, p, alpha)
         assert np.array_equal(ctx.select_seeds(k)[0], got[0])
+
+
+# ---- per-edge IC probabilities (Sec. 2's IC model: each edge its own p_e) -------------------
+
+def _edge_probs(model, G, m):
+    if model == "wic":
+        return G.set_wic()
+    lo, hi = (0.0, 0.1) if model == "u01" else (0.1, 0.3)
+    p = np.random.default_rng(17).uniform(lo, hi, m)
+    G.set_probs(p)
+    return p
+
+
+@pytest.mark.parametrize("threshold", [0, 1, 2**64 - 1])
+@pytest.mark.parametrize("alpha", [1.0, 0.1])
+@pytest.mark.parametrize("model", ["u01", "u13", "wic"])
+def test_per_edge_probabilities_match_the_oracle(model, alpha, threshold):
+    """Uniform U(0,0.1), U(0.1,0.3) (the array passed to both sides) and the weighted cascade
+    2/(d_u+d_v) (computed by each side): labels, gains, compact sketches, seeds, gains and
+    spread bit for bit; threshold 1 / 2^64-1 force each batch evaluator, 0 is automatic."""
+    n, u, v = graphgen.chung_lu(20000, 100000, 2.1, 2000.0, 5)
+    G = oracle.Graph(n, u, v)
+    p = _edge_probs(model, G, len(u))
+    R, seed, k = 64, 42, 10
+    L = G.labels(seed, -1.0, R, mode=oracle.MODE_EDGE)
+    ctr = oracle.centers(n, seed, alpha)
+    lab, sz = oracle.compact(L, ctr)
+    o_seeds, o_gains = oracle.greedy(L, k)
+    with im.IMContext(n, u, v) as ctx:
+        if model == "wic":
+            ctx.set_edge_probs(im.IM_PROBS_WIC)
+        else:
+            ctx.set_edge_probs(im.IM_PROBS_ARRAY, p)
+        im.im_set_refresh_threshold(ctx.h, threshold)
+        ctx.build_sketches(R, seed, 0.5, alpha)          # p is ignored under per-edge models
+        for r in (0, 31, 63):
+            assert np.array_equal(ctx.labels(r), L[r]), r
+        assert np.array_equal(ctx.gains(), oracle.gains(L))
+        g_lab, g_sz = ctx.compact()
+        assert np.array_equal(g_lab, lab) and np.array_equal(g_sz, sz)
+        seeds, gains = ctx.select_seeds(k)
+        assert np.array_equal(seeds, o_seeds) and np.array_equal(gains, o_gains)
+        assert ctx.spread(seeds) == oracle.spread(L, seeds) == int(o_gains.sum())
+
+
+def test_per_edge_probability_api():
+    n, u, v = graphgen.erdos_renyi(2000, 8000, 21)
+    R, seed, p0 = 32, 9, 0.15
+    with im.IMContext(n, u, v) as ctx:
+        ctx.build_sketches(R, seed, p0, 0.2)
+        want = (ctx.gains(),) + ctx.compact() + ctx.select_seeds(6)
+        # the same probability on every edge, from the host and from the device, is the uniform model
+        for arr in (np.full(len(u), p0), torch.full((len(u),), p0, dtype=torch.float64, device="cuda")):
+            ctx.set_edge_probs(im.IM_PROBS_ARRAY, arr)
+            with pytest.raises(im.IMError) as e:
+                ctx.select_seeds(1)
+            assert e.value.code == im.IM_ESTATE
+            ctx.build_sketches(R, seed, 0.9, 0.2)
+            got = (ctx.gains(),) + ctx.compact() + ctx.select_seeds(6)
+            for a, b in zip(got, want):
+                assert np.array_equal(a, b)
+        # back to one p; a new graph also returns to it
+        ctx.set_edge_probs(im.IM_PROBS_UNIFORM)
+        ctx.build_sketches(R, seed, p0, 0.2)
+        assert np.array_equal(ctx.select_seeds(6)[0], want[3])
+        ctx.set_edge_probs(im.IM_PROBS_WIC)
+        ctx.load_graph(n, u, v)
+        ctx.build_sketches(R, seed, p0, 0.2)
+        assert np.array_equal(ctx.select_seeds(6)[0], want[3])
+        with pytest.raises(im.IMError) as e:
+            im.im_set_edge_probs(ctx.h, 7)
+        assert e.value.code == im.IM_EINVAL
+        with pytest.raises(im.IMError) as e:
+            im.im_set_edge_probs(ctx.h, im.IM_PROBS_ARRAY, None)
+        assert e.value.code == im.IM_EINVAL
