@@ -179,6 +179,15 @@ def kernel_rooflines(prof, live_build, n, m, R, steps, peaks, peak_src, clk, has
 
 
 # ----------------------------------------------------------------------- CPU baseline
+def edge_probs(prm, m):
+    """Per-edge probabilities of the workload, or None for one p: U(0, 0.1) / U(0.1, 0.3)
+    drawn from a seeded generator (passed to the engine as an array), "wic" computed by it."""
+    if prm["probs"] in ("u01", "u13"):
+        lo, hi = (0.0, 0.1) if prm["probs"] == "u01" else (0.1, 0.3)
+        return np.random.default_rng(prm["seed"] + 17).uniform(lo, hi, m)
+    return None
+
+
 def cpu_sample(n, u, v, prm, sketches=CPU_SAMPLE_SKETCHES):
     """The oracle on a bounded sample: the first `sketches` sketches of the workload, all
     steps of the path (labels, gains, compact sketches, greedy, spread)."""
@@ -186,7 +195,14 @@ def cpu_sample(n, u, v, prm, sketches=CPU_SAMPLE_SKETCHES):
     threads = oracle.max_threads()
     t0 = time.perf_counter()
     G = oracle.Graph(n, u, v)
-    L = G.labels(prm["seed"], prm["p"], sketches, threads=threads)
+    mode = oracle.MODE_HASH
+    if prm["probs"] == "wic":
+        G.set_wic()
+        mode = oracle.MODE_EDGE
+    elif prm["probs"] != "uniform":
+        G.set_probs(edge_probs(prm, len(u)))
+        mode = oracle.MODE_EDGE
+    L = G.labels(prm["seed"], prm["p"], sketches, mode=mode, threads=threads)
     oracle.gains(L)
     ctr = oracle.centers(n, prm["seed"], prm["alpha"])
     oracle.compact(L, ctr)
@@ -218,7 +234,7 @@ def run_reference(args, n, u, v, prm):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic",
-        "config": {"workload": prm["name"], "n": n, "m": len(u), "p": prm["p"], "R": prm["R"],
+        "config": {"workload": prm["name"], "n": n, "m": len(u), "p": prm["p"], "probs": prm["probs"], "R": prm["R"],
                    "alpha": prm["alpha"], "k": prm["k"], "sample_sketches": CPU_SAMPLE_SKETCHES},
         "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": res["cores"], "kind": "oracle",
                          "sample": res["sample"]},
@@ -245,6 +261,15 @@ def run_ours(args, n, u, v, prm):
     du = torch.from_numpy(u.view(np.int32)).cuda()
     dv = torch.from_numpy(v.view(np.int32)).cuda()
     ctx = im.IMContext(n, du, dv, stream=stream.cuda_stream)
+    pe = edge_probs(prm, m)
+
+    def set_probs(c):
+        if prm["probs"] == "wic":
+            c.set_edge_probs(im.IM_PROBS_WIC)
+        elif pe is not None:
+            c.set_edge_probs(im.IM_PROBS_ARRAY, pe)
+
+    set_probs(ctx)
     if args.sketch_batch:
         im.im_set_sketch_batch(ctx.h, args.sketch_batch)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
@@ -311,6 +336,7 @@ def run_ours(args, n, u, v, prm):
 
     def e2e_step():
         c2.load_graph(n, pu, pv)
+        set_probs(c2)
         c2.build_sketches(R, prm["seed"], prm["p"], prm["alpha"])
         s2, g2 = c2.select_seeds(k)
         return c2.spread(s2)
@@ -349,7 +375,7 @@ def run_ours(args, n, u, v, prm):
             "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u64", "data": "synthetic",
-            "config": {"workload": prm["name"], "n": n, "m": m, "p": prm["p"], "R": R,
+            "config": {"workload": prm["name"], "n": n, "m": m, "p": prm["p"], "probs": prm["probs"], "R": R,
                        "alpha": prm["alpha"], "k": k, "l2": "flushed before every step",
                        "parallelism": f"replicas{ws}"},
             "time_to_k_ms": ms_build + ms_select,
@@ -362,7 +388,8 @@ def run_ours(args, n, u, v, prm):
             "kernel_rooflines": list(roofs.values()),
             "cpu_baseline": cpu,
             "e2e": {"value": pairs * ws / e2e_s, "unit": "pairs/s",
-                    "h2d_bytes_per_step": 8 * m, "d2h_bytes_per_step": 12 * k + 8},
+                    "h2d_bytes_per_step": 8 * m + (8 * m if pe is not None else 0),
+                    "d2h_bytes_per_step": 12 * k + 8},
             "gpu_launches": launches,
             "clocks": clk,
             "kernels_ms_per_step": {kname: round(t / args.steps, 4) for kname, (t, _) in
@@ -385,9 +412,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(graphgen.WORKLOADS))
     ap.add_argument("--sketch-batch", type=int, default=0, help="sketches per edge pass (0 = auto)")
+    ap.add_argument("--probs", default="uniform", choices=["uniform", "u01", "u13", "wic"],
+                    help="IC probabilities: the workload's p, or per edge U(0,0.1), U(0.1,0.3), 2/(d_u+d_v)")
     args = ap.parse_args()
     n, u, v, prm = graphgen.workload(args.workload)
     prm["name"] = args.workload
+    prm["probs"] = args.probs
     if args.impl == "reference":
         return run_reference(args, n, u, v, prm)
     return run_ours(args, n, u, v, prm)

@@ -292,8 +292,8 @@ int im_set_edge_probs(im_ctx* c, int model, const double* p, int ptr_kind) {
     c->seeds.clear();
     c->seed_gains.clear();
     c->round_evals.clear();
-    im_select_graph_free(c);
-    c->prob_model = IM_PROBS_UNIFORM;
+    c->prob_model = IM_PROBS_UNIFORM;   // (the next build re-captures the selection graph if the
+                                        // sampler it carries changed)
     if (model == IM_PROBS_UNIFORM) return IM_OK;
     const double* dp = p;
     double* tmp = nullptr;
