@@ -24,6 +24,8 @@ constexpr uint64_t kSingleTasks = 152ull * 64;
 constexpr int kBfsChunks = 4;
 // per-warp visited set of a search (open addressing, >= 2 x the queue capacity + one chunk)
 constexpr uint32_t kHashSlots = 512;
+// warps of a block that searches one (vertex, sketch) together (the first hop)
+constexpr int kBlockWarps = 8;
 
 // Insert y into a warp's visited set; true if it was not there.  The set never holds more
 // than kQcap + 32 ids, so a free slot is always found.
@@ -200,6 +202,104 @@ __device__ BfsOut warp_bfs_from(const GraphView& g, const SketchView& s, uint32_
     for (int d = 16; d; d >>= 1) minv = min(minv, __shfl_xor_sync(kFull, minv, d));
     o.minv = minv;
     o.count = tail;
+    return o;
+}
+
+// ---- GetCenter by a whole block: the first hop shared by its warps -------------------------
+// A hub's first hop (its own adjacency list) dominates its search when few of its arcs are
+// live (small p_e on hub edges, e.g. the weighted cascade).  The block's warps scan x's arcs
+// together, 4 chunks of 32 per warp in flight, and stop as soon as one meets a live center
+// (every center of a component carries its label); otherwise the distinct live non-center
+// neighbours they collected seed warp 0's warp_bfs_from, which finishes the search.
+constexpr uint32_t kBlockSlots = 1024;   // the block's set of x's neighbours
+
+struct BlockSearchSmem {
+    uint32_t qw[kQcap + kHashSlots];   // warp 0's queue and visited set
+    uint32_t list[kQcap];              // x's live non-center neighbours
+    uint32_t set[kBlockSlots];         // ... deduplicated
+    uint32_t label, count, overflow, seen;
+};
+
+// Insert y into the block's set with at most kBlockSlots probes: 1 new, 0 already there,
+// -1 full (the warps may insert beyond the list's capacity before they see the overflow).
+__device__ __forceinline__ int visit_bounded(uint32_t* set, uint32_t y) {
+    uint32_t h = (y * 0x9E3779B1u) >> (32 - 10);
+    for (uint32_t i = 0; i < kBlockSlots; ++i) {
+        const uint32_t old = atomicCAS(set + h, kNone, y);
+        if (old == kNone) return 1;
+        if (old == y) return 0;
+        h = (h + 1) & (kBlockSlots - 1);
+    }
+    return -1;
+}
+
+// Call with the whole block (it synchronises); the result is valid in warp 0.
+__device__ BfsOut block_search(const GraphView& g, const SketchView& s, uint32_t x, uint32_t r, bool want_seed,
+                               BlockSearchSmem& sm, SelState* st_counters) {
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (uint32_t i = threadIdx.x; i < kBlockSlots; i += blockDim.x) sm.set[i] = kNone;
+    if (threadIdx.x == 0) {
+        sm.label = kNone;
+        sm.count = 0;
+        sm.overflow = 0;
+        sm.seen = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) visit_bounded(sm.set, x);
+    __syncthreads();
+    const uint64_t a0 = g.off[x], a1 = g.off[x + 1];
+    const uint64_t rg = (uint64_t)(r + 1u) * kGamma;
+    const uint64_t Tw = uniform_T(s.smp);
+    for (uint64_t base = a0 + (uint64_t)warp * 128; base < a1; base += (uint64_t)nwarps * 128) {
+        // stop once a live center was met or the neighbour list overflowed (warp-uniform)
+        const uint32_t stop = __shfl_sync(kFull, (*(volatile uint32_t*)&sm.label != kNone) |
+                                                     *(volatile uint32_t*)&sm.overflow, 0);
+        if (stop) break;
+        uint4 arcs4[4];
+        uint64_t tk[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint64_t a = base + 32u * k + lane;
+            arcs4[k] = a < a1 ? g.arcs[a] : make_uint4(0, 0, 0, 0);
+            tk[k] = (a < a1 && s.smp.aT) ? s.smp.aT[a] : Tw;
+        }
+        bool found = false;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint64_t a = base + 32u * k + lane;
+            bool live = false;
+            if (a < a1) live = live_T_fast(((uint64_t)arcs4[k].w << 32) | arcs4[k].z, rg, tk[k]);
+            const bool cen = arcs4[k].x >> 31;
+            const unsigned cb = __ballot_sync(kFull, live && cen);
+            if (cb) {
+                if ((int)lane == __ffs(cb) - 1) atomicCAS(&sm.label, kNone, s.label[(size_t)arcs4[k].y * s.R + r]);
+                found = true;
+                break;
+            }
+            if (live) {
+                const uint32_t y = arcs4[k].x & kArcIdMask;
+                const int fresh = visit_bounded(sm.set, y);
+                if (fresh < 0) {
+                    sm.overflow = 1;
+                } else if (fresh) {
+                    const uint32_t pos = atomicAdd(&sm.count, 1u);
+                    if (pos < kQcap - 1) sm.list[pos] = y;
+                    else sm.overflow = 1;
+                    if (want_seed && is_seed(s, y)) sm.seen = 1;
+                }
+            }
+        }
+        if (found) break;
+    }
+    __syncthreads();
+    BfsOut o;
+    o.label = sm.label; o.count = 0; o.minv = x; o.seen = 0; o.overflow = 0;
+    if (o.label != kNone) return o;
+    if (sm.overflow) {
+        o.overflow = 1;
+        return o;
+    }
+    if (warp == 0) o = warp_bfs_from(g, s, x, r, sm.qw, want_seed, sm.list, sm.count, 1, st_counters);
     return o;
 }
 
@@ -747,18 +847,15 @@ k_eval(GraphView g, SketchView s, SelState* st, const uint32_t* __restrict__ bat
     }
 }
 
-// Marginal for small batches: one warp per (member j, sketch r), so a round that
-// re-evaluates a handful of vertices finishes in the latency of one search.
-__global__ void __launch_bounds__(kEvalWarps * 32)
+// Marginal for small batches: one block per (member j, sketch r), so that a round that
+// re-evaluates a handful of vertices finishes in the latency of one search, the block's warps
+// sharing the member's first hop (block_search).
+__global__ void __launch_bounds__(kBlockWarps * 32)
 k_eval_single(GraphView g, SketchView s, SelState* st, const uint32_t* __restrict__ batch,
               unsigned long long* __restrict__ fresh, FbTask* __restrict__ fbt, uint32_t fb_cap) {
-    __shared__ uint32_t qws[kEvalWarps][kQcap + kHashSlots];
-    uint32_t* qw = qws[threadIdx.x >> 5];
-    const unsigned lane = threadIdx.x & 31;
+    __shared__ BlockSearchSmem sm;
     const unsigned long long total = (unsigned long long)st->batch_n * s.R;
-    const unsigned long long wstride = (unsigned long long)gridDim.x * kEvalWarps;
-    for (unsigned long long t = (unsigned long long)blockIdx.x * kEvalWarps + (threadIdx.x >> 5); t < total;
-         t += wstride) {
+    for (unsigned long long t = blockIdx.x; t < total; t += gridDim.x) {   // uniform over the block
         const uint32_t j = (uint32_t)(t / s.R), r = (uint32_t)(t % s.R);
         const uint32_t x = batch[j];
         unsigned long long d = 0;
@@ -767,53 +864,52 @@ k_eval_single(GraphView g, SketchView s, SelState* st, const uint32_t* __restric
             const uint32_t sz = s.size[(size_t)l * s.R + r];
             d = (sz & kCovered) ? 0u : sz;
         } else {
-            const BfsOut o = warp_bfs_from(g, s, x, r, qw, true, nullptr, 0, 0, st);
-            if (!o.overflow && lane == 0)
-                s.labcache[(size_t)(x & (kLabSlots - 1)) * s.R + r] = ((uint64_t)x << 32) | o.label;
-            if (o.overflow) {
-                if (lane == 0) push_fallback(st, fbt, fb_cap, x, r, FB_EVAL, j);
-            } else if (o.label != kNone) {
-                const uint32_t sz = s.size[(size_t)o.label * s.R + r];
-                d = (sz & kCovered) ? 0u : sz;
-            } else {
-                d = o.seen ? 0u : o.count;
+            const BfsOut o = block_search(g, s, x, r, true, sm, st);
+            if (threadIdx.x == 0) {
+                if (!o.overflow)
+                    s.labcache[(size_t)(x & (kLabSlots - 1)) * s.R + r] = ((uint64_t)x << 32) | o.label;
+                if (o.overflow) {
+                    push_fallback(st, fbt, fb_cap, x, r, FB_EVAL, j);
+                } else if (o.label != kNone) {
+                    const uint32_t sz = s.size[(size_t)o.label * s.R + r];
+                    d = (sz & kCovered) ? 0u : sz;
+                } else {
+                    d = o.seen ? 0u : o.count;
+                }
             }
         }
-        if (lane == 0 && d) atomicAdd(fresh + j, d);
-        __syncwarp();
+        if (threadIdx.x == 0 && d) atomicAdd(fresh + j, d);
+        __syncthreads();
     }
 }
 
 // MarkSeed (Alg. 3): in every sketch, flag the component of the last round's winner as
-// covered.  One warp per sketch: a single vertex is marked per round, so latency, not total
-// work, decides.
-__global__ void __launch_bounds__(kEvalWarps * 32)
+// covered.  One block per sketch (a single vertex is marked per round, so latency, not
+// total work, decides); labels the winner's evaluation already found are reused.
+__device__ __forceinline__ uint32_t mark_label(const GraphView& g, const SketchView& s, uint32_t sd, uint32_t r,
+                                               BlockSearchSmem& sm, SelState* st, bool* overflow) {
+    *overflow = false;
+    if (is_center(s, sd)) return s.label[(size_t)center_index(s, sd) * s.R + r];
+    // a label found when sd was evaluated is still valid: labels depend on the sketch only
+    const uint64_t e = s.labcache[(size_t)(sd & (kLabSlots - 1)) * s.R + r];
+    if ((uint32_t)(e >> 32) == sd) return (uint32_t)e;
+    const BfsOut o = block_search(g, s, sd, r, false, sm, st);   // block-uniform branch
+    *overflow = o.overflow;
+    return o.label;
+}
+
+__global__ void __launch_bounds__(kBlockWarps * 32)
 k_mark_seed(GraphView g, SketchView s, SelState* st, FbTask* __restrict__ fbt, uint32_t fb_cap,
             uint8_t* __restrict__ seedflag, uint64_t* __restrict__ key) {
-    __shared__ uint32_t qws[kEvalWarps][kQcap + kHashSlots];
+    __shared__ BlockSearchSmem sm;
     const uint32_t sd = st->sd;
-    uint32_t* qw = qws[threadIdx.x >> 5];
-    const unsigned lane = threadIdx.x & 31;
-    const uint32_t r = blockIdx.x * kEvalWarps + (threadIdx.x >> 5);
+    const uint32_t r = blockIdx.x;
     if (r < s.R) {
-        if (is_center(s, sd)) {
-            if (lane == 0) {
-                const uint32_t l = s.label[(size_t)center_index(s, sd) * s.R + r];
-                atomicOr(s.size + (size_t)l * s.R + r, kCovered);
-            }
-        } else {
-            // a label found when sd was evaluated is still valid: labels depend on the sketch only
-            const uint64_t e = s.labcache[(size_t)(sd & (kLabSlots - 1)) * s.R + r];
-            if ((uint32_t)(e >> 32) == sd) {
-                const uint32_t l = (uint32_t)e;
-                if (lane == 0 && l != kNone) atomicOr(s.size + (size_t)l * s.R + r, kCovered);
-            } else {
-                const BfsOut o = warp_bfs_from(g, s, sd, r, qw, false, nullptr, 0, 0, st);
-                if (lane == 0) {
-                    if (o.overflow) push_fallback(st, fbt, fb_cap, sd, r, FB_MARK, 0);
-                    else if (o.label != kNone) atomicOr(s.size + (size_t)o.label * s.R + r, kCovered);
-                }
-            }
+        bool over = false;
+        const uint32_t l = mark_label(g, s, sd, r, sm, st, &over);
+        if (threadIdx.x == 0) {
+            if (over) push_fallback(st, fbt, fb_cap, sd, r, FB_MARK, 0);
+            else if (l != kNone) atomicOr(s.size + (size_t)l * s.R + r, kCovered);
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -823,59 +919,50 @@ k_mark_seed(GraphView g, SketchView s, SelState* st, FbTask* __restrict__ fbt, u
 }
 
 // MarkSeed of the last round's winner x fused with the Marginal of this round's only
-// candidate y (batch slot 0), one warp per sketch: the warp marks x's component first, so
+// candidate y (batch slot 0), one block per sketch: the block marks x's component first, so
 // that y's search finds it covered; a component without a center that holds x counts as
 // holding a seed through s.pend (x's flag is set concurrently).  If x's search overflows,
 // the fallback kernel does both for that sketch (FB_MARK_EVAL), in the same order.
-__global__ void __launch_bounds__(kEvalWarps * 32)
+__global__ void __launch_bounds__(kBlockWarps * 32)
 k_mark_eval(GraphView g, SketchView s, SelState* st, const uint32_t* __restrict__ batch,
             unsigned long long* __restrict__ fresh, FbTask* __restrict__ fbt, uint32_t fb_cap,
             uint8_t* __restrict__ seedflag, uint64_t* __restrict__ key) {
-    __shared__ uint32_t qws[kEvalWarps][kQcap + kHashSlots];
+    __shared__ BlockSearchSmem sm;
+    __shared__ int s_marked;
     const uint32_t x = st->sd, y = batch[0];
     s.pend = x;
-    uint32_t* qw = qws[threadIdx.x >> 5];
-    const unsigned lane = threadIdx.x & 31;
-    const uint32_t r = blockIdx.x * kEvalWarps + (threadIdx.x >> 5);
+    const uint32_t r = blockIdx.x;
     if (r < s.R) {
-        uint32_t lx = kNone;
-        bool marked = true;
-        if (is_center(s, x)) {
-            lx = s.label[(size_t)center_index(s, x) * s.R + r];
-        } else {
-            const uint64_t e = s.labcache[(size_t)(x & (kLabSlots - 1)) * s.R + r];
-            if ((uint32_t)(e >> 32) == x) {
-                lx = (uint32_t)e;
-            } else {
-                const BfsOut o = warp_bfs_from(g, s, x, r, qw, false, nullptr, 0, 0, st);
-                if (o.overflow) marked = false;
-                else lx = o.label;
-            }
+        bool over = false;
+        const uint32_t lx = mark_label(g, s, x, r, sm, st, &over);
+        if (threadIdx.x == 0) {
+            s_marked = !over;
+            if (over) push_fallback(st, fbt, fb_cap, x, r, FB_MARK_EVAL, y);
+            else if (lx != kNone) atomicOr(s.size + (size_t)lx * s.R + r, kCovered);
         }
-        if (!marked) {
-            if (lane == 0) push_fallback(st, fbt, fb_cap, x, r, FB_MARK_EVAL, y);
-        } else {
-            if (lane == 0 && lx != kNone) atomicOr(s.size + (size_t)lx * s.R + r, kCovered);
-            __syncwarp();
+        __syncthreads();
+        if (s_marked) {   // block-uniform
             unsigned long long d = 0;
             if (is_center(s, y)) {
                 const uint32_t l = s.label[(size_t)center_index(s, y) * s.R + r];
                 const uint32_t sz = __ldcg(s.size + (size_t)l * s.R + r);
                 d = (sz & kCovered) ? 0u : sz;
             } else {
-                const BfsOut o = warp_bfs_from(g, s, y, r, qw, true, nullptr, 0, 0, st);
-                if (!o.overflow && lane == 0)
-                    s.labcache[(size_t)(y & (kLabSlots - 1)) * s.R + r] = ((uint64_t)y << 32) | o.label;
-                if (o.overflow) {
-                    if (lane == 0) push_fallback(st, fbt, fb_cap, y, r, FB_EVAL, 0);
-                } else if (o.label != kNone) {
-                    const uint32_t sz = __ldcg(s.size + (size_t)o.label * s.R + r);
-                    d = (sz & kCovered) ? 0u : sz;
-                } else {
-                    d = o.seen ? 0u : o.count;
+                const BfsOut o = block_search(g, s, y, r, true, sm, st);
+                if (threadIdx.x == 0) {
+                    if (!o.overflow)
+                        s.labcache[(size_t)(y & (kLabSlots - 1)) * s.R + r] = ((uint64_t)y << 32) | o.label;
+                    if (o.overflow) {
+                        push_fallback(st, fbt, fb_cap, y, r, FB_EVAL, 0);
+                    } else if (o.label != kNone) {
+                        const uint32_t sz = __ldcg(s.size + (size_t)o.label * s.R + r);
+                        d = (sz & kCovered) ? 0u : sz;
+                    } else {
+                        d = o.seen ? 0u : o.count;
+                    }
                 }
             }
-            if (lane == 0 && d) atomicAdd(fresh, d);
+            if (threadIdx.x == 0 && d) atomicAdd(fresh, d);
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1191,11 +1278,11 @@ int enqueue_mode(im_ctx* c, unsigned mode, int passes, const SelHandles& hd) {
     if (mode == M_ROUND_START) return launch_reduce_plan(c, hd);
     if (mode == M_MARK || mode == M_MARK_DIRECT) {
         if (mode == M_MARK)
-            IM_LAUNCH(c, K_MARK_SEED, k_mark_seed, (c->R + kEvalWarps - 1) / kEvalWarps, kEvalWarps * 32, 0, g, s,
-                      st, c->d_fb_tasks, c->fb_cap, c->d_seedflag, c->d_key);
+            IM_LAUNCH(c, K_MARK_SEED, k_mark_seed, c->R, kBlockWarps * 32, 0, g, s, st, c->d_fb_tasks, c->fb_cap,
+                      c->d_seedflag, c->d_key);
         else
-            IM_LAUNCH(c, K_MARK_SEED, k_mark_eval, (c->R + kEvalWarps - 1) / kEvalWarps, kEvalWarps * 32, 0, g, s,
-                      st, c->d_batch, fresh, c->d_fb_tasks, c->fb_cap, c->d_seedflag, c->d_key);
+            IM_LAUNCH(c, K_MARK_SEED, k_mark_eval, c->R, kBlockWarps * 32, 0, g, s, st, c->d_batch, fresh,
+                      c->d_fb_tasks, c->fb_cap, c->d_seedflag, c->d_key);
         launch_fallback(c, g, s);
         return launch_reduce_plan(c, hd);
     }
@@ -1213,14 +1300,14 @@ int enqueue_mode(im_ctx* c, unsigned mode, int passes, const SelHandles& hd) {
                   fresh);
     switch (mode) {
     case M_DIRECT:
-        IM_LAUNCH(c, K_EVAL, k_eval_single, search_grid(c->R), kEvalWarps * 32, 0, g, s, st, c->d_batch, fresh,
-                  c->d_fb_tasks, c->fb_cap);
+        IM_LAUNCH(c, K_EVAL, k_eval_single, c->R, kBlockWarps * 32, 0, g, s, st, c->d_batch, fresh, c->d_fb_tasks,
+                  c->fb_cap);
         launch_fallback(c, g, s);
         break;
     case M_GATHER_SINGLE:
     case M_HIST_SINGLE:
-        IM_LAUNCH(c, K_EVAL, k_eval_single, search_grid(kSingleTasks), kEvalWarps * 32, 0, g, s, st, c->d_batch,
-                  fresh, c->d_fb_tasks, c->fb_cap);
+        IM_LAUNCH(c, K_EVAL, k_eval_single, grid_for(kSingleTasks, 1, 152u * 8u), kBlockWarps * 32, 0, g, s, st,
+                  c->d_batch, fresh, c->d_fb_tasks, c->fb_cap);
         launch_fallback(c, g, s);
         break;
     case M_GATHER_CHUNK:
