@@ -384,6 +384,7 @@ def run_ours(args, n, u, v, prm):
             "evaluations": int(st["evaluations"]),
             "refresh_batches": int(st["refresh_batches"]),
             "spec_batches": int(st["spec_batches"]),
+            "hubs": int(st["hubs"]),
             "roofline": roof,
             "kernel_rooflines": list(roofs.values()),
             "cpu_baseline": cpu,

@@ -173,6 +173,7 @@ typedef struct {
     uint64_t build_live_pairs;      /* of those, unioned by the last im_build_sketches      */
     uint64_t spec_batches;          /* batches evaluated from a candidate first seed's
                                        overlaps (see im_set_seed_speculation)             */
+    uint64_t hubs;                  /* hubs of the last build (see im_set_hubs)            */
 } im_stats;
 
 int im_get_stats(im_ctx* ctx, im_stats* out);
@@ -255,6 +256,17 @@ int im_set_graph(im_ctx* ctx, int on);
  * per candidate; needs the single-lane pipeline; takes effect at the next im_build_sketches.
  * Seeds, gains and evaluation counts do not depend on it. */
 int im_set_seed_speculation(im_ctx* ctx, uint32_t candidates);
+
+/* Tuning: hubs.  GetCenter (Alg. 3) from a vertex whose component reaches a high-degree
+ * non-center tests that vertex's whole adjacency list, in every sketch where it is reached.
+ * With hubs, up to `cap` non-centers of degree >= `min_degree` (the largest degrees, ties to
+ * the smaller id) also get a label and a size per sketch, kept after the compact sketch's
+ * rho rows, so that a search stops at them as at a center.  Seeds, gains, spread and the
+ * compact sketch (im_get_compact) do not depend on it.  cap = IM_HUBS_AUTO (default):
+ * max(1024, n / 64); 0 disables; at most n - rho are used.  min_degree 0 is taken as 1
+ * (default 32).  Costs 8 R bytes per hub; takes effect at the next im_build_sketches. */
+#define IM_HUBS_AUTO 0xFFFFFFFFu
+int im_set_hubs(im_ctx* ctx, uint32_t cap, uint32_t min_degree);
 
 /* Measurement: the rate of the sampling kernel's per-pair compute (64-bit add, high word of
  * the hash, compare, live-mask update) on register values only -- the ceiling of the

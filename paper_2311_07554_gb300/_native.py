@@ -34,7 +34,8 @@ class im_stats(ctypes.Structure):
                 ("sketch_batch", ctypes.c_uint32), ("hop1_arcs", ctypes.c_uint64),
                 ("hop2_searches", ctypes.c_uint64), ("hop2_chunks", ctypes.c_uint64),
                 ("refresh_batches", ctypes.c_uint64), ("live_pairs", ctypes.c_uint64),
-                ("build_live_pairs", ctypes.c_uint64), ("spec_batches", ctypes.c_uint64)]
+                ("build_live_pairs", ctypes.c_uint64), ("spec_batches", ctypes.c_uint64),
+                ("hubs", ctypes.c_uint64)]
 
 
 def lib():
@@ -73,6 +74,7 @@ def lib():
         "im_set_graph": ([vp, i32], i32),
         "im_hash_peak": ([u32, c.POINTER(dbl)], i32),
         "im_set_seed_speculation": ([vp, u32], i32),
+        "im_set_hubs": ([vp, u32, u32], i32),
         "im_stream": ([vp], vp),
         "im_sketch_static": ([u32, u64, vp, vp, u64, dbl, u32, vp, vp, vp], i32),
         "im_last_error": ([vp], c.c_char_p),
@@ -255,6 +257,13 @@ def im_set_graph(ctx, on: bool):
 
 def im_set_seed_speculation(ctx, candidates: int):
     _check(ctx, lib().im_set_seed_speculation(ctx, candidates))
+
+
+IM_HUBS_AUTO = 0xFFFFFFFF
+
+
+def im_set_hubs(ctx, cap: int = IM_HUBS_AUTO, min_degree: int = 32):
+    _check(ctx, lib().im_set_hubs(ctx, cap, min_degree))
 
 
 def im_hash_peak(iters: int = 4096) -> float:

@@ -198,7 +198,7 @@ int im_create(im_ctx** out, uint32_t n, uint64_t m, const uint32_t* u, const uin
     do {
         if (cudaMalloc(&c->d_sel, sizeof(SelState)) != cudaSuccess ||
             cudaMallocHost(&c->h_sel, sizeof(SelState)) != cudaSuccess ||
-            cudaMallocHost(&c->h_live, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+            cudaMallocHost(&c->h_live, 3 * sizeof(unsigned long long)) != cudaSuccess) {
             rc = im_fail(c, IM_ENOMEM, "selection state");
             break;
         }
@@ -236,6 +236,13 @@ int im_set_seed_speculation(im_ctx* c, uint32_t candidates) {
     if (!c) return IM_EINVAL;
     if (candidates > kSpecMax) return im_fail(c, IM_EINVAL, "at most 8 candidate first seeds");
     c->spec_req = candidates;
+    return IM_OK;
+}
+
+int im_set_hubs(im_ctx* c, uint32_t cap, uint32_t min_degree) {
+    if (!c) return IM_EINVAL;
+    c->hub_cap = cap;
+    c->hub_min_deg = min_degree ? min_degree : 1u;
     return IM_OK;
 }
 
@@ -359,7 +366,13 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
         if (cap > (double)(1ull << 28)) cap = (double)(1ull << 28);
         live_cap = (uint64_t)cap;
     }
-    const size_t nc = (size_t)rho * R;
+    // hubs (im_select_hubs): label / size rows after the rho compact rows
+    uint32_t hub_rows = 0;
+    if (!all) {
+        const uint32_t cap = c->hub_cap == imk::kHubsAuto ? std::max<uint32_t>(1024, n / 64) : c->hub_cap;
+        hub_rows = std::min<uint32_t>(cap, n - rho);
+    }
+    const size_t nc = ((size_t)rho + hub_rows) * R;
     // candidate first seeds need the batches in order (they are chosen after the first one)
     const uint32_t nspec = c->lanes == 1 ? std::min<uint32_t>(c->spec_req, n) : 0u;
     // A build with the same shapes reuses the device buffers (no cudaFree / cudaMalloc, which
@@ -374,6 +387,7 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
     }
     c->built = false;
     c->R = R; c->seed = seed; c->p = p; c->alpha = alpha; c->rho = rho; c->all_centers = all;
+    c->hub_rows = hub_rows;
     c->key_bits = (uint32_t)bits;
     c->smp = smp;
     c->batch_used = B;
@@ -416,8 +430,10 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
     // live pairs before the build, read with the build's final synchronisation
     IM_CUDA(c, cudaMemcpyAsync(c->h_live, c->d_live_total, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                                c->stream));
+    c->h_live[2] = 0;
     if (!all) {
         rc = im_select_centers(c, c->d_cflags, c->d_cpos);
+        if (!rc) rc = im_select_hubs(c, c->d_cflags, c->d_cpos);
         if (rc) { free_sketch_state(c); return rc; }
     }
     if (!rc && nspec && !c->d_spec_keys) {
@@ -434,6 +450,7 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
         if (e != cudaSuccess) rc = im_cuda_check(c, e, "sketch construction");
     }
     c->build_live_pairs = c->h_live[1] - c->h_live[0];
+    c->hubs = (uint32_t)c->h_live[2];
     if (rc) { free_sketch_state(c); return rc; }
     c->built = true;
     return IM_OK;
@@ -581,6 +598,7 @@ int im_get_stats(im_ctx* c, im_stats* out) {
         out->refresh_batches = c->h_sel->refresh_batches;
         out->batches = c->h_sel->batches;
         out->spec_batches = c->h_sel->spec_batches;
+        out->hubs = c->hubs;
         unsigned long long lt = 0;
         cudaMemcpy(&lt, c->d_live_total, sizeof lt, cudaMemcpyDeviceToHost);
         out->live_pairs = lt;

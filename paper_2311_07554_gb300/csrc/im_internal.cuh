@@ -21,6 +21,7 @@ constexpr uint32_t kSpreadKMax = 16384;
 constexpr uint32_t kArcIdMask = 0x7FFFFFFFu;            // arc word 0: neighbour id | center bit
 constexpr uint32_t kLabSlots = 256;                     // label cache: vertex slots (x mod 256)
 constexpr size_t kCenterSelBytes = 4096;                // device state of the center radix select
+constexpr uint32_t kHubsAuto = 0xFFFFFFFFu;                // im_ctx::hub_cap default
 constexpr uint32_t kSpecMax = 8;                        // candidate first seeds (see im_ctx::spec_req)
 
 // splitmix64 output finaliser (Steele, Lea, Flood 2014).
@@ -113,8 +114,8 @@ struct SketchView {
     uint32_t R, rho, all_centers;
     const uint32_t* cbits;   // center bitmap, ceil(n/32) words (unused when all_centers)
     const uint32_t* cidx;    // center index per vertex, kNone otherwise (unused when all)
-    const uint32_t* label;   // [rho][R]
-    uint32_t* size;          // [rho][R], bit 31 = covered by a seed
+    const uint32_t* label;   // [rho + hubs][R]
+    uint32_t* size;          // [rho + hubs][R], bit 31 = covered by a seed
     const uint8_t* seed_flag;
     uint32_t pend;           // a seed whose flag is being set concurrently (kNone: none)
     uint64_t* labcache;      // [kLabSlots][R] labels found by searches, reused by MarkSeed
@@ -260,13 +261,18 @@ struct im_ctx {
     uint64_t seed = 0;
     double p = 0.0, alpha = 1.0;
     imk::Sampler smp{};
-    uint32_t* d_cbits = nullptr;
-    uint32_t* d_cidx = nullptr;
+    uint32_t* d_cbits = nullptr;     // centers and hubs
+    uint32_t* d_cidx = nullptr;      // center index (< rho), hub index (rho + i), or kNone
     uint32_t* d_centers = nullptr;
-    uint32_t* d_label = nullptr;
-    uint32_t* d_size = nullptr;
+    uint32_t* d_label = nullptr;     // [rho + hub_rows][R]
+    uint32_t* d_size = nullptr;      // [rho + hub_rows][R]
     uint64_t* d_gain0 = nullptr;
     size_t compact_cap = 0;          // entries allocated for label / size
+    // Hubs: high-degree non-centers that the searches treat as centers (rows rho + i of
+    // label / size, see im_select_hubs).  hub_cap = kHubsAuto: max(1024, n / 64); 0: none.
+    uint32_t hub_cap = imk::kHubsAuto, hub_min_deg = 32;
+    uint32_t hub_rows = 0;           // rows allocated after the rho compact rows
+    uint32_t hubs = 0;               // hubs of the last build (<= hub_rows)
 
     // selection
     uint64_t* d_key = nullptr;
@@ -342,7 +348,7 @@ struct im_ctx {
     uint32_t* d_cflags = nullptr;        // n: center flags
     uint64_t* d_cpos = nullptr;          // n + 1: their exclusive scan
     uint8_t* d_csel = nullptr;           // kCenterSelBytes: radix-select state
-    unsigned long long* h_live = nullptr;   // pinned: live-pair counter before / after a build
+    unsigned long long* h_live = nullptr;   // pinned: live-pair counter before / after a build, hubs
 
     // misc scratch (scan partials, center select)
     void* d_tmp = nullptr;
@@ -378,6 +384,7 @@ int im_edge_probs(im_ctx* c, int model, const double* d_p);   // per-edge thresh
 int im_scan_u32_to_u64(im_ctx* c, const uint32_t* d_in, uint64_t* d_out, uint64_t count);
 // im_sketch.cu
 int im_select_centers(im_ctx* c, uint32_t* d_flags_tmp, uint64_t* d_scan_tmp);
+int im_select_hubs(im_ctx* c, uint32_t* d_flags_tmp, uint64_t* d_scan_tmp);
 int im_sketch_batches(im_ctx* c);
 
 int im_labels_min(im_ctx* c, uint32_t r, uint32_t* d_out);

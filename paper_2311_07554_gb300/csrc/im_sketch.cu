@@ -479,6 +479,64 @@ __global__ void k_center_index(uint32_t n, uint32_t rho, const uint32_t* __restr
 }
 
 
+// ---- hubs: high-degree non-centers that the searches treat as centers -----------------
+// GetCenter from a vertex whose component reaches a high-degree vertex tests that vertex's
+// whole adjacency list unless it is a center -- nearly every time when its edges have small
+// probabilities (the weighted cascade).  The hubs, at most hub_rows non-centers of degree
+// >= min_deg with the largest degrees (ties to the smaller id), get label / size rows of
+// their own after the rho compact rows (index rho + i) and are offered to the union-find's
+// minimum like centers.  A component's key is then its smallest center index if it has a
+// center, else its smallest hub index: every search that meets one of its centers or hubs
+// reads the same size row, which MarkSeed flags.  Rows [0, rho) stay the compact sketch of
+// Sec. 3 bit for bit; the hub rows only shorten searches and change no value.
+__device__ __forceinline__ uint64_t hub_key(uint32_t v, const uint64_t* __restrict__ off,
+                                            const uint32_t* __restrict__ cidx, uint32_t min_deg) {
+    if (cidx[v] != kNone) return ~0ull;   // a center already
+    const uint64_t d = off[v + 1] - off[v];
+    if (d < min_deg) return ~0ull;        // min_deg >= 1, so every eligible key is below ~0
+    const uint32_t dd = d >= 0xFFFFFFFFull ? 0xFFFFFFFEu : (uint32_t)d;
+    return ((uint64_t)(0xFFFFFFFFu - dd) << 32) | v;
+}
+
+__global__ void k_hub_hist(uint32_t n, const uint64_t* __restrict__ off, const uint32_t* __restrict__ cidx,
+                           uint32_t min_deg, CenterSel* st) {
+    __shared__ unsigned int h[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const unsigned long long prefix = st->prefix, pm = st->prefmask;
+    const int shift = st->shift;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const uint64_t key = hub_key(v, off, cidx, min_deg);
+        if ((key & pm) == prefix) atomicAdd(&h[(key >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 256; i += blockDim.x)
+        if (h[i]) atomicAdd(&st->hist[i], h[i]);
+}
+
+__global__ void k_hub_flags(uint32_t n, const uint64_t* __restrict__ off, const uint32_t* __restrict__ cidx,
+                            uint32_t min_deg, const CenterSel* st, uint32_t* __restrict__ flags,
+                            uint32_t* __restrict__ cbits) {
+    const unsigned long long theta = st->prefix;   // the hub_rows-th smallest key
+    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const uint32_t v = base + threadIdx.x;
+        bool f = false;
+        if (v < n) {
+            const uint64_t key = hub_key(v, off, cidx, min_deg);
+            f = key <= theta && key != ~0ull;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (v < n) flags[v] = f ? 1u : 0u;
+        if ((threadIdx.x & 31) == 0 && v < n && bal) cbits[v >> 5] |= bal;   // this warp's word
+    }
+}
+
+__global__ void k_hub_index(uint32_t n, uint32_t rho, const uint32_t* __restrict__ flags,
+                            const uint64_t* __restrict__ pos, uint32_t* __restrict__ cidx) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        if (flags[v]) cidx[v] = rho + (uint32_t)pos[v];
+}
+
 // Sampling and unions of one batch as two kernels (records of live pairs in between).
 int launch_sample_split(im_ctx* c, im_ctx::Lane& L, uint32_t r0, uint32_t nb) {
     const unsigned T = 256;
@@ -574,6 +632,33 @@ int im_select_centers(im_ctx* c, uint32_t* d_flags, uint64_t* d_pos) {
     if (rc) return rc;
     IM_LAUNCH(c, K_CENTER_INDEX, k_center_index, grid_for(n, T, 152u * 8u), T, 0, n, c->rho, d_flags, d_pos,
               c->d_cidx, c->d_centers);
+    IM_CUDA(c, cudaGetLastError());
+    return IM_OK;
+}
+
+// Hubs after the centers (kernels above); their count goes to the pinned word h_live[2].
+int im_select_hubs(im_ctx* c, uint32_t* d_flags, uint64_t* d_pos) {
+    const uint32_t n = c->n;
+    if (c->hub_rows == 0) {
+        c->h_live[2] = 0;
+        return IM_OK;
+    }
+    CenterSel* st = reinterpret_cast<CenterSel*>(c->d_csel);
+    const unsigned T = 256;
+    const uint32_t md = c->hub_min_deg ? c->hub_min_deg : 1u;
+    IM_LAUNCH(c, K_CENTER_PICK, k_center_init, 1, 256, 0, st, c->hub_rows);
+    for (int pass = 0; pass < 8; ++pass) {
+        IM_LAUNCH(c, K_CENTER_HIST, k_hub_hist, grid_for(n, T, 152u * 8u), T, 0, n, c->d_off, c->d_cidx, md, st);
+        IM_LAUNCH(c, K_CENTER_PICK, k_center_pick, 1, 32, 0, st);
+    }
+    IM_LAUNCH(c, K_CENTER_FLAGS, k_hub_flags, grid_for(n, T, 152u * 8u), T, 0, n, c->d_off, c->d_cidx, md, st,
+              d_flags, c->d_cbits);
+    const int rc = im_scan_u32_to_u64(c, d_flags, d_pos, n);
+    if (rc) return rc;
+    IM_LAUNCH(c, K_CENTER_INDEX, k_hub_index, grid_for(n, T, 152u * 8u), T, 0, n, c->rho, d_flags, d_pos,
+              c->d_cidx);
+    IM_CUDA(c, cudaMemcpyAsync(c->h_live + 2, d_pos + n, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                               c->stream));
     IM_CUDA(c, cudaGetLastError());
     return IM_OK;
 }

@@ -467,3 +467,48 @@ def test_per_edge_probability_api():
         with pytest.raises(im.IMError) as e:
             im.im_set_edge_probs(ctx.h, im.IM_PROBS_ARRAY, None)
         assert e.value.code == im.IM_EINVAL
+
+
+# ---- hubs: high-degree non-centers with label rows of their own (search shortcut) -------------
+
+@pytest.mark.parametrize("threshold", [1, 2**64 - 1])
+@pytest.mark.parametrize("model", ["uniform", "wic"])
+@pytest.mark.parametrize("hubs", [(0, 32), (im.IM_HUBS_AUTO, 32), (7, 1), (2**31, 1)])
+def test_hubs_change_no_value(hubs, model, threshold):
+    """Seeds, gains, spread and the compact sketch are the oracle's with no hubs, the automatic
+    set, a handful, and every non-center a hub; both batch evaluators; the hub count is
+    min(cap, non-centers of degree >= min_degree)."""
+    n, u, v = graphgen.chung_lu(20000, 100000, 2.1, 2000.0, 5)
+    G = oracle.Graph(n, u, v)
+    R, seed, k, alpha, p = 64, 42, 12, 0.05, 0.03
+    if model == "wic":
+        G.set_wic()
+        L = G.labels(seed, -1.0, R, mode=oracle.MODE_EDGE)
+    else:
+        L = G.labels(seed, p, R)
+    ctr = oracle.centers(n, seed, alpha)
+    lab, sz = oracle.compact(L, ctr)
+    o_seeds, o_gains = oracle.greedy(L, k)
+    deg = np.bincount(np.concatenate([u, v]), minlength=n)
+    noncenter = np.ones(n, bool)
+    noncenter[ctr] = False
+    cap = max(1024, n // 64) if hubs[0] == im.IM_HUBS_AUTO else hubs[0]
+    want_hubs = min(cap, int((noncenter & (deg >= hubs[1])).sum()))
+    sets = [o_seeds[:3], np.argsort(-deg)[:40].astype(np.uint32), np.arange(0, n, 97, dtype=np.uint32)]
+    with im.IMContext(n, u, v) as ctx:
+        if model == "wic":
+            ctx.set_edge_probs(im.IM_PROBS_WIC)
+        im.im_set_hubs(ctx.h, *hubs)
+        im.im_set_refresh_threshold(ctx.h, threshold)
+        ctx.build_sketches(R, seed, p, alpha)
+        g_lab, g_sz = ctx.compact()
+        assert np.array_equal(g_lab, lab) and np.array_equal(g_sz, sz)
+        seeds, gains = ctx.select_seeds(k)
+        assert np.array_equal(seeds, o_seeds) and np.array_equal(gains, o_gains)
+        for s in sets:
+            assert ctx.spread(s) == oracle.spread(L, s)
+        assert ctx.stats()["hubs"] == want_hubs
+        # the selection again after a reset (hub rows' covered flags are cleared too)
+        ctx.reset_selection()
+        seeds2, gains2 = ctx.select_seeds(k)
+        assert np.array_equal(seeds2, o_seeds) and np.array_equal(gains2, o_gains)
