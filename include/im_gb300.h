@@ -233,7 +233,7 @@ int im_sketch_static(uint32_t n, uint64_t m, const uint32_t* d_u, const uint32_t
 /* Tuning: re-evaluation batches of at least `min_batch` candidates are evaluated by
  * recomputing every sketch's components (Sketch(r), Alg. 3) and looking each candidate up,
  * instead of one GetCenter search per (candidate, sketch); the values are identical.
- * 0 = automatic (max(16384, n / 16)); UINT64_MAX disables it.  Takes effect at the next
+ * 0 = automatic (max(16384, n / 4)); UINT64_MAX disables it.  Takes effect at the next
  * im_build_sketches. */
 int im_set_refresh_threshold(im_ctx* ctx, uint64_t min_batch);
 

@@ -262,7 +262,7 @@ int im_set_pipeline(im_ctx* c, uint32_t lanes) {
 int im_set_refresh_threshold(im_ctx* c, uint64_t min_batch) {
     if (!c) return IM_EINVAL;
     c->refresh_req = min_batch;
-    if (c->built) c->refresh_min = min_batch ? min_batch : std::max<uint64_t>(16384, c->n / 16);
+    if (c->built) c->refresh_min = min_batch ? min_batch : std::max<uint64_t>(16384, c->n / 4);
     return IM_OK;
 }
 
@@ -425,7 +425,7 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
         c->batch_alloc = B;
         c->compact_cap = nc;
     }
-    c->refresh_min = c->refresh_req ? c->refresh_req : std::max<uint64_t>(16384, n / 16);
+    c->refresh_min = c->refresh_req ? c->refresh_req : std::max<uint64_t>(16384, n / 4);
     int rc = IM_OK;
     // live pairs before the build, read with the build's final synchronisation
     IM_CUDA(c, cudaMemcpyAsync(c->h_live, c->d_live_total, sizeof(unsigned long long), cudaMemcpyDeviceToHost,

@@ -72,16 +72,26 @@ k_sample_union(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, ui
 
 // Sampling alone: every live (edge, sketch) pair of the batch becomes a record (u, v, b, 0),
 // appended with one atomic per warp.  The hash work (nb mixes per edge) is pure ALU; the
-// latency-bound unions then run one thread per record in k_union_live.
+// latency-bound unions then run one thread per record in k_union_live.  The kernel also
+// initialises the batch's forest (k_batch_init's stores), which the memory system drains
+// while the hashing runs.
 template <int B>
 __global__ void __launch_bounds__(256)
 k_sample_emit(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, uint32_t r0,
               uint32_t nb, uint4* __restrict__ out, unsigned long long* __restrict__ out_n,
-              uint64_t cap) {
+              uint64_t cap, uint32_t* __restrict__ parent, uint64_t* __restrict__ word, uint32_t n,
+              const uint32_t* __restrict__ cidx, int key_mode) {
     const uint64_t npairs = (m + 1) >> 1;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t g0 = (uint64_t)(r0 + 1u) * kGamma;
     const unsigned lane = threadIdx.x & 31;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const uint64_t w = ((uint64_t)label_key(v, key_mode, cidx) << 32) | 1u;
+        for (uint32_t b = 0; b < nb; ++b) {
+            parent[(size_t)b * n + v] = v;
+            word[(size_t)b * n + v] = w;
+        }
+    }
     for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < npairs; base += stride) {
         const uint64_t i = base + threadIdx.x;
         uint32_t live0 = 0, live1 = 0;
@@ -402,52 +412,25 @@ __global__ void k_labels_out(const uint32_t* __restrict__ P, const uint64_t* __r
 }
 
 // ---- centers: the rho smallest ckey(v) = mix(v ^ csalt) (distinct: mix is a bijection) ----
+// Radix selection of the need-th smallest 64-bit key, 8 bits per pass from the top: a pass
+// histograms the digit of the keys that match the prefix chosen so far, and the last of its
+// blocks (ticket) picks the digit that holds the need-th key.
 struct CenterSel {
     unsigned long long prefix, prefmask, need;
     int shift;
-    unsigned int pad;
+    unsigned int ticket;
     unsigned int hist[256];
 };
 
-__global__ void k_center_init(CenterSel* st, uint32_t rho) {
+__global__ void k_center_init(CenterSel* st, uint32_t need) {
     if (threadIdx.x == 0) {
         st->prefix = 0;
         st->prefmask = 0;
-        st->need = rho;
+        st->need = need;
         st->shift = 56;
-        st->pad = 0;
+        st->ticket = 0;
     }
     for (int i = threadIdx.x; i < 256; i += blockDim.x) st->hist[i] = 0;
-}
-
-__global__ void k_center_hist(uint32_t n, uint64_t csalt, CenterSel* st) {
-    __shared__ unsigned int h[256];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
-    __syncthreads();
-    const unsigned long long prefix = st->prefix, pm = st->prefmask;
-    const int shift = st->shift;
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        uint64_t key = mix64((uint64_t)v ^ csalt);
-        if ((key & pm) == prefix) atomicAdd(&h[(key >> shift) & 255u], 1u);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < 256; i += blockDim.x)
-        if (h[i]) atomicAdd(&st->hist[i], h[i]);
-}
-
-__global__ void k_center_pick(CenterSel* st) {
-    if (threadIdx.x != 0) return;
-    unsigned long long cum = 0;
-    int d = 0;
-    for (; d < 255; ++d) {
-        if (cum + st->hist[d] >= st->need) break;
-        cum += st->hist[d];
-    }
-    st->need -= cum;
-    st->prefix |= (unsigned long long)d << st->shift;
-    st->prefmask |= 255ull << st->shift;
-    st->shift -= 8;
-    for (int i = 0; i < 256; ++i) st->hist[i] = 0;
 }
 
 __global__ void k_center_flags(uint32_t n, uint64_t csalt, const CenterSel* st,
@@ -498,20 +481,58 @@ __device__ __forceinline__ uint64_t hub_key(uint32_t v, const uint64_t* __restri
     return ((uint64_t)(0xFFFFFFFFu - dd) << 32) | v;
 }
 
-__global__ void k_hub_hist(uint32_t n, const uint64_t* __restrict__ off, const uint32_t* __restrict__ cidx,
-                           uint32_t min_deg, CenterSel* st) {
+// One pass of the radix selection over the center keys (kHub = false) or the hub keys.
+template <bool kHub>
+__global__ void __launch_bounds__(256)
+k_select_pass(uint32_t n, uint64_t csalt, const uint64_t* __restrict__ off, const uint32_t* __restrict__ cidx,
+              uint32_t min_deg, CenterSel* st) {
     __shared__ unsigned int h[256];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+    __shared__ unsigned int wsum[8];
+    __shared__ unsigned int s_last, s_d;
+    __shared__ unsigned long long s_cum;
+    const unsigned tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;   // blockDim.x == 256
+    h[tid] = 0;
     __syncthreads();
     const unsigned long long prefix = st->prefix, pm = st->prefmask;
     const int shift = st->shift;
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        const uint64_t key = hub_key(v, off, cidx, min_deg);
+    for (uint32_t v = blockIdx.x * blockDim.x + tid; v < n; v += gridDim.x * blockDim.x) {
+        const uint64_t key = kHub ? hub_key(v, off, cidx, min_deg) : mix64((uint64_t)v ^ csalt);
         if ((key & pm) == prefix) atomicAdd(&h[(key >> shift) & 255u], 1u);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 256; i += blockDim.x)
-        if (h[i]) atomicAdd(&st->hist[i], h[i]);
+    if (h[tid]) atomicAdd(&st->hist[tid], h[tid]);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1 ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return;
+    // the last block: every block's counts are in st->hist
+    __threadfence();
+    const unsigned cnt = __ldcg(&st->hist[tid]);
+    unsigned incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, incl, d);
+        if ((int)lane >= d) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    if (tid == 0) s_d = 255;
+    __syncthreads();
+    for (unsigned w = 0; w < warp; ++w) incl += wsum[w];
+    const unsigned long long need = st->need;
+    // the digit: the first bin whose inclusive count reaches need (bin 255 if none before it)
+    if (tid < 255 && incl >= need && incl - cnt < need) s_d = tid;
+    __syncthreads();
+    if (tid == s_d) s_cum = incl - cnt;
+    __syncthreads();
+    if (tid == 0) {
+        st->need = need - s_cum;
+        st->prefix = prefix | ((unsigned long long)s_d << shift);
+        st->prefmask = pm | (255ull << shift);
+        st->shift = shift - 8;
+        st->ticket = 0;
+    }
+    st->hist[tid] = 0;
 }
 
 __global__ void k_hub_flags(uint32_t n, const uint64_t* __restrict__ off, const uint32_t* __restrict__ cidx,
@@ -538,7 +559,7 @@ __global__ void k_hub_index(uint32_t n, uint32_t rho, const uint32_t* __restrict
 }
 
 // Sampling and unions of one batch as two kernels (records of live pairs in between).
-int launch_sample_split(im_ctx* c, im_ctx::Lane& L, uint32_t r0, uint32_t nb) {
+int launch_sample_split(im_ctx* c, im_ctx::Lane& L, uint32_t r0, uint32_t nb, int key_mode) {
     const unsigned T = 256;
     const uint64_t npairs = (c->m + 1) >> 1;
     const uint4* ep = reinterpret_cast<const uint4*>(c->d_edges);
@@ -549,7 +570,7 @@ int launch_sample_split(im_ctx* c, im_ctx::Lane& L, uint32_t r0, uint32_t nb) {
 #define IM_SE(BB)                                                                                 \
     do {                                                                                          \
         IM_LAUNCH(c, K_SAMPLE_EMIT, k_sample_emit<BB>, gs, T, 0, ep, c->m, c->smp, r0, nb, L.live,   \
-                  L.live_n, c->live_cap);                                                         \
+                  L.live_n, c->live_cap, L.parent, L.word, c->n, c->d_cidx, key_mode);             \
         IM_LAUNCH(c, K_UNION, k_union_live<BB>, gu, T, 0, L.live, L.live_n, c->live_cap, L.parent, \
                   c->n, ep, c->m, c->smp, r0, nb, c->d_live_total);                               \
     } while (0)
@@ -577,11 +598,13 @@ int launch_sample_fused(im_ctx* c, im_ctx::Lane& L, uint32_t r0, uint32_t nb) {
 int batch_components(im_ctx* c, im_ctx::Lane& L, uint32_t r0, uint32_t nb, int key_mode) {
     const uint32_t n = c->n;
     const unsigned T = 256;
-    IM_LAUNCH(c, K_BATCH_INIT, k_batch_init, grid_for((uint64_t)n * nb, T, 152u * 16u), T, 0,
-              L.parent, L.word, n, nb, c->d_cidx, key_mode);
-    if ((c->smp.eT || c->smp.all_live || c->smp.T != 0) && c->m > 0) {
-        const int rc = (L.live && nb <= c->batch_used) ? launch_sample_split(c, L, r0, nb)
-                                                       : launch_sample_fused(c, L, r0, nb);
+    const bool sample = (c->smp.eT || c->smp.all_live || c->smp.T != 0) && c->m > 0;
+    const bool split = sample && L.live && nb <= c->batch_used;   // the emit kernel initialises
+    if (!split)
+        IM_LAUNCH(c, K_BATCH_INIT, k_batch_init, grid_for((uint64_t)n * nb, T, 152u * 16u), T, 0,
+                  L.parent, L.word, n, nb, c->d_cidx, key_mode);
+    if (sample) {
+        const int rc = split ? launch_sample_split(c, L, r0, nb, key_mode) : launch_sample_fused(c, L, r0, nb);
         if (rc) return rc;
     }
     // about 8 blocks per SM in all: each block sweeps a stretch of one sketch
@@ -622,10 +645,9 @@ int im_select_centers(im_ctx* c, uint32_t* d_flags, uint64_t* d_pos) {
     const uint64_t csalt = mix64(c->seed ^ 0xC3ull);
     const unsigned T = 256;
     IM_LAUNCH(c, K_CENTER_PICK, k_center_init, 1, 256, 0, st, c->rho);
-    for (int pass = 0; pass < 8; ++pass) {
-        IM_LAUNCH(c, K_CENTER_HIST, k_center_hist, grid_for(n, T, 152u * 8u), T, 0, n, csalt, st);
-        IM_LAUNCH(c, K_CENTER_PICK, k_center_pick, 1, 32, 0, st);
-    }
+    for (int pass = 0; pass < 8; ++pass)
+        IM_LAUNCH(c, K_CENTER_HIST, k_select_pass<false>, grid_for(n, T, 152u * 4u), T, 0, n, csalt,
+                  (const uint64_t*)nullptr, (const uint32_t*)nullptr, 0u, st);
     IM_LAUNCH(c, K_CENTER_FLAGS, k_center_flags, grid_for(n, T, 152u * 8u), T, 0, n, csalt, st,
               d_flags, c->d_cbits);
     const int rc = im_scan_u32_to_u64(c, d_flags, d_pos, n);
@@ -647,10 +669,9 @@ int im_select_hubs(im_ctx* c, uint32_t* d_flags, uint64_t* d_pos) {
     const unsigned T = 256;
     const uint32_t md = c->hub_min_deg ? c->hub_min_deg : 1u;
     IM_LAUNCH(c, K_CENTER_PICK, k_center_init, 1, 256, 0, st, c->hub_rows);
-    for (int pass = 0; pass < 8; ++pass) {
-        IM_LAUNCH(c, K_CENTER_HIST, k_hub_hist, grid_for(n, T, 152u * 8u), T, 0, n, c->d_off, c->d_cidx, md, st);
-        IM_LAUNCH(c, K_CENTER_PICK, k_center_pick, 1, 32, 0, st);
-    }
+    for (int pass = 0; pass < 8; ++pass)
+        IM_LAUNCH(c, K_CENTER_HIST, k_select_pass<true>, grid_for(n, T, 152u * 4u), T, 0, n, 0ull, c->d_off,
+                  c->d_cidx, md, st);
     IM_LAUNCH(c, K_CENTER_FLAGS, k_hub_flags, grid_for(n, T, 152u * 8u), T, 0, n, c->d_off, c->d_cidx, md, st,
               d_flags, c->d_cbits);
     const int rc = im_scan_u32_to_u64(c, d_flags, d_pos, n);
