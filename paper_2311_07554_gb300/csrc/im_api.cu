@@ -19,7 +19,7 @@ const char* const kNames[K_COUNT] = {
     "reduce_reset", "reduce", "plan", "sel_hist", "sel_pick", "gather", "eval",
     "fallback", "finalize", "mark_seed", "spread_tasks", "spread_dedup", "labels_min",
     "labels_out", "arc_keys", "sample_emit", "union", "cover_roots", "refresh_gather",
-    "count_above", "zero", "select_graph", "sel_begin"};
+    "count_above", "zero", "select_graph", "sel_begin", "sel_step"};
 
 int bitlen64(uint64_t x) {
     int b = 0;

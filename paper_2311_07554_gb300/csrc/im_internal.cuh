@@ -174,6 +174,8 @@ struct SelState {
     unsigned int spec_idx;          // which candidate the first seed is, else kNone
     unsigned int spec_ids[kSpecMax];
     unsigned long long spec_batches;
+    unsigned int phase;             // SelPhase: what the next k_sel_step launch does
+    unsigned int rare;              // SelRare: an evaluator outside k_sel_step is due
 };
 
 enum SelError : unsigned int {
@@ -200,11 +202,22 @@ enum SelMode : unsigned int {
     M_NONE = 14           // nothing: the selection is over
 };
 
+// Phases of k_sel_step.  A batch of mode M runs as a few of them in a row: radix passes
+// (PH_SEL_PASS, hist modes), the gather (PH_GATHER), then an evaluation phase that also scans
+// the other candidates and plans the next batch (PH_EVAL, PH_MARK_EVAL), or PH_SPEC_EVAL +
+// PH_SCAN.  A round opens with PH_SCAN or PH_MARK; PH_COUNT counts candidates above the best.
+enum SelPhase : unsigned int {
+    PH_NONE = 0, PH_SCAN, PH_MARK, PH_MARK_EVAL, PH_EVAL, PH_SEL_PASS, PH_GATHER, PH_SPEC_EVAL, PH_COUNT
+};
+
+// Evaluators with launch sequences of their own (the switch of the selection graph).
+enum SelRare : unsigned int { RARE_CHUNK = 0, RARE_REFRESH = 1, RARE_COUNT = 2, RARE_NONE = 3 };
+
 // Conditional-node handles of the selection graph; on == 0 outside the graph.
 struct SelHandles {
-    cudaGraphConditionalHandle loop, mode;
+    cudaGraphConditionalHandle outer, inner, rare;
     unsigned int on;
-    unsigned int launches[M_COUNT];   // kernels each step mode launches
+    unsigned int rare_launches[RARE_COUNT];   // kernels each rare evaluator launches
 };
 
 struct FbTask {
@@ -219,7 +232,7 @@ enum KernelId {
     K_REDUCE_RESET, K_REDUCE, K_SEL_INIT, K_SEL_HIST, K_SEL_PICK, K_GATHER, K_EVAL,
     K_FALLBACK, K_FINALIZE, K_MARK_SEED, K_SPREAD_TASKS, K_SPREAD_DEDUP, K_LABELS_MIN,
     K_LABELS_OUT, K_ARC_KEYS, K_SAMPLE_EMIT, K_UNION, K_COVER_ROOTS, K_REFRESH_GATHER, K_COUNT_ABOVE,
-    K_ZERO, K_SELECT_GRAPH, K_SEL_BEGIN, K_COUNT
+    K_ZERO, K_SELECT_GRAPH, K_SEL_BEGIN, K_SEL_STEP, K_COUNT
 };
 
 const char* kernel_name(int id);
@@ -296,6 +309,7 @@ struct im_ctx {
     cudaStream_t cap_stream = nullptr;   // owned; only used to capture
     cudaGraph_t sel_graph = nullptr;
     cudaGraphExec_t sel_exec = nullptr;
+    unsigned step_grid = 0;          // blocks of k_sel_step (resident at once)
     bool capturing = false;              // launches go into a graph: no events, no counting
     bool count_only = false;             // launches are only counted (dry run)
     uint64_t dry_count = 0;

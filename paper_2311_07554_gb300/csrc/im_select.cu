@@ -419,31 +419,46 @@ __global__ void k_init_keys(const uint64_t* __restrict__ gain0, uint32_t n, uint
         size[i] &= ~kCovered;
 }
 
-// Unevaluated candidates whose stale key beats the best fresh key of the round: an upper
-// bound on what is left to evaluate in this round (the winner's fresh key is >= best).
-__global__ void __launch_bounds__(256)
-k_count_above(const uint64_t* __restrict__ key, const uint32_t* __restrict__ stamp,
-              const uint8_t* __restrict__ seedflag, uint32_t n, SelState* st) {
-    const unsigned long long best = st->best;
-    // only needed when the round goes on (the next batch's size depends on it)
-    if (!(st->n_unev > 0 && best <= st->stale_max)) return;
-    const uint32_t round = st->round;
-    unsigned long long cnt = 0;
-    if (best)
-        for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-            if (!seedflag[v] && stamp[v] != round && key[v] > best) ++cnt;
-#pragma unroll
-    for (int d = 16; d; d >>= 1) cnt += __shfl_xor_sync(kFull, cnt, d);
-    __shared__ unsigned long long s_cnt[8];
-    if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5] = cnt;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) cnt += s_cnt[i];
-        if (cnt) atomicAdd(&st->count_above, cnt);
+
+constexpr uint32_t kPending = 0x80000000u;   // stamp bit: batch member awaiting its fresh key
+
+// The first phase of a step of the given mode (PH_NONE: the selection is over).
+__device__ __forceinline__ unsigned first_phase(unsigned mode) {
+    switch (mode) {
+    case M_ROUND_START: return PH_SCAN;
+    case M_MARK: return PH_MARK;
+    case M_MARK_DIRECT: return PH_MARK_EVAL;
+    case M_COUNT_ABOVE: return PH_COUNT;
+    case M_DIRECT: return PH_EVAL;
+    case M_SPEC_DIRECT: return PH_SPEC_EVAL;
+    case M_HIST_SINGLE: case M_HIST_CHUNK: case M_SPEC_HIST: return PH_SEL_PASS;
+    case M_GATHER_SINGLE: case M_GATHER_CHUNK: case M_SPEC_GATHER: case M_REFRESH: return PH_GATHER;
+    default: return PH_NONE;
     }
 }
 
-constexpr uint32_t kPending = 0x80000000u;   // stamp bit: batch member awaiting its fresh key
+// The next step is `mode`: its first phase, and the graph's loops entered (or left).
+__device__ void set_step(SelState* st, const SelHandles& hd, unsigned mode) {
+    const unsigned ph = first_phase(mode);
+    st->phase = ph;
+    st->rare = RARE_NONE;
+    if (hd.on) {
+        cudaGraphSetConditional(hd.outer, ph != PH_NONE ? 1u : 0u);
+        cudaGraphSetConditional(hd.inner, ph != PH_NONE ? 1u : 0u);
+        cudaGraphSetConditional(hd.rare, RARE_NONE);
+    }
+}
+
+// The batch is evaluated outside k_sel_step: leave the inner loop for the graph's switch.
+__device__ void set_rare(SelState* st, const SelHandles& hd, unsigned rare) {
+    st->phase = PH_NONE;
+    st->rare = rare;
+    atomicAdd(&st->launches, (unsigned long long)hd.rare_launches[rare]);   // block 0 counts concurrently
+    if (hd.on) {
+        cudaGraphSetConditional(hd.inner, 0u);
+        cudaGraphSetConditional(hd.rare, rare);
+    }
+}
 
 // Next step of the round, decided from the state the last reduction left (Alg. 2's stop
 // test; Alg. 4's doubling batch size): either a batch of ~B of the largest stale keys, picked
@@ -469,10 +484,7 @@ __device__ void plan_step(SelState* st, uint32_t* __restrict__ batch, unsigned l
         st->count_above = 0;
         st->cont = 0;
         st->mode = M_NONE;
-        if (hd.on) {
-            cudaGraphSetConditional(hd.loop, 0u);
-            cudaGraphSetConditional(hd.mode, M_NONE);
-        }
+        set_step(st, hd, M_NONE);
         return;
     }
     if (st->pending) {   // the batch evaluated since the last step
@@ -615,386 +627,11 @@ __device__ void plan_step(SelState* st, uint32_t* __restrict__ batch, unsigned l
     }
     st->cont = cont;
     st->mode = mode;
-    if (cont) st->launches += hd.launches[mode];
-    if (hd.on) {
-        cudaGraphSetConditional(hd.loop, cont);
-        cudaGraphSetConditional(hd.mode, mode);
-    }
+    set_step(st, hd, cont ? mode : M_NONE);
 }
 
-// The planning step after k_count_above.
-__global__ void k_decide(SelState* st, uint32_t* __restrict__ batch, unsigned long long* __restrict__ fresh,
-                         uint64_t* __restrict__ key, uint32_t* __restrict__ stamp,
-                         uint32_t* __restrict__ seed_list, uint64_t* __restrict__ gain_list,
-                         uint64_t* __restrict__ round_evals, uint32_t n, uint32_t R, uint32_t bits,
-                         SelHandles hd) {
-    if (threadIdx.x == 0)
-        plan_step(st, batch, fresh, key, stamp, seed_list, gain_list, round_evals, n, R, bits, hd, true);
-}
 
-// One pass over the candidates: the members of the batch just evaluated (stamp kPending, key
-// = their batch slot) receive their fresh keys; then best = max fresh key of the round,
-// stale_max / n_unev over the others.  The last block to finish plans the next step.
-__global__ void __launch_bounds__(256)
-k_reduce_plan(uint64_t* __restrict__ key, uint32_t* __restrict__ stamp, const uint8_t* __restrict__ seedflag,
-              SelState* st, uint32_t* __restrict__ batch, unsigned long long* __restrict__ fresh,
-              uint32_t* __restrict__ seed_list, uint64_t* __restrict__ gain_list,
-              uint64_t* __restrict__ round_evals, uint32_t n, uint32_t R, uint32_t bits, SelHandles hd) {
-    __shared__ unsigned long long s_bf[8], s_sm[8], s_cnt[8];
-    __shared__ int s_last;
-    const uint32_t round = st->round;
-    unsigned long long bf = 0, sm = 0, cnt = 0;
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        if (seedflag[v]) continue;
-        unsigned long long k = key[v];
-        uint32_t sp = stamp[v];
-        if (sp & kPending) {   // evaluated in this batch: its fresh key (Alg. 2)
-            k = pack_key(fresh[(uint32_t)k], v, bits);
-            key[v] = k;
-            stamp[v] = round;
-            sp = round;
-        }
-        if (sp == round) bf = max(bf, k);
-        else { sm = max(sm, k); ++cnt; }
-    }
-#pragma unroll
-    for (int d = 16; d; d >>= 1) {
-        bf = max(bf, __shfl_xor_sync(kFull, bf, d));
-        sm = max(sm, __shfl_xor_sync(kFull, sm, d));
-        cnt += __shfl_xor_sync(kFull, cnt, d);
-    }
-    const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) { s_bf[w] = bf; s_sm[w] = sm; s_cnt[w] = cnt; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
-            bf = max(bf, s_bf[i]); sm = max(sm, s_sm[i]); cnt += s_cnt[i];
-        }
-        if (bf) atomicMax(&st->best, bf);
-        if (sm) atomicMax(&st->stale_max, sm);
-        if (cnt) atomicAdd(&st->n_unev, cnt);
-        __threadfence();
-        s_last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!s_last) return;
-    if (threadIdx.x == 0) {
-        __threadfence();
-        st->ticket = 0;
-        plan_step(st, batch, fresh, key, stamp, seed_list, gain_list, round_evals, n, R, bits, hd, false);
-    }
-}
-
-// Candidate first seeds of this build.
-__global__ void k_spec_init(SelState* st, const uint32_t* __restrict__ ids, uint32_t count) {
-    if (threadIdx.x == 0) {
-        st->spec_count = count;
-        st->spec_idx = kNone;
-        for (uint32_t k = 0; k < count; ++k) st->spec_ids[k] = ids[k];
-    }
-}
-
-// M_SPEC: Marginal(x | {s0}) = gain0(x) - sum_r |C_r(x)| [s0 in C_r(x)] for every batch member.
-__global__ void __launch_bounds__(256)
-k_spec_eval(const SelState* st, const uint32_t* __restrict__ batch, const uint64_t* __restrict__ gain0,
-            const uint64_t* __restrict__ spec_ov, uint32_t n, unsigned long long* __restrict__ fresh) {
-    const uint32_t bn = st->batch_n;
-    const uint64_t* ov = spec_ov + (size_t)st->spec_idx * n;
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < bn; j += gridDim.x * blockDim.x) {
-        const uint32_t x = batch[j];
-        fresh[j] = gain0[x] - ov[x];
-    }
-}
-
-// One radix pass over the unevaluated candidates: block histograms of the next key byte,
-// added to st->hist; the last block to finish picks the byte (parallel over 256 bins) and
-// either fixes the threshold theta (batch between B and 2B, or exact at the last byte) or
-// narrows the prefix for the next pass.
-__global__ void __launch_bounds__(256)
-k_sel_pass(const uint64_t* __restrict__ key, const uint32_t* __restrict__ stamp,
-           const uint8_t* __restrict__ seedflag, uint32_t n, SelState* st) {
-    if (st->done) return;
-    const uint32_t round = st->round;
-    __shared__ unsigned int h[256];
-    __shared__ unsigned long long sfx[256];
-    __shared__ int s_last;
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
-    __syncthreads();
-    const unsigned long long prefix = st->prefix, pm = st->prefmask;
-    const int shift = st->shift;
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        if (seedflag[v] || stamp[v] == round) continue;
-        const unsigned long long k = key[v];
-        if ((k & pm) == prefix) atomicAdd(&h[(k >> shift) & 255u], 1u);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < 256; i += blockDim.x)
-        if (h[i]) atomicAdd(&st->hist[i], h[i]);
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(&st->pass_blocks, 1u) == gridDim.x - 1);
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    // last block: suffix sums over the 256 bins (bin d counts keys whose byte is d)
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) sfx[i] = __ldcg(&st->hist[i]);
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        // lane l owns bins 8l .. 8l+7; inclusive suffix sum from the top bin down
-        const int l = threadIdx.x;
-        unsigned long long loc[8], acc = 0;
-        for (int i = 7; i >= 0; --i) { acc += sfx[8 * l + i]; loc[i] = acc; }
-        unsigned long long tot_above = 0;   // keys in the bins of the lanes above
-        for (int j = 0; j < 32; ++j) {
-            const unsigned long long y = __shfl_sync(0xffffffffu, acc, j);
-            if (j > l) tot_above += y;
-        }
-        for (int i = 0; i < 8; ++i) sfx[8 * l + i] = loc[i] + tot_above;   // keys with byte >= bin
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned long long need = st->need;
-        int d = 255;
-        while (d > 0 && sfx[d] < need) --d;      // highest bin whose suffix reaches need
-        const unsigned long long above = (d < 255) ? sfx[d + 1] : 0ull;
-        const unsigned long long with_bin = st->taken + sfx[d];
-        if (with_bin <= 2 * st->borig || st->shift == 0) {
-            st->theta = st->prefix | ((unsigned long long)d << st->shift);
-            st->done = 1;
-        } else {
-            st->taken += above;
-            st->need -= above;
-            st->prefix |= (unsigned long long)d << st->shift;
-            st->prefmask |= 255ull << st->shift;
-            st->shift -= 8;
-        }
-        st->pass_blocks = 0;
-    }
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) st->hist[i] = 0;
-}
-
-__global__ void __launch_bounds__(256)
-k_gather(uint64_t* key, uint32_t* stamp, const uint8_t* __restrict__ seedflag, uint32_t n, SelState* st,
-         uint32_t* __restrict__ batch, unsigned long long* __restrict__ fresh) {
-    const uint32_t round = st->round;
-    // a candidate whose stale key is below the best fresh key cannot win (keys are distinct)
-    const unsigned long long bp = st->best_prev;
-    const unsigned long long theta = max(st->theta, bp ? bp + 1 : 0ull);
-    const unsigned lane = threadIdx.x & 31;
-    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
-        const uint32_t v = base + threadIdx.x;
-        bool take = false;
-        if (v < n && !seedflag[v] && stamp[v] != round) take = key[v] >= theta;
-        const unsigned bal = __ballot_sync(kFull, take);
-        if (!bal) continue;
-        uint32_t pos0 = 0;
-        if (lane == 0) pos0 = atomicAdd(&st->batch_n, (unsigned)__popc(bal));
-        pos0 = __shfl_sync(kFull, pos0, 0);
-        if (take) {
-            const uint32_t j = pos0 + __popc(bal & ((1u << lane) - 1u));
-            batch[j] = v;
-            fresh[j] = 0;
-            key[v] = j;                      // its batch slot, until k_reduce_plan
-            stamp[v] = round | kPending;
-        }
-    }
-}
-
-// Marginal (Alg. 3) of every batch member: tasks (member j, chunk of 32 sketches).
-__global__ void __launch_bounds__(kEvalWarps * 32)
-k_eval(GraphView g, SketchView s, SelState* st, const uint32_t* __restrict__ batch,
-       unsigned long long* __restrict__ fresh, FbTask* __restrict__ fbt, uint32_t fb_cap,
-       uint32_t nchunk) {
-    __shared__ uint32_t qls[kEvalWarps][32 * kLaneQ];
-    __shared__ uint32_t qws[kEvalWarps][kQcap + kHashSlots];
-    uint32_t* ql = qls[threadIdx.x >> 5];
-    uint32_t* qw = qws[threadIdx.x >> 5];
-    const unsigned lane = threadIdx.x & 31;
-    const unsigned long long total = (unsigned long long)st->batch_n * nchunk;
-    for (;;) {
-        unsigned long long t = 0;
-        if (lane == 0) t = atomicAdd(&st->eval_next, 1ull);
-        t = __shfl_sync(kFull, t, 0);
-        if (t >= total) break;
-        const uint32_t j = (uint32_t)(t / nchunk), ch = (uint32_t)(t % nchunk);
-        const uint32_t x = batch[j];
-        const uint32_t r_lo = ch * 32, r_hi = min(s.R, r_lo + 32);
-        const uint32_t r = r_lo + lane;
-        unsigned long long d = 0;
-        if (is_center(s, x)) {
-            if (r < r_hi) {
-                const uint32_t l = s.label[(size_t)center_index(s, x) * s.R + r];
-                const uint32_t sz = s.size[(size_t)l * s.R + r];
-                d = (sz & kCovered) ? 0u : sz;
-            }
-        } else {
-            const LaneRes o = get_center_32(g, s, x, r_lo, r_hi, ql, qw, true, st);
-            if (r < r_hi && !o.overflow)
-                s.labcache[(size_t)(x & (kLabSlots - 1)) * s.R + r] = ((uint64_t)x << 32) | o.label;
-            if (r < r_hi) {
-                if (o.overflow) {
-                    push_fallback(st, fbt, fb_cap, x, r, FB_EVAL, j);
-                } else if (o.label != kNone) {
-                    const uint32_t sz = s.size[(size_t)o.label * s.R + r];
-                    d = (sz & kCovered) ? 0u : sz;
-                } else {
-                    d = o.seen ? 0u : o.count;
-                }
-            }
-        }
-        const unsigned long long sum = warp_sum_u64(d);
-        if (lane == 0 && sum) atomicAdd(fresh + j, sum);
-    }
-}
-
-// Marginal for small batches: one block per (member j, sketch r), so that a round that
-// re-evaluates a handful of vertices finishes in the latency of one search, the block's warps
-// sharing the member's first hop (block_search).
-__global__ void __launch_bounds__(kBlockWarps * 32)
-k_eval_single(GraphView g, SketchView s, SelState* st, const uint32_t* __restrict__ batch,
-              unsigned long long* __restrict__ fresh, FbTask* __restrict__ fbt, uint32_t fb_cap) {
-    __shared__ BlockSearchSmem sm;
-    const unsigned long long total = (unsigned long long)st->batch_n * s.R;
-    for (unsigned long long t = blockIdx.x; t < total; t += gridDim.x) {   // uniform over the block
-        const uint32_t j = (uint32_t)(t / s.R), r = (uint32_t)(t % s.R);
-        const uint32_t x = batch[j];
-        unsigned long long d = 0;
-        if (is_center(s, x)) {
-            const uint32_t l = s.label[(size_t)center_index(s, x) * s.R + r];
-            const uint32_t sz = s.size[(size_t)l * s.R + r];
-            d = (sz & kCovered) ? 0u : sz;
-        } else {
-            const BfsOut o = block_search(g, s, x, r, true, sm, st);
-            if (threadIdx.x == 0) {
-                if (!o.overflow)
-                    s.labcache[(size_t)(x & (kLabSlots - 1)) * s.R + r] = ((uint64_t)x << 32) | o.label;
-                if (o.overflow) {
-                    push_fallback(st, fbt, fb_cap, x, r, FB_EVAL, j);
-                } else if (o.label != kNone) {
-                    const uint32_t sz = s.size[(size_t)o.label * s.R + r];
-                    d = (sz & kCovered) ? 0u : sz;
-                } else {
-                    d = o.seen ? 0u : o.count;
-                }
-            }
-        }
-        if (threadIdx.x == 0 && d) atomicAdd(fresh + j, d);
-        __syncthreads();
-    }
-}
-
-// MarkSeed (Alg. 3): in every sketch, flag the component of the last round's winner as
-// covered.  One block per sketch (a single vertex is marked per round, so latency, not
-// total work, decides); labels the winner's evaluation already found are reused.
-__device__ __forceinline__ uint32_t mark_label(const GraphView& g, const SketchView& s, uint32_t sd, uint32_t r,
-                                               BlockSearchSmem& sm, SelState* st, bool* overflow) {
-    *overflow = false;
-    if (is_center(s, sd)) return s.label[(size_t)center_index(s, sd) * s.R + r];
-    // a label found when sd was evaluated is still valid: labels depend on the sketch only
-    const uint64_t e = s.labcache[(size_t)(sd & (kLabSlots - 1)) * s.R + r];
-    if ((uint32_t)(e >> 32) == sd) return (uint32_t)e;
-    const BfsOut o = block_search(g, s, sd, r, false, sm, st);   // block-uniform branch
-    *overflow = o.overflow;
-    return o.label;
-}
-
-__global__ void __launch_bounds__(kBlockWarps * 32)
-k_mark_seed(GraphView g, SketchView s, SelState* st, FbTask* __restrict__ fbt, uint32_t fb_cap,
-            uint8_t* __restrict__ seedflag, uint64_t* __restrict__ key) {
-    __shared__ BlockSearchSmem sm;
-    const uint32_t sd = st->sd;
-    const uint32_t r = blockIdx.x;
-    if (r < s.R) {
-        bool over = false;
-        const uint32_t l = mark_label(g, s, sd, r, sm, st, &over);
-        if (threadIdx.x == 0) {
-            if (over) push_fallback(st, fbt, fb_cap, sd, r, FB_MARK, 0);
-            else if (l != kNone) atomicOr(s.size + (size_t)l * s.R + r, kCovered);
-        }
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        seedflag[sd] = 1;
-        key[sd] = 0;
-    }
-}
-
-// MarkSeed of the last round's winner x fused with the Marginal of this round's only
-// candidate y (batch slot 0), one block per sketch: the block marks x's component first, so
-// that y's search finds it covered; a component without a center that holds x counts as
-// holding a seed through s.pend (x's flag is set concurrently).  If x's search overflows,
-// the fallback kernel does both for that sketch (FB_MARK_EVAL), in the same order.
-__global__ void __launch_bounds__(kBlockWarps * 32)
-k_mark_eval(GraphView g, SketchView s, SelState* st, const uint32_t* __restrict__ batch,
-            unsigned long long* __restrict__ fresh, FbTask* __restrict__ fbt, uint32_t fb_cap,
-            uint8_t* __restrict__ seedflag, uint64_t* __restrict__ key) {
-    __shared__ BlockSearchSmem sm;
-    __shared__ int s_marked;
-    const uint32_t x = st->sd, y = batch[0];
-    s.pend = x;
-    const uint32_t r = blockIdx.x;
-    if (r < s.R) {
-        bool over = false;
-        const uint32_t lx = mark_label(g, s, x, r, sm, st, &over);
-        if (threadIdx.x == 0) {
-            s_marked = !over;
-            if (over) push_fallback(st, fbt, fb_cap, x, r, FB_MARK_EVAL, y);
-            else if (lx != kNone) atomicOr(s.size + (size_t)lx * s.R + r, kCovered);
-        }
-        __syncthreads();
-        if (s_marked) {   // block-uniform
-            unsigned long long d = 0;
-            if (is_center(s, y)) {
-                const uint32_t l = s.label[(size_t)center_index(s, y) * s.R + r];
-                const uint32_t sz = __ldcg(s.size + (size_t)l * s.R + r);
-                d = (sz & kCovered) ? 0u : sz;
-            } else {
-                const BfsOut o = block_search(g, s, y, r, true, sm, st);
-                if (threadIdx.x == 0) {
-                    if (!o.overflow)
-                        s.labcache[(size_t)(y & (kLabSlots - 1)) * s.R + r] = ((uint64_t)y << 32) | o.label;
-                    if (o.overflow) {
-                        push_fallback(st, fbt, fb_cap, y, r, FB_EVAL, 0);
-                    } else if (o.label != kNone) {
-                        const uint32_t sz = __ldcg(s.size + (size_t)o.label * s.R + r);
-                        d = (sz & kCovered) ? 0u : sz;
-                    } else {
-                        d = o.seen ? 0u : o.count;
-                    }
-                }
-            }
-            if (threadIdx.x == 0 && d) atomicAdd(fresh, d);
-        }
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        seedflag[x] = 1;
-        key[x] = 0;
-    }
-}
-
-// Before a selection run: the number of seeds to reach and the refresh threshold.
-__global__ void k_set_target(SelState* st, uint32_t round_end, unsigned long long refresh_min) {
-    if (threadIdx.x == 0) {
-        st->round_end = round_end;
-        st->refresh_min = refresh_min;
-    }
-}
-
-// First node of the selection graph: enter the loop, opening a round, if seeds are missing.
-__global__ void k_sel_begin(SelState* st, SelHandles hd) {
-    if (threadIdx.x == 0) {
-        const unsigned go = (!st->err && st->round < st->round_end) ? 1u : 0u;
-        st->launches += 1 + (go ? hd.launches[M_ROUND_START] : 0u);
-        if (hd.on) {
-            cudaGraphSetConditional(hd.loop, go);
-            cudaGraphSetConditional(hd.mode, M_ROUND_START);
-        }
-    }
-}
-
-__global__ void k_phase_reset(SelState* st) {
-    if (threadIdx.x == 0) { st->fb_n = 0; st->eval_next = 0; st->batch_n = 0; }
-}
-
+// ---- BFS fallback: searches that outgrew the shared-memory queue ------------------------
 // A search from v in sketch r with the queue and visited bitmap of a fallback slot (global
 // memory: no size limit); the bitmap is cleared again before returning.
 struct FbOut {
@@ -1069,20 +706,20 @@ __device__ __forceinline__ unsigned long long fb_delta(const SketchView& s, uint
     return o.seen ? 0u : o.tail;
 }
 
-// Searches that overflowed the shared-memory queue: one warp per slot, queue and visited
-// bitmap in global scratch (n entries / n bits per slot).  FB_MARK_EVAL (from k_mark_eval):
-// MarkSeed of the winner f.v, then the Marginal of the candidate f.idx (batch slot 0), in order.
-__global__ void __launch_bounds__(32)
-k_fallback(GraphView g, SketchView s, SelState* st, const FbTask* __restrict__ fbt, uint32_t fb_cap,
-           uint32_t* __restrict__ fbq, uint32_t* __restrict__ fbb,
-           unsigned long long* __restrict__ fresh, uint64_t* __restrict__ spread_pairs) {
+// The queued fallback tasks, one warp per slot (`worker` of `nworkers`; slot = worker).
+// FB_MARK_EVAL: MarkSeed of the winner f.v, then the Marginal of the candidate f.idx (batch
+// slot 0), in order.
+__device__ void fallback_run(const GraphView& g, const SketchView& s, SelState* st, const FbTask* __restrict__ fbt,
+                             uint32_t fb_cap, uint32_t* __restrict__ fbq, uint32_t* __restrict__ fbb,
+                             unsigned long long* __restrict__ fresh, uint64_t* __restrict__ spread_pairs,
+                             uint32_t worker, uint32_t nworkers) {
     const unsigned lane = threadIdx.x & 31;
-    const uint32_t ntask = min(st->fb_n, fb_cap);
+    const uint32_t ntask = min(__ldcg(&st->fb_n), fb_cap);
     const uint32_t n = g.n;
     const uint32_t nw = (n + 31) >> 5;
-    uint32_t* q = fbq + (size_t)blockIdx.x * n;
-    uint32_t* bits = fbb + (size_t)blockIdx.x * nw;
-    for (uint32_t t = blockIdx.x; t < ntask; t += gridDim.x) {
+    uint32_t* q = fbq + (size_t)worker * n;
+    uint32_t* bits = fbb + (size_t)worker * nw;
+    for (uint32_t t = worker; t < ntask; t += nworkers) {
         const FbTask f = fbt[t];
         const uint32_t r = f.r;
         if (f.kind == FB_MARK_EVAL) {
@@ -1118,6 +755,497 @@ k_fallback(GraphView g, SketchView s, SelState* st, const FbTask* __restrict__ f
         __syncwarp();
     }
 }
+
+__global__ void __launch_bounds__(32)
+k_fallback(GraphView g, SketchView s, SelState* st, const FbTask* __restrict__ fbt, uint32_t fb_cap,
+           uint32_t* __restrict__ fbq, uint32_t* __restrict__ fbb,
+           unsigned long long* __restrict__ fresh, uint64_t* __restrict__ spread_pairs) {
+    fallback_run(g, s, st, fbt, fb_cap, fbq, fbb, fresh, spread_pairs, blockIdx.x, gridDim.x);
+}
+
+// ---- the step kernel ----------------------------------------------------------------
+// Everything one launch of k_sel_step needs.
+struct StepArgs {
+    GraphView g;
+    SketchView s;
+    SelState* st;
+    uint64_t* key;
+    uint32_t* stamp;
+    uint8_t* seedflag;
+    uint32_t* batch;
+    unsigned long long* fresh;
+    uint32_t* seed_list;
+    uint64_t* gain_list;
+    uint64_t* round_evals;
+    const uint64_t* gain0;
+    const uint64_t* spec_ov;
+    FbTask* fbt;
+    uint32_t* fbq;
+    uint32_t* fbb;
+    uint32_t fb_cap, fb_slots;
+    uint32_t n, R, bits;
+    SelHandles hd;
+};
+
+union StepSmem {
+    BlockSearchSmem bs;
+    struct {
+        unsigned int h[256];
+        unsigned long long sfx[256];
+    } sp;
+};
+
+__device__ __forceinline__ void block_max_sum(unsigned long long& a, unsigned long long& b, unsigned long long& c) {
+    __shared__ unsigned long long s_a[8], s_b[8], s_c[8];
+#pragma unroll
+    for (int d = 16; d; d >>= 1) {
+        a = max(a, __shfl_xor_sync(kFull, a, d));
+        b = max(b, __shfl_xor_sync(kFull, b, d));
+        c += __shfl_xor_sync(kFull, c, d);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { s_a[w] = a; s_b[w] = b; s_c[w] = c; }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) { a = max(a, s_a[i]); b = max(b, s_b[i]); c += s_c[i]; }
+    __syncthreads();
+}
+
+// The reduction of a step over every candidate (Alg. 2's stale bound and stop test): best =
+// max fresh key this round, stale_max / n_unev over the candidates not yet evaluated in it.
+// With `finalize`, batch members awaiting their fresh key (stamp kPending, key = their batch
+// slot) receive it here; otherwise an evaluation runs concurrently and they are skipped (the
+// last block finalises them).  `skip` is a seed whose flag the step sets at its end.
+__device__ void scan_candidates(const StepArgs& a, bool finalize, uint32_t skip) {
+    SelState* st = a.st;
+    const uint32_t round = st->round;
+    unsigned long long bf = 0, sm = 0, cnt = 0;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += gridDim.x * blockDim.x) {
+        if (a.seedflag[v] || v == skip) continue;
+        uint32_t sp = a.stamp[v];
+        unsigned long long k = a.key[v];
+        if (sp & kPending) {   // evaluated in this batch
+            if (!finalize) continue;
+            k = pack_key(__ldcg(a.fresh + (uint32_t)k), v, a.bits);
+            a.key[v] = k;
+            a.stamp[v] = round;
+            sp = round;
+        }
+        if (sp == round) bf = max(bf, k);
+        else { sm = max(sm, k); ++cnt; }
+    }
+    block_max_sum(bf, sm, cnt);
+    if (threadIdx.x == 0) {
+        if (bf) atomicMax(&st->best, bf);
+        if (sm) atomicMax(&st->stale_max, sm);
+        if (cnt) atomicAdd(&st->n_unev, cnt);
+    }
+}
+
+// Fresh keys of the batch members (last block, after the evaluation).
+__device__ void finalize_batch(const StepArgs& a) {
+    SelState* st = a.st;
+    const uint32_t round = st->round, bn = __ldcg(&st->batch_n);
+    unsigned long long bf = 0, unused_b = 0, unused_c = 0;
+    for (uint32_t j = threadIdx.x; j < bn; j += blockDim.x) {
+        const uint32_t x = a.batch[j];
+        const unsigned long long k = pack_key(__ldcg(a.fresh + j), x, a.bits);
+        a.key[x] = k;
+        a.stamp[x] = round;
+        bf = max(bf, k);
+    }
+    block_max_sum(bf, unused_b, unused_c);
+    if (threadIdx.x == 0 && bf) atomicMax(&st->best, bf);
+}
+
+// MarkSeed (Alg. 3): in every sketch, flag the component of the last round's winner as
+// covered.  One block per sketch (a single vertex is marked per round, so latency, not
+// total work, decides); labels the winner's evaluation already found are reused.
+__device__ __forceinline__ uint32_t mark_label(const GraphView& g, const SketchView& s, uint32_t sd, uint32_t r,
+                                               BlockSearchSmem& sm, SelState* st, bool* overflow) {
+    *overflow = false;
+    if (is_center(s, sd)) return s.label[(size_t)center_index(s, sd) * s.R + r];
+    // a label found when sd was evaluated is still valid: labels depend on the sketch only
+    const uint64_t e = s.labcache[(size_t)(sd & (kLabSlots - 1)) * s.R + r];
+    if ((uint32_t)(e >> 32) == sd) return (uint32_t)e;
+    const BfsOut o = block_search(g, s, sd, r, false, sm, st);   // block-uniform branch
+    *overflow = o.overflow;
+    return o.label;
+}
+
+__device__ void mark_tasks(const StepArgs& a, BlockSearchSmem& sm) {
+    const uint32_t sd = a.st->sd;
+    for (uint32_t r = blockIdx.x; r < a.R; r += gridDim.x) {   // uniform over the block
+        bool over = false;
+        const uint32_t l = mark_label(a.g, a.s, sd, r, sm, a.st, &over);
+        if (threadIdx.x == 0) {
+            if (over) push_fallback(a.st, a.fbt, a.fb_cap, sd, r, FB_MARK, 0);
+            else if (l != kNone) atomicOr(a.s.size + (size_t)l * a.R + r, kCovered);
+        }
+        __syncthreads();
+    }
+}
+
+// Marginal (Alg. 3) of a candidate in one sketch by a whole block; adds it to fresh[j].
+__device__ void marginal_block(const StepArgs& a, const SketchView& s, uint32_t x, uint32_t r, uint32_t j,
+                               BlockSearchSmem& sm) {
+    unsigned long long d = 0;
+    if (is_center(s, x)) {
+        const uint32_t l = s.label[(size_t)center_index(s, x) * s.R + r];
+        const uint32_t sz = __ldcg(s.size + (size_t)l * s.R + r);
+        d = (sz & kCovered) ? 0u : sz;
+    } else {
+        const BfsOut o = block_search(a.g, s, x, r, true, sm, a.st);
+        if (threadIdx.x == 0) {
+            if (!o.overflow)
+                s.labcache[(size_t)(x & (kLabSlots - 1)) * s.R + r] = ((uint64_t)x << 32) | o.label;
+            if (o.overflow) {
+                push_fallback(a.st, a.fbt, a.fb_cap, x, r, FB_EVAL, j);
+            } else if (o.label != kNone) {
+                const uint32_t sz = __ldcg(s.size + (size_t)o.label * s.R + r);
+                d = (sz & kCovered) ? 0u : sz;
+            } else {
+                d = o.seen ? 0u : o.count;
+            }
+        }
+    }
+    if (threadIdx.x == 0 && d) atomicAdd(a.fresh + j, d);
+}
+
+// Marginal for small batches: one block per (member j, sketch r), so that a round that
+// re-evaluates a handful of vertices finishes in the latency of one search, the block's warps
+// sharing the member's first hop (block_search).
+__device__ void eval_tasks(const StepArgs& a, BlockSearchSmem& sm) {
+    const unsigned long long total = (unsigned long long)__ldcg(&a.st->batch_n) * a.R;
+    for (unsigned long long t = blockIdx.x; t < total; t += gridDim.x) {   // uniform over the block
+        const uint32_t j = (uint32_t)(t / a.R), r = (uint32_t)(t % a.R);
+        marginal_block(a, a.s, a.batch[j], r, j, sm);
+        __syncthreads();
+    }
+}
+
+// MarkSeed of the last round's winner x fused with the Marginal of this round's only
+// candidate y (batch slot 0), one block per sketch: the block marks x's component first, so
+// that y's search finds it covered; a component without a center that holds x counts as
+// holding a seed through s.pend (x's flag is set at the end of the step).  If x's search
+// overflows, the fallback does both for that sketch (FB_MARK_EVAL), in the same order.
+__device__ void mark_eval_tasks(const StepArgs& a, BlockSearchSmem& sm) {
+    __shared__ int s_marked;
+    const uint32_t x = a.st->sd, y = a.batch[0];
+    SketchView s = a.s;
+    s.pend = x;
+    for (uint32_t r = blockIdx.x; r < a.R; r += gridDim.x) {   // uniform over the block
+        bool over = false;
+        const uint32_t lx = mark_label(a.g, s, x, r, sm, a.st, &over);
+        if (threadIdx.x == 0) {
+            s_marked = !over;
+            if (over) push_fallback(a.st, a.fbt, a.fb_cap, x, r, FB_MARK_EVAL, y);
+            else if (lx != kNone) atomicOr(s.size + (size_t)lx * s.R + r, kCovered);
+        }
+        __syncthreads();
+        if (s_marked) marginal_block(a, s, y, r, 0, sm);
+        __syncthreads();
+    }
+}
+
+// Marginal(x | {s0}) = gain0(x) - sum_r |C_r(x)| [s0 in C_r(x)] for every batch member (round
+// 1 after a candidate first seed s0).
+__device__ void spec_eval_tasks(const StepArgs& a) {
+    const uint32_t bn = __ldcg(&a.st->batch_n);
+    const uint64_t* ov = a.spec_ov + (size_t)a.st->spec_idx * a.n;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < bn; j += gridDim.x * blockDim.x) {
+        const uint32_t x = a.batch[j];
+        a.fresh[j] = a.gain0[x] - ov[x];
+    }
+}
+
+// Unevaluated candidates whose stale key beats the best fresh key of the round: an upper
+// bound on what is left to evaluate in this round (the winner's fresh key is >= best).
+__device__ void count_above_tasks(const StepArgs& a) {
+    SelState* st = a.st;
+    const unsigned long long best = st->best;
+    // only needed when the round goes on (the next batch's size depends on it)
+    const bool need = st->n_unev > 0 && best <= st->stale_max && best;
+    const uint32_t round = st->round;
+    unsigned long long cnt = 0, unused_a = 0, unused_b = 0;
+    if (need)
+        for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += gridDim.x * blockDim.x)
+            if (!a.seedflag[v] && a.stamp[v] != round && a.key[v] > best) ++cnt;
+    block_max_sum(unused_a, unused_b, cnt);
+    if (threadIdx.x == 0 && cnt) atomicAdd(&st->count_above, cnt);
+}
+
+// One radix pass over the unevaluated candidates: block histograms of the next key byte,
+// added to st->hist; the last block picks the byte (sel_pass_pick).
+__device__ void sel_pass_tasks(const StepArgs& a, StepSmem& sm) {
+    SelState* st = a.st;
+    const uint32_t round = st->round;
+    unsigned int* h = sm.sp.h;
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const unsigned long long prefix = st->prefix, pm = st->prefmask;
+    const int shift = st->shift;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += gridDim.x * blockDim.x) {
+        if (a.seedflag[v] || a.stamp[v] == round) continue;
+        const unsigned long long k = a.key[v];
+        if ((k & pm) == prefix) atomicAdd(&h[(k >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 256; i += blockDim.x)
+        if (h[i]) atomicAdd(&st->hist[i], h[i]);
+}
+
+// Last block of a pass: either fix the threshold theta (batch between B and 2B, or exact at
+// the last byte) or narrow the prefix for the next pass.
+__device__ void sel_pass_pick(SelState* st, StepSmem& sm) {
+    unsigned long long* sfx = sm.sp.sfx;
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) sfx[i] = __ldcg(&st->hist[i]);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        // lane l owns bins 8l .. 8l+7; inclusive suffix sum from the top bin down
+        const int l = threadIdx.x;
+        unsigned long long loc[8], acc = 0;
+        for (int i = 7; i >= 0; --i) { acc += sfx[8 * l + i]; loc[i] = acc; }
+        unsigned long long tot_above = 0;   // keys in the bins of the lanes above
+        for (int j = 0; j < 32; ++j) {
+            const unsigned long long y = __shfl_sync(0xffffffffu, acc, j);
+            if (j > l) tot_above += y;
+        }
+        for (int i = 0; i < 8; ++i) sfx[8 * l + i] = loc[i] + tot_above;   // keys with byte >= bin
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long need = st->need;
+        int d = 255;
+        while (d > 0 && sfx[d] < need) --d;      // highest bin whose suffix reaches need
+        const unsigned long long above = (d < 255) ? sfx[d + 1] : 0ull;
+        const unsigned long long with_bin = st->taken + sfx[d];
+        if (with_bin <= 2 * st->borig || st->shift == 0) {
+            st->theta = st->prefix | ((unsigned long long)d << st->shift);
+            st->done = 1;
+        } else {
+            st->taken += above;
+            st->need -= above;
+            st->prefix |= (unsigned long long)d << st->shift;
+            st->prefmask |= 255ull << st->shift;
+            st->shift -= 8;
+        }
+    }
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) st->hist[i] = 0;
+}
+
+// The batch: every unevaluated candidate with a stale key >= theta (and above the best fresh
+// key: one below it cannot win, keys being distinct).
+__device__ void gather_tasks(const StepArgs& a) {
+    SelState* st = a.st;
+    const uint32_t round = st->round;
+    const unsigned long long bp = st->best_prev;
+    const unsigned long long theta = max(st->theta, bp ? bp + 1 : 0ull);
+    const unsigned lane = threadIdx.x & 31;
+    for (uint32_t base = blockIdx.x * blockDim.x; base < a.n; base += gridDim.x * blockDim.x) {
+        const uint32_t v = base + threadIdx.x;
+        bool take = false;
+        if (v < a.n && !a.seedflag[v] && a.stamp[v] != round) take = a.key[v] >= theta;
+        const unsigned bal = __ballot_sync(kFull, take);
+        if (!bal) continue;
+        uint32_t pos0 = 0;
+        if (lane == 0) pos0 = atomicAdd(&st->batch_n, (unsigned)__popc(bal));
+        pos0 = __shfl_sync(kFull, pos0, 0);
+        if (take) {
+            const uint32_t j = pos0 + __popc(bal & ((1u << lane) - 1u));
+            a.batch[j] = v;
+            a.fresh[j] = 0;
+            a.key[v] = j;                      // its batch slot, until its fresh key
+            a.stamp[v] = round | kPending;
+        }
+    }
+}
+
+// One phase of the selection per launch (SelState::phase); the last block to finish runs the
+// phase's epilogue: the radix pick, the next phase, or -- after an evaluation -- the queued
+// fallback searches, the batch's fresh keys, MarkSeed's flag and the plan of the next step
+// (plan_step).  The grid is fixed (about the resident blocks); phases stride over their work.
+__global__ void __launch_bounds__(kBlockWarps * 32)
+k_sel_step(StepArgs a) {
+    __shared__ StepSmem sm;
+    __shared__ unsigned int s_last;
+    SelState* st = a.st;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&st->launches, 1ull);
+    const unsigned phase = st->phase;
+    if (phase == PH_NONE) return;
+    const bool marking = phase == PH_MARK || phase == PH_MARK_EVAL;
+    switch (phase) {
+    case PH_SCAN: scan_candidates(a, true, kNone); break;
+    case PH_MARK:
+        mark_tasks(a, sm.bs);
+        scan_candidates(a, false, st->sd);
+        break;
+    case PH_MARK_EVAL:
+        mark_eval_tasks(a, sm.bs);
+        scan_candidates(a, false, st->sd);
+        break;
+    case PH_EVAL:
+        eval_tasks(a, sm.bs);
+        scan_candidates(a, false, kNone);
+        break;
+    case PH_SEL_PASS: sel_pass_tasks(a, sm); break;
+    case PH_GATHER: gather_tasks(a); break;
+    case PH_SPEC_EVAL: spec_eval_tasks(a); break;
+    case PH_COUNT: count_above_tasks(a); break;
+    default: break;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1 ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x == 0) st->ticket = 0;
+    switch (phase) {
+    case PH_SEL_PASS:
+        sel_pass_pick(st, sm);
+        if (threadIdx.x == 0) st->phase = st->done ? PH_GATHER : PH_SEL_PASS;
+        return;
+    case PH_GATHER:
+        if (threadIdx.x == 0) {
+            const unsigned mode = st->mode;
+            if (mode == M_GATHER_CHUNK || mode == M_HIST_CHUNK) set_rare(st, a.hd, RARE_CHUNK);
+            else if (mode == M_REFRESH) set_rare(st, a.hd, RARE_REFRESH);
+            else if (mode == M_SPEC_GATHER || mode == M_SPEC_HIST) st->phase = PH_SPEC_EVAL;
+            else st->phase = PH_EVAL;
+        }
+        return;
+    case PH_SPEC_EVAL:
+        if (threadIdx.x == 0) st->phase = PH_SCAN;
+        return;
+    default: break;
+    }
+    if (phase == PH_MARK || phase == PH_MARK_EVAL || phase == PH_EVAL) {
+        // searches that outgrew the shared queue, one warp per fallback slot
+        if (__ldcg(&st->fb_n)) {
+            const uint32_t nwk = min((uint32_t)(blockDim.x >> 5), a.fb_slots);
+            if ((threadIdx.x >> 5) < nwk)
+                fallback_run(a.g, a.s, st, a.fbt, a.fb_cap, a.fbq, a.fbb, a.fresh, nullptr, threadIdx.x >> 5, nwk);
+            __threadfence();
+            __syncthreads();
+        }
+        if (phase != PH_MARK) finalize_batch(a);
+        if (marking && threadIdx.x == 0) {
+            a.seedflag[st->sd] = 1;
+            a.key[st->sd] = 0;
+        }
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        plan_step(st, a.batch, a.fresh, a.key, a.stamp, a.seed_list, a.gain_list, a.round_evals, a.n, a.R, a.bits,
+                  a.hd, phase == PH_COUNT);
+    }
+}
+
+// The reduction and plan after an evaluator outside k_sel_step (PH_SCAN's work as a kernel).
+__global__ void __launch_bounds__(256)
+k_reduce_plan(StepArgs a) {
+    __shared__ unsigned int s_last;
+    SelState* st = a.st;
+    scan_candidates(a, true, kNone);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1 ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        st->ticket = 0;
+        plan_step(st, a.batch, a.fresh, a.key, a.stamp, a.seed_list, a.gain_list, a.round_evals, a.n, a.R, a.bits,
+                  a.hd, false);
+    }
+}
+
+// Candidate first seeds of this build.
+__global__ void k_spec_init(SelState* st, const uint32_t* __restrict__ ids, uint32_t count) {
+    if (threadIdx.x == 0) {
+        st->spec_count = count;
+        st->spec_idx = kNone;
+        for (uint32_t k = 0; k < count; ++k) st->spec_ids[k] = ids[k];
+    }
+}
+
+// Before a selection run: the number of seeds to reach and the refresh threshold.
+__global__ void k_set_target(SelState* st, uint32_t round_end, unsigned long long refresh_min) {
+    if (threadIdx.x == 0) {
+        st->round_end = round_end;
+        st->refresh_min = refresh_min;
+    }
+}
+
+// First node of a selection run: open a round (PH_SCAN) if seeds are missing.
+__global__ void k_sel_begin(SelState* st, SelHandles hd) {
+    if (threadIdx.x == 0) {
+        const unsigned go = (!st->err && st->round < st->round_end) ? 1u : 0u;
+        st->launches += 1;
+        st->phase = go ? PH_SCAN : PH_NONE;
+        st->rare = RARE_NONE;
+        if (hd.on) {
+            cudaGraphSetConditional(hd.outer, go);
+            cudaGraphSetConditional(hd.inner, go);
+            cudaGraphSetConditional(hd.rare, RARE_NONE);
+        }
+    }
+}
+
+__global__ void k_phase_reset(SelState* st) {
+    if (threadIdx.x == 0) { st->fb_n = 0; st->eval_next = 0; st->batch_n = 0; }
+}
+
+// Marginal (Alg. 3) of every batch member: tasks (member j, chunk of 32 sketches).
+__global__ void __launch_bounds__(kEvalWarps * 32)
+k_eval(GraphView g, SketchView s, SelState* st, const uint32_t* __restrict__ batch,
+       unsigned long long* __restrict__ fresh, FbTask* __restrict__ fbt, uint32_t fb_cap,
+       uint32_t nchunk) {
+    __shared__ uint32_t qls[kEvalWarps][32 * kLaneQ];
+    __shared__ uint32_t qws[kEvalWarps][kQcap + kHashSlots];
+    uint32_t* ql = qls[threadIdx.x >> 5];
+    uint32_t* qw = qws[threadIdx.x >> 5];
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned long long total = (unsigned long long)st->batch_n * nchunk;
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(&st->eval_next, 1ull);
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= total) break;
+        const uint32_t j = (uint32_t)(t / nchunk), ch = (uint32_t)(t % nchunk);
+        const uint32_t x = batch[j];
+        const uint32_t r_lo = ch * 32, r_hi = min(s.R, r_lo + 32);
+        const uint32_t r = r_lo + lane;
+        unsigned long long d = 0;
+        if (is_center(s, x)) {
+            if (r < r_hi) {
+                const uint32_t l = s.label[(size_t)center_index(s, x) * s.R + r];
+                const uint32_t sz = s.size[(size_t)l * s.R + r];
+                d = (sz & kCovered) ? 0u : sz;
+            }
+        } else {
+            const LaneRes o = get_center_32(g, s, x, r_lo, r_hi, ql, qw, true, st);
+            if (r < r_hi && !o.overflow)
+                s.labcache[(size_t)(x & (kLabSlots - 1)) * s.R + r] = ((uint64_t)x << 32) | o.label;
+            if (r < r_hi) {
+                if (o.overflow) {
+                    push_fallback(st, fbt, fb_cap, x, r, FB_EVAL, j);
+                } else if (o.label != kNone) {
+                    const uint32_t sz = s.size[(size_t)o.label * s.R + r];
+                    d = (sz & kCovered) ? 0u : sz;
+                } else {
+                    d = o.seen ? 0u : o.count;
+                }
+            }
+        }
+        const unsigned long long sum = warp_sum_u64(d);
+        if (lane == 0 && sum) atomicAdd(fresh + j, sum);
+    }
+}
+
+// Marginal for small batches: one block per (member j, sketch r), so that a round that
+// re-evaluates a handful of vertices finishes in the latency of one search, the block's warps
 
 // ---- spread: per (seed i, sketch r) the component's identity and size, then dedup -----
 __global__ void __launch_bounds__(kEvalWarps * 32)
@@ -1202,6 +1330,23 @@ SketchView sketch_view(const im_ctx* c) {
     return s;
 }
 
+StepArgs step_args(const im_ctx* c, const SelHandles& hd) {
+    StepArgs a;
+    a.g = graph_view(c);
+    a.s = sketch_view(c);
+    a.st = c->d_sel;
+    a.key = c->d_key; a.stamp = c->d_stamp; a.seedflag = c->d_seedflag;
+    a.batch = c->d_batch; a.fresh = (unsigned long long*)c->d_fresh;
+    a.seed_list = c->d_seed_list; a.gain_list = c->d_gain_list; a.round_evals = c->d_round_evals;
+    a.gain0 = c->d_gain0; a.spec_ov = c->lane[0].spec_ov;
+    a.fbt = c->d_fb_tasks; a.fbq = c->d_fb_queue; a.fbb = c->d_fb_bits;
+    a.fb_cap = c->fb_cap;
+    a.fb_slots = (c->all_centers || !c->d_fb_queue) ? 0u : c->fb_slots;
+    a.n = c->n; a.R = c->R; a.bits = c->key_bits;
+    a.hd = hd;
+    return a;
+}
+
 // copy the device state to the pinned mirror and wait
 int pull_state(im_ctx* c) {
     IM_CUDA(c, cudaMemcpyAsync(c->h_sel, c->d_sel, sizeof(SelState), cudaMemcpyDeviceToHost, c->stream));
@@ -1248,93 +1393,50 @@ int im_selection_init(im_ctx* c) {
 
 namespace {
 
-// Radix passes a batch can need: one per key byte from the top byte of the largest key
-// (gains are at most R n, so keys stay below 2^(b + bitlen(R n))).
-int max_radix_passes(const im_ctx* c) {
-    uint64_t top = (uint64_t)c->R * c->n;
-    int bl = 0;
-    while (top) { ++bl; top >>= 1; }
-    const int key_top = (int)c->key_bits + bl - 1;
-    return (key_top > 63 ? 63 : key_top) / 8 + 1;
-}
-
-// The launches of one batch of the given mode (the body of the graph's switch); passes =
-// radix passes to queue (each returns at once once the threshold is fixed).
-int launch_reduce_plan(im_ctx* c, const SelHandles& hd) {
-    IM_LAUNCH(c, K_REDUCE, k_reduce_plan, grid_for(c->n, 256, 152u * 8u), 256, 0, c->d_key, c->d_stamp,
-              c->d_seedflag, c->d_sel, c->d_batch, (unsigned long long*)c->d_fresh, c->d_seed_list,
-              c->d_gain_list, c->d_round_evals, c->n, c->R, c->key_bits, hd);
+// The grid of k_sel_step: the blocks that fit on the device at once.
+int size_step_grid(im_ctx* c) {
+    if (c->step_grid) return IM_OK;
+    int per_sm = 0, sms = 0;
+    IM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sel_step, kBlockWarps * 32, 0));
+    IM_CUDA(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    c->step_grid = (unsigned)std::max(1, per_sm) * (unsigned)std::max(1, sms);
     return IM_OK;
 }
 
-int enqueue_mode(im_ctx* c, unsigned mode, int passes, const SelHandles& hd) {
-    const uint32_t n = c->n;
-    const unsigned T = 256;
-    const unsigned gridn = grid_for(n, T, 152u * 8u);
-    const GraphView g = graph_view(c);
-    const SketchView s = sketch_view(c);
+// One phase of the selection (k_sel_step).
+int launch_step(im_ctx* c, const SelHandles& hd) {
+    const int rc = size_step_grid(c);
+    if (rc) return rc;
+    IM_LAUNCH(c, K_SEL_STEP, k_sel_step, c->step_grid, kBlockWarps * 32, 0, step_args(c, hd));
+    return IM_OK;
+}
+
+int launch_reduce_plan(im_ctx* c, const SelHandles& hd) {
+    IM_LAUNCH(c, K_REDUCE, k_reduce_plan, grid_for(c->n, 256, 152u * 8u), 256, 0, step_args(c, hd));
+    return IM_OK;
+}
+
+// The launches of an evaluator outside k_sel_step (a case of the graph's switch), once the
+// batch is gathered: large batches by one warp per (member, 32 sketches), very large ones by
+// recomputing the sketches; then the reduction and plan.
+int enqueue_rare(im_ctx* c, unsigned rare, const SelHandles& hd) {
     SelState* st = c->d_sel;
     unsigned long long* fresh = (unsigned long long*)c->d_fresh;
-    if (mode == M_ROUND_START) return launch_reduce_plan(c, hd);
-    if (mode == M_MARK || mode == M_MARK_DIRECT) {
-        if (mode == M_MARK)
-            IM_LAUNCH(c, K_MARK_SEED, k_mark_seed, c->R, kBlockWarps * 32, 0, g, s, st, c->d_fb_tasks, c->fb_cap,
-                      c->d_seedflag, c->d_key);
-        else
-            IM_LAUNCH(c, K_MARK_SEED, k_mark_eval, c->R, kBlockWarps * 32, 0, g, s, st, c->d_batch, fresh,
-                      c->d_fb_tasks, c->fb_cap, c->d_seedflag, c->d_key);
-        launch_fallback(c, g, s);
-        return launch_reduce_plan(c, hd);
-    }
-    if (mode == M_COUNT_ABOVE) {
-        IM_LAUNCH(c, K_COUNT_ABOVE, k_count_above, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n, st);
-        IM_LAUNCH(c, K_SEL_INIT, k_decide, 1, 32, 0, st, c->d_batch, fresh, c->d_key, c->d_stamp, c->d_seed_list,
-                  c->d_gain_list, c->d_round_evals, n, c->R, c->key_bits, hd);
-        return IM_OK;
-    }
-    if (mode == M_HIST_SINGLE || mode == M_HIST_CHUNK || mode == M_SPEC_HIST)
-        for (int p = 0; p < passes; ++p)
-            IM_LAUNCH(c, K_SEL_HIST, k_sel_pass, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n, st);
-    if (mode != M_DIRECT && mode != M_SPEC_DIRECT)
-        IM_LAUNCH(c, K_GATHER, k_gather, gridn, T, 0, c->d_key, c->d_stamp, c->d_seedflag, n, st, c->d_batch,
-                  fresh);
-    switch (mode) {
-    case M_DIRECT:
-        IM_LAUNCH(c, K_EVAL, k_eval_single, c->R, kBlockWarps * 32, 0, g, s, st, c->d_batch, fresh, c->d_fb_tasks,
-                  c->fb_cap);
-        launch_fallback(c, g, s);
-        break;
-    case M_GATHER_SINGLE:
-    case M_HIST_SINGLE:
-        IM_LAUNCH(c, K_EVAL, k_eval_single, grid_for(kSingleTasks, 1, 152u * 8u), kBlockWarps * 32, 0, g, s, st,
-                  c->d_batch, fresh, c->d_fb_tasks, c->fb_cap);
-        launch_fallback(c, g, s);
-        break;
-    case M_GATHER_CHUNK:
-    case M_HIST_CHUNK: {
+    if (rare == RARE_CHUNK) {
+        const GraphView g = graph_view(c);
+        const SketchView s = sketch_view(c);
         const uint32_t nchunk = (c->R + 31) / 32;
-        IM_LAUNCH(c, K_EVAL, k_eval, search_grid((uint64_t)n * nchunk), kEvalWarps * 32, 0, g, s, st, c->d_batch,
+        IM_LAUNCH(c, K_EVAL, k_eval, search_grid((uint64_t)c->n * nchunk), kEvalWarps * 32, 0, g, s, st, c->d_batch,
                   fresh, c->d_fb_tasks, c->fb_cap, nchunk);
         launch_fallback(c, g, s);
-        break;
-    }
-    case M_REFRESH: {
+    } else if (rare == RARE_REFRESH) {
         const int rc = im_refresh_eval(c, c->d_batch, &st->batch_n, fresh, c->d_seed_list, &st->round);
         if (rc) return rc;
-        break;
-    }
-    case M_SPEC_DIRECT:
-    case M_SPEC_GATHER:
-    case M_SPEC_HIST:
-        IM_LAUNCH(c, K_REFRESH_GATHER, k_spec_eval, gridn, T, 0, st, c->d_batch, c->d_gain0, c->lane[0].spec_ov, n,
-                  fresh);
-        break;
-    default:
-        return im_fail(c, IM_EDEVICE, "unknown batch mode");
+    } else {
+        return im_fail(c, IM_EDEVICE, "unknown batch evaluator");
     }
     return launch_reduce_plan(c, hd);
 }
-
 
 int cap_begin(im_ctx* c, cudaGraph_t graph, const cudaGraphNode_t* deps, size_t ndeps) {
     IM_CUDA(c, cudaStreamBeginCaptureToGraph(c->cap_stream, graph, deps, nullptr, ndeps,
@@ -1400,49 +1502,60 @@ int cap_conditional(im_ctx* c, cudaGraphConditionalHandle h, cudaGraphConditiona
                                                    cudaStreamSetCaptureDependencies));
     return IM_OK;
 }
-
 // The whole lazy-greedy loop as one graph, so that rounds run back to back without the host:
-//   sel_begin; while (loop) { switch (mode) { one step: a round's opening reduction, a batch,
-//                                             a count, or a MarkSeed (possibly fused with
-//                                             the next round's first batch) } }
-// Every decision is taken on the device (k_reduce_plan / k_decide via plan_step).  The loop
-// is bounded: a round ends after at most 82 batches, the selection after round_end rounds.
+//   sel_begin;
+//   while (outer) {
+//       while (inner) { k_sel_step x kStepsPerLoop }      -- one phase per launch
+//       switch (rare) { chunk evaluation | recomputation, then k_reduce_plan }
+//   }
+// Every decision is taken on the device (plan_step, run by the last block of a step).  An
+// iteration of a while loop or a switch costs several microseconds, a kernel node about one,
+// so the phases of ordinary batches are launches of one kernel in a loop, not cases of a
+// switch.  The loop is bounded: a round ends after at most 82 batches, the selection after
+// round_end rounds.
+constexpr int kStepsPerLoop = 4;
+
 int build_select_graph_steps(im_ctx* c) {
     SelHandles hd{};
     hd.on = 1;
-    const int passes = max_radix_passes(c);
-    // launches per step mode, counted by dry runs of the same code
+    // launches of each rare evaluator, counted by dry runs of the same code
     c->count_only = true;
     int rc = IM_OK;
-    for (unsigned m = 0; m < M_COUNT && !rc; ++m) {
+    for (unsigned m = 0; m < RARE_COUNT && !rc; ++m) {
         c->dry_count = 0;
-        rc = enqueue_mode(c, m, passes, hd);
-        hd.launches[m] = (unsigned)c->dry_count;
+        rc = enqueue_rare(c, m, hd);
+        hd.rare_launches[m] = (unsigned)c->dry_count;
     }
     c->count_only = false;
     if (rc) return rc;
+    if ((rc = size_step_grid(c))) return rc;   // before the capture
 
     IM_CUDA(c, cudaGraphCreate(&c->sel_graph, 0));
-    // the loop node first, so that its switch's handle exists before sel_begin (which sets
-    // it) is captured in front of it
-    IM_CUDA(c, cudaGraphConditionalHandleCreate(&hd.loop, c->sel_graph, 0, 0));
-    cudaGraph_t wloop = nullptr, cases[M_COUNT] = {};
-    cudaGraphNode_t lnode = nullptr;
-    if ((rc = add_conditional(c, c->sel_graph, hd.loop, cudaGraphCondTypeWhile, 1, &wloop, &lnode))) return rc;
-    IM_CUDA(c, cudaGraphConditionalHandleCreate(&hd.mode, wloop, M_NONE, 0));
+    // the outer loop node first, so that the handles sel_begin sets exist before it is captured
+    IM_CUDA(c, cudaGraphConditionalHandleCreate(&hd.outer, c->sel_graph, 0, 0));
+    cudaGraph_t obody = nullptr, ibody = nullptr, rcases[RARE_COUNT] = {};
+    cudaGraphNode_t onode = nullptr;
+    if ((rc = add_conditional(c, c->sel_graph, hd.outer, cudaGraphCondTypeWhile, 1, &obody, &onode))) return rc;
+    IM_CUDA(c, cudaGraphConditionalHandleCreate(&hd.inner, obody, 0, 0));
+    IM_CUDA(c, cudaGraphConditionalHandleCreate(&hd.rare, obody, RARE_NONE, 0));
     if ((rc = cap_begin(c, c->sel_graph, nullptr, 0))) return rc;
     IM_LAUNCH(c, K_SEL_BEGIN, k_sel_begin, 1, 32, 0, c->d_sel, hd);
     cudaGraphNode_t first = nullptr;
     if ((rc = cap_frontier(c, &first))) return rc;
     if ((rc = cap_end(c))) return rc;
-    IM_CUDA(c, cudaGraphAddDependencies(c->sel_graph, &first, &lnode, nullptr, 1));
+    IM_CUDA(c, cudaGraphAddDependencies(c->sel_graph, &first, &onode, nullptr, 1));
 
-    if ((rc = cap_begin(c, wloop, nullptr, 0))) return rc;
-    if ((rc = cap_conditional(c, hd.mode, cudaGraphCondTypeSwitch, M_COUNT, cases))) return rc;
+    if ((rc = cap_begin(c, obody, nullptr, 0))) return rc;
+    if ((rc = cap_conditional(c, hd.inner, cudaGraphCondTypeWhile, 1, &ibody))) return rc;
+    if ((rc = cap_conditional(c, hd.rare, cudaGraphCondTypeSwitch, RARE_COUNT, rcases))) return rc;
     if ((rc = cap_end(c))) return rc;
-    for (unsigned m = 0; m < M_COUNT; ++m) {
-        if ((rc = cap_begin(c, cases[m], nullptr, 0))) return rc;
-        if ((rc = enqueue_mode(c, m, passes, hd))) return rc;
+    if ((rc = cap_begin(c, ibody, nullptr, 0))) return rc;
+    for (int i = 0; i < kStepsPerLoop && !rc; ++i) rc = launch_step(c, hd);
+    if (rc) return rc;
+    if ((rc = cap_end(c))) return rc;
+    for (unsigned m = 0; m < RARE_COUNT; ++m) {
+        if ((rc = cap_begin(c, rcases[m], nullptr, 0))) return rc;
+        if ((rc = enqueue_rare(c, m, hd))) return rc;
         if ((rc = cap_end(c))) return rc;
     }
     IM_CUDA(c, cudaGraphInstantiate(&c->sel_exec, c->sel_graph, 0));
@@ -1477,19 +1590,18 @@ const char* sel_error_text(unsigned e) {
     }
 }
 
-// The same steps driven from the host: one synchronisation per step to read the decision.
+// The same phases driven from the host: one synchronisation per launch to read the decision.
 int run_rounds_host(im_ctx* c) {
     const SelHandles none{};
-    int rc = pull_state(c);
-    if (rc) return rc;
-    if (c->h_sel->err || c->h_sel->round >= c->h_sel->round_end) return IM_OK;
-    unsigned mode = M_ROUND_START;
+    IM_LAUNCH(c, K_SEL_BEGIN, k_sel_begin, 1, 32, 0, c->d_sel, none);
     for (;;) {
-        const bool hist = mode == M_HIST_SINGLE || mode == M_HIST_CHUNK || mode == M_SPEC_HIST;
-        if ((rc = enqueue_mode(c, mode, hist ? c->h_sel->shift / 8 + 1 : 0, none))) return rc;
-        if ((rc = pull_state(c))) return rc;
-        if (!c->h_sel->cont) return IM_OK;
-        mode = c->h_sel->mode;
+        int rc = pull_state(c);
+        if (rc) return rc;
+        const SelState& h = *c->h_sel;
+        if (h.rare != RARE_NONE) rc = enqueue_rare(c, h.rare, none);
+        else if (h.phase != PH_NONE) rc = launch_step(c, none);
+        else return IM_OK;
+        if (rc) return rc;
     }
 }
 
@@ -1569,3 +1681,4 @@ int im_spread_run(im_ctx* c, uint32_t k, uint64_t* out) {
     *out = h;
     return IM_OK;
 }
+
