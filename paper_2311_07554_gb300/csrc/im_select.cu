@@ -811,21 +811,40 @@ __device__ __forceinline__ void block_max_sum(unsigned long long& a, unsigned lo
     __syncthreads();
 }
 
+// f(v, seedflag[v], stamp[v], key[v]) for the candidates v assigned to thread t0 of nthr:
+// four consecutive ids per iteration with one vector load per array, so that a thread has
+// all its loads of an iteration in flight at once.
+template <class F>
+__device__ __forceinline__ void for_candidates(const StepArgs& a, uint32_t t0, uint32_t nthr, F f) {
+    const uint32_t n4 = a.n >> 2;
+    const uchar4* sf4 = reinterpret_cast<const uchar4*>(a.seedflag);
+    const uint4* sp4 = reinterpret_cast<const uint4*>(a.stamp);
+    const ulonglong2* k2 = reinterpret_cast<const ulonglong2*>(a.key);
+    for (uint32_t i = t0; i < n4; i += nthr) {
+        const uchar4 sf = sf4[i];
+        const uint4 sp = sp4[i];
+        const ulonglong2 ka = k2[2 * i], kb = k2[2 * i + 1];
+        f(4 * i, sf.x, sp.x, ka.x);
+        f(4 * i + 1, sf.y, sp.y, ka.y);
+        f(4 * i + 2, sf.z, sp.z, kb.x);
+        f(4 * i + 3, sf.w, sp.w, kb.y);
+    }
+    for (uint32_t v = 4 * n4 + t0; v < a.n; v += nthr) f(v, a.seedflag[v], a.stamp[v], a.key[v]);
+}
+
 // The reduction of a step over every candidate (Alg. 2's stale bound and stop test): best =
 // max fresh key this round, stale_max / n_unev over the candidates not yet evaluated in it.
 // With `finalize`, batch members awaiting their fresh key (stamp kPending, key = their batch
 // slot) receive it here; otherwise an evaluation runs concurrently and they are skipped (the
 // last block finalises them).  `skip` is a seed whose flag the step sets at its end.
-__device__ void scan_candidates(const StepArgs& a, bool finalize, uint32_t skip) {
+__device__ void scan_candidates(const StepArgs& a, bool finalize, uint32_t skip, uint32_t t0, uint32_t nthr) {
     SelState* st = a.st;
     const uint32_t round = st->round;
     unsigned long long bf = 0, sm = 0, cnt = 0;
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += gridDim.x * blockDim.x) {
-        if (a.seedflag[v] || v == skip) continue;
-        uint32_t sp = a.stamp[v];
-        unsigned long long k = a.key[v];
+    for_candidates(a, t0, nthr, [&](uint32_t v, uint8_t sf, uint32_t sp, unsigned long long k) {
+        if (sf || v == skip) return;
         if (sp & kPending) {   // evaluated in this batch
-            if (!finalize) continue;
+            if (!finalize) return;
             k = pack_key(__ldcg(a.fresh + (uint32_t)k), v, a.bits);
             a.key[v] = k;
             a.stamp[v] = round;
@@ -833,13 +852,18 @@ __device__ void scan_candidates(const StepArgs& a, bool finalize, uint32_t skip)
         }
         if (sp == round) bf = max(bf, k);
         else { sm = max(sm, k); ++cnt; }
-    }
+    });
     block_max_sum(bf, sm, cnt);
     if (threadIdx.x == 0) {
         if (bf) atomicMax(&st->best, bf);
         if (sm) atomicMax(&st->stale_max, sm);
         if (cnt) atomicAdd(&st->n_unev, cnt);
     }
+}
+
+// scan_candidates over the whole grid
+__device__ __forceinline__ void scan_all(const StepArgs& a, bool finalize, uint32_t skip) {
+    scan_candidates(a, finalize, skip, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // Fresh keys of the batch members (last block, after the evaluation).
@@ -969,8 +993,10 @@ __device__ void count_above_tasks(const StepArgs& a) {
     const uint32_t round = st->round;
     unsigned long long cnt = 0, unused_a = 0, unused_b = 0;
     if (need)
-        for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += gridDim.x * blockDim.x)
-            if (!a.seedflag[v] && a.stamp[v] != round && a.key[v] > best) ++cnt;
+        for_candidates(a, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x,
+                       [&](uint32_t, uint8_t sf, uint32_t sp, unsigned long long k) {
+                           if (!sf && sp != round && k > best) ++cnt;
+                       });
     block_max_sum(unused_a, unused_b, cnt);
     if (threadIdx.x == 0 && cnt) atomicAdd(&st->count_above, cnt);
 }
@@ -985,11 +1011,10 @@ __device__ void sel_pass_tasks(const StepArgs& a, StepSmem& sm) {
     __syncthreads();
     const unsigned long long prefix = st->prefix, pm = st->prefmask;
     const int shift = st->shift;
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += gridDim.x * blockDim.x) {
-        if (a.seedflag[v] || a.stamp[v] == round) continue;
-        const unsigned long long k = a.key[v];
-        if ((k & pm) == prefix) atomicAdd(&h[(k >> shift) & 255u], 1u);
-    }
+    for_candidates(a, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x,
+                   [&](uint32_t, uint8_t sf, uint32_t sp, unsigned long long k) {
+                       if (!sf && sp != round && (k & pm) == prefix) atomicAdd(&h[(k >> shift) & 255u], 1u);
+                   });
     __syncthreads();
     for (int i = threadIdx.x; i < 256; i += blockDim.x)
         if (h[i]) atomicAdd(&st->hist[i], h[i]);
@@ -1042,21 +1067,43 @@ __device__ void gather_tasks(const StepArgs& a) {
     const unsigned long long bp = st->best_prev;
     const unsigned long long theta = max(st->theta, bp ? bp + 1 : 0ull);
     const unsigned lane = threadIdx.x & 31;
-    for (uint32_t base = blockIdx.x * blockDim.x; base < a.n; base += gridDim.x * blockDim.x) {
-        const uint32_t v = base + threadIdx.x;
-        bool take = false;
-        if (v < a.n && !a.seedflag[v] && a.stamp[v] != round) take = a.key[v] >= theta;
-        const unsigned bal = __ballot_sync(kFull, take);
-        if (!bal) continue;
+    const uint32_t stride = gridDim.x * blockDim.x * 4;
+    // the loop bound is uniform over the warp: lanes cover ids base + 4 lane .. + 3
+    for (uint32_t base = (blockIdx.x * blockDim.x + (threadIdx.x & ~31u)) * 4; base < a.n; base += stride) {
+        const uint32_t v0 = base + 4 * lane;
+        uint32_t take = 0;   // bit e: candidate v0 + e joins the batch
+        if (v0 + 3 < a.n) {
+            const uchar4 sf = reinterpret_cast<const uchar4*>(a.seedflag)[v0 >> 2];
+            const uint4 sp = reinterpret_cast<const uint4*>(a.stamp)[v0 >> 2];
+            const ulonglong2 ka = reinterpret_cast<const ulonglong2*>(a.key)[v0 >> 1];
+            const ulonglong2 kb = reinterpret_cast<const ulonglong2*>(a.key)[(v0 >> 1) + 1];
+            take = (!sf.x && sp.x != round && ka.x >= theta ? 1u : 0u) | (!sf.y && sp.y != round && ka.y >= theta ? 2u : 0u) |
+                   (!sf.z && sp.z != round && kb.x >= theta ? 4u : 0u) | (!sf.w && sp.w != round && kb.y >= theta ? 8u : 0u);
+        } else {
+            for (uint32_t e = 0; e < 4; ++e) {
+                const uint32_t v = v0 + e;
+                if (v < a.n && !a.seedflag[v] && a.stamp[v] != round && a.key[v] >= theta) take |= 1u << e;
+            }
+        }
+        const uint32_t cnt = __popc(take);
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, d);
+            if ((int)lane >= d) incl += y;
+        }
+        const uint32_t wtot = __shfl_sync(kFull, incl, 31);
+        if (!wtot) continue;
         uint32_t pos0 = 0;
-        if (lane == 0) pos0 = atomicAdd(&st->batch_n, (unsigned)__popc(bal));
-        pos0 = __shfl_sync(kFull, pos0, 0);
-        if (take) {
-            const uint32_t j = pos0 + __popc(bal & ((1u << lane) - 1u));
+        if (lane == 31) pos0 = atomicAdd(&st->batch_n, wtot);
+        uint32_t j = __shfl_sync(kFull, pos0, 31) + incl - cnt;
+        for (uint32_t t = take; t; t &= t - 1) {
+            const uint32_t v = v0 + __ffs(t) - 1;
             a.batch[j] = v;
             a.fresh[j] = 0;
             a.key[v] = j;                      // its batch slot, until its fresh key
             a.stamp[v] = round | kPending;
+            ++j;
         }
     }
 }
@@ -1074,19 +1121,26 @@ k_sel_step(StepArgs a) {
     const unsigned phase = st->phase;
     if (phase == PH_NONE) return;
     const bool marking = phase == PH_MARK || phase == PH_MARK_EVAL;
+    // evaluation phases: if enough blocks are left over, blocks [0, ntask) search (one task
+    // each) while the others scan the candidates; else every block scans after its searches
+    const unsigned long long ntask = phase == PH_EVAL ? (unsigned long long)__ldcg(&st->batch_n) * a.R : a.R;
+    const uint32_t free0 = (ntask + 64 <= gridDim.x) ? (uint32_t)ntask : 0u;
+    const bool scanner = blockIdx.x >= free0;
+    const uint32_t t0 = (blockIdx.x - (scanner ? free0 : 0u)) * blockDim.x + threadIdx.x;
+    const uint32_t nthr = (gridDim.x - free0) * blockDim.x;
     switch (phase) {
-    case PH_SCAN: scan_candidates(a, true, kNone); break;
+    case PH_SCAN: scan_all(a, true, kNone); break;
     case PH_MARK:
-        mark_tasks(a, sm.bs);
-        scan_candidates(a, false, st->sd);
+        if (!free0 || !scanner) mark_tasks(a, sm.bs);
+        if (scanner) scan_candidates(a, false, st->sd, t0, nthr);
         break;
     case PH_MARK_EVAL:
-        mark_eval_tasks(a, sm.bs);
-        scan_candidates(a, false, st->sd);
+        if (!free0 || !scanner) mark_eval_tasks(a, sm.bs);
+        if (scanner) scan_candidates(a, false, st->sd, t0, nthr);
         break;
     case PH_EVAL:
-        eval_tasks(a, sm.bs);
-        scan_candidates(a, false, kNone);
+        if (!free0 || !scanner) eval_tasks(a, sm.bs);
+        if (scanner) scan_candidates(a, false, kNone, t0, nthr);
         break;
     case PH_SEL_PASS: sel_pass_tasks(a, sm); break;
     case PH_GATHER: gather_tasks(a); break;
@@ -1147,7 +1201,7 @@ __global__ void __launch_bounds__(256)
 k_reduce_plan(StepArgs a) {
     __shared__ unsigned int s_last;
     SelState* st = a.st;
-    scan_candidates(a, true, kNone);
+    scan_all(a, true, kNone);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) s_last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1 ? 1u : 0u;
