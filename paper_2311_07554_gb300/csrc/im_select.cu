@@ -474,7 +474,7 @@ __device__ void plan_step(SelState* st, uint32_t* __restrict__ batch, unsigned l
                           uint64_t* __restrict__ round_evals, uint32_t n, uint32_t R, uint32_t bits,
                           const SelHandles& hd, bool have_count) {
     unsigned cont = 0, mode = M_NONE;
-    const unsigned long long nu = __ldcg(&st->n_unev), smax = __ldcg(&st->stale_max), best = __ldcg(&st->best);
+    const unsigned long long nu = st->n_unev, smax = st->stale_max, best = st->best;
     const unsigned j = st->j;
     const uint64_t mask = (1ull << bits) - 1ull;
     if (j == 0 && st->round >= st->round_end) {   // every requested seed is chosen and marked
@@ -491,11 +491,11 @@ __device__ void plan_step(SelState* st, uint32_t* __restrict__ batch, unsigned l
         st->pending = 0;
         const unsigned bn = st->batch_n;
         st->evals_total += bn;
-        st->fb_total += min(__ldcg(&st->fb_n), 0xFFFFFFFFu);
+        st->fb_total += min(st->fb_n, 0xFFFFFFFFu);
         st->fb_n = 0;    // the fallback kernel has run; MarkSeed may queue its own searches
         if (!st->err && bn == 0) st->err = SEL_NO_PROGRESS;
     }
-    if (!st->err && __ldcg(&st->fb_overflow)) st->err = SEL_FB_OVERFLOW;
+    if (!st->err && st->fb_overflow) st->err = SEL_FB_OVERFLOW;
     if (!st->err && nu > 0 && best <= smax) {
         if (j > 81) st->err = SEL_NO_PROGRESS;   // doubling covers any n within 64 batches
         else cont = 1;
@@ -511,7 +511,7 @@ __device__ void plan_step(SelState* st, uint32_t* __restrict__ batch, unsigned l
         // has grown large), evaluate every one of them at once by recomputing the sketches;
         // the round then ends, since all remaining stale keys are below the new best.
         const unsigned long long rmin = st->refresh_min;
-        const unsigned long long above = __ldcg(&st->count_above);
+        const unsigned long long above = st->count_above;
         const bool refresh = expect >= rmin || (best && above >= rmin);
         if (refresh) {
             B = nu;
@@ -630,6 +630,27 @@ __device__ void plan_step(SelState* st, uint32_t* __restrict__ batch, unsigned l
     set_step(st, hd, cont ? mode : M_NONE);
 }
 
+
+// plan_step by the last block of a launch: the state is copied to shared memory (its fields
+// are read and written many times, one after the other), planned there and copied back.
+// Every other block of the launch has finished, so nothing else touches the state meanwhile.
+__device__ void plan_shared(SelState* st, uint32_t* __restrict__ batch, unsigned long long* __restrict__ fresh,
+                            uint64_t* __restrict__ key, uint32_t* __restrict__ stamp,
+                            uint32_t* __restrict__ seed_list, uint64_t* __restrict__ gain_list,
+                            uint64_t* __restrict__ round_evals, uint32_t n, uint32_t R, uint32_t bits,
+                            const SelHandles& hd, bool have_count) {
+    static_assert(sizeof(SelState) % 8 == 0, "state copied in 8-byte words");
+    constexpr uint32_t kWords = sizeof(SelState) / 8;
+    __shared__ SelState ss;
+    unsigned long long* g = reinterpret_cast<unsigned long long*>(st);
+    unsigned long long* l = reinterpret_cast<unsigned long long*>(&ss);
+    for (uint32_t i = threadIdx.x; i < kWords; i += blockDim.x) l[i] = __ldcg(g + i);
+    __syncthreads();
+    if (threadIdx.x == 0) plan_step(&ss, batch, fresh, key, stamp, seed_list, gain_list, round_evals, n, R, bits, hd,
+                                    have_count);
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < kWords; i += blockDim.x) g[i] = l[i];
+}
 
 // ---- BFS fallback: searches that outgrew the shared-memory queue ------------------------
 // A search from v in sketch r with the queue and visited bitmap of a fallback slot (global
@@ -1023,26 +1044,29 @@ __device__ void sel_pass_tasks(const StepArgs& a, StepSmem& sm) {
 // Last block of a pass: either fix the threshold theta (batch between B and 2B, or exact at
 // the last byte) or narrow the prefix for the next pass.
 __device__ void sel_pass_pick(SelState* st, StepSmem& sm) {
-    unsigned long long* sfx = sm.sp.sfx;
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) sfx[i] = __ldcg(&st->hist[i]);
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        // lane l owns bins 8l .. 8l+7; inclusive suffix sum from the top bin down
-        const int l = threadIdx.x;
-        unsigned long long loc[8], acc = 0;
-        for (int i = 7; i >= 0; --i) { acc += sfx[8 * l + i]; loc[i] = acc; }
-        unsigned long long tot_above = 0;   // keys in the bins of the lanes above
-        for (int j = 0; j < 32; ++j) {
-            const unsigned long long y = __shfl_sync(0xffffffffu, acc, j);
-            if (j > l) tot_above += y;
-        }
-        for (int i = 0; i < 8; ++i) sfx[8 * l + i] = loc[i] + tot_above;   // keys with byte >= bin
+    __shared__ unsigned long long s_wsum[8];
+    __shared__ int s_d;
+    unsigned long long* sfx = sm.sp.sfx;   // sfx[d]: candidates whose byte is >= d
+    const unsigned tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;   // blockDim.x == 256
+    unsigned long long x = __ldcg(&st->hist[tid]);
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {   // suffix sum within the warp
+        const unsigned long long y = __shfl_down_sync(kFull, x, d);
+        if (lane + d < 32) x += y;
     }
+    if (lane == 0) s_wsum[warp] = x;
+    if (tid == 0) s_d = 0;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned long long need = st->need;
-        int d = 255;
-        while (d > 0 && sfx[d] < need) --d;      // highest bin whose suffix reaches need
+    for (unsigned w = warp + 1; w < 8; ++w) x += s_wsum[w];
+    sfx[tid] = x;
+    st->hist[tid] = 0;
+    __syncthreads();
+    const unsigned long long need = st->need;
+    // the highest bin whose suffix reaches need (suffixes fall with the bin; bin 0 if none)
+    if (x >= need && (tid == 255 || sfx[tid + 1] < need)) s_d = (int)tid;
+    __syncthreads();
+    if (tid == 0) {
+        const int d = s_d;
         const unsigned long long above = (d < 255) ? sfx[d + 1] : 0ull;
         const unsigned long long with_bin = st->taken + sfx[d];
         if (with_bin <= 2 * st->borig || st->shift == 0) {
@@ -1056,7 +1080,6 @@ __device__ void sel_pass_pick(SelState* st, StepSmem& sm) {
             st->shift -= 8;
         }
     }
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) st->hist[i] = 0;
 }
 
 // The batch: every unevaluated candidate with a stale key >= theta (and above the best fresh
@@ -1189,11 +1212,10 @@ k_sel_step(StepArgs a) {
             a.key[st->sd] = 0;
         }
     }
-    if (threadIdx.x == 0) {
-        __threadfence();
-        plan_step(st, a.batch, a.fresh, a.key, a.stamp, a.seed_list, a.gain_list, a.round_evals, a.n, a.R, a.bits,
-                  a.hd, phase == PH_COUNT);
-    }
+    __threadfence();
+    __syncthreads();
+    plan_shared(st, a.batch, a.fresh, a.key, a.stamp, a.seed_list, a.gain_list, a.round_evals, a.n, a.R, a.bits,
+                a.hd, phase == PH_COUNT);
 }
 
 // The reduction and plan after an evaluator outside k_sel_step (PH_SCAN's work as a kernel).
@@ -1207,12 +1229,11 @@ k_reduce_plan(StepArgs a) {
     if (threadIdx.x == 0) s_last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1 ? 1u : 0u;
     __syncthreads();
     if (!s_last) return;
-    if (threadIdx.x == 0) {
-        __threadfence();
-        st->ticket = 0;
-        plan_step(st, a.batch, a.fresh, a.key, a.stamp, a.seed_list, a.gain_list, a.round_evals, a.n, a.R, a.bits,
-                  a.hd, false);
-    }
+    __threadfence();
+    if (threadIdx.x == 0) st->ticket = 0;
+    __syncthreads();
+    plan_shared(st, a.batch, a.fresh, a.key, a.stamp, a.seed_list, a.gain_list, a.round_evals, a.n, a.R, a.bits,
+                a.hd, false);
 }
 
 // Candidate first seeds of this build.
