@@ -327,6 +327,18 @@ def run_ours(args, n, u, v, prm):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step, ms_build, ms_select = t.tolist()
 
+    # Monte-Carlo influence of the selected seeds (the paper's quality measure), after the
+    # timed region: MC_SIMS live-edge worlds of an independent hash seed.
+    mc = None
+    if args.mc_sims > 0:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mc_total = ctx.mc_spread(seeds, args.mc_sims, prm["seed"] + 1000)
+        mc_s = time.perf_counter() - t0
+        mc = {"sims": args.mc_sims, "hash_seed": prm["seed"] + 1000, "ms": mc_s * 1e3,
+              "sigma_estimate": mc_total / args.mc_sims, "sketch_estimate": int(sp) / R,
+              "pairs_per_s": m * args.mc_sims / mc_s}
+
     # End to end through the public API with host buffers (pinned): a long-lived context
     # (created once, like a serving engine) receives each step's graph from host memory
     # (im_load_graph: h2d copy, validation, CSR) and returns seeds, gains and the spread.
@@ -385,6 +397,7 @@ def run_ours(args, n, u, v, prm):
             "refresh_batches": int(st["refresh_batches"]),
             "spec_batches": int(st["spec_batches"]),
             "hubs": int(st["hubs"]),
+            "mc_eval": mc,
             "roofline": roof,
             "kernel_rooflines": list(roofs.values()),
             "cpu_baseline": cpu,
@@ -415,10 +428,15 @@ def main():
     ap.add_argument("--sketch-batch", type=int, default=0, help="sketches per edge pass (0 = auto)")
     ap.add_argument("--probs", default="uniform", choices=["uniform", "u01", "u13", "wic"],
                     help="IC probabilities: the workload's p, or per edge U(0,0.1), U(0.1,0.3), 2/(d_u+d_v)")
+    ap.add_argument("--mc-sims", type=int, default=20000,
+                    help="Monte-Carlo simulations to evaluate the selected seeds with, after the timed region (0: none)")
+    ap.add_argument("--alpha", type=float, default=None, help="center fraction (default: the workload's)")
     args = ap.parse_args()
     n, u, v, prm = graphgen.workload(args.workload)
     prm["name"] = args.workload
     prm["probs"] = args.probs
+    if args.alpha is not None:
+        prm["alpha"] = args.alpha
     if args.impl == "reference":
         return run_reference(args, n, u, v, prm)
     return run_ours(args, n, u, v, prm)

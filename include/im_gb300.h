@@ -257,6 +257,25 @@ int im_set_graph(im_ctx* ctx, int on);
  * Seeds, gains and evaluation counts do not depend on it. */
 int im_set_seed_speculation(im_ctx* ctx, uint32_t candidates);
 
+/*
+ * im_mc_spread -- Monte-Carlo influence of a seed set: the paper's quality measure (Sec. 5
+ * averages the number of vertices an IC cascade from S activates over independent
+ * simulations).  An IC cascade activates exactly the vertices reachable from S over the live
+ * edges of an independently sampled live-edge graph (Sec. 2), so simulation r is the
+ * live-edge world that a sketch with index r would sample under the edge hash seed `mc_seed`
+ * and the context's probabilities (the p of the last im_build_sketches, or the per-edge model
+ * set then).  Different mc_seed values give independent simulations; the sketches' own seed
+ * gives back their worlds.
+ *   seeds     HOST array of k vertex ids (< n; duplicates allowed), k <= 16384; not modified.
+ *   sims      number of simulations (0 gives 0).
+ *   out       HOST: sum over the simulations of |vertices reachable from S|, an exact integer;
+ *             the estimate of sigma(S) is *out / sims.
+ * Reuses the build's per-batch scratch (the sketches themselves are untouched).  Blocks until
+ * done.  Errors: IM_ESTATE (no build yet), IM_EINVAL (NULL arrays, k too large, an id >= n),
+ * IM_ENOMEM, IM_ECUDA.
+ */
+int im_mc_spread(im_ctx* ctx, const uint32_t* seeds, uint32_t k, uint32_t sims, uint64_t mc_seed, uint64_t* out);
+
 /* Tuning: hubs.  GetCenter (Alg. 3) from a vertex whose component reaches a high-degree
  * non-center tests that vertex's whole adjacency list, in every sketch where it is reached.
  * With hubs, up to `cap` non-centers of degree >= `min_degree` (the largest degrees, ties to

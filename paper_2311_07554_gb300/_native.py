@@ -75,6 +75,7 @@ def lib():
         "im_hash_peak": ([u32, c.POINTER(dbl)], i32),
         "im_set_seed_speculation": ([vp, u32], i32),
         "im_set_hubs": ([vp, u32, u32], i32),
+        "im_mc_spread": ([vp, ctypes.POINTER(ctypes.c_uint32), u32, u32, u64, ctypes.POINTER(ctypes.c_uint64)], i32),
         "im_stream": ([vp], vp),
         "im_sketch_static": ([u32, u64, vp, vp, u64, dbl, u32, vp, vp, vp], i32),
         "im_last_error": ([vp], c.c_char_p),
@@ -259,6 +260,16 @@ def im_set_seed_speculation(ctx, candidates: int):
     _check(ctx, lib().im_set_seed_speculation(ctx, candidates))
 
 
+def im_mc_spread(ctx, seeds, sims: int, mc_seed: int) -> int:
+    """Sum over `sims` Monte-Carlo simulations (live-edge worlds of hash seed `mc_seed`) of the
+    number of vertices reachable from the seeds; the estimate of sigma(S) is the result / sims."""
+    s = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint32))
+    out = ctypes.c_uint64(0)
+    _check(ctx, lib().im_mc_spread(ctx, s.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), len(s), sims, mc_seed,
+                                   ctypes.byref(out)))
+    return int(out.value)
+
+
 IM_HUBS_AUTO = 0xFFFFFFFF
 
 
@@ -325,6 +336,9 @@ class IMContext:
 
     def spread(self, seeds):
         return im_spread(self.h, seeds)
+
+    def mc_spread(self, seeds, sims, mc_seed):
+        return im_mc_spread(self.h, seeds, sims, mc_seed)
 
     def reset_selection(self):
         im_reset_selection(self.h)

@@ -500,6 +500,29 @@ int im_spread(im_ctx* c, const uint32_t* seeds, uint32_t k, uint64_t* spread_out
     return im_spread_run(c, k, spread_out);
 }
 
+int im_mc_spread(im_ctx* c, const uint32_t* seeds, uint32_t k, uint32_t sims, uint64_t mc_seed, uint64_t* out) {
+    if (!c) return IM_EINVAL;
+    if (!c->built) return im_fail(c, IM_ESTATE, "im_build_sketches has not run");
+    if (!out) return im_fail(c, IM_EINVAL, "out is NULL");
+    if (k > kSpreadKMax) return im_fail(c, IM_EINVAL, "k exceeds 16384");
+    if (k > 0 && !seeds) return im_fail(c, IM_EINVAL, "seeds is NULL");
+    for (uint32_t i = 0; i < k; ++i)
+        if (seeds[i] >= c->n) return im_fail(c, IM_EINVAL, "seed id >= n");
+    if (!c->d_spread_seeds && !dalloc(c->d_spread_seeds, kSpreadKMax))
+        return im_fail(c, IM_ENOMEM, "spread seeds");
+    if (k > 0)
+        IM_CUDA(c, cudaMemcpyAsync(c->d_spread_seeds, seeds, k * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                                   c->stream));
+    IM_CUDA(c, cudaMemsetAsync(c->d_spread_total, 0, sizeof(unsigned long long), c->stream));
+    int rc = im_mc_run(c, c->d_spread_seeds, k, sims, mc_seed, c->d_spread_total);
+    if (rc) return rc;
+    unsigned long long h = 0;
+    IM_CUDA(c, cudaMemcpyAsync(&h, c->d_spread_total, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    IM_CUDA(c, cudaStreamSynchronize(c->stream));
+    *out = h;
+    return IM_OK;
+}
+
 int im_get_labels(im_ctx* c, uint32_t r, uint32_t* out, int ptr_kind) {
     if (!c) return IM_EINVAL;
     if (!c->built) return im_fail(c, IM_ESTATE, "im_build_sketches has not run");

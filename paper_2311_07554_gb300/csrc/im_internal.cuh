@@ -399,6 +399,8 @@ int im_scan_u32_to_u64(im_ctx* c, const uint32_t* d_in, uint64_t* d_out, uint64_
 // im_sketch.cu
 int im_select_centers(im_ctx* c, uint32_t* d_flags_tmp, uint64_t* d_scan_tmp);
 int im_select_hubs(im_ctx* c, uint32_t* d_flags_tmp, uint64_t* d_scan_tmp);
+int im_mc_run(im_ctx* c, const uint32_t* d_seeds, uint32_t k, uint32_t sims, uint64_t mc_seed,
+              unsigned long long* d_total);
 int im_sketch_batches(im_ctx* c);
 
 int im_labels_min(im_ctx* c, uint32_t r, uint32_t* d_out);

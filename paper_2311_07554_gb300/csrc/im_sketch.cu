@@ -388,6 +388,24 @@ __global__ void k_cover_roots(const uint32_t* __restrict__ parent, uint64_t* __r
     }
 }
 
+// Monte-Carlo spread of one batch of simulations: every seed's root is flagged (kCovered on
+// its root word's size), and the first seed to flag a root adds that component's size.
+__global__ void __launch_bounds__(256)
+k_mc_cover(const uint32_t* __restrict__ parent, uint64_t* __restrict__ word, uint32_t n, uint32_t nb,
+           const uint32_t* __restrict__ seeds, uint32_t k, unsigned long long* __restrict__ total) {
+    const uint32_t tasks = nb * k;
+    unsigned long long acc = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < tasks; i += gridDim.x * blockDim.x) {
+        const uint32_t b = i / k, sd = seeds[i % k];
+        const uint32_t root = parent[(size_t)b * n + sd];
+        const uint32_t old = atomicOr(w_count(word + (size_t)b * n + root), kCovered);
+        if (!(old & kCovered)) acc += old;
+    }
+#pragma unroll
+    for (int d = 16; d; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(total, acc);
+}
+
 // Recomputation evaluator: fresh[j] += sum_b size of member j's component unless covered.
 __global__ void k_refresh_gather(const uint32_t* __restrict__ parent, const uint64_t* __restrict__ word,
                                  uint32_t n, uint32_t nb, const uint32_t* __restrict__ batch,
@@ -791,5 +809,27 @@ int im_refresh_eval(im_ctx* c, const uint32_t* d_batch, const unsigned int* d_ba
             IM_LAUNCH(c, K_REFRESH_GATHER, k_add_u64, grid_for(n, T, 152u * 8u), T, 0, d_fresh,
                       (const unsigned long long*)c->lane[1].fresh, (uint64_t)0, d_batch_n);
     }
+    return rc;
+}
+
+// Monte-Carlo influence of the seeds d_seeds[0..k): simulation r is the live-edge world of
+// sketch index r under the edge hash of `mc_seed` (the sketches' hash reading with another
+// seed) and the context's probabilities; *d_total += sum_r |union of the seeds' components|.
+// Runs batch by batch on lane 0 with the build's scratch.
+int im_mc_run(im_ctx* c, const uint32_t* d_seeds, uint32_t k, uint32_t sims, uint64_t mc_seed,
+              unsigned long long* d_total) {
+    const Sampler saved = c->smp;
+    c->smp.salt = mix64(mc_seed + kGamma);
+    c->cur = c->stream;
+    int rc = IM_OK;
+    for (uint32_t r0 = 0; r0 < sims && !rc; r0 += c->batch_used) {
+        const uint32_t nb = sims - r0 < c->batch_used ? sims - r0 : c->batch_used;
+        im_ctx::Lane& L = c->lane[0];
+        rc = batch_components(c, L, r0, nb, 2);
+        if (!rc && k > 0)
+            IM_LAUNCH(c, K_COVER_ROOTS, k_mc_cover, grid_for((uint64_t)nb * k, 256, 152u * 4u), 256, 0, L.parent,
+                      L.word, c->n, nb, d_seeds, k, d_total);
+    }
+    c->smp = saved;
     return rc;
 }

@@ -512,3 +512,51 @@ def test_hubs_change_no_value(hubs, model, threshold):
         ctx.reset_selection()
         seeds2, gains2 = ctx.select_seeds(k)
         assert np.array_equal(seeds2, o_seeds) and np.array_equal(gains2, o_gains)
+
+
+# ---- Monte-Carlo influence evaluator (the paper's quality measure) ---------------------------
+
+@pytest.mark.parametrize("alpha", [1.0, 0.1])
+@pytest.mark.parametrize("model", ["uniform", "wic", "u13"])
+def test_mc_spread_matches_the_oracle(model, alpha):
+    """Sum over simulations of the vertices reachable from the seeds = the oracle's spread over
+    the live-edge worlds of the simulation hash seed; ragged simulation counts, duplicates,
+    the empty set; the build's own seed gives back the sketches' spread; the sketches are
+    untouched (the selection continues as the oracle's)."""
+    n, u, v = graphgen.chung_lu(20000, 100000, 2.1, 2000.0, 5)
+    G = oracle.Graph(n, u, v)
+    R, seed, k, p = 64, 42, 12, 0.03
+    mode = oracle.MODE_HASH
+    if model == "wic":
+        G.set_wic()
+        mode = oracle.MODE_EDGE
+    elif model == "u13":
+        parr = np.random.default_rng(5).uniform(0.1, 0.3, len(u))
+        G.set_probs(parr)
+        mode = oracle.MODE_EDGE
+    L = G.labels(seed, p, R, mode=mode)
+    o_seeds, o_gains = oracle.greedy(L, k)
+    with im.IMContext(n, u, v) as ctx:
+        with pytest.raises(im.IMError) as e:
+            ctx.mc_spread([0], 4, 1)
+        assert e.value.code == im.IM_ESTATE
+        if model == "wic":
+            ctx.set_edge_probs(im.IM_PROBS_WIC)
+        elif model == "u13":
+            ctx.set_edge_probs(im.IM_PROBS_ARRAY, parr)
+        ctx.build_sketches(R, seed, p, alpha)
+        seeds, gains = ctx.select_seeds(6)
+        for sims, mc_seed in ((1, 7), (37, 7), (300, 11)):
+            Lm = G.labels(mc_seed, p, sims, mode=mode)
+            assert ctx.mc_spread(seeds, sims, mc_seed) == oracle.spread(Lm, seeds), (sims, mc_seed)
+        L37 = G.labels(7, p, 37, mode=mode)
+        dup = np.concatenate([seeds[:3], seeds[:3], [int(seeds[0])]])
+        assert ctx.mc_spread(dup, 37, 7) == oracle.spread(L37, seeds[:3])
+        assert ctx.mc_spread(np.array([], np.uint32), 37, 7) == 0
+        assert ctx.mc_spread(seeds, 0, 7) == 0
+        assert ctx.mc_spread(seeds, R, seed) == ctx.spread(seeds)
+        with pytest.raises(im.IMError) as e:
+            ctx.mc_spread([n], 4, 1)
+        assert e.value.code == im.IM_EINVAL
+        seeds, gains = ctx.select_seeds(k)   # continues after the evaluations
+        assert np.array_equal(seeds, o_seeds) and np.array_equal(gains, o_gains)

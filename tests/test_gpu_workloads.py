@@ -2,7 +2,8 @@
 
 * Chung-Lu n=10^6, m=10^7, p=0.02, R=256, alpha=0.1, k=100 (the bench workload): every output
   is compared with the oracle bit for bit -- initial gains, centers, the complete compact
-  sketches, the 100 seeds and their gains, the spread, and labels of sampled sketches.
+  sketches, the 100 seeds and their gains, the spread, labels of sampled sketches, and the
+  Monte-Carlo influence of the seeds over 40 simulations.
 * R-MAT scale 24, 2^28 edges, p=0.01, R=256, alpha=0.05, k=200: the oracle recomputes two
   sketches in full (labels, compact columns) and the centers; the rest is checked through
   properties that hold at any size (gain sums equal sums of squared component sizes over the
@@ -42,6 +43,7 @@ def test_chunglu_1M_full_parity():
         seeds, sgains = ctx.select_seeds(k)
         spread = ctx.spread(seeds)
         labels = {r: ctx.labels(r) for r in (0, 77, 255)}
+        mc = ctx.mc_spread(seeds, 40, 9001)   # 40 simulations of an independent hash seed
     G = oracle.Graph(n, u, v)
     L = G.labels(seed, p, R)
     for r, got in labels.items():
@@ -54,6 +56,7 @@ def test_chunglu_1M_full_parity():
     o_seeds, o_gains = oracle.greedy(L, k, variant=1)
     assert np.array_equal(seeds, o_seeds) and np.array_equal(sgains, o_gains)
     assert spread == oracle.spread(L, seeds) == int(o_gains.sum())
+    assert mc == oracle.spread(G.labels(9001, p, 40), seeds)
 
 
 @pytest.mark.skipif(os.environ.get("IM_SKIP_RMAT") == "1", reason="R-MAT scale 24 disabled")
