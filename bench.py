@@ -418,6 +418,42 @@ def run_ours(args, n, u, v, prm):
     return 0
 
 
+def run_c4(args):
+    """The batched workload: 64 independent Chung-Lu instances (graphgen.c4_instances), run by
+    im_run_batch with `--workers` contexts side by side, against the same instances one at a
+    time (one worker).  Outputs must be identical; value = all instances' edge-sketch pairs
+    per second of the batched run (host clock: several streams; h2d graph uploads included)."""
+    import torch
+    import paper_2311_07554_gb300 as im
+
+    torch.cuda.set_device(0)
+    inst = graphgen.c4_instances(64)
+    pairs = sum(len(d["u"]) * d["R"] for d in inst)
+
+    def timed(workers):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = im.im_run_batch(inst, workers=workers)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, res
+
+    for _ in range(max(1, args.warmup)):
+        timed(args.workers)
+    seq_t, seq = min((timed(1) for _ in range(max(1, args.steps))), key=lambda x: x[0])
+    bat_t, bat = min((timed(args.workers) for _ in range(max(1, args.steps))), key=lambda x: x[0])
+    same = all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[2] == b[2] for a, b in zip(seq, bat))
+    line = {"metric": METRIC, "value": pairs / bat_t, "unit": "pairs/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": bat_t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "c4_chunglu_x64", "instances": len(inst), "workers": args.workers,
+                       "edges": int(sum(len(d["u"]) for d in inst)), "pairs": int(pairs),
+                       "alpha": 1.0, "parallelism": "replicas1"},
+            "sequential_ms": seq_t * 1e3, "speedup_vs_sequential": seq_t / bat_t, "identical": bool(same),
+            "timing": "best of --steps runs, host clock around the whole batch"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -431,7 +467,11 @@ def main():
     ap.add_argument("--mc-sims", type=int, default=20000,
                     help="Monte-Carlo simulations to evaluate the selected seeds with, after the timed region (0: none)")
     ap.add_argument("--alpha", type=float, default=None, help="center fraction (default: the workload's)")
+    ap.add_argument("--c4", action="store_true", help="the batched workload: 64 instances side by side")
+    ap.add_argument("--workers", type=int, default=4, help="contexts side by side for --c4")
     args = ap.parse_args()
+    if args.c4:
+        return run_c4(args)
     n, u, v, prm = graphgen.workload(args.workload)
     prm["name"] = args.workload
     prm["probs"] = args.probs

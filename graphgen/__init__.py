@@ -132,6 +132,28 @@ WORKLOADS = {
 }
 
 
+def c4_instances(count: int = 64, first_seed: int = 1000, n_range=(1e4, 2e6)):
+    """The batched workload: `count` independent Chung-Lu instances.  Instance i takes the seed
+    first_seed + i for its parameter draws and its graph: n log-uniform in n_range, average
+    degree U(4, 32) (m = n deg / 2), exponent 2.1, maximum expected degree min(50,000, n/4),
+    p from {.01, .02, .05, .1}, R from {64, 128, 256}, k from {10, 50, 100}; every vertex a
+    center (alpha = 1); the hash seed is the instance seed."""
+    out = []
+    lo, hi = np.log(n_range[0]), np.log(n_range[1])
+    for i in range(count):
+        s = first_seed + i
+        rng = np.random.default_rng(s)
+        n = int(round(float(np.exp(rng.uniform(lo, hi)))))
+        deg = float(rng.uniform(4.0, 32.0))
+        m = int(round(n * deg / 2))
+        p = float(rng.choice([0.01, 0.02, 0.05, 0.1]))
+        R = int(rng.choice([64, 128, 256]))
+        k = int(rng.choice([10, 50, 100]))
+        n_, u, v = chung_lu(n, m, 2.1, min(50_000.0, n / 4), s)
+        out.append(dict(n=n_, u=u, v=v, p=p, R=R, k=min(k, n_), seed=s, alpha=1.0))
+    return out
+
+
 def workload(name: str):
     """Return (n, u, v, params) for a named workload."""
     w = WORKLOADS[name]

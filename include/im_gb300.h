@@ -276,6 +276,40 @@ int im_set_seed_speculation(im_ctx* ctx, uint32_t candidates);
  */
 int im_mc_spread(im_ctx* ctx, const uint32_t* seeds, uint32_t k, uint32_t sims, uint64_t mc_seed, uint64_t* out);
 
+/*
+ * im_run_batch -- many independent instances on the current device: for each, the whole of
+ * Alg. 1 (im_create / im_load_graph, im_build_sketches, im_select_seeds, im_spread), with
+ * results identical to running the instances one by one.  `workers` host threads each own a
+ * context with its own stream and take the next instance (largest m R + n R first), so the
+ * instances' kernels overlap on the GPU; a context keeps its buffers across the instances it
+ * runs while they fit (no cudaMalloc / cudaFree, which would synchronise the device).
+ *   inst[i].n, m, u, v      the graph: HOST edge lists of m entries (as im_create); not modified
+ *   inst[i].R, seed, p, alpha, k   as im_build_sketches and im_select_seeds (the probability
+ *                            model is one p per instance)
+ *   inst[i].seeds_out, gains_out   HOST, k entries each; spread_out: HOST, 1 entry
+ *   inst[i].status           out: IM_OK or the error of that instance's first failing call
+ * Returns IM_OK if every instance succeeded, else the first failing instance's status (in
+ * input order); IM_EINVAL if inst is NULL, workers is 0 or an output pointer is NULL.
+ * Blocks until every instance is done.
+ */
+typedef struct {
+    uint32_t n;
+    uint64_t m;
+    const uint32_t* u;
+    const uint32_t* v;
+    uint32_t R;
+    uint32_t k;
+    uint64_t seed;
+    double p;
+    double alpha;
+    uint32_t* seeds_out;
+    uint64_t* gains_out;
+    uint64_t* spread_out;
+    int status;
+} im_instance;
+
+int im_run_batch(im_instance* inst, uint32_t count, uint32_t workers);
+
 /* Tuning: hubs.  GetCenter (Alg. 3) from a vertex whose component reaches a high-degree
  * non-center tests that vertex's whole adjacency list, in every sketch where it is reached.
  * With hubs, up to `cap` non-centers of degree >= `min_degree` (the largest degrees, ties to

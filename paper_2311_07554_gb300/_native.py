@@ -38,6 +38,15 @@ class im_stats(ctypes.Structure):
                 ("hubs", ctypes.c_uint64)]
 
 
+class im_instance(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32), ("m", ctypes.c_uint64),
+                ("u", ctypes.POINTER(ctypes.c_uint32)), ("v", ctypes.POINTER(ctypes.c_uint32)),
+                ("R", ctypes.c_uint32), ("k", ctypes.c_uint32), ("seed", ctypes.c_uint64),
+                ("p", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("seeds_out", ctypes.POINTER(ctypes.c_uint32)), ("gains_out", ctypes.POINTER(ctypes.c_uint64)),
+                ("spread_out", ctypes.POINTER(ctypes.c_uint64)), ("status", ctypes.c_int)]
+
+
 def lib():
     """Load the library (raises if it is missing: there is no fallback path)."""
     global _lib
@@ -75,6 +84,7 @@ def lib():
         "im_hash_peak": ([u32, c.POINTER(dbl)], i32),
         "im_set_seed_speculation": ([vp, u32], i32),
         "im_set_hubs": ([vp, u32, u32], i32),
+        "im_run_batch": ([c.POINTER(im_instance), u32, u32], i32),
         "im_mc_spread": ([vp, ctypes.POINTER(ctypes.c_uint32), u32, u32, u64, ctypes.POINTER(ctypes.c_uint64)], i32),
         "im_stream": ([vp], vp),
         "im_sketch_static": ([u32, u64, vp, vp, u64, dbl, u32, vp, vp, vp], i32),
@@ -268,6 +278,34 @@ def im_mc_spread(ctx, seeds, sims: int, mc_seed: int) -> int:
     _check(ctx, lib().im_mc_spread(ctx, s.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), len(s), sims, mc_seed,
                                    ctypes.byref(out)))
     return int(out.value)
+
+
+def im_run_batch(instances, workers: int = 8):
+    """Run independent instances concurrently (one context and stream per worker thread).
+
+    `instances`: dicts with n, u, v (host uint32 arrays), R, k, seed, p, alpha.  Returns a list of
+    (seeds, gains, spread) in input order; raises IMError with the first failing status."""
+    keep = []
+    arr = (im_instance * len(instances))()
+    outs = []
+    for i, d in enumerate(instances):
+        u = np.ascontiguousarray(np.asarray(d["u"], dtype=np.uint32))
+        v = np.ascontiguousarray(np.asarray(d["v"], dtype=np.uint32))
+        k = int(d["k"])
+        sd = np.zeros(k, np.uint32)
+        gn = np.zeros(k, np.uint64)
+        sp = np.zeros(1, np.uint64)
+        keep += [u, v]
+        outs.append((sd, gn, sp))
+        P32, P64 = ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint64)
+        arr[i] = im_instance(int(d["n"]), len(u), u.ctypes.data_as(P32), v.ctypes.data_as(P32), int(d["R"]), k,
+                             int(d["seed"]), float(d["p"]), float(d["alpha"]), sd.ctypes.data_as(P32),
+                             gn.ctypes.data_as(P64), sp.ctypes.data_as(P64), 0)
+    rc = lib().im_run_batch(arr, len(instances), workers)
+    if rc != IM_OK:
+        bad = next(i for i in range(len(instances)) if arr[i].status != IM_OK)
+        raise IMError(rc, f"instance {bad} failed with status {arr[bad].status}")
+    return [(sd, gn, int(sp[0])) for sd, gn, sp in outs]
 
 
 IM_HUBS_AUTO = 0xFFFFFFFF

@@ -67,7 +67,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     newest = max(o.stat().st_mtime for o in objs)
     if force or procs or not LIB.exists() or LIB.stat().st_mtime < newest:
         tmp = LIB.with_suffix(f".so.tmp{os.getpid()}")
-        cmd = [nvcc(), *ARCH, "-shared", "-o", str(tmp), *map(str, objs)]
+        cmd = [nvcc(), *ARCH, "-shared", "-o", str(tmp), *map(str, objs), "-lpthread"]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         subprocess.check_call(cmd)

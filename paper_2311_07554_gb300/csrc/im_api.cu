@@ -63,6 +63,9 @@ void free_sketch_state(im_ctx* c) {
     c->fb_slots = 0;
     c->fb_cap = 0;
     c->compact_cap = 0;
+    c->cap_n = 0;
+    c->cap_R = 0;
+    c->cap_nspec = 0;
     c->built = false;
 }
 
@@ -143,12 +146,34 @@ static int load_graph(im_ctx* c, const uint32_t* u, const uint32_t* v, int ptr_k
     if (ptr_kind == IM_PTR_HOST && m > 0) {
         if (c->upload_cap < m) {
             dfree(c->d_upload);
+            if (c->h_upload) cudaFreeHost(c->h_upload);
+            c->h_upload = nullptr;
             c->upload_cap = 0;
-            if (!dalloc(c->d_upload, 2 * m)) return im_fail(c, IM_ENOMEM, "edge upload");
-            c->upload_cap = m;
+            const uint64_t cap = std::max(m, c->res_m);
+            if (!dalloc(c->d_upload, 2 * cap)) return im_fail(c, IM_ENOMEM, "edge upload");
+            c->upload_cap = cap;
         }
-        IM_CUDA(c, cudaMemcpyAsync(c->d_upload, u, m * sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream));
-        IM_CUDA(c, cudaMemcpyAsync(c->d_upload + m, v, m * sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream));
+        // pageable lists go through a pinned buffer, so that the copy engine reads them
+        // directly and contexts on other threads do not queue behind the driver's staging
+        cudaPointerAttributes at{};
+        const bool pinned = cudaPointerGetAttributes(&at, u) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+                            cudaPointerGetAttributes(&at, v) == cudaSuccess && at.type == cudaMemoryTypeHost;
+        cudaGetLastError();
+        const uint32_t *su = u, *sv = v;
+        if (!pinned) {
+            if (!c->h_upload && cudaMallocHost(&c->h_upload, 2 * c->upload_cap * sizeof(uint32_t)) != cudaSuccess) {
+                c->h_upload = nullptr;
+                cudaGetLastError();
+            }
+            if (c->h_upload) {
+                memcpy(c->h_upload, u, m * sizeof(uint32_t));
+                memcpy(c->h_upload + m, v, m * sizeof(uint32_t));
+                su = c->h_upload;
+                sv = c->h_upload + m;
+            }
+        }
+        IM_CUDA(c, cudaMemcpyAsync(c->d_upload, su, m * sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream));
+        IM_CUDA(c, cudaMemcpyAsync(c->d_upload + m, sv, m * sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream));
         pu = c->d_upload;
         pv = c->d_upload + m;
     }
@@ -162,6 +187,13 @@ extern "C" {
 
 int im_create(im_ctx** out, uint32_t n, uint64_t m, const uint32_t* u, const uint32_t* v,
               int ptr_kind, void* stream) {
+    return im_create_reserved(out, n, m, u, v, ptr_kind, stream, nullptr);
+}
+
+}  // extern "C"
+
+int im_create_reserved(im_ctx** out, uint32_t n, uint64_t m, const uint32_t* u, const uint32_t* v, int ptr_kind,
+                       void* stream, const ImReserve* res) {
     if (!out) return im_fail(nullptr, IM_EINVAL, "out is NULL");
     *out = nullptr;
     if (n == 0 || n >= 0x80000000u) return im_fail(nullptr, IM_EINVAL, "n must be in [1, 2^31)");
@@ -173,6 +205,17 @@ int im_create(im_ctx** out, uint32_t n, uint64_t m, const uint32_t* u, const uin
     if (!c) return im_fail(nullptr, IM_ENOMEM, "context");
     c->n = n;
     c->m = m;
+    if (res) {
+        c->res_n = res->n;
+        c->res_R = res->R;
+        c->res_m = res->m;
+        c->res_nc = res->nc;
+        // live-pair records of a batch of 32 sketches at the largest p m (as im_build_sketches)
+        const double ex = res->pm * 32.0;
+        double cap = ex > 0 ? 1.3 * ex + 16.0 * std::sqrt(ex) + 65536.0 : 0.0;
+        if (cap > (double)(1ull << 28)) cap = (double)(1ull << 28);
+        c->res_live = (uint64_t)cap;
+    }
     cudaGetDevice(&c->device);
     if (stream) {
         c->stream = (cudaStream_t)stream;
@@ -224,6 +267,8 @@ int im_create(im_ctx** out, uint32_t n, uint64_t m, const uint32_t* u, const uin
     return IM_OK;
 }
 
+extern "C" {
+
 int im_set_sketch_batch(im_ctx* c, uint32_t batch) {
     if (!c) return IM_EINVAL;
     if (batch != 0 && (batch > 32 || (batch & (batch - 1)) != 0))
@@ -273,8 +318,9 @@ int im_load_graph(im_ctx* c, uint32_t n, uint64_t m, const uint32_t* u, const ui
     if (ptr_kind != IM_PTR_HOST && ptr_kind != IM_PTR_DEVICE) return im_fail(c, IM_EINVAL, "bad ptr_kind");
     if (m > 0 && (!u || !v)) return im_fail(c, IM_EINVAL, "edge arrays are NULL");
     IM_CUDA(c, cudaStreamSynchronize(c->stream));
-    if (n != c->n) free_sketch_state(c);   // every per-vertex buffer changes size
-    if (m != c->m) { dfree(c->d_edgeT); dfree(c->d_arcT); }
+    if (n > c->cap_n) free_sketch_state(c);   // the per-vertex buffers are too small
+    if (n != c->n || m != c->m) im_select_graph_free(c);   // it captured n and m
+    if (m > c->edgeT_cap) { dfree(c->d_edgeT); dfree(c->d_arcT); c->edgeT_cap = 0; }
     c->prob_model = IM_PROBS_UNIFORM;      // probabilities belong to the old edge list
     c->built = false;
     c->seeds.clear();
@@ -375,15 +421,19 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
     const size_t nc = ((size_t)rho + hub_rows) * R;
     // candidate first seeds need the batches in order (they are chosen after the first one)
     const uint32_t nspec = c->lanes == 1 ? std::min<uint32_t>(c->spec_req, n) : 0u;
-    // A build with the same shapes reuses the device buffers (no cudaFree / cudaMalloc, which
-    // synchronise the device) and, if the sampler is unchanged too, the selection graph.
-    const bool same_layout = c->batch_alloc == B && c->R == R && c->compact_cap == nc &&
-                             c->all_centers == all && c->live_cap == live_cap && c->spec_count == nspec;
-    if (!same_layout) {
+    // A build that fits the device buffers reuses them (cudaMalloc / cudaFree synchronise the
+    // device, stalling every stream, other contexts' included); the selection graph, which
+    // captured the shapes and the sampler, is kept only while both are unchanged.
+    const bool fits = c->batch_alloc > 0 && n <= c->cap_n && B <= c->batch_alloc && R <= c->cap_R &&
+                      nc <= c->compact_cap && live_cap <= c->live_cap && nspec <= c->cap_nspec &&
+                      (all || c->d_cidx != nullptr);
+    const bool same_shape = c->R == R && c->rho == rho && c->hub_rows == hub_rows && c->batch_used == B &&
+                            c->all_centers == all && c->spec_count == nspec;
+    if (!fits) {
         free_sketch_state(c);
-    } else if (c->smp.salt != smp.salt || c->smp.T != smp.T || c->smp.all_live != smp.all_live ||
+    } else if (!same_shape || c->smp.salt != smp.salt || c->smp.T != smp.T || c->smp.all_live != smp.all_live ||
                c->smp.eT != smp.eT || c->smp.aT != smp.aT) {
-        im_select_graph_free(c);   // the captured kernels carry the sampler
+        im_select_graph_free(c);   // the captured kernels carry the shapes and the sampler
     }
     c->built = false;
     c->R = R; c->seed = seed; c->p = p; c->alpha = alpha; c->rho = rho; c->all_centers = all;
@@ -392,29 +442,36 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
     c->smp = smp;
     c->batch_used = B;
     c->spec_count = nspec;
-    if (!same_layout) {
-        bool ok = dalloc(c->d_gain0, n) && dalloc(c->d_key, n) && dalloc(c->d_stamp, n) &&
-                  dalloc(c->d_seedflag, n) && dalloc(c->d_batch, n) && dalloc(c->d_fresh, n) &&
-                  dalloc(c->d_seed_list, n) && dalloc(c->d_labcache, (size_t)kLabSlots * R) &&
-                  dalloc(c->d_gain_list, n) && dalloc(c->d_round_evals, n) &&
-                  dalloc(c->d_label, nc) && dalloc(c->d_size, nc) &&
-                  dalloc(c->lane[0].parent, (size_t)B * n) && dalloc(c->lane[0].word, (size_t)B * n) &&
-                  dalloc(c->lane[1].parent, (size_t)B * n) && dalloc(c->lane[1].word, (size_t)B * n) &&
-                  dalloc(c->lane[1].gain, n) && dalloc(c->lane[1].fresh, n);
-        if (ok && nspec) ok = dalloc(c->lane[0].spec_ov, (size_t)nspec * n);
-        if (ok && live_cap) {
-            c->live_cap = live_cap;
+    if (!fits) {
+        // at least the context's reserve (im_create_reserved), so that later builds fit
+        const uint32_t na = std::max(n, c->res_n), Ra = std::max(R, c->res_R);
+        const size_t nca = std::max<size_t>(nc, c->res_nc);
+        const uint64_t livea = std::max(live_cap, c->res_live);
+        const uint32_t nsa = std::min(std::max(nspec, c->res_n ? std::min<uint32_t>(c->spec_req, kSpecMax) : 0u),
+                                      kSpecMax);
+        const bool compact = !all || c->res_n > 0;   // a reserved context may serve compact builds
+        bool ok = dalloc(c->d_gain0, na) && dalloc(c->d_key, na) && dalloc(c->d_stamp, na) &&
+                  dalloc(c->d_seedflag, na) && dalloc(c->d_batch, na) && dalloc(c->d_fresh, na) &&
+                  dalloc(c->d_seed_list, na) && dalloc(c->d_labcache, (size_t)kLabSlots * Ra) &&
+                  dalloc(c->d_gain_list, na) && dalloc(c->d_round_evals, na) &&
+                  dalloc(c->d_label, nca) && dalloc(c->d_size, nca) &&
+                  dalloc(c->lane[0].parent, (size_t)B * na) && dalloc(c->lane[0].word, (size_t)B * na) &&
+                  dalloc(c->lane[1].parent, (size_t)B * na) && dalloc(c->lane[1].word, (size_t)B * na) &&
+                  dalloc(c->lane[1].gain, na) && dalloc(c->lane[1].fresh, na);
+        if (ok && nsa) ok = dalloc(c->lane[0].spec_ov, (size_t)nsa * na);
+        if (ok && livea) {
+            c->live_cap = livea;
             ok = dalloc(c->lane[0].live, c->live_cap) && dalloc(c->lane[0].live_n, 1) &&
                  dalloc(c->lane[1].live, c->live_cap) && dalloc(c->lane[1].live_n, 1);
         }
-        if (ok && !all) {
-            const size_t nw = ((size_t)n + 31) / 32;
+        if (ok && compact) {
+            const size_t nw = ((size_t)na + 31) / 32;
             c->fb_slots = 8;
             c->fb_cap = 1u << 22;
-            ok = dalloc(c->d_cbits, nw) && dalloc(c->d_cidx, n) && dalloc(c->d_centers, rho) &&
-                 dalloc(c->d_fb_queue, (size_t)c->fb_slots * n) &&
+            ok = dalloc(c->d_cbits, nw) && dalloc(c->d_cidx, na) && dalloc(c->d_centers, na) &&
+                 dalloc(c->d_fb_queue, (size_t)c->fb_slots * na) &&
                  dalloc(c->d_fb_bits, (size_t)c->fb_slots * nw) && dalloc(c->d_fb_tasks, c->fb_cap) &&
-                 dalloc(c->d_cflags, n) && dalloc(c->d_cpos, (size_t)n + 1) &&
+                 dalloc(c->d_cflags, na) && dalloc(c->d_cpos, (size_t)na + 1) &&
                  dalloc(c->d_csel, kCenterSelBytes);
             if (ok) ok = cudaMemsetAsync(c->d_fb_bits, 0, (size_t)c->fb_slots * nw * 4, c->stream) == cudaSuccess;
         }
@@ -423,7 +480,10 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
             return im_fail(c, IM_ENOMEM, "sketch memory");
         }
         c->batch_alloc = B;
-        c->compact_cap = nc;
+        c->compact_cap = nca;
+        c->cap_n = na;
+        c->cap_R = Ra;
+        c->cap_nspec = nsa;
     }
     c->refresh_min = c->refresh_req ? c->refresh_req : std::max<uint64_t>(16384, n / 4);
     int rc = IM_OK;
@@ -442,7 +502,7 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
     }
     if (!rc) rc = im_arc_keys(c, smp.salt);
     if (!rc) rc = im_sketch_batches(c);
-    if (!rc) rc = im_selection_init(c);
+    if (!rc) rc = im_selection_init(c, true);   // the build wrote every size entry
     if (!rc) {
         cudaError_t e = cudaMemcpyAsync(c->h_live + 1, c->d_live_total, sizeof(unsigned long long),
                                         cudaMemcpyDeviceToHost, c->stream);
@@ -473,7 +533,7 @@ int im_select_seeds(im_ctx* c, uint32_t k, uint32_t* seeds_out, uint64_t* gains_
 int im_reset_selection(im_ctx* c) {
     if (!c) return IM_EINVAL;
     if (!c->built) return im_fail(c, IM_ESTATE, "im_build_sketches has not run");
-    int rc = im_selection_init(c);
+    int rc = im_selection_init(c, false);
     if (rc) return rc;
     IM_CUDA(c, cudaStreamSynchronize(c->stream));
     return IM_OK;
@@ -672,6 +732,7 @@ void im_destroy(im_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_sketch_state(c);
     dfree(c->d_edges); dfree(c->d_off); dfree(c->d_arcs); dfree(c->d_arc_cur); dfree(c->d_upload);
+    if (c->h_upload) cudaFreeHost(c->h_upload);
     dfree(c->d_edgeT); dfree(c->d_arcT);
     dfree(c->d_spread_pairs); dfree(c->d_spread_seeds); dfree(c->d_spread_total); dfree(c->d_live_total);
     if (c->d_sel) cudaFree(c->d_sel);

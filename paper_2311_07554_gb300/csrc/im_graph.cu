@@ -251,24 +251,28 @@ int im_graph_build(im_ctx* c, const uint32_t* d_u, const uint32_t* d_v) {
     const uint64_t m = c->m;
     uint64_t m_pad = (m + 1) & ~1ull;
     if (m_pad == 0) m_pad = 2;
-    if (!(c->d_edges && c->graph_n_alloc == n && c->graph_m_alloc == m)) {
-        // new sizes: new buffers (a captured selection graph points at the old ones)
+    if (!(c->d_edges && n <= c->graph_n_alloc && m <= c->graph_m_alloc)) {
+        // larger sizes: new buffers (a captured selection graph points at the old ones), at
+        // least the context's reserve
         im_select_graph_free(c);
         cudaFree(c->d_edges); cudaFree(c->d_off); cudaFree(c->d_arcs); cudaFree(c->d_arc_cur);
         c->d_edges = nullptr; c->d_off = nullptr; c->d_arcs = nullptr; c->d_arc_cur = nullptr;
         c->graph_n_alloc = 0;
         c->graph_m_alloc = 0;
-        if (cudaMalloc(&c->d_edges, m_pad * sizeof(uint2)) != cudaSuccess)
+        const uint32_t na = n > c->res_n ? n : c->res_n;
+        const uint64_t ma = m > c->res_m ? m : c->res_m;
+        const uint64_t ma_pad = ((ma + 1) & ~1ull) + 2;
+        if (cudaMalloc(&c->d_edges, ma_pad * sizeof(uint2)) != cudaSuccess)
             return im_fail(c, IM_ENOMEM, "edge list");
-        if (cudaMalloc(&c->d_off, ((size_t)n + 1) * sizeof(uint64_t)) != cudaSuccess)
+        if (cudaMalloc(&c->d_off, ((size_t)na + 1) * sizeof(uint64_t)) != cudaSuccess)
             return im_fail(c, IM_ENOMEM, "csr offsets");
-        if (cudaMalloc(&c->d_arcs, (2 * m + 2) * sizeof(uint4)) != cudaSuccess)
+        if (cudaMalloc(&c->d_arcs, (2 * ma + 2) * sizeof(uint4)) != cudaSuccess)
             return im_fail(c, IM_ENOMEM, "csr arcs");
         // two cursors per vertex for the arc fill; the first n + 5 words serve as degree scratch
-        if (cudaMalloc(&c->d_arc_cur, (2 * (size_t)n + 8) * sizeof(uint32_t)) != cudaSuccess)
+        if (cudaMalloc(&c->d_arc_cur, (2 * (size_t)na + 8) * sizeof(uint32_t)) != cudaSuccess)
             return im_fail(c, IM_ENOMEM, "arc cursors");
-        c->graph_n_alloc = n;
-        c->graph_m_alloc = m;
+        c->graph_n_alloc = na;
+        c->graph_m_alloc = ma;
     }
     IM_CUDA(c, cudaMemsetAsync(c->d_edges, 0, m_pad * sizeof(uint2), c->stream));
     uint32_t* deg = c->d_arc_cur;
@@ -310,6 +314,7 @@ int im_edge_probs(im_ctx* c, int model, const double* d_p) {
         if (cudaMalloc(&c->d_edgeT, (m_pad + 2) * sizeof(uint64_t)) != cudaSuccess ||
             cudaMalloc(&c->d_arcT, (2 * m + 2) * sizeof(uint64_t)) != cudaSuccess)
             return im_fail(c, IM_ENOMEM, "edge thresholds");
+        c->edgeT_cap = m;
     }
     IM_CUDA(c, cudaMemsetAsync(c->d_edgeT, 0, (m_pad + 2) * sizeof(uint64_t), c->stream));
     if (m > 0) {

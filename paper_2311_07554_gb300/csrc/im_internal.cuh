@@ -262,8 +262,10 @@ struct im_ctx {
     int prob_model = 0;              // IM_PROBS_*
     uint64_t* d_edgeT = nullptr;     // threshold words by edge (input order, padded to even)
     uint64_t* d_arcT = nullptr;      // the same by arc, written by every arc fill
+    uint64_t edgeT_cap = 0;          // edges d_edgeT / d_arcT were allocated for
     double mean_p = 0.0;
     uint32_t* d_upload = nullptr;    // staging for host edge lists (2 x upload_cap ids)
+    uint32_t* h_upload = nullptr;    // pinned staging for pageable host edge lists (same size)
     uint64_t upload_cap = 0;   // 2n arc-fill cursors (centers from the front, others from the back)
     uint64_t arc_salt = 0;
     bool arc_keys_valid = false;
@@ -342,7 +344,13 @@ struct im_ctx {
     cudaStream_t cur = nullptr;                  // stream the next launch goes to
     uint32_t lanes = 1;                          // 1: batches in order on the context stream
     uint32_t batch_req = 0, batch_used = 0, batch_alloc = 0;
-    uint64_t live_cap = 0;
+    uint64_t live_cap = 0;           // live-pair records allocated per lane
+    // capacities of the sketch buffers (a later build that fits reuses them)
+    uint32_t cap_n = 0, cap_R = 0, cap_nspec = 0;
+    // sizes to allocate at least (im_create_reserved): a context that will serve several
+    // instances allocates once, for the largest of each dimension
+    uint32_t res_n = 0, res_R = 0;
+    uint64_t res_m = 0, res_nc = 0, res_live = 0;
     unsigned long long* d_live_total = nullptr;  // live (edge, sketch) pairs unioned, cumulative
 
     // BFS fallback scratch
@@ -399,6 +407,15 @@ int im_scan_u32_to_u64(im_ctx* c, const uint32_t* d_in, uint64_t* d_out, uint64_
 // im_sketch.cu
 int im_select_centers(im_ctx* c, uint32_t* d_flags_tmp, uint64_t* d_scan_tmp);
 int im_select_hubs(im_ctx* c, uint32_t* d_flags_tmp, uint64_t* d_scan_tmp);
+// Minimum allocation sizes of a context that is to serve several instances.
+struct ImReserve {
+    uint32_t n, R;        // vertices, sketches
+    uint64_t m;           // edges
+    uint64_t nc;          // compact (and hub) label entries: rows x R
+    double pm;            // largest p m (live-pair records per sketch)
+};
+int im_create_reserved(im_ctx** out, uint32_t n, uint64_t m, const uint32_t* u, const uint32_t* v, int ptr_kind,
+                       void* stream, const ImReserve* res);
 int im_mc_run(im_ctx* c, const uint32_t* d_seeds, uint32_t k, uint32_t sims, uint64_t mc_seed,
               unsigned long long* d_total);
 int im_sketch_batches(im_ctx* c);
@@ -407,7 +424,7 @@ int im_labels_min(im_ctx* c, uint32_t r, uint32_t* d_out);
 int im_refresh_eval(im_ctx* c, const uint32_t* d_batch, const unsigned int* d_batch_n,
                     unsigned long long* d_fresh, const uint32_t* d_seeds, const unsigned int* d_nseeds);
 // im_select.cu
-int im_selection_init(im_ctx* c);
+int im_selection_init(im_ctx* c, bool fresh);
 int im_select_run(im_ctx* c, uint32_t k);   // rounds until k seeds are chosen
 void im_select_graph_free(im_ctx* c);
 int im_spread_run(im_ctx* c, uint32_t k, uint64_t* out);

@@ -1449,10 +1449,12 @@ unsigned search_grid(uint64_t tasks) {
 
 }  // namespace
 
-// Reset the selection state: keys from the initial gains, no seeds, no coverage.
-int im_selection_init(im_ctx* c) {
+// Reset the selection state: keys from the initial gains, no seeds, no coverage.  Right after
+// a build every size entry was just written without its covered bit (fresh = true), so only
+// a reset of an earlier selection clears the bits.
+int im_selection_init(im_ctx* c, bool fresh) {
     const unsigned T = 256;
-    const uint64_t nsize = ((uint64_t)c->rho + c->hub_rows) * c->R;   // compact and hub rows
+    const uint64_t nsize = fresh ? 0 : ((uint64_t)c->rho + c->hub_rows) * c->R;   // compact and hub rows
     IM_LAUNCH(c, K_INIT_KEYS, k_init_keys, grid_for(c->n > nsize ? c->n : nsize, T, 152u * 16u), T, 0,
               c->d_gain0, c->n, c->key_bits, c->d_key, c->d_stamp, c->d_seedflag, c->d_size, nsize);
     IM_CUDA(c, cudaMemsetAsync(c->d_sel, 0, sizeof(SelState), c->stream));

@@ -318,6 +318,90 @@ k_gain_compact(const uint32_t* __restrict__ parent, const uint64_t* __restrict__
     }
 }
 
+// The same when every vertex is a center (full labels): every vertex writes a row segment
+// [r0, r0 + nb) of labels and sizes, which one thread per vertex would write 4 bytes at a
+// time, R entries apart from its neighbours'.  A block takes tiles of 32 consecutive
+// vertices (lane = vertex); warp w reads sketches b = w, w + 8, ... of the batch (coalesced
+// parent loads), and the tile's labels and sizes are staged in shared memory, so that each
+// row segment is written by one warp in one coalesced store.
+constexpr int kGainWarps = 8;
+
+template <int kSpec>
+__global__ void __launch_bounds__(kGainWarps * 32)
+k_gain_full(const uint32_t* __restrict__ parent, const uint64_t* __restrict__ word, uint32_t n,
+            uint32_t nb, uint32_t r0, uint32_t R, uint64_t* __restrict__ gain, int first,
+            uint32_t* __restrict__ label, uint32_t* __restrict__ size, const uint32_t* __restrict__ spec_ids,
+            uint32_t nspec, uint64_t* __restrict__ spec_ov) {
+    constexpr int KS = kSpec > 0 ? kSpec : 1;
+    __shared__ uint32_t sroot[32][KS];
+    __shared__ uint32_t tl[32][33], ts[32][33];          // [sketch][vertex] of the tile
+    __shared__ uint32_t tci[32];                          // the tile's center indices
+    __shared__ unsigned long long tg[kGainWarps][32];     // per-warp partial gains
+    __shared__ unsigned long long tov[kSpec > 0 ? kGainWarps : 1][KS][32];
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (kSpec > 0) {
+        for (uint32_t i = threadIdx.x; i < nb * nspec; i += blockDim.x) {
+            const uint32_t bb = i / nspec, k = i % nspec;
+            sroot[bb][k] = parent[(size_t)bb * n + spec_ids[k]];
+        }
+        __syncthreads();
+    }
+    for (uint32_t v0 = blockIdx.x * 32u; v0 < n; v0 += gridDim.x * 32u) {   // uniform over the block
+        const uint32_t v = v0 + lane;
+        const bool valid = v < n;
+        const uint32_t ci = valid ? v : kNone;
+        unsigned long long g = 0;
+        unsigned long long ov[KS];
+#pragma unroll
+        for (int k = 0; k < KS; ++k) ov[k] = 0;
+        if (valid) {
+            for (uint32_t bb = warp; bb < nb; bb += kGainWarps) {
+                const uint32_t root = parent[(size_t)bb * n + v];
+                const uint64_t w = word[(size_t)bb * n + root];
+                const uint32_t c = (uint32_t)w;
+                g += c;
+#pragma unroll
+                for (int k = 0; k < kSpec; ++k)
+                    if ((uint32_t)k < nspec && root == sroot[bb][k]) ov[k] += c;
+                if (ci != kNone) {
+                    const uint32_t l = (uint32_t)(w >> 32);   // smallest center index of the component
+                    tl[bb][lane] = l;
+                    ts[bb][lane] = (l == ci) ? c : 0u;
+                }
+            }
+        }
+        tg[warp][lane] = g;
+#pragma unroll
+        for (int k = 0; k < kSpec; ++k) tov[kSpec > 0 ? warp : 0][k][lane] = ov[k];
+        if (warp == 0) tci[lane] = ci;
+        __syncthreads();
+        if (warp == 0 && valid) {
+            unsigned long long t = 0;
+#pragma unroll
+            for (int w = 0; w < kGainWarps; ++w) t += tg[w][lane];
+            gain[v] = first ? t : gain[v] + t;
+#pragma unroll
+            for (int k = 0; k < kSpec; ++k) {
+                if ((uint32_t)k >= nspec) continue;
+                unsigned long long o = 0;
+#pragma unroll
+                for (int w = 0; w < kGainWarps; ++w) o += tov[kSpec > 0 ? w : 0][k][lane];
+                if (o) spec_ov[(size_t)k * n + v] += o;
+            }
+        }
+        // rows: warp w writes the row segments of the tile's vertices w, w + 8, ...
+        for (uint32_t j = warp; j < 32; j += kGainWarps) {
+            const uint32_t cj = tci[j];
+            if (cj != kNone && lane < nb) {
+                const size_t o = (size_t)cj * R + r0 + lane;
+                label[o] = tl[lane][j];
+                size[o] = ts[lane][j];
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // The first batch's overlap sums, once the candidates are known (its forest is still there).
 __global__ void __launch_bounds__(256)
 k_spec_overlap(const uint32_t* __restrict__ parent, const uint64_t* __restrict__ word, uint32_t n,
@@ -720,9 +804,14 @@ int im_sketch_batches(im_ctx* c) {
         const int first = i < c->lanes ? 1 : 0;
         const uint32_t nspec = i ? c->spec_count : 0;   // candidates are known after batch 0
 #define IM_GAIN(ALL, K)                                                                             \
-    IM_LAUNCH(c, K_GAIN_COMPACT, (k_gain_compact<ALL, K>), grid_for(n, T, 152u * 16u), T, 0, L.parent, L.word, \
-              n, nb, r0, R, gain, first, c->d_cidx, c->d_label, c->d_size, c->d_spec_ids, nspec,        \
-              c->lane[0].spec_ov)
+    if (ALL)                                                                                        \
+        IM_LAUNCH(c, K_GAIN_COMPACT, (k_gain_full<K>), grid_for(n, 32, 152u * 8u), kGainWarps * 32, 0, L.parent, \
+                  L.word, n, nb, r0, R, gain, first, c->d_label, c->d_size, c->d_spec_ids, nspec,       \
+                  c->lane[0].spec_ov);                                                              \
+    else                                                                                            \
+        IM_LAUNCH(c, K_GAIN_COMPACT, (k_gain_compact<false, K>), grid_for(n, T, 152u * 16u), T, 0, L.parent,   \
+                  L.word, n, nb, r0, R, gain, first, c->d_cidx, c->d_label, c->d_size, c->d_spec_ids, nspec, \
+                  c->lane[0].spec_ov)
         if (c->all_centers) {
             if (nspec == 0) IM_GAIN(true, 0);
             else if (nspec <= 4) IM_GAIN(true, 4);

@@ -560,3 +560,56 @@ def test_mc_spread_matches_the_oracle(model, alpha):
         assert e.value.code == im.IM_EINVAL
         seeds, gains = ctx.select_seeds(k)   # continues after the evaluations
         assert np.array_equal(seeds, o_seeds) and np.array_equal(gains, o_gains)
+
+
+# ---- many instances at once (the batched workload) --------------------------------------------
+
+def _one_by_one(d):
+    with im.IMContext(d["n"], d["u"], d["v"]) as ctx:
+        ctx.build_sketches(d["R"], d["seed"], d["p"], d["alpha"])
+        seeds, gains = ctx.select_seeds(d["k"])
+        return seeds, gains, ctx.spread(seeds)
+
+
+def test_run_batch_matches_one_by_one_and_the_oracle():
+    """Instances of the batched workload's recipe (smaller n), run by 3 workers concurrently:
+    seeds, gains and spread equal those of separate contexts; the two smallest against the
+    oracle."""
+    inst = graphgen.c4_instances(8, first_seed=1000, n_range=(2e3, 3e4))
+    got = im.im_run_batch(inst, workers=3)
+    for d, (s, g, sp) in zip(inst, got):
+        s1, g1, sp1 = _one_by_one(d)
+        assert np.array_equal(s, s1) and np.array_equal(g, g1) and sp == sp1
+    for i in sorted(range(len(inst)), key=lambda i: inst[i]["n"])[:2]:
+        d = inst[i]
+        L = oracle.Graph(d["n"], d["u"], d["v"]).labels(d["seed"], d["p"], d["R"])
+        o_seeds, o_gains = oracle.greedy(L, d["k"])
+        assert np.array_equal(got[i][0], o_seeds) and np.array_equal(got[i][1], o_gains)
+        assert got[i][2] == oracle.spread(L, o_seeds)
+    # errors: a bad instance reports its own status, the others still run
+    bad = dict(inst[0])
+    bad["k"] = bad["n"] + 1
+    with pytest.raises(im.IMError):
+        im.im_run_batch([inst[1], bad], workers=2)
+
+
+def test_one_context_across_graph_sizes():
+    """A context that loads larger, smaller and mid-sized graphs in turn (its buffers reused
+    while they fit, the selection graph rebuilt) gives what fresh contexts give."""
+    graphs = [graphgen.chung_lu(30000, 150000, 2.1, 3000.0, 11), graphgen.erdos_renyi(5000, 20000, 12),
+              graphgen.chung_lu(20000, 90000, 2.1, 2000.0, 13), graphgen.chung_lu(30000, 150000, 2.1, 3000.0, 11)]
+    params = [(64, 3, 0.04, 0.1, 8), (128, 4, 0.1, 1.0, 5), (32, 5, 0.02, 0.05, 12), (96, 6, 0.03, 0.2, 7)]
+    n0, u0, v0 = graphs[0]
+    with im.IMContext(n0, u0, v0) as ctx:
+        for (n, u, v), (R, seed, p, alpha, k) in zip(graphs, params):
+            ctx.load_graph(n, u, v)
+            ctx.build_sketches(R, seed, p, alpha)
+            s, g = ctx.select_seeds(k)
+            sp = ctx.spread(s)
+            lab, sz = ctx.compact()
+            with im.IMContext(n, u, v) as fresh:
+                fresh.build_sketches(R, seed, p, alpha)
+                s1, g1 = fresh.select_seeds(k)
+                assert np.array_equal(s, s1) and np.array_equal(g, g1) and sp == fresh.spread(s1)
+                lab1, sz1 = fresh.compact()
+                assert np.array_equal(lab, lab1) and np.array_equal(sz, sz1)
