@@ -454,6 +454,65 @@ def run_c4(args):
     return 0
 
 
+def run_c5(args):
+    """The serving workload: 8 resident R-MAT graphs (scales 18, 18, 19, 20, 21, 21, 22, 23,
+    average degree 16) x p in {.01, .05} = 16 models (R = 128, alpha = 0.1), and requests for
+    k ~ U[5, 200] seeds of a uniformly drawn model arriving as a Poisson process of
+    --rate requests/s for --duration s, replayed by the native engine (im_server_*).  Reports
+    queries/s and latency percentiles; checks that every answer equals the prefix of the model's
+    sequence computed alone (a separate context) for the four smallest models."""
+    import torch
+    import paper_2311_07554_gb300 as im
+
+    torch.cuda.set_device(0)
+    scales = [18, 18, 19, 20, 21, 21, 22, 23]
+    graphs = [graphgen.rmat(sc, 8 << sc, 0.57, 0.19, 0.19, 3000 + i) for i, sc in enumerate(scales)]
+    models = []   # (graph index, p, seed)
+    srv = im.IMServer()
+    t_admit = time.perf_counter()
+    footprint = 0
+    for gi, (n, u, v) in enumerate(graphs):
+        for p in (0.01, 0.05):
+            mid, fp = srv.add_model(n, u, v, 128, 42 + len(models), p, 0.1)
+            models.append((gi, p, 42 + len(models)))
+            footprint += fp
+    t_admit = time.perf_counter() - t_admit
+    rng = np.random.default_rng(2311)
+    nreq = int(args.rate * args.duration)
+    arrivals = np.cumsum(rng.exponential(1e9 / args.rate, nreq))
+    reqs = [(int(rng.integers(0, len(models))), int(rng.integers(5, 201)), int(t)) for t in arrivals]
+    out = srv.replay(reqs)
+    srv.close()
+    lat = np.array([(o["done_ns"] - t) / 1e6 for o, (_, _, t) in zip(out, reqs)])
+    span = (max(o["done_ns"] for o in out) - min(t for _, _, t in reqs)) / 1e9
+    # the four smallest models alone
+    same = True
+    for mid in range(4):
+        gi, p, seed = models[mid]
+        n, u, v = graphs[gi]
+        ks = [k for m, k, _ in reqs if m == mid]
+        if not ks:
+            continue
+        with im.IMContext(n, u, v) as ctx:
+            ctx.build_sketches(128, seed, p, 0.1)
+            s, g = ctx.select_seeds(max(ks))
+        for o, (m, k, _) in zip(out, reqs):
+            if m == mid:
+                same &= bool(np.array_equal(o["seeds"], s[:k]) and np.array_equal(o["gains"], g[:k]))
+    line = {"metric": "queries/s", "value": len(reqs) / span, "unit": "queries/s", "n_gpus": 1, "steps": 1,
+            "warmup": 0, "ms_per_step": span * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "c5_rmat_serving", "models": len(models), "scales": scales, "R": 128,
+                       "alpha": 0.1, "p": [0.01, 0.05], "rate_per_s": args.rate, "duration_s": args.duration,
+                       "requests": len(reqs), "k": "U[5,200]", "parallelism": "replicas1"},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
+                           "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
+            "admission": {"seconds": t_admit, "estimated_device_bytes": footprint},
+            "identical_alone_vs_mix": bool(same)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -469,9 +528,14 @@ def main():
     ap.add_argument("--alpha", type=float, default=None, help="center fraction (default: the workload's)")
     ap.add_argument("--c4", action="store_true", help="the batched workload: 64 instances side by side")
     ap.add_argument("--workers", type=int, default=4, help="contexts side by side for --c4")
+    ap.add_argument("--c5", action="store_true", help="the serving workload: 16 resident models, Poisson requests")
+    ap.add_argument("--rate", type=float, default=200.0, help="requests per second for --c5")
+    ap.add_argument("--duration", type=float, default=10.0, help="seconds of requests for --c5")
     args = ap.parse_args()
     if args.c4:
         return run_c4(args)
+    if args.c5:
+        return run_c5(args)
     n, u, v, prm = graphgen.workload(args.workload)
     prm["name"] = args.workload
     prm["probs"] = args.probs

@@ -310,6 +310,47 @@ typedef struct {
 
 int im_run_batch(im_instance* inst, uint32_t count, uint32_t workers);
 
+/*
+ * Serving: resident sketch sets answering requests for seed sets (the paper has no serving
+ * layer; this engine is built on its greedy-prefix property: Alg. 1 picks one seed per round,
+ * so the best k seeds it finds are the first k of one sequence, whatever other k were asked).
+ *
+ * im_server_create     an empty engine on the current device.
+ * im_server_add_model  admits one model -- a graph (HOST edge lists as im_create) with R, seed,
+ *                      p, alpha (as im_build_sketches) -- if its estimated device footprint
+ *                      (*footprint_out, bytes) leaves 2 GiB of the device free (else IM_ENOMEM,
+ *                      nothing allocated), builds its sketches, and starts its host thread.
+ *                      *model_out = its id (0, 1, ...).
+ * im_server_replay     submits every request at its arrival time (arrival_ns after the call
+ *                      starts) and returns when all are answered.  A model's thread takes all
+ *                      of its pending requests at once and extends the model's seed sequence
+ *                      to their largest k (one selection run answers them all); the answer to
+ *                      (model, k) is the first k seeds of that sequence, their marginal gains and
+ *                      the spread estimate sum_{i<k} gain_i (= im_spread of those seeds, by
+ *                      telescoping).  submit_ns / done_ns: when the request was queued and
+ *                      answered, from the call's start.  Returns IM_OK, or the first failing
+ *                      request's status (IM_EINVAL for a model id or k out of range).
+ * im_server_destroy    stops the threads and frees every model.
+ */
+typedef struct im_server im_server;
+typedef struct {
+    uint32_t model;
+    uint32_t k;
+    uint64_t arrival_ns;
+    uint32_t* seeds_out;    /* HOST, k entries (or NULL) */
+    uint64_t* gains_out;    /* HOST, k entries (or NULL) */
+    uint64_t* spread_out;   /* HOST, 1 entry (or NULL) */
+    uint64_t submit_ns;     /* out */
+    uint64_t done_ns;       /* out */
+    int status;             /* out */
+} im_request;
+
+int im_server_create(im_server** out);
+int im_server_add_model(im_server* srv, uint32_t n, uint64_t m, const uint32_t* u, const uint32_t* v, uint32_t R,
+                        uint64_t seed, double p, double alpha, uint32_t* model_out, uint64_t* footprint_out);
+int im_server_replay(im_server* srv, im_request* req, uint32_t count);
+int im_server_destroy(im_server* srv);
+
 /* Tuning: hubs.  GetCenter (Alg. 3) from a vertex whose component reaches a high-degree
  * non-center tests that vertex's whole adjacency list, in every sketch where it is reached.
  * With hubs, up to `cap` non-centers of degree >= `min_degree` (the largest degrees, ties to

@@ -47,6 +47,13 @@ class im_instance(ctypes.Structure):
                 ("spread_out", ctypes.POINTER(ctypes.c_uint64)), ("status", ctypes.c_int)]
 
 
+class im_request(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_uint32), ("k", ctypes.c_uint32), ("arrival_ns", ctypes.c_uint64),
+                ("seeds_out", ctypes.POINTER(ctypes.c_uint32)), ("gains_out", ctypes.POINTER(ctypes.c_uint64)),
+                ("spread_out", ctypes.POINTER(ctypes.c_uint64)), ("submit_ns", ctypes.c_uint64),
+                ("done_ns", ctypes.c_uint64), ("status", ctypes.c_int)]
+
+
 def lib():
     """Load the library (raises if it is missing: there is no fallback path)."""
     global _lib
@@ -85,6 +92,10 @@ def lib():
         "im_set_seed_speculation": ([vp, u32], i32),
         "im_set_hubs": ([vp, u32, u32], i32),
         "im_run_batch": ([c.POINTER(im_instance), u32, u32], i32),
+        "im_server_create": ([c.POINTER(vp)], i32),
+        "im_server_add_model": ([vp, u32, u64, vp, vp, u32, u64, dbl, dbl, c.POINTER(u32), c.POINTER(u64)], i32),
+        "im_server_replay": ([vp, c.POINTER(im_request), u32], i32),
+        "im_server_destroy": ([vp], i32),
         "im_mc_spread": ([vp, ctypes.POINTER(ctypes.c_uint32), u32, u32, u64, ctypes.POINTER(ctypes.c_uint64)], i32),
         "im_stream": ([vp], vp),
         "im_sketch_static": ([u32, u64, vp, vp, u64, dbl, u32, vp, vp, vp], i32),
@@ -306,6 +317,66 @@ def im_run_batch(instances, workers: int = 8):
         bad = next(i for i in range(len(instances)) if arr[i].status != IM_OK)
         raise IMError(rc, f"instance {bad} failed with status {arr[bad].status}")
     return [(sd, gn, int(sp[0])) for sd, gn, sp in outs]
+
+
+class IMServer:
+    """Resident models answering requests for k seeds (im_server_*)."""
+
+    def __init__(self):
+        h = ctypes.c_void_p()
+        rc = lib().im_server_create(ctypes.byref(h))
+        if rc != IM_OK:
+            raise IMError(rc, "im_server_create")
+        self.h = h
+        self._keep = []
+
+    def add_model(self, n, u, v, R, seed, p, alpha):
+        """Admit a model; returns (model id, estimated device bytes)."""
+        u = np.ascontiguousarray(np.asarray(u, dtype=np.uint32))
+        v = np.ascontiguousarray(np.asarray(v, dtype=np.uint32))
+        mid = ctypes.c_uint32(0)
+        fp = ctypes.c_uint64(0)
+        rc = lib().im_server_add_model(self.h, n, len(u), u.ctypes.data, v.ctypes.data, R, seed, p, alpha,
+                                       ctypes.byref(mid), ctypes.byref(fp))
+        if rc != IM_OK:
+            raise IMError(rc, f"im_server_add_model (estimated {fp.value} bytes)")
+        return int(mid.value), int(fp.value)
+
+    def replay(self, requests):
+        """requests: (model, k, arrival_ns) tuples.  Returns dicts with seeds, gains, spread,
+        submit_ns, done_ns, in input order."""
+        arr = (im_request * len(requests))()
+        outs = []
+        P32, P64 = ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint64)
+        for i, (model, k, t) in enumerate(requests):
+            sd = np.zeros(k, np.uint32)
+            gn = np.zeros(k, np.uint64)
+            sp = np.zeros(1, np.uint64)
+            outs.append((sd, gn, sp))
+            arr[i] = im_request(model, k, int(t), sd.ctypes.data_as(P32), gn.ctypes.data_as(P64),
+                                sp.ctypes.data_as(P64), 0, 0, 0)
+        rc = lib().im_server_replay(self.h, arr, len(requests))
+        if rc != IM_OK:
+            raise IMError(rc, "im_server_replay")
+        return [dict(seeds=sd, gains=gn, spread=int(sp[0]), submit_ns=int(arr[i].submit_ns),
+                     done_ns=int(arr[i].done_ns)) for i, (sd, gn, sp) in enumerate(outs)]
+
+    def close(self):
+        if self.h:
+            lib().im_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 IM_HUBS_AUTO = 0xFFFFFFFF

@@ -613,3 +613,40 @@ def test_one_context_across_graph_sizes():
                 assert np.array_equal(s, s1) and np.array_equal(g, g1) and sp == fresh.spread(s1)
                 lab1, sz1 = fresh.compact()
                 assert np.array_equal(lab, lab1) and np.array_equal(sz, sz1)
+
+
+# ---- serving: resident models answering requests for k seeds -----------------------------------
+
+def test_server_answers_are_greedy_prefixes():
+    """Requests replayed at their arrival times on three resident models: every answer is the
+    first k seeds (and gains) of the model's greedy sequence computed alone, its spread the
+    sum of those gains (= the spread of the k seeds); one model against the oracle."""
+    graphs = [graphgen.chung_lu(20000, 100000, 2.1, 2000.0, 21), graphgen.erdos_renyi(8000, 30000, 22),
+              graphgen.chung_lu(12000, 60000, 2.1, 1500.0, 23)]
+    params = [(64, 5, 0.03, 0.1), (32, 6, 0.08, 1.0), (48, 7, 0.05, 0.05)]
+    rng = np.random.default_rng(3)
+    reqs = [(int(rng.integers(0, 3)), int(rng.integers(1, 40)), int(t)) for t in np.cumsum(rng.exponential(2e6, 80))]
+    with im.IMServer() as srv:
+        for (n, u, v), (R, seed, p, alpha) in zip(graphs, params):
+            mid, fp = srv.add_model(n, u, v, R, seed, p, alpha)
+            assert fp > 0
+        out = srv.replay(reqs)
+        with pytest.raises(im.IMError) as e:
+            srv.replay([(3, 5, 0)])
+        assert e.value.code == im.IM_EINVAL
+    kmax = [max([k for m, k, _ in reqs if m == i] + [1]) for i in range(3)]
+    alone = []
+    for (n, u, v), (R, seed, p, alpha), k in zip(graphs, params, kmax):
+        with im.IMContext(n, u, v) as ctx:
+            ctx.build_sketches(R, seed, p, alpha)
+            s, g = ctx.select_seeds(k)
+            alone.append((s, g, ctx))
+            for (m, kk, _), o in zip(reqs, out):
+                if m == len(alone) - 1:
+                    assert np.array_equal(o["seeds"], s[:kk]) and np.array_equal(o["gains"], g[:kk])
+                    assert o["spread"] == int(g[:kk].sum()) == ctx.spread(s[:kk])
+                    assert o["done_ns"] >= o["submit_ns"]
+    n, u, v = graphs[1]
+    L = oracle.Graph(n, u, v).labels(params[1][1], params[1][2], params[1][0])
+    o_seeds, o_gains = oracle.greedy(L, kmax[1])
+    assert np.array_equal(alone[1][0], o_seeds) and np.array_equal(alone[1][1], o_gains)
