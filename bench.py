@@ -106,8 +106,19 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def _src_digest(name: str) -> str:
-    return hashlib.sha1((SRC / name).read_bytes()).hexdigest()[:12]
+def _kernel_digest(name: str, fn: str) -> str:
+    """sha1 of a kernel's own source text (its name through its closing brace) in csrc/name:
+    the ncu counters of a kernel stay valid while that text is unchanged."""
+    text = (SRC / name).read_text()
+    i = text.find("\n" + fn + "(")
+    if i < 0:
+        return ""
+    depth, k = 0, text.index("{", i)
+    for k in range(k, len(text)):
+        depth += {"{": 1, "}": -1}.get(text[k], 0)
+        if depth == 0:
+            break
+    return hashlib.sha1(text[i + 1:k + 1].encode()).hexdigest()[:12]
 
 
 def _traffic(kernel: str, units_per_launch: float):
@@ -117,7 +128,7 @@ def _traffic(kernel: str, units_per_launch: float):
         return None
     try:
         d = json.loads(f.read_text()).get(kernel)
-        if not d or d.get("source_sha1") != _src_digest(d["source"]):
+        if not d or d.get("kernel_sha1") != _kernel_digest(d["source"], d["function"]):
             return None
         return d["bytes_per_unit"] * units_per_launch
     except Exception:
