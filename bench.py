@@ -189,6 +189,40 @@ def kernel_rooflines(prof, live_build, n, m, R, steps, peaks, peak_src, clk, has
     return out
 
 
+def sketch_roofline(prof, n, m, R, B, p_mean, alpha, steps, sketch_ms, peaks, hash_peak, live_build):
+    """Sketch construction (one im_build_sketches) against the HBM roofline, as the modelled
+    bytes of a build: per sketch 8m/B (edge stream shared by B sketches) + 2 p m 32 (random
+    parent sectors of the live pairs) + 20 n (initialisation, compression, histogram, gain
+    gather, label reads) + 8 rho (compact output), plus 8 n once (gains).  Beside it the ALU
+    floor of the hashing (m R pairs at the measured per-pair rate) and the DRAM bytes ncu
+    measured for the four sketch kernels (null if any of them changed since)."""
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    rho = min(n, int(np.ceil(alpha * n)))
+    per_sketch = 8.0 * m / B + 2.0 * p_mean * m * 32.0 + 20.0 * n + 8.0 * rho
+    model_bytes = R * per_sketch + 8.0 * n
+    hbm_floor_ms = model_bytes / (hbm * 1e9) * 1e3
+    alu_floor_ms = float(m) * R / hash_peak * 1e3
+    units = {"sample_emit": float(m) * R * steps, "union": float(live_build),
+             "compress_count": float(n) * R * steps, "gain_compact": float(n) * R * steps}
+    measured = 0.0
+    for k, u in units.items():
+        t = _traffic(k, u)   # bytes per unit x units of the timed steps
+        if t is None or k not in prof:
+            measured = None
+            break
+        measured += t
+    out = {"model_bytes_per_build": model_bytes, "hbm_floor_ms": hbm_floor_ms, "sketch_ms": sketch_ms,
+           "frac_of_hbm_roofline": hbm_floor_ms / sketch_ms, "alu_floor_ms": alu_floor_ms,
+           "frac_of_alu_floor": alu_floor_ms / sketch_ms, "peak_gbs": hbm,
+           "note": "modelled bytes as SURVEY 8(d); the hashing's ALU floor is above the HBM floor"}
+    if measured is not None:
+        gbs = measured / steps / (sketch_ms / 1e3) / 1e9
+        out["ncu_dram_bytes_per_build"] = measured / steps
+        out["ncu_dram_gbs"] = gbs
+        out["ncu_dram_frac"] = gbs / hbm
+    return out
+
+
 # ----------------------------------------------------------------------- CPU baseline
 def edge_probs(prm, m):
     """Per-edge probabilities of the workload, or None for one p: U(0, 0.1) / U(0.1, 0.3)
@@ -390,6 +424,11 @@ def run_ours(args, n, u, v, prm):
         roof = roofs.get(top[0]) or (max(roofs.values(), key=lambda r: r["share_of_device_time"])
                                      if roofs else None)
         cpu = cpu_sample(n, u, v, prm)
+        p_mean = prm["p"] if pe is None and prm["probs"] == "uniform" else None
+        if p_mean is None:
+            p_mean = float(np.mean(pe)) if pe is not None else float(live_build) / (m * R * args.steps)
+        sk_roof = sketch_roofline(prof, n, m, R, int(st["sketch_batch"]), p_mean, prm["alpha"], args.steps,
+                                  ms_build, peaks, hash_peak, live_build)
         line = {
             "metric": METRIC,
             "value": pairs * ws / (ms_step / 1e3),
@@ -410,6 +449,7 @@ def run_ours(args, n, u, v, prm):
             "hubs": int(st["hubs"]),
             "mc_eval": mc,
             "roofline": roof,
+            "sketch_roofline": sk_roof,
             "kernel_rooflines": list(roofs.values()),
             "cpu_baseline": cpu,
             "e2e": {"value": pairs * ws / e2e_s, "unit": "pairs/s",

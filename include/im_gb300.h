@@ -237,9 +237,9 @@ int im_sketch_static(uint32_t n, uint64_t m, const uint32_t* d_u, const uint32_t
  * im_build_sketches. */
 int im_set_refresh_threshold(im_ctx* ctx, uint64_t min_batch);
 
-/* Tuning: 2 runs consecutive sketch batches on two streams so that one batch's hashing
- * overlaps another's union-find (both lanes' scratch is allocated either way); 1 (default)
- * runs them in order on the context stream. */
+/* Tuning: 2 (default) runs consecutive sketch batches on two streams so that one batch's
+ * hashing (ALU-bound) overlaps another's union-find (latency-bound); 1 runs them in order on
+ * the context stream.  Both lanes' scratch is allocated either way; results do not depend on it. */
 int im_set_pipeline(im_ctx* ctx, uint32_t lanes);
 
 /* Execution of the selection loop (Alg. 2 / Alg. 4 rounds).  1 (default): the whole loop is
@@ -253,7 +253,7 @@ int im_set_graph(im_ctx* ctx, int on);
  * ov_c(v) = sum_r |C_r(v)| [c in C_r(v)].  If the first seed is one of them, the second round's
  * batches are evaluated as Marginal(v | {c}) = gain0(v) - ov_c(v) (exact) instead of by
  * searches or by recomputing the sketches.  0 disables; default 4, at most 8; costs 8 n bytes
- * per candidate; needs the single-lane pipeline; takes effect at the next im_build_sketches.
+ * per candidate (twice with two lanes); takes effect at the next im_build_sketches.
  * Seeds, gains and evaluation counts do not depend on it. */
 int im_set_seed_speculation(im_ctx* ctx, uint32_t candidates);
 

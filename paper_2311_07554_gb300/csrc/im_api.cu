@@ -230,6 +230,7 @@ int im_create_reserved(im_ctx** out, uint32_t n, uint64_t m, const uint32_t* u, 
     c->cur = c->stream;
     if (cudaStreamCreateWithFlags(&c->lane_stream1, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_spec, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         g_create_error = "stream or event creation failed";
         im_destroy(c);
@@ -419,8 +420,8 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
         hub_rows = std::min<uint32_t>(cap, n - rho);
     }
     const size_t nc = ((size_t)rho + hub_rows) * R;
-    // candidate first seeds need the batches in order (they are chosen after the first one)
-    const uint32_t nspec = c->lanes == 1 ? std::min<uint32_t>(c->spec_req, n) : 0u;
+    // candidate first seeds (chosen after the first batch; a second lane waits for them)
+    const uint32_t nspec = std::min<uint32_t>(c->spec_req, n);
     // A build that fits the device buffers reuses them (cudaMalloc / cudaFree synchronise the
     // device, stalling every stream, other contexts' included); the selection graph, which
     // captured the shapes and the sampler, is kept only while both are unchanged.
@@ -458,7 +459,7 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
                   dalloc(c->lane[0].parent, (size_t)B * na) && dalloc(c->lane[0].word, (size_t)B * na) &&
                   dalloc(c->lane[1].parent, (size_t)B * na) && dalloc(c->lane[1].word, (size_t)B * na) &&
                   dalloc(c->lane[1].gain, na) && dalloc(c->lane[1].fresh, na);
-        if (ok && nsa) ok = dalloc(c->lane[0].spec_ov, (size_t)nsa * na);
+        if (ok && nsa) ok = dalloc(c->lane[0].spec_ov, (size_t)nsa * na) && dalloc(c->lane[1].spec_ov, (size_t)nsa * na);
         if (ok && livea) {
             c->live_cap = livea;
             ok = dalloc(c->lane[0].live, c->live_cap) && dalloc(c->lane[0].live_n, 1) &&
@@ -745,6 +746,7 @@ void im_destroy(im_ctx* c) {
     if (c->lane_stream1) { cudaStreamSynchronize(c->lane_stream1); cudaStreamDestroy(c->lane_stream1); }
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_spec) cudaEventDestroy(c->ev_spec);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;

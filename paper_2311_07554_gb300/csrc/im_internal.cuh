@@ -340,9 +340,9 @@ struct im_ctx {
     };
     Lane lane[2];
     cudaStream_t lane_stream1 = nullptr;         // owned
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_spec = nullptr;
     cudaStream_t cur = nullptr;                  // stream the next launch goes to
-    uint32_t lanes = 1;                          // 1: batches in order on the context stream
+    uint32_t lanes = 2;                          // sketch batches alternate between two streams
     uint32_t batch_req = 0, batch_used = 0, batch_alloc = 0;
     uint64_t live_cap = 0;           // live-pair records allocated per lane
     // capacities of the sketch buffers (a later build that fits reuses them)

@@ -1145,9 +1145,14 @@ k_sel_step(StepArgs a) {
     if (phase == PH_NONE) return;
     const bool marking = phase == PH_MARK || phase == PH_MARK_EVAL;
     // evaluation phases: if enough blocks are left over, blocks [0, ntask) search (one task
-    // each) while the others scan the candidates; else every block scans after its searches
+    // each) while the others scan the candidates; else, or when every task is a lookup (the
+    // vertices are centers or hubs: no search), every block scans after its tasks
     const unsigned long long ntask = phase == PH_EVAL ? (unsigned long long)__ldcg(&st->batch_n) * a.R : a.R;
-    const uint32_t free0 = (ntask + 64 <= gridDim.x) ? (uint32_t)ntask : 0u;
+    bool lookups = false;
+    if (phase == PH_MARK) lookups = is_center(a.s, st->sd);
+    else if (phase == PH_MARK_EVAL) lookups = is_center(a.s, st->sd) && is_center(a.s, a.batch[0]);
+    else if (phase == PH_EVAL) lookups = __ldcg(&st->batch_n) == 1 && is_center(a.s, a.batch[0]);
+    const uint32_t free0 = (!lookups && ntask + 64 <= gridDim.x) ? (uint32_t)ntask : 0u;
     const bool scanner = blockIdx.x >= free0;
     const uint32_t t0 = (blockIdx.x - (scanner ? free0 : 0u)) * blockDim.x + threadIdx.x;
     const uint32_t nthr = (gridDim.x - free0) * blockDim.x;

@@ -793,6 +793,10 @@ int im_sketch_batches(im_ctx* c) {
     const unsigned T = 256;
     int rc = lanes_fork(c);
     if (rc) return rc;
+    // lane 1 sums its overlaps in a buffer of its own (added at the end)
+    if (c->lanes > 1 && c->spec_count)
+        IM_CUDA(c, cudaMemsetAsync(c->lane[1].spec_ov, 0, (size_t)c->spec_count * n * sizeof(uint64_t),
+                                   c->lane_stream1));
     uint32_t i = 0;
     for (uint32_t r0 = 0; r0 < R; r0 += c->batch_used, ++i) {
         const uint32_t nb = R - r0 < c->batch_used ? R - r0 : c->batch_used;
@@ -803,15 +807,17 @@ int im_sketch_batches(im_ctx* c) {
         uint64_t* gain = (i % c->lanes) ? L.gain : c->d_gain0;
         const int first = i < c->lanes ? 1 : 0;
         const uint32_t nspec = i ? c->spec_count : 0;   // candidates are known after batch 0
+        // the candidates come from batch 0 (lane 0): lane 1's first gain pass waits for them
+        if (nspec && (i % c->lanes) && i < c->lanes) IM_CUDA(c, cudaStreamWaitEvent(L.stream, c->ev_spec, 0));
 #define IM_GAIN(ALL, K)                                                                             \
     if (ALL)                                                                                        \
         IM_LAUNCH(c, K_GAIN_COMPACT, (k_gain_full<K>), grid_for(n, 32, 152u * 8u), kGainWarps * 32, 0, L.parent, \
                   L.word, n, nb, r0, R, gain, first, c->d_label, c->d_size, c->d_spec_ids, nspec,       \
-                  c->lane[0].spec_ov);                                                              \
+                  L.spec_ov);                                                                       \
     else                                                                                            \
         IM_LAUNCH(c, K_GAIN_COMPACT, (k_gain_compact<false, K>), grid_for(n, T, 152u * 16u), T, 0, L.parent,   \
                   L.word, n, nb, r0, R, gain, first, c->d_cidx, c->d_label, c->d_size, c->d_spec_ids, nspec, \
-                  c->lane[0].spec_ov)
+                  L.spec_ov)
         if (c->all_centers) {
             if (nspec == 0) IM_GAIN(true, 0);
             else if (nspec <= 4) IM_GAIN(true, 4);
@@ -830,6 +836,7 @@ int im_sketch_batches(im_ctx* c) {
                           c->d_spec_keys, k, c->d_spec_ids);
             IM_LAUNCH(c, K_CENTER_PICK, k_spec_ids, 1, 32, 0, c->d_spec_keys, c->spec_count, c->key_bits,
                       c->d_spec_ids);
+            IM_CUDA(c, cudaEventRecord(c->ev_spec, c->cur));   // the candidates are known
             IM_LAUNCH(c, K_GAIN_COMPACT, k_spec_overlap, grid_for(n, T, 152u * 16u), T, 0, L.parent, L.word, n, nb,
                       c->d_spec_ids, c->spec_count, c->lane[0].spec_ov);
         }
@@ -840,6 +847,10 @@ int im_sketch_batches(im_ctx* c) {
         IM_LAUNCH(c, K_GAIN_COMPACT, k_add_u64, grid_for(n, T, 152u * 8u), T, 0,
                   (unsigned long long*)c->d_gain0, (const unsigned long long*)c->lane[1].gain, (uint64_t)n,
                   (const unsigned int*)nullptr);
+        if (c->spec_count)
+            IM_LAUNCH(c, K_GAIN_COMPACT, k_add_u64, grid_for((uint64_t)c->spec_count * n, T, 152u * 8u), T, 0,
+                      (unsigned long long*)c->lane[0].spec_ov, (const unsigned long long*)c->lane[1].spec_ov,
+                      (uint64_t)c->spec_count * n, (const unsigned int*)nullptr);
     }
     IM_CUDA(c, cudaGetLastError());
     return IM_OK;

@@ -313,26 +313,31 @@ def test_rebuilds_in_one_context_match_fresh_contexts():
 
 @pytest.mark.parametrize("graph", ["chunglu", "er"])
 @pytest.mark.parametrize("candidates", [0, 1, 4, 8])
-def test_first_seed_speculation_gives_the_same_selection(candidates, graph):
+@pytest.mark.parametrize("lanes", [1, 2])
+def test_first_seed_speculation_gives_the_same_selection(candidates, graph, lanes):
     """Round 1's batches evaluated from the build's overlap sums of candidate first seeds (the
     vertices with the largest gains over the first batch of 32 sketches) give the plain
     selection, with the same batches and evaluation counts; the speculation is used exactly
     when the first seed is among the candidates (computed here from the oracle's labels).
     On the Chung-Lu graph the hubs tie at the top and the smallest id wins, as in the full
-    argmax; on the Erdos-Renyi graph the first seed ranks third, so one candidate misses it."""
+    argmax; on the Erdos-Renyi graph the first seed ranks third, so one candidate misses it.
+    With two lanes (R = 128: two batches per lane) lane 1 waits for the candidates and sums its
+    overlaps apart."""
+    R = 64 if lanes == 1 else 128
     if graph == "chunglu":
         n, u, v = graphgen.chung_lu(20000, 100000, 2.1, 2000.0, 5)
     else:
         n, u, v = graphgen.erdos_renyi(2000, 10000, 7)
     G = oracle.Graph(n, u, v)
-    L = G.labels(42, 0.05, 64)
+    L = G.labels(42, 0.05, R)
     o_seeds, o_gains = oracle.greedy(L, 8)
     g32 = oracle.gains(L[:32]).astype(np.int64)
     cand = np.lexsort((np.arange(n), -g32))[:candidates]
     hit = bool(np.isin(o_seeds[0], cand))
     with im.IMContext(n, u, v) as ctx:
         im.im_set_seed_speculation(ctx.h, candidates)
-        ctx.build_sketches(64, 42, 0.05, 0.1)
+        im.im_set_pipeline(ctx.h, lanes)
+        ctx.build_sketches(R, 42, 0.05, 0.1)
         assert ctx.stats()["sketch_batch"] == 32
         s1, g1 = ctx.select_seeds(2)                 # through round 1, then the rest
         seeds, gains = ctx.select_seeds(8)
@@ -340,13 +345,14 @@ def test_first_seed_speculation_gives_the_same_selection(candidates, graph):
         ev = ctx.round_evals()
     with im.IMContext(n, u, v) as ref:
         im.im_set_seed_speculation(ref.h, 0)
-        ref.build_sketches(64, 42, 0.05, 0.1)
+        ref.build_sketches(R, 42, 0.05, 0.1)
         ref.select_seeds(8)
         assert np.array_equal(ev, ref.round_evals()) and st["batches"] == ref.stats()["batches"]
     assert np.array_equal(s1, seeds[:2])
     assert np.array_equal(seeds, o_seeds) and np.array_equal(gains, o_gains)
     assert (st["spec_batches"] > 0) == hit
-    assert hit == (candidates >= (1 if graph == "chunglu" else 3))
+    if lanes == 1:
+        assert hit == (candidates >= (1 if graph == "chunglu" else 3))
     with pytest.raises(im.IMError) as e:
         with im.IMContext(n, u, v) as ctx:
             im.im_set_seed_speculation(ctx.h, 9)
