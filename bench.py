@@ -317,6 +317,8 @@ def run_ours(args, n, u, v, prm):
     set_probs(ctx)
     if args.sketch_batch:
         im.im_set_sketch_batch(ctx.h, args.sketch_batch)
+    if args.select_host:   # the selection's kernels launched by the host (profilable one by one)
+        im.im_set_graph(ctx.h, 0)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
 
     def step():
@@ -577,6 +579,8 @@ def main():
     ap.add_argument("--mc-sims", type=int, default=20000,
                     help="Monte-Carlo simulations to evaluate the selected seeds with, after the timed region (0: none)")
     ap.add_argument("--alpha", type=float, default=None, help="center fraction (default: the workload's)")
+    ap.add_argument("--select-host", action="store_true",
+                    help="drive the selection from the host instead of the CUDA graph (for kernel profiling)")
     ap.add_argument("--c4", action="store_true", help="the batched workload: 64 instances side by side")
     ap.add_argument("--workers", type=int, default=4, help="contexts side by side for --c4")
     ap.add_argument("--c5", action="store_true", help="the serving workload: 16 resident models, Poisson requests")
