@@ -736,6 +736,7 @@ void im_destroy(im_ctx* c) {
     if (c->h_upload) cudaFreeHost(c->h_upload);
     dfree(c->d_edgeT); dfree(c->d_arcT);
     dfree(c->d_spread_pairs); dfree(c->d_spread_seeds); dfree(c->d_spread_total); dfree(c->d_live_total);
+    dfree(c->d_topb);
     if (c->d_sel) cudaFree(c->d_sel);
     if (c->h_sel) cudaFreeHost(c->h_sel);
     if (c->h_live) cudaFreeHost(c->h_live);

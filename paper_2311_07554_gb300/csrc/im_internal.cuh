@@ -176,6 +176,10 @@ struct SelState {
     unsigned long long spec_batches;
     unsigned int phase;             // SelPhase: what the next k_sel_step launch does
     unsigned int rare;              // SelRare: an evaluator outside k_sel_step is due
+    unsigned int topb;              // batch size PH_TOPB selects (0: radix passes and a gather)
+    unsigned int pad2;
+    unsigned long long above_bound; // unevaluated candidates above the best fresh key before the
+                                    // last batch: an upper bound on count_above
 };
 
 enum SelError : unsigned int {
@@ -207,7 +211,8 @@ enum SelMode : unsigned int {
 // the other candidates and plans the next batch (PH_EVAL, PH_MARK_EVAL), or PH_SPEC_EVAL +
 // PH_SCAN.  A round opens with PH_SCAN or PH_MARK; PH_COUNT counts candidates above the best.
 enum SelPhase : unsigned int {
-    PH_NONE = 0, PH_SCAN, PH_MARK, PH_MARK_EVAL, PH_EVAL, PH_SEL_PASS, PH_GATHER, PH_SPEC_EVAL, PH_COUNT
+    PH_NONE = 0, PH_SCAN, PH_MARK, PH_MARK_EVAL, PH_EVAL, PH_SEL_PASS, PH_GATHER, PH_SPEC_EVAL, PH_COUNT,
+    PH_TOPB   // a batch of at most 32: the largest stale keys in one pass (replaces passes + gather)
 };
 
 // Evaluators with launch sequences of their own (the switch of the selection graph).
@@ -312,6 +317,7 @@ struct im_ctx {
     cudaGraph_t sel_graph = nullptr;
     cudaGraphExec_t sel_exec = nullptr;
     unsigned step_grid = 0;          // blocks of k_sel_step (resident at once)
+    uint64_t* d_topb = nullptr;      // 32 keys per step-kernel block (PH_TOPB)
     bool capturing = false;              // launches go into a graph: no events, no counting
     bool count_only = false;             // launches are only counted (dry run)
     uint64_t dry_count = 0;

@@ -421,6 +421,7 @@ __global__ void k_init_keys(const uint64_t* __restrict__ gain0, uint32_t n, uint
 
 
 constexpr uint32_t kPending = 0x80000000u;   // stamp bit: batch member awaiting its fresh key
+constexpr uint32_t kTopB = 32;               // largest batch PH_TOPB selects (one key per lane)
 
 // The first phase of a step of the given mode (PH_NONE: the selection is over).
 __device__ __forceinline__ unsigned first_phase(unsigned mode) {
@@ -439,7 +440,8 @@ __device__ __forceinline__ unsigned first_phase(unsigned mode) {
 
 // The next step is `mode`: its first phase, and the graph's loops entered (or left).
 __device__ void set_step(SelState* st, const SelHandles& hd, unsigned mode) {
-    const unsigned ph = first_phase(mode);
+    unsigned ph = first_phase(mode);
+    if ((ph == PH_SEL_PASS || ph == PH_GATHER) && st->topb) ph = PH_TOPB;
     st->phase = ph;
     st->rare = RARE_NONE;
     if (hd.on) {
@@ -481,6 +483,7 @@ __device__ void plan_step(SelState* st, uint32_t* __restrict__ batch, unsigned l
         st->best = 0;                              // a later run opens this round again
         st->stale_max = 0;
         st->n_unev = 0;
+        st->above_bound = 0;
         st->count_above = 0;
         st->cont = 0;
         st->mode = M_NONE;
@@ -500,7 +503,9 @@ __device__ void plan_step(SelState* st, uint32_t* __restrict__ batch, unsigned l
         if (j > 81) st->err = SEL_NO_PROGRESS;   // doubling covers any n within 64 batches
         else cont = 1;
     }
-    if (cont && best && !have_count) {
+    // the count of candidates above the best fresh key only decides a recomputation, which
+    // needs at least refresh_min of them: skipped when the scans' upper bound is below that
+    if (cont && best && !have_count && st->above_bound >= st->refresh_min) {
         mode = M_COUNT_ABOVE;
         st->count_above = 0;
     } else if (cont) {
@@ -549,6 +554,7 @@ __device__ void plan_step(SelState* st, uint32_t* __restrict__ batch, unsigned l
         st->best = 0;
         st->stale_max = 0;
         st->n_unev = 0;
+        st->above_bound = 0;
         st->count_above = 0;
         if (direct) {
             const uint32_t x = (uint32_t)(mask - (smax & mask));
@@ -566,6 +572,11 @@ __device__ void plan_step(SelState* st, uint32_t* __restrict__ batch, unsigned l
              : direct  ? M_DIRECT
              : single  ? (hist ? M_HIST_SINGLE : M_GATHER_SINGLE)
                        : (hist ? M_HIST_CHUNK : M_GATHER_CHUNK);
+        // a batch of at most kTopB -- the B largest stale keys, or every unevaluated candidate
+        // when at most 2B remain -- is selected in one pass (PH_TOPB) instead of radix passes
+        // and a gather
+        const unsigned long long want = hist ? B : nu;
+        st->topb = (!direct && !refresh && (single || spec) && want <= kTopB) ? (unsigned)want : 0u;
         st->pending = 1;
         st->j = j + 1;
         st->batches++;
@@ -597,6 +608,7 @@ __device__ void plan_step(SelState* st, uint32_t* __restrict__ batch, unsigned l
             st->best = 0;
             st->stale_max = 0;
             st->n_unev = 0;
+            st->above_bound = 0;
             st->count_above = 0;
             cont = 1;
             mode = M_MARK;
@@ -805,6 +817,7 @@ struct StepArgs {
     uint32_t* fbb;
     uint32_t fb_cap, fb_slots;
     uint32_t n, R, bits;
+    uint64_t* topb;   // kTopB keys per block (PH_TOPB)
     SelHandles hd;
 };
 
@@ -814,21 +827,27 @@ union StepSmem {
         unsigned int h[256];
         unsigned long long sfx[256];
     } sp;
+    unsigned long long lists[kBlockWarps][kTopB];   // PH_TOPB: each warp's largest keys
 };
 
-__device__ __forceinline__ void block_max_sum(unsigned long long& a, unsigned long long& b, unsigned long long& c) {
-    __shared__ unsigned long long s_a[8], s_b[8], s_c[8];
+// Block reduction (valid in thread 0): maxima of a and b, sums of c and e.
+__device__ __forceinline__ void block_max_sum(unsigned long long& a, unsigned long long& b, unsigned long long& c,
+                                              unsigned long long& e) {
+    __shared__ unsigned long long s_a[8], s_b[8], s_c[8], s_e[8];
 #pragma unroll
     for (int d = 16; d; d >>= 1) {
         a = max(a, __shfl_xor_sync(kFull, a, d));
         b = max(b, __shfl_xor_sync(kFull, b, d));
         c += __shfl_xor_sync(kFull, c, d);
+        e += __shfl_xor_sync(kFull, e, d);
     }
     const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) { s_a[w] = a; s_b[w] = b; s_c[w] = c; }
+    if ((threadIdx.x & 31) == 0) { s_a[w] = a; s_b[w] = b; s_c[w] = c; s_e[w] = e; }
     __syncthreads();
     if (threadIdx.x == 0)
-        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) { a = max(a, s_a[i]); b = max(b, s_b[i]); c += s_c[i]; }
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+            a = max(a, s_a[i]); b = max(b, s_b[i]); c += s_c[i]; e += s_e[i];
+        }
     __syncthreads();
 }
 
@@ -861,7 +880,8 @@ __device__ __forceinline__ void for_candidates(const StepArgs& a, uint32_t t0, u
 __device__ void scan_candidates(const StepArgs& a, bool finalize, uint32_t skip, uint32_t t0, uint32_t nthr) {
     SelState* st = a.st;
     const uint32_t round = st->round;
-    unsigned long long bf = 0, sm = 0, cnt = 0;
+    const unsigned long long bp = st->best_prev;   // the best fresh key before this batch
+    unsigned long long bf = 0, sm = 0, cnt = 0, above = 0;
     for_candidates(a, t0, nthr, [&](uint32_t v, uint8_t sf, uint32_t sp, unsigned long long k) {
         if (sf || v == skip) return;
         if (sp & kPending) {   // evaluated in this batch
@@ -872,13 +892,14 @@ __device__ void scan_candidates(const StepArgs& a, bool finalize, uint32_t skip,
             sp = round;
         }
         if (sp == round) bf = max(bf, k);
-        else { sm = max(sm, k); ++cnt; }
+        else { sm = max(sm, k); ++cnt; above += k > bp ? 1u : 0u; }
     });
-    block_max_sum(bf, sm, cnt);
+    block_max_sum(bf, sm, cnt, above);
     if (threadIdx.x == 0) {
         if (bf) atomicMax(&st->best, bf);
         if (sm) atomicMax(&st->stale_max, sm);
         if (cnt) atomicAdd(&st->n_unev, cnt);
+        if (above) atomicAdd(&st->above_bound, above);
     }
 }
 
@@ -891,7 +912,7 @@ __device__ __forceinline__ void scan_all(const StepArgs& a, bool finalize, uint3
 __device__ void finalize_batch(const StepArgs& a) {
     SelState* st = a.st;
     const uint32_t round = st->round, bn = __ldcg(&st->batch_n);
-    unsigned long long bf = 0, unused_b = 0, unused_c = 0;
+    unsigned long long bf = 0, unused_b = 0, unused_c = 0, unused_e = 0;
     for (uint32_t j = threadIdx.x; j < bn; j += blockDim.x) {
         const uint32_t x = a.batch[j];
         const unsigned long long k = pack_key(__ldcg(a.fresh + j), x, a.bits);
@@ -899,7 +920,7 @@ __device__ void finalize_batch(const StepArgs& a) {
         a.stamp[x] = round;
         bf = max(bf, k);
     }
-    block_max_sum(bf, unused_b, unused_c);
+    block_max_sum(bf, unused_b, unused_c, unused_e);
     if (threadIdx.x == 0 && bf) atomicMax(&st->best, bf);
 }
 
@@ -1012,13 +1033,13 @@ __device__ void count_above_tasks(const StepArgs& a) {
     // only needed when the round goes on (the next batch's size depends on it)
     const bool need = st->n_unev > 0 && best <= st->stale_max && best;
     const uint32_t round = st->round;
-    unsigned long long cnt = 0, unused_a = 0, unused_b = 0;
+    unsigned long long cnt = 0, unused_a = 0, unused_b = 0, unused_e = 0;
     if (need)
         for_candidates(a, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x,
                        [&](uint32_t, uint8_t sf, uint32_t sp, unsigned long long k) {
                            if (!sf && sp != round && k > best) ++cnt;
                        });
-    block_max_sum(unused_a, unused_b, cnt);
+    block_max_sum(unused_a, unused_b, cnt, unused_e);
     if (threadIdx.x == 0 && cnt) atomicAdd(&st->count_above, cnt);
 }
 
@@ -1131,6 +1152,105 @@ __device__ void gather_tasks(const StepArgs& a) {
     }
 }
 
+// ---- PH_TOPB: the largest stale keys in one pass -------------------------------------
+// A warp keeps the `want` (<= kTopB) largest keys seen so far sorted in its first lanes (lane
+// i: the i-th largest; 0 = empty, every real key is >= 1).  A key above the list's last one
+// is inserted at its rank, the entries below moving down one lane (lanes >= want hold no
+// information).
+__device__ __forceinline__ void warp_insert(unsigned long long& L, unsigned long long k, uint32_t want) {
+    const unsigned lane = threadIdx.x & 31;
+    unsigned m = __ballot_sync(kFull, k > __shfl_sync(kFull, L, want - 1));
+    while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        const unsigned long long x = __shfl_sync(kFull, k, src);
+        if (x <= __shfl_sync(kFull, L, want - 1)) continue;   // pushed out by the keys before it
+        const int pos = __popc(__ballot_sync(kFull, L > x));
+        const unsigned long long up = __shfl_up_sync(kFull, L, 1);
+        if ((int)lane > pos) L = up;
+        else if ((int)lane == pos) L = x;
+    }
+}
+
+// The 8 lists of the block merged into warp 0's (every warp calls it).
+__device__ __forceinline__ unsigned long long block_merge(unsigned long long L, uint32_t want, StepSmem& sm) {
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    sm.lists[warp][lane] = lane < want ? L : 0ull;
+    __syncthreads();
+    if (warp == 0)
+        for (int w = 1; w < kBlockWarps; ++w) warp_insert(L, sm.lists[w][lane], want);
+    __syncthreads();
+    return L;
+}
+
+// Every block: its `want` largest eligible keys (unevaluated, above the best fresh key) into
+// topb[block]; 4 consecutive candidates per lane and iteration (vector loads), skipped with
+// one ballot when none of them beats the warp's last kept key.
+__device__ void topb_tasks(const StepArgs& a, StepSmem& sm) {
+    const SelState* st = a.st;
+    const uint32_t round = st->round, want = st->topb;
+    const unsigned long long bp = st->best_prev;
+    const unsigned long long lo = bp ? bp + 1 : 1ull;
+    const unsigned lane = threadIdx.x & 31;
+    unsigned long long L = 0;
+    const uint32_t stride = gridDim.x * blockDim.x * 4;
+    for (uint32_t base = (blockIdx.x * blockDim.x + (threadIdx.x & ~31u)) * 4; base < a.n; base += stride) {
+        const uint32_t v0 = base + 4 * lane;   // the loop bound is uniform over the warp
+        unsigned long long k[4] = {0, 0, 0, 0};
+        if (v0 + 3 < a.n) {
+            const uchar4 sf = reinterpret_cast<const uchar4*>(a.seedflag)[v0 >> 2];
+            const uint4 sp = reinterpret_cast<const uint4*>(a.stamp)[v0 >> 2];
+            const ulonglong2 ka = reinterpret_cast<const ulonglong2*>(a.key)[v0 >> 1];
+            const ulonglong2 kb = reinterpret_cast<const ulonglong2*>(a.key)[(v0 >> 1) + 1];
+            k[0] = (!sf.x && sp.x != round && ka.x >= lo) ? ka.x : 0;
+            k[1] = (!sf.y && sp.y != round && ka.y >= lo) ? ka.y : 0;
+            k[2] = (!sf.z && sp.z != round && kb.x >= lo) ? kb.x : 0;
+            k[3] = (!sf.w && sp.w != round && kb.y >= lo) ? kb.y : 0;
+        } else {
+            for (uint32_t e = 0; e < 4; ++e) {
+                const uint32_t v = v0 + e;
+                if (v < a.n && !a.seedflag[v] && a.stamp[v] != round && a.key[v] >= lo) k[e] = a.key[v];
+            }
+        }
+        const unsigned long long kmax = max(max(k[0], k[1]), max(k[2], k[3]));
+        if (!__any_sync(kFull, kmax > __shfl_sync(kFull, L, want - 1))) continue;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) warp_insert(L, k[e], want);
+    }
+    L = block_merge(L, want, sm);
+    if ((threadIdx.x >> 5) == 0) a.topb[(size_t)blockIdx.x * kTopB + lane] = lane < want ? L : 0ull;
+}
+
+// Last block: the grid's lists merged (the first `want` entries of each); the largest become
+// the batch.
+__device__ void topb_pick(const StepArgs& a, StepSmem& sm) {
+    SelState* st = a.st;
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t want = st->topb, round = st->round;
+    unsigned long long L = 0;
+    // entry (block b, rank i < want) at b * kTopB + i: each warp takes blocks warp, warp + 8, ...
+    // 32 / want of them per step
+    const uint32_t per = kTopB / want;   // blocks per 32 lanes (want is at most kTopB)
+    for (uint32_t b0 = warp * per; b0 < gridDim.x; b0 += kBlockWarps * per) {   // uniform over the warp
+        const uint32_t b = b0 + lane / want, i = lane % want;
+        warp_insert(L, (lane < per * want && b < gridDim.x) ? __ldcg(a.topb + (size_t)b * kTopB + i) : 0ull, want);
+    }
+    L = block_merge(L, want, sm);
+    if (warp == 0) {
+        const uint64_t mask = (1ull << a.bits) - 1ull;
+        const bool take = lane < want && L != 0;
+        if (take) {
+            const uint32_t v = (uint32_t)(mask - (L & mask));
+            a.batch[lane] = v;
+            a.fresh[lane] = 0;
+            a.key[v] = lane;                       // its batch slot, until its fresh key
+            a.stamp[v] = round | kPending;
+        }
+        const unsigned cnt = __popc(__ballot_sync(kFull, take));
+        if (lane == 0) st->batch_n = cnt;
+    }
+}
+
 // One phase of the selection per launch (SelState::phase); the last block to finish runs the
 // phase's epilogue: the radix pick, the next phase, or -- after an evaluation -- the queued
 // fallback searches, the batch's fresh keys, MarkSeed's flag and the plan of the next step
@@ -1172,6 +1292,7 @@ k_sel_step(StepArgs a) {
         break;
     case PH_SEL_PASS: sel_pass_tasks(a, sm); break;
     case PH_GATHER: gather_tasks(a); break;
+    case PH_TOPB: topb_tasks(a, sm); break;
     case PH_SPEC_EVAL: spec_eval_tasks(a); break;
     case PH_COUNT: count_above_tasks(a); break;
     default: break;
@@ -1187,6 +1308,10 @@ k_sel_step(StepArgs a) {
     case PH_SEL_PASS:
         sel_pass_pick(st, sm);
         if (threadIdx.x == 0) st->phase = st->done ? PH_GATHER : PH_SEL_PASS;
+        return;
+    case PH_TOPB:
+        topb_pick(a, sm);
+        if (threadIdx.x == 0) st->phase = (st->mode == M_SPEC_GATHER || st->mode == M_SPEC_HIST) ? PH_SPEC_EVAL : PH_EVAL;
         return;
     case PH_GATHER:
         if (threadIdx.x == 0) {
@@ -1423,6 +1548,7 @@ StepArgs step_args(const im_ctx* c, const SelHandles& hd) {
     a.fb_cap = c->fb_cap;
     a.fb_slots = (c->all_centers || !c->d_fb_queue) ? 0u : c->fb_slots;
     a.n = c->n; a.R = c->R; a.bits = c->key_bits;
+    a.topb = c->d_topb;
     a.hd = hd;
     return a;
 }
@@ -1481,7 +1607,10 @@ int size_step_grid(im_ctx* c) {
     int per_sm = 0, sms = 0;
     IM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sel_step, kBlockWarps * 32, 0));
     IM_CUDA(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
-    c->step_grid = (unsigned)std::max(1, per_sm) * (unsigned)std::max(1, sms);
+    const unsigned grid = (unsigned)std::max(1, per_sm) * (unsigned)std::max(1, sms);
+    if (cudaMalloc(&c->d_topb, (size_t)grid * kTopB * sizeof(uint64_t)) != cudaSuccess)
+        return im_fail(c, IM_ENOMEM, "top-B scratch");
+    c->step_grid = grid;
     return IM_OK;
 }
 
