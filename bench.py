@@ -45,6 +45,23 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(values, dist, device):
+    """Each value's maximum over the ranks (the slowest replica decides the job's time);
+    unchanged without a process group."""
+    if dist is None:
+        return [float(x) for x in values]
+    import torch
+    t = torch.tensor([float(x) for x in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_rate(units_per_rank, ranks, seconds):
+    """Whole-job throughput of `ranks` replicas that each processed units_per_rank in at most
+    `seconds` (the max over ranks)."""
+    return units_per_rank * ranks / seconds
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -369,10 +386,7 @@ def run_ours(args, n, u, v, prm):
     ms_step = sum(times) / len(times)
     ms_build = sum(t_build) / len(t_build)
     ms_select = sum(t_select) / len(t_select)
-    if dist:
-        t = torch.tensor([ms_step, ms_build, ms_select], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step, ms_build, ms_select = t.tolist()
+    ms_step, ms_build, ms_select = max_over_ranks([ms_step, ms_build, ms_select], dist, "cuda")
 
     # Monte-Carlo influence of the selected seeds (the paper's quality measure), after the
     # timed region: MC_SIMS live-edge worlds of an independent hash seed.
@@ -411,10 +425,7 @@ def run_ours(args, n, u, v, prm):
         e2e_times.append(time.perf_counter() - t0)
     e2e_s = sum(e2e_times) / len(e2e_times)
     c2.close()
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks([e2e_s], dist, "cuda")[0]
 
     if rank == 0:
         peaks, peak_src = _peaks()
@@ -433,7 +444,7 @@ def run_ours(args, n, u, v, prm):
                                   ms_build, peaks, hash_peak, live_build)
         line = {
             "metric": METRIC,
-            "value": pairs * ws / (ms_step / 1e3),
+            "value": job_rate(pairs, ws, ms_step / 1e3),
             "unit": "pairs/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_step,
@@ -454,7 +465,7 @@ def run_ours(args, n, u, v, prm):
             "sketch_roofline": sk_roof,
             "kernel_rooflines": list(roofs.values()),
             "cpu_baseline": cpu,
-            "e2e": {"value": pairs * ws / e2e_s, "unit": "pairs/s",
+            "e2e": {"value": job_rate(pairs, ws, e2e_s), "unit": "pairs/s",
                     "h2d_bytes_per_step": 8 * m + (8 * m if pe is not None else 0),
                     "d2h_bytes_per_step": 12 * k + 8},
             "gpu_launches": launches,
