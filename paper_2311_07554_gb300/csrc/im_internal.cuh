@@ -144,7 +144,7 @@ struct SelState {
     unsigned long long prefix, prefmask, need, taken, theta, borig;
     int shift, done;
     unsigned int hist[256];
-    unsigned int pass_blocks;       // blocks of the current radix pass that have finished
+    unsigned int pad0;
     unsigned long long eval_next;   // task counter of the evaluation kernel
     unsigned int batch_n;
     unsigned int fb_n;              // fallback tasks queued

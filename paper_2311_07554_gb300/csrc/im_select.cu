@@ -527,7 +527,6 @@ __device__ void plan_step(SelState* st, uint32_t* __restrict__ batch, unsigned l
         st->taken = 0;
         st->prefix = 0;
         st->theta = 0;
-        st->pass_blocks = 0;
         bool hist = false, direct = false;
         if (nu <= 2 * B || smax == 0) {
             st->done = 1;                // take every unevaluated candidate
