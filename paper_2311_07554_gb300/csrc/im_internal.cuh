@@ -141,11 +141,12 @@ struct SelState {
     unsigned long long n_unev;      // number of unevaluated candidates
     unsigned long long count_above; // unevaluated candidates whose stale key beats best
     unsigned long long best_prev;   // best fresh key when the current batch was chosen
+    // radix selection of a batch (PH_SEL_PASS): key prefix so far, keys still to take, threshold
     unsigned long long prefix, prefmask, need, taken, theta, borig;
     int shift, done;
     unsigned int hist[256];
     unsigned int pad0;
-    unsigned long long eval_next;   // task counter of the evaluation kernel
+    unsigned long long eval_next;   // task counter of the chunk evaluation kernel
     unsigned int batch_n;
     unsigned int fb_n;              // fallback tasks queued
     unsigned int fb_overflow;
@@ -156,7 +157,7 @@ struct SelState {
     unsigned long long hop2_chunks;     // 32-arc chunks scanned by those searches
     unsigned int err;               // SelError: the selection stopped (the host reports it)
     unsigned int pad;
-    // round and batch control, decided on the device (k_plan / k_mark_seed)
+    // round and batch control, decided on the device (plan_step)
     unsigned int round;             // seeds chosen so far
     unsigned int round_end;         // stop after this many seeds
     unsigned int j;                 // batches evaluated in the current round
@@ -166,8 +167,8 @@ struct SelState {
     unsigned long long refresh_min; // batches at least this large are evaluated by refresh
     unsigned long long evals_mark;  // evals_total when the round started
     unsigned long long batches, refresh_batches;
-    unsigned long long launches;    // kernels launched by the selection graph
-    unsigned int ticket;            // blocks of k_reduce_plan done (the last one plans)
+    unsigned long long launches;    // kernels the selection graph launched
+    unsigned int ticket;            // blocks of the current launch done (the last one runs its epilogue)
     unsigned int pending;           // a batch was evaluated and awaits its accounting
     // candidate first seeds whose overlaps the build accumulated (M_SPEC evaluates round 1)
     unsigned int spec_count;
