@@ -1723,7 +1723,7 @@ int cap_conditional(im_ctx* c, cudaGraphConditionalHandle h, cudaGraphConditiona
 // so the phases of ordinary batches are launches of one kernel in a loop, not cases of a
 // switch.  The loop is bounded: a round ends after at most 82 batches, the selection after
 // round_end rounds.
-constexpr int kStepsPerLoop = 4;
+constexpr int kStepsPerLoop = 8;
 
 int build_select_graph_steps(im_ctx* c) {
     SelHandles hd{};
