@@ -144,8 +144,6 @@ struct SelState {
     // radix selection of a batch (PH_SEL_PASS): key prefix so far, keys still to take, threshold
     unsigned long long prefix, prefmask, need, taken, theta, borig;
     int shift, done;
-    unsigned int hist[256];
-    unsigned int pad0;
     unsigned long long eval_next;   // task counter of the chunk evaluation kernel
     unsigned int batch_n;
     unsigned int fb_n;              // fallback tasks queued
@@ -181,6 +179,8 @@ struct SelState {
     unsigned int pad2;
     unsigned long long above_bound; // unevaluated candidates above the best fresh key before the
                                     // last batch: an upper bound on count_above
+    // last: the radix pass histogram (plan_step never reads it, so its copy stops before it)
+    unsigned int hist[256];
 };
 
 enum SelError : unsigned int {

@@ -650,8 +650,8 @@ __device__ void plan_shared(SelState* st, uint32_t* __restrict__ batch, unsigned
                             uint32_t* __restrict__ seed_list, uint64_t* __restrict__ gain_list,
                             uint64_t* __restrict__ round_evals, uint32_t n, uint32_t R, uint32_t bits,
                             const SelHandles& hd, bool have_count) {
-    static_assert(sizeof(SelState) % 8 == 0, "state copied in 8-byte words");
-    constexpr uint32_t kWords = sizeof(SelState) / 8;
+    static_assert(offsetof(SelState, hist) % 8 == 0, "state copied in 8-byte words");
+    constexpr uint32_t kWords = offsetof(SelState, hist) / 8;   // everything but the histogram
     __shared__ SelState ss;
     unsigned long long* g = reinterpret_cast<unsigned long long*>(st);
     unsigned long long* l = reinterpret_cast<unsigned long long*>(&ss);
@@ -907,10 +907,25 @@ __device__ __forceinline__ void scan_all(const StepArgs& a, bool finalize, uint3
     scan_candidates(a, finalize, skip, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
-// Fresh keys of the batch members (last block, after the evaluation).
+// Fresh keys of the batch members (last block, after the evaluation; every thread calls it).
 __device__ void finalize_batch(const StepArgs& a) {
     SelState* st = a.st;
     const uint32_t round = st->round, bn = __ldcg(&st->batch_n);
+    if (bn <= 32) {   // one warp, no block barrier
+        if (threadIdx.x < 32) {
+            unsigned long long k = 0;
+            if (threadIdx.x < bn) {
+                const uint32_t x = a.batch[threadIdx.x];
+                k = pack_key(__ldcg(a.fresh + threadIdx.x), x, a.bits);
+                a.key[x] = k;
+                a.stamp[x] = round;
+            }
+#pragma unroll
+            for (int d = 16; d; d >>= 1) k = max(k, __shfl_xor_sync(kFull, k, d));
+            if (threadIdx.x == 0 && k) atomicMax(&st->best, k);
+        }
+        return;
+    }
     unsigned long long bf = 0, unused_b = 0, unused_c = 0, unused_e = 0;
     for (uint32_t j = threadIdx.x; j < bn; j += blockDim.x) {
         const uint32_t x = a.batch[j];
