@@ -331,6 +331,8 @@ int im_run_batch(im_instance* inst, uint32_t count, uint32_t workers);
  *                      answered, from the call's start.  Returns IM_OK, or the first failing
  *                      request's status (IM_EINVAL for a model id or k out of range).
  * im_server_destroy    stops the threads and frees every model.
+ * The control calls (create, add_model, replay, destroy) are made from one thread, one at a
+ * time; the engine's own threads only touch their model.
  */
 typedef struct im_server im_server;
 typedef struct {
