@@ -33,7 +33,7 @@ import graphgen  # noqa: E402
 METRIC = "sampled edge-sketch pairs/s"
 DEFAULT_WORKLOAD = "chunglu_n1M_m10M"
 CPU_SAMPLE_SKETCHES = 32        # per step of the reference arm (--impl reference)
-CPU_BASELINE_SKETCHES = 256     # the cpu_baseline of our arm: about 10 s of oracle work
+CPU_BASELINE_PAIRS = 2.56e9     # the cpu_baseline of our arm: about 10 s of oracle work
 PROFILES = ROOT / "profiles"
 SRC = ROOT / "paper_2311_07554_gb300" / "csrc"
 
@@ -437,7 +437,7 @@ def run_ours(args, n, u, v, prm):
         roofs = kernel_rooflines(prof, live_build, n, m, R, args.steps, peaks, peak_src, clk, hash_peak)
         roof = roofs.get(top[0]) or (max(roofs.values(), key=lambda r: r["share_of_device_time"])
                                      if roofs else None)
-        cpu = cpu_sample(n, u, v, prm, sketches=min(CPU_BASELINE_SKETCHES, R))
+        cpu = cpu_sample(n, u, v, prm, sketches=int(max(1, min(R, CPU_BASELINE_PAIRS // m))))
         p_mean = prm["p"] if pe is None and prm["probs"] == "uniform" else None
         if p_mean is None:
             p_mean = float(np.mean(pe)) if pe is not None else float(live_build) / (m * R * args.steps)
