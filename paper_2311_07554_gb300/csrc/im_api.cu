@@ -733,6 +733,7 @@ void im_destroy(im_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_sketch_state(c);
     dfree(c->d_edges); dfree(c->d_off); dfree(c->d_arcs); dfree(c->d_arc_cur); dfree(c->d_upload);
+    dfree(c->d_adj); dfree(c->d_src);
     if (c->h_upload) cudaFreeHost(c->h_upload);
     dfree(c->d_edgeT); dfree(c->d_arcT);
     dfree(c->d_spread_pairs); dfree(c->d_spread_seeds); dfree(c->d_spread_total); dfree(c->d_live_total);

@@ -67,11 +67,12 @@ __device__ __forceinline__ uint64_t arc_slot(bool valid, uint32_t x, bool to_cen
     return to_center ? off[x] + base : off[x + 1] - 1 - base;
 }
 
+// The static adjacency of a loaded graph (once per graph): every arc's neighbour and edge id
+// at a slot of its source's CSR range, and the source itself, so that the per-build fill can
+// stream the arcs in CSR order (consecutive arcs share their source).
 __global__ void __launch_bounds__(256)
-k_arc_fill(const uint2* __restrict__ edges, uint64_t m, const uint64_t* __restrict__ off,
-           uint32_t* __restrict__ ccur, uint32_t* __restrict__ ncur, uint4* __restrict__ arcs,
-           uint64_t salt, const uint32_t* __restrict__ cbits, const uint32_t* __restrict__ cidx,
-           int all_centers, const uint64_t* __restrict__ eT, uint64_t* __restrict__ aT) {
+k_adj_fill(const uint2* __restrict__ edges, uint64_t m, const uint64_t* __restrict__ off,
+           uint32_t* __restrict__ cur, uint2* __restrict__ adj, uint32_t* __restrict__ src) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     // the loop bound is uniform over the block, so every warp-wide call has all lanes
     for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < m; base += stride) {
@@ -79,22 +80,45 @@ k_arc_fill(const uint2* __restrict__ edges, uint64_t m, const uint64_t* __restri
         const bool valid = e < m;
         uint2 ed = make_uint2(0, 0);
         if (valid) ed = edges[e];
-        const uint64_t key = mix64(salt ^ e);
-        const bool cx = valid && (all_centers || ((cbits[ed.x >> 5] >> (ed.x & 31)) & 1u));
-        const bool cy = valid && (all_centers || ((cbits[ed.y >> 5] >> (ed.y & 31)) & 1u));
-        const uint64_t pa = arc_slot(valid, ed.x, cy, off, ccur, ncur);
-        const uint64_t pb = arc_slot(valid, ed.y, cx, off, ccur, ncur);
+        const uint64_t pa = arc_slot(valid, ed.x, true, off, cur, cur);
+        const uint64_t pb = arc_slot(valid, ed.y, true, off, cur, cur);
         if (valid) {
-            const uint32_t klo = (uint32_t)key, khi = (uint32_t)(key >> 32);
-            const uint32_t iy = !cy ? kNone : all_centers ? ed.y : cidx[ed.y];
-            const uint32_t ix = !cx ? kNone : all_centers ? ed.x : cidx[ed.x];
-            arcs[pa] = make_uint4(ed.y | ((cy ? 1u : 0u) << 31), iy, klo, khi);
-            arcs[pb] = make_uint4(ed.x | ((cx ? 1u : 0u) << 31), ix, klo, khi);
-            if (eT) {   // per-edge probabilities: each arc carries its edge's threshold
-                const uint64_t T = eT[e];
-                aT[pa] = T;
-                aT[pb] = T;
-            }
+            adj[pa] = make_uint2(ed.y, (uint32_t)e);
+            adj[pb] = make_uint2(ed.x, (uint32_t)e);
+            src[pa] = ed.x;
+            src[pb] = ed.y;
+        }
+    }
+}
+
+// Every build: the arcs of each vertex rewritten with the build's hash keys and center bits,
+// arcs to centers first (front cursor), the others from the back.  One thread per arc in CSR
+// order: the arcs of a warp mostly share their source, so a hub costs one cursor atomic per
+// 32 arcs (arc_slot merges equal (source, side) keys), not one per arc.
+__global__ void __launch_bounds__(256)
+k_arc_fill(const uint2* __restrict__ adj, const uint32_t* __restrict__ src, uint64_t narcs,
+           const uint64_t* __restrict__ off, uint32_t* __restrict__ ccur, uint32_t* __restrict__ ncur,
+           uint4* __restrict__ arcs, uint64_t salt, const uint32_t* __restrict__ cbits,
+           const uint32_t* __restrict__ cidx, int all_centers, const uint64_t* __restrict__ eT,
+           uint64_t* __restrict__ aT) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < narcs; base += stride) {
+        const uint64_t a = base + threadIdx.x;
+        const bool valid = a < narcs;
+        uint2 ye = make_uint2(0, 0);
+        uint32_t x = 0;
+        if (valid) {
+            ye = adj[a];
+            x = src[a];
+        }
+        const uint32_t y = ye.x;
+        const bool cy = valid && (all_centers || ((cbits[y >> 5] >> (y & 31)) & 1u));
+        const uint64_t p = arc_slot(valid, x, cy, off, ccur, ncur);
+        if (valid) {
+            const uint64_t key = mix64(salt ^ (uint64_t)ye.y);
+            const uint32_t iy = !cy ? kNone : all_centers ? y : cidx[y];
+            arcs[p] = make_uint4(y | ((cy ? 1u : 0u) << 31), iy, (uint32_t)key, (uint32_t)(key >> 32));
+            if (eT) aT[p] = eT[ye.y];   // per-edge probabilities: each arc carries its edge's threshold
         }
     }
 }
@@ -256,7 +280,9 @@ int im_graph_build(im_ctx* c, const uint32_t* d_u, const uint32_t* d_v) {
         // least the context's reserve
         im_select_graph_free(c);
         cudaFree(c->d_edges); cudaFree(c->d_off); cudaFree(c->d_arcs); cudaFree(c->d_arc_cur);
+        cudaFree(c->d_adj); cudaFree(c->d_src);
         c->d_edges = nullptr; c->d_off = nullptr; c->d_arcs = nullptr; c->d_arc_cur = nullptr;
+        c->d_adj = nullptr; c->d_src = nullptr;
         c->graph_n_alloc = 0;
         c->graph_m_alloc = 0;
         const uint32_t na = n > c->res_n ? n : c->res_n;
@@ -268,6 +294,9 @@ int im_graph_build(im_ctx* c, const uint32_t* d_u, const uint32_t* d_v) {
             return im_fail(c, IM_ENOMEM, "csr offsets");
         if (cudaMalloc(&c->d_arcs, (2 * ma + 2) * sizeof(uint4)) != cudaSuccess)
             return im_fail(c, IM_ENOMEM, "csr arcs");
+        if (cudaMalloc(&c->d_adj, (2 * ma + 2) * sizeof(uint2)) != cudaSuccess ||
+            cudaMalloc(&c->d_src, (2 * ma + 2) * sizeof(uint32_t)) != cudaSuccess)
+            return im_fail(c, IM_ENOMEM, "static adjacency");
         // two cursors per vertex for the arc fill; the first n + 5 words serve as degree scratch
         if (cudaMalloc(&c->d_arc_cur, (2 * (size_t)na + 8) * sizeof(uint32_t)) != cudaSuccess)
             return im_fail(c, IM_ENOMEM, "arc cursors");
@@ -300,6 +329,14 @@ int im_graph_build(im_ctx* c, const uint32_t* d_u, const uint32_t* d_v) {
         }
         rc = im_scan_u32_to_u64(c, deg, c->d_off, n);
         if (rc) break;
+        if (m > 0) {   // the static adjacency (the cursors start from 0 again)
+            if (cudaMemsetAsync(c->d_arc_cur, 0, (size_t)n * sizeof(uint32_t), c->stream) != cudaSuccess) {
+                rc = im_fail(c, IM_ECUDA, "memset");
+                break;
+            }
+            IM_LAUNCH(c, K_CSR_FILL, k_adj_fill, grid_for(m, B, 152u * 16u), B, 0, c->d_edges, m, c->d_off,
+                      c->d_arc_cur, c->d_adj, c->d_src);
+        }
         cudaError_t e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) rc = im_cuda_check(c, e, "csr build");
     } while (0);
@@ -338,9 +375,9 @@ int im_arc_keys(im_ctx* c, uint64_t salt) {
     if (c->m > 0) {
         const uint32_t n = c->n;
         IM_CUDA(c, cudaMemsetAsync(c->d_arc_cur, 0, 2 * (size_t)n * sizeof(uint32_t), c->stream));
-        IM_LAUNCH(c, K_ARC_KEYS, k_arc_fill, grid_for(c->m, 256, 152u * 16u), 256, 0, c->d_edges, c->m, c->d_off,
-                  c->d_arc_cur, c->d_arc_cur + n, c->d_arcs, salt, c->d_cbits, c->d_cidx, (int)c->all_centers,
-                  c->smp.eT, c->d_arcT);
+        IM_LAUNCH(c, K_ARC_KEYS, k_arc_fill, grid_for(2 * c->m, 256, 152u * 16u), 256, 0, c->d_adj, c->d_src,
+                  2 * c->m, c->d_off, c->d_arc_cur, c->d_arc_cur + n, c->d_arcs, salt, c->d_cbits, c->d_cidx,
+                  (int)c->all_centers, c->smp.eT, c->d_arcT);
     }
     IM_CUDA(c, cudaGetLastError());
     c->arc_salt = salt;

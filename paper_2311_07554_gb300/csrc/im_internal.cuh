@@ -260,6 +260,8 @@ struct im_ctx {
     uint2* d_edges = nullptr;
     uint64_t* d_off = nullptr;
     uint4* d_arcs = nullptr;
+    uint2* d_adj = nullptr;          // static adjacency: (neighbour, edge id) per arc, CSR order
+    uint32_t* d_src = nullptr;       // ... and its source
     uint32_t* d_arc_cur = nullptr;
     uint32_t graph_n_alloc = 0;      // n, m the graph buffers were allocated for
     uint64_t graph_m_alloc = 0;
