@@ -82,7 +82,8 @@ __global__ void k_iota(uint32_t* p, uint32_t cnt) {
 void resolve_events(im_ctx* c) {
     if (c->ev_pending.empty()) return;
     cudaStreamSynchronize(c->stream);
-    if (c->lane_stream1) cudaStreamSynchronize(c->lane_stream1);
+    for (uint32_t i = 1; i < kMaxLanes; ++i)
+        if (c->lane_stream[i]) cudaStreamSynchronize(c->lane_stream[i]);
     for (auto& pe : c->ev_pending) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, c->ev_pool[pe.second.first], c->ev_pool[pe.second.second]) == cudaSuccess)
@@ -228,16 +229,18 @@ int im_create_reserved(im_ctx** out, uint32_t n, uint64_t m, const uint32_t* u, 
         c->own_stream = true;
     }
     c->cur = c->stream;
-    if (cudaStreamCreateWithFlags(&c->lane_stream1, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_spec, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    bool made = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+                cudaEventCreateWithFlags(&c->ev_spec, cudaEventDisableTiming) == cudaSuccess;
+    for (uint32_t i = 1; i < kMaxLanes && made; ++i)
+        made = cudaStreamCreateWithFlags(&c->lane_stream[i], cudaStreamNonBlocking) == cudaSuccess &&
+               cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!made) {
         g_create_error = "stream or event creation failed";
         im_destroy(c);
         return IM_ECUDA;
     }
     c->lane[0].stream = c->stream;
-    c->lane[1].stream = c->lane_stream1;
+    for (uint32_t i = 1; i < kMaxLanes; ++i) c->lane[i].stream = c->lane_stream[i];
     int rc = IM_OK;
     do {
         if (cudaMalloc(&c->d_sel, sizeof(SelState)) != cudaSuccess ||
@@ -300,7 +303,7 @@ int im_set_graph(im_ctx* c, int on) {
 
 int im_set_pipeline(im_ctx* c, uint32_t lanes) {
     if (!c) return IM_EINVAL;
-    if (lanes != 1 && lanes != 2) return im_fail(c, IM_EINVAL, "lanes must be 1 or 2");
+    if (lanes < 1 || lanes > kMaxLanes) return im_fail(c, IM_EINVAL, "lanes must be 1 or 2");
     c->lanes = lanes;
     return IM_OK;
 }
@@ -456,14 +459,15 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
                   dalloc(c->d_seed_list, na) && dalloc(c->d_labcache, (size_t)kLabSlots * Ra) &&
                   dalloc(c->d_gain_list, na) && dalloc(c->d_round_evals, na) &&
                   dalloc(c->d_label, nca) && dalloc(c->d_size, nca) &&
-                  dalloc(c->lane[0].parent, (size_t)B * na) && dalloc(c->lane[0].word, (size_t)B * na) &&
-                  dalloc(c->lane[1].parent, (size_t)B * na) && dalloc(c->lane[1].word, (size_t)B * na) &&
-                  dalloc(c->lane[1].gain, na) && dalloc(c->lane[1].fresh, na);
-        if (ok && nsa) ok = dalloc(c->lane[0].spec_ov, (size_t)nsa * na) && dalloc(c->lane[1].spec_ov, (size_t)nsa * na);
+                  dalloc(c->lane[0].parent, (size_t)B * na) && dalloc(c->lane[0].word, (size_t)B * na);
+        for (uint32_t i = 1; i < kMaxLanes && ok; ++i)
+            ok = dalloc(c->lane[i].parent, (size_t)B * na) && dalloc(c->lane[i].word, (size_t)B * na) &&
+                 dalloc(c->lane[i].gain, na) && dalloc(c->lane[i].fresh, na);
+        for (uint32_t i = 0; i < kMaxLanes && ok && nsa; ++i) ok = dalloc(c->lane[i].spec_ov, (size_t)nsa * na);
         if (ok && livea) {
             c->live_cap = livea;
-            ok = dalloc(c->lane[0].live, c->live_cap) && dalloc(c->lane[0].live_n, 1) &&
-                 dalloc(c->lane[1].live, c->live_cap) && dalloc(c->lane[1].live_n, 1);
+            for (uint32_t i = 0; i < kMaxLanes && ok; ++i)
+                ok = dalloc(c->lane[i].live, c->live_cap) && dalloc(c->lane[i].live_n, 1);
         }
         if (ok && compact) {
             const size_t nw = ((size_t)na + 31) / 32;
@@ -745,11 +749,13 @@ void im_destroy(im_ctx* c) {
     dfree(c->d_spec_keys);
     dfree(c->d_spec_ids);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
-    if (c->lane_stream1) { cudaStreamSynchronize(c->lane_stream1); cudaStreamDestroy(c->lane_stream1); }
+    for (uint32_t i = 1; i < kMaxLanes; ++i) {
+        if (c->lane_stream[i]) { cudaStreamSynchronize(c->lane_stream[i]); cudaStreamDestroy(c->lane_stream[i]); }
+        if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
+    }
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_spec) cudaEventDestroy(c->ev_spec);
-    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }

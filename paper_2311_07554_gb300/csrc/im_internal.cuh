@@ -22,6 +22,7 @@ constexpr uint32_t kArcIdMask = 0x7FFFFFFFu;            // arc word 0: neighbour
 constexpr uint32_t kLabSlots = 256;                     // label cache: vertex slots (x mod 256)
 constexpr size_t kCenterSelBytes = 4096;                // device state of the center radix select
 constexpr uint32_t kHubsAuto = 0xFFFFFFFFu;                // im_ctx::hub_cap default
+constexpr uint32_t kMaxLanes = 2;                          // sketch batches in flight at most (a third lane measured no faster)
 constexpr uint32_t kSpecMax = 8;                        // candidate first seeds (see im_ctx::spec_req)
 
 // splitmix64 output finaliser (Steele, Lea, Flood 2014).
@@ -347,9 +348,10 @@ struct im_ctx {
         unsigned long long* fresh = nullptr;     // lane 1: its share of a refresh evaluation
         uint64_t* spec_ov = nullptr;             // [spec][n] overlap sums (lane 0's is the total)
     };
-    Lane lane[2];
-    cudaStream_t lane_stream1 = nullptr;         // owned
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_spec = nullptr;
+    Lane lane[imk::kMaxLanes];
+    cudaStream_t lane_stream[imk::kMaxLanes] = {};    // lanes 1.. (owned); lane 0 is the context stream
+    cudaEvent_t ev_fork = nullptr, ev_spec = nullptr;
+    cudaEvent_t ev_join[imk::kMaxLanes] = {};
     cudaStream_t cur = nullptr;                  // stream the next launch goes to
     uint32_t lanes = 2;                          // sketch batches alternate between two streams
     uint32_t batch_req = 0, batch_used = 0, batch_alloc = 0;

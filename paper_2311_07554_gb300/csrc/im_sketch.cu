@@ -722,18 +722,20 @@ __global__ void k_add_u64(unsigned long long* __restrict__ dst, const unsigned l
         dst[i] += src[i];
 }
 
-// Lane 1 starts after everything queued so far on the context stream ...
-int lanes_fork(im_ctx* c) {
+// Lanes 1.. start after everything queued so far on the context stream ...
+int lanes_fork(im_ctx* c, uint32_t lanes) {
     IM_CUDA(c, cudaEventRecord(c->ev_fork, c->stream));
-    IM_CUDA(c, cudaStreamWaitEvent(c->lane_stream1, c->ev_fork, 0));
+    for (uint32_t i = 1; i < lanes; ++i) IM_CUDA(c, cudaStreamWaitEvent(c->lane_stream[i], c->ev_fork, 0));
     return IM_OK;
 }
 
-// ... and the context stream continues after everything queued on lane 1.
-int lanes_join(im_ctx* c) {
+// ... and the context stream continues after everything queued on the other lanes.
+int lanes_join(im_ctx* c, uint32_t lanes) {
     c->cur = c->stream;
-    IM_CUDA(c, cudaEventRecord(c->ev_join, c->lane_stream1));
-    IM_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    for (uint32_t i = 1; i < lanes; ++i) {
+        IM_CUDA(c, cudaEventRecord(c->ev_join[i], c->lane_stream[i]));
+        IM_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_join[i], 0));
+    }
     return IM_OK;
 }
 
@@ -787,28 +789,29 @@ int im_select_hubs(im_ctx* c, uint32_t* d_flags, uint64_t* d_pos) {
 }
 
 // Build all R sketches batch by batch; writes gain0, label, size.  Batch i runs on lane
-// i mod lanes; lane 1 (if used) accumulates its gains separately, added at the end.
+// i mod lanes; lanes 1.. accumulate their gains (and overlap sums) separately, added at the end.
 int im_sketch_batches(im_ctx* c) {
-    const uint32_t n = c->n, R = c->R;
+    const uint32_t n = c->n, R = c->R, lanes = c->lanes;
     const unsigned T = 256;
-    int rc = lanes_fork(c);
+    int rc = lanes_fork(c, lanes);
     if (rc) return rc;
-    // lane 1 sums its overlaps in a buffer of its own (added at the end)
-    if (c->lanes > 1 && c->spec_count)
-        IM_CUDA(c, cudaMemsetAsync(c->lane[1].spec_ov, 0, (size_t)c->spec_count * n * sizeof(uint64_t),
-                                   c->lane_stream1));
+    // lanes 1.. sum their overlaps in buffers of their own
+    for (uint32_t li = 1; li < lanes && c->spec_count; ++li)
+        IM_CUDA(c, cudaMemsetAsync(c->lane[li].spec_ov, 0, (size_t)c->spec_count * n * sizeof(uint64_t),
+                                   c->lane_stream[li]));
     uint32_t i = 0;
     for (uint32_t r0 = 0; r0 < R; r0 += c->batch_used, ++i) {
         const uint32_t nb = R - r0 < c->batch_used ? R - r0 : c->batch_used;
-        im_ctx::Lane& L = c->lane[i % c->lanes];
+        const uint32_t li = i % lanes;
+        im_ctx::Lane& L = c->lane[li];
         c->cur = L.stream;
         rc = batch_components(c, L, r0, nb, c->all_centers ? 0 : 1);
-        if (rc) { lanes_join(c); return rc; }
-        uint64_t* gain = (i % c->lanes) ? L.gain : c->d_gain0;
-        const int first = i < c->lanes ? 1 : 0;
+        if (rc) { lanes_join(c, lanes); return rc; }
+        uint64_t* gain = li ? L.gain : c->d_gain0;
+        const int first = i < lanes ? 1 : 0;
         const uint32_t nspec = i ? c->spec_count : 0;   // candidates are known after batch 0
-        // the candidates come from batch 0 (lane 0): lane 1's first gain pass waits for them
-        if (nspec && (i % c->lanes) && i < c->lanes) IM_CUDA(c, cudaStreamWaitEvent(L.stream, c->ev_spec, 0));
+        // the candidates come from batch 0 (lane 0): another lane's first gain pass waits for them
+        if (nspec && li && i < lanes) IM_CUDA(c, cudaStreamWaitEvent(L.stream, c->ev_spec, 0));
 #define IM_GAIN(ALL, K)                                                                             \
     if (ALL)                                                                                        \
         IM_LAUNCH(c, K_GAIN_COMPACT, (k_gain_full<K>), grid_for(n, 32, 152u * 8u), kGainWarps * 32, 0, L.parent, \
@@ -841,15 +844,15 @@ int im_sketch_batches(im_ctx* c) {
                       c->d_spec_ids, c->spec_count, c->lane[0].spec_ov);
         }
     }
-    rc = lanes_join(c);
+    rc = lanes_join(c, lanes);
     if (rc) return rc;
-    if (c->lanes > 1 && i > 1) {
+    for (uint32_t li = 1; li < lanes && li < i; ++li) {   // the lanes that ran a batch
         IM_LAUNCH(c, K_GAIN_COMPACT, k_add_u64, grid_for(n, T, 152u * 8u), T, 0,
-                  (unsigned long long*)c->d_gain0, (const unsigned long long*)c->lane[1].gain, (uint64_t)n,
+                  (unsigned long long*)c->d_gain0, (const unsigned long long*)c->lane[li].gain, (uint64_t)n,
                   (const unsigned int*)nullptr);
         if (c->spec_count)
             IM_LAUNCH(c, K_GAIN_COMPACT, k_add_u64, grid_for((uint64_t)c->spec_count * n, T, 152u * 8u), T, 0,
-                      (unsigned long long*)c->lane[0].spec_ov, (const unsigned long long*)c->lane[1].spec_ov,
+                      (unsigned long long*)c->lane[0].spec_ov, (const unsigned long long*)c->lane[li].spec_ov,
                       (uint64_t)c->spec_count * n, (const unsigned int*)nullptr);
     }
     IM_CUDA(c, cudaGetLastError());
@@ -879,21 +882,22 @@ int im_refresh_eval(im_ctx* c, const uint32_t* d_batch, const unsigned int* d_ba
     const unsigned T = 256;
     // The member count and the seed count are read on the device, so the launches do not
     // depend on them and the sequence can be captured in the selection graph.  Captured, it
-    // stays on the capturing stream (one lane); otherwise two lanes may alternate.
+    // stays on the capturing stream (one lane); otherwise the lanes alternate.
     const uint32_t lanes = (c->capturing || c->count_only) ? 1u : c->lanes;
     cudaStream_t s0 = c->cur;
     int rc = IM_OK;
     if (lanes > 1) {
-        rc = lanes_fork(c);
+        rc = lanes_fork(c, lanes);
         if (rc) return rc;
-        IM_CUDA(c, cudaMemsetAsync(c->lane[1].fresh, 0, (size_t)n * sizeof(uint64_t), c->lane_stream1));
+        for (uint32_t li = 1; li < lanes; ++li)
+            IM_CUDA(c, cudaMemsetAsync(c->lane[li].fresh, 0, (size_t)n * sizeof(uint64_t), c->lane_stream[li]));
     }
     uint32_t i = 0;
     for (uint32_t r0 = 0; r0 < R; r0 += c->batch_used, ++i) {
         const uint32_t nb = R - r0 < c->batch_used ? R - r0 : c->batch_used;
         const uint32_t li = i % lanes;
         im_ctx::Lane& L = c->lane[li];
-        c->cur = li ? c->lane_stream1 : s0;
+        c->cur = li ? c->lane_stream[li] : s0;
         rc = batch_components(c, L, r0, nb, 2);
         if (rc) break;
         IM_LAUNCH(c, K_COVER_ROOTS, k_cover_roots, 152u * 4u, T, 0, L.parent, L.word, n, nb, d_seeds,
@@ -903,11 +907,11 @@ int im_refresh_eval(im_ctx* c, const uint32_t* d_batch, const unsigned int* d_ba
     }
     c->cur = s0;
     if (lanes > 1) {
-        const int rj = lanes_join(c);
+        const int rj = lanes_join(c, lanes);
         if (!rc) rc = rj;
-        if (!rc && i > 1)
+        for (uint32_t li = 1; li < lanes && li < i && !rc; ++li)
             IM_LAUNCH(c, K_REFRESH_GATHER, k_add_u64, grid_for(n, T, 152u * 8u), T, 0, d_fresh,
-                      (const unsigned long long*)c->lane[1].fresh, (uint64_t)0, d_batch_n);
+                      (const unsigned long long*)c->lane[li].fresh, (uint64_t)0, d_batch_n);
     }
     return rc;
 }
