@@ -177,7 +177,8 @@ struct SelState {
     unsigned int phase;             // SelPhase: what the next k_sel_step launch does
     unsigned int rare;              // SelRare: an evaluator outside k_sel_step is due
     unsigned int topb;              // batch size PH_TOPB selects (0: radix passes and a gather)
-    unsigned int pad2;
+    unsigned int cond[3];           // the values last given to the graph's outer, inner and rare
+                                    // conditions (a call to set one is skipped when unchanged)
     unsigned long long above_bound; // unevaluated candidates above the best fresh key before the
                                     // last batch: an upper bound on count_above
     // last: the radix pass histogram (plan_step never reads it, so its copy stops before it)

@@ -438,6 +438,15 @@ __device__ __forceinline__ unsigned first_phase(unsigned mode) {
     }
 }
 
+// A graph condition set from the device, skipped when it already holds the value (each call
+// costs a device-runtime round trip; the loops' values rarely change).
+__device__ __forceinline__ void set_cond(SelState* st, int which, cudaGraphConditionalHandle h, unsigned v) {
+    if (st->cond[which] != v) {
+        cudaGraphSetConditional(h, v);
+        st->cond[which] = v;
+    }
+}
+
 // The next step is `mode`: its first phase, and the graph's loops entered (or left).
 __device__ void set_step(SelState* st, const SelHandles& hd, unsigned mode) {
     unsigned ph = first_phase(mode);
@@ -445,9 +454,9 @@ __device__ void set_step(SelState* st, const SelHandles& hd, unsigned mode) {
     st->phase = ph;
     st->rare = RARE_NONE;
     if (hd.on) {
-        cudaGraphSetConditional(hd.outer, ph != PH_NONE ? 1u : 0u);
-        cudaGraphSetConditional(hd.inner, ph != PH_NONE ? 1u : 0u);
-        cudaGraphSetConditional(hd.rare, RARE_NONE);
+        set_cond(st, 0, hd.outer, ph != PH_NONE ? 1u : 0u);
+        set_cond(st, 1, hd.inner, ph != PH_NONE ? 1u : 0u);
+        set_cond(st, 2, hd.rare, RARE_NONE);
     }
 }
 
@@ -457,8 +466,8 @@ __device__ void set_rare(SelState* st, const SelHandles& hd, unsigned rare) {
     st->rare = rare;
     atomicAdd(&st->launches, (unsigned long long)hd.rare_launches[rare]);   // block 0 counts concurrently
     if (hd.on) {
-        cudaGraphSetConditional(hd.inner, 0u);
-        cudaGraphSetConditional(hd.rare, rare);
+        set_cond(st, 1, hd.inner, 0u);
+        set_cond(st, 2, hd.rare, rare);
     }
 }
 
@@ -1404,10 +1413,13 @@ __global__ void k_sel_begin(SelState* st, SelHandles hd) {
         st->launches += 1;
         st->phase = go ? PH_SCAN : PH_NONE;
         st->rare = RARE_NONE;
-        if (hd.on) {
+        if (hd.on) {   // every launch of the graph starts from these values
             cudaGraphSetConditional(hd.outer, go);
             cudaGraphSetConditional(hd.inner, go);
             cudaGraphSetConditional(hd.rare, RARE_NONE);
+            st->cond[0] = go;
+            st->cond[1] = go;
+            st->cond[2] = RARE_NONE;
         }
     }
 }
