@@ -232,7 +232,7 @@ def sketch_roofline(prof, n, m, R, B, p_mean, alpha, steps, sketch_ms, peaks, ha
     out = {"model_bytes_per_build": model_bytes, "hbm_floor_ms": hbm_floor_ms, "sketch_ms": sketch_ms,
            "frac_of_hbm_roofline": hbm_floor_ms / sketch_ms, "alu_floor_ms": alu_floor_ms,
            "frac_of_alu_floor": alu_floor_ms / sketch_ms, "peak_gbs": hbm,
-           "note": "modelled bytes as SURVEY 8(d); the hashing's ALU floor is above the HBM floor"}
+           "note": "modelled bytes per sketch 8m/B + 2pm*32 + 20n + 8rho, + 8n per build; the hashing's ALU floor is above the HBM floor"}
     if measured is not None:
         gbs = measured / steps / (sketch_ms / 1e3) / 1e9
         out["ncu_dram_bytes_per_build"] = measured / steps
