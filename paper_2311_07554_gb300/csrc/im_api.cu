@@ -50,6 +50,7 @@ void free_sketch_state(im_ctx* c) {
     dfree(c->d_label); dfree(c->d_size); dfree(c->d_gain0);
     dfree(c->d_key); dfree(c->d_stamp); dfree(c->d_seedflag);
     dfree(c->d_batch); dfree(c->d_fresh); dfree(c->d_seed_list); dfree(c->d_labcache);
+    dfree(c->d_pair_undo);
     dfree(c->d_gain_list); dfree(c->d_round_evals);
     im_select_graph_free(c);   // the graph holds pointers to the buffers freed here
     for (auto& L : c->lane) {
@@ -457,6 +458,7 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
         bool ok = dalloc(c->d_gain0, na) && dalloc(c->d_key, na) && dalloc(c->d_stamp, na) &&
                   dalloc(c->d_seedflag, na) && dalloc(c->d_batch, na) && dalloc(c->d_fresh, na) &&
                   dalloc(c->d_seed_list, na) && dalloc(c->d_labcache, (size_t)kLabSlots * Ra) &&
+                  dalloc(c->d_pair_undo, Ra) &&
                   dalloc(c->d_gain_list, na) && dalloc(c->d_round_evals, na) &&
                   dalloc(c->d_label, nca) && dalloc(c->d_size, nca) &&
                   dalloc(c->lane[0].parent, (size_t)B * na) && dalloc(c->lane[0].word, (size_t)B * na);

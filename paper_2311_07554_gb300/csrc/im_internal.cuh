@@ -119,13 +119,14 @@ struct SketchView {
     uint32_t* size;          // [rho + hubs][R], bit 31 = covered by a seed
     const uint8_t* seed_flag;
     uint32_t pend;           // a seed whose flag is being set concurrently (kNone: none)
+    uint32_t pend2;          // a second one: the candidate assumed to win (kNone: none)
     uint64_t* labcache;      // [kLabSlots][R] labels found by searches, reused by MarkSeed
     Sampler smp;
 };
 
-// Whether x is a seed: its flag, or the seed a MarkSeed running in the same kernel is adding.
+// Whether x is a seed: its flag, or a seed a step running in the same kernel is adding.
 __device__ __forceinline__ bool is_seed(const SketchView& s, uint32_t x) {
-    return s.seed_flag[x] || x == s.pend;
+    return s.seed_flag[x] || x == s.pend || x == s.pend2;
 }
 
 __device__ __forceinline__ bool is_center(const SketchView& s, uint32_t x) {
@@ -181,6 +182,15 @@ struct SelState {
                                     // conditions (a call to set one is skipped when unchanged)
     unsigned long long above_bound; // unevaluated candidates above the best fresh key before the
                                     // last batch: an upper bound on count_above
+    unsigned long long stale_2nd;   // second largest stale key over the unevaluated candidates
+    // a round evaluated ahead (M_MARK_PAIR): the next round's only candidate, evaluated as if
+    // the current round's candidate had won; its stale key, and whether a search overflowed
+    unsigned long long pair_kz;
+    unsigned int pair;
+    unsigned int pair_fail;
+    unsigned int pair_penalty;      // grows when y lost, decays when it won or no pair ran: pairs
+                                    // run while it is below kPairOff
+    unsigned int pad2;
     // last: the radix pass histogram (plan_step never reads it, so its copy stops before it)
     unsigned int hist[256];
 };
@@ -206,7 +216,11 @@ enum SelMode : unsigned int {
     M_MARK = 11,          // MarkSeed of the last round's winner, then the next round opens
     M_MARK_DIRECT = 12,   // MarkSeed of the last round's winner fused with a B = 1 batch
     M_COUNT = 13,
-    M_NONE = 14           // nothing: the selection is over
+    M_NONE = 14,          // nothing: the selection is over
+    // M_MARK_DIRECT that also evaluates the second largest stale key z as the next round's
+    // first batch, assuming the top key y wins this round (MarkSeed(y) applied in each sketch
+    // after y's Marginal there, undone if y loses)
+    M_MARK_PAIR = 15
 };
 
 // Phases of k_sel_step.  A batch of mode M runs as a few of them in a row: radix passes
@@ -309,6 +323,7 @@ struct im_ctx {
     imk::SelState* h_sel = nullptr;  // pinned mirror
     uint32_t* d_seed_list = nullptr;   // seeds chosen so far, on the device (n entries)
     uint64_t* d_labcache = nullptr;    // [kLabSlots][R]: (vertex << 32) | label found by GetCenter
+    uint32_t* d_pair_undo = nullptr;   // [R]: the size row an M_MARK_PAIR step covered, else kNone
     uint64_t refresh_min = 0;          // batches at least this large are evaluated by refresh
     uint64_t refresh_req = 0;          // user setting (0 = automatic)
     std::vector<uint32_t> seeds;

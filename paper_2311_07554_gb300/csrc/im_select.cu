@@ -421,6 +421,10 @@ __global__ void k_init_keys(const uint64_t* __restrict__ gain0, uint32_t n, uint
 
 
 constexpr uint32_t kPending = 0x80000000u;   // stamp bit: batch member awaiting its fresh key
+// M_MARK_PAIR steps pay off when the evaluated-ahead round is usually taken: a lost pair adds
+// kPairLoss to the penalty, a taken one shrinks it by a quarter, and a round that could have
+// had a pair but was refused takes kPairRetry off, so that pairs are tried again after a while
+constexpr uint32_t kPairOff = 64, kPairLoss = 96, kPairRetry = 4;
 constexpr uint32_t kTopB = 32;               // largest batch PH_TOPB selects (one key per lane)
 
 // The first phase of a step of the given mode (PH_NONE: the selection is over).
@@ -428,7 +432,7 @@ __device__ __forceinline__ unsigned first_phase(unsigned mode) {
     switch (mode) {
     case M_ROUND_START: return PH_SCAN;
     case M_MARK: return PH_MARK;
-    case M_MARK_DIRECT: return PH_MARK_EVAL;
+    case M_MARK_DIRECT: case M_MARK_PAIR: return PH_MARK_EVAL;
     case M_COUNT_ABOVE: return PH_COUNT;
     case M_DIRECT: return PH_EVAL;
     case M_SPEC_DIRECT: return PH_SPEC_EVAL;
@@ -471,6 +475,88 @@ __device__ void set_rare(SelState* st, const SelHandles& hd, unsigned rare) {
     }
 }
 
+// The outcome of an M_MARK_PAIR step: MarkSeed(x), then in each sketch y's Marginal, MarkSeed(y)
+// and z's Marginal with x and y as seeds (z: the largest stale key after y's).  Every other
+// stale key is at most z's, so y wins its round iff its fresh key beats z's stale key.  If y
+// wins, the state becomes what an M_MARK_DIRECT step for y followed by one for z would leave:
+// y's round closed and recorded, z's round opened with z evaluated (the step's scan left out
+// x, y and z, as the second step's would).  If a search of the step overflowed, z's value is
+// incomplete: y's round is closed and the next step marks y everywhere (MarkSeed is
+// idempotent) and opens z's round afresh.  If y loses, z's value is dropped (the step's
+// epilogue has undone y's marks) and the round goes on from y's batch with z among the
+// unevaluated candidates.  Returns true if the next step is already set.
+__device__ bool pair_resolve(SelState* st, uint32_t* __restrict__ batch, unsigned long long* __restrict__ fresh,
+                             uint64_t* __restrict__ key, uint32_t* __restrict__ stamp, uint8_t* __restrict__ seedflag,
+                             uint32_t* __restrict__ seed_list, uint64_t* __restrict__ gain_list,
+                             uint64_t* __restrict__ round_evals, uint32_t n, uint32_t bits, const SelHandles& hd) {
+    st->pair = 0;
+    const bool fail = st->pair_fail != 0;
+    st->pair_fail = 0;
+    const uint32_t y = batch[0], z = batch[1];
+    const unsigned long long fy = key[y];   // finalised by the step
+    if (st->err || st->fb_overflow) return false;   // the selection stops
+    const bool won = fy > st->pair_kz;
+    st->pair_penalty = (won && !fail) ? st->pair_penalty - st->pair_penalty / 4 : min(st->pair_penalty + kPairLoss, 1024u);
+    if (!won) {
+        // y loses: z is an unevaluated candidate again, the largest left
+        st->stale_2nd = st->stale_max;
+        st->stale_max = st->pair_kz;
+        st->n_unev += 1;
+        st->above_bound += 1;   // best_prev is 0 for this batch
+        return false;
+    }
+    // y's batch accounted and its round closed, as plan_step does
+    st->pending = 0;
+    st->evals_total += 1;
+    st->fb_total += min(st->fb_n, 0xFFFFFFFFu);
+    st->fb_n = 0;
+    const uint32_t rd = st->round;
+    st->sd = y;
+    seed_list[rd] = y;
+    gain_list[rd] = fy >> bits;
+    round_evals[rd] = st->evals_total - st->evals_mark;
+    st->round = rd + 1;
+    st->evals_mark = st->evals_total;
+    seedflag[y] = 1;   // its components are marked (or it is the pending seed of its searches)
+    key[y] = 0;
+    if (fail) {
+        st->j = 0;
+        st->best = 0;
+        st->stale_max = 0;
+        st->stale_2nd = 0;
+        st->n_unev = 0;
+        st->above_bound = 0;
+        st->count_above = 0;
+        st->cont = 1;
+        st->mode = M_MARK;
+        set_step(st, hd, M_MARK);
+        return true;
+    }
+    // z's round: its first batch {z} is evaluated
+    const unsigned long long fz = pack_key(fresh[1], z, bits);
+    key[z] = fz;
+    stamp[z] = rd + 1;
+    batch[0] = z;
+    fresh[0] = fresh[1];
+    st->batch_n = 1;
+    st->eval_next = 0;
+    st->best_prev = 0;
+    st->borig = 1;
+    st->need = 1;
+    st->taken = 0;
+    st->prefix = 0;
+    st->theta = st->pair_kz;
+    st->shift = 0;
+    st->prefmask = 0;
+    st->done = 1;
+    st->pending = 1;
+    st->j = 1;
+    st->batches++;
+    st->best = fz;
+    st->count_above = 0;
+    return false;
+}
+
 // Next step of the round, decided from the state the last reduction left (Alg. 2's stop
 // test; Alg. 4's doubling batch size): either a batch of ~B of the largest stale keys, picked
 // by radix selection on the key bytes below the top byte of stale_max (all of them when at
@@ -480,17 +566,21 @@ __device__ void set_rare(SelState* st, const SelHandles& hd, unsigned rare) {
 // best fresh key, which a first M_COUNT_ABOVE step counts.  Errors stop the selection.  Run
 // by one thread; sets the selection graph's batch loop and batch switch.
 __device__ void plan_step(SelState* st, uint32_t* __restrict__ batch, unsigned long long* __restrict__ fresh,
-                          uint64_t* __restrict__ key, uint32_t* __restrict__ stamp,
+                          uint64_t* __restrict__ key, uint32_t* __restrict__ stamp, uint8_t* __restrict__ seedflag,
                           uint32_t* __restrict__ seed_list, uint64_t* __restrict__ gain_list,
                           uint64_t* __restrict__ round_evals, uint32_t n, uint32_t R, uint32_t bits,
                           const SelHandles& hd, bool have_count) {
-    unsigned cont = 0, mode = M_NONE;
-    const unsigned long long nu = st->n_unev, smax = st->stale_max, best = st->best;
-    const unsigned j = st->j;
     const uint64_t mask = (1ull << bits) - 1ull;
+    if (st->pair && pair_resolve(st, batch, fresh, key, stamp, seedflag, seed_list, gain_list, round_evals, n, bits,
+                                 hd))
+        return;
+    unsigned cont = 0, mode = M_NONE;
+    const unsigned long long nu = st->n_unev, smax = st->stale_max, best = st->best, s2 = st->stale_2nd;
+    const unsigned j = st->j;
     if (j == 0 && st->round >= st->round_end) {   // every requested seed is chosen and marked
         st->best = 0;                              // a later run opens this round again
         st->stale_max = 0;
+        st->stale_2nd = 0;
         st->n_unev = 0;
         st->above_bound = 0;
         st->count_above = 0;
@@ -561,6 +651,7 @@ __device__ void plan_step(SelState* st, uint32_t* __restrict__ batch, unsigned l
         st->best_prev = best;
         st->best = 0;
         st->stale_max = 0;
+        st->stale_2nd = 0;
         st->n_unev = 0;
         st->above_bound = 0;
         st->count_above = 0;
@@ -615,6 +706,7 @@ __device__ void plan_step(SelState* st, uint32_t* __restrict__ batch, unsigned l
             st->evals_mark = st->evals_total;
             st->best = 0;
             st->stale_max = 0;
+            st->stale_2nd = 0;
             st->n_unev = 0;
             st->above_bound = 0;
             st->count_above = 0;
@@ -642,6 +734,18 @@ __device__ void plan_step(SelState* st, uint32_t* __restrict__ batch, unsigned l
                 st->j = 1;
                 st->batches++;
                 mode = M_MARK_DIRECT;
+                // the round after it too, if it needs one: its first batch is the second
+                // largest stale key z, evaluated in the same step as if y wins
+                const bool pair_ok = st->pair_penalty < kPairOff;
+                if (!pair_ok) st->pair_penalty -= min(st->pair_penalty, kPairRetry);
+                if (pair_ok && rd + 2 < st->round_end && nu > 3 && s2 > 0 && st->refresh_min > 3) {
+                    batch[1] = (uint32_t)(mask - (s2 & mask));
+                    fresh[1] = 0;
+                    st->pair = 1;
+                    st->pair_fail = 0;
+                    st->pair_kz = s2;
+                    mode = M_MARK_PAIR;
+                }
             }
         }
     }
@@ -655,7 +759,7 @@ __device__ void plan_step(SelState* st, uint32_t* __restrict__ batch, unsigned l
 // are read and written many times, one after the other), planned there and copied back.
 // Every other block of the launch has finished, so nothing else touches the state meanwhile.
 __device__ void plan_shared(SelState* st, uint32_t* __restrict__ batch, unsigned long long* __restrict__ fresh,
-                            uint64_t* __restrict__ key, uint32_t* __restrict__ stamp,
+                            uint64_t* __restrict__ key, uint32_t* __restrict__ stamp, uint8_t* __restrict__ seedflag,
                             uint32_t* __restrict__ seed_list, uint64_t* __restrict__ gain_list,
                             uint64_t* __restrict__ round_evals, uint32_t n, uint32_t R, uint32_t bits,
                             const SelHandles& hd, bool have_count) {
@@ -666,7 +770,7 @@ __device__ void plan_shared(SelState* st, uint32_t* __restrict__ batch, unsigned
     unsigned long long* l = reinterpret_cast<unsigned long long*>(&ss);
     for (uint32_t i = threadIdx.x; i < kWords; i += blockDim.x) l[i] = __ldcg(g + i);
     __syncthreads();
-    if (threadIdx.x == 0) plan_step(&ss, batch, fresh, key, stamp, seed_list, gain_list, round_evals, n, R, bits, hd,
+    if (threadIdx.x == 0) plan_step(&ss, batch, fresh, key, stamp, seedflag, seed_list, gain_list, round_evals, n, R, bits, hd,
                                     have_count);
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < kWords; i += blockDim.x) g[i] = l[i];
@@ -826,6 +930,7 @@ struct StepArgs {
     uint32_t fb_cap, fb_slots;
     uint32_t n, R, bits;
     uint64_t* topb;   // kTopB keys per block (PH_TOPB)
+    uint32_t* pair_undo;   // [R]: the size row an M_MARK_PAIR step covered in each sketch, or kNone
     SelHandles hd;
 };
 
@@ -859,6 +964,26 @@ __device__ __forceinline__ void block_max_sum(unsigned long long& a, unsigned lo
     __syncthreads();
 }
 
+// The two largest of the block's (m1 >= m2) pairs; the result is valid in thread 0.
+__device__ __forceinline__ void block_top2(unsigned long long& m1, unsigned long long& m2) {
+    __shared__ unsigned long long s_1[8], s_2[8];
+#pragma unroll
+    for (int d = 16; d; d >>= 1) {
+        const unsigned long long o1 = __shfl_xor_sync(kFull, m1, d), o2 = __shfl_xor_sync(kFull, m2, d);
+        m2 = max(min(m1, o1), max(m2, o2));
+        m1 = max(m1, o1);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { s_1[w] = m1; s_2[w] = m2; }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+            m2 = max(min(m1, s_1[i]), max(m2, s_2[i]));
+            m1 = max(m1, s_1[i]);
+        }
+    __syncthreads();
+}
+
 // f(v, seedflag[v], stamp[v], key[v]) for the candidates v assigned to thread t0 of nthr:
 // four consecutive ids per iteration with one vector load per array, so that a thread has
 // all its loads of an iteration in flight at once.
@@ -884,14 +1009,21 @@ __device__ __forceinline__ void for_candidates(const StepArgs& a, uint32_t t0, u
 // max fresh key this round, stale_max / n_unev over the candidates not yet evaluated in it.
 // With `finalize`, batch members awaiting their fresh key (stamp kPending, key = their batch
 // slot) receive it here; otherwise an evaluation runs concurrently and they are skipped (the
-// last block finalises them).  `skip` is a seed whose flag the step sets at its end.
-__device__ void scan_candidates(const StepArgs& a, bool finalize, uint32_t skip, uint32_t t0, uint32_t nthr) {
+// last block finalises them).  `skip` is a seed whose flag the step sets at its end, `skip2` a
+// candidate evaluated ahead for the next round (left out).  With kTop2 (steps that evaluate a
+// single candidate, which may close a round and open the next with a pair) the second largest
+// stale key is kept too: a block's largest key m1 and second m2 go to stale_max and stale_2nd
+// as old = atomicMax(stale_max, m1); atomicMax(stale_2nd, max(m2, min(old, m1))), which leaves
+// the second largest of all keys in stale_2nd whatever the order of the blocks.
+template <bool kTop2>
+__device__ void scan_candidates(const StepArgs& a, bool finalize, uint32_t skip, uint32_t skip2, uint32_t t0,
+                                uint32_t nthr) {
     SelState* st = a.st;
     const uint32_t round = st->round;
     const unsigned long long bp = st->best_prev;   // the best fresh key before this batch
-    unsigned long long bf = 0, sm = 0, cnt = 0, above = 0;
+    unsigned long long bf = 0, s1 = 0, s2 = 0, cnt = 0, above = 0, unused = 0;
     for_candidates(a, t0, nthr, [&](uint32_t v, uint8_t sf, uint32_t sp, unsigned long long k) {
-        if (sf || v == skip) return;
+        if (sf || v == skip || v == skip2) return;
         if (sp & kPending) {   // evaluated in this batch
             if (!finalize) return;
             k = pack_key(__ldcg(a.fresh + (uint32_t)k), v, a.bits);
@@ -899,13 +1031,29 @@ __device__ void scan_candidates(const StepArgs& a, bool finalize, uint32_t skip,
             a.stamp[v] = round;
             sp = round;
         }
-        if (sp == round) bf = max(bf, k);
-        else { sm = max(sm, k); ++cnt; above += k > bp ? 1u : 0u; }
+        if (sp == round) {
+            bf = max(bf, k);
+        } else {
+            if (kTop2) {
+                if (k > s1) { s2 = s1; s1 = k; } else if (k > s2) { s2 = k; }
+            } else {
+                s1 = max(s1, k);
+            }
+            ++cnt;
+            above += k > bp ? 1u : 0u;
+        }
     });
-    block_max_sum(bf, sm, cnt, above);
+    if (kTop2) block_top2(s1, s2);
+    block_max_sum(bf, kTop2 ? unused : s1, cnt, above);
     if (threadIdx.x == 0) {
         if (bf) atomicMax(&st->best, bf);
-        if (sm) atomicMax(&st->stale_max, sm);
+        if (kTop2 && s1) {
+            const unsigned long long old = atomicMax(&st->stale_max, s1);
+            const unsigned long long sub = max(s2, min(old, s1));
+            if (sub) atomicMax(&st->stale_2nd, sub);
+        } else if (s1) {
+            atomicMax(&st->stale_max, s1);
+        }
         if (cnt) atomicAdd(&st->n_unev, cnt);
         if (above) atomicAdd(&st->above_bound, above);
     }
@@ -913,7 +1061,7 @@ __device__ void scan_candidates(const StepArgs& a, bool finalize, uint32_t skip,
 
 // scan_candidates over the whole grid
 __device__ __forceinline__ void scan_all(const StepArgs& a, bool finalize, uint32_t skip) {
-    scan_candidates(a, finalize, skip, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+    scan_candidates<false>(a, finalize, skip, kNone, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // Fresh keys of the batch members (last block, after the evaluation; every thread calls it).
@@ -975,21 +1123,29 @@ __device__ void mark_tasks(const StepArgs& a, BlockSearchSmem& sm) {
     }
 }
 
-// Marginal (Alg. 3) of a candidate in one sketch by a whole block; adds it to fresh[j].
+constexpr uint32_t kLabelOverflow = 0xFFFFFFFEu;   // a search outgrew its queue (labels are < n)
+
+// Marginal (Alg. 3) of a candidate in one sketch by a whole block; adds it to fresh[j].  With
+// label_out, thread 0 also stores the component's label there (kNone: no center,
+// kLabelOverflow: the search overflowed).  An `ahead` evaluation (M_MARK_PAIR's z) queues no
+// fallback search: an overflow voids it.
 __device__ void marginal_block(const StepArgs& a, const SketchView& s, uint32_t x, uint32_t r, uint32_t j,
-                               BlockSearchSmem& sm) {
+                               BlockSearchSmem& sm, bool ahead = false, uint32_t* label_out = nullptr) {
     unsigned long long d = 0;
     if (is_center(s, x)) {
         const uint32_t l = s.label[(size_t)center_index(s, x) * s.R + r];
         const uint32_t sz = __ldcg(s.size + (size_t)l * s.R + r);
         d = (sz & kCovered) ? 0u : sz;
+        if (threadIdx.x == 0 && label_out) *label_out = l;
     } else {
         const BfsOut o = block_search(a.g, s, x, r, true, sm, a.st);
         if (threadIdx.x == 0) {
+            if (label_out) *label_out = o.overflow ? kLabelOverflow : o.label;
             if (!o.overflow)
                 s.labcache[(size_t)(x & (kLabSlots - 1)) * s.R + r] = ((uint64_t)x << 32) | o.label;
             if (o.overflow) {
-                push_fallback(a.st, a.fbt, a.fb_cap, x, r, FB_EVAL, j);
+                if (ahead) a.st->pair_fail = 1;
+                else push_fallback(a.st, a.fbt, a.fb_cap, x, r, FB_EVAL, j);
             } else if (o.label != kNone) {
                 const uint32_t sz = __ldcg(s.size + (size_t)o.label * s.R + r);
                 d = (sz & kCovered) ? 0u : sz;
@@ -1020,19 +1176,42 @@ __device__ void eval_tasks(const StepArgs& a, BlockSearchSmem& sm) {
 // overflows, the fallback does both for that sketch (FB_MARK_EVAL), in the same order.
 __device__ void mark_eval_tasks(const StepArgs& a, BlockSearchSmem& sm) {
     __shared__ int s_marked;
+    __shared__ uint32_t s_ly;
     const uint32_t x = a.st->sd, y = a.batch[0];
+    const bool pair = a.st->pair != 0;
     SketchView s = a.s;
     s.pend = x;
+    SketchView s2 = s;   // z's searches: x and y are seeds
+    s2.pend2 = y;
     for (uint32_t r = blockIdx.x; r < a.R; r += gridDim.x) {   // uniform over the block
         bool over = false;
         const uint32_t lx = mark_label(a.g, s, x, r, sm, a.st, &over);
         if (threadIdx.x == 0) {
             s_marked = !over;
+            s_ly = kLabelOverflow;
             if (over) push_fallback(a.st, a.fbt, a.fb_cap, x, r, FB_MARK_EVAL, y);
             else if (lx != kNone) atomicOr(s.size + (size_t)lx * s.R + r, kCovered);
         }
         __syncthreads();
-        if (s_marked) marginal_block(a, s, y, r, 0, sm);
+        if (s_marked) marginal_block(a, s, y, r, 0, sm, false, pair ? &s_ly : nullptr);
+        __syncthreads();
+        if (!pair) continue;
+        // M_MARK_PAIR: MarkSeed(y) here as if y wins (recorded, to be undone if it loses), then
+        // z's Marginal; a sketch whose y search went to the fallback voids z's evaluation
+        if (threadIdx.x == 0) {
+            const uint32_t ly = s_ly;
+            uint32_t undo = kNone;
+            if (ly == kLabelOverflow) {
+                a.st->pair_fail = 1;
+            } else if (ly != kNone) {
+                const uint32_t old = atomicOr(s.size + (size_t)ly * s.R + r, kCovered);
+                if (!(old & kCovered)) undo = ly;
+            }
+            a.pair_undo[r] = undo;
+            s_marked = ly != kLabelOverflow;
+        }
+        __syncthreads();
+        if (s_marked) marginal_block(a, s2, a.batch[1], r, 1, sm, true, nullptr);
         __syncthreads();
     }
 }
@@ -1293,7 +1472,8 @@ k_sel_step(StepArgs a) {
     const unsigned long long ntask = phase == PH_EVAL ? (unsigned long long)__ldcg(&st->batch_n) * a.R : a.R;
     bool lookups = false;
     if (phase == PH_MARK) lookups = is_center(a.s, st->sd);
-    else if (phase == PH_MARK_EVAL) lookups = is_center(a.s, st->sd) && is_center(a.s, a.batch[0]);
+    else if (phase == PH_MARK_EVAL)
+        lookups = is_center(a.s, st->sd) && is_center(a.s, a.batch[0]) && (!st->pair || is_center(a.s, a.batch[1]));
     else if (phase == PH_EVAL) lookups = __ldcg(&st->batch_n) == 1 && is_center(a.s, a.batch[0]);
     const uint32_t free0 = (!lookups && ntask + 64 <= gridDim.x) ? (uint32_t)ntask : 0u;
     const bool scanner = blockIdx.x >= free0;
@@ -1303,15 +1483,18 @@ k_sel_step(StepArgs a) {
     case PH_SCAN: scan_all(a, true, kNone); break;
     case PH_MARK:
         if (!free0 || !scanner) mark_tasks(a, sm.bs);
-        if (scanner) scan_candidates(a, false, st->sd, t0, nthr);
+        if (scanner) scan_candidates<false>(a, false, st->sd, kNone, t0, nthr);
         break;
     case PH_MARK_EVAL:
         if (!free0 || !scanner) mark_eval_tasks(a, sm.bs);
-        if (scanner) scan_candidates(a, false, st->sd, t0, nthr);
+        if (scanner) scan_candidates<true>(a, false, st->sd, st->pair ? a.batch[1] : kNone, t0, nthr);
         break;
     case PH_EVAL:
         if (!free0 || !scanner) eval_tasks(a, sm.bs);
-        if (scanner) scan_candidates(a, false, kNone, t0, nthr);
+        if (scanner) {
+            if (__ldcg(&st->batch_n) == 1) scan_candidates<true>(a, false, kNone, kNone, t0, nthr);
+            else scan_candidates<false>(a, false, kNone, kNone, t0, nthr);
+        }
         break;
     case PH_SEL_PASS: sel_pass_tasks(a, sm); break;
     case PH_GATHER: gather_tasks(a); break;
@@ -1364,11 +1547,21 @@ k_sel_step(StepArgs a) {
             a.seedflag[st->sd] = 1;
             a.key[st->sd] = 0;
         }
+        // M_MARK_PAIR: if y lost its round (its fresh key is not above z's stale key), the
+        // MarkSeed(y) the step applied is undone (plan_step resolves the rest)
+        if (phase == PH_MARK_EVAL && st->pair) {
+            const unsigned long long fy = pack_key(__ldcg(a.fresh), a.batch[0], a.bits);
+            if (fy <= st->pair_kz)
+                for (uint32_t r = threadIdx.x; r < a.R; r += blockDim.x) {
+                    const uint32_t l = a.pair_undo[r];
+                    if (l != kNone) atomicAnd(a.s.size + (size_t)l * a.R + r, ~kCovered);
+                }
+        }
     }
     __threadfence();
     __syncthreads();
-    plan_shared(st, a.batch, a.fresh, a.key, a.stamp, a.seed_list, a.gain_list, a.round_evals, a.n, a.R, a.bits,
-                a.hd, phase == PH_COUNT);
+    plan_shared(st, a.batch, a.fresh, a.key, a.stamp, a.seedflag, a.seed_list, a.gain_list, a.round_evals, a.n, a.R,
+                a.bits, a.hd, phase == PH_COUNT);
 }
 
 // The reduction and plan after an evaluator outside k_sel_step (PH_SCAN's work as a kernel).
@@ -1385,8 +1578,8 @@ k_reduce_plan(StepArgs a) {
     __threadfence();
     if (threadIdx.x == 0) st->ticket = 0;
     __syncthreads();
-    plan_shared(st, a.batch, a.fresh, a.key, a.stamp, a.seed_list, a.gain_list, a.round_evals, a.n, a.R, a.bits,
-                a.hd, false);
+    plan_shared(st, a.batch, a.fresh, a.key, a.stamp, a.seedflag, a.seed_list, a.gain_list, a.round_evals, a.n, a.R,
+                a.bits, a.hd, false);
 }
 
 // Candidate first seeds of this build.
@@ -1558,6 +1751,7 @@ SketchView sketch_view(const im_ctx* c) {
     s.cbits = c->d_cbits; s.cidx = c->d_cidx; s.label = c->d_label; s.size = c->d_size;
     s.seed_flag = c->d_seedflag; s.labcache = c->d_labcache; s.smp = c->smp;
     s.pend = kNone;
+    s.pend2 = kNone;
     return s;
 }
 
@@ -1575,6 +1769,7 @@ StepArgs step_args(const im_ctx* c, const SelHandles& hd) {
     a.fb_slots = (c->all_centers || !c->d_fb_queue) ? 0u : c->fb_slots;
     a.n = c->n; a.R = c->R; a.bits = c->key_bits;
     a.topb = c->d_topb;
+    a.pair_undo = c->d_pair_undo;
     a.hd = hd;
     return a;
 }
