@@ -364,6 +364,36 @@ int im_server_destroy(im_server* srv);
 #define IM_HUBS_AUTO 0xFFFFFFFFu
 int im_set_hubs(im_ctx* ctx, uint32_t cap, uint32_t min_degree);
 
+/*
+ * Autotuning of the knobs that leave every result unchanged: sketches per edge pass
+ * (im_set_sketch_batch: automatic, 16, 8), sketch batches in flight (im_set_pipeline: 2, 1)
+ * and, for compact sketches (alpha < 1), hubs (im_set_hubs: IM_HUBS_AUTO, none; the
+ * context's minimum degree is kept).  Every combination builds the sketches of (R, seed, p,
+ * alpha) and selects k seeds (Alg. 1) `reps` + 1 times, the first untimed (it may capture the
+ * selection graph); its time is the smallest of the timed runs, on the host clock, whose
+ * calls are synchronous.  The fastest combination is set on the context and
+ * the sketches are built once more with it, so that the context is ready for
+ * im_select_seeds.  Every combination must give the same seeds: if one does not, the call
+ * fails with IM_EDEVICE.
+ *
+ * out (caller-owned) receives the chosen knobs, their times and those of the first
+ * combination (the defaults).  Errors: IM_EINVAL for a NULL ctx or out, reps == 0 or
+ * k outside [1, n], and any error of im_build_sketches or im_select_seeds, which stops the
+ * search; the knobs are then left as the failing combination set them.
+ */
+typedef struct {
+    uint32_t sketch_batch;   /* chosen im_set_sketch_batch value (0 = automatic)      */
+    uint32_t lanes;          /* chosen im_set_pipeline value                          */
+    uint32_t hub_cap;        /* chosen im_set_hubs cap (IM_HUBS_AUTO or 0)             */
+    uint32_t tried;          /* combinations timed                                    */
+    double build_ms;         /* im_build_sketches with the chosen knobs (ms)          */
+    double select_ms;        /* im_select_seeds(k) with the chosen knobs (ms)         */
+    double default_build_ms; /* the same for the first combination (the defaults)     */
+    double default_select_ms;
+} im_tuning;
+int im_autotune(im_ctx* ctx, uint32_t R, uint64_t seed, double p, double alpha, uint32_t k, uint32_t reps,
+                im_tuning* out);
+
 /* Measurement: the rate of the sampling kernel's per-pair compute (64-bit add, high word of
  * the hash, compare, live-mask update) on register values only -- the ceiling of the
  * sampling with no memory traffic -- in (edge, sketch) pairs per second on the current

@@ -7,7 +7,7 @@ CUDA kernels behind the C ABI of ``include/im_gb300.h``; this package is its bin
 from ._native import (  # noqa: F401
     IM_EDEVICE, IM_EINVAL, IM_ENOMEM, IM_ESTATE, IM_HUBS_AUTO, IM_OK, IM_PROBS_ARRAY, IM_PROBS_UNIFORM, IM_PROBS_WIC,
     IM_PTR_DEVICE, IM_PTR_HOST, IMContext, IMServer,
-    IMError, im_build_sketches, im_create, im_destroy, im_get_centers, im_get_compact,
+    IMError, im_autotune, im_build_sketches, im_create, im_destroy, im_get_centers, im_get_compact,
     im_get_gains, im_get_labels, im_hash_peak, im_load_graph, im_mc_spread, im_set_edge_probs, im_get_round_evals, im_get_stats, im_profile_enable,
     im_profile_get, im_profile_reset, im_reset_selection, im_run_batch, im_select_seeds,
     im_set_graph, im_set_hubs, im_set_pipeline, im_set_seed_speculation, im_set_refresh_threshold, im_set_sketch_batch, im_sketch_static, im_spread, im_stream, lib)

@@ -54,6 +54,12 @@ class im_request(ctypes.Structure):
                 ("done_ns", ctypes.c_uint64), ("status", ctypes.c_int)]
 
 
+class im_tuning(ctypes.Structure):
+    _fields_ = [("sketch_batch", ctypes.c_uint32), ("lanes", ctypes.c_uint32), ("hub_cap", ctypes.c_uint32),
+                ("tried", ctypes.c_uint32), ("build_ms", ctypes.c_double), ("select_ms", ctypes.c_double),
+                ("default_build_ms", ctypes.c_double), ("default_select_ms", ctypes.c_double)]
+
+
 def lib():
     """Load the library (raises if it is missing: there is no fallback path)."""
     global _lib
@@ -91,6 +97,7 @@ def lib():
         "im_hash_peak": ([u32, c.POINTER(dbl)], i32),
         "im_set_seed_speculation": ([vp, u32], i32),
         "im_set_hubs": ([vp, u32, u32], i32),
+        "im_autotune": ([vp, u32, u64, dbl, dbl, u32, u32, c.POINTER(im_tuning)], i32),
         "im_run_batch": ([c.POINTER(im_instance), u32, u32], i32),
         "im_server_create": ([c.POINTER(vp)], i32),
         "im_server_add_model": ([vp, u32, u64, vp, vp, u32, u64, dbl, dbl, c.POINTER(u32), c.POINTER(u64)], i32),
@@ -386,6 +393,14 @@ def im_set_hubs(ctx, cap: int = IM_HUBS_AUTO, min_degree: int = 32):
     _check(ctx, lib().im_set_hubs(ctx, cap, min_degree))
 
 
+def im_autotune(ctx, R: int, seed: int, p: float, alpha: float, k: int, reps: int = 1) -> dict:
+    """Times every combination of sketch batch, lanes and hubs on (R, seed, p, alpha, k), sets the
+    fastest and builds the sketches with it; returns the chosen knobs and their times."""
+    out = im_tuning()
+    _check(ctx, lib().im_autotune(ctx, R, seed, p, alpha, k, reps, ctypes.byref(out)))
+    return {f: getattr(out, f) for f, _ in im_tuning._fields_}
+
+
 def im_hash_peak(iters: int = 4096) -> float:
     """Pairs per second of the sampling kernel's per-pair compute on registers only."""
     out = ctypes.c_double(0)
@@ -448,6 +463,9 @@ class IMContext:
 
     def mc_spread(self, seeds, sims, mc_seed):
         return im_mc_spread(self.h, seeds, sims, mc_seed)
+
+    def autotune(self, R, seed, p, alpha, k, reps=1):
+        return im_autotune(self.h, R, seed, p, alpha, k, reps)
 
     def reset_selection(self):
         im_reset_selection(self.h)

@@ -67,6 +67,9 @@ def test_argument_errors_need_no_gpu(libpath):
     with pytest.raises(im.IMError) as e:
         im.im_create(0, __import__("numpy").zeros(0, "uint32"), __import__("numpy").zeros(0, "uint32"))
     assert e.value.code == _native.IM_EINVAL
+    with pytest.raises(im.IMError) as e:
+        im.im_autotune(None, 64, 1, 0.05, 0.1, 5)
+    assert e.value.code == _native.IM_EINVAL
 
 
 def test_product_package_never_imports_the_oracle():
@@ -74,3 +77,27 @@ def test_product_package_never_imports_the_oracle():
     for f in list(pkg.rglob("*.py")) + list(pkg.rglob("*.cu")) + list(pkg.rglob("*.cuh")):
         t = f.read_text()
         assert "import oracle" not in t and "from oracle" not in t and "im_oracle" not in t, f
+
+
+@pytest.mark.parametrize("name", ["im_stats", "im_instance", "im_request", "im_tuning"])
+def test_struct_layouts_match_the_header(tmp_path, name):
+    """The binding's ctypes structs have the header's sizes and field offsets (a C compiler
+    reads the header)."""
+    import ctypes
+    import shutil
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    st = getattr(_native, name)
+    fields = [f for f, _ in st._fields_]
+    src = tmp_path / "layout.c"
+    lines = ['#include <stddef.h>', '#include <stdio.h>', f'#include "{HEADER}"', "int main(void) {",
+             f'    printf("%zu\\n", sizeof({name}));']
+    lines += [f'    printf("%zu\\n", offsetof({name}, {f}));' for f in fields]
+    lines += ["    return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-o", str(exe), str(src)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [ctypes.sizeof(st)] + [getattr(st, f).offset for f in fields]
+    assert got == want
