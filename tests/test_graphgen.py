@@ -47,3 +47,19 @@ def test_rmat_shape():
 def test_impossible_request_fails():
     with pytest.raises(RuntimeError):
         graphgen.erdos_renyi(4, 7, 0)
+
+
+def test_batched_instances_follow_their_recipe():
+    insts = graphgen.c4_instances(6, first_seed=1000, n_range=(1e3, 2e4))
+    again = graphgen.c4_instances(6, first_seed=1000, n_range=(1e3, 2e4))
+    assert len(insts) == 6
+    for i, (d, e) in enumerate(zip(insts, again)):
+        assert d["seed"] == 1000 + i and d["alpha"] == 1.0
+        assert 1e3 * 0.99 <= d["n"] <= 2e4 * 1.01
+        assert d["p"] in (0.01, 0.02, 0.05, 0.1) and d["R"] in (64, 128, 256) and d["k"] in (10, 50, 100)
+        m = len(d["u"])
+        assert 4 * d["n"] / 2 * 0.99 <= m <= 32 * d["n"] / 2 * 1.01     # average degree in [4, 32]
+        u, v = d["u"].astype(np.int64), d["v"].astype(np.int64)
+        assert (u < v).all() and (v < d["n"]).all()                    # canonical, no loops
+        assert len(np.unique(u * d["n"] + v)) == m                     # no duplicates
+        assert np.array_equal(d["u"], e["u"]) and np.array_equal(d["v"], e["v"])   # seeded
