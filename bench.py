@@ -542,10 +542,7 @@ def run_c5(args):
             models.append((gi, p, 42 + len(models)))
             footprint += fp
     t_admit = time.perf_counter() - t_admit
-    rng = np.random.default_rng(2311)
-    nreq = int(args.rate * args.duration)
-    arrivals = np.cumsum(rng.exponential(1e9 / args.rate, nreq))
-    reqs = [(int(rng.integers(0, len(models))), int(rng.integers(5, 201)), int(t)) for t in arrivals]
+    reqs = graphgen.c5_requests(len(models), args.rate, args.duration)
     out = srv.replay(reqs)
     srv.close()
     lat = np.array([(o["done_ns"] - t) / 1e6 for o, (_, _, t) in zip(out, reqs)])

@@ -154,6 +154,16 @@ def c4_instances(count: int = 64, first_seed: int = 1000, n_range=(1e4, 2e6)):
     return out
 
 
+def c5_requests(models: int, rate: float, duration: float, seed: int = 2311):
+    """The serving workload's request trace: Poisson arrivals at `rate` per second for
+    `duration` seconds, each asking a uniform model for k ~ U{5..200} seeds.  Returns
+    (model, k, arrival_ns) tuples in arrival order."""
+    rng = np.random.default_rng(seed)
+    nreq = int(rate * duration)
+    arrivals = np.cumsum(rng.exponential(1e9 / rate, nreq))
+    return [(int(rng.integers(0, models)), int(rng.integers(5, 201)), int(t)) for t in arrivals]
+
+
 def workload(name: str):
     """Return (n, u, v, params) for a named workload."""
     w = WORKLOADS[name]

@@ -63,3 +63,16 @@ def test_batched_instances_follow_their_recipe():
         assert (u < v).all() and (v < d["n"]).all()                    # canonical, no loops
         assert len(np.unique(u * d["n"] + v)) == m                     # no duplicates
         assert np.array_equal(d["u"], e["u"]) and np.array_equal(d["v"], e["v"])   # seeded
+
+
+def test_serving_trace_is_a_seeded_poisson_stream():
+    reqs = graphgen.c5_requests(16, 200.0, 10.0)
+    assert reqs == graphgen.c5_requests(16, 200.0, 10.0)
+    assert len(reqs) == 2000
+    models, ks, t = (np.array(x) for x in zip(*reqs))
+    assert models.min() >= 0 and models.max() < 16 and len(set(models.tolist())) == 16
+    assert ks.min() >= 5 and ks.max() <= 200
+    gaps = np.diff(np.concatenate([[0], t])) / 1e9
+    assert (gaps >= 0).all()
+    assert abs(gaps.mean() - 1 / 200.0) < 0.1 / 200.0             # exponential gaps, mean 1/rate
+    assert abs(gaps.std() / gaps.mean() - 1.0) < 0.1              # coefficient of variation 1
