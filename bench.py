@@ -6,7 +6,15 @@ compact sketches), select k seeds with the device lazy greedy, and the spread of
 value = m * R (sampled edge-sketch pairs) per step / step time, summed over ranks.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload chunglu_n1M_m10M]
+                    [--workload rmat_s24_m256M] [--no-extras]
+
+The default workload is the R-MAT graph of scale 24 with 2^28 edges (p = 0.01, R = 256,
+alpha = 0.05, k = 200), the largest configuration of the paper's kind that one GPU holds.
+The same JSON line carries, unless --no-extras, three more measurements of the same run:
+"secondary" (the Chung-Lu n = 10^6, m = 10^7 workload, timed the same way), "batched" (64
+independent Chung-Lu instances: one at a time against the batched engine, outputs compared)
+and "serving" (Poisson requests against resident R-MAT models: queries/s, p50/p99 latency,
+answers compared with the same requests run alone).
 
 Under torchrun every rank runs an independent replica of the workload (the path needs no
 exchange); rank 0 prints the JSON line with the max time over ranks.
@@ -31,9 +39,8 @@ sys.path.insert(0, str(ROOT))
 import graphgen  # noqa: E402
 
 METRIC = "sampled edge-sketch pairs/s"
-DEFAULT_WORKLOAD = "chunglu_n1M_m10M"
-CPU_SAMPLE_SKETCHES = 32        # per step of the reference arm (--impl reference)
-CPU_BASELINE_PAIRS = 2.56e9     # the cpu_baseline of our arm: about 10 s of oracle work
+DEFAULT_WORKLOAD = "rmat_s24_m256M"
+SECONDARY_WORKLOAD = "chunglu_n1M_m10M"
 PROFILES = ROOT / "profiles"
 SRC = ROOT / "paper_2311_07554_gb300" / "csrc"
 
@@ -251,12 +258,10 @@ def edge_probs(prm, m):
     return None
 
 
-def cpu_sample(n, u, v, prm, sketches=CPU_SAMPLE_SKETCHES):
-    """The oracle on a bounded sample: the first `sketches` sketches of the workload, all
-    steps of the path (labels, gains, compact sketches, greedy, spread)."""
+def oracle_graph(n, u, v, prm):
+    """The oracle's CSR of the workload with its probabilities (built once, outside any timing:
+    the graph is resident on both arms) and the sampling mode to call it with."""
     import oracle
-    threads = oracle.max_threads()
-    t0 = time.perf_counter()
     G = oracle.Graph(n, u, v)
     mode = oracle.MODE_HASH
     if prm["probs"] == "wic":
@@ -265,58 +270,79 @@ def cpu_sample(n, u, v, prm, sketches=CPU_SAMPLE_SKETCHES):
     elif prm["probs"] != "uniform":
         G.set_probs(edge_probs(prm, len(u)))
         mode = oracle.MODE_EDGE
-    L = G.labels(prm["seed"], prm["p"], sketches, mode=mode, threads=threads)
+    return G, mode
+
+
+def cpu_sample(G, mode, prm, sketches, r0=0):
+    """The oracle on a bounded sample: sketches r0 .. r0+sketches-1 of the workload, every step
+    of the path on them (BFS labels, gains, compact sketches, greedy, spread).  The oracle runs
+    its sketches in parallel, one per host thread, so a sample of as many sketches as there are
+    cores takes about as long as one sketch."""
+    import oracle
+    threads = oracle.max_threads()
+    t0 = time.perf_counter()
+    L = G.labels(prm["seed"], prm["p"], sketches, r0=r0, mode=mode, threads=threads)
     oracle.gains(L)
-    ctr = oracle.centers(n, prm["seed"], prm["alpha"])
+    ctr = oracle.centers(G.n, prm["seed"], prm["alpha"])
     oracle.compact(L, ctr)
-    seeds, _ = oracle.greedy(L, prm["k"])
+    seeds, _ = oracle.greedy(L, min(prm["k"], G.n))
     oracle.spread(L, seeds)
     dt = time.perf_counter() - t0
-    m = len(u)
-    return {"value": m * sketches / dt, "unit": "pairs/s", "cores": threads, "kind": "oracle",
+    return {"value": G.m * sketches / dt, "unit": "pairs/s", "cores": threads, "kind": "oracle",
             "seconds": dt,
-            "sample": f"{sketches} of {prm['R']} sketches of {prm['name']}, k={prm['k']}, "
-                      f"whole path (BFS labels, gains, compact sketches, greedy, spread)"}
+            "sample": f"sketches {r0}..{r0 + sketches - 1} of the {prm['R']} of {prm['name']}, k={prm['k']}, "
+                      f"whole path (BFS labels, gains, compact sketches, greedy, spread) on the resident "
+                      f"graph (CSR built once, untimed)"}
+
+
+def cpu_sketches(prm):
+    """Sketches per oracle sample: one per host thread (about 20 s of work on the R-MAT
+    scale-24 graph, a few seconds on the Chung-Lu one)."""
+    import oracle
+    return int(max(1, min(prm["R"], oracle.max_threads())))
 
 
 # ----------------------------------------------------------------------------- arms
 def run_reference(args, n, u, v, prm):
+    """The reference arm of this build: the oracle, as it stands, on the host cores.  Each step
+    is a bounded sample of the workload (cpu_sketches(prm) sketches through the whole path);
+    warm-up steps run one sketch.  Rank 0 alone runs under torchrun."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    for _ in range(args.warmup):
-        cpu_sample(n, u, v, prm, sketches=max(1, CPU_SAMPLE_SKETCHES // 8))
+    G, mode = oracle_graph(n, u, v, prm)
+    S = cpu_sketches(prm)
+    for i in range(args.warmup):
+        cpu_sample(G, mode, prm, 1, r0=i % prm["R"])
     t0 = time.perf_counter()
     res = None
-    for _ in range(args.steps):
-        res = cpu_sample(n, u, v, prm)
+    for i in range(args.steps):
+        res = cpu_sample(G, mode, prm, S, r0=(i * S) % max(1, prm["R"] - S + 1))
     dt = (time.perf_counter() - t0) / max(1, args.steps)
-    value = len(u) * CPU_SAMPLE_SKETCHES / dt
+    value = len(u) * S / dt
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic",
         "config": {"workload": prm["name"], "n": n, "m": len(u), "p": prm["p"], "probs": prm["probs"], "R": prm["R"],
-                   "alpha": prm["alpha"], "k": prm["k"], "sample_sketches": CPU_SAMPLE_SKETCHES},
+                   "alpha": prm["alpha"], "k": prm["k"], "sample_sketches": S},
         "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": res["cores"], "kind": "oracle",
-                         "sample": res["sample"]},
+                         "sample": res["sample"] + f"; {S} sketches per step"},
         "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_ours(args, n, u, v, prm):
+def measure_workload(args, n, u, v, prm, steps, warmup, dist, ws, local, full=True):
+    """Times `steps` steps of the whole path on one workload (L2 flushed before each step,
+    outside the events) and returns the contract line's fields for it.  With full=True also
+    the e2e leg (public API from pinned host buffers), the Monte-Carlo evaluation, the
+    oracle's cpu_baseline, per-kernel rooflines and the clocks."""
     import torch
     import paper_2311_07554_gb300 as im
 
-    ws, rank, local = _dist()
-    torch.cuda.set_device(local)
-    dist = None
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
     m = len(u)
     R, k = prm["R"], prm["k"]
     pairs = m * R
@@ -339,20 +365,17 @@ def run_ours(args, n, u, v, prm):
         im.im_set_graph(ctx.h, 0)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
 
-    def step():
-        ctx.build_sketches(R, prm["seed"], prm["p"], prm["alpha"])
-        seeds, gains = ctx.select_seeds(k)
-        sp = ctx.spread(seeds)
-        return seeds, gains, sp
-
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         flush.fill_(1)
-        step()
+        ctx.build_sketches(R, prm["seed"], prm["p"], prm["alpha"])
+        s0, _ = ctx.select_seeds(k)
+        ctx.spread(s0)
     torch.cuda.synchronize()
 
     # timed region: K steps, L2 flushed before each (outside the events)
     im.im_profile_reset(ctx.h)
     im.im_profile_enable(ctx.h, True)
+    launches0 = int(ctx.stats()["launches"])
     live_build = 0
     clocks = ClockSampler(local)
     if dist:
@@ -362,7 +385,7 @@ def run_ours(args, n, u, v, prm):
     times, t_build, t_select = [], [], []
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     seeds = gains = sp = None
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.fill_(1)
         ev[0].record(stream)
         ctx.build_sketches(R, prm["seed"], prm["p"], prm["alpha"])
@@ -382,24 +405,62 @@ def run_ours(args, n, u, v, prm):
     clk = clocks.stop()
     prof = im.im_profile_get(ctx.h)
     st = ctx.stats()
-    launches = int(st["launches"])
+    launches = int(st["launches"]) - launches0
     im.im_profile_enable(ctx.h, False)
     ms_step = sum(times) / len(times)
     ms_build = sum(t_build) / len(t_build)
     ms_select = sum(t_select) / len(t_select)
     ms_step, ms_build, ms_select = max_over_ranks([ms_step, ms_build, ms_select], dist, "cuda")
 
+    peaks, peak_src = _peaks()
+    hash_peak = im.im_hash_peak(4096)
+    roofs = kernel_rooflines(prof, live_build, n, m, R, steps, peaks, peak_src, clk, hash_peak)
+    top = max(((kn, x) for kn, x in prof.items() if kn != "select_graph"), key=lambda kv: kv[1][0])
+    roof = roofs.get(top[0]) or (max(roofs.values(), key=lambda r: r["share_of_device_time"]) if roofs else None)
+    p_mean = prm["p"] if pe is None and prm["probs"] == "uniform" else None
+    if p_mean is None:
+        p_mean = float(np.mean(pe)) if pe is not None else float(live_build) / (m * R * steps)
+    sk_roof = sketch_roofline(prof, n, m, R, int(st["sketch_batch"]), p_mean, prm["alpha"], steps,
+                              ms_build, peaks, hash_peak, live_build)
+    out = {
+        "workload": prm["name"],
+        "value": job_rate(pairs, ws, ms_step / 1e3), "ms_per_step": ms_step, "steps": steps, "warmup": warmup,
+        "config": {"workload": prm["name"], "n": n, "m": m, "p": prm["p"], "probs": prm["probs"], "R": R,
+                   "alpha": prm["alpha"], "k": k, "l2": "flushed before every step (256 MB write)",
+                   "parallelism": f"replicas{ws}"},
+        "time_to_k_ms": ms_build + ms_select,
+        "sketch_ms": ms_build, "select_ms": ms_select,
+        "sketch_pairs_per_s": pairs / (ms_build / 1e3),
+        "evaluations": int(st["evaluations"]),
+        "refresh_batches": int(st["refresh_batches"]),
+        "spec_batches": int(st["spec_batches"]),
+        "hubs": int(st["hubs"]),
+        "roofline": roof,
+        "sketch_roofline": sk_roof,
+        "kernel_rooflines": list(roofs.values()),
+        "gpu_launches": launches,
+        "clocks": clk,
+        "kernels_ms_per_step": {kname: round(t / steps, 4) for kname, (t, _) in
+                                sorted(prof.items(), key=lambda kv: -kv[1][0])},
+        "top_kernel": top[0],
+        "seeds_head": [int(x) for x in seeds[:5]], "spread": int(sp),
+    }
+    if not full:
+        ctx.close()
+        return out
+
     # Monte-Carlo influence of the selected seeds (the paper's quality measure), after the
     # timed region: MC_SIMS live-edge worlds of an independent hash seed.
-    mc = None
     if args.mc_sims > 0:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         mc_total = ctx.mc_spread(seeds, args.mc_sims, prm["seed"] + 1000)
         mc_s = time.perf_counter() - t0
-        mc = {"sims": args.mc_sims, "hash_seed": prm["seed"] + 1000, "ms": mc_s * 1e3,
-              "sigma_estimate": mc_total / args.mc_sims, "sketch_estimate": int(sp) / R,
-              "pairs_per_s": m * args.mc_sims / mc_s}
+        out["mc_eval"] = {"sims": args.mc_sims, "hash_seed": prm["seed"] + 1000, "ms": mc_s * 1e3,
+                          "sigma_estimate": mc_total / args.mc_sims, "sketch_estimate": int(sp) / R,
+                          "pairs_per_s": m * args.mc_sims / mc_s}
+    ctx.close()
+    del du, dv
 
     # End to end through the public API with host buffers (pinned): a long-lived context
     # (created once, like a serving engine) receives each step's graph from host memory
@@ -418,7 +479,7 @@ def run_ours(args, n, u, v, prm):
     e2e_step()
     torch.cuda.synchronize()
     e2e_times = []
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(max(1, min(steps, 3))):
         flush.fill_(1)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -427,72 +488,72 @@ def run_ours(args, n, u, v, prm):
     e2e_s = sum(e2e_times) / len(e2e_times)
     c2.close()
     e2e_s = max_over_ranks([e2e_s], dist, "cuda")[0]
+    out["e2e"] = {"value": job_rate(pairs, ws, e2e_s), "unit": "pairs/s",
+                  "h2d_bytes_per_step": 8 * m + (8 * m if pe is not None else 0),
+                  "d2h_bytes_per_step": 12 * k + 8}
+    return out
 
+
+def run_ours(args, n, u, v, prm):
+    import torch
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    res = measure_workload(args, n, u, v, prm, args.steps, args.warmup, dist, ws, local, full=True)
+    extras = {}
     if rank == 0:
-        peaks, peak_src = _peaks()
-        total_ms = sum(x[0] for x in prof.values())
-        # the selection graph is a sequence of kernels, not one: rank real kernels only
-        top = max(((kn, x) for kn, x in prof.items() if kn != "select_graph"), key=lambda kv: kv[1][0])
-        hash_peak = im.im_hash_peak(4096)
-        roofs = kernel_rooflines(prof, live_build, n, m, R, args.steps, peaks, peak_src, clk, hash_peak)
-        roof = roofs.get(top[0]) or (max(roofs.values(), key=lambda r: r["share_of_device_time"])
-                                     if roofs else None)
-        cpu = cpu_sample(n, u, v, prm, sketches=int(max(1, min(R, CPU_BASELINE_PAIRS // m))))
-        p_mean = prm["p"] if pe is None and prm["probs"] == "uniform" else None
-        if p_mean is None:
-            p_mean = float(np.mean(pe)) if pe is not None else float(live_build) / (m * R * args.steps)
-        sk_roof = sketch_roofline(prof, n, m, R, int(st["sketch_batch"]), p_mean, prm["alpha"], args.steps,
-                                  ms_build, peaks, hash_peak, live_build)
+        # the oracle on a bounded sample of the same workload, on the host cores (rank 0 only)
+        G, mode = oracle_graph(n, u, v, prm)
+        res["cpu_baseline"] = cpu_sample(G, mode, prm, cpu_sketches(prm))
+        del G
+    if not args.no_extras and ws == 1:
+        n2, u2, v2, prm2 = graphgen.workload(SECONDARY_WORKLOAD)
+        prm2["name"] = SECONDARY_WORKLOAD
+        prm2["probs"] = "uniform"
+        sec = measure_workload(args, n2, u2, v2, prm2, min(args.steps, 10), max(3, min(args.warmup, 3)),
+                               None, 1, local, full=False)
+        extras["secondary"] = {SECONDARY_WORKLOAD: {k: sec[k] for k in (
+            "value", "ms_per_step", "steps", "config", "time_to_k_ms", "sketch_ms", "select_ms",
+            "sketch_pairs_per_s", "sketch_roofline", "roofline", "kernels_ms_per_step", "spread", "clocks")}}
+        extras["batched"] = batched_leg(args)
+        extras["serving"] = serving_leg(args, duration=args.serve_seconds)
+    if rank == 0:
         line = {
             "metric": METRIC,
-            "value": job_rate(pairs, ws, ms_step / 1e3),
+            "value": res["value"],
             "unit": "pairs/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms_step,
+            "ms_per_step": res["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u64", "data": "synthetic",
-            "config": {"workload": prm["name"], "n": n, "m": m, "p": prm["p"], "probs": prm["probs"], "R": R,
-                       "alpha": prm["alpha"], "k": k, "l2": "flushed before every step",
-                       "parallelism": f"replicas{ws}"},
-            "time_to_k_ms": ms_build + ms_select,
-            "sketch_ms": ms_build, "select_ms": ms_select,
-            "sketch_pairs_per_s": pairs / (ms_build / 1e3),
-            "evaluations": int(st["evaluations"]),
-            "refresh_batches": int(st["refresh_batches"]),
-            "spec_batches": int(st["spec_batches"]),
-            "hubs": int(st["hubs"]),
-            "mc_eval": mc,
-            "roofline": roof,
-            "sketch_roofline": sk_roof,
-            "kernel_rooflines": list(roofs.values()),
-            "cpu_baseline": cpu,
-            "e2e": {"value": job_rate(pairs, ws, e2e_s), "unit": "pairs/s",
-                    "h2d_bytes_per_step": 8 * m + (8 * m if pe is not None else 0),
-                    "d2h_bytes_per_step": 12 * k + 8},
-            "gpu_launches": launches,
-            "clocks": clk,
-            "kernels_ms_per_step": {kname: round(t / args.steps, 4) for kname, (t, _) in
-                                    sorted(prof.items(), key=lambda kv: -kv[1][0])},
-            "top_kernel": top[0],
-            "seeds_head": [int(x) for x in seeds[:5]], "spread": int(sp),
+            "config": res["config"],
         }
+        for key in ("time_to_k_ms", "sketch_ms", "select_ms", "sketch_pairs_per_s", "evaluations",
+                    "refresh_batches", "spec_batches", "hubs", "mc_eval", "roofline", "sketch_roofline",
+                    "kernel_rooflines", "cpu_baseline", "e2e", "gpu_launches", "clocks", "kernels_ms_per_step",
+                    "top_kernel", "seeds_head", "spread"):
+            if key in res:
+                line[key] = res[key]
+        line.update(extras)
         print(json.dumps(line), flush=True)
-    ctx.close()
     if dist:
         dist.destroy_process_group()
     return 0
 
 
-def run_c4(args):
-    """The batched workload: 64 independent Chung-Lu instances (graphgen.c4_instances), run by
-    im_run_batch with `--workers` contexts side by side, against the same instances one at a
-    time (one worker).  Outputs must be identical; value = all instances' edge-sketch pairs
-    per second of the batched run (host clock: several streams; h2d graph uploads included)."""
+def batched_leg(args, count=64):
+    """The batched workload: `count` independent Chung-Lu instances (graphgen.c4_instances) run
+    one at a time (one worker, per-instance launches) and by the batched engine
+    (im_run_batch); outputs must be identical.  Host clock around each whole batch, best of
+    `reps` runs after one untimed run of each (h2d graph uploads included in both)."""
     import torch
     import paper_2311_07554_gb300 as im
 
-    torch.cuda.set_device(0)
-    inst = graphgen.c4_instances(64)
+    inst = graphgen.c4_instances(count)
     pairs = sum(len(d["u"]) * d["R"] for d in inst)
 
     def timed(workers):
@@ -502,30 +563,26 @@ def run_c4(args):
         torch.cuda.synchronize()
         return time.perf_counter() - t0, res
 
-    for _ in range(max(1, args.warmup)):
-        timed(args.workers)
-    seq_t, seq = min((timed(1) for _ in range(max(1, args.steps))), key=lambda x: x[0])
-    bat_t, bat = min((timed(args.workers) for _ in range(max(1, args.steps))), key=lambda x: x[0])
+    reps = 2
+    timed(1)
+    timed(args.workers)
+    seq_t, seq = min((timed(1) for _ in range(reps)), key=lambda x: x[0])
+    bat_t, bat = min((timed(args.workers) for _ in range(reps)), key=lambda x: x[0])
     same = all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[2] == b[2] for a, b in zip(seq, bat))
-    line = {"metric": METRIC, "value": pairs / bat_t, "unit": "pairs/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": bat_t * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "c4_chunglu_x64", "instances": len(inst), "workers": args.workers,
-                       "edges": int(sum(len(d["u"]) for d in inst)), "pairs": int(pairs),
-                       "alpha": 1.0, "parallelism": "replicas1"},
-            "sequential_ms": seq_t * 1e3, "speedup_vs_sequential": seq_t / bat_t, "identical": bool(same),
-            "timing": "best of --steps runs, host clock around the whole batch"}
-    print(json.dumps(line), flush=True)
-    return 0
+    return {"workload": "c4_chunglu_x64", "instances": len(inst), "edges": int(sum(len(d["u"]) for d in inst)),
+            "pairs": int(pairs), "workers": args.workers,
+            "per_instance_ms": seq_t * 1e3, "batched_ms": bat_t * 1e3,
+            "speedup": seq_t / bat_t, "pairs_per_s": pairs / bat_t, "identical": bool(same),
+            "timing": f"best of {reps} runs of each, host clock around the whole batch"}
 
 
-def run_c5(args):
+def serving_leg(args, duration=10.0):
     """The serving workload: 8 resident R-MAT graphs (scales 18, 18, 19, 20, 21, 21, 22, 23,
     average degree 16) x p in {.01, .05} = 16 models (R = 128, alpha = 0.1), and requests for
     k ~ U[5, 200] seeds of a uniformly drawn model arriving as a Poisson process of
-    --rate requests/s for --duration s, replayed by the native engine (im_server_*).  Reports
-    queries/s and latency percentiles; checks that every answer equals the prefix of the model's
-    sequence computed alone (a separate context) for the four smallest models."""
+    args.rate requests/s for `duration` s, replayed by the native engine (im_server_*).
+    Reports queries/s and latency percentiles; checks that every answer equals the prefix of
+    the model's sequence computed alone (a separate context) for the four smallest models."""
     import torch
     import paper_2311_07554_gb300 as im
 
@@ -542,7 +599,7 @@ def run_c5(args):
             models.append((gi, p, 42 + len(models)))
             footprint += fp
     t_admit = time.perf_counter() - t_admit
-    reqs = graphgen.c5_requests(len(models), args.rate, args.duration)
+    reqs = graphgen.c5_requests(len(models), args.rate, duration)
     out = srv.replay(reqs)
     srv.close()
     lat = np.array([(o["done_ns"] - t) / 1e6 for o, (_, _, t) in zip(out, reqs)])
@@ -561,16 +618,39 @@ def run_c5(args):
         for o, (m, k, _) in zip(out, reqs):
             if m == mid:
                 same &= bool(np.array_equal(o["seeds"], s[:k]) and np.array_equal(o["gains"], g[:k]))
-    line = {"metric": "queries/s", "value": len(reqs) / span, "unit": "queries/s", "n_gpus": 1, "steps": 1,
-            "warmup": 0, "ms_per_step": span * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "c5_rmat_serving", "models": len(models), "scales": scales, "R": 128,
-                       "alpha": 0.1, "p": [0.01, 0.05], "rate_per_s": args.rate, "duration_s": args.duration,
-                       "requests": len(reqs), "k": "U[5,200]", "parallelism": "replicas1"},
+    return {"workload": "c5_rmat_serving", "queries_per_s": len(reqs) / span, "span_s": span,
+            "models": len(models), "scales": scales, "R": 128, "alpha": 0.1, "p": [0.01, 0.05],
+            "rate_per_s": args.rate, "duration_s": duration, "requests": len(reqs), "k": "U[5,200]",
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
                            "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
             "admission": {"seconds": t_admit, "estimated_device_bytes": footprint},
             "identical_alone_vs_mix": bool(same)}
+
+
+def run_c4(args):
+    """--c4 alone: the batched leg as its own contract line."""
+    import torch
+    torch.cuda.set_device(0)
+    b = batched_leg(args)
+    line = {"metric": METRIC, "value": b["pairs_per_s"], "unit": "pairs/s", "n_gpus": 1, "steps": 2,
+            "warmup": 1, "ms_per_step": b["batched_ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": b["workload"], "instances": b["instances"], "workers": b["workers"],
+                       "edges": b["edges"], "pairs": b["pairs"], "alpha": 1.0, "parallelism": "replicas1"},
+            "batched": b}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_c5(args):
+    """--c5 alone: the serving leg as its own contract line."""
+    s = serving_leg(args, duration=args.duration)
+    line = {"metric": "queries/s", "value": s["queries_per_s"], "unit": "queries/s", "n_gpus": 1, "steps": 1,
+            "warmup": 0, "ms_per_step": s["span_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": s["workload"], "models": s["models"], "requests": s["requests"],
+                       "parallelism": "replicas1"},
+            "serving": s}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -582,6 +662,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(graphgen.WORKLOADS))
+    ap.add_argument("--no-extras", action="store_true",
+                    help="time the workload only (no secondary workload, batched or serving legs)")
     ap.add_argument("--sketch-batch", type=int, default=0, help="sketches per edge pass (0 = auto)")
     ap.add_argument("--probs", default="uniform", choices=["uniform", "u01", "u13", "wic"],
                     help="IC probabilities: the workload's p, or per edge U(0,0.1), U(0.1,0.3), 2/(d_u+d_v)")
@@ -590,11 +672,13 @@ def main():
     ap.add_argument("--alpha", type=float, default=None, help="center fraction (default: the workload's)")
     ap.add_argument("--select-host", action="store_true",
                     help="drive the selection from the host instead of the CUDA graph (for kernel profiling)")
-    ap.add_argument("--c4", action="store_true", help="the batched workload: 64 instances side by side")
-    ap.add_argument("--workers", type=int, default=4, help="contexts side by side for --c4")
-    ap.add_argument("--c5", action="store_true", help="the serving workload: 16 resident models, Poisson requests")
-    ap.add_argument("--rate", type=float, default=200.0, help="requests per second for --c5")
+    ap.add_argument("--c4", action="store_true", help="the batched workload alone")
+    ap.add_argument("--workers", type=int, default=4, help="contexts side by side for the batched workload")
+    ap.add_argument("--c5", action="store_true", help="the serving workload alone")
+    ap.add_argument("--rate", type=float, default=200.0, help="requests per second of the serving workload")
     ap.add_argument("--duration", type=float, default=10.0, help="seconds of requests for --c5")
+    ap.add_argument("--serve-seconds", type=float, default=5.0,
+                    help="seconds of requests of the serving leg in the default line")
     args = ap.parse_args()
     if args.c4:
         return run_c4(args)

@@ -129,6 +129,11 @@ WORKLOADS = {
     "rmat_s24_m256M": dict(
         graph=lambda: rmat(24, 1 << 28, 0.57, 0.19, 0.19, 3), p=0.01, R=256, alpha=0.05,
         k=200, seed=42),
+    # the same recipe at scale 21 (n = 2^21, 2^25 edges): small enough for the profiler's
+    # multi-pass captures, still larger than L2 per sketch batch
+    "rmat_s21_m32M": dict(
+        graph=lambda: rmat(21, 1 << 25, 0.57, 0.19, 0.19, 3), p=0.01, R=256, alpha=0.05,
+        k=200, seed=42),
 }
 
 

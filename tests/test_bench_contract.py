@@ -28,8 +28,16 @@ def _json_lines(out):
     return [json.loads(l) for l in out.splitlines() if l.startswith("{")]
 
 
+def test_default_workload_is_rmat_scale24():
+    sys.path.insert(0, str(ROOT))
+    import bench
+    assert bench.DEFAULT_WORKLOAD == "rmat_s24_m256M"
+    import graphgen
+    assert bench.DEFAULT_WORKLOAD in graphgen.WORKLOADS and bench.SECONDARY_WORKLOAD in graphgen.WORKLOADS
+
+
 def test_reference_arm_prints_one_contract_line():
-    r = _run("--impl", "reference", "--steps", "1", "--warmup", "0")
+    r = _run("--impl", "reference", "--steps", "1", "--warmup", "1", "--workload", "chunglu_n1M_m10M")
     assert r.returncode == 0, r.stderr[-2000:]
     lines = _json_lines(r.stdout)
     assert len(lines) == 1
@@ -37,7 +45,7 @@ def test_reference_arm_prints_one_contract_line():
     assert d["impl"] == "reference"
     assert d["metric"] == "sampled edge-sketch pairs/s" and d["unit"] == "pairs/s"
     assert d["higher_is_better"] is True and d["scaling"] == "weak"
-    assert d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] == 0
+    assert d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] == 1
     assert d["vs_baseline"] is None and d["data"] == "synthetic" and d["dtype"] == "u64"
     assert d["value"] > 0 and d["ms_per_step"] > 0
     cfg = d["config"]
