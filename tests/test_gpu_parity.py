@@ -221,7 +221,7 @@ def test_argument_errors():
 
 
 def test_lazy_evaluation_counts_are_bounded():
-    # Sec. 4: batched lazy evaluation does at most a constant factor more work than CELF
+    # Sec. 4: batched lazy evaluation does at most twice the work of CELF
     n, u, v, prm = graphgen.workload("er_n2000_m10000")
     G = oracle.Graph(n, u, v)
     L = G.labels(prm["seed"], prm["p"], prm["R"])
@@ -232,7 +232,12 @@ def test_lazy_evaluation_counts_are_bounded():
         ctx.select_seeds(k)
         ev = ctx.round_evals()
     assert ev[0] == 0
-    assert np.all(ev <= 4 * ev_celf + 2)
+    # Sec. 4.1: prefix doubling re-evaluates the candidates in CELF's order and stops at the
+    # end of the first batch that holds CELF's stopping point, so a round costs at most 2 c - 1
+    # evaluations where CELF costs c; a pair step (one round's candidate evaluated with the
+    # next round's) adds at most one evaluation to a round
+    assert np.all(ev <= 2 * ev_celf + 1)
+    assert int(ev.sum()) <= 2 * int(ev_celf.sum())
 
 
 @pytest.mark.parametrize("threshold", [1, 2**64 - 1])
