@@ -248,6 +248,24 @@ def test_greedy_variants_and_celf_agree(er_c1):
     assert np.all(ev <= n)
 
 
+def test_celf_evaluation_counts_counted_by_hand():
+    """Alg. 2 (CELF) on memoised components given directly, every step counted by hand.
+
+    n = 5, R = 2.  Sketch 0: components {0, 1, 2}, {3}, {4}; sketch 1: {0}, {1, 3}, {2, 4}.
+    Initial gains 4, 5, 5, 3, 3.  Round 0 takes vertex 1 (5, smaller id than 2) without an
+    evaluation.  Round 1 pops 2 (fresh 2 < 4, back), 0 (fresh 1 < 3, back), 3 (fresh 1 < 3,
+    back), 4 (fresh 3 > 2): 4 evaluations.  Round 2 pops 2 (fresh 0), then 0 (fresh 1, beats 3's
+    stale 1 on the id): 2.  Round 3: 3 (fresh 1 > 0): 1.  Round 4: 2, the last entry: 1."""
+    L = np.array([[0, 0, 0, 3, 4], [0, 1, 2, 1, 2]], np.uint32)
+    seeds, gains, ev = oracle.celf(L, 5)
+    assert seeds.tolist() == [1, 4, 0, 3, 2]
+    assert gains.tolist() == [5, 3, 1, 1, 0]
+    assert ev.tolist() == [0, 4, 2, 1, 1]
+    g_seeds, g_gains = oracle.greedy(L, 5)
+    assert g_seeds.tolist() == seeds.tolist() and g_gains.tolist() == gains.tolist()
+    assert oracle.gains(L).tolist() == [4, 5, 5, 3, 3]
+
+
 def test_submodularity_along_the_seed_sequence(er_c1):
     n, u, v, prm, G, L = er_c1
     k = 6
