@@ -361,6 +361,10 @@ def measure_workload(args, n, u, v, prm, steps, warmup, dist, ws, local, full=Tr
     set_probs(ctx)
     if args.sketch_batch:
         im.im_set_sketch_batch(ctx.h, args.sketch_batch)
+    if args.union_path is not None:
+        im.im_set_union_path(ctx.h, args.union_path)
+    if args.lanes:
+        im.im_set_pipeline(ctx.h, args.lanes)
     if args.select_host:   # the selection's kernels launched by the host (profilable one by one)
         im.im_set_graph(ctx.h, 0)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
@@ -665,6 +669,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="time the workload only (no secondary workload, batched or serving legs)")
     ap.add_argument("--sketch-batch", type=int, default=0, help="sketches per edge pass (0 = auto)")
+    ap.add_argument("--union-path", type=int, default=None, choices=[0, 1],
+                    help="0: hashing and unions in one kernel (default), 1: live-pair records and a union kernel")
+    ap.add_argument("--lanes", type=int, default=0, help="sketch batches in flight (0 = the default, 2)")
     ap.add_argument("--probs", default="uniform", choices=["uniform", "u01", "u13", "wic"],
                     help="IC probabilities: the workload's p, or per edge U(0,0.1), U(0.1,0.3), 2/(d_u+d_v)")
     ap.add_argument("--mc-sims", type=int, default=20000,

@@ -195,6 +195,14 @@ const char* im_kernel_name(int kernel_id);
  * next im_build_sketches. */
 int im_set_sketch_batch(im_ctx* ctx, uint32_t batch);
 
+/* Failure injection for tests (no counterpart in the paper): after `after` more device
+ * allocations of the library (any context, any thread) have succeeded, the next one fails as
+ * if the device were out of memory -- nothing is allocated, the call that needed it returns
+ * IM_ENOMEM and leaves its context usable (a later call allocates again) -- and the hook
+ * disarms itself.  A negative `after` disarms it.  No GPU work is involved: the failure is
+ * made on the host, before cudaMalloc would be called.  Returns IM_OK. */
+int im_debug_fail_alloc(int64_t after);
+
 /*
  * im_sketch_static -- labels and component sizes of one sketch, for callers that cannot
  * allocate device memory.  The paper has no counterpart of this call.
@@ -217,8 +225,12 @@ int im_set_sketch_batch(im_ctx* ctx, uint32_t batch);
  *
  * Scratch: a file-scope static device array of 2 * IM_STATIC_MAX_N + 64 uint32 words
  * (8 MiB + 256 B), present on every device where the library is loaded, until the process
- * exits.  Its device address is looked up (cudaGetSymbolAddress) by the first call made with
- * a given device current, so make that first call before any stream capture.  All calls
+ * exits.  Its device address is looked up (cudaGetSymbolAddress, which allocates nothing) in
+ * the calling thread's current context by every call made outside stream capture, so any
+ * context works: the primary one, one created after a cudaDeviceReset, or a non-primary
+ * context made current.  A call made while `stream` is being captured uses the address the
+ * last uncaptured call found on that device: make one call on the device, in the context
+ * that the capture uses, before capturing (without one the call fails with IM_ECUDA).  All calls
  * share the array; each call clears what it needs, but calls whose GPU work overlaps (two
  * streams, two threads) race on it and give wrong results: serialise them.
  * Errors: IM_EINVAL (n out of range, m >= 2^32, NULL arrays, an edge id >= n or a self-loop
@@ -241,6 +253,17 @@ int im_set_refresh_threshold(im_ctx* ctx, uint64_t min_batch);
  * hashing (ALU-bound) overlaps another's union-find (latency-bound); 1 runs them in order on
  * the context stream.  Both lanes' scratch is allocated either way; results do not depend on it. */
 int im_set_pipeline(im_ctx* ctx, uint32_t lanes);
+
+/* Tuning: how a sketch batch's unions meet its sampling (Sec. 3: the live edges of Sample(e, r)
+ * are united per sketch; Alg. 3).  IM_UNION_RECORDS (default): the live pairs are written to
+ * a record buffer of the context (about 1.3 p m B x 16 bytes per lane) and united by a second
+ * kernel that keeps several unions of each thread in flight.  IM_UNION_FUSED: one kernel
+ * hashes the batch's (edge, sketch) pairs and unites the live ones through a per-warp queue
+ * in shared memory, so that no live pair is stored (no record buffer).  Results do not depend
+ * on it.  Takes effect at the next im_build_sketches; IM_EINVAL for another value. */
+#define IM_UNION_FUSED 0
+#define IM_UNION_RECORDS 1
+int im_set_union_path(im_ctx* ctx, int path);
 
 /* Execution of the selection loop (Alg. 2 / Alg. 4 rounds).  1 (default): the whole loop is
  * one CUDA graph whose while / switch nodes are set by the device, so rounds and batches run

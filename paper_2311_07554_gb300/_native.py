@@ -93,6 +93,8 @@ def lib():
         "im_set_sketch_batch": ([vp, u32], i32),
         "im_set_refresh_threshold": ([vp, u64], i32),
         "im_set_pipeline": ([vp, u32], i32),
+        "im_set_union_path": ([vp, i32], i32),
+        "im_debug_fail_alloc": ([c.c_int64], i32),
         "im_set_graph": ([vp, i32], i32),
         "im_hash_peak": ([u32, c.POINTER(dbl)], i32),
         "im_set_seed_speculation": ([vp, u32], i32),
@@ -278,6 +280,22 @@ def im_set_refresh_threshold(ctx, min_batch: int):
 
 def im_set_pipeline(ctx, lanes: int):
     _check(ctx, lib().im_set_pipeline(ctx, lanes))
+
+
+def im_debug_fail_alloc(after: int):
+    """Test hook: the device allocation after `after` more successful ones fails (IM_ENOMEM);
+    negative disarms."""
+    lib().im_debug_fail_alloc(int(after))
+
+
+IM_UNION_FUSED = 0
+IM_UNION_RECORDS = 1
+
+
+def im_set_union_path(ctx, path: int):
+    """IM_UNION_FUSED: hashing and unions in one kernel; IM_UNION_RECORDS: live-pair records
+    united by a second kernel."""
+    _check(ctx, lib().im_set_union_path(ctx, path))
 
 
 def im_set_graph(ctx, on: bool):

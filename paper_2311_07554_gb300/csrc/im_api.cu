@@ -4,6 +4,8 @@
 #include <cstring>
 #include <algorithm>
 
+#include <atomic>
+
 #include "im_internal.cuh"
 
 using namespace imk;
@@ -37,7 +39,7 @@ template <typename T>
 bool dalloc(T*& p, size_t count) {
     dfree(p);
     void* q = nullptr;
-    if (cudaMalloc(&q, count * sizeof(T) + 16) != cudaSuccess) {
+    if (im_dev_malloc(&q, count * sizeof(T) + 16) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
@@ -68,6 +70,23 @@ void free_sketch_state(im_ctx* c) {
     c->cap_R = 0;
     c->cap_nspec = 0;
     c->built = false;
+}
+
+// Every buffer a build's kernels write is allocated (a host-side check before any launch).
+bool sketch_buffers_ready(const im_ctx* c, uint32_t nspec) {
+    bool ok = c->d_gain0 && c->d_key && c->d_stamp && c->d_seedflag && c->d_batch && c->d_fresh &&
+              c->d_seed_list && c->d_labcache && c->d_pair_undo && c->d_gain_list && c->d_round_evals &&
+              c->d_label && c->d_size && c->d_live_total;
+    for (uint32_t i = 0; i < kMaxLanes && ok; ++i) {
+        const im_ctx::Lane& L = c->lane[i];
+        ok = L.parent && L.word && (i == 0 || (L.gain && L.fresh)) && (!c->live_cap || (L.live && L.live_n)) &&
+             (!nspec || L.spec_ov);
+    }
+    if (ok && !c->all_centers)
+        ok = c->d_cbits && c->d_cidx && c->d_centers && c->d_fb_queue && c->d_fb_bits && c->d_fb_tasks &&
+             c->d_cflags && c->d_cpos && c->d_csel;
+    if (ok && nspec) ok = c->d_spec_keys && c->d_spec_ids;
+    return ok;
 }
 
 __global__ void k_mask_covered(uint32_t* p, uint64_t cnt) {
@@ -125,6 +144,24 @@ void im_prof_end(im_ctx* c, int kid, int ev0) {
     if (!c->prof || ev0 < 0) return;
     cudaEventRecord(c->ev_pool[ev0 + 1], c->cur);
     c->ev_pending.push_back({kid, {ev0, ev0 + 1}});
+}
+
+// Failure injection for tests (im_debug_fail_alloc): the number of device allocations still
+// to succeed before one fails, or -1 when disarmed.
+static std::atomic<int64_t> g_fail_alloc_after{-1};
+
+cudaError_t im_dev_malloc(void** p, size_t bytes) {
+    int64_t left = g_fail_alloc_after.load();
+    while (left >= 0) {
+        if (g_fail_alloc_after.compare_exchange_weak(left, left - 1)) {
+            if (left == 0) {   // this allocation is the one that fails; the hook disarms itself
+                *p = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+            break;
+        }
+    }
+    return cudaMalloc(p, bytes);
 }
 
 int im_fail(im_ctx* c, int code, const std::string& msg) {
@@ -244,7 +281,7 @@ int im_create_reserved(im_ctx** out, uint32_t n, uint64_t m, const uint32_t* u, 
     for (uint32_t i = 1; i < kMaxLanes; ++i) c->lane[i].stream = c->lane_stream[i];
     int rc = IM_OK;
     do {
-        if (cudaMalloc(&c->d_sel, sizeof(SelState)) != cudaSuccess ||
+        if (im_dev_malloc(&c->d_sel, sizeof(SelState)) != cudaSuccess ||
             cudaMallocHost(&c->h_sel, sizeof(SelState)) != cudaSuccess ||
             cudaMallocHost(&c->h_live, 3 * sizeof(unsigned long long)) != cudaSuccess) {
             rc = im_fail(c, IM_ENOMEM, "selection state");
@@ -252,12 +289,12 @@ int im_create_reserved(im_ctx** out, uint32_t n, uint64_t m, const uint32_t* u, 
         }
         cudaMemsetAsync(c->d_sel, 0, sizeof(SelState), c->stream);
         memset(c->h_sel, 0, sizeof(SelState));
-        if (cudaMalloc(&c->d_live_total, sizeof(unsigned long long)) != cudaSuccess ||
+        if (im_dev_malloc(&c->d_live_total, sizeof(unsigned long long)) != cudaSuccess ||
             cudaMemsetAsync(c->d_live_total, 0, sizeof(unsigned long long), c->stream) != cudaSuccess) {
             rc = im_fail(c, IM_ENOMEM, "counters");
             break;
         }
-        if (cudaMalloc(&c->d_spread_total, sizeof(unsigned long long)) != cudaSuccess) {
+        if (im_dev_malloc(&c->d_spread_total, sizeof(unsigned long long)) != cudaSuccess) {
             rc = im_fail(c, IM_ENOMEM, "spread total");
             break;
         }
@@ -306,6 +343,14 @@ int im_set_pipeline(im_ctx* c, uint32_t lanes) {
     if (!c) return IM_EINVAL;
     if (lanes < 1 || lanes > kMaxLanes) return im_fail(c, IM_EINVAL, "lanes must be 1 or 2");
     c->lanes = lanes;
+    return IM_OK;
+}
+
+int im_set_union_path(im_ctx* c, int path) {
+    if (!c) return IM_EINVAL;
+    if (path != IM_UNION_FUSED && path != IM_UNION_RECORDS)
+        return im_fail(c, IM_EINVAL, "union path must be IM_UNION_FUSED or IM_UNION_RECORDS");
+    c->union_path = path;
     return IM_OK;
 }
 
@@ -410,7 +455,7 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
     // live-pair records of one batch: expected p m B, with a generous margin; a batch that
     // still overflows falls back to the fused sample+union loop on the device
     uint64_t live_cap = 0;
-    if (c->m > 0 && (smp.eT || smp.all_live || smp.T != 0)) {
+    if (c->union_path == IM_UNION_RECORDS && c->m > 0 && (smp.eT || smp.all_live || smp.T != 0)) {
         const double pe = smp.eT ? c->mean_p : smp.all_live ? 1.0 : p;
         const double ex = pe * (double)c->m * B;
         double cap = 1.3 * ex + 16.0 * std::sqrt(ex) + 65536.0;
@@ -451,7 +496,7 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
         // at least the context's reserve (im_create_reserved), so that later builds fit
         const uint32_t na = std::max(n, c->res_n), Ra = std::max(R, c->res_R);
         const size_t nca = std::max<size_t>(nc, c->res_nc);
-        const uint64_t livea = std::max(live_cap, c->res_live);
+        const uint64_t livea = c->union_path == IM_UNION_RECORDS ? std::max(live_cap, c->res_live) : live_cap;
         const uint32_t nsa = std::min(std::max(nspec, c->res_n ? std::min<uint32_t>(c->spec_req, kSpecMax) : 0u),
                                       kSpecMax);
         const bool compact = !all || c->res_n > 0;   // a reserved context may serve compact builds
@@ -469,7 +514,7 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
         if (ok && livea) {
             c->live_cap = livea;
             for (uint32_t i = 0; i < kMaxLanes && ok; ++i)
-                ok = dalloc(c->lane[i].live, c->live_cap) && dalloc(c->lane[i].live_n, 1);
+                ok = dalloc(c->lane[i].live, c->live_cap) && dalloc(c->lane[i].live_n, 2);
         }
         if (ok && compact) {
             const size_t nw = ((size_t)na + 31) / 32;
@@ -498,16 +543,28 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
     IM_CUDA(c, cudaMemcpyAsync(c->h_live, c->d_live_total, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                                c->stream));
     c->h_live[2] = 0;
+    if (nspec && (!c->d_spec_keys || !c->d_spec_ids)) {
+        // both or neither: a build after a failed one allocates them again
+        if (!dalloc(c->d_spec_keys, kSpecMax) || !dalloc(c->d_spec_ids, kSpecMax)) {
+            dfree(c->d_spec_keys);
+            dfree(c->d_spec_ids);
+            rc = im_fail(c, IM_ENOMEM, "first seed candidates");
+        }
+    }
+    if (!rc && !sketch_buffers_ready(c, nspec))
+        rc = im_fail(c, IM_ESTATE, "sketch buffers missing after allocation");
+    if (rc) { free_sketch_state(c); return rc; }
     if (!all) {
         rc = im_select_centers(c, c->d_cflags, c->d_cpos);
         if (!rc) rc = im_select_hubs(c, c->d_cflags, c->d_cpos);
         if (rc) { free_sketch_state(c); return rc; }
     }
-    if (!rc && nspec && !c->d_spec_keys) {
-        if (!dalloc(c->d_spec_keys, kSpecMax) || !dalloc(c->d_spec_ids, kSpecMax))
-            rc = im_fail(c, IM_ENOMEM, "first seed candidates");
-    }
     if (!rc) rc = im_arc_keys(c, smp.salt);
+    // record counters of the lanes start at zero (each union kernel resets its lane's after use)
+    for (uint32_t i = 0; i < kMaxLanes && !rc; ++i)
+        if (c->lane[i].live_n &&
+            cudaMemsetAsync(c->lane[i].live_n, 0, 2 * sizeof(unsigned long long), c->stream) != cudaSuccess)
+            rc = im_fail(c, IM_ECUDA, "record counter reset");
     if (!rc) rc = im_sketch_batches(c);
     if (!rc) rc = im_selection_init(c, true);   // the build wrote every size entry
     if (!rc) {
@@ -729,6 +786,11 @@ int im_profile_get(im_ctx* c, int kernel_id, double* total_ms, uint64_t* launche
 int im_kernel_count(void) { return K_COUNT; }
 
 const char* im_kernel_name(int kernel_id) { return kernel_name(kernel_id); }
+
+int im_debug_fail_alloc(int64_t after) {
+    g_fail_alloc_after.store(after < 0 ? -1 : after);
+    return IM_OK;
+}
 
 void* im_stream(im_ctx* c) { return c ? (void*)c->stream : nullptr; }
 

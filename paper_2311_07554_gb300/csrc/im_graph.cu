@@ -257,7 +257,7 @@ int im_scan_u32_to_u64(im_ctx* c, const uint32_t* d_in, uint64_t* d_out, uint64_
         if (c->d_tmp) cudaFree(c->d_tmp);
         c->d_tmp = nullptr;
         c->tmp_bytes = 0;
-        if (cudaMalloc(&c->d_tmp, need) != cudaSuccess) return im_fail(c, IM_ENOMEM, "scan scratch");
+        if (im_dev_malloc(&c->d_tmp, need) != cudaSuccess) return im_fail(c, IM_ENOMEM, "scan scratch");
         c->tmp_bytes = need;
     }
     uint64_t* part = (uint64_t*)c->d_tmp;
@@ -288,17 +288,17 @@ int im_graph_build(im_ctx* c, const uint32_t* d_u, const uint32_t* d_v) {
         const uint32_t na = n > c->res_n ? n : c->res_n;
         const uint64_t ma = m > c->res_m ? m : c->res_m;
         const uint64_t ma_pad = ((ma + 1) & ~1ull) + 2;
-        if (cudaMalloc(&c->d_edges, ma_pad * sizeof(uint2)) != cudaSuccess)
+        if (im_dev_malloc(&c->d_edges, ma_pad * sizeof(uint2)) != cudaSuccess)
             return im_fail(c, IM_ENOMEM, "edge list");
-        if (cudaMalloc(&c->d_off, ((size_t)na + 1) * sizeof(uint64_t)) != cudaSuccess)
+        if (im_dev_malloc(&c->d_off, ((size_t)na + 1) * sizeof(uint64_t)) != cudaSuccess)
             return im_fail(c, IM_ENOMEM, "csr offsets");
-        if (cudaMalloc(&c->d_arcs, (2 * ma + 2) * sizeof(uint4)) != cudaSuccess)
+        if (im_dev_malloc(&c->d_arcs, (2 * ma + 2) * sizeof(uint4)) != cudaSuccess)
             return im_fail(c, IM_ENOMEM, "csr arcs");
-        if (cudaMalloc(&c->d_adj, (2 * ma + 2) * sizeof(uint2)) != cudaSuccess ||
-            cudaMalloc(&c->d_src, (2 * ma + 2) * sizeof(uint32_t)) != cudaSuccess)
+        if (im_dev_malloc(&c->d_adj, (2 * ma + 2) * sizeof(uint2)) != cudaSuccess ||
+            im_dev_malloc(&c->d_src, (2 * ma + 2) * sizeof(uint32_t)) != cudaSuccess)
             return im_fail(c, IM_ENOMEM, "static adjacency");
         // two cursors per vertex for the arc fill; the first n + 5 words serve as degree scratch
-        if (cudaMalloc(&c->d_arc_cur, (2 * (size_t)na + 8) * sizeof(uint32_t)) != cudaSuccess)
+        if (im_dev_malloc(&c->d_arc_cur, (2 * (size_t)na + 8) * sizeof(uint32_t)) != cudaSuccess)
             return im_fail(c, IM_ENOMEM, "arc cursors");
         c->graph_n_alloc = na;
         c->graph_m_alloc = ma;
@@ -348,9 +348,14 @@ int im_edge_probs(im_ctx* c, int model, const double* d_p) {
     const uint64_t m = c->m;
     const uint64_t m_pad = (m + 1) & ~1ull;   // k_sample_emit reads them in pairs
     if (!c->d_edgeT) {
-        if (cudaMalloc(&c->d_edgeT, (m_pad + 2) * sizeof(uint64_t)) != cudaSuccess ||
-            cudaMalloc(&c->d_arcT, (2 * m + 2) * sizeof(uint64_t)) != cudaSuccess)
+        if (im_dev_malloc(&c->d_edgeT, (m_pad + 2) * sizeof(uint64_t)) != cudaSuccess ||
+            im_dev_malloc(&c->d_arcT, (2 * m + 2) * sizeof(uint64_t)) != cudaSuccess) {
+            cudaFree(c->d_edgeT);   // both or neither (a later call allocates them again)
+            cudaFree(c->d_arcT);
+            c->d_edgeT = nullptr;
+            c->d_arcT = nullptr;
             return im_fail(c, IM_ENOMEM, "edge thresholds");
+        }
         c->edgeT_cap = m;
     }
     IM_CUDA(c, cudaMemsetAsync(c->d_edgeT, 0, (m_pad + 2) * sizeof(uint64_t), c->stream));

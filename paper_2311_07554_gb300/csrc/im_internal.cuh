@@ -370,6 +370,7 @@ struct im_ctx {
     cudaEvent_t ev_join[imk::kMaxLanes] = {};
     cudaStream_t cur = nullptr;                  // stream the next launch goes to
     uint32_t lanes = 2;                          // sketch batches alternate between two streams
+    int union_path = IM_UNION_RECORDS;           // im_set_union_path
     uint32_t batch_req = 0, batch_used = 0, batch_alloc = 0;
     uint64_t live_cap = 0;           // live-pair records allocated per lane
     // capacities of the sketch buffers (a later build that fits reuses them)
@@ -457,6 +458,12 @@ void im_select_graph_free(im_ctx* c);
 int im_spread_run(im_ctx* c, uint32_t k, uint64_t* out);
 
 int im_fail(im_ctx* c, int code, const std::string& msg);
+// Every device allocation of the library goes through here: cudaMalloc, unless a failure was
+// injected (im_debug_fail_alloc), in which case nothing is allocated and
+// cudaErrorMemoryAllocation is returned.
+cudaError_t im_dev_malloc(void** p, size_t bytes);
+template <typename T>
+inline cudaError_t im_dev_malloc(T** p, size_t bytes) { return im_dev_malloc(reinterpret_cast<void**>(p), bytes); }
 int im_cuda_check(im_ctx* c, cudaError_t e, const char* what);
 
 #define IM_CUDA(c, call)                                                                \

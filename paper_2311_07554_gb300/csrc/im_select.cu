@@ -1829,7 +1829,7 @@ int size_step_grid(im_ctx* c) {
     IM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sel_step, kBlockWarps * 32, 0));
     IM_CUDA(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
     const unsigned grid = (unsigned)std::max(1, per_sm) * (unsigned)std::max(1, sms);
-    if (cudaMalloc(&c->d_topb, (size_t)grid * kTopB * sizeof(uint64_t)) != cudaSuccess)
+    if (im_dev_malloc(&c->d_topb, (size_t)grid * kTopB * sizeof(uint64_t)) != cudaSuccess)
         return im_fail(c, IM_ENOMEM, "top-B scratch");
     c->step_grid = grid;
     return IM_OK;

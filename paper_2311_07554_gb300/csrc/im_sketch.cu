@@ -70,6 +70,66 @@ k_sample_union(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, ui
         sample_union_pair<B>(edge_pairs[i], i, m, smp, g0, nb, parent, n);
 }
 
+// Live (edge, sketch) pairs of one edge pair (edges 2i, 2i + 1) in sketches r0 .. r0+nb-1:
+// bit b of live0 / live1 is set iff edge 2i / 2i+1 is live in sketch r0 + b.  Candidates are
+// found on the high word of the hash (a superset of the live pairs, about 2^-31 larger) and
+// settled with the full hash; the edge key mix(salt ^ e) is computed once for the batch.
+template <int B>
+__device__ __forceinline__ void pair_live_masks(uint64_t i, uint64_t m, const Sampler& smp, uint32_t r0,
+                                                uint32_t nb, uint64_t g0, uint32_t& live0, uint32_t& live1) {
+    const uint64_t e0 = 2 * i, e1 = 2 * i + 1;
+    const uint64_t k0 = mix64(smp.salt ^ e0), k1 = mix64(smp.salt ^ e1);
+    uint64_t T0 = uniform_T(smp), T1 = T0;
+    if (smp.eT) {   // per-edge thresholds, stored pairwise like the edges
+        const ulonglong2 tt = __ldcs(reinterpret_cast<const ulonglong2*>(smp.eT) + i);
+        T0 = tt.x;
+        T1 = tt.y;
+    }
+    const uint32_t all = (nb >= 32) ? 0xFFFFFFFFu : ((1u << nb) - 1u);
+    live0 = live1 = 0;
+    if (T0 == kAllLive && T1 == kAllLive) {
+        live0 = live1 = all;
+    } else {
+        const uint32_t h0 = (uint32_t)(T0 >> 32), h1 = (uint32_t)(T1 >> 32);
+        const uint32_t th0 = h0 == 0xFFFFFFFFu ? h0 : h0 + 1u;
+        const uint32_t th1 = h1 == 0xFFFFFFFFu ? h1 : h1 + 1u;
+        uint64_t x0 = k0 + g0, x1 = k1 + g0;
+        if (nb == (uint32_t)B) {
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                if (mix64_hi_raw(x0) <= th0) live0 |= 1u << b;
+                if (mix64_hi_raw(x1) <= th1) live1 |= 1u << b;
+                x0 += kGamma;
+                x1 += kGamma;
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                if (b < (int)nb) {
+                    if (mix64_hi_raw(x0) <= th0) live0 |= 1u << b;
+                    if (mix64_hi_raw(x1) <= th1) live1 |= 1u << b;
+                }
+                x0 += kGamma;
+                x1 += kGamma;
+            }
+        }
+        // exact test for the candidates (about a fraction p of all pairs)
+        if (T0 == kAllLive) live0 = all;
+        else
+            for (uint32_t t = live0; t; t &= t - 1) {
+                const int b = __ffs(t) - 1;
+                if (!live_T(k0, (uint64_t)(r0 + b + 1u) * kGamma, T0)) live0 &= ~(1u << b);
+            }
+        if (T1 == kAllLive) live1 = all;
+        else
+            for (uint32_t t = live1; t; t &= t - 1) {
+                const int b = __ffs(t) - 1;
+                if (!live_T(k1, (uint64_t)(r0 + b + 1u) * kGamma, T1)) live1 &= ~(1u << b);
+            }
+    }
+    if (e1 >= m) live1 = 0;
+}
+
 // Sampling alone: every live (edge, sketch) pair of the batch becomes a record (u, v, b, 0),
 // appended with one atomic per warp.  The hash work (nb mixes per edge) is pure ALU; the
 // latency-bound unions then run one thread per record in k_union_live.  The kernel also
@@ -96,62 +156,9 @@ k_sample_emit(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, uin
         const uint64_t i = base + threadIdx.x;
         uint32_t live0 = 0, live1 = 0;
         uint4 two = make_uint4(0, 0, 0, 0);
-        uint64_t k0 = 0, k1 = 0;
         if (i < npairs) {
             two = __ldcs(edge_pairs + i);   // streamed once per batch: keep L2 for the forest
-            const uint64_t e0 = 2 * i, e1 = 2 * i + 1;
-            k0 = mix64(smp.salt ^ e0);
-            k1 = mix64(smp.salt ^ e1);
-            uint64_t T0 = uniform_T(smp), T1 = T0;
-            if (smp.eT) {   // per-edge thresholds, stored pairwise like the edges
-                const ulonglong2 tt = __ldcs(reinterpret_cast<const ulonglong2*>(smp.eT) + i);
-                T0 = tt.x;
-                T1 = tt.y;
-            }
-            const uint32_t all = (nb >= 32) ? 0xFFFFFFFFu : ((1u << nb) - 1u);
-            if (T0 == kAllLive && T1 == kAllLive) {
-                live0 = live1 = all;
-            } else {
-                // candidates by the high word of the hash (a superset of the live pairs, about
-                // 2^-31 larger); they are settled exactly below
-                const uint32_t h0 = (uint32_t)(T0 >> 32), h1 = (uint32_t)(T1 >> 32);
-                const uint32_t th0 = h0 == 0xFFFFFFFFu ? h0 : h0 + 1u;
-                const uint32_t th1 = h1 == 0xFFFFFFFFu ? h1 : h1 + 1u;
-                uint64_t x0 = k0 + g0, x1 = k1 + g0;
-                if (nb == (uint32_t)B) {
-#pragma unroll
-                    for (int b = 0; b < B; ++b) {
-                        if (mix64_hi_raw(x0) <= th0) live0 |= 1u << b;
-                        if (mix64_hi_raw(x1) <= th1) live1 |= 1u << b;
-                        x0 += kGamma;
-                        x1 += kGamma;
-                    }
-                } else {
-#pragma unroll
-                    for (int b = 0; b < B; ++b) {
-                        if (b < (int)nb) {
-                            if (mix64_hi_raw(x0) <= th0) live0 |= 1u << b;
-                            if (mix64_hi_raw(x1) <= th1) live1 |= 1u << b;
-                        }
-                        x0 += kGamma;
-                        x1 += kGamma;
-                    }
-                }
-                // exact test for the candidates (about a fraction p of all pairs)
-                if (T0 == kAllLive) live0 = all;
-                else
-                    for (uint32_t t = live0; t; t &= t - 1) {
-                        const int b = __ffs(t) - 1;
-                        if (!live_T(k0, (uint64_t)(r0 + b + 1u) * kGamma, T0)) live0 &= ~(1u << b);
-                    }
-                if (T1 == kAllLive) live1 = all;
-                else
-                    for (uint32_t t = live1; t; t &= t - 1) {
-                        const int b = __ffs(t) - 1;
-                        if (!live_T(k1, (uint64_t)(r0 + b + 1u) * kGamma, T1)) live1 &= ~(1u << b);
-                    }
-            }
-            if (e1 >= m) live1 = 0;
+            pair_live_masks<B>(i, m, smp, r0, nb, g0, live0, live1);
         }
         const uint32_t cntl = __popc(live0) + __popc(live1);
         uint32_t incl = cntl;
@@ -181,15 +188,108 @@ k_sample_emit(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, uin
     }
 }
 
-// One thread per live record; if the record buffer overflowed, redo the batch with the fused
+// Forest of one batch: P[b][v] = v, W[b][v] = (label key of v, size 1).  grid.y = sketch.
+__global__ void __launch_bounds__(256)
+k_forest_init(uint32_t* __restrict__ parent, uint64_t* __restrict__ word, uint32_t n,
+              const uint32_t* __restrict__ cidx, int key_mode) {
+    uint32_t* P = parent + (size_t)blockIdx.y * n;
+    uint64_t* W = word + (size_t)blockIdx.y * n;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        P[v] = v;
+        W[v] = ((uint64_t)label_key(v, key_mode, cidx) << 32) | 1u;
+    }
+}
+
+// Sampling and unions of one batch in one pass over the edges (the forest initialised
+// before).  The live pairs a warp finds go to a queue of the warp in shared memory, one per
+// lane and round; whenever 32 are queued, every lane unites one of them (Rem's union).  The
+// unions are latency-bound and the hashing ALU-bound: while a warp waits on its unions, the
+// SM issues the other warps' hashing, so no record of a live pair ever reaches device memory.
+constexpr int kUnionQ = 64;      // queue entries per warp: at most 31 left + 32 appended
+constexpr int kUniteWarps = 8;
+
+template <int B>
+__global__ void __launch_bounds__(kUniteWarps * 32)
+k_sample_unite(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, uint32_t r0, uint32_t nb,
+               uint32_t* __restrict__ parent, uint32_t n, unsigned long long* __restrict__ live_total) {
+    __shared__ uint32_t qx[kUniteWarps][kUnionQ], qy[kUniteWarps][kUnionQ];
+    __shared__ uint8_t qb[kUniteWarps][kUnionQ];
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t* QX = qx[warp];
+    uint32_t* QY = qy[warp];
+    uint8_t* QB = qb[warp];
+    uint32_t qn = 0;              // queued entries (the same in every lane)
+    uint32_t mine = 0;            // live pairs this lane found
+    const uint64_t npairs = (m + 1) >> 1;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t g0 = (uint64_t)(r0 + 1u) * kGamma;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < npairs; base += stride) {
+        const uint64_t i = base + threadIdx.x;
+        uint32_t l0 = 0, l1 = 0;
+        uint4 two = make_uint4(0, 0, 0, 0);
+        if (i < npairs) {
+            two = __ldcs(edge_pairs + i);
+            pair_live_masks<B>(i, m, smp, r0, nb, g0, l0, l1);
+        }
+        mine += __popc(l0) + __popc(l1);
+        for (;;) {
+            const bool has = (l0 | l1) != 0u;
+            const unsigned bal = __ballot_sync(0xffffffffu, has);
+            if (!bal) break;
+            if (has) {
+                uint32_t x, y, b;
+                if (l0) { b = __ffs(l0) - 1; l0 &= l0 - 1; x = two.x; y = two.y; }
+                else    { b = __ffs(l1) - 1; l1 &= l1 - 1; x = two.z; y = two.w; }
+                const uint32_t pos = qn + __popc(bal & lt);
+                QX[pos] = x;
+                QY[pos] = y;
+                QB[pos] = (uint8_t)b;
+            }
+            qn += __popc(bal);
+            __syncwarp();
+            if (qn >= 32) {
+                qn -= 32;
+                const uint32_t x = QX[qn + lane], y = QY[qn + lane], b = QB[qn + lane];
+                __syncwarp();   // every lane has its entry before the queue grows again
+                unite_rem(parent + (size_t)b * n, x, y);
+            }
+        }
+    }
+    __syncwarp();
+    if (lane < qn) unite_rem(parent + (size_t)QB[lane] * n, QX[lane], QY[lane]);
+#pragma unroll
+    for (int d = 16; d; d >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, d);
+    if (lane == 0 && mine) atomicAdd(live_total, (unsigned long long)mine);
+}
+
+// Rem's union of the batch's live records.  Each thread keeps kUnionChains records in flight
+// (the state of their climbs in registers): every round issues one memory operation per chain
+// -- a parent load or a hooking CAS -- and uses its result in the next round, so a thread
+// waits for one round trip per round instead of one per step of every union.  The record
+// count rec_n[0] is reset by the last block to read it (ticket rec_n[1]), ready for the lane's
+// next batch.  If the record buffer overflowed, the batch is redone with the fused
 // sample+union loop instead (decided on the device, so no host round trip).
+constexpr int kUnionChains = 4;
+
 template <int B>
 __global__ void __launch_bounds__(256)
-k_union_live(const uint4* __restrict__ recs, const unsigned long long* __restrict__ rec_n, uint64_t cap,
+k_union_live(const uint4* __restrict__ recs, unsigned long long* __restrict__ rec_n, uint64_t cap,
              uint32_t* __restrict__ parent, uint32_t n, const uint4* __restrict__ edge_pairs,
              uint64_t m, Sampler smp, uint32_t r0, uint32_t nb, unsigned long long* __restrict__ total) {
-    const unsigned long long cnt = *rec_n;
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(total, cnt);
+    __shared__ unsigned long long s_cnt;
+    if (threadIdx.x == 0) {
+        const unsigned long long c0 = *reinterpret_cast<volatile unsigned long long*>(rec_n);
+        s_cnt = c0;
+        __threadfence();
+        if (atomicAdd(rec_n + 1, 1ull) == gridDim.x - 1ull) {   // every block has the count
+            rec_n[0] = 0;
+            rec_n[1] = 0;
+            atomicAdd(total, c0);
+        }
+    }
+    __syncthreads();
+    const unsigned long long cnt = s_cnt;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     if (cnt > cap) {
         const uint64_t npairs = (m + 1) >> 1;
@@ -198,14 +298,61 @@ k_union_live(const uint4* __restrict__ recs, const unsigned long long* __restric
             sample_union_pair<B>(edge_pairs[i], i, m, smp, g0, nb, parent, n);
         return;
     }
-    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < cnt; j += stride) {
-        const uint4 rc = recs[j];
-        unite_rem(parent + (size_t)rc.z * n, rc.x, rc.y);
+    constexpr int K = kUnionChains;
+    uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t* P[K];
+    uint32_t rx[K], ry[K], px[K], py[K], hres[K];
+    bool act[K], hooked[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        act[k] = false;
+        hooked[k] = false;
+        P[k] = parent;
+        rx[k] = ry[k] = px[k] = py[k] = hres[k] = 0;
     }
-}
-
-__global__ void k_zero_u64(unsigned long long* p) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) *p = 0;
+    for (;;) {
+        // chains without a record take the next one and load both endpoints' parents
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (!act[k] && j < cnt) {
+                const uint4 rc = recs[j];
+                j += stride;
+                P[k] = parent + (size_t)rc.z * n;
+                rx[k] = rc.x;
+                ry[k] = rc.y;
+                px[k] = __ldca(P[k] + rx[k]);
+                py[k] = __ldca(P[k] + ry[k]);
+                act[k] = true;
+            }
+            any |= act[k];
+        }
+        if (!any) break;
+        // one step of every chain (Rem's union with splicing, im_uf.cuh), its memory operation
+        // left in flight for the next round
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (!act[k]) continue;
+            if (hooked[k]) {
+                hooked[k] = false;
+                if (hres[k] == rx[k]) { act[k] = false; continue; }   // hooked rx under py
+                px[k] = hres[k];                                       // rx got a parent meanwhile
+            }
+            if (px[k] == py[k]) { act[k] = false; continue; }          // the paths met
+            if (px[k] < py[k]) {
+                uint32_t t = rx[k]; rx[k] = ry[k]; ry[k] = t;
+                t = px[k]; px[k] = py[k]; py[k] = t;
+            }
+            if (rx[k] == px[k]) {
+                hres[k] = atomicCAS(P[k] + rx[k], rx[k], py[k]);      // hook the root rx under py
+                hooked[k] = true;
+            } else {
+                atomicCAS(P[k] + rx[k], px[k], py[k]);                 // splice
+                rx[k] = px[k];
+                px[k] = __ldca(P[k] + rx[k]);
+            }
+        }
+    }
 }
 
 // grid.y = sketch within the batch.  Full compression, then per root the component size and
@@ -271,11 +418,15 @@ k_compress_count(uint32_t* __restrict__ parent, uint64_t* __restrict__ word, uin
     }
 }
 
+// sketches whose loads a gain thread keeps in flight together (fewer with overlap sums, whose
+// accumulators take the registers)
+template <int kSpec> struct GainUnroll { static constexpr int value = kSpec > 0 ? 4 : 8; };
+
 // Initial gains and compact sketches of one batch; with nspec > 0 also the overlap sums of
 // the candidate first seeds (their roots per sketch staged in shared memory).  kSpec is the
 // capacity of the per-thread overlap accumulators (0, 4 or 8; nspec <= kSpec).
 template <bool kAll, int kSpec>
-__global__ void __launch_bounds__(256, 6)
+__global__ void __launch_bounds__(256, 4)
 k_gain_compact(const uint32_t* __restrict__ parent, const uint64_t* __restrict__ word, uint32_t n,
                uint32_t nb, uint32_t r0, uint32_t R, uint64_t* __restrict__ gain, int first,
                const uint32_t* __restrict__ cidx, uint32_t* __restrict__ label,
@@ -296,19 +447,33 @@ k_gain_compact(const uint32_t* __restrict__ parent, const uint64_t* __restrict__
 #pragma unroll
         for (int k = 0; k < kSpec; ++k) ov[k] = 0;
         const uint32_t ci = kAll ? v : cidx[v];
-        for (uint32_t b = 0; b < nb; ++b) {
-            const uint32_t root = parent[(size_t)b * n + v];
-            const uint64_t w = word[(size_t)b * n + root];
-            const uint32_t c = (uint32_t)w;
-            g += c;
+        // U sketches at a time: their parent loads, then their root words, are
+        // independent, so a thread waits for two memory round trips per group, not per sketch
+        constexpr int U = GainUnroll<kSpec>::value;
+        for (uint32_t b0 = 0; b0 < nb; b0 += U) {
+            uint32_t rt[U];
+            uint64_t wv[U];
 #pragma unroll
-            for (int k = 0; k < kSpec; ++k)
-                if ((uint32_t)k < nspec && root == sroot[b][k]) ov[k] += c;
-            if (ci != kNone) {
-                const uint32_t l = (uint32_t)(w >> 32);   // smallest center index of the component
-                const size_t o = (size_t)ci * R + r0 + b;
-                label[o] = l;
-                size[o] = (l == ci) ? c : 0u;
+            for (int j = 0; j < U; ++j) rt[j] = b0 + j < nb ? parent[(size_t)(b0 + j) * n + v] : 0u;
+#pragma unroll
+            for (int j = 0; j < U; ++j) wv[j] = b0 + j < nb ? word[(size_t)(b0 + j) * n + rt[j]] : 0ull;
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const uint32_t b = b0 + j;
+                if (b >= nb) break;
+                const uint32_t root = rt[j];
+                const uint64_t w = wv[j];
+                const uint32_t c = (uint32_t)w;
+                g += c;
+#pragma unroll
+                for (int k = 0; k < kSpec; ++k)
+                    if ((uint32_t)k < nspec && root == sroot[b][k]) ov[k] += c;
+                if (ci != kNone) {
+                    const uint32_t l = (uint32_t)(w >> 32);   // smallest center index of the component
+                    const size_t o = (size_t)ci * R + r0 + b;
+                    label[o] = l;
+                    size[o] = (l == ci) ? c : 0u;
+                }
             }
         }
         gain[v] = first ? g : gain[v] + g;
@@ -660,15 +825,17 @@ __global__ void k_hub_index(uint32_t n, uint32_t rho, const uint32_t* __restrict
         if (flags[v]) cidx[v] = rho + (uint32_t)pos[v];
 }
 
+// Blocks of the sampling kernel per SM (grid-stride over the edge pairs).
+constexpr unsigned kEmitBlocksPerSM = 16;
+
 // Sampling and unions of one batch as two kernels (records of live pairs in between).
 int launch_sample_split(im_ctx* c, im_ctx::Lane& L, uint32_t r0, uint32_t nb, int key_mode) {
     const unsigned T = 256;
     const uint64_t npairs = (c->m + 1) >> 1;
     const uint4* ep = reinterpret_cast<const uint4*>(c->d_edges);
-    const unsigned gs = grid_for(npairs, T, 152u * 16u);
+    const unsigned gs = grid_for(npairs, T, 152u * kEmitBlocksPerSM);
     const double pl = c->smp.eT ? c->mean_p : c->smp.all_live ? 1.0 : c->p;
     const unsigned gu = grid_for((uint64_t)(pl * (double)c->m * nb) + 1, T, 152u * 16u);
-    IM_LAUNCH(c, K_ZERO, k_zero_u64, 1, 32, 0, L.live_n);
 #define IM_SE(BB)                                                                                 \
     do {                                                                                          \
         IM_LAUNCH(c, K_SAMPLE_EMIT, k_sample_emit<BB>, gs, T, 0, ep, c->m, c->smp, r0, nb, L.live,   \
@@ -696,18 +863,53 @@ int launch_sample_fused(im_ctx* c, im_ctx::Lane& L, uint32_t r0, uint32_t nb) {
     return IM_OK;
 }
 
+// Sampling and unions of one batch in one kernel (k_sample_unite), after the forest
+// initialisation.  The grid is what the SMs hold at once: each warp's queue of live pairs
+// lives as long as the warp.
+int launch_sample_unite(im_ctx* c, im_ctx::Lane& L, uint32_t r0, uint32_t nb) {
+    const uint64_t npairs = (c->m + 1) >> 1;
+    const uint4* ep = reinterpret_cast<const uint4*>(c->d_edges);
+    const unsigned T = kUniteWarps * 32;
+#define IM_SU(BB)                                                                                    \
+    do {                                                                                             \
+        static int per_sm = 0;                                                                       \
+        if (per_sm == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample_unite<BB>, T, 0) \
+                               != cudaSuccess) per_sm = 4;                                           \
+        if (per_sm < 1) per_sm = 1;                                                                  \
+        const unsigned g = grid_for(npairs, T, 152u * (unsigned)per_sm);                             \
+        IM_LAUNCH(c, K_SAMPLE_UNION, k_sample_unite<BB>, g, T, 0, ep, c->m, c->smp, r0, nb, L.parent, c->n, \
+                  c->d_live_total);                                                                  \
+    } while (0)
+    const uint32_t cap = c->batch_used;
+    if (cap <= 1) IM_SU(1);
+    else if (cap <= 2) IM_SU(2);
+    else if (cap <= 4) IM_SU(4);
+    else if (cap <= 8) IM_SU(8);
+    else if (cap <= 16) IM_SU(16);
+    else IM_SU(32);
+#undef IM_SU
+    return IM_OK;
+}
+
 // init + sampling + unions + compression of sketches r0 .. r0+nb-1 in lane L (on c->cur)
 int batch_components(im_ctx* c, im_ctx::Lane& L, uint32_t r0, uint32_t nb, int key_mode) {
     const uint32_t n = c->n;
     const unsigned T = 256;
     const bool sample = (c->smp.eT || c->smp.all_live || c->smp.T != 0) && c->m > 0;
-    const bool split = sample && L.live && nb <= c->batch_used;   // the emit kernel initialises
-    if (!split)
-        IM_LAUNCH(c, K_BATCH_INIT, k_batch_init, grid_for((uint64_t)n * nb, T, 152u * 16u), T, 0,
-                  L.parent, L.word, n, nb, c->d_cidx, key_mode);
-    if (sample) {
-        const int rc = split ? launch_sample_split(c, L, r0, nb, key_mode) : launch_sample_fused(c, L, r0, nb);
+    if (sample && c->union_path == IM_UNION_FUSED && nb <= c->batch_used) {
+        IM_LAUNCH(c, K_BATCH_INIT, k_forest_init, dim3(grid_for(n, T, (152u * 16u + nb - 1) / nb), nb), T, 0,
+                  L.parent, L.word, n, c->d_cidx, key_mode);
+        const int rc = launch_sample_unite(c, L, r0, nb);
         if (rc) return rc;
+    } else {
+        const bool split = sample && L.live && nb <= c->batch_used;   // the emit kernel initialises
+        if (!split)
+            IM_LAUNCH(c, K_BATCH_INIT, k_batch_init, grid_for((uint64_t)n * nb, T, 152u * 16u), T, 0,
+                      L.parent, L.word, n, nb, c->d_cidx, key_mode);
+        if (sample) {
+            const int rc = split ? launch_sample_split(c, L, r0, nb, key_mode) : launch_sample_fused(c, L, r0, nb);
+            if (rc) return rc;
+        }
     }
     // about 8 blocks per SM in all: each block sweeps a stretch of one sketch
     dim3 g(std::max(1u, std::min(grid_for(n, T), (152u * 8u + nb - 1) / nb)), nb);

@@ -4,7 +4,7 @@
 // compression, component histogram) for a single sketch, but its union-find scratch lives in
 // one file-scope device array of fixed size instead of memory obtained from cudaMalloc.
 // Host code must not pass the array's name to a kernel (on the host it is only a stand-in
-// symbol); the device address is looked up once per device with cudaGetSymbolAddress.
+// symbol); its device address comes from cudaGetSymbolAddress in the current context.
 #include <cmath>
 #include <mutex>
 
@@ -72,18 +72,27 @@ __global__ void k_static_write(const uint32_t* __restrict__ P, const uint32_t* _
     }
 }
 
-// Device address of the static scratch on the current device (looked up once per device).
-cudaError_t static_scratch(uint32_t** out) {
+// Device address of the static scratch in the current context.  Outside stream capture it is
+// looked up on every call (cudaGetSymbolAddress allocates nothing), so a context created
+// after a cudaDeviceReset, or a non-primary context made current, gets its own address; the
+// last address found on each device is kept for calls made while `st` is being captured,
+// which must not make runtime calls that are not stream operations.
+cudaError_t static_scratch(cudaStream_t st, uint32_t** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_ptr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess) return e;
         g_static_ptr[dev] = (uint32_t*)p;
+    } else if (!g_static_ptr[dev]) {
+        return cudaErrorStreamCaptureUnsupported;
     }
     *out = g_static_ptr[dev];
     return cudaSuccess;
@@ -104,12 +113,12 @@ extern "C" int im_sketch_static(uint32_t n, uint64_t m, const uint32_t* d_u, con
     if (!d_labels && !d_sizes) return static_fail(IM_EINVAL, "no output requested");
     if (p != p) return static_fail(IM_EINVAL, "p is NaN");
     uint32_t* base = nullptr;
-    cudaError_t e = static_scratch(&base);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = static_scratch(st, &base);
     if (e != cudaSuccess) return static_fail(IM_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
     uint32_t* P = base;
     uint32_t* C = base + IM_STATIC_MAX_N;
     uint32_t* status = base + 2 * (size_t)IM_STATIC_MAX_N;
-    cudaStream_t st = (cudaStream_t)stream;
     Sampler smp{};   // one p for every edge: no per-edge thresholds
     smp.salt = mix64(seed + kGamma);
     smp.all_live = p >= 1.0 ? 1u : 0u;

@@ -108,6 +108,24 @@ def test_sketch_batch_sizes_agree(batch, lanes):
     _compare(g, o, 5)
 
 
+@pytest.mark.parametrize("path", [0, 1])
+@pytest.mark.parametrize("alpha", [1.0, 0.2])
+def test_union_paths_agree(path, alpha):
+    # IM_UNION_FUSED (hashing and unions in one kernel) and IM_UNION_RECORDS (live-pair records
+    # and a union kernel with several unions in flight per thread): both equal the oracle
+    n, u, v = graphgen.erdos_renyi(2500, 9000, 17)
+    with im.IMContext(n, u, v) as ctx:
+        im.im_set_union_path(ctx.h, path)
+        ctx.build_sketches(40, 42, 0.15, alpha)
+        g = dict(gains=ctx.gains(), centers=ctx.centers())
+        g["label"], g["size"] = ctx.compact()
+        g["seeds"], g["seed_gains"] = ctx.select_seeds(6)
+        g["spread"] = ctx.spread(g["seeds"])
+        g["labels"] = {r: ctx.labels(r) for r in (0, 39)}
+    o = _oracle(n, u, v, 42, 0.15, 40, alpha, 6)
+    _compare(g, o, 6)
+
+
 @pytest.mark.parametrize("R", [1, 31, 33, 64])
 def test_ragged_sketch_counts(R):
     n, u, v = graphgen.erdos_renyi(777, 3333, 5)

@@ -3,8 +3,9 @@
 Such callers (a process whose own pool allocator owns the device memory and caps it, or a
 latency-critical loop where cudaMalloc/cudaFree would synchronise the device) pass every
 buffer in; the call's scratch is a static device array.  Checked through the C ABI against
-the context path (im_get_labels, im_get_compact with alpha = 1) on two calls in a row, so
-that leftovers of the first call in the shared scratch would show up in the second.
+the context path (im_get_labels, im_get_compact with alpha = 1) and against the CPU oracle's
+labels on two calls in a row, so that leftovers of the first call in the shared scratch
+would show up in the second.
 """
 import ctypes
 
@@ -12,6 +13,7 @@ import numpy as np
 import pytest
 
 import graphgen
+import oracle
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -48,12 +50,15 @@ def test_static_entry_point_matches_context_path_twice():
     labels = torch.empty(n, dtype=torch.int32, device="cuda")
     sizes = torch.empty(n, dtype=torch.int32, device="cuda")
     # two calls in a row with different sketches and probabilities
+    G = oracle.Graph(n, u, v)
     for seed, p, r in ((42, 0.3, 5), (7, 0.45, 2)):
         got_l, got_s = _static_call(n, du, dv, seed, p, r, labels, sizes)
         want_l, want_s = _reference(n, u, v, seed, p, r)
         assert np.array_equal(got_l, want_l)
         assert np.array_equal(got_s, want_s)
-        assert np.array_equal(got_s, np.bincount(want_l, minlength=n)[want_l])
+        o_l = G.labels(seed, p, 1, r0=r)[0]          # the oracle: BFS labels of sketch r
+        assert np.array_equal(got_l, o_l)
+        assert np.array_equal(got_s, np.bincount(o_l, minlength=n)[o_l])
 
 
 def test_static_entry_point_rejects_oversized_graphs():
