@@ -334,28 +334,41 @@ typedef struct {
 int im_run_batch(im_instance* inst, uint32_t count, uint32_t workers);
 
 /*
- * Serving: resident sketch sets answering requests for seed sets (the paper has no serving
- * layer; this engine is built on its greedy-prefix property: Alg. 1 picks one seed per round,
- * so the best k seeds it finds are the first k of one sequence, whatever other k were asked).
+ * Serving: sketch sets held in HBM under a memory budget, answering requests for seed sets
+ * (the paper has no serving layer; this engine is built on its greedy-prefix property: Alg. 1
+ * picks one seed per round, so the best k seeds it finds are the first k of one sequence,
+ * whatever other k were asked).
  *
- * im_server_create     an empty engine on the current device.
- * im_server_add_model  admits one model -- a graph (HOST edge lists as im_create) with R, seed,
- *                      p, alpha (as im_build_sketches) -- if its estimated device footprint
- *                      (*footprint_out, bytes) leaves 2 GiB of the device free (else IM_ENOMEM,
- *                      nothing allocated), builds its sketches, and starts its host thread.
- *                      *model_out = its id (0, 1, ...).
+ * im_server_create     an empty engine on the current device; its budget is the device's free
+ *                      memory at this call minus 2 GiB.
+ * im_server_set_budget the device bytes resident models may hold together (IM_ESTATE if the
+ *                      models resident now already hold more).
+ * im_server_add_model  registers one model -- a graph (HOST edge lists, copied) with R, seed, p,
+ *                      alpha (as im_build_sketches).  *footprint_out = its estimated device
+ *                      bytes (im_footprint_estimate).  IM_ENOMEM, with nothing allocated, if
+ *                      that exceeds the whole budget; IM_EINVAL for an invalid edge list.  The
+ *                      sketches are built now if they fit beside the resident models, else at
+ *                      the model's first request.  *model_out = its id (0, 1, ...).
  * im_server_replay     submits every request at its arrival time (arrival_ns after the call
  *                      starts) and returns when all are answered.  A model's thread takes all
- *                      of its pending requests at once and extends the model's seed sequence
- *                      to their largest k (one selection run answers them all); the answer to
- *                      (model, k) is the first k seeds of that sequence, their marginal gains and
- *                      the spread estimate sum_{i<k} gain_i (= im_spread of those seeds, by
- *                      telescoping).  submit_ns / done_ns: when the request was queued and
- *                      answered, from the call's start.  Returns IM_OK, or the first failing
- *                      request's status (IM_EINVAL for a model id or k out of range).
+ *                      of its pending requests at once; if the model's sequence known so far
+ *                      answers them they need no GPU; otherwise the model is admitted -- when
+ *                      its footprint does not fit under the budget, idle resident models are
+ *                      evicted (least recently used first; their sequences stay on the host)
+ *                      and, if none is idle, the request waits until one is -- and its
+ *                      device-resident loop (im_serve_launch) extends the sequence to the
+ *                      largest k.  The answer to (model, k) is the first k seeds, their
+ *                      marginal gains and the spread estimate sum_{i<k} gain_i (= im_spread of
+ *                      those seeds, by telescoping), whatever else was in flight and however
+ *                      often the model was evicted and rebuilt.  submit_ns / done_ns: when the
+ *                      request was queued and answered, from the call's start.  Returns IM_OK,
+ *                      or the first failing request's status (IM_EINVAL for a model id or k out
+ *                      of range).
+ * im_server_stats      one model's footprint, builds, evictions, residency and seeds known, and
+ *                      the engine's budget and bytes in use.
  * im_server_destroy    stops the threads and frees every model.
- * The control calls (create, add_model, replay, destroy) are made from one thread, one at a
- * time; the engine's own threads only touch their model.
+ * The control calls (create, set_budget, add_model, replay, stats, destroy) are made from one
+ * thread, one at a time; the engine's own threads only touch their model.
  */
 typedef struct im_server im_server;
 typedef struct {
@@ -370,11 +383,29 @@ typedef struct {
     int status;             /* out */
 } im_request;
 
+typedef struct {
+    uint64_t footprint;     /* estimated device bytes while resident */
+    uint32_t builds;        /* sketch builds so far (1 + rebuilds after evictions) */
+    uint32_t evictions;
+    uint32_t resident;      /* 1 if its sketches are in HBM now */
+    uint32_t known_seeds;   /* length of its sequence known on the host */
+    uint64_t budget;        /* the engine's budget and bytes held by resident models */
+    uint64_t used;
+} im_model_stats;
+
 int im_server_create(im_server** out);
+int im_server_set_budget(im_server* srv, uint64_t bytes);
 int im_server_add_model(im_server* srv, uint32_t n, uint64_t m, const uint32_t* u, const uint32_t* v, uint32_t R,
                         uint64_t seed, double p, double alpha, uint32_t* model_out, uint64_t* footprint_out);
 int im_server_replay(im_server* srv, im_request* req, uint32_t count);
+int im_server_stats(im_server* srv, uint32_t model, im_model_stats* out);
 int im_server_destroy(im_server* srv);
+
+/* Estimated device bytes of one context holding a graph of n vertices and m edges with R
+ * sketches at probability p and center fraction alpha (graph, per-vertex arrays, two lanes of
+ * union-find scratch and live-pair records, compact and hub rows); an upper bound on what
+ * im_create + im_build_sketches allocate.  IM_EINVAL for n = 0, R = 0 or alpha outside (0, 1]. */
+int im_footprint_estimate(uint32_t n, uint64_t m, uint32_t R, double p, double alpha, uint64_t* bytes_out);
 
 /* Tuning: hubs.  GetCenter (Alg. 3) from a vertex whose component reaches a high-degree
  * non-center tests that vertex's whole adjacency list, in every sketch where it is reached.
@@ -386,6 +417,53 @@ int im_server_destroy(im_server* srv);
  * (default 32).  Costs 8 R bytes per hub; takes effect at the next im_build_sketches. */
 #define IM_HUBS_AUTO 0xFFFFFFFFu
 int im_set_hubs(im_ctx* ctx, uint32_t cap, uint32_t min_degree);
+
+/*
+ * Device-resident request loop (serving).  Alg. 1 picks one seed per round, so the answer to
+ * "k seeds" is the first k seeds of one greedy sequence; a loop on the device answers requests
+ * for k from a mailbox and extends the sequence only as far as the largest k asked.
+ *
+ * The mailbox lives in mapped pinned host memory (allocated by im_mailbox_create, owned by
+ * the caller until im_mailbox_destroy): a ring of `ring` requested k values and room for the
+ * first `kcap` seeds and gains.  im_serve_launch starts, on the context's stream, one CUDA
+ * graph that repeats: wait for requests (the device polls the mailbox), run the lazy-greedy
+ * rounds (Alg. 2 / Alg. 4, the same kernels as im_select_seeds) up to the largest pending k,
+ * publish the new seeds and gains into the mailbox.  Requests pushed while it runs are taken
+ * by its next wait -- no new launch, no host round trip.  Every wait of the device is bounded:
+ * when no request arrives for idle_us microseconds (at most 10^7; also after 2^24 polls) the
+ * loop ends with status IM_ETIMEOUT and clears its `running` flag; a request pushed after that
+ * needs a new im_serve_launch.
+ *
+ * While a loop serves a context (from im_serve_launch to im_serve_finish) the context's other
+ * calls that use the sequence or the sketches return IM_ESTATE.  One context is not thread-safe:
+ * push, wait, launch and finish are made from one thread (or under the caller's lock).
+ *
+ *   im_mailbox_create   ring in [1, 65536], kcap in [1, n].  IM_ENOMEM without host memory.
+ *   im_mailbox_push     queue a request for k in [1, kcap] seeds; IM_ESTATE when `ring`
+ *                       requests are still untaken.
+ *   im_serve_launch     start a loop (idle_us as above); a context that was rebuilt since the
+ *                       last loop publishes its new sequence from the start.
+ *   im_mailbox_wait     wait on the host until the first k seeds are published, then copy them
+ *                       (and their marginal gains) to seeds / gains (caller-owned, k entries,
+ *                       either may be NULL).  IM_ETIMEOUT after timeout_us; IM_ESTATE when no
+ *                       loop is running and fewer than k seeds are published; IM_EDEVICE when
+ *                       the loop's selection stopped on an error.
+ *   im_mailbox_state    running flag, status of the last loop, seeds published.
+ *   im_serve_finish     ask the loop to end at its next wait, wait for it, and bring the
+ *                       context's own copy of the sequence up to date (im_select_seeds then
+ *                       continues it).  *loop_status: IM_OK (ended by this call),
+ *                       IM_ETIMEOUT (it had idled out), IM_EDEVICE.
+ *   im_mailbox_destroy  IM_ESTATE while a loop still serves the mailbox.
+ * The paper has no serving layer; the rounds are those of Alg. 2 / Alg. 4.
+ */
+typedef struct im_mailbox im_mailbox;
+int im_mailbox_create(im_ctx* ctx, uint32_t ring, uint32_t kcap, im_mailbox** out);
+int im_mailbox_push(im_mailbox* mb, uint32_t k);
+int im_serve_launch(im_mailbox* mb, uint32_t idle_us);
+int im_mailbox_wait(im_mailbox* mb, uint32_t k, uint32_t timeout_us, uint32_t* seeds, uint64_t* gains);
+int im_mailbox_state(const im_mailbox* mb, uint32_t* running, int32_t* status, uint32_t* answered);
+int im_serve_finish(im_mailbox* mb, int32_t* loop_status);
+int im_mailbox_destroy(im_mailbox* mb);
 
 /*
  * Autotuning of the knobs that leave every result unchanged: sketches per edge pass

@@ -54,6 +54,12 @@ class im_request(ctypes.Structure):
                 ("done_ns", ctypes.c_uint64), ("status", ctypes.c_int)]
 
 
+class im_model_stats(ctypes.Structure):
+    _fields_ = [("footprint", ctypes.c_uint64), ("builds", ctypes.c_uint32), ("evictions", ctypes.c_uint32),
+                ("resident", ctypes.c_uint32), ("known_seeds", ctypes.c_uint32), ("budget", ctypes.c_uint64),
+                ("used", ctypes.c_uint64)]
+
+
 class im_tuning(ctypes.Structure):
     _fields_ = [("sketch_batch", ctypes.c_uint32), ("lanes", ctypes.c_uint32), ("hub_cap", ctypes.c_uint32),
                 ("tried", ctypes.c_uint32), ("build_ms", ctypes.c_double), ("select_ms", ctypes.c_double),
@@ -95,6 +101,16 @@ def lib():
         "im_set_pipeline": ([vp, u32], i32),
         "im_set_union_path": ([vp, i32], i32),
         "im_debug_fail_alloc": ([c.c_int64], i32),
+        "im_mailbox_create": ([vp, u32, u32, c.POINTER(vp)], i32),
+        "im_server_set_budget": ([vp, u64], i32),
+        "im_server_stats": ([vp, u32, c.POINTER(im_model_stats)], i32),
+        "im_footprint_estimate": ([u32, u64, u32, dbl, dbl, c.POINTER(u64)], i32),
+        "im_mailbox_push": ([vp, u32], i32),
+        "im_serve_launch": ([vp, u32], i32),
+        "im_mailbox_wait": ([vp, u32, u32, vp, vp], i32),
+        "im_mailbox_state": ([vp, c.POINTER(u32), c.POINTER(c.c_int32), c.POINTER(u32)], i32),
+        "im_serve_finish": ([vp, c.POINTER(c.c_int32)], i32),
+        "im_mailbox_destroy": ([vp], i32),
         "im_set_graph": ([vp, i32], i32),
         "im_hash_peak": ([u32, c.POINTER(dbl)], i32),
         "im_set_seed_speculation": ([vp, u32], i32),
@@ -367,6 +383,18 @@ class IMServer:
             raise IMError(rc, f"im_server_add_model (estimated {fp.value} bytes)")
         return int(mid.value), int(fp.value)
 
+    def set_budget(self, nbytes: int):
+        rc = lib().im_server_set_budget(self.h, int(nbytes))
+        if rc != IM_OK:
+            raise IMError(rc, "im_server_set_budget")
+
+    def stats(self, model: int) -> dict:
+        out = im_model_stats()
+        rc = lib().im_server_stats(self.h, model, ctypes.byref(out))
+        if rc != IM_OK:
+            raise IMError(rc, "im_server_stats")
+        return {f: getattr(out, f) for f, _ in im_model_stats._fields_}
+
     def replay(self, requests):
         """requests: (model, k, arrival_ns) tuples.  Returns dicts with seeds, gains, spread,
         submit_ns, done_ns, in input order."""
@@ -417,6 +445,15 @@ def im_autotune(ctx, R: int, seed: int, p: float, alpha: float, k: int, reps: in
     out = im_tuning()
     _check(ctx, lib().im_autotune(ctx, R, seed, p, alpha, k, reps, ctypes.byref(out)))
     return {f: getattr(out, f) for f, _ in im_tuning._fields_}
+
+
+def im_footprint_estimate(n: int, m: int, R: int, p: float, alpha: float) -> int:
+    """Estimated device bytes of a context holding that graph and its sketches."""
+    out = ctypes.c_uint64(0)
+    rc = lib().im_footprint_estimate(n, m, R, p, alpha, ctypes.byref(out))
+    if rc != IM_OK:
+        raise IMError(rc, "im_footprint_estimate")
+    return int(out.value)
 
 
 def im_hash_peak(iters: int = 4096) -> float:
@@ -522,3 +559,44 @@ class IMContext:
             self.close()
         except Exception:
             pass
+
+class Mailbox:
+    """A device-resident request loop's mailbox on a context (im_mailbox_* / im_serve_*)."""
+
+    def __init__(self, ctx, ring: int = 64, kcap: int | None = None):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        _check(ctx.h, lib().im_mailbox_create(ctx.h, ring, kcap if kcap else ctx.n, ctypes.byref(h)))
+        self.h = h
+
+    def push(self, k: int):
+        _check(self.ctx.h, lib().im_mailbox_push(self.h, k))
+
+    def launch(self, idle_us: int = 20000):
+        _check(self.ctx.h, lib().im_serve_launch(self.h, idle_us))
+
+    def wait(self, k: int, timeout_us: int = 30_000_000):
+        seeds = np.zeros(k, np.uint32)
+        gains = np.zeros(k, np.uint64)
+        _check(self.ctx.h, lib().im_mailbox_wait(self.h, k, timeout_us, seeds.ctypes.data_as(ctypes.c_void_p),
+                                                 gains.ctypes.data_as(ctypes.c_void_p)))
+        return seeds, gains
+
+    def state(self):
+        r, st, a = ctypes.c_uint32(0), ctypes.c_int32(0), ctypes.c_uint32(0)
+        _check(self.ctx.h, lib().im_mailbox_state(self.h, ctypes.byref(r), ctypes.byref(st), ctypes.byref(a)))
+        return {"running": int(r.value), "status": int(st.value), "answered": int(a.value)}
+
+    def finish(self) -> int:
+        st = ctypes.c_int32(0)
+        _check(self.ctx.h, lib().im_serve_finish(self.h, ctypes.byref(st)))
+        return int(st.value)
+
+    def close(self):
+        """Ends a loop still serving the mailbox (im_serve_finish), then frees it."""
+        if self.h:
+            st = ctypes.c_int32(0)
+            lib().im_serve_finish(self.h, ctypes.byref(st))
+            _check(self.ctx.h, lib().im_mailbox_destroy(self.h))
+            self.h = None
+

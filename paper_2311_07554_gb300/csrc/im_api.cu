@@ -363,6 +363,7 @@ int im_set_refresh_threshold(im_ctx* c, uint64_t min_batch) {
 
 int im_load_graph(im_ctx* c, uint32_t n, uint64_t m, const uint32_t* u, const uint32_t* v, int ptr_kind) {
     if (!c) return IM_EINVAL;
+    if (c->serving) return im_fail(c, IM_ESTATE, "a serving loop owns the context (im_serve_finish first)");
     if (n == 0 || n >= 0x80000000u) return im_fail(c, IM_EINVAL, "n must be in [1, 2^31)");
     if (m >= 0xFFFFFFFFull) return im_fail(c, IM_EINVAL, "m must be < 2^32");
     if (ptr_kind != IM_PTR_HOST && ptr_kind != IM_PTR_DEVICE) return im_fail(c, IM_EINVAL, "bad ptr_kind");
@@ -383,6 +384,7 @@ int im_load_graph(im_ctx* c, uint32_t n, uint64_t m, const uint32_t* u, const ui
 
 int im_set_edge_probs(im_ctx* c, int model, const double* p, int ptr_kind) {
     if (!c) return IM_EINVAL;
+    if (c->serving) return im_fail(c, IM_ESTATE, "a serving loop owns the context (im_serve_finish first)");
     if (!c->graph_ok) return im_fail(c, IM_ESTATE, "no valid graph is loaded");
     if (model != IM_PROBS_UNIFORM && model != IM_PROBS_ARRAY && model != IM_PROBS_WIC)
         return im_fail(c, IM_EINVAL, "unknown probability model");
@@ -417,6 +419,7 @@ int im_set_edge_probs(im_ctx* c, int model, const double* p, int ptr_kind) {
 
 int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alpha) {
     if (!c) return IM_EINVAL;
+    if (c->serving) return im_fail(c, IM_ESTATE, "a serving loop owns the context (im_serve_finish first)");
     if (!c->graph_ok) return im_fail(c, IM_ESTATE, "no valid graph is loaded");
     if (R == 0 || R > 65536) return im_fail(c, IM_EINVAL, "R must be in [1, 65536]");
     if (!(alpha > 0.0) || alpha > 1.0) return im_fail(c, IM_EINVAL, "alpha must be in (0, 1]");
@@ -582,6 +585,7 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
 
 int im_select_seeds(im_ctx* c, uint32_t k, uint32_t* seeds_out, uint64_t* gains_out) {
     if (!c) return IM_EINVAL;
+    if (c->serving) return im_fail(c, IM_ESTATE, "a serving loop owns the context (im_serve_finish first)");
     if (!c->built) return im_fail(c, IM_ESTATE, "im_build_sketches has not run");
     if (k == 0 || k > c->n) return im_fail(c, IM_EINVAL, "k must be in [1, n]");
     if (!seeds_out) return im_fail(c, IM_EINVAL, "seeds_out is NULL");
@@ -596,6 +600,7 @@ int im_select_seeds(im_ctx* c, uint32_t k, uint32_t* seeds_out, uint64_t* gains_
 
 int im_reset_selection(im_ctx* c) {
     if (!c) return IM_EINVAL;
+    if (c->serving) return im_fail(c, IM_ESTATE, "a serving loop owns the context (im_serve_finish first)");
     if (!c->built) return im_fail(c, IM_ESTATE, "im_build_sketches has not run");
     int rc = im_selection_init(c, false);
     if (rc) return rc;
@@ -605,6 +610,7 @@ int im_reset_selection(im_ctx* c) {
 
 int im_spread(im_ctx* c, const uint32_t* seeds, uint32_t k, uint64_t* spread_out) {
     if (!c) return IM_EINVAL;
+    if (c->serving) return im_fail(c, IM_ESTATE, "a serving loop owns the context (im_serve_finish first)");
     if (!c->built) return im_fail(c, IM_ESTATE, "im_build_sketches has not run");
     if (!spread_out) return im_fail(c, IM_EINVAL, "spread_out is NULL");
     if (k > kSpreadKMax) return im_fail(c, IM_EINVAL, "k exceeds 16384");
@@ -626,6 +632,7 @@ int im_spread(im_ctx* c, const uint32_t* seeds, uint32_t k, uint64_t* spread_out
 
 int im_mc_spread(im_ctx* c, const uint32_t* seeds, uint32_t k, uint32_t sims, uint64_t mc_seed, uint64_t* out) {
     if (!c) return IM_EINVAL;
+    if (c->serving) return im_fail(c, IM_ESTATE, "a serving loop owns the context (im_serve_finish first)");
     if (!c->built) return im_fail(c, IM_ESTATE, "im_build_sketches has not run");
     if (!out) return im_fail(c, IM_EINVAL, "out is NULL");
     if (k > kSpreadKMax) return im_fail(c, IM_EINVAL, "k exceeds 16384");
@@ -798,6 +805,7 @@ const char* im_last_error(const im_ctx* c) { return c ? c->err.c_str() : g_creat
 
 void im_destroy(im_ctx* c) {
     if (!c) return;
+    im_serve_stop(c);
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_sketch_state(c);
     dfree(c->d_edges); dfree(c->d_off); dfree(c->d_arcs); dfree(c->d_arc_cur); dfree(c->d_upload);

@@ -136,6 +136,29 @@ __device__ __forceinline__ uint32_t center_index(const SketchView& s, uint32_t x
     return s.all_centers ? x : __ldg(s.cidx + x);
 }
 
+// Request mailbox of a device-resident selection loop (im_serve_launch), in mapped pinned host
+// memory.  The host writes a requested k into the ring and raises head; the loop on the
+// device takes every pending request, extends the greedy sequence to the largest k, copies
+// the new seeds and gains behind the ring and raises `answered`.  Layout: this header, then
+// k[ring] (u32), seeds[kcap] (u32), gains[kcap] (u64, 8-byte aligned).
+struct MailboxShared {
+    unsigned int head;           // host: requests pushed (counts up)
+    unsigned int tail;           // device: requests taken (counts up)
+    unsigned int answered;       // device: seeds published
+    int status;                  // device: IM_ETIMEOUT after an idle exit, IM_EDEVICE after a
+                                 // selection error, else IM_OK
+    unsigned int running;        // host sets it before a launch; the device clears it when its loop
+                                 // stops taking requests
+    unsigned int stop;           // host: end the loop at its next wait
+    unsigned int exits;          // device: loop launches that ended
+    unsigned int ring;           // capacity of k[] (requests in flight)
+    unsigned int kcap;           // capacity of seeds[] / gains[]
+    unsigned int pad0;
+    unsigned long long idle_ns;  // a wait with no request ends the loop after this long
+    unsigned int pad[4];
+};
+static_assert(sizeof(MailboxShared) == 64, "mailbox header");
+
 // Device-side selection state (one per context).
 struct SelState {
     unsigned long long best;        // max fresh key this round
@@ -336,6 +359,12 @@ struct im_ctx {
     cudaStream_t cap_stream = nullptr;   // owned; only used to capture
     cudaGraph_t sel_graph = nullptr;
     cudaGraphExec_t sel_exec = nullptr;
+    // the device-resident request loop (im_serve_launch): built for one mailbox at a time
+    cudaGraph_t serve_graph = nullptr;
+    cudaGraphExec_t serve_exec = nullptr;
+    const void* serve_mb = nullptr;          // the mailbox serve_exec was built for
+    bool serving = false;                    // a loop was launched and not finished: the host copy
+                                             // of the sequence (seeds, seed_gains) is stale
     unsigned step_grid = 0;          // blocks of k_sel_step (resident at once)
     uint64_t* d_topb = nullptr;      // 32 keys per step-kernel block (PH_TOPB)
     bool capturing = false;              // launches go into a graph: no events, no counting
@@ -456,6 +485,7 @@ int im_selection_init(im_ctx* c, bool fresh);
 int im_select_run(im_ctx* c, uint32_t k);   // rounds until k seeds are chosen
 void im_select_graph_free(im_ctx* c);
 int im_spread_run(im_ctx* c, uint32_t k, uint64_t* out);
+void im_serve_stop(im_ctx* c);   // asks a serving loop on the context to end (before a destroy)
 
 int im_fail(im_ctx* c, int code, const std::string& msg);
 // Every device allocation of the library goes through here: cudaMalloc, unless a failure was

@@ -10,6 +10,10 @@
 // keys are upper bounds by submodularity (Eq. 2), so the winner equals plain greedy's.
 #include <cstring>
 
+#include <chrono>
+#include <new>
+#include <thread>
+
 #include "im_internal.cuh"
 
 using namespace imk;
@@ -1947,6 +1951,43 @@ int cap_conditional(im_ctx* c, cudaGraphConditionalHandle h, cudaGraphConditiona
 // round_end rounds.
 constexpr int kStepsPerLoop = 8;
 
+// The selection loop added to `root` after the nodes `deps`: k_sel_begin, then
+//   while (outer) { while (inner) { k_sel_step x kStepsPerLoop }; switch (rare) { ... } }
+// *last receives the outer loop node.  hd carries the rare evaluators' launch counts on entry.
+int add_selection(im_ctx* c, cudaGraph_t root, const cudaGraphNode_t* deps, size_t ndeps, SelHandles& hd,
+                  cudaGraphNode_t* last) {
+    int rc = IM_OK;
+    // the outer loop node first, so that the handles sel_begin sets exist before it is captured
+    IM_CUDA(c, cudaGraphConditionalHandleCreate(&hd.outer, root, 0, 0));
+    cudaGraph_t obody = nullptr, ibody = nullptr, rcases[RARE_COUNT] = {};
+    cudaGraphNode_t onode = nullptr;
+    if ((rc = add_conditional(c, root, hd.outer, cudaGraphCondTypeWhile, 1, &obody, &onode))) return rc;
+    IM_CUDA(c, cudaGraphConditionalHandleCreate(&hd.inner, obody, 0, 0));
+    IM_CUDA(c, cudaGraphConditionalHandleCreate(&hd.rare, obody, RARE_NONE, 0));
+    if ((rc = cap_begin(c, root, deps, ndeps))) return rc;
+    IM_LAUNCH(c, K_SEL_BEGIN, k_sel_begin, 1, 32, 0, c->d_sel, hd);
+    cudaGraphNode_t first = nullptr;
+    if ((rc = cap_frontier(c, &first))) return rc;
+    if ((rc = cap_end(c))) return rc;
+    IM_CUDA(c, cudaGraphAddDependencies(root, &first, &onode, nullptr, 1));
+
+    if ((rc = cap_begin(c, obody, nullptr, 0))) return rc;
+    if ((rc = cap_conditional(c, hd.inner, cudaGraphCondTypeWhile, 1, &ibody))) return rc;
+    if ((rc = cap_conditional(c, hd.rare, cudaGraphCondTypeSwitch, RARE_COUNT, rcases))) return rc;
+    if ((rc = cap_end(c))) return rc;
+    if ((rc = cap_begin(c, ibody, nullptr, 0))) return rc;
+    for (int i = 0; i < kStepsPerLoop && !rc; ++i) rc = launch_step(c, hd);
+    if (rc) return rc;
+    if ((rc = cap_end(c))) return rc;
+    for (unsigned m = 0; m < RARE_COUNT; ++m) {
+        if ((rc = cap_begin(c, rcases[m], nullptr, 0))) return rc;
+        if ((rc = enqueue_rare(c, m, hd))) return rc;
+        if ((rc = cap_end(c))) return rc;
+    }
+    *last = onode;
+    return IM_OK;
+}
+
 int build_select_graph_steps(im_ctx* c) {
     SelHandles hd{};
     hd.on = 1;
@@ -1963,33 +2004,8 @@ int build_select_graph_steps(im_ctx* c) {
     if ((rc = size_step_grid(c))) return rc;   // before the capture
 
     IM_CUDA(c, cudaGraphCreate(&c->sel_graph, 0));
-    // the outer loop node first, so that the handles sel_begin sets exist before it is captured
-    IM_CUDA(c, cudaGraphConditionalHandleCreate(&hd.outer, c->sel_graph, 0, 0));
-    cudaGraph_t obody = nullptr, ibody = nullptr, rcases[RARE_COUNT] = {};
     cudaGraphNode_t onode = nullptr;
-    if ((rc = add_conditional(c, c->sel_graph, hd.outer, cudaGraphCondTypeWhile, 1, &obody, &onode))) return rc;
-    IM_CUDA(c, cudaGraphConditionalHandleCreate(&hd.inner, obody, 0, 0));
-    IM_CUDA(c, cudaGraphConditionalHandleCreate(&hd.rare, obody, RARE_NONE, 0));
-    if ((rc = cap_begin(c, c->sel_graph, nullptr, 0))) return rc;
-    IM_LAUNCH(c, K_SEL_BEGIN, k_sel_begin, 1, 32, 0, c->d_sel, hd);
-    cudaGraphNode_t first = nullptr;
-    if ((rc = cap_frontier(c, &first))) return rc;
-    if ((rc = cap_end(c))) return rc;
-    IM_CUDA(c, cudaGraphAddDependencies(c->sel_graph, &first, &onode, nullptr, 1));
-
-    if ((rc = cap_begin(c, obody, nullptr, 0))) return rc;
-    if ((rc = cap_conditional(c, hd.inner, cudaGraphCondTypeWhile, 1, &ibody))) return rc;
-    if ((rc = cap_conditional(c, hd.rare, cudaGraphCondTypeSwitch, RARE_COUNT, rcases))) return rc;
-    if ((rc = cap_end(c))) return rc;
-    if ((rc = cap_begin(c, ibody, nullptr, 0))) return rc;
-    for (int i = 0; i < kStepsPerLoop && !rc; ++i) rc = launch_step(c, hd);
-    if (rc) return rc;
-    if ((rc = cap_end(c))) return rc;
-    for (unsigned m = 0; m < RARE_COUNT; ++m) {
-        if ((rc = cap_begin(c, rcases[m], nullptr, 0))) return rc;
-        if ((rc = enqueue_rare(c, m, hd))) return rc;
-        if ((rc = cap_end(c))) return rc;
-    }
+    if ((rc = add_selection(c, c->sel_graph, nullptr, 0, hd, &onode))) return rc;
     IM_CUDA(c, cudaGraphInstantiate(&c->sel_exec, c->sel_graph, 0));
     return IM_OK;
 }
@@ -2037,6 +2053,144 @@ int run_rounds_host(im_ctx* c) {
     }
 }
 
+// ---- the device-resident request loop -------------------------------------------------
+// serve graph:  while (serve) { k_mb_take; <selection loop>; k_mb_publish }
+// k_mb_take waits (bounded) for requests in the mailbox and sets the selection's target to the
+// largest requested k; the selection loop runs the rounds up to it (Alg. 1, Alg. 2 / Alg. 4);
+// k_mb_publish copies the new seeds and gains into the mailbox.  A wait that sees no request
+// for idle_ns (or kMbMaxPolls polls) ends the loop with IM_ETIMEOUT; the host launches it again
+// for its next request.
+
+__device__ __forceinline__ unsigned ld_acquire_sys(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_sys(unsigned* p, unsigned v) {
+    asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr unsigned kMbMaxPolls = 1u << 24;   // polls of one wait at most, whatever the clock says
+
+__global__ void k_mb_take(MailboxShared* mb, SelState* st, cudaGraphConditionalHandle serve, uint32_t n,
+                          unsigned long long refresh_min) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const unsigned* kring = reinterpret_cast<const unsigned*>(mb + 1);
+    const unsigned ring = mb->ring, kcap = mb->kcap;
+    const unsigned long long idle_ns = mb->idle_ns;
+    const unsigned tail = mb->tail;   // only this kernel writes it
+    const unsigned long long t0 = global_ns();
+    for (unsigned polls = 0;; ++polls) {
+        const unsigned stop = ld_acquire_sys(&mb->stop);
+        unsigned head = ld_acquire_sys(&mb->head);
+        bool idle = false;
+        if (!stop && head == tail && (polls >= kMbMaxPolls || global_ns() - t0 >= idle_ns)) {
+            // idle: clear `running`, then look once more -- a request pushed before the host read
+            // running == 0 is taken now; one pushed after it gets a new launch from the host
+            atomicExch_system(&mb->running, 0u);
+            __threadfence_system();
+            head = ld_acquire_sys(&mb->head);
+            if (head == tail) idle = true;
+            else atomicExch_system(&mb->running, 1u);
+        }
+        if (stop || idle) {
+            if (stop) atomicExch_system(&mb->running, 0u);
+            *reinterpret_cast<volatile int*>(&mb->status) = stop ? IM_OK : IM_ETIMEOUT;
+            st->round_end = st->round;   // no round in this pass of the loop
+            __threadfence_system();
+            atomicAdd_system(&mb->exits, 1u);
+            cudaGraphSetConditional(serve, 0);
+            return;
+        }
+        if (head != tail) {
+            const unsigned cnt = head - tail < ring ? head - tail : ring;   // the host keeps <= ring in flight
+            unsigned kmax = 0;
+            for (unsigned i = 0; i < cnt; ++i) kmax = max(kmax, kring[(tail + i) % ring]);
+            st_release_sys(&mb->tail, tail + cnt);
+            kmax = min(min(kmax, n), kcap);
+            st->round_end = max(st->round, kmax);   // the sequence only grows
+            st->refresh_min = refresh_min;
+            *reinterpret_cast<volatile int*>(&mb->status) = IM_OK;
+            cudaGraphSetConditional(serve, 1);
+            return;
+        }
+        __nanosleep(500);
+    }
+}
+
+__global__ void k_mb_publish(MailboxShared* mb, const SelState* st, const uint32_t* __restrict__ seed_list,
+                             const uint64_t* __restrict__ gain_list, cudaGraphConditionalHandle serve) {
+    __shared__ unsigned from, to;
+    if (threadIdx.x == 0) {
+        from = *reinterpret_cast<volatile unsigned*>(&mb->answered);
+        to = min(st->round, mb->kcap);
+    }
+    __syncthreads();
+    unsigned* seeds = reinterpret_cast<unsigned*>(mb + 1) + mb->ring;
+    const size_t goff = ((size_t)(mb->ring + mb->kcap) * 4 + 7) & ~(size_t)7;
+    unsigned long long* gains = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(mb + 1) + goff);
+    for (unsigned i = from + threadIdx.x; i < to; i += blockDim.x) {
+        seeds[i] = seed_list[i];
+        gains[i] = gain_list[i];
+    }
+    __threadfence_system();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (to > from) st_release_sys(&mb->answered, to);
+        if (st->err || st->fb_overflow) {   // the selection stopped: so does the loop
+            *reinterpret_cast<volatile int*>(&mb->status) = IM_EDEVICE;
+            atomicExch_system(&mb->running, 0u);
+            __threadfence_system();
+            atomicAdd_system(&mb->exits, 1u);
+            cudaGraphSetConditional(serve, 0);
+        }
+    }
+}
+
+size_t mailbox_bytes(uint32_t ring, uint32_t kcap) {
+    return sizeof(MailboxShared) + ((((size_t)ring + kcap) * 4 + 7) & ~(size_t)7) + (size_t)kcap * 8;
+}
+
+int build_serve_graph(im_ctx* c, MailboxShared* dmb) {
+    SelHandles hd{};
+    hd.on = 1;
+    c->count_only = true;
+    int rc = IM_OK;
+    for (unsigned m = 0; m < RARE_COUNT && !rc; ++m) {
+        c->dry_count = 0;
+        rc = enqueue_rare(c, m, hd);
+        hd.rare_launches[m] = (unsigned)c->dry_count;
+    }
+    c->count_only = false;
+    if (rc) return rc;
+    if ((rc = size_step_grid(c))) return rc;
+    IM_CUDA(c, cudaGraphCreate(&c->serve_graph, 0));
+    cudaGraphConditionalHandle hserve;
+    IM_CUDA(c, cudaGraphConditionalHandleCreate(&hserve, c->serve_graph, 1, cudaGraphCondAssignDefault));
+    cudaGraph_t body = nullptr;
+    cudaGraphNode_t snode = nullptr;
+    if ((rc = add_conditional(c, c->serve_graph, hserve, cudaGraphCondTypeWhile, 1, &body, &snode))) return rc;
+    if ((rc = cap_begin(c, body, nullptr, 0))) return rc;
+    IM_LAUNCH(c, K_SEL_BEGIN, k_mb_take, 1, 32, 0, dmb, c->d_sel, hserve, c->n, (unsigned long long)c->refresh_min);
+    cudaGraphNode_t take = nullptr;
+    if ((rc = cap_frontier(c, &take))) return rc;
+    if ((rc = cap_end(c))) return rc;
+    cudaGraphNode_t onode = nullptr;
+    if ((rc = add_selection(c, body, &take, 1, hd, &onode))) return rc;
+    if ((rc = cap_begin(c, body, &onode, 1))) return rc;
+    IM_LAUNCH(c, K_SEL_BEGIN, k_mb_publish, 1, 256, 0, dmb, c->d_sel, c->d_seed_list, c->d_gain_list, hserve);
+    if ((rc = cap_end(c))) return rc;
+    IM_CUDA(c, cudaGraphInstantiate(&c->serve_exec, c->serve_graph, 0));
+    return IM_OK;
+}
+
 }  // namespace
 
 void im_select_graph_free(im_ctx* c) {
@@ -2044,6 +2198,27 @@ void im_select_graph_free(im_ctx* c) {
     if (c->sel_graph) cudaGraphDestroy(c->sel_graph);
     c->sel_exec = nullptr;
     c->sel_graph = nullptr;
+    if (c->serve_exec) cudaGraphExecDestroy(c->serve_exec);
+    if (c->serve_graph) cudaGraphDestroy(c->serve_graph);
+    c->serve_exec = nullptr;
+    c->serve_graph = nullptr;
+    c->serve_mb = nullptr;
+}
+
+// Appends the device's seeds, gains and evaluation counts of rounds [r0, r1) to the host copy.
+static int copy_new_seeds(im_ctx* c, uint32_t r0, uint32_t r1) {
+    if (r1 <= r0) return IM_OK;
+    const size_t cnt = r1 - r0;
+    std::vector<uint32_t> sd(cnt);
+    std::vector<uint64_t> gn(cnt), ev(cnt);
+    IM_CUDA(c, cudaMemcpyAsync(sd.data(), c->d_seed_list + r0, cnt * 4, cudaMemcpyDeviceToHost, c->stream));
+    IM_CUDA(c, cudaMemcpyAsync(gn.data(), c->d_gain_list + r0, cnt * 8, cudaMemcpyDeviceToHost, c->stream));
+    IM_CUDA(c, cudaMemcpyAsync(ev.data(), c->d_round_evals + r0, cnt * 8, cudaMemcpyDeviceToHost, c->stream));
+    IM_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->seeds.insert(c->seeds.end(), sd.begin(), sd.end());
+    c->seed_gains.insert(c->seed_gains.end(), gn.begin(), gn.end());
+    c->round_evals.insert(c->round_evals.end(), ev.begin(), ev.end());
+    return IM_OK;
 }
 
 // Rounds of lazy greedy (NextSeed + MarkSeed) until k seeds are chosen.
@@ -2068,19 +2243,7 @@ int im_select_run(im_ctx* c, uint32_t k) {
     c->dev_launches_seen = h.launches;
     // rounds completed before any error keep their seeds
     const uint32_t r1 = h.round < k ? h.round : k;
-    if (r1 > r0) {
-        const size_t cnt = r1 - r0;
-        std::vector<uint32_t> sd(cnt);
-        std::vector<uint64_t> gn(cnt), ev(cnt);
-        IM_CUDA(c, cudaMemcpyAsync(sd.data(), c->d_seed_list + r0, cnt * 4, cudaMemcpyDeviceToHost, c->stream));
-        IM_CUDA(c, cudaMemcpyAsync(gn.data(), c->d_gain_list + r0, cnt * 8, cudaMemcpyDeviceToHost, c->stream));
-        IM_CUDA(c, cudaMemcpyAsync(ev.data(), c->d_round_evals + r0, cnt * 8, cudaMemcpyDeviceToHost, c->stream));
-        IM_CUDA(c, cudaStreamSynchronize(c->stream));
-        c->seeds.insert(c->seeds.end(), sd.begin(), sd.end());
-        c->seed_gains.insert(c->seed_gains.end(), gn.begin(), gn.end());
-        c->round_evals.insert(c->round_evals.end(), ev.begin(), ev.end());
-    }
-    if (h.err) return im_fail(c, IM_EDEVICE, sel_error_text(h.err));
+    if ((rc = copy_new_seeds(c, r0, r1))) return rc;    if (h.err) return im_fail(c, IM_EDEVICE, sel_error_text(h.err));
     if (h.fb_overflow) return im_fail(c, IM_EDEVICE, sel_error_text(SEL_FB_OVERFLOW));
     if (r1 < k) return im_fail(c, IM_EDEVICE, "selection stopped early");
     return IM_OK;
@@ -2114,3 +2277,195 @@ int im_spread_run(im_ctx* c, uint32_t k, uint64_t* out) {
     return IM_OK;
 }
 
+// ---- device-resident request loop: host side -------------------------------------------
+struct im_mailbox {
+    im_ctx* ctx = nullptr;
+    MailboxShared* h = nullptr;   // host view (mapped pinned memory)
+    MailboxShared* d = nullptr;   // device view
+};
+
+namespace {
+
+unsigned* mb_ring(const im_mailbox* mb) { return reinterpret_cast<unsigned*>(mb->h + 1); }
+unsigned* mb_seeds(const im_mailbox* mb) { return mb_ring(mb) + mb->h->ring; }
+unsigned long long* mb_gains(const im_mailbox* mb) {
+    const size_t goff = (((size_t)mb->h->ring + mb->h->kcap) * 4 + 7) & ~(size_t)7;
+    return reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(mb->h + 1) + goff);
+}
+template <typename T> T load_acq(const T* p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
+template <typename T> void store_rel(T* p, T v) { __atomic_store_n(p, v, __ATOMIC_RELEASE); }
+
+}  // namespace
+
+// A context destroyed while a loop serves it asks that loop to stop first.
+void im_serve_stop(im_ctx* c) {
+    if (c->serving && c->serve_mb)
+        store_rel(&static_cast<im_mailbox*>(const_cast<void*>(c->serve_mb))->h->stop, 1u);
+}
+
+extern "C" {
+
+int im_mailbox_create(im_ctx* c, uint32_t ring, uint32_t kcap, im_mailbox** out) {
+    if (!c || !out) return IM_EINVAL;
+    if (ring == 0 || ring > 65536) return im_fail(c, IM_EINVAL, "ring must be in [1, 65536]");
+    if (kcap == 0 || kcap > c->n) return im_fail(c, IM_EINVAL, "kcap must be in [1, n]");
+    im_mailbox* mb = new (std::nothrow) im_mailbox();
+    if (!mb) return im_fail(c, IM_ENOMEM, "mailbox");
+    void* p = nullptr;
+    const size_t bytes = mailbox_bytes(ring, kcap);
+    if (cudaHostAlloc(&p, bytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+        cudaGetLastError();
+        delete mb;
+        return im_fail(c, IM_ENOMEM, "mailbox (mapped host memory)");
+    }
+    memset(p, 0, bytes);
+    mb->ctx = c;
+    mb->h = static_cast<MailboxShared*>(p);
+    mb->h->ring = ring;
+    mb->h->kcap = kcap;
+    void* dp = nullptr;
+    if (cudaHostGetDevicePointer(&dp, p, 0) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeHost(p);
+        delete mb;
+        return im_fail(c, IM_ECUDA, "mailbox device pointer");
+    }
+    mb->d = static_cast<MailboxShared*>(dp);
+    *out = mb;
+    return IM_OK;
+}
+
+int im_mailbox_destroy(im_mailbox* mb) {
+    if (!mb) return IM_EINVAL;
+    im_ctx* c = mb->ctx;
+    if (c->serving && c->serve_mb == mb) return im_fail(c, IM_ESTATE, "a loop still serves this mailbox");
+    if (c->serve_mb == mb) {   // its graph points at this mailbox
+        if (c->serve_exec) cudaGraphExecDestroy(c->serve_exec);
+        if (c->serve_graph) cudaGraphDestroy(c->serve_graph);
+        c->serve_exec = nullptr;
+        c->serve_graph = nullptr;
+        c->serve_mb = nullptr;
+    }
+    cudaFreeHost(mb->h);
+    delete mb;
+    return IM_OK;
+}
+
+int im_mailbox_push(im_mailbox* mb, uint32_t k) {
+    if (!mb) return IM_EINVAL;
+    MailboxShared* h = mb->h;
+    if (k == 0 || k > h->kcap) return im_fail(mb->ctx, IM_EINVAL, "k must be in [1, kcap]");
+    const unsigned head = h->head, tail = load_acq(&h->tail);
+    if (head - tail >= h->ring) return im_fail(mb->ctx, IM_ESTATE, "mailbox ring is full");
+    mb_ring(mb)[head % h->ring] = k;
+    store_rel(&h->head, head + 1);
+    return IM_OK;
+}
+
+int im_mailbox_state(const im_mailbox* mb, uint32_t* running, int32_t* status, uint32_t* answered) {
+    if (!mb) return IM_EINVAL;
+    __atomic_thread_fence(__ATOMIC_SEQ_CST);
+    if (running) *running = load_acq(&mb->h->running);
+    if (status) *status = load_acq(&mb->h->status);
+    if (answered) *answered = load_acq(&mb->h->answered);
+    return IM_OK;
+}
+
+int im_serve_launch(im_mailbox* mb, uint32_t idle_us) {
+    if (!mb) return IM_EINVAL;
+    im_ctx* c = mb->ctx;
+    if (!c->built) return im_fail(c, IM_ESTATE, "im_build_sketches has not run");
+    if (idle_us == 0 || idle_us > 10000000u) return im_fail(c, IM_EINVAL, "idle_us must be in [1, 10^7]");
+    if (c->serving && c->serve_mb != mb) return im_fail(c, IM_ESTATE, "another mailbox's loop serves the context");
+    if (!c->serving) {
+        // a new loop publishes the context's sequence from its start (the sketches may have been
+        // rebuilt since this mailbox was last served)
+        store_rel(&mb->h->answered, 0u);
+        store_rel(&mb->h->status, (int)IM_OK);
+    }
+    if (c->serve_mb != mb || !c->serve_exec) {
+        if (c->serve_exec) cudaGraphExecDestroy(c->serve_exec);
+        if (c->serve_graph) cudaGraphDestroy(c->serve_graph);
+        c->serve_exec = nullptr;
+        c->serve_graph = nullptr;
+        c->serve_mb = nullptr;
+        if (!c->cap_stream) IM_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        const int rc = build_serve_graph(c, mb->d);
+        if (rc) {
+            c->count_only = false;
+            if (c->capturing) {
+                cudaGraph_t g = nullptr;
+                cudaStreamEndCapture(c->cap_stream, &g);
+                c->capturing = false;
+            }
+            c->cur = c->stream;
+            cudaGetLastError();
+            if (c->serve_exec) cudaGraphExecDestroy(c->serve_exec);
+            if (c->serve_graph) cudaGraphDestroy(c->serve_graph);
+            c->serve_exec = nullptr;
+            c->serve_graph = nullptr;
+            return rc;
+        }
+        c->serve_mb = mb;
+    }
+    mb->h->idle_ns = (unsigned long long)idle_us * 1000ull;
+    store_rel(&mb->h->stop, 0u);
+    store_rel(&mb->h->running, 1u);
+    __atomic_thread_fence(__ATOMIC_SEQ_CST);
+    c->serving = true;
+    IM_CUDA(c, cudaGraphLaunch(c->serve_exec, c->stream));
+    return IM_OK;
+}
+
+int im_mailbox_wait(im_mailbox* mb, uint32_t k, uint32_t timeout_us, uint32_t* seeds, uint64_t* gains) {
+    if (!mb) return IM_EINVAL;
+    im_ctx* c = mb->ctx;
+    MailboxShared* h = mb->h;
+    if (k == 0 || k > h->kcap) return im_fail(c, IM_EINVAL, "k must be in [1, kcap]");
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(timeout_us);
+    for (;;) {
+        __atomic_thread_fence(__ATOMIC_SEQ_CST);
+        unsigned answered = load_acq(&h->answered);
+        if (answered < k) {
+            if (load_acq(&h->status) == IM_EDEVICE) return im_fail(c, IM_EDEVICE, "the serving loop's selection stopped");
+            if (!load_acq(&h->running)) {
+                answered = load_acq(&h->answered);   // published before the loop stopped
+                if (answered < k) return im_fail(c, IM_ESTATE, "no loop serves this mailbox (launch one)");
+            }
+        }
+        if (answered >= k) {
+            for (uint32_t i = 0; i < k; ++i) {
+                if (seeds) seeds[i] = mb_seeds(mb)[i];
+                if (gains) gains[i] = mb_gains(mb)[i];
+            }
+            return IM_OK;
+        }
+        if (std::chrono::steady_clock::now() >= deadline) return im_fail(c, IM_ETIMEOUT, "no answer in time");
+        std::this_thread::sleep_for(std::chrono::microseconds(10));
+    }
+}
+
+int im_serve_finish(im_mailbox* mb, int32_t* loop_status) {
+    if (!mb) return IM_EINVAL;
+    im_ctx* c = mb->ctx;
+    store_rel(&mb->h->stop, 1u);
+    __atomic_thread_fence(__ATOMIC_SEQ_CST);
+    IM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (loop_status) *loop_status = load_acq(&mb->h->status);
+    store_rel(&mb->h->stop, 0u);
+    if (!c->serving) return IM_OK;
+    c->serving = false;
+    // the host copy of the sequence catches up with the rounds the loop ran
+    int rc = pull_state(c);
+    if (rc) return rc;
+    const SelState& hs = *c->h_sel;
+    if (c->use_graph) c->launches += hs.launches - c->dev_launches_seen;
+    c->dev_launches_seen = hs.launches;
+    rc = copy_new_seeds(c, (uint32_t)c->seeds.size(), hs.round);
+    if (rc) return rc;
+    if (hs.err) return im_fail(c, IM_EDEVICE, sel_error_text(hs.err));
+    if (hs.fb_overflow) return im_fail(c, IM_EDEVICE, sel_error_text(SEL_FB_OVERFLOW));
+    return IM_OK;
+}
+
+}  // extern "C"

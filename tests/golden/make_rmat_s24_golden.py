@@ -66,7 +66,7 @@ def main() -> int:
     ctr = oracle.centers(n, seed, alpha)
     lab, sz = oracle.compact(L, ctr)
     compact = {"centers": len(ctr), "centers_sha256": sha(ctr.astype(np.uint32)),
-               "label_sha256": sha(lab), "size_sha256": sha(sz)}
+               "compact_label_sha256": sha(lab), "compact_size_sha256": sha(sz)}
     del lab, sz
     gc.collect()
     log("compact")
@@ -81,7 +81,7 @@ def main() -> int:
         "seeds": [int(x) for x in seeds], "seed_gains": [int(x) for x in gains],
         "celf_evals": [int(x) for x in evals], "spread": int(spread),
         "gains0_sha256": sha(g0.astype(np.uint64)), "gains0_sum": int(g0.sum()),
-        "gains0_max": int(g0.max()), "label_sha256": label_sha, **compact,
+        "gains0_max": int(g0.max()), "sketch_label_sha256": label_sha, **compact,
     }
     assert spread == int(gains.sum()), "telescoping spread"
     OUT.write_text(json.dumps(out, indent=1) + "\n")

@@ -106,8 +106,9 @@ def test_rmat_scale24_full_parity_with_stored_oracle_values():
     assert int(gains.sum()) == gold["gains0_sum"] and int(gains.max()) == gold["gains0_max"]
     assert _sha(gains.astype(np.uint64)) == gold["gains0_sha256"]
     assert len(ctr) == gold["centers"] and _sha(ctr.astype(np.uint32)) == gold["centers_sha256"]
-    assert _sha(lab) == gold["label_sha256"] and _sha(sz) == gold["size_sha256"]
-    bad = [r for r in range(R) if label_sha[r] != gold["label_sha256"][r]]
+    assert _sha(lab) == gold["compact_label_sha256"] and _sha(sz) == gold["compact_size_sha256"]
+    assert len(gold["sketch_label_sha256"]) == R
+    bad = [r for r in range(R) if label_sha[r] != gold["sketch_label_sha256"][r]]
     assert not bad, f"labels differ in sketches {bad[:10]}"
     # the oracle, run here on two sketches
     G = oracle.Graph(n, u, v)
