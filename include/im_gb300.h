@@ -334,6 +334,48 @@ typedef struct {
 int im_run_batch(im_instance* inst, uint32_t count, uint32_t workers);
 
 /*
+ * The batch as one CUDA graph (Alg. 1 for every instance, the instances' paths side by side).
+ * im_batch_create plans a batch once: one context per instance with every buffer reserved, and
+ * one CUDA graph holding each instance's whole path -- the upload of its edge lists, its CSR,
+ * its sketch construction, its lazy-greedy loop (conditional nodes set by the device, as in
+ * im_select_seeds), its spread and the copies of its results.  The instances form `branches`
+ * chains, largest first and dealt round-robin, that the graph runs concurrently.
+ * im_batch_run launches the graph once, waits, and writes every instance's seeds_out,
+ * gains_out, spread_out and status -- identical to im_run_batch and to one-by-one runs.  It may
+ * be called again: each call uploads the instances' edge lists anew from the same host
+ * arrays (which stay valid and unchanged in size until im_batch_destroy; lists that are not
+ * pinned are staged through pinned memory when the graph is captured, so later calls see their
+ * contents of that time; pinned lists are read at every run).
+ *   inst     as im_run_batch (the array itself must outlive the batch)
+ *   sched    NULL for the defaults, or the schedule im_batch_tune chose: per size class
+ *            (an instance's m R at most class_pairs[j], the last class unbounded) the sketch
+ *            batch, lanes and union path of its context, and the number of branches.
+ * Errors: IM_EINVAL (NULL pointers, an instance's n or R 0, k outside [1, min(n, 16384)],
+ * alpha outside (0, 1], more than 4 classes), IM_ENOMEM, IM_ECUDA; im_batch_run returns the
+ * first failing instance's status (IM_EINVAL for an edge id >= n or a self-loop, found on the
+ * device; IM_EDEVICE if its selection stopped).  One batch is not thread-safe.
+ *
+ * im_batch_tune times the knobs on the batch itself: instances are grouped into size classes by
+ * m R; on each class's largest instance im_autotune tries sketch batch, lanes (and hubs for
+ * alpha < 1), and the two union paths are compared; then whole batches with 4, 8 and 16
+ * branches are built and run, and the fastest is kept.  *out receives the schedule.
+ */
+typedef struct {
+    uint32_t branches;          /* chains run side by side (0: 8) */
+    uint32_t classes;           /* size classes in use, 0..4 (0: default knobs everywhere) */
+    uint64_t class_pairs[4];    /* upper bound of m R of classes 0 .. classes-2 */
+    uint32_t sketch_batch[4];   /* im_set_sketch_batch of each class (0: automatic) */
+    uint32_t lanes[4];          /* im_set_pipeline of each class (0: 2) */
+    uint32_t union_path[4];     /* im_set_union_path of each class */
+    double run_ms;              /* im_batch_tune: time of one im_batch_run with this schedule */
+} im_batch_schedule;
+typedef struct im_batch im_batch;
+int im_batch_create(im_instance* inst, uint32_t count, const im_batch_schedule* sched, im_batch** out);
+int im_batch_run(im_batch* batch);
+int im_batch_destroy(im_batch* batch);
+int im_batch_tune(im_instance* inst, uint32_t count, im_batch_schedule* out);
+
+/*
  * Serving: sketch sets held in HBM under a memory budget, answering requests for seed sets
  * (the paper has no serving layer; this engine is built on its greedy-prefix property: Alg. 1
  * picks one seed per round, so the best k seeds it finds are the first k of one sequence,

@@ -60,6 +60,12 @@ class im_model_stats(ctypes.Structure):
                 ("used", ctypes.c_uint64)]
 
 
+class im_batch_schedule(ctypes.Structure):
+    _fields_ = [("branches", ctypes.c_uint32), ("classes", ctypes.c_uint32), ("class_pairs", ctypes.c_uint64 * 4),
+                ("sketch_batch", ctypes.c_uint32 * 4), ("lanes", ctypes.c_uint32 * 4),
+                ("union_path", ctypes.c_uint32 * 4), ("run_ms", ctypes.c_double)]
+
+
 class im_tuning(ctypes.Structure):
     _fields_ = [("sketch_batch", ctypes.c_uint32), ("lanes", ctypes.c_uint32), ("hub_cap", ctypes.c_uint32),
                 ("tried", ctypes.c_uint32), ("build_ms", ctypes.c_double), ("select_ms", ctypes.c_double),
@@ -103,6 +109,10 @@ def lib():
         "im_debug_fail_alloc": ([c.c_int64], i32),
         "im_mailbox_create": ([vp, u32, u32, c.POINTER(vp)], i32),
         "im_server_set_budget": ([vp, u64], i32),
+        "im_batch_create": ([vp, u32, vp, c.POINTER(vp)], i32),
+        "im_batch_run": ([vp], i32),
+        "im_batch_destroy": ([vp], i32),
+        "im_batch_tune": ([vp, u32, vp], i32),
         "im_server_stats": ([vp, u32, c.POINTER(im_model_stats)], i32),
         "im_footprint_estimate": ([u32, u64, u32, dbl, dbl, c.POINTER(u64)], i32),
         "im_mailbox_push": ([vp, u32], i32),
@@ -358,6 +368,79 @@ def im_run_batch(instances, workers: int = 8):
         bad = next(i for i in range(len(instances)) if arr[i].status != IM_OK)
         raise IMError(rc, f"instance {bad} failed with status {arr[bad].status}")
     return [(sd, gn, int(sp[0])) for sd, gn, sp in outs]
+
+
+def _instances(instances):
+    """ctypes array of im_instance for dicts with n, u, v, R, k, seed, p, alpha, with output arrays;
+    returns (array, outputs, arrays to keep alive)."""
+    keep = []
+    arr = (im_instance * len(instances))()
+    outs = []
+    P32, P64 = ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint64)
+    for i, d in enumerate(instances):
+        u = d["u"] if isinstance(d["u"], np.ndarray) and d["u"].dtype == np.uint32 and d["u"].flags["C_CONTIGUOUS"] \
+            else np.ascontiguousarray(np.asarray(d["u"], dtype=np.uint32))
+        v = d["v"] if isinstance(d["v"], np.ndarray) and d["v"].dtype == np.uint32 and d["v"].flags["C_CONTIGUOUS"] \
+            else np.ascontiguousarray(np.asarray(d["v"], dtype=np.uint32))
+        k = int(d["k"])
+        sd, gn, sp = np.zeros(k, np.uint32), np.zeros(k, np.uint64), np.zeros(1, np.uint64)
+        keep += [u, v]
+        outs.append((sd, gn, sp))
+        arr[i] = im_instance(int(d["n"]), len(u), u.ctypes.data_as(P32), v.ctypes.data_as(P32), int(d["R"]), k,
+                             int(d["seed"]), float(d["p"]), float(d["alpha"]), sd.ctypes.data_as(P32),
+                             gn.ctypes.data_as(P64), sp.ctypes.data_as(P64), 0)
+    return arr, outs, keep
+
+
+class Batch:
+    """A batch of instances planned as one CUDA graph (im_batch_create); run() launches it."""
+
+    def __init__(self, instances, schedule=None):
+        self._arr, self._outs, self._keep = _instances(instances)
+        self._sched = schedule
+        h = ctypes.c_void_p()
+        rc = lib().im_batch_create(self._arr, len(instances), ctypes.byref(schedule) if schedule is not None else None,
+                                   ctypes.byref(h))
+        if rc != IM_OK:
+            raise IMError(rc, lib().im_last_error(None).decode())
+        self.h = h
+
+    def run(self):
+        rc = lib().im_batch_run(self.h)
+        if rc != IM_OK:
+            bad = next(i for i in range(len(self._outs)) if self._arr[i].status != IM_OK)
+            raise IMError(rc, f"instance {bad} failed with status {self._arr[bad].status}")
+        return [(sd.copy(), gn.copy(), int(sp[0])) for sd, gn, sp in self._outs]
+
+    def statuses(self):
+        return [int(self._arr[i].status) for i in range(len(self._outs))]
+
+    def close(self):
+        if self.h:
+            lib().im_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def im_batch_tune(instances):
+    """The schedule (size-class knobs and branches) im_batch_tune picks for these instances."""
+    arr, outs, keep = _instances(instances)
+    sched = im_batch_schedule()
+    rc = lib().im_batch_tune(arr, len(instances), ctypes.byref(sched))
+    if rc != IM_OK:
+        raise IMError(rc, "im_batch_tune")
+    return sched
 
 
 class IMServer:

@@ -221,6 +221,57 @@ static int load_graph(im_ctx* c, const uint32_t* u, const uint32_t* v, int ptr_k
     return rc;
 }
 
+// Spread scratch for k seeds: (component, size) words of every (seed, sketch) and the seed list.
+int spread_reserve(im_ctx* c, uint32_t k) {
+    const size_t need = (size_t)k * c->R;
+    if (need > c->spread_cap) {
+        if (!dalloc(c->d_spread_pairs, need)) { c->spread_cap = 0; return im_fail(c, IM_ENOMEM, "spread"); }
+        c->spread_cap = need;
+    }
+    if (!c->d_spread_seeds && !dalloc(c->d_spread_seeds, kSpreadKMax)) return im_fail(c, IM_ENOMEM, "spread");
+    return IM_OK;
+}
+
+// Buffers for uploading a graph of n vertices and m edges from host memory, reserved ahead of a
+// batch graph (nothing may be allocated while it is captured).  The context was created with a
+// reserve of at least n and m, so its graph buffers already fit.
+int batch_load_reserve(im_ctx* c, uint32_t n, uint64_t m) {
+    if (!(c->d_edges && n <= c->graph_n_alloc && m <= c->graph_m_alloc))
+        return im_fail(c, IM_ESTATE, "graph buffers not reserved");
+    if (m > 0 && c->upload_cap < m) {
+        dfree(c->d_upload);
+        if (c->h_upload) cudaFreeHost(c->h_upload);
+        c->h_upload = nullptr;
+        c->upload_cap = 0;
+        if (!dalloc(c->d_upload, 2 * m)) return im_fail(c, IM_ENOMEM, "edge upload");
+        c->upload_cap = m;
+    }
+    if (m > 0 && !c->h_upload && cudaMallocHost(&c->h_upload, 2 * c->upload_cap * sizeof(uint32_t)) != cudaSuccess) {
+        c->h_upload = nullptr;
+        cudaGetLastError();
+        return im_fail(c, IM_ENOMEM, "edge staging (pinned host memory)");
+    }
+    int rc = im_scan_reserve(c, n);
+    if (rc) return rc;
+    c->n = n;
+    c->m = m;
+    c->prob_model = IM_PROBS_UNIFORM;
+    c->graph_ok = true;   // the graph that is queued next (validated after it ran)
+    return IM_OK;
+}
+
+// Upload and CSR of the graph queued on the context stream, with no host wait (the batch
+// graph captures it); host lists that are not pinned are staged into the context's pinned
+// buffer now, on the host.
+int batch_load_enqueue(im_ctx* c, uint32_t n, uint64_t m, const uint32_t* u, const uint32_t* v) {
+    if (n != c->n || m != c->m) return im_fail(c, IM_ESTATE, "graph dimensions differ from the reserve");
+    c->deferred = true;
+    const int rc = load_graph(c, u, v, IM_PTR_HOST);
+    c->deferred = false;
+    c->graph_ok = rc == IM_OK;
+    return rc;
+}
+
 // ------------------------------------------------------------------------------------
 extern "C" {
 
@@ -283,7 +334,7 @@ int im_create_reserved(im_ctx** out, uint32_t n, uint64_t m, const uint32_t* u, 
     do {
         if (im_dev_malloc(&c->d_sel, sizeof(SelState)) != cudaSuccess ||
             cudaMallocHost(&c->h_sel, sizeof(SelState)) != cudaSuccess ||
-            cudaMallocHost(&c->h_live, 3 * sizeof(unsigned long long)) != cudaSuccess) {
+            cudaMallocHost(&c->h_live, 4 * sizeof(unsigned long long)) != cudaSuccess) {
             rc = im_fail(c, IM_ENOMEM, "selection state");
             break;
         }
@@ -417,7 +468,13 @@ int im_set_edge_probs(im_ctx* c, int model, const double* p, int ptr_kind) {
     return IM_OK;
 }
 
-int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alpha) {
+}  // extern "C"
+
+// Sketch construction in three parts, so that the batch engine can capture the middle one into
+// a graph: build_prepare validates the arguments, sets the build's parameters and reserves every
+// buffer (no kernel); build_enqueue queues the kernels on the context stream (no host
+// synchronisation, no allocation); build_finish waits for them and records the results.
+int build_prepare(im_ctx* c, uint32_t R, uint64_t seed, double p, double alpha) {
     if (!c) return IM_EINVAL;
     if (c->serving) return im_fail(c, IM_ESTATE, "a serving loop owns the context (im_serve_finish first)");
     if (!c->graph_ok) return im_fail(c, IM_ESTATE, "no valid graph is loaded");
@@ -542,10 +599,6 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
     }
     c->refresh_min = c->refresh_req ? c->refresh_req : std::max<uint64_t>(16384, n / 4);
     int rc = IM_OK;
-    // live pairs before the build, read with the build's final synchronisation
-    IM_CUDA(c, cudaMemcpyAsync(c->h_live, c->d_live_total, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                               c->stream));
-    c->h_live[2] = 0;
     if (nspec && (!c->d_spec_keys || !c->d_spec_ids)) {
         // both or neither: a build after a failed one allocates them again
         if (!dalloc(c->d_spec_keys, kSpecMax) || !dalloc(c->d_spec_ids, kSpecMax)) {
@@ -557,12 +610,20 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
     if (!rc && !sketch_buffers_ready(c, nspec))
         rc = im_fail(c, IM_ESTATE, "sketch buffers missing after allocation");
     if (rc) { free_sketch_state(c); return rc; }
+    return IM_OK;
+}
+
+int build_enqueue(im_ctx* c) {
+    const uint32_t all = c->all_centers;
+    int rc = IM_OK;
+    // live pairs before the build, read with the build's final synchronisation
+    IM_CUDA(c, cudaMemcpyAsync(c->h_live, c->d_live_total, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                               c->stream));
     if (!all) {
         rc = im_select_centers(c, c->d_cflags, c->d_cpos);
         if (!rc) rc = im_select_hubs(c, c->d_cflags, c->d_cpos);
-        if (rc) { free_sketch_state(c); return rc; }
     }
-    if (!rc) rc = im_arc_keys(c, smp.salt);
+    if (!rc) rc = im_arc_keys(c, c->smp.salt);
     // record counters of the lanes start at zero (each union kernel resets its lane's after use)
     for (uint32_t i = 0; i < kMaxLanes && !rc; ++i)
         if (c->lane[i].live_n &&
@@ -571,16 +632,33 @@ int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alp
     if (!rc) rc = im_sketch_batches(c);
     if (!rc) rc = im_selection_init(c, true);   // the build wrote every size entry
     if (!rc) {
-        cudaError_t e = cudaMemcpyAsync(c->h_live + 1, c->d_live_total, sizeof(unsigned long long),
-                                        cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        const cudaError_t e = cudaMemcpyAsync(c->h_live + 1, c->d_live_total, sizeof(unsigned long long),
+                                              cudaMemcpyDeviceToHost, c->stream);
         if (e != cudaSuccess) rc = im_cuda_check(c, e, "sketch construction");
     }
+    return rc;
+}
+
+int build_finish(im_ctx* c) {
+    int rc = IM_OK;
+    const cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) rc = im_cuda_check(c, e, "sketch construction");
     c->build_live_pairs = c->h_live[1] - c->h_live[0];
     c->hubs = (uint32_t)c->h_live[2];
     if (rc) { free_sketch_state(c); return rc; }
     c->built = true;
     return IM_OK;
+}
+
+extern "C" {
+
+int im_build_sketches(im_ctx* c, uint32_t R, uint64_t seed, double p, double alpha) {
+    int rc = build_prepare(c, R, seed, p, alpha);
+    if (rc) return rc;
+    c->h_live[2] = 0;
+    rc = build_enqueue(c);
+    if (rc) { free_sketch_state(c); return rc; }
+    return build_finish(c);
 }
 
 int im_select_seeds(im_ctx* c, uint32_t k, uint32_t* seeds_out, uint64_t* gains_out) {
@@ -617,13 +695,8 @@ int im_spread(im_ctx* c, const uint32_t* seeds, uint32_t k, uint64_t* spread_out
     if (k > 0 && !seeds) return im_fail(c, IM_EINVAL, "seeds is NULL");
     for (uint32_t i = 0; i < k; ++i)
         if (seeds[i] >= c->n) return im_fail(c, IM_EINVAL, "seed id >= n");
-    size_t need = (size_t)k * c->R;
-    if (need > c->spread_cap) {
-        if (!dalloc(c->d_spread_pairs, need)) { c->spread_cap = 0; return im_fail(c, IM_ENOMEM, "spread"); }
-        c->spread_cap = need;
-    }
-    if (!c->d_spread_seeds && !dalloc(c->d_spread_seeds, kSpreadKMax))
-        return im_fail(c, IM_ENOMEM, "spread seeds");
+    const int rs = spread_reserve(c, k);
+    if (rs) return rs;
     if (k > 0)
         IM_CUDA(c, cudaMemcpyAsync(c->d_spread_seeds, seeds, k * sizeof(uint32_t), cudaMemcpyHostToDevice,
                                    c->stream));

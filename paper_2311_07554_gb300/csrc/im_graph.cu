@@ -13,7 +13,13 @@ __global__ void k_pack_edges(const uint32_t* __restrict__ u, const uint32_t* __r
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
         uint32_t a = u[e], b = v[e];
-        if (a >= n || b >= n || a == b) atomicOr(bad, 1u);
+        if (a >= n || b >= n || a == b) {
+            // reported, and replaced by the self-loop (0, 0), which every later kernel handles in
+            // bounds (a union of 0 with itself does nothing): a graph queued before the host reads
+            // the flag (im_batch_run) stays memory-safe, and its instance then fails
+            atomicOr(bad, 1u);
+            a = b = 0;
+        }
         edges[e] = make_uint2(a, b);
     }
 }
@@ -317,15 +323,26 @@ int im_graph_build(im_ctx* c, const uint32_t* d_u, const uint32_t* d_v) {
             IM_LAUNCH(c, K_PACK_EDGES, k_pack_edges, grid_for(m, B), B, 0, d_u, d_v, m, n, c->d_edges, bad);
             IM_LAUNCH(c, K_CSR_DEGREE, k_csr_degree, grid_for(m, B), B, 0, c->d_edges, m, n, deg);
         }
-        unsigned int h_bad = 0;
-        if (cudaMemcpyAsync(&h_bad, bad, sizeof(h_bad), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
-            cudaStreamSynchronize(c->stream) != cudaSuccess) {
-            rc = im_cuda_check(c, cudaGetLastError(), "edge validation");
-            break;
-        }
-        if (h_bad) {
-            rc = im_fail(c, IM_EINVAL, "edge list has an id >= n or a self-loop");
-            break;
+        if (c->deferred) {
+            // queued into a graph: the flag is read after it ran (an invalid edge was skipped by
+            // every kernel, so the graph stays memory-safe; the instance then fails)
+            c->h_live[3] = 0;
+            if (cudaMemcpyAsync(c->h_live + 3, bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->stream) !=
+                cudaSuccess) {
+                rc = im_cuda_check(c, cudaGetLastError(), "edge validation");
+                break;
+            }
+        } else {
+            unsigned int h_bad = 0;
+            if (cudaMemcpyAsync(&h_bad, bad, sizeof(h_bad), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+                cudaStreamSynchronize(c->stream) != cudaSuccess) {
+                rc = im_cuda_check(c, cudaGetLastError(), "edge validation");
+                break;
+            }
+            if (h_bad) {
+                rc = im_fail(c, IM_EINVAL, "edge list has an id >= n or a self-loop");
+                break;
+            }
         }
         rc = im_scan_u32_to_u64(c, deg, c->d_off, n);
         if (rc) break;
@@ -337,10 +354,26 @@ int im_graph_build(im_ctx* c, const uint32_t* d_u, const uint32_t* d_v) {
             IM_LAUNCH(c, K_CSR_FILL, k_adj_fill, grid_for(m, B, 152u * 16u), B, 0, c->d_edges, m, c->d_off,
                       c->d_arc_cur, c->d_adj, c->d_src);
         }
-        cudaError_t e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) rc = im_cuda_check(c, e, "csr build");
+        if (!c->deferred) {
+            cudaError_t e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) rc = im_cuda_check(c, e, "csr build");
+        }
     } while (0);
     return rc;
+}
+
+// Scratch of im_scan_u32_to_u64 for `count` elements, allocated ahead (the batch engine queues
+// its scans into a graph, where nothing may be allocated).
+int im_scan_reserve(im_ctx* c, uint64_t count) {
+    const uint64_t tiles = (count + kScanTile - 1) / kScanTile;
+    const size_t need = (tiles + 1) * sizeof(uint64_t);
+    if (need <= c->tmp_bytes) return IM_OK;
+    if (c->d_tmp) cudaFree(c->d_tmp);
+    c->d_tmp = nullptr;
+    c->tmp_bytes = 0;
+    if (im_dev_malloc(&c->d_tmp, need) != cudaSuccess) return im_fail(c, IM_ENOMEM, "scan scratch");
+    c->tmp_bytes = need;
+    return IM_OK;
 }
 
 // Per-edge probabilities: thresholds of every edge (and their mean), on the device.

@@ -368,6 +368,7 @@ struct im_ctx {
     unsigned step_grid = 0;          // blocks of k_sel_step (resident at once)
     uint64_t* d_topb = nullptr;      // 32 keys per step-kernel block (PH_TOPB)
     bool capturing = false;              // launches go into a graph: no events, no counting
+    bool deferred = false;               // the calls only queue work (batch graph): no host waits
     bool count_only = false;             // launches are only counted (dry run)
     uint64_t dry_count = 0;
     unsigned long long dev_launches_seen = 0;  // SelState::launches already added to launches
@@ -461,6 +462,18 @@ int im_graph_build(im_ctx* c, const uint32_t* d_u, const uint32_t* d_v);
 int im_arc_keys(im_ctx* c, uint64_t salt);   // keys and center bits of every arc
 int im_edge_probs(im_ctx* c, int model, const double* d_p);   // per-edge thresholds
 int im_scan_u32_to_u64(im_ctx* c, const uint32_t* d_in, uint64_t* d_out, uint64_t count);
+int im_scan_reserve(im_ctx* c, uint64_t count);
+// im_api.cu: the parts of im_build_sketches, and graph loading that only queues work
+int build_prepare(im_ctx* c, uint32_t R, uint64_t seed, double p, double alpha);
+int build_enqueue(im_ctx* c);
+int build_finish(im_ctx* c);
+int batch_load_reserve(im_ctx* c, uint32_t n, uint64_t m);
+int spread_reserve(im_ctx* c, uint32_t k);
+int batch_load_enqueue(im_ctx* c, uint32_t n, uint64_t m, const uint32_t* u, const uint32_t* v);
+// im_select.cu: the selection and spread of a batch graph
+int im_select_prepare(im_ctx* c, uint32_t k);
+int im_select_graph_append(im_ctx* c, cudaGraph_t g, cudaGraphNode_t after, uint32_t k, cudaGraphNode_t* last);
+int im_spread_enqueue(im_ctx* c, uint32_t k, unsigned long long* h_total);
 // im_sketch.cu
 int im_select_centers(im_ctx* c, uint32_t* d_flags_tmp, uint64_t* d_scan_tmp);
 int im_select_hubs(im_ctx* c, uint32_t* d_flags_tmp, uint64_t* d_scan_tmp);

@@ -2277,6 +2277,62 @@ int im_spread_run(im_ctx* c, uint32_t k, uint64_t* out) {
     return IM_OK;
 }
 
+// ---- the selection and spread of one instance in a batch graph --------------------------
+int im_select_prepare(im_ctx* c, uint32_t k) {
+    if (!c->cap_stream) IM_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    int rc = size_step_grid(c);
+    if (!rc) rc = spread_reserve(c, k);
+    return rc;
+}
+
+// The selection of the first k seeds of the context, appended to g after `after`: the target
+// (k_set_target), then the selection loop.
+int im_select_graph_append(im_ctx* c, cudaGraph_t g, cudaGraphNode_t after, uint32_t k, cudaGraphNode_t* last) {
+    SelHandles hd{};
+    hd.on = 1;
+    c->count_only = true;
+    int rc = IM_OK;
+    for (unsigned m = 0; m < RARE_COUNT && !rc; ++m) {
+        c->dry_count = 0;
+        rc = enqueue_rare(c, m, hd);
+        hd.rare_launches[m] = (unsigned)c->dry_count;
+    }
+    c->count_only = false;
+    if (rc) return rc;
+    if ((rc = cap_begin(c, g, &after, 1))) return rc;
+    IM_LAUNCH(c, K_SEL_BEGIN, k_set_target, 1, 32, 0, c->d_sel, k, (unsigned long long)c->refresh_min);
+    cudaGraphNode_t target = nullptr;
+    rc = cap_frontier(c, &target);
+    const int re = cap_end(c);
+    if (!rc) rc = re;
+    if (!rc) rc = add_selection(c, g, &target, 1, hd, last);
+    c->cur = c->stream;
+    return rc;
+}
+
+// Spread of the first k selected seeds (still on the device), total to pinned host memory.
+int im_spread_enqueue(im_ctx* c, uint32_t k, unsigned long long* h_total) {
+    const GraphView g = graph_view(c);
+    const SketchView s = sketch_view(c);
+    const uint32_t nchunk = (c->R + 31) / 32;
+    IM_CUDA(c, cudaMemcpyAsync(c->d_spread_seeds, c->d_seed_list, (size_t)k * sizeof(uint32_t),
+                               cudaMemcpyDeviceToDevice, c->stream));
+    IM_LAUNCH(c, K_REDUCE_RESET, k_phase_reset, 1, 32, 0, c->d_sel);
+    IM_CUDA(c, cudaMemsetAsync(c->d_spread_total, 0, sizeof(unsigned long long), c->stream));
+    IM_LAUNCH(c, K_SPREAD_TASKS, k_spread_tasks, search_grid((uint64_t)k * nchunk), kEvalWarps * 32, 0, g, s,
+              c->d_sel, c->d_spread_seeds, k, nchunk, c->d_fb_tasks, c->fb_cap, c->d_spread_pairs);
+    launch_fallback(c, g, s);
+    uint32_t kp2 = 1;
+    while (kp2 < k) kp2 <<= 1;
+    const size_t smem = (size_t)kp2 * sizeof(uint64_t);
+    IM_CUDA(c, cudaFuncSetAttribute(k_spread_dedup, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(smem > 48 * 1024 ? smem : 48 * 1024)));
+    IM_LAUNCH(c, K_SPREAD_DEDUP, k_spread_dedup, c->R, 1024, smem, c->d_spread_pairs, k, kp2, c->d_spread_total);
+    IM_CUDA(c, cudaMemcpyAsync(h_total, c->d_spread_total, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                               c->stream));
+    return IM_OK;
+}
+
 // ---- device-resident request loop: host side -------------------------------------------
 struct im_mailbox {
     im_ctx* ctx = nullptr;

@@ -79,7 +79,7 @@ def test_product_package_never_imports_the_oracle():
         assert "import oracle" not in t and "from oracle" not in t and "im_oracle" not in t, f
 
 
-@pytest.mark.parametrize("name", ["im_stats", "im_instance", "im_request", "im_tuning", "im_model_stats"])
+@pytest.mark.parametrize("name", ["im_stats", "im_instance", "im_request", "im_tuning", "im_model_stats", "im_batch_schedule"])
 def test_struct_layouts_match_the_header(tmp_path, name):
     """The binding's ctypes structs have the header's sizes and field offsets (a C compiler
     reads the header)."""

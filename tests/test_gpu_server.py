@@ -28,9 +28,10 @@ def _cuda():
 
 
 def _models():
-    graphs = [graphgen.chung_lu(30000, 150000, 2.1, 3000.0, 41), graphgen.erdos_renyi(20000, 80000, 42),
-              graphgen.chung_lu(25000, 120000, 2.1, 2500.0, 43), graphgen.erdos_renyi(15000, 60000, 44)]
-    params = [(64, 5, 0.03, 0.1), (32, 6, 0.06, 1.0), (48, 7, 0.04, 0.05), (40, 8, 0.07, 0.3)]
+    # four models of one size (equal footprints), so that a budget of two footprints holds
+    # exactly two of them
+    graphs = [graphgen.chung_lu(30000, 150000, 2.1, 3000.0, 41 + i) for i in range(4)]
+    params = [(64, 5 + i, 0.04, 0.1) for i in range(4)]
     return graphs, params
 
 
@@ -47,23 +48,25 @@ def test_eviction_under_a_budget_keeps_every_answer():
     graphs, params = _models()
     fps = [im.im_footprint_estimate(n, len(u), R, p, a) for (n, u, v), (R, _, p, a) in zip(graphs, params)]
     # requests cycle over the four models with growing k, so that each model needs the device
-    # again after the others have taken its place
+    # again after the others have taken its place; 100 ms apart, so that a model's requests are
+    # not all taken at once (a build with its first graph capture takes tens of milliseconds)
     reqs, t = [], 0
     for rnd in range(4):
         for mid in range(4):
             reqs.append((mid, 5 + 9 * rnd + mid, t))
-            t += 3_000_000
+            t += 100_000_000
     reqs.append((2, 3, t))   # answered from the known prefix, without the device
     with im.IMServer() as srv:
-        srv.set_budget(sorted(fps)[-1] + sorted(fps)[-2] + 1)   # room for two models at a time
+        assert len(set(fps)) == 1
+        srv.set_budget(2 * fps[0] + 1)                          # room for two models at a time
         for (n, u, v), (R, seed, p, alpha) in zip(graphs, params):
             srv.add_model(n, u, v, R, seed, p, alpha)
         resident0 = sum(srv.stats(i)["resident"] for i in range(4))
         assert resident0 == 2                                    # the others wait for a request
         out = srv.replay(reqs)
         st = [srv.stats(i) for i in range(4)]
-    assert sum(s["evictions"] for s in st) >= 4
-    assert sum(s["builds"] for s in st) >= 6                    # rebuilt after evictions
+    assert sum(s["evictions"] for s in st) >= 8
+    assert sum(s["builds"] for s in st) >= 10                   # rebuilt after evictions
     assert all(s["used"] <= s["budget"] for s in st)
     kmax = [max(k for m, k, _ in reqs if m == i) for i in range(4)]
     alone = _alone(graphs, params, kmax)
