@@ -323,12 +323,7 @@ int im_create_reserved(im_ctx** out, uint32_t n, uint64_t m, const uint32_t* u, 
     for (uint32_t i = 1; i < kMaxLanes && made; ++i)
         made = cudaStreamCreateWithFlags(&c->lane_stream[i], cudaStreamNonBlocking) == cudaSuccess &&
                cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming) == cudaSuccess;
-    int prio_least = 0, prio_greatest = 0;
-    if (made) made = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) == cudaSuccess;
-    for (uint32_t i = 0; i < kMaxLanes && made; ++i)
-        made = cudaStreamCreateWithPriority(&c->post_stream[i], cudaStreamNonBlocking, prio_greatest) == cudaSuccess &&
-               cudaEventCreateWithFlags(&c->ev_emitted[i], cudaEventDisableTiming) == cudaSuccess &&
-               cudaEventCreateWithFlags(&c->ev_posted[i], cudaEventDisableTiming) == cudaSuccess;
+
     if (!made) {
         g_create_error = "stream or event creation failed";
         im_destroy(c);
@@ -903,11 +898,6 @@ void im_destroy(im_ctx* c) {
     for (uint32_t i = 1; i < kMaxLanes; ++i) {
         if (c->lane_stream[i]) { cudaStreamSynchronize(c->lane_stream[i]); cudaStreamDestroy(c->lane_stream[i]); }
         if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
-    }
-    for (uint32_t i = 0; i < kMaxLanes; ++i) {
-        if (c->post_stream[i]) { cudaStreamSynchronize(c->post_stream[i]); cudaStreamDestroy(c->post_stream[i]); }
-        if (c->ev_emitted[i]) cudaEventDestroy(c->ev_emitted[i]);
-        if (c->ev_posted[i]) cudaEventDestroy(c->ev_posted[i]);
     }
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);

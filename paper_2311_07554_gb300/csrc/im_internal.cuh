@@ -398,14 +398,6 @@ struct im_ctx {
     cudaStream_t lane_stream[imk::kMaxLanes] = {};    // lanes 1.. (owned); lane 0 is the context stream
     cudaEvent_t ev_fork = nullptr, ev_spec = nullptr;
     cudaEvent_t ev_join[imk::kMaxLanes] = {};
-    // Each lane's union-find, compression and gain kernels run on a stream of the device's
-    // highest priority (post_stream), its sampling kernel on the lane stream: when blocks of the
-    // other lane's sampling kernel retire, the block scheduler hands their slots to the waiting
-    // latency-bound kernels first, so the two kinds of work share the SMs instead of taking turns.
-    cudaStream_t post_stream[imk::kMaxLanes] = {};
-    cudaEvent_t ev_emitted[imk::kMaxLanes] = {};   // a lane's sampling kernel is done
-    cudaEvent_t ev_posted[imk::kMaxLanes] = {};    // a lane's batch is done (its buffers are free)
-    cudaStream_t post_next = nullptr;              // set: the union and what follows go here
     cudaStream_t cur = nullptr;                  // stream the next launch goes to
     uint32_t lanes = 2;                          // sketch batches alternate between two streams
     int union_path = IM_UNION_RECORDS;           // im_set_union_path

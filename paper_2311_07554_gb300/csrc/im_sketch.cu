@@ -827,8 +827,6 @@ __global__ void k_hub_index(uint32_t n, uint32_t rho, const uint32_t* __restrict
 
 // Blocks of the sampling kernel per SM (grid-stride over the edge pairs).
 constexpr unsigned kEmitBlocksPerSM = 16;
-// The union-find, compression and gain kernels of a build on high-priority streams (im_ctx::post_stream).
-constexpr bool kPostStreams = true;
 
 // Sampling and unions of one batch as two kernels (records of live pairs in between).
 int launch_sample_split(im_ctx* c, im_ctx::Lane& L, uint32_t r0, uint32_t nb, int key_mode) {
@@ -842,12 +840,6 @@ int launch_sample_split(im_ctx* c, im_ctx::Lane& L, uint32_t r0, uint32_t nb, in
     do {                                                                                          \
         IM_LAUNCH(c, K_SAMPLE_EMIT, k_sample_emit<BB>, gs, T, 0, ep, c->m, c->smp, r0, nb, L.live,   \
                   L.live_n, c->live_cap, L.parent, L.word, c->n, c->d_cidx, key_mode);             \
-        if (c->post_next) {                                                                       \
-            const int li_ = (int)(&L - c->lane);                                                  \
-            IM_CUDA(c, cudaEventRecord(c->ev_emitted[li_], c->cur));                              \
-            IM_CUDA(c, cudaStreamWaitEvent(c->post_next, c->ev_emitted[li_], 0));                 \
-            c->cur = c->post_next;                                                                \
-        }                                                                                         \
         IM_LAUNCH(c, K_UNION, k_union_live<BB>, gu, T, 0, L.live, L.live_n, c->live_cap, L.parent, \
                   c->n, ep, c->m, c->smp, r0, nb, c->d_live_total);                               \
     } while (0)
@@ -1015,15 +1007,7 @@ int im_sketch_batches(im_ctx* c) {
         const uint32_t li = i % lanes;
         im_ctx::Lane& L = c->lane[li];
         c->cur = L.stream;
-        const bool post = kPostStreams && lanes > 1 && c->live_cap && !c->count_only;
-        if (post) {
-            // the lane's buffers are free once its previous batch's post work is done
-            if (i >= lanes) IM_CUDA(c, cudaStreamWaitEvent(L.stream, c->ev_posted[li], 0));
-            else IM_CUDA(c, cudaStreamWaitEvent(c->post_stream[li], c->ev_fork, 0));
-            c->post_next = c->post_stream[li];
-        }
         rc = batch_components(c, L, r0, nb, c->all_centers ? 0 : 1);
-        c->post_next = nullptr;
         if (rc) { lanes_join(c, lanes); return rc; }
         uint64_t* gain = li ? L.gain : c->d_gain0;
         const int first = i < lanes ? 1 : 0;
@@ -1061,11 +1045,7 @@ int im_sketch_batches(im_ctx* c) {
             IM_LAUNCH(c, K_GAIN_COMPACT, k_spec_overlap, grid_for(n, T, 152u * 16u), T, 0, L.parent, L.word, n, nb,
                       c->d_spec_ids, c->spec_count, c->lane[0].spec_ov);
         }
-        if (post) IM_CUDA(c, cudaEventRecord(c->ev_posted[li], c->cur));
     }
-    if (kPostStreams && lanes > 1 && c->live_cap && !c->count_only)   // the lane streams continue after their post work
-        for (uint32_t li = 0; li < lanes && li < i; ++li)
-            IM_CUDA(c, cudaStreamWaitEvent(c->lane[li].stream, c->ev_posted[li], 0));
     rc = lanes_join(c, lanes);
     if (rc) return rc;
     for (uint32_t li = 1; li < lanes && li < i; ++li) {   // the lanes that ran a batch
