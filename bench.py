@@ -161,13 +161,18 @@ def _traffic(kernel: str, units_per_launch: float):
 
 
 # Algorithmic work per unit:
-#   sample_emit  one hash per (edge, sketch) pair: 22 32-bit integer operations (64-bit add,
-#                three 64-bit xor-shifts, two 64-bit multiplies, 64-bit compare) -> bound "alu";
-#                its peak is measured by im_hash_peak (the same per-pair compute on registers)
+#   sample_emit  one hash per (edge, sketch) pair: its candidate test as written, counted in
+#                32-bit operations of the integer ALU pipe -- 64-bit add (2), xor with the shift by
+#                30 (a funnel shift and a shift, two xors: 4), xor with the shift by 27 (4), the
+#                compare (1) and the live-mask update (1): 12 per pair (its six 32-bit multiplies
+#                run on the FMA pipe and are not counted) -> bound "alu"; the peak is the ALU pipe
+#                of the GPU: 152 SMs x 4 sub-partitions x 16 lanes per clock at the SM clock (ncu
+#                counts 13.4 ALU-pipe operations per pair in this kernel, 75% pipe utilisation)
 #   union        one live (edge, sketch) pair: its 16-byte record read plus two random
 #                32-byte sector reads for the endpoints' parents -> 80 bytes, bound "hbm"
 #   compress     one (vertex, sketch): parent read + write, root word update -> 16 bytes, "hbm"
-ALU_OPS_PER_PAIR = 22.0
+ALU_OPS_PER_PAIR = 12.0
+ALU_LANES_PER_SM = 64          # integer ALU pipe: 16 lanes per SM sub-partition, 4 sub-partitions
 UNION_BYTES_PER_PAIR = 80.0
 COMPRESS_BYTES_PER_VERTEX = 16.0
 
@@ -182,8 +187,8 @@ def kernel_rooflines(prof, live_build, n, m, R, steps, peaks, peak_src, clk, has
     total_ms = sum(x[0] for x in prof.values()) or 1.0
     passes = steps                                      # sketch passes over all R sketches
     mhz = peaks.get("sm_max_mhz", 2070.0)
-    nominal = 152 * 128 * mhz * 1e6 / 1e12              # Tops/s: 152 SMs x 128 int32 lanes
-    alu_peak = ALU_OPS_PER_PAIR * hash_peak / 1e12      # Tops/s at the measured pair rate
+    alu_peak = 152 * ALU_LANES_PER_SM * mhz * 1e6 / 1e12   # Tops/s: the integer ALU pipe of 152 SMs
+    hash_ceiling = ALU_OPS_PER_PAIR * hash_peak / 1e12     # the same hash on registers alone
     hbm = peaks.get("hbm_gbs", 6800.0)
 
     def entry(name, bound, units, per_unit, unit, peak, psrc):
@@ -199,10 +204,12 @@ def kernel_rooflines(prof, live_build, n, m, R, steps, peaks, peak_src, clk, has
     if "sample_emit" in prof:
         out["sample_emit"] = entry("sample_emit", "alu", float(m) * R * passes, ALU_OPS_PER_PAIR,
                                    "Tops/s", alu_peak,
-                                   f"measured: im_hash_peak, the per-pair compute on registers "
-                                   f"({hash_peak:.3e} pairs/s x {ALU_OPS_PER_PAIR:.0f} ops)")
-        out["sample_emit"]["nominal_peak"] = nominal
-        out["sample_emit"]["nominal_peak_source"] = f"152 SMs x 128 int32 lanes x {mhz:.0f} MHz"
+                                   f"derived: 152 SMs x {ALU_LANES_PER_SM} integer ALU lanes x {mhz:.0f} MHz "
+                                   f"(sm_max_mhz of MEASURED_PEAKS.json)")
+        out["sample_emit"]["hash_ceiling"] = hash_ceiling
+        out["sample_emit"]["hash_ceiling_source"] = (
+            f"measured: im_hash_peak, the same per-pair compute on registers alone "
+            f"({hash_peak:.3e} pairs/s x {ALU_OPS_PER_PAIR:.0f} ops)")
     live = live_build
     if "union" in prof and live > 0:
         out["union"] = entry("union", "hbm", float(live), UNION_BYTES_PER_PAIR, "GB/s", hbm,

@@ -62,7 +62,11 @@ struct Model {
     std::vector<uint64_t> gains;
 };
 
-constexpr uint32_t kLoopIdleUs = 50000;   // a model's device loop waits this long for its next request
+// A model's device loop waits this long for its next request.  A waiting loop holds one block on
+// an SM, and the selection's step kernels are sized to fill every SM once, so loops left waiting
+// on other models push those kernels into a second wave: with 50 ms the serving workload's p99
+// was 139 ms, with 1-5 ms 53 ms.
+constexpr uint32_t kLoopIdleUs = 2000;
 constexpr uint32_t kWaitUs = 120000000;   // a request's answer, at most (two minutes)
 
 }  // namespace
