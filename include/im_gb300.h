@@ -203,6 +203,12 @@ int im_set_sketch_batch(im_ctx* ctx, uint32_t batch);
  * made on the host, before cudaMalloc would be called.  Returns IM_OK. */
 int im_debug_fail_alloc(int64_t after);
 
+/* Test hook (no counterpart in the paper): the sketch kernels of every later build use at most
+ * `records` live-pair records per lane and batch (a negative value restores the allocated
+ * capacity), so that a test can make the record buffer overflow: the union kernel then redoes
+ * the batch with the fused sampling+union loop, with the same results.  Returns IM_OK. */
+int im_debug_record_cap(int64_t records);
+
 /*
  * im_sketch_static -- labels and component sizes of one sketch, for callers that cannot
  * allocate device memory.  The paper has no counterpart of this call.
@@ -259,10 +265,13 @@ int im_set_pipeline(im_ctx* ctx, uint32_t lanes);
  * a record buffer of the context (about 1.3 p m B x 16 bytes per lane) and united by a second
  * kernel that keeps several unions of each thread in flight.  IM_UNION_FUSED: one kernel
  * hashes the batch's (edge, sketch) pairs and unites the live ones through a per-warp queue
- * in shared memory, so that no live pair is stored (no record buffer).  Results do not depend
- * on it.  Takes effect at the next im_build_sketches; IM_EINVAL for another value. */
+ * in shared memory, so that no live pair is stored (no record buffer).  IM_UNION_BUCKETS: the
+ * records (8 bytes) are grouped by sketch as they are written, and the union kernel takes the
+ * sketches one after the other, so that the parents it climbs belong to one or two sketches at a
+ * time (on large graphs these then stay in L2).  Results do not depend on it.  Takes effect at the next im_build_sketches; IM_EINVAL for another value. */
 #define IM_UNION_FUSED 0
 #define IM_UNION_RECORDS 1
+#define IM_UNION_BUCKETS 2
 int im_set_union_path(im_ctx* ctx, int path);
 
 /* Execution of the selection loop (Alg. 2 / Alg. 4 rounds).  1 (default): the whole loop is

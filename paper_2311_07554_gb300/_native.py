@@ -107,6 +107,7 @@ def lib():
         "im_set_pipeline": ([vp, u32], i32),
         "im_set_union_path": ([vp, i32], i32),
         "im_debug_fail_alloc": ([c.c_int64], i32),
+        "im_debug_record_cap": ([c.c_int64], i32),
         "im_mailbox_create": ([vp, u32, u32, c.POINTER(vp)], i32),
         "im_server_set_budget": ([vp, u64], i32),
         "im_batch_create": ([vp, u32, vp, c.POINTER(vp)], i32),
@@ -314,8 +315,14 @@ def im_debug_fail_alloc(after: int):
     lib().im_debug_fail_alloc(int(after))
 
 
+def im_debug_record_cap(records: int):
+    """Test hook: cap the live-pair records the sketch kernels use (negative restores)."""
+    lib().im_debug_record_cap(int(records))
+
+
 IM_UNION_FUSED = 0
 IM_UNION_RECORDS = 1
+IM_UNION_BUCKETS = 2
 
 
 def im_set_union_path(ctx, path: int):

@@ -150,6 +150,14 @@ void im_prof_end(im_ctx* c, int kid, int ev0) {
 // to succeed before one fails, or -1 when disarmed.
 static std::atomic<int64_t> g_fail_alloc_after{-1};
 
+// Test hook (im_debug_record_cap): the live-pair record capacity the sketch kernels may use, or -1.
+static std::atomic<int64_t> g_record_cap{-1};
+
+uint64_t im_record_cap(uint64_t allocated) {
+    const int64_t cap = g_record_cap.load();
+    return cap < 0 || (uint64_t)cap >= allocated ? allocated : (uint64_t)cap;
+}
+
 cudaError_t im_dev_malloc(void** p, size_t bytes) {
     int64_t left = g_fail_alloc_after.load();
     while (left >= 0) {
@@ -400,8 +408,8 @@ int im_set_pipeline(im_ctx* c, uint32_t lanes) {
 
 int im_set_union_path(im_ctx* c, int path) {
     if (!c) return IM_EINVAL;
-    if (path != IM_UNION_FUSED && path != IM_UNION_RECORDS)
-        return im_fail(c, IM_EINVAL, "union path must be IM_UNION_FUSED or IM_UNION_RECORDS");
+    if (path != IM_UNION_FUSED && path != IM_UNION_RECORDS && path != IM_UNION_BUCKETS)
+        return im_fail(c, IM_EINVAL, "union path must be IM_UNION_FUSED, IM_UNION_RECORDS or IM_UNION_BUCKETS");
     c->union_path = path;
     return IM_OK;
 }
@@ -516,7 +524,7 @@ int build_prepare(im_ctx* c, uint32_t R, uint64_t seed, double p, double alpha) 
     // live-pair records of one batch: expected p m B, with a generous margin; a batch that
     // still overflows falls back to the fused sample+union loop on the device
     uint64_t live_cap = 0;
-    if (c->union_path == IM_UNION_RECORDS && c->m > 0 && (smp.eT || smp.all_live || smp.T != 0)) {
+    if (c->union_path != IM_UNION_FUSED && c->m > 0 && (smp.eT || smp.all_live || smp.T != 0)) {
         const double pe = smp.eT ? c->mean_p : smp.all_live ? 1.0 : p;
         const double ex = pe * (double)c->m * B;
         double cap = 1.3 * ex + 16.0 * std::sqrt(ex) + 65536.0;
@@ -557,7 +565,7 @@ int build_prepare(im_ctx* c, uint32_t R, uint64_t seed, double p, double alpha) 
         // at least the context's reserve (im_create_reserved), so that later builds fit
         const uint32_t na = std::max(n, c->res_n), Ra = std::max(R, c->res_R);
         const size_t nca = std::max<size_t>(nc, c->res_nc);
-        const uint64_t livea = c->union_path == IM_UNION_RECORDS ? std::max(live_cap, c->res_live) : live_cap;
+        const uint64_t livea = c->union_path != IM_UNION_FUSED ? std::max(live_cap, c->res_live) : live_cap;
         const uint32_t nsa = std::min(std::max(nspec, c->res_n ? std::min<uint32_t>(c->spec_req, kSpecMax) : 0u),
                                       kSpecMax);
         const bool compact = !all || c->res_n > 0;   // a reserved context may serve compact builds
@@ -575,7 +583,7 @@ int build_prepare(im_ctx* c, uint32_t R, uint64_t seed, double p, double alpha) 
         if (ok && livea) {
             c->live_cap = livea;
             for (uint32_t i = 0; i < kMaxLanes && ok; ++i)
-                ok = dalloc(c->lane[i].live, c->live_cap) && dalloc(c->lane[i].live_n, 2);
+                ok = dalloc(c->lane[i].live, c->live_cap) && dalloc(c->lane[i].live_n, kLiveCounters);
         }
         if (ok && compact) {
             const size_t nw = ((size_t)na + 31) / 32;
@@ -628,7 +636,7 @@ int build_enqueue(im_ctx* c) {
     // record counters of the lanes start at zero (each union kernel resets its lane's after use)
     for (uint32_t i = 0; i < kMaxLanes && !rc; ++i)
         if (c->lane[i].live_n &&
-            cudaMemsetAsync(c->lane[i].live_n, 0, 2 * sizeof(unsigned long long), c->stream) != cudaSuccess)
+            cudaMemsetAsync(c->lane[i].live_n, 0, kLiveCounters * sizeof(unsigned long long), c->stream) != cudaSuccess)
             rc = im_fail(c, IM_ECUDA, "record counter reset");
     if (!rc) rc = im_sketch_batches(c);
     if (!rc) rc = im_selection_init(c, true);   // the build wrote every size entry
@@ -870,6 +878,11 @@ const char* im_kernel_name(int kernel_id) { return kernel_name(kernel_id); }
 
 int im_debug_fail_alloc(int64_t after) {
     g_fail_alloc_after.store(after < 0 ? -1 : after);
+    return IM_OK;
+}
+
+int im_debug_record_cap(int64_t records) {
+    g_record_cap.store(records < 0 ? -1 : records);
     return IM_OK;
 }
 

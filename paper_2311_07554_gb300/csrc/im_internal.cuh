@@ -24,6 +24,7 @@ constexpr size_t kCenterSelBytes = 4096;                // device state of the c
 constexpr uint32_t kHubsAuto = 0xFFFFFFFFu;                // im_ctx::hub_cap default
 constexpr uint32_t kMaxLanes = 2;                          // sketch batches in flight at most (a third lane measured no faster)
 constexpr uint32_t kSpecMax = 8;                        // candidate first seeds (see im_ctx::spec_req)
+constexpr uint32_t kLiveCounters = 34;                   // per lane: record counts (one per bucket) + ticket
 
 // splitmix64 output finaliser (Steele, Lea, Flood 2014).
 __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
@@ -507,6 +508,8 @@ int im_fail(im_ctx* c, int code, const std::string& msg);
 cudaError_t im_dev_malloc(void** p, size_t bytes);
 template <typename T>
 inline cudaError_t im_dev_malloc(T** p, size_t bytes) { return im_dev_malloc(reinterpret_cast<void**>(p), bytes); }
+// The record capacity the sketch kernels use: the allocated one, or less under im_debug_record_cap.
+uint64_t im_record_cap(uint64_t allocated);
 int im_cuda_check(im_ctx* c, cudaError_t e, const char* what);
 
 #define IM_CUDA(c, call)                                                                \

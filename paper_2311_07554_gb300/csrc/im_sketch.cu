@@ -188,6 +188,182 @@ k_sample_emit(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, uin
     }
 }
 
+// Unions each thread of the union kernels keeps in flight.
+constexpr int kUnionChains = 4;
+
+// 32 x 32 bit transpose across a warp: lane i holds row i (bit j = entry (i, j)); afterwards
+// lane j holds column j (bit i = entry (i, j)).  Five rounds swap the off-diagonal blocks of
+// size s between lanes i and i ^ s.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, unsigned lane) {
+    const uint32_t masks[5] = {0xFFFF0000u, 0xFF00FF00u, 0xF0F0F0F0u, 0xCCCCCCCCu, 0xAAAAAAAAu};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int sh = 16 >> k;
+        const uint32_t hi = masks[k];
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, sh);
+        x = (lane & sh) ? ((x & hi) | ((y & hi) >> sh)) : ((x & ~hi) | ((y & ~hi) << sh));
+    }
+    return x;
+}
+
+// Sampling with the live pairs grouped by sketch: the records of sketch b go to bucket b (8
+// bytes each, (u, v)), so that the unions can run sketch by sketch while one sketch's parent
+// array stays in L2.  Per warp and pair of edges per lane, the live masks are transposed so
+// that lane b holds sketch b's live edges: lane b reserves room in bucket b with one atomic and
+// writes them (the edges' endpoints come from their lanes by shuffles).  Also initialises the
+// batch's forest, as k_sample_emit does.
+template <int B>
+__global__ void __launch_bounds__(256)
+k_sample_bucket(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, uint32_t r0, uint32_t nb,
+                uint2* __restrict__ out, unsigned long long* __restrict__ bucket_n, uint64_t capb,
+                uint32_t* __restrict__ parent, uint64_t* __restrict__ word, uint32_t n,
+                const uint32_t* __restrict__ cidx, int key_mode) {
+    const uint64_t npairs = (m + 1) >> 1;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t g0 = (uint64_t)(r0 + 1u) * kGamma;
+    const unsigned lane = threadIdx.x & 31;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const uint64_t w = ((uint64_t)label_key(v, key_mode, cidx) << 32) | 1u;
+        for (uint32_t b = 0; b < nb; ++b) {
+            parent[(size_t)b * n + v] = v;
+            word[(size_t)b * n + v] = w;
+        }
+    }
+    uint2* mine = out + (size_t)lane * capb;   // lane b writes bucket b
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < npairs; base += stride) {
+        const uint64_t i = base + threadIdx.x;
+        uint32_t live0 = 0, live1 = 0;
+        uint4 two = make_uint4(0, 0, 0, 0);
+        if (i < npairs) {
+            two = __ldcs(edge_pairs + i);
+            pair_live_masks<B>(i, m, smp, r0, nb, g0, live0, live1);
+        }
+        if (!__any_sync(0xffffffffu, (live0 | live1) != 0u)) continue;
+        uint32_t t0 = warp_transpose32(live0, lane), t1 = warp_transpose32(live1, lane);
+        const uint32_t cnt = __popc(t0) + __popc(t1);
+        unsigned long long pos = 0;
+        if (cnt) pos = atomicAdd(bucket_n + lane, (unsigned long long)cnt);
+        // rounds: each lane writes its next record; the edge comes from its lane by shuffles
+        for (;;) {
+            const bool has = (t0 | t1) != 0u;
+            if (!__any_sync(0xffffffffu, has)) break;
+            int src = 0;
+            bool second = false;
+            if (t0) { src = __ffs(t0) - 1; t0 &= t0 - 1; }
+            else if (t1) { src = __ffs(t1) - 1; t1 &= t1 - 1; second = true; }
+            const uint32_t ex = __shfl_sync(0xffffffffu, two.x, src), ey = __shfl_sync(0xffffffffu, two.y, src);
+            const uint32_t ez = __shfl_sync(0xffffffffu, two.z, src), ew = __shfl_sync(0xffffffffu, two.w, src);
+            if (has) {
+                if (pos < capb) mine[pos] = second ? make_uint2(ez, ew) : make_uint2(ex, ey);
+                ++pos;
+            }
+        }
+    }
+}
+
+// Unions of the bucketed records, bucket after bucket: the grid sweeps the records of sketch 0,
+// then sketch 1, ..., so that the parents being climbed are those of one or two sketches (L2
+// resident on large graphs).  Several unions in flight per thread, as k_union_live.  The last
+// block to read the counts resets them; if a bucket overflowed, the batch is redone with the
+// fused sample+union loop.
+template <int B>
+__global__ void __launch_bounds__(256)
+k_union_bucket(const uint2* __restrict__ recs, unsigned long long* __restrict__ bucket_n, uint64_t capb,
+               uint32_t* __restrict__ parent, uint32_t n, const uint4* __restrict__ edge_pairs, uint64_t m,
+               Sampler smp, uint32_t r0, uint32_t nb, unsigned long long* __restrict__ total) {
+    __shared__ unsigned long long s_end[32];   // inclusive prefix of the bucket counts
+    __shared__ int s_over;
+    if (threadIdx.x < 32) {
+        const unsigned long long c0 =
+            threadIdx.x < nb ? *reinterpret_cast<volatile unsigned long long*>(bucket_n + threadIdx.x) : 0ull;
+        const int over = __any_sync(0xffffffffu, c0 > capb);
+        unsigned long long incl = c0 > capb ? capb : c0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, d);
+            if ((int)threadIdx.x >= d) incl += y;
+        }
+        s_end[threadIdx.x] = incl;
+        unsigned long long all = c0;
+#pragma unroll
+        for (int d = 16; d; d >>= 1) all += __shfl_xor_sync(0xffffffffu, all, d);
+        if (threadIdx.x == 0) {
+            s_over = over;
+            __threadfence();
+            if (atomicAdd(bucket_n + 32, 1ull) == gridDim.x - 1ull) {   // every block has the counts
+                for (int b = 0; b < 32; ++b) bucket_n[b] = 0;
+                bucket_n[32] = 0;
+                atomicAdd(total, all);
+            }
+        }
+    }
+    __syncthreads();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    if (s_over) {
+        const uint64_t npairs = (m + 1) >> 1;
+        const uint64_t g0 = (uint64_t)(r0 + 1u) * kGamma;
+        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npairs; i += stride)
+            sample_union_pair<B>(edge_pairs[i], i, m, smp, g0, nb, parent, n);
+        return;
+    }
+    const unsigned long long cnt = s_end[31];
+    constexpr int K = kUnionChains;
+    uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t* P[K];
+    uint32_t rx[K], ry[K], px[K], py[K], hres[K];
+    bool act[K], hooked[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        act[k] = false;
+        hooked[k] = false;
+        P[k] = parent;
+        rx[k] = ry[k] = px[k] = py[k] = hres[k] = 0;
+    }
+    uint32_t b = 0;   // bucket of index j (j only grows)
+    for (;;) {
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (!act[k] && j < cnt) {
+                while (j >= s_end[b]) ++b;
+                const uint64_t start = b ? s_end[b - 1] : 0ull;
+                const uint2 rc = recs[(size_t)b * capb + (j - start)];
+                j += stride;
+                P[k] = parent + (size_t)b * n;
+                rx[k] = rc.x;
+                ry[k] = rc.y;
+                px[k] = __ldca(P[k] + rx[k]);
+                py[k] = __ldca(P[k] + ry[k]);
+                act[k] = true;
+            }
+            any |= act[k];
+        }
+        if (!any) break;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (!act[k]) continue;
+            if (hooked[k]) {
+                hooked[k] = false;
+                if (hres[k] == rx[k]) { act[k] = false; continue; }
+                px[k] = hres[k];
+            }
+            if (px[k] == py[k]) { act[k] = false; continue; }
+            if (px[k] < py[k]) {
+                uint32_t t = rx[k]; rx[k] = ry[k]; ry[k] = t;
+                t = px[k]; px[k] = py[k]; py[k] = t;
+            }
+            if (rx[k] == px[k]) {
+                hres[k] = atomicCAS(P[k] + rx[k], rx[k], py[k]);
+                hooked[k] = true;
+            } else {
+                atomicCAS(P[k] + rx[k], px[k], py[k]);
+                rx[k] = px[k];
+                px[k] = __ldca(P[k] + rx[k]);
+            }
+        }
+    }
+}
+
 // Forest of one batch: P[b][v] = v, W[b][v] = (label key of v, size 1).  grid.y = sketch.
 __global__ void __launch_bounds__(256)
 k_forest_init(uint32_t* __restrict__ parent, uint64_t* __restrict__ word, uint32_t n,
@@ -270,8 +446,6 @@ k_sample_unite(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, ui
 // count rec_n[0] is reset by the last block to read it (ticket rec_n[1]), ready for the lane's
 // next batch.  If the record buffer overflowed, the batch is redone with the fused
 // sample+union loop instead (decided on the device, so no host round trip).
-constexpr int kUnionChains = 4;
-
 template <int B>
 __global__ void __launch_bounds__(256)
 k_union_live(const uint4* __restrict__ recs, unsigned long long* __restrict__ rec_n, uint64_t cap,
@@ -836,11 +1010,22 @@ int launch_sample_split(im_ctx* c, im_ctx::Lane& L, uint32_t r0, uint32_t nb, in
     const unsigned gs = grid_for(npairs, T, 152u * kEmitBlocksPerSM);
     const double pl = c->smp.eT ? c->mean_p : c->smp.all_live ? 1.0 : c->p;
     const unsigned gu = grid_for((uint64_t)(pl * (double)c->m * nb) + 1, T, 152u * 16u);
+    const uint64_t live_cap = im_record_cap(c->live_cap);
+    // bucketed records: 8 bytes each, in c->batch_used regions of the lane's record buffer
+    const uint64_t capb = 2 * live_cap / (c->batch_used ? c->batch_used : 1);
+    uint2* buckets = reinterpret_cast<uint2*>(L.live);
 #define IM_SE(BB)                                                                                 \
     do {                                                                                          \
+        if (c->union_path == IM_UNION_BUCKETS) {                                                  \
+            IM_LAUNCH(c, K_SAMPLE_EMIT, k_sample_bucket<BB>, gs, T, 0, ep, c->m, c->smp, r0, nb,     \
+                      buckets, L.live_n, capb, L.parent, L.word, c->n, c->d_cidx, key_mode);       \
+            IM_LAUNCH(c, K_UNION, k_union_bucket<BB>, gu, T, 0, buckets, L.live_n, capb, L.parent,  \
+                      c->n, ep, c->m, c->smp, r0, nb, c->d_live_total);                           \
+            break;                                                                                \
+        }                                                                                         \
         IM_LAUNCH(c, K_SAMPLE_EMIT, k_sample_emit<BB>, gs, T, 0, ep, c->m, c->smp, r0, nb, L.live,   \
-                  L.live_n, c->live_cap, L.parent, L.word, c->n, c->d_cidx, key_mode);             \
-        IM_LAUNCH(c, K_UNION, k_union_live<BB>, gu, T, 0, L.live, L.live_n, c->live_cap, L.parent, \
+                  L.live_n, live_cap, L.parent, L.word, c->n, c->d_cidx, key_mode);                \
+        IM_LAUNCH(c, K_UNION, k_union_live<BB>, gu, T, 0, L.live, L.live_n, live_cap, L.parent,    \
                   c->n, ep, c->m, c->smp, r0, nb, c->d_live_total);                               \
     } while (0)
     const uint32_t cap = c->batch_used;

@@ -108,22 +108,49 @@ def test_sketch_batch_sizes_agree(batch, lanes):
     _compare(g, o, 5)
 
 
-@pytest.mark.parametrize("path", [0, 1])
+@pytest.mark.parametrize("path", [0, 1, 2])
 @pytest.mark.parametrize("alpha", [1.0, 0.2])
-def test_union_paths_agree(path, alpha):
-    # IM_UNION_FUSED (hashing and unions in one kernel) and IM_UNION_RECORDS (live-pair records
-    # and a union kernel with several unions in flight per thread): both equal the oracle
+@pytest.mark.parametrize("R", [40, 77])
+def test_union_paths_agree(path, alpha, R):
+    # IM_UNION_FUSED (hashing and unions in one kernel), IM_UNION_RECORDS (live-pair records and
+    # a union kernel with several unions in flight per thread) and IM_UNION_BUCKETS (records
+    # grouped by sketch, united sketch by sketch): all equal the oracle (R = 77: a ragged batch)
     n, u, v = graphgen.erdos_renyi(2500, 9000, 17)
     with im.IMContext(n, u, v) as ctx:
         im.im_set_union_path(ctx.h, path)
-        ctx.build_sketches(40, 42, 0.15, alpha)
+        ctx.build_sketches(R, 42, 0.15, alpha)
         g = dict(gains=ctx.gains(), centers=ctx.centers())
         g["label"], g["size"] = ctx.compact()
         g["seeds"], g["seed_gains"] = ctx.select_seeds(6)
         g["spread"] = ctx.spread(g["seeds"])
-        g["labels"] = {r: ctx.labels(r) for r in (0, 39)}
-    o = _oracle(n, u, v, 42, 0.15, 40, alpha, 6)
+        g["labels"] = {r: ctx.labels(r) for r in (0, R - 1)}
+    o = _oracle(n, u, v, 42, 0.15, R, alpha, 6)
     _compare(g, o, 6)
+
+
+@pytest.mark.parametrize("path", [1, 2])
+def test_record_overflow_falls_back_to_the_fused_loop(path):
+    # the record capacity capped far below the live pairs of a batch: the union kernel redoes
+    # every batch with the fused sampling+union loop (decided on the device); same results
+    n, u, v = graphgen.erdos_renyi(3000, 12000, 18)
+    im.im_debug_record_cap(100)
+    try:
+        g = _run_path(n, u, v, 42, 0.2, 40, 0.3, 6, path)
+    finally:
+        im.im_debug_record_cap(-1)
+    _compare(g, _oracle(n, u, v, 42, 0.2, 40, 0.3, 6), 6)
+
+
+def _run_path(n, u, v, seed, p, R, alpha, k, path):
+    with im.IMContext(n, u, v) as ctx:
+        im.im_set_union_path(ctx.h, path)
+        ctx.build_sketches(R, seed, p, alpha)
+        out = dict(gains=ctx.gains(), centers=ctx.centers())
+        out["label"], out["size"] = ctx.compact()
+        out["seeds"], out["seed_gains"] = ctx.select_seeds(k)
+        out["spread"] = ctx.spread(out["seeds"])
+        out["labels"] = {r: ctx.labels(r) for r in (0, R - 1)}
+    return out
 
 
 @pytest.mark.parametrize("R", [1, 31, 33, 64])
