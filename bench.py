@@ -438,6 +438,7 @@ def measure_workload(args, n, u, v, prm, steps, warmup, dist, ws, local, full=Tr
         "value": job_rate(pairs, ws, ms_step / 1e3), "ms_per_step": ms_step, "steps": steps, "warmup": warmup,
         "config": {"workload": prm["name"], "n": n, "m": m, "p": prm["p"], "probs": prm["probs"], "R": R,
                    "alpha": prm["alpha"], "k": k, "l2": "flushed before every step (256 MB write)",
+                   "union_path": ("fused", "records", "buckets")[int(st["union_path"])],
                    "parallelism": f"replicas{ws}"},
         "time_to_k_ms": ms_build + ms_select,
         "sketch_ms": ms_build, "select_ms": ms_select,
@@ -716,8 +717,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="time the workload only (no secondary workload, batched or serving legs)")
     ap.add_argument("--sketch-batch", type=int, default=0, help="sketches per edge pass (0 = auto)")
-    ap.add_argument("--union-path", type=int, default=None, choices=[0, 1],
-                    help="0: hashing and unions in one kernel (default), 1: live-pair records and a union kernel")
+    ap.add_argument("--union-path", type=int, default=None, choices=[0, 1, 2, 3],
+                    help="0: hashing and unions in one kernel, 1: live-pair records and a union kernel, "
+                         "2: records grouped by sketch, 3: 2 on large graphs, else 1 (default)")
     ap.add_argument("--lanes", type=int, default=0, help="sketch batches in flight (0 = the default, 2)")
     ap.add_argument("--probs", default="uniform", choices=["uniform", "u01", "u13", "wic"],
                     help="IC probabilities: the workload's p, or per edge U(0,0.1), U(0.1,0.3), 2/(d_u+d_v)")

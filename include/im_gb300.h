@@ -174,6 +174,7 @@ typedef struct {
     uint64_t spec_batches;          /* batches evaluated from a candidate first seed's
                                        overlaps (see im_set_seed_speculation)             */
     uint64_t hubs;                  /* hubs of the last build (see im_set_hubs)            */
+    uint32_t union_path;            /* union path of the last build (IM_UNION_AUTO resolved) */
 } im_stats;
 
 int im_get_stats(im_ctx* ctx, im_stats* out);
@@ -261,17 +262,21 @@ int im_set_refresh_threshold(im_ctx* ctx, uint64_t min_batch);
 int im_set_pipeline(im_ctx* ctx, uint32_t lanes);
 
 /* Tuning: how a sketch batch's unions meet its sampling (Sec. 3: the live edges of Sample(e, r)
- * are united per sketch; Alg. 3).  IM_UNION_RECORDS (default): the live pairs are written to
- * a record buffer of the context (about 1.3 p m B x 16 bytes per lane) and united by a second
- * kernel that keeps several unions of each thread in flight.  IM_UNION_FUSED: one kernel
- * hashes the batch's (edge, sketch) pairs and unites the live ones through a per-warp queue
- * in shared memory, so that no live pair is stored (no record buffer).  IM_UNION_BUCKETS: the
- * records (8 bytes) are grouped by sketch as they are written, and the union kernel takes the
- * sketches one after the other, so that the parents it climbs belong to one or two sketches at a
- * time (on large graphs these then stay in L2).  Results do not depend on it.  Takes effect at the next im_build_sketches; IM_EINVAL for another value. */
+ * are united per sketch; Alg. 3).  IM_UNION_RECORDS: the live pairs are written to a record
+ * buffer of the context (about 1.3 p m B x 16 bytes per lane) and united by a second kernel
+ * that keeps several unions of each thread in flight.  IM_UNION_FUSED: one kernel hashes the
+ * batch's (edge, sketch) pairs and unites the live ones through a per-warp queue in shared
+ * memory, so that no live pair is stored (no record buffer).  IM_UNION_BUCKETS: the records
+ * (8 bytes, in the same buffer) are grouped by sketch and by sampling block as they are written,
+ * and the union kernel takes the sketches one after the other, so that the parents it climbs
+ * belong to one or two sketches at a time (on large graphs these then stay in L2).
+ * IM_UNION_AUTO (default): IM_UNION_BUCKETS when a batch's parent arrays (4 n B bytes) exceed
+ * 256 MiB, else IM_UNION_RECORDS.  Results do not depend on it.  Takes effect at the next
+ * im_build_sketches; IM_EINVAL for another value. */
 #define IM_UNION_FUSED 0
 #define IM_UNION_RECORDS 1
 #define IM_UNION_BUCKETS 2
+#define IM_UNION_AUTO 3
 int im_set_union_path(im_ctx* ctx, int path);
 
 /* Execution of the selection loop (Alg. 2 / Alg. 4 rounds).  1 (default): the whole loop is
@@ -366,7 +371,7 @@ int im_run_batch(im_instance* inst, uint32_t count, uint32_t workers);
  *
  * im_batch_tune times the knobs on the batch itself: instances are grouped into size classes by
  * m R; on each class's largest instance im_autotune tries sketch batch, lanes (and hubs for
- * alpha < 1), and the two union paths are compared; then whole batches with 4, 8 and 16
+ * alpha < 1), and the three union paths (im_set_union_path) are compared; then whole batches with 4, 8 and 16
  * branches are built and run, and the fastest is kept.  *out receives the schedule.
  */
 typedef struct {

@@ -35,7 +35,7 @@ class im_stats(ctypes.Structure):
                 ("hop2_searches", ctypes.c_uint64), ("hop2_chunks", ctypes.c_uint64),
                 ("refresh_batches", ctypes.c_uint64), ("live_pairs", ctypes.c_uint64),
                 ("build_live_pairs", ctypes.c_uint64), ("spec_batches", ctypes.c_uint64),
-                ("hubs", ctypes.c_uint64)]
+                ("hubs", ctypes.c_uint64), ("union_path", ctypes.c_uint32)]
 
 
 class im_instance(ctypes.Structure):
@@ -323,11 +323,13 @@ def im_debug_record_cap(records: int):
 IM_UNION_FUSED = 0
 IM_UNION_RECORDS = 1
 IM_UNION_BUCKETS = 2
+IM_UNION_AUTO = 3
 
 
 def im_set_union_path(ctx, path: int):
     """IM_UNION_FUSED: hashing and unions in one kernel; IM_UNION_RECORDS: live-pair records
-    united by a second kernel."""
+    united by a second kernel; IM_UNION_BUCKETS: records grouped by sketch, united sketch after
+    sketch; IM_UNION_AUTO (default): buckets when a batch's parent arrays exceed 256 MiB."""
     _check(ctx, lib().im_set_union_path(ctx, path))
 
 

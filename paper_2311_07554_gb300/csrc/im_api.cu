@@ -408,8 +408,9 @@ int im_set_pipeline(im_ctx* c, uint32_t lanes) {
 
 int im_set_union_path(im_ctx* c, int path) {
     if (!c) return IM_EINVAL;
-    if (path != IM_UNION_FUSED && path != IM_UNION_RECORDS && path != IM_UNION_BUCKETS)
-        return im_fail(c, IM_EINVAL, "union path must be IM_UNION_FUSED, IM_UNION_RECORDS or IM_UNION_BUCKETS");
+    if (path != IM_UNION_FUSED && path != IM_UNION_RECORDS && path != IM_UNION_BUCKETS && path != IM_UNION_AUTO)
+        return im_fail(c, IM_EINVAL,
+                       "union path must be IM_UNION_FUSED, IM_UNION_RECORDS, IM_UNION_BUCKETS or IM_UNION_AUTO");
     c->union_path = path;
     return IM_OK;
 }
@@ -521,10 +522,14 @@ int build_prepare(im_ctx* c, uint32_t R, uint64_t seed, double p, double alpha) 
     while (rp2 < R) rp2 <<= 1;
     if (B > rp2) B = rp2;
 
+    // IM_UNION_AUTO: bucketed records once a batch's parent arrays (4 n B bytes) are well beyond
+    // L2, where taking the sketches one after the other keeps the climbed parents there
+    const int upath = c->union_path != IM_UNION_AUTO ? c->union_path
+                      : (uint64_t)n * B * 4 > (256ull << 20) ? IM_UNION_BUCKETS : IM_UNION_RECORDS;
     // live-pair records of one batch: expected p m B, with a generous margin; a batch that
     // still overflows falls back to the fused sample+union loop on the device
     uint64_t live_cap = 0;
-    if (c->union_path != IM_UNION_FUSED && c->m > 0 && (smp.eT || smp.all_live || smp.T != 0)) {
+    if (upath != IM_UNION_FUSED && c->m > 0 && (smp.eT || smp.all_live || smp.T != 0)) {
         const double pe = smp.eT ? c->mean_p : smp.all_live ? 1.0 : p;
         const double ex = pe * (double)c->m * B;
         double cap = 1.3 * ex + 16.0 * std::sqrt(ex) + 65536.0;
@@ -547,7 +552,7 @@ int build_prepare(im_ctx* c, uint32_t R, uint64_t seed, double p, double alpha) 
                       nc <= c->compact_cap && live_cap <= c->live_cap && nspec <= c->cap_nspec &&
                       (all || c->d_cidx != nullptr);
     const bool same_shape = c->R == R && c->rho == rho && c->hub_rows == hub_rows && c->batch_used == B &&
-                            c->all_centers == all && c->spec_count == nspec;
+                            c->all_centers == all && c->spec_count == nspec && c->union_used == upath;
     if (!fits) {
         free_sketch_state(c);
     } else if (!same_shape || c->smp.salt != smp.salt || c->smp.T != smp.T || c->smp.all_live != smp.all_live ||
@@ -560,12 +565,13 @@ int build_prepare(im_ctx* c, uint32_t R, uint64_t seed, double p, double alpha) 
     c->key_bits = (uint32_t)bits;
     c->smp = smp;
     c->batch_used = B;
+    c->union_used = upath;
     c->spec_count = nspec;
     if (!fits) {
         // at least the context's reserve (im_create_reserved), so that later builds fit
         const uint32_t na = std::max(n, c->res_n), Ra = std::max(R, c->res_R);
         const size_t nca = std::max<size_t>(nc, c->res_nc);
-        const uint64_t livea = c->union_path != IM_UNION_FUSED ? std::max(live_cap, c->res_live) : live_cap;
+        const uint64_t livea = upath != IM_UNION_FUSED ? std::max(live_cap, c->res_live) : live_cap;
         const uint32_t nsa = std::min(std::max(nspec, c->res_n ? std::min<uint32_t>(c->spec_req, kSpecMax) : 0u),
                                       kSpecMax);
         const bool compact = !all || c->res_n > 0;   // a reserved context may serve compact builds
@@ -821,6 +827,7 @@ int im_get_stats(im_ctx* c, im_stats* out) {
     out->launches = c->launches;
 
     out->sketch_batch = c->batch_used;
+    out->union_path = (uint32_t)c->union_used;
     uint64_t ev = 0;
     for (auto x : c->round_evals) ev += x;
     out->evaluations = ev;

@@ -360,9 +360,11 @@ extern "C" int im_batch_tune(im_instance* inst, uint32_t count, im_batch_schedul
             im_set_sketch_batch(c, t.sketch_batch);
             im_set_pipeline(c, t.lanes);
             im_set_hubs(c, t.hub_cap, 32);
-            const double rec = time_union_path(c, in, IM_UNION_RECORDS);
-            const double fus = time_union_path(c, in, IM_UNION_FUSED);
-            s.union_path[cl] = fus < rec ? IM_UNION_FUSED : IM_UNION_RECORDS;
+            double best_t = 1e30;
+            for (int path : {IM_UNION_RECORDS, IM_UNION_BUCKETS, IM_UNION_FUSED}) {
+                const double t_path = time_union_path(c, in, path);
+                if (t_path < best_t) { best_t = t_path; s.union_path[cl] = (uint32_t)path; }
+            }
         }
         im_destroy(c);
     }

@@ -24,7 +24,9 @@ constexpr size_t kCenterSelBytes = 4096;                // device state of the c
 constexpr uint32_t kHubsAuto = 0xFFFFFFFFu;                // im_ctx::hub_cap default
 constexpr uint32_t kMaxLanes = 2;                          // sketch batches in flight at most (a third lane measured no faster)
 constexpr uint32_t kSpecMax = 8;                        // candidate first seeds (see im_ctx::spec_req)
-constexpr uint32_t kLiveCounters = 34;                   // per lane: record counts (one per bucket) + ticket
+// per lane: record count and ticket (two words), or, for bucketed records, the overflow flag and
+// its ticket, then one count per (sketch, sampling block) region: 8 + 32 x 152 x 16 words
+constexpr uint32_t kLiveCounters = (8 + 32u * 152u * 16u) / 2 + 1;   // in 64-bit words
 
 // splitmix64 output finaliser (Steele, Lea, Flood 2014).
 __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
@@ -401,7 +403,8 @@ struct im_ctx {
     cudaEvent_t ev_join[imk::kMaxLanes] = {};
     cudaStream_t cur = nullptr;                  // stream the next launch goes to
     uint32_t lanes = 2;                          // sketch batches alternate between two streams
-    int union_path = IM_UNION_RECORDS;           // im_set_union_path
+    int union_path = IM_UNION_AUTO;              // im_set_union_path
+    int union_used = IM_UNION_RECORDS;           // the path the last build took (AUTO resolved)
     uint32_t batch_req = 0, batch_used = 0, batch_alloc = 0;
     uint64_t live_cap = 0;           // live-pair records allocated per lane
     // capacities of the sketch buffers (a later build that fits reuses them)

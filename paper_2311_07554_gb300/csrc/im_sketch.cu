@@ -206,22 +206,27 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, unsigned lane) 
     return x;
 }
 
-// Sampling with the live pairs grouped by sketch: the records of sketch b go to bucket b (8
-// bytes each, (u, v)), so that the unions can run sketch by sketch while one sketch's parent
-// array stays in L2.  Per warp and pair of edges per lane, the live masks are transposed so
-// that lane b holds sketch b's live edges: lane b reserves room in bucket b with one atomic and
-// writes them (the edges' endpoints come from their lanes by shuffles).  Also initialises the
-// batch's forest, as k_sample_emit does.
+// Sampling with the live pairs grouped by sketch and by block: block k writes the records (8
+// bytes, (u, v)) of sketch b into region b * gridDim.x + k of the record buffer, counting them in
+// shared memory, so no global atomic is needed; the unions then take the regions sketch by
+// sketch, while one sketch's parent array stays in L2.  Per warp and pair of edges per lane, the
+// live masks are transposed so that lane b holds sketch b's live edges; lane b reserves room in
+// its block's region of sketch b with one shared-memory atomic and writes them (the endpoints
+// come from their lanes by shuffles).  At the end every block stores its region counts (and
+// raises *overflow if a region did not fit).  Also initialises the batch's forest, as
+// k_sample_emit does.
 template <int B>
 __global__ void __launch_bounds__(256)
 k_sample_bucket(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, uint32_t r0, uint32_t nb,
-                uint2* __restrict__ out, unsigned long long* __restrict__ bucket_n, uint64_t capb,
-                uint32_t* __restrict__ parent, uint64_t* __restrict__ word, uint32_t n,
-                const uint32_t* __restrict__ cidx, int key_mode) {
+                uint2* __restrict__ out, uint32_t* __restrict__ region_n, uint32_t capr,
+                unsigned int* __restrict__ overflow, uint32_t* __restrict__ parent, uint64_t* __restrict__ word,
+                uint32_t n, const uint32_t* __restrict__ cidx, int key_mode) {
+    __shared__ uint32_t cnt[32];
     const uint64_t npairs = (m + 1) >> 1;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t g0 = (uint64_t)(r0 + 1u) * kGamma;
     const unsigned lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) cnt[threadIdx.x] = 0;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         const uint64_t w = ((uint64_t)label_key(v, key_mode, cidx) << 32) | 1u;
         for (uint32_t b = 0; b < nb; ++b) {
@@ -229,7 +234,8 @@ k_sample_bucket(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, u
             word[(size_t)b * n + v] = w;
         }
     }
-    uint2* mine = out + (size_t)lane * capb;   // lane b writes bucket b
+    __syncthreads();
+    uint2* mine = out + ((size_t)lane * gridDim.x + blockIdx.x) * capr;   // lane b: sketch b's region
     for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < npairs; base += stride) {
         const uint64_t i = base + threadIdx.x;
         uint32_t live0 = 0, live1 = 0;
@@ -240,11 +246,10 @@ k_sample_bucket(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, u
         }
         if (!__any_sync(0xffffffffu, (live0 | live1) != 0u)) continue;
         uint32_t t0 = warp_transpose32(live0, lane), t1 = warp_transpose32(live1, lane);
-        const uint32_t cnt = __popc(t0) + __popc(t1);
-        unsigned long long pos = 0;
-        if (cnt) pos = atomicAdd(bucket_n + lane, (unsigned long long)cnt);
-        // rounds: each lane writes its next record; the edge comes from its lane by shuffles
-        for (;;) {
+        const uint32_t c = __popc(t0) + __popc(t1);
+        uint32_t pos = 0;
+        if (c) pos = atomicAdd(&cnt[lane], c);
+        for (;;) {   // rounds: each lane writes its next record
             const bool has = (t0 | t1) != 0u;
             if (!__any_sync(0xffffffffu, has)) break;
             int src = 0;
@@ -254,86 +259,86 @@ k_sample_bucket(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, u
             const uint32_t ex = __shfl_sync(0xffffffffu, two.x, src), ey = __shfl_sync(0xffffffffu, two.y, src);
             const uint32_t ez = __shfl_sync(0xffffffffu, two.z, src), ew = __shfl_sync(0xffffffffu, two.w, src);
             if (has) {
-                if (pos < capb) mine[pos] = second ? make_uint2(ez, ew) : make_uint2(ex, ey);
+                if (pos < capr) mine[pos] = second ? make_uint2(ez, ew) : make_uint2(ex, ey);
                 ++pos;
             }
         }
     }
+    __syncthreads();
+    if (threadIdx.x < nb) {
+        const uint32_t k = cnt[threadIdx.x];
+        region_n[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = k;
+        if (k > capr) atomicOr(overflow, 1u);
+    }
 }
 
-// Unions of the bucketed records, bucket after bucket: the grid sweeps the records of sketch 0,
-// then sketch 1, ..., so that the parents being climbed are those of one or two sketches (L2
-// resident on large graphs).  Several unions in flight per thread, as k_union_live.  The last
-// block to read the counts resets them; if a bucket overflowed, the batch is redone with the
-// fused sample+union loop.
+// Unions of the bucketed records: block (b, q) = blockIdx.x / groups, % groups unites the records
+// of sketch b written by sampling blocks q * rpb .. q * rpb + rpb - 1 (its regions, taken as one
+// list: each thread walks it with its own cursor), so the grid sweeps the sketches in order and
+// the parents being climbed belong to one or two sketches at a time (L2-resident on large
+// graphs).  Several unions in flight per thread, as k_union_live.  The last block resets the
+// overflow flag; if it was raised, the batch is redone with the fused sample+union loop.
+constexpr uint32_t kBucketRegionsPerBlock = 64;
 template <int B>
 __global__ void __launch_bounds__(256)
-k_union_bucket(const uint2* __restrict__ recs, unsigned long long* __restrict__ bucket_n, uint64_t capb,
-               uint32_t* __restrict__ parent, uint32_t n, const uint4* __restrict__ edge_pairs, uint64_t m,
-               Sampler smp, uint32_t r0, uint32_t nb, unsigned long long* __restrict__ total) {
-    __shared__ unsigned long long s_end[32];   // inclusive prefix of the bucket counts
-    __shared__ int s_over;
-    if (threadIdx.x < 32) {
-        const unsigned long long c0 =
-            threadIdx.x < nb ? *reinterpret_cast<volatile unsigned long long*>(bucket_n + threadIdx.x) : 0ull;
-        const int over = __any_sync(0xffffffffu, c0 > capb);
-        unsigned long long incl = c0 > capb ? capb : c0;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, d);
-            if ((int)threadIdx.x >= d) incl += y;
-        }
-        s_end[threadIdx.x] = incl;
-        unsigned long long all = c0;
-#pragma unroll
-        for (int d = 16; d; d >>= 1) all += __shfl_xor_sync(0xffffffffu, all, d);
-        if (threadIdx.x == 0) {
-            s_over = over;
-            __threadfence();
-            if (atomicAdd(bucket_n + 32, 1ull) == gridDim.x - 1ull) {   // every block has the counts
-                for (int b = 0; b < 32; ++b) bucket_n[b] = 0;
-                bucket_n[32] = 0;
-                atomicAdd(total, all);
-            }
+k_union_bucket(const uint2* __restrict__ recs, const uint32_t* __restrict__ region_n, uint32_t regions,
+               uint32_t rpb, uint32_t capr, unsigned int* __restrict__ overflow, uint32_t* __restrict__ parent,
+               uint32_t n, const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, uint32_t r0,
+               uint32_t nb, unsigned long long* __restrict__ total) {
+    __shared__ unsigned int s_over;
+    __shared__ uint32_t s_cnt[kBucketRegionsPerBlock];
+    const uint32_t groups = (regions + rpb - 1) / rpb;
+    const uint32_t b = blockIdx.x / groups;
+    const uint32_t k0 = (blockIdx.x % groups) * rpb;
+    const uint32_t nreg = min(rpb, regions - k0);
+    const uint32_t reg0 = b * regions + k0;   // first region: sketch b, sampling block k0
+    if (threadIdx.x < nreg) {
+        const uint32_t c = region_n[reg0 + threadIdx.x];
+        s_cnt[threadIdx.x] = c < capr ? c : capr;
+        if (c) atomicAdd(total, (unsigned long long)c);
+    }
+    if (threadIdx.x == 0) {
+        s_over = *reinterpret_cast<volatile unsigned int*>(overflow);
+        __threadfence();
+        if (atomicAdd(overflow + 1, 1u) == gridDim.x - 1u) {   // every block has read the flag
+            overflow[0] = 0;
+            overflow[1] = 0;
         }
     }
     __syncthreads();
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     if (s_over) {
         const uint64_t npairs = (m + 1) >> 1;
         const uint64_t g0 = (uint64_t)(r0 + 1u) * kGamma;
+        const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
         for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npairs; i += stride)
             sample_union_pair<B>(edge_pairs[i], i, m, smp, g0, nb, parent, n);
         return;
     }
-    const unsigned long long cnt = s_end[31];
+    uint32_t* Pb = parent + (size_t)b * n;
+    // cursor: record j of region r (of this block's list); advanced by blockDim.x records
+    uint32_t r = 0, j = threadIdx.x;
+    while (r < nreg && j >= s_cnt[r]) j -= s_cnt[r++];
     constexpr int K = kUnionChains;
-    uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t* P[K];
     uint32_t rx[K], ry[K], px[K], py[K], hres[K];
     bool act[K], hooked[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         act[k] = false;
         hooked[k] = false;
-        P[k] = parent;
         rx[k] = ry[k] = px[k] = py[k] = hres[k] = 0;
     }
-    uint32_t b = 0;   // bucket of index j (j only grows)
     for (;;) {
         bool any = false;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            if (!act[k] && j < cnt) {
-                while (j >= s_end[b]) ++b;
-                const uint64_t start = b ? s_end[b - 1] : 0ull;
-                const uint2 rc = recs[(size_t)b * capb + (j - start)];
-                j += stride;
-                P[k] = parent + (size_t)b * n;
+            if (!act[k] && r < nreg) {
+                const uint2 rc = recs[(size_t)(reg0 + r) * capr + j];
+                j += blockDim.x;
+                while (r < nreg && j >= s_cnt[r]) j -= s_cnt[r++];
                 rx[k] = rc.x;
                 ry[k] = rc.y;
-                px[k] = __ldca(P[k] + rx[k]);
-                py[k] = __ldca(P[k] + ry[k]);
+                px[k] = __ldca(Pb + rx[k]);
+                py[k] = __ldca(Pb + ry[k]);
                 act[k] = true;
             }
             any |= act[k];
@@ -353,12 +358,12 @@ k_union_bucket(const uint2* __restrict__ recs, unsigned long long* __restrict__ 
                 t = px[k]; px[k] = py[k]; py[k] = t;
             }
             if (rx[k] == px[k]) {
-                hres[k] = atomicCAS(P[k] + rx[k], rx[k], py[k]);
+                hres[k] = atomicCAS(Pb + rx[k], rx[k], py[k]);
                 hooked[k] = true;
             } else {
-                atomicCAS(P[k] + rx[k], px[k], py[k]);
+                atomicCAS(Pb + rx[k], px[k], py[k]);
                 rx[k] = px[k];
-                px[k] = __ldca(P[k] + rx[k]);
+                px[k] = __ldca(Pb + rx[k]);
             }
         }
     }
@@ -1011,16 +1016,35 @@ int launch_sample_split(im_ctx* c, im_ctx::Lane& L, uint32_t r0, uint32_t nb, in
     const double pl = c->smp.eT ? c->mean_p : c->smp.all_live ? 1.0 : c->p;
     const unsigned gu = grid_for((uint64_t)(pl * (double)c->m * nb) + 1, T, 152u * 16u);
     const uint64_t live_cap = im_record_cap(c->live_cap);
-    // bucketed records: 8 bytes each, in c->batch_used regions of the lane's record buffer
-    const uint64_t capb = 2 * live_cap / (c->batch_used ? c->batch_used : 1);
+    // bucketed records: 8 bytes each, one region per (sketch, sampling block) in the lane's record
+    // buffer; counts and the overflow flag in the lane's counter array
+    const uint32_t B_ = c->batch_used ? c->batch_used : 1;
+    const uint32_t capr = (uint32_t)std::min<uint64_t>(2 * live_cap / ((uint64_t)B_ * gs), 0xFFFFFFFFull);
     uint2* buckets = reinterpret_cast<uint2*>(L.live);
+    uint32_t* region_n = reinterpret_cast<uint32_t*>(L.live_n) + 8;   // after the flag words
+    unsigned int* overflow = reinterpret_cast<unsigned int*>(L.live_n);
+    // union blocks: several of one sketch's regions per block (up to about 4K records), as long
+    // as the sketches that the resident blocks work on -- the fraction of a sketch that they
+    // cover, plus the sketch being finished -- keep their parents within 32 MiB of L2.  With
+    // 64 MiB parent arrays, one region per block.
+    static int union_per_sm = 0;
+    if (union_per_sm == 0 &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&union_per_sm, k_union_bucket<32>, T, 0) != cudaSuccess)
+        union_per_sm = 8;
+    const double resident = 152.0 * std::max(1, union_per_sm);
+    const double sketches_in_l2 = (32.0 * (1 << 20)) / (4.0 * std::max(1u, c->n));
+    const double per_region = std::max(1.0, pl * (double)c->m / gs);
+    const double rpb_d = std::min({(double)kBucketRegionsPerBlock, 4096.0 / per_region,
+                                   (sketches_in_l2 - 1.0) * gs / resident});
+    const uint32_t rpb = (uint32_t)std::max(1.0, rpb_d);
+    const unsigned gub = ((gs + rpb - 1) / rpb) * nb;
 #define IM_SE(BB)                                                                                 \
     do {                                                                                          \
-        if (c->union_path == IM_UNION_BUCKETS) {                                                  \
+        if (c->union_used == IM_UNION_BUCKETS) {                                                  \
             IM_LAUNCH(c, K_SAMPLE_EMIT, k_sample_bucket<BB>, gs, T, 0, ep, c->m, c->smp, r0, nb,     \
-                      buckets, L.live_n, capb, L.parent, L.word, c->n, c->d_cidx, key_mode);       \
-            IM_LAUNCH(c, K_UNION, k_union_bucket<BB>, gu, T, 0, buckets, L.live_n, capb, L.parent,  \
-                      c->n, ep, c->m, c->smp, r0, nb, c->d_live_total);                           \
+                      buckets, region_n, capr, overflow, L.parent, L.word, c->n, c->d_cidx, key_mode); \
+            IM_LAUNCH(c, K_UNION, k_union_bucket<BB>, gub, T, 0, buckets, region_n, gs, rpb, capr,      \
+                      overflow, L.parent, c->n, ep, c->m, c->smp, r0, nb, c->d_live_total);       \
             break;                                                                                \
         }                                                                                         \
         IM_LAUNCH(c, K_SAMPLE_EMIT, k_sample_emit<BB>, gs, T, 0, ep, c->m, c->smp, r0, nb, L.live,   \
@@ -1081,7 +1105,7 @@ int batch_components(im_ctx* c, im_ctx::Lane& L, uint32_t r0, uint32_t nb, int k
     const uint32_t n = c->n;
     const unsigned T = 256;
     const bool sample = (c->smp.eT || c->smp.all_live || c->smp.T != 0) && c->m > 0;
-    if (sample && c->union_path == IM_UNION_FUSED && nb <= c->batch_used) {
+    if (sample && c->union_used == IM_UNION_FUSED && nb <= c->batch_used) {
         IM_LAUNCH(c, K_BATCH_INIT, k_forest_init, dim3(grid_for(n, T, (152u * 16u + nb - 1) / nb), nb), T, 0,
                   L.parent, L.word, n, c->d_cidx, key_mode);
         const int rc = launch_sample_unite(c, L, r0, nb);

@@ -153,6 +153,39 @@ def _run_path(n, u, v, seed, p, R, alpha, k, path):
     return out
 
 
+@pytest.mark.parametrize("R", [40, 64])
+def test_bucketed_unions_over_many_regions(R):
+    # a graph large enough that the bucketed sampling writes one region per (sketch, sampling
+    # block) for thousands of blocks and each union block takes several regions of one sketch
+    # (R = 40: a ragged second batch); equal to the oracle and to the record path
+    n, u, v = graphgen.chung_lu(200000, 2000000, 2.1, 2000.0, 19)
+    g = _run_path(n, u, v, 42, 0.1, R, 0.1, 5, im.IM_UNION_BUCKETS)
+    o = _oracle(n, u, v, 42, 0.1, R, 0.1, 5)
+    _compare(g, o, 5)
+    r = _run_path(n, u, v, 42, 0.1, R, 0.1, 5, im.IM_UNION_RECORDS)
+    for key in ("gains", "label", "size", "seeds", "seed_gains"):
+        assert np.array_equal(g[key], r[key]), key
+
+
+def test_automatic_union_path():
+    # IM_UNION_AUTO (the default) takes the record path while a batch's parent arrays fit in
+    # 256 MiB and the bucketed path beyond
+    n, u, v = graphgen.erdos_renyi(3000, 9000, 21)
+    with im.IMContext(n, u, v) as ctx:
+        ctx.build_sketches(32, 42, 0.1, 1.0)
+        assert ctx.stats()["union_path"] == im.IM_UNION_RECORDS
+    n2 = 2200000                        # 4 n B = 282 MB with 32 sketches per batch
+    u2 = np.arange(0, 200000, dtype=np.uint32)
+    v2 = (u2 * 7 + 1) % n2
+    with im.IMContext(n2, u2, v2.astype(np.uint32)) as ctx:
+        im.im_set_sketch_batch(ctx.h, 32)
+        ctx.build_sketches(32, 42, 0.5, 1.0)
+        assert ctx.stats()["union_path"] == im.IM_UNION_BUCKETS
+        im.im_set_union_path(ctx.h, im.IM_UNION_RECORDS)
+        ctx.build_sketches(32, 42, 0.5, 1.0)
+        assert ctx.stats()["union_path"] == im.IM_UNION_RECORDS
+
+
 @pytest.mark.parametrize("R", [1, 31, 33, 64])
 def test_ragged_sketch_counts(R):
     n, u, v = graphgen.erdos_renyi(777, 3333, 5)
