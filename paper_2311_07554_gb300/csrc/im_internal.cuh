@@ -15,6 +15,10 @@ namespace imk {
 constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;   // splitmix64 increment
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint32_t kCovered = 0x80000000u;            // size word: component holds a seed
+// parent entry of a root after the counting pass: the root has members (vertex ids are < 2^31),
+// so its root word holds the component's size and key; an unflagged root is a singleton
+constexpr uint32_t kRootFlag = 0x80000000u;
+constexpr uint32_t kIdMask = 0x7FFFFFFFu;
 constexpr uint32_t kNoCenterTag = 0x80000000u;        // spread: component id without a center
 constexpr uint32_t kQcap = 256;                       // per-warp BFS queue (shared memory)
 constexpr uint32_t kSpreadKMax = 16384;

@@ -538,7 +538,10 @@ k_union_live(const uint4* __restrict__ recs, unsigned long long* __restrict__ re
 // the minimum label key.  Equal roots are merged inside a warp (match_any); each block keeps
 // a small direct-mapped cache of roots (claimed by the first root that maps to a slot), so
 // the roots that recur within a block -- a giant component's above all -- cost one global
-// atomic pair per block, flushed once at its end; other roots are updated in place.
+// atomic pair per block, flushed once at its end; other roots are updated in place.  Every
+// root that receives members gets kRootFlag on its parent entry (same value from every
+// writer), so that the gain pass reads root words only for vertices in components of two or
+// more: an unflagged root is a singleton of size 1 whose key is its own.
 // key_mode 0: every vertex offers lk(v) = v (the smallest id); 1: only centers offer their
 // center index (components without a center need no label); 2: sizes only.
 constexpr int kCountSlots = 64;
@@ -581,6 +584,7 @@ k_compress_count(uint32_t* __restrict__ parent, uint64_t* __restrict__ word, uin
                     atomicAdd(&tcnt[h], cnt);
                     if (gmin != kNone) atomicMin(&tmin[h], gmin);
                 } else {
+                    __stcg(P + root, root | kRootFlag);
                     atomicAdd(w_count(W + root), cnt);
                     if (gmin != kNone) atomicMin(w_key(W + root), gmin);
                 }
@@ -591,6 +595,7 @@ k_compress_count(uint32_t* __restrict__ parent, uint64_t* __restrict__ word, uin
     for (int i = threadIdx.x; i < kCountSlots; i += blockDim.x) {
         const uint32_t rt = tkey[i];
         if (rt != kNone) {
+            __stcg(P + rt, rt | kRootFlag);
             atomicAdd(w_count(W + rt), tcnt[i]);
             if (tmin[i] != kNone) atomicMin(w_key(W + rt), tmin[i]);
         }
@@ -615,7 +620,7 @@ k_gain_compact(const uint32_t* __restrict__ parent, const uint64_t* __restrict__
     if (kSpec > 0) {
         for (uint32_t i = threadIdx.x; i < nb * nspec; i += blockDim.x) {
             const uint32_t b = i / nspec, k = i % nspec;
-            sroot[b][k] = parent[(size_t)b * n + spec_ids[k]];
+            sroot[b][k] = parent[(size_t)b * n + spec_ids[k]] & kIdMask;
         }
         __syncthreads();
     }
@@ -627,20 +632,23 @@ k_gain_compact(const uint32_t* __restrict__ parent, const uint64_t* __restrict__
         for (int k = 0; k < kSpec; ++k) ov[k] = 0;
         const uint32_t ci = kAll ? v : cidx[v];
         // U sketches at a time: their parent loads, then their root words, are
-        // independent, so a thread waits for two memory round trips per group, not per sketch
+        // independent, so a thread waits for two memory round trips per group, not per sketch.
+        // A singleton (unflagged root of itself) needs no root word: size 1, its own key.
         constexpr int U = GainUnroll<kSpec>::value;
+        const uint64_t own = ((uint64_t)ci << 32) | 1u;
         for (uint32_t b0 = 0; b0 < nb; b0 += U) {
             uint32_t rt[U];
             uint64_t wv[U];
 #pragma unroll
-            for (int j = 0; j < U; ++j) rt[j] = b0 + j < nb ? parent[(size_t)(b0 + j) * n + v] : 0u;
+            for (int j = 0; j < U; ++j) rt[j] = b0 + j < nb ? parent[(size_t)(b0 + j) * n + v] : v;
 #pragma unroll
-            for (int j = 0; j < U; ++j) wv[j] = b0 + j < nb ? word[(size_t)(b0 + j) * n + rt[j]] : 0ull;
+            for (int j = 0; j < U; ++j)
+                wv[j] = rt[j] != v ? word[(size_t)(b0 + j) * n + (rt[j] & kIdMask)] : own;
 #pragma unroll
             for (int j = 0; j < U; ++j) {
                 const uint32_t b = b0 + j;
                 if (b >= nb) break;
-                const uint32_t root = rt[j];
+                const uint32_t root = rt[j] & kIdMask;
                 const uint64_t w = wv[j];
                 const uint32_t c = (uint32_t)w;
                 g += c;
@@ -686,7 +694,7 @@ k_gain_full(const uint32_t* __restrict__ parent, const uint64_t* __restrict__ wo
     if (kSpec > 0) {
         for (uint32_t i = threadIdx.x; i < nb * nspec; i += blockDim.x) {
             const uint32_t bb = i / nspec, k = i % nspec;
-            sroot[bb][k] = parent[(size_t)bb * n + spec_ids[k]];
+            sroot[bb][k] = parent[(size_t)bb * n + spec_ids[k]] & kIdMask;
         }
         __syncthreads();
     }
@@ -700,8 +708,9 @@ k_gain_full(const uint32_t* __restrict__ parent, const uint64_t* __restrict__ wo
         for (int k = 0; k < KS; ++k) ov[k] = 0;
         if (valid) {
             for (uint32_t bb = warp; bb < nb; bb += kGainWarps) {
-                const uint32_t root = parent[(size_t)bb * n + v];
-                const uint64_t w = word[(size_t)bb * n + root];
+                const uint32_t pv = parent[(size_t)bb * n + v];
+                const uint32_t root = pv & kIdMask;
+                const uint64_t w = pv != v ? word[(size_t)bb * n + root] : (((uint64_t)v << 32) | 1u);
                 const uint32_t c = (uint32_t)w;
                 g += c;
 #pragma unroll
@@ -754,7 +763,7 @@ k_spec_overlap(const uint32_t* __restrict__ parent, const uint64_t* __restrict__
     __shared__ uint32_t sroot[32][kSpecMax];
     for (uint32_t i = threadIdx.x; i < nb * nspec; i += blockDim.x) {
         const uint32_t b = i / nspec, k = i % nspec;
-        sroot[b][k] = parent[(size_t)b * n + spec_ids[k]];
+        sroot[b][k] = parent[(size_t)b * n + spec_ids[k]] & kIdMask;
     }
     __syncthreads();
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
@@ -762,7 +771,7 @@ k_spec_overlap(const uint32_t* __restrict__ parent, const uint64_t* __restrict__
 #pragma unroll
         for (uint32_t k = 0; k < kSpecMax; ++k) ov[k] = 0;
         for (uint32_t b = 0; b < nb; ++b) {
-            const uint32_t root = parent[(size_t)b * n + v];
+            const uint32_t root = parent[(size_t)b * n + v] & kIdMask;
             bool any = false;
 #pragma unroll
             for (uint32_t k = 0; k < kSpecMax; ++k) any |= k < nspec && root == sroot[b][k];
@@ -811,7 +820,7 @@ __global__ void k_cover_roots(const uint32_t* __restrict__ parent, uint64_t* __r
     const uint32_t total = nb * nseeds;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
         const uint32_t b = i / nseeds, sd = seeds[i % nseeds];
-        const uint32_t root = parent[(size_t)b * n + sd];
+        const uint32_t root = parent[(size_t)b * n + sd] & kIdMask;
         atomicOr(w_count(word + (size_t)b * n + root), kCovered);
     }
 }
@@ -825,7 +834,7 @@ k_mc_cover(const uint32_t* __restrict__ parent, uint64_t* __restrict__ word, uin
     unsigned long long acc = 0;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < tasks; i += gridDim.x * blockDim.x) {
         const uint32_t b = i / k, sd = seeds[i % k];
-        const uint32_t root = parent[(size_t)b * n + sd];
+        const uint32_t root = parent[(size_t)b * n + sd] & kIdMask;
         const uint32_t old = atomicOr(w_count(word + (size_t)b * n + root), kCovered);
         if (!(old & kCovered)) acc += old;
     }
@@ -844,7 +853,7 @@ __global__ void k_refresh_gather(const uint32_t* __restrict__ parent, const uint
         const uint32_t x = batch[j];
         unsigned long long d = 0;
         for (uint32_t b = 0; b < nb; ++b) {
-            const uint32_t c = (uint32_t)word[(size_t)b * n + parent[(size_t)b * n + x]];
+            const uint32_t c = (uint32_t)word[(size_t)b * n + (parent[(size_t)b * n + x] & kIdMask)];
             d += (c & kCovered) ? 0u : c;
         }
         fresh[j] += d;
@@ -854,7 +863,7 @@ __global__ void k_refresh_gather(const uint32_t* __restrict__ parent, const uint
 __global__ void k_labels_out(const uint32_t* __restrict__ P, const uint64_t* __restrict__ W, uint32_t n,
                              uint32_t* __restrict__ out) {
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-        out[v] = (uint32_t)(W[P[v]] >> 32);
+        out[v] = (uint32_t)(W[P[v] & kIdMask] >> 32);
 }
 
 // ---- centers: the rho smallest ckey(v) = mix(v ^ csalt) (distinct: mix is a bijection) ----

@@ -67,12 +67,14 @@ __device__ __forceinline__ void unite_rem(uint32_t* P, uint32_t x, uint32_t y) {
 
 // Full compression once no union runs any more: walk to the (final) root without writing,
 // then store that root along the path.  Only the root is ever written, so a concurrent
-// compression of an overlapping path cannot leave an intermediate ancestor behind.
+// compression of an overlapping path cannot leave an intermediate ancestor behind.  A root's
+// own entry may carry kRootFlag (set by the counting pass: the root has members), which the
+// walk ignores.
 __device__ __forceinline__ uint32_t compress_to_root(uint32_t* P, uint32_t v) {
     uint32_t root = v;
-    for (uint32_t p = __ldca(P + root); p != root; p = __ldca(P + root)) root = p;
+    for (uint32_t p = __ldca(P + root) & kIdMask; p != root; p = __ldca(P + root) & kIdMask) root = p;
     for (uint32_t x = v; x != root;) {
-        const uint32_t nx = __ldca(P + x);
+        const uint32_t nx = __ldca(P + x) & kIdMask;
         if (nx != root) __stcg(P + x, root);
         x = nx;
     }

@@ -43,7 +43,7 @@ def test_chunglu_1M_full_parity():
     dv = torch.from_numpy(v.view(np.int32)).cuda()
     with im.IMContext(n, du, dv) as ctx:
         ctx.build_sketches(R, seed, p, alpha)
-        assert ctx.stats()["union_path"] == im.IM_UNION_BUCKETS     # the default on this size
+        assert ctx.stats()["union_path"] == im.IM_UNION_RECORDS     # the default on this size
         gains = ctx.gains()
         ctr = ctx.centers()
         lab, sz = ctx.compact()
