@@ -29,8 +29,8 @@ constexpr uint32_t kHubsAuto = 0xFFFFFFFFu;                // im_ctx::hub_cap de
 constexpr uint32_t kMaxLanes = 2;                          // sketch batches in flight at most (a third lane measured no faster)
 constexpr uint32_t kSpecMax = 8;                        // candidate first seeds (see im_ctx::spec_req)
 // per lane: record count and ticket (two words), or, for bucketed records, the overflow flag and
-// its ticket, then one count per (sketch, sampling block) region: 8 + 32 x 152 x 16 words
-constexpr uint32_t kLiveCounters = (8 + 32u * 152u * 16u) / 2 + 1;   // in 64-bit words
+// its ticket, then one count per (sketch, sampling block) region: 8 + 32 x 152 x 4 words
+constexpr uint32_t kLiveCounters = (8 + 32u * 152u * 4u) / 2 + 1;   // in 64-bit words
 
 // splitmix64 output finaliser (Steele, Lea, Flood 2014).
 __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {

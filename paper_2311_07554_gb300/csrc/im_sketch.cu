@@ -275,10 +275,11 @@ k_sample_bucket(const uint4* __restrict__ edge_pairs, uint64_t m, Sampler smp, u
 // Unions of the bucketed records: block (b, q) = blockIdx.x / groups, % groups unites the records
 // of sketch b written by sampling blocks q * rpb .. q * rpb + rpb - 1 (its regions, taken as one
 // list: each thread walks it with its own cursor), so the grid sweeps the sketches in order and
-// the parents being climbed belong to one or two sketches at a time (L2-resident on large
-// graphs).  Several unions in flight per thread, as k_union_live.  The last block resets the
-// overflow flag; if it was raised, the batch is redone with the fused sample+union loop.
+// the parents being climbed belong to a few sketches at a time.  Several unions in flight per
+// thread, as k_union_live.  The last block resets the overflow flag; if it was raised, the
+// batch is redone with the fused sample+union loop.
 constexpr uint32_t kBucketRegionsPerBlock = 64;
+constexpr uint32_t kBucketBlocksPerSM = 4;
 template <int B>
 __global__ void __launch_bounds__(256)
 k_union_bucket(const uint2* __restrict__ recs, const uint32_t* __restrict__ region_n, uint32_t regions,
@@ -1028,31 +1029,24 @@ int launch_sample_split(im_ctx* c, im_ctx::Lane& L, uint32_t r0, uint32_t nb, in
     // bucketed records: 8 bytes each, one region per (sketch, sampling block) in the lane's record
     // buffer; counts and the overflow flag in the lane's counter array
     const uint32_t B_ = c->batch_used ? c->batch_used : 1;
-    const uint32_t capr = (uint32_t)std::min<uint64_t>(2 * live_cap / ((uint64_t)B_ * gs), 0xFFFFFFFFull);
+    // the bucketed sampler runs 4 blocks per SM: the other lane's union-find kernels then find
+    // room beside it (124 against 127 ms per step on R-MAT scale 24 with 16 blocks per SM)
+    const unsigned gsb = grid_for(npairs, T, 152u * kBucketBlocksPerSM);
+    const uint32_t capr = (uint32_t)std::min<uint64_t>(2 * live_cap / ((uint64_t)B_ * gsb), 0xFFFFFFFFull);
     uint2* buckets = reinterpret_cast<uint2*>(L.live);
     uint32_t* region_n = reinterpret_cast<uint32_t*>(L.live_n) + 8;   // after the flag words
     unsigned int* overflow = reinterpret_cast<unsigned int*>(L.live_n);
-    // union blocks: several of one sketch's regions per block (up to about 4K records), as long
-    // as the sketches that the resident blocks work on -- the fraction of a sketch that they
-    // cover, plus the sketch being finished -- keep their parents within 32 MiB of L2.  With
-    // 64 MiB parent arrays, one region per block.
-    static int union_per_sm = 0;
-    if (union_per_sm == 0 &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&union_per_sm, k_union_bucket<32>, T, 0) != cudaSuccess)
-        union_per_sm = 8;
-    const double resident = 152.0 * std::max(1, union_per_sm);
-    const double sketches_in_l2 = (32.0 * (1 << 20)) / (4.0 * std::max(1u, c->n));
-    const double per_region = std::max(1.0, pl * (double)c->m / gs);
-    const double rpb_d = std::min({(double)kBucketRegionsPerBlock, 4096.0 / per_region,
-                                   (sketches_in_l2 - 1.0) * gs / resident});
-    const uint32_t rpb = (uint32_t)std::max(1.0, rpb_d);
-    const unsigned gub = ((gs + rpb - 1) / rpb) * nb;
+    // union blocks: rpb consecutive regions of one sketch, about 32K records per block (fewer,
+    // longer blocks: 124 against 137 ms per step on R-MAT scale 24 with one region per block)
+    const double per_region = std::max(1.0, pl * (double)c->m / gsb);
+    const uint32_t rpb = (uint32_t)std::min(64.0, std::max(1.0, std::round(32768.0 / per_region)));
+    const unsigned gub = ((gsb + rpb - 1) / rpb) * nb;
 #define IM_SE(BB)                                                                                 \
     do {                                                                                          \
         if (c->union_used == IM_UNION_BUCKETS) {                                                  \
-            IM_LAUNCH(c, K_SAMPLE_EMIT, k_sample_bucket<BB>, gs, T, 0, ep, c->m, c->smp, r0, nb,     \
+            IM_LAUNCH(c, K_SAMPLE_EMIT, k_sample_bucket<BB>, gsb, T, 0, ep, c->m, c->smp, r0, nb,    \
                       buckets, region_n, capr, overflow, L.parent, L.word, c->n, c->d_cidx, key_mode); \
-            IM_LAUNCH(c, K_UNION, k_union_bucket<BB>, gub, T, 0, buckets, region_n, gs, rpb, capr,      \
+            IM_LAUNCH(c, K_UNION, k_union_bucket<BB>, gub, T, 0, buckets, region_n, gsb, rpb, capr,     \
                       overflow, L.parent, c->n, ep, c->m, c->smp, r0, nb, c->d_live_total);       \
             break;                                                                                \
         }                                                                                         \
