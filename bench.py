@@ -146,11 +146,15 @@ def _kernel_digest(name: str, fn: str) -> str:
     return hashlib.sha1(text[i + 1:k + 1].encode()).hexdigest()[:12]
 
 
-def _traffic(kernel: str, units_per_launch: float):
-    """DRAM bytes per launch from the committed ncu summary, if taken on the current source."""
+def _traffic(kernel: str, units_per_launch: float, path: str = "records"):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current source.
+    The sampling and union entries of the bucketed path ("@buckets") are those of its own
+    kernels (k_sample_bucket, k_union_bucket)."""
     f = PROFILES / "dram_traffic.json"
     if not f.exists():
         return None
+    if path == "buckets" and kernel in ("sample_emit", "union"):
+        kernel += "@buckets"
     try:
         d = json.loads(f.read_text()).get(kernel)
         if not d or d.get("kernel_sha1") != _kernel_digest(d["source"], d["function"]):
@@ -168,16 +172,17 @@ def _traffic(kernel: str, units_per_launch: float):
 #                run on the FMA pipe and are not counted) -> bound "alu"; the peak is the ALU pipe
 #                of the GPU: 152 SMs x 4 sub-partitions x 16 lanes per clock at the SM clock (ncu
 #                counts 13.4 ALU-pipe operations per pair in this kernel, 75% pipe utilisation)
-#   union        one live (edge, sketch) pair: its 16-byte record read plus two random
-#                32-byte sector reads for the endpoints' parents -> 80 bytes, bound "hbm"
+#   union        one live (edge, sketch) pair: its record read (16 bytes; 8 on the bucketed
+#                path) plus two random 32-byte sector reads for the endpoints' parents -> 80
+#                (72) bytes, bound "hbm"
 #   compress     one (vertex, sketch): parent read + write, root word update -> 16 bytes, "hbm"
 ALU_OPS_PER_PAIR = 12.0
 ALU_LANES_PER_SM = 64          # integer ALU pipe: 16 lanes per SM sub-partition, 4 sub-partitions
-UNION_BYTES_PER_PAIR = 80.0
+UNION_BYTES_PER_PAIR = {"records": 80.0, "buckets": 72.0, "fused": 64.0}
 COMPRESS_BYTES_PER_VERTEX = 16.0
 
 
-def kernel_rooflines(prof, live_build, n, m, R, steps, peaks, peak_src, clk, hash_peak):
+def kernel_rooflines(prof, live_build, n, m, R, steps, peaks, peak_src, clk, hash_peak, path="records"):
     """Rooflines of the sketch kernels launched by the builds of the timed steps.
 
     The refresh passes of the selection run inside the selection graph, whose time is one
@@ -197,7 +202,7 @@ def kernel_rooflines(prof, live_build, n, m, R, steps, peaks, peak_src, clk, has
         per_launch = units / nl
         ach = per_launch * per_unit / avg_s / (1e12 if unit == "Tops/s" else 1e9)
         return {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
-                "frac": ach / peak, "traffic": _traffic(name, per_launch),
+                "frac": ach / peak, "traffic": _traffic(name, per_launch, path),
                 "units_per_launch": per_launch, "avg_launch_ms": avg_s * 1e3,
                 "share_of_device_time": ms / total_ms, "peak_source": psrc}
 
@@ -212,7 +217,7 @@ def kernel_rooflines(prof, live_build, n, m, R, steps, peaks, peak_src, clk, has
             f"({hash_peak:.3e} pairs/s x {ALU_OPS_PER_PAIR:.0f} ops)")
     live = live_build
     if "union" in prof and live > 0:
-        out["union"] = entry("union", "hbm", float(live), UNION_BYTES_PER_PAIR, "GB/s", hbm,
+        out["union"] = entry("union", "hbm", float(live), UNION_BYTES_PER_PAIR[path], "GB/s", hbm,
                              f"hbm_gbs of MEASURED_PEAKS.json ({peak_src})")
     if "compress_count" in prof:
         out["compress_count"] = entry("compress_count", "hbm", float(n) * R * passes,
@@ -221,7 +226,8 @@ def kernel_rooflines(prof, live_build, n, m, R, steps, peaks, peak_src, clk, has
     return out
 
 
-def sketch_roofline(prof, n, m, R, B, p_mean, alpha, steps, sketch_ms, peaks, hash_peak, live_build):
+def sketch_roofline(prof, n, m, R, B, p_mean, alpha, steps, sketch_ms, peaks, hash_peak, live_build,
+                    path="records"):
     """Sketch construction (one im_build_sketches) against the HBM roofline, as the modelled
     bytes of a build: per sketch 8m/B (edge stream shared by B sketches) + 2 p m 32 (random
     parent sectors of the live pairs) + 20 n (initialisation, compression, histogram, gain
@@ -238,7 +244,7 @@ def sketch_roofline(prof, n, m, R, B, p_mean, alpha, steps, sketch_ms, peaks, ha
              "compress_count": float(n) * R * steps, "gain_compact": float(n) * R * steps}
     measured = 0.0
     for k, u in units.items():
-        t = _traffic(k, u)   # bytes per unit x units of the timed steps
+        t = _traffic(k, u, path)   # bytes per unit x units of the timed steps
         if t is None or k not in prof:
             measured = None
             break
@@ -425,20 +431,21 @@ def measure_workload(args, n, u, v, prm, steps, warmup, dist, ws, local, full=Tr
 
     peaks, peak_src = _peaks()
     hash_peak = im.im_hash_peak(4096)
-    roofs = kernel_rooflines(prof, live_build, n, m, R, steps, peaks, peak_src, clk, hash_peak)
+    upath = ("fused", "records", "buckets")[int(st["union_path"])]
+    roofs = kernel_rooflines(prof, live_build, n, m, R, steps, peaks, peak_src, clk, hash_peak, upath)
     top = max(((kn, x) for kn, x in prof.items() if kn != "select_graph"), key=lambda kv: kv[1][0])
     roof = roofs.get(top[0]) or (max(roofs.values(), key=lambda r: r["share_of_device_time"]) if roofs else None)
     p_mean = prm["p"] if pe is None and prm["probs"] == "uniform" else None
     if p_mean is None:
         p_mean = float(np.mean(pe)) if pe is not None else float(live_build) / (m * R * steps)
     sk_roof = sketch_roofline(prof, n, m, R, int(st["sketch_batch"]), p_mean, prm["alpha"], steps,
-                              ms_build, peaks, hash_peak, live_build)
+                              ms_build, peaks, hash_peak, live_build, upath)
     out = {
         "workload": prm["name"],
         "value": job_rate(pairs, ws, ms_step / 1e3), "ms_per_step": ms_step, "steps": steps, "warmup": warmup,
         "config": {"workload": prm["name"], "n": n, "m": m, "p": prm["p"], "probs": prm["probs"], "R": R,
                    "alpha": prm["alpha"], "k": k, "l2": "flushed before every step (256 MB write)",
-                   "union_path": ("fused", "records", "buckets")[int(st["union_path"])],
+                   "union_path": upath,
                    "parallelism": f"replicas{ws}"},
         "time_to_k_ms": ms_build + ms_select,
         "sketch_ms": ms_build, "select_ms": ms_select,
