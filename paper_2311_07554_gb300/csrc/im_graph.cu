@@ -97,6 +97,79 @@ k_adj_fill(const uint2* __restrict__ edges, uint64_t m, const uint64_t* __restri
     }
 }
 
+// The static adjacency of a large graph in two passes, so that the scatter into adjacency
+// lists stays in L2: k_adj_bin groups the arcs by source range (kAdjBins ranges of width V),
+// each range's arcs written to that range's own CSR span [off[b V], off[(b+1) V]) of a
+// scratch array (the build's arc array, not yet in use at load time); k_adj_place then takes
+// the binned arcs in order, so that the blocks running at any moment place the arcs of one or
+// two source ranges, whose cursors, offsets and adjacency slots (tens of MB) stay in L2.  A
+// tile of kAdjTileEdges edges per block reserves room per range with one global atomic per
+// range (counted in shared memory first).
+constexpr uint32_t kAdjBins = 256;
+constexpr uint32_t kAdjEdgesPerThread = 4;
+
+__global__ void k_adj_bin_init(const uint64_t* __restrict__ off, uint32_t n, uint32_t V,
+                               unsigned long long* __restrict__ bcur) {
+    const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < kAdjBins) bcur[b] = off[min((uint64_t)b * V, (uint64_t)n)];
+}
+
+__global__ void __launch_bounds__(256)
+k_adj_bin(const uint2* __restrict__ edges, uint64_t m, uint32_t V, unsigned long long* __restrict__ bcur,
+          uint4* __restrict__ binned) {
+    __shared__ uint32_t hist[kAdjBins];
+    __shared__ unsigned long long base[kAdjBins];
+    const uint64_t tile = (uint64_t)blockDim.x * kAdjEdgesPerThread;
+    for (uint64_t t0 = (uint64_t)blockIdx.x * tile; t0 < m; t0 += (uint64_t)gridDim.x * tile) {
+        for (uint32_t i = threadIdx.x; i < kAdjBins; i += blockDim.x) hist[i] = 0;
+        __syncthreads();
+        uint2 ed[kAdjEdgesPerThread];
+        uint32_t rk[2 * kAdjEdgesPerThread];
+#pragma unroll
+        for (uint32_t j = 0; j < kAdjEdgesPerThread; ++j) {
+            const uint64_t e = t0 + (uint64_t)j * blockDim.x + threadIdx.x;   // coalesced
+            ed[j] = e < m ? edges[e] : make_uint2(0, 0);
+            if (e < m) {
+                rk[2 * j] = atomicAdd(&hist[ed[j].x / V], 1u);
+                rk[2 * j + 1] = atomicAdd(&hist[ed[j].y / V], 1u);
+            }
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < kAdjBins; i += blockDim.x)
+            base[i] = hist[i] ? atomicAdd(&bcur[i], (unsigned long long)hist[i]) : 0ull;
+        __syncthreads();
+#pragma unroll
+        for (uint32_t j = 0; j < kAdjEdgesPerThread; ++j) {
+            const uint64_t e = t0 + (uint64_t)j * blockDim.x + threadIdx.x;
+            if (e < m) {
+                const uint32_t x = ed[j].x, y = ed[j].y;
+                binned[base[x / V] + rk[2 * j]] = make_uint4(x, y, (uint32_t)e, (uint32_t)(e >> 32));
+                binned[base[y / V] + rk[2 * j + 1]] = make_uint4(y, x, (uint32_t)e, (uint32_t)(e >> 32));
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Arcs in CSR order of their source ranges; each goes to a slot of its source's list.
+__global__ void __launch_bounds__(256)
+k_adj_place(const uint4* __restrict__ binned, uint64_t narcs, const uint64_t* __restrict__ off,
+            uint32_t* __restrict__ cur, uint2* __restrict__ adj, uint32_t* __restrict__ src) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    // the loop bound is uniform over the block, so every warp-wide call has all lanes
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < narcs; base += stride) {
+        const uint64_t a = base + threadIdx.x;
+        const bool valid = a < narcs;
+        uint4 r = make_uint4(0, 0, 0, 0);
+        if (valid) r = __ldcs(binned + a);
+        const uint64_t pa = arc_slot(valid, r.x, true, off, cur, cur);
+        if (valid) {
+            adj[pa] = make_uint2(r.y, r.z);
+            src[pa] = r.x;
+        }
+    }
+}
+
 // Every build: the arcs of each vertex rewritten with the build's hash keys and center bits,
 // arcs to centers first (front cursor), the others from the back.  One thread per arc in CSR
 // order: the arcs of a warp mostly share their source, so a hub costs one cursor atomic per
@@ -351,8 +424,21 @@ int im_graph_build(im_ctx* c, const uint32_t* d_u, const uint32_t* d_v) {
                 rc = im_fail(c, IM_ECUDA, "memset");
                 break;
             }
-            IM_LAUNCH(c, K_CSR_FILL, k_adj_fill, grid_for(m, B, 152u * 16u), B, 0, c->d_edges, m, c->d_off,
-                      c->d_arc_cur, c->d_adj, c->d_src);
+            if (m >= (1ull << 24) && n >= 4 * kAdjBins && m < (1ull << 32)) {
+                // large graphs: binned by source range first (the arc array is the scratch; the
+                // range cursors sit in the second half of the cursor array)
+                const uint32_t V = (n + kAdjBins - 1) / kAdjBins;
+                unsigned long long* bcur = reinterpret_cast<unsigned long long*>(c->d_arc_cur + n + (n & 1u));
+                uint4* binned = reinterpret_cast<uint4*>(c->d_arcs);
+                IM_LAUNCH(c, K_CSR_FILL, k_adj_bin_init, 1, kAdjBins, 0, c->d_off, n, V, bcur);
+                IM_LAUNCH(c, K_CSR_FILL, k_adj_bin, grid_for((m + kAdjEdgesPerThread - 1) / kAdjEdgesPerThread, B,
+                                                             152u * 8u), B, 0, c->d_edges, m, V, bcur, binned);
+                IM_LAUNCH(c, K_CSR_FILL, k_adj_place, grid_for(2 * m, B, 152u * 16u), B, 0, binned, 2 * m,
+                          c->d_off, c->d_arc_cur, c->d_adj, c->d_src);
+            } else {
+                IM_LAUNCH(c, K_CSR_FILL, k_adj_fill, grid_for(m, B, 152u * 16u), B, 0, c->d_edges, m, c->d_off,
+                          c->d_arc_cur, c->d_adj, c->d_src);
+            }
         }
         if (!c->deferred) {
             cudaError_t e = cudaStreamSynchronize(c->stream);

@@ -1037,9 +1037,12 @@ int launch_sample_split(im_ctx* c, im_ctx::Lane& L, uint32_t r0, uint32_t nb, in
     uint32_t* region_n = reinterpret_cast<uint32_t*>(L.live_n) + 8;   // after the flag words
     unsigned int* overflow = reinterpret_cast<unsigned int*>(L.live_n);
     // union blocks: rpb consecutive regions of one sketch, about 32K records per block (fewer,
-    // longer blocks: 124 against 137 ms per step on R-MAT scale 24 with one region per block)
+    // longer blocks: 124 against 137 ms per step on R-MAT scale 24 with one region per block),
+    // but at least 8 blocks per SM in all, so that smaller graphs still fill the GPU
     const double per_region = std::max(1.0, pl * (double)c->m / gsb);
-    const uint32_t rpb = (uint32_t)std::min(64.0, std::max(1.0, std::round(32768.0 / per_region)));
+    const double rpb_fill = std::floor((double)gsb * nb / (152.0 * 8.0));
+    const uint32_t rpb = (uint32_t)std::min({64.0, std::max(1.0, std::round(32768.0 / per_region)),
+                                             std::max(1.0, rpb_fill)});
     const unsigned gub = ((gsb + rpb - 1) / rpb) * nb;
 #define IM_SE(BB)                                                                                 \
     do {                                                                                          \

@@ -167,6 +167,16 @@ def test_bucketed_unions_over_many_regions(R):
         assert np.array_equal(g[key], r[key]), key
 
 
+def test_large_graph_adjacency_built_in_source_ranges():
+    # from 2^24 edges the static adjacency is built in two passes (arcs binned by source range,
+    # then placed range by range); the searches of the selection walk it: seeds, gains, spread,
+    # compact sketches and labels equal the oracle's
+    n, u, v = graphgen.erdos_renyi(1 << 20, (1 << 24) + 4097, 7)
+    g = _run(n, u, v, 42, 0.05, 8, 0.1, 5)
+    o = _oracle(n, u, v, 42, 0.05, 8, 0.1, 5)
+    _compare(g, o, 5)
+
+
 def test_automatic_union_path():
     # IM_UNION_AUTO (the default) takes the record path while a batch's parent arrays fit in
     # 256 MiB and the bucketed path beyond
