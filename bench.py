@@ -148,15 +148,14 @@ def _kernel_digest(name: str, fn: str) -> str:
 
 def _traffic(kernel: str, units_per_launch: float, path: str = "records"):
     """DRAM bytes per launch from the committed ncu summary, if taken on the current source.
-    The sampling and union entries of the bucketed path ("@buckets") are those of its own
-    kernels (k_sample_bucket, k_union_bucket)."""
+    An entry "name@path" (the bucketed path's own sampling, union and compression kernels)
+    takes precedence over "name" for builds on that union path."""
     f = PROFILES / "dram_traffic.json"
     if not f.exists():
         return None
-    if path == "buckets" and kernel in ("sample_emit", "union"):
-        kernel += "@buckets"
     try:
-        d = json.loads(f.read_text()).get(kernel)
+        table = json.loads(f.read_text())
+        d = table.get(f"{kernel}@{path}") or table.get(kernel)
         if not d or d.get("kernel_sha1") != _kernel_digest(d["source"], d["function"]):
             return None
         return d["bytes_per_unit"] * units_per_launch
