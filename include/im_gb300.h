@@ -59,7 +59,9 @@ int im_create(im_ctx** out, uint32_t n, uint64_t m, const uint32_t* u, const uin
 
 /*
  * im_load_graph -- replace the context's graph by another edge list (same conventions as
- * im_create; host lists are copied through a staging buffer the context keeps).  Device
+ * im_create; page-locked host lists that the device can address are read in place by the
+ * packing kernel, other host lists are copied through a staging buffer the context keeps;
+ * either way the call returns after the lists were read).  Device
  * buffers are reused while n and m are unchanged, and the sketch buffers and selection graph
  * of the next im_build_sketches too when its shapes are; a long-lived context thus serves one
  * graph after another without allocating.  The sketches and any selection are discarded:

@@ -191,6 +191,21 @@ static int load_graph(im_ctx* c, const uint32_t* u, const uint32_t* v, int ptr_k
     const uint64_t m = c->m;
     const uint32_t *pu = u, *pv = v;
     if (ptr_kind == IM_PTR_HOST && m > 0) {
+        // page-locked lists that the device can address (the runtime gives a device pointer for
+        // them) are read by the packing kernel in place, over the CPU-GPU link: no staging copy
+        cudaPointerAttributes au{}, av{};
+        const bool mapped = cudaPointerGetAttributes(&au, u) == cudaSuccess && au.type == cudaMemoryTypeHost &&
+                            au.devicePointer && cudaPointerGetAttributes(&av, v) == cudaSuccess &&
+                            av.type == cudaMemoryTypeHost && av.devicePointer;
+        cudaGetLastError();
+        if (mapped) {
+            const int rc = im_graph_build(c, static_cast<const uint32_t*>(au.devicePointer),
+                                          static_cast<const uint32_t*>(av.devicePointer));
+            if (rc == IM_OK) c->graph_ok = true;
+            return rc;
+        }
+    }
+    if (ptr_kind == IM_PTR_HOST && m > 0) {
         if (c->upload_cap < m) {
             dfree(c->d_upload);
             if (c->h_upload) cudaFreeHost(c->h_upload);
