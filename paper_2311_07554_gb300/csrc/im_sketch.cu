@@ -696,7 +696,7 @@ template <int kSpec> struct GainUnroll { static constexpr int value = kSpec > 0 
 // the candidate first seeds (their roots per sketch staged in shared memory).  kSpec is the
 // capacity of the per-thread overlap accumulators (0, 4 or 8; nspec <= kSpec).
 template <bool kAll, int kSpec>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, kSpec > 0 ? 6 : 8)
 k_gain_compact(const uint32_t* __restrict__ parent, const uint64_t* __restrict__ word, uint32_t n,
                uint32_t nb, uint32_t r0, uint32_t R, uint64_t* __restrict__ gain, int first,
                const uint32_t* __restrict__ cidx, uint32_t* __restrict__ label,
