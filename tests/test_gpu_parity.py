@@ -452,6 +452,32 @@ def test_first_seed_speculation_gives_the_same_selection(candidates, graph, lane
     assert e.value.code == im.IM_EINVAL
 
 
+def test_page_locked_host_lists_are_read_in_place():
+    """Edge lists in page-locked host memory (torch pin_memory) are read by the packing kernel
+    where they are, without a staging copy: the results equal the oracle's, for a new context
+    and for a graph loaded into an existing one; a bad id in such a list is still refused."""
+    n, u, v = graphgen.erdos_renyi(1500, 6001, 3)
+    pu = torch.from_numpy(u.view(np.int32)).pin_memory()
+    pv = torch.from_numpy(v.view(np.int32)).pin_memory()
+    o = _oracle(n, u, v, 42, 0.1, 45, 0.2, 5)
+    with im.IMContext(n, pu, pv) as ctx:
+        ctx.build_sketches(45, 42, 0.1, 0.2)
+        s1, g1 = ctx.select_seeds(5)
+        n2, u2, v2 = graphgen.erdos_renyi(900, 5000, 5)
+        ctx.load_graph(n2, torch.from_numpy(u2.view(np.int32)).pin_memory(),
+                       torch.from_numpy(v2.view(np.int32)).pin_memory())
+        ctx.build_sketches(45, 42, 0.1, 0.2)
+        s2, g2 = ctx.select_seeds(5)
+        bad = pv.clone().pin_memory()
+        bad[17] = n + 3
+        with pytest.raises(im.IMError) as e:
+            ctx.load_graph(n, pu, bad)
+        assert e.value.code == im.IM_EINVAL
+    assert np.array_equal(s1, o["seeds"]) and np.array_equal(g1, o["seed_gains"])
+    o2 = _oracle(n2, u2, v2, 42, 0.1, 45, 0.2, 5)
+    assert np.array_equal(s2, o2["seeds"]) and np.array_equal(g2, o2["seed_gains"])
+
+
 def test_load_graph_serves_one_graph_after_another():
     """One context, several graphs (same n and m: buffers and selection graph reused; other
     sizes: reallocated; host and device edge lists): each gives the results of a fresh
