@@ -66,3 +66,24 @@ def test_cuda_arm_fails_without_a_gpu():
     r = _run("--steps", "1", "--warmup", "0")
     assert r.returncode != 0
     assert not _json_lines(r.stdout)
+
+
+def test_dram_traffic_entries_match_the_current_kernels():
+    # every committed ncu figure names the kernel it was taken on and that kernel's source
+    # digest; a kernel edited since its capture makes the bench report null traffic, so the
+    # committed table is checked to be current.  Builds on the bucketed path take the
+    # "@buckets" entries (their own sampling, union and compression kernels).
+    sys.path.insert(0, str(ROOT))
+    import bench
+    table = json.loads((ROOT / "profiles" / "dram_traffic.json").read_text())
+    for key, d in table.items():
+        assert d["kernel_sha1"] == bench._kernel_digest(d["source"], d["function"]), key
+        assert (ROOT / "profiles" / d["profile"]).exists(), key
+    for name in ("sample_emit", "union", "compress_count"):
+        b = table[name + "@buckets"]["bytes_per_unit"]
+        assert bench._traffic(name, 1000.0, "buckets") == pytest.approx(1000.0 * b)
+        r = table[name]["bytes_per_unit"]
+        assert bench._traffic(name, 1000.0, "records") == pytest.approx(1000.0 * r)
+    assert table["sample_emit@buckets"]["function"] == "k_sample_bucket"
+    assert table["union@buckets"]["function"] == "k_union_bucket"
+    assert table["compress_count"]["function"] == "k_compress_queue"
