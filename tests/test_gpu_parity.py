@@ -562,6 +562,47 @@ def test_per_edge_probabilities_match_the_oracle(model, alpha, threshold):
         assert ctx.spread(seeds) == oracle.spread(L, seeds) == int(o_gains.sum())
 
 
+@pytest.mark.parametrize("path", [0, 1, 2])
+@pytest.mark.parametrize("model", ["u13", "wic"])
+def test_per_edge_probabilities_on_every_union_path(model, path):
+    """The per-edge thresholds through each union path (the bucketed sampler reads them in
+    pairs with the edges, as the others do): equal to the oracle."""
+    n, u, v = graphgen.chung_lu(20000, 100000, 2.1, 2000.0, 6)
+    G = oracle.Graph(n, u, v)
+    p = _edge_probs(model, G, len(u))
+    R, seed, k, alpha = 40, 43, 8, 0.1
+    L = G.labels(seed, -1.0, R, mode=oracle.MODE_EDGE)
+    ctr = oracle.centers(n, seed, alpha)
+    lab, sz = oracle.compact(L, ctr)
+    o_seeds, o_gains = oracle.greedy(L, k)
+    with im.IMContext(n, u, v) as ctx:
+        im.im_set_union_path(ctx.h, path)
+        if model == "wic":
+            ctx.set_edge_probs(im.IM_PROBS_WIC)
+        else:
+            ctx.set_edge_probs(im.IM_PROBS_ARRAY, p)
+        ctx.build_sketches(R, seed, 0.5, alpha)
+        assert ctx.stats()["union_path"] == path
+        for r in (0, 39):
+            assert np.array_equal(ctx.labels(r), L[r]), r
+        assert np.array_equal(ctx.gains(), oracle.gains(L))
+        g_lab, g_sz = ctx.compact()
+        assert np.array_equal(g_lab, lab) and np.array_equal(g_sz, sz)
+        seeds, gains = ctx.select_seeds(k)
+        assert np.array_equal(seeds, o_seeds) and np.array_equal(gains, o_gains)
+
+
+@pytest.mark.parametrize("path", [0, 1, 2])
+def test_p_zero_and_p_one_on_every_union_path(path):
+    # no live edge, and every edge live (all pairs become records: the record paths' capacity
+    # is sized for it), through each union path
+    n, u, v = graphgen.erdos_renyi(700, 2100, 8)
+    for p in (0.0, 1.0):
+        g = _run_path(n, u, v, 42, p, 33, 0.25, 4, path)
+        o = _oracle(n, u, v, 42, p, 33, 0.25, 4)
+        _compare(g, o, 4)
+
+
 def test_per_edge_probability_api():
     n, u, v = graphgen.erdos_renyi(2000, 8000, 21)
     R, seed, p0 = 32, 9, 0.15
