@@ -2,8 +2,10 @@
 //
 // Batches of B sketches share one pass over the edge list.  Per sketch b of a batch:
 //   init        P[b][v] = v;  W[b][v] = (key = lk(v), count = 1)
-//   sample      every live (edge, sketch) pair of the batch becomes a record (u, v, b)
-//   union       one thread per record, Rem's union with splicing (parents below children)
+//   sample      every live (edge, sketch) pair of the batch becomes a record (u, v, b), or on
+//               the bucketed path (large graphs) a record (u, v) in a region of sketch b
+//   union       one thread per record, Rem's union with splicing (parents below children);
+//               the bucketed path unites the sketches one after the other
 //   compress    P[b][v] <- root; per root, for every other member: count += 1 and
 //               key = min over members of the
 //               label key of its centers (center index) -- with every vertex a center this
@@ -12,7 +14,9 @@
 //               root (the smallest center index in its component), size[i] = count if
 //               label[i] = i, else 0 (Alg. 3)
 // W[b][x] is one 64-bit word per root: low half = component size (bit 31 is the "holds a
-// seed" flag of the recomputation evaluator), high half = the component's minimum key.
+// seed" flag of the recomputation evaluator), high half = the component's minimum key.  A
+// root with members carries kRootFlag on its own parent entry, so that the gain pass knows
+// singletons (size 1, own key) without reading their root words.
 #include <algorithm>
 
 #include "im_internal.cuh"
