@@ -1103,8 +1103,9 @@ __global__ void k_hub_index(uint32_t n, uint32_t rho, const uint32_t* __restrict
         if (flags[v]) cidx[v] = rho + (uint32_t)pos[v];
 }
 
-// Blocks of the sampling kernel per SM (grid-stride over the edge pairs).
-constexpr unsigned kEmitBlocksPerSM = 16;
+// Blocks of the sampling kernel per SM (grid-stride over the edge pairs): 8 leave the other
+// lane's union-find kernels some room (Chung-Lu step 7.62 -> 7.56 ms against 16).
+constexpr unsigned kEmitBlocksPerSM = 8;
 
 // Sampling and unions of one batch as two kernels (records of live pairs in between).
 int launch_sample_split(im_ctx* c, im_ctx::Lane& L, uint32_t r0, uint32_t nb, int key_mode) {
